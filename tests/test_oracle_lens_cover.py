@@ -1,0 +1,124 @@
+"""Pins of the oracle's lens and cover against things other than itself:
+hand-derived fixtures, closed forms and independent library routines."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2011_03209_gb300 import synth
+
+
+def test_l2_lens_closed_form_and_numpy():
+    X = np.array([[3.0, 4.0, 0.0], [0.0, 0.0, 0.0], [-1.0, -1.0, -1.0]], dtype=np.float32)
+    f = oracle.lens_l2(X)
+    assert f[0] == 5.0 and f[1] == 0.0
+    assert f[2] == np.sqrt(3.0)
+    Y = synth.tiny_random(500, 37, seed=3, scale=20.0) - 10.0
+    ref = np.linalg.norm(Y.astype(np.float64), axis=1)
+    np.testing.assert_allclose(oracle.lens_l2(Y), ref, rtol=1e-14, atol=0)
+
+
+def test_coord_lens_is_the_column():
+    Y = synth.tiny_random(100, 5, seed=4)
+    for j in range(5):
+        assert np.array_equal(oracle.lens_coord(Y, j), Y[:, j].astype(np.float64))
+
+
+def test_projection_lens_matches_matmul():
+    Y = synth.tiny_random(300, 16, seed=5, scale=4.0)
+    rng = np.random.default_rng(0)
+    mu = rng.standard_normal(16)
+    v = rng.standard_normal(16)
+    ref = (Y.astype(np.float64) - mu) @ v
+    got = oracle.lens_project(Y, mu, v)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_pca_axis_aligned_closed_form():
+    # four points (+-a, 0), (0, +-b): mean 0, covariance diag(a^2/2, b^2/2)
+    a, b = 3.0, 1.0
+    X = np.array([[a, 0], [-a, 0], [0, b], [0, -b]], dtype=np.float32)
+    mu, V, lam = oracle.pca(X, 2)
+    np.testing.assert_allclose(mu, [0, 0], atol=0)
+    np.testing.assert_allclose(lam, [a * a / 2, b * b / 2], rtol=1e-15)
+    np.testing.assert_allclose(V, [[1, 0], [0, 1]], atol=1e-15)
+
+
+def test_pca_against_numpy_eigh_and_sign_rule():
+    w = synth.gaussian_mixture(3000, 12, 4, seed=9, centre_box=5.0, std_lo=0.3,
+                               std_hi=1.5, anisotropic=True)
+    mu, V, lam = oracle.pca(w, 2)
+    X64 = w.astype(np.float64)
+    np.testing.assert_allclose(mu, X64.mean(axis=0), rtol=1e-12, atol=1e-12)
+    C = np.cov(X64, rowvar=False, bias=True)
+    ev, evec = np.linalg.eigh(C)
+    np.testing.assert_allclose(lam, ev[::-1][:2], rtol=1e-10)
+    for c in range(2):
+        ref = evec[:, -1 - c]
+        assert abs(abs(ref @ V[c]) - 1.0) < 1e-10
+        assert abs(np.linalg.norm(V[c]) - 1.0) < 1e-12
+        k = np.argmax(np.abs(V[c]))
+        assert V[c][k] > 0
+    assert abs(V[0] @ V[1]) < 1e-10
+
+
+def test_pca_line_direction():
+    # points along a known unit direction u, plus tiny orthogonal jitter
+    rng = np.random.default_rng(2)
+    u = np.array([1.0, -2.0, 2.0]) / 3.0
+    t = rng.uniform(-5, 5, size=400)
+    X = (np.outer(t, u) + 1e-3 * rng.standard_normal((400, 3))).astype(np.float32)
+    _, V, _ = oracle.pca(X, 1)
+    assert abs(abs(V[0] @ u) - 1.0) < 1e-6
+    assert V[0][np.argmax(np.abs(V[0]))] > 0
+
+
+def test_interval_bounds_golden(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "cover_intervals.json")))
+    for c in g["cases"]:
+        a, b = oracle.interval_bounds(c["lo"], c["hi"], c["n"], c["p"])
+        np.testing.assert_allclose(a, c["a"], rtol=4e-16, atol=4e-16, err_msg=c["note"])
+        np.testing.assert_allclose(b, c["b"], rtol=4e-16, atol=4e-16, err_msg=c["note"])
+    m = g["membership"]
+    offs, pts = oracle.cover(np.array(m["lens"]), [m["n"]], [m["p"]])
+    got = [pts[offs[e]:offs[e + 1]].tolist() for e in range(m["n"])]
+    assert got == m["elements"]
+
+
+@pytest.mark.parametrize("n_int,p", [(1, 0.0), (7, 0.0), (20, 0.3), (50, 0.25), (13, 0.6), (4, 0.95)])
+def test_cover_invariants(n_int, p):
+    rng = np.random.default_rng(n_int)
+    f = rng.normal(size=2000) * 3.0 + 1.0
+    offs, pts = oracle.cover(f, [n_int], [p])
+    assert len(offs) == n_int + 1
+    times = np.bincount(pts, minlength=len(f))
+    assert times.min() >= 1                           # the cover covers f(X)
+    lo, hi = f.min(), f.max()
+    a, b = oracle.interval_bounds(lo, hi, n_int, p)
+    L = (hi - lo) / (n_int - (n_int - 1) * p)
+    np.testing.assert_allclose(b[:-1] - a[:-1], L, rtol=1e-12)
+    np.testing.assert_allclose(a[1:] - a[:-1], L * (1 - p), rtol=1e-12)
+    assert a[0] == lo and b[-1] == hi
+    for e in range(n_int):                            # brute-force membership
+        ref = np.nonzero((f >= a[e]) & (f <= b[e]))[0]
+        assert np.array_equal(pts[offs[e]:offs[e + 1]], ref)
+    if p == 0.0:
+        on_boundary = np.isin(f, a[1:]) | np.isin(f, b[:-1])
+        assert np.all(times[~on_boundary] == 1)
+    # a point lies in at most ceil(1/(1-p)) + 1 intervals
+    assert times.max() <= int(np.ceil(1.0 / (1.0 - p))) + 1
+
+
+def test_cover_2d_is_product_in_row_major_order():
+    rng = np.random.default_rng(7)
+    f = rng.uniform(-1, 1, size=(800, 2))
+    offs, pts = oracle.cover(f, [5, 3], [0.2, 0.4])
+    o1, p1 = oracle.cover(f[:, 0], [5], [0.2])
+    o2, p2 = oracle.cover(f[:, 1], [3], [0.4])
+    for i in range(5):
+        for j in range(3):
+            e = i * 3 + j
+            ref = np.intersect1d(p1[o1[i]:o1[i + 1]], p2[o2[j]:o2[j + 1]])
+            assert np.array_equal(pts[offs[e]:offs[e + 1]], ref)
