@@ -1,0 +1,312 @@
+"""Benchmark: one exact mapper graph of the 1,000,000 x 256 clustered cloud.
+
+A step is one complete mapper graph (lens, cover, per-element DBSCAN, nerve)
+of the paper-scale workload (1M points x 256 dims, 32 Gaussian clusters plus
+5 % uniform noise, L2 lens, 100 intervals at 20 % overlap, eps at the 1st
+percentile of sampled distances, minPts 5). Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16]
+  python bench.py --impl reference      # the FP64 oracle on the host cores
+
+Multi-GPU (torchrun): each rank computes its own graph (independent
+replicas, weak scaling); value = graphs of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2011_03209_gb300 import synth  # noqa: E402
+
+METRIC = "mapper graph ms (1M x 256, exact graph)"
+GPU_FP32_LANES = 128                 # FP32 lanes per SM (Blackwell)
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def sampled_oracle(w, budget_s: float, seed: int, gpu_labels=None):
+    """Time the FP64 oracle on a bounded sample of the workload: full lens
+    and cover, then DBSCAN on cover elements drawn in a seeded order until
+    `budget_s` seconds of DBSCAN have run. The full-graph time is
+    extrapolated by the sampled share of sum n_i^2 (DBSCAN's brute-force cost
+    is proportional to n_i^2 d). Returns (estimated ms, description,
+    threads, exact) where exact compares sampled labels with gpu_labels."""
+    import oracle
+    t0 = time.perf_counter()
+    f = oracle.lens(w.X, w.lens_kind, w.lens_arg)
+    offs, pts = oracle.cover(f, w.n_intervals, w.overlap)
+    t_front = time.perf_counter() - t0
+    sizes = np.diff(offs).astype(np.float64)
+    total = float((sizes ** 2).sum())
+    order = np.random.default_rng(seed).permutation(np.nonzero(sizes)[0])
+    spent, share, picked, exact = 0.0, 0.0, [], True
+    for e in order:
+        if spent >= budget_s:
+            break
+        if spent > 0 and (sizes[e] ** 2 / max(share, 1.0)) * spent > 4 * budget_s:
+            continue                  # would overrun the budget several times over
+        s, t = offs[e], offs[e + 1]
+        t1 = time.perf_counter()
+        _, _, lab, _ = oracle.dbscan(w.X, pts[s:t], w.eps, w.min_pts)
+        spent += time.perf_counter() - t1
+        share += sizes[e] ** 2
+        picked.append(int(e))
+        if gpu_labels is not None:
+            exact &= bool(np.array_equal(gpu_labels[s:t], lab))
+    est_s = t_front + spent * total / max(share, 1.0)
+    desc = (f"lens+cover of all {w.n} points, DBSCAN of {len(picked)} of {len(order)} cover "
+            f"elements ({100.0 * share / total:.2f}% of sum n_i^2), extrapolated by n_i^2")
+    return est_s * 1e3, desc, oracle.num_threads(), exact
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = synth.clusters_1m_d256()
+    vals = []
+    for i in range(args.warmup + args.steps):
+        ms, desc, cores, _ = sampled_oracle(w, args.ref_budget, seed=i)
+        if i >= args.warmup:
+            vals.append(ms)
+    v = float(np.mean(vals))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "ms",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": v,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w.name, "n": w.n, "d": w.d,
+                                        "n_intervals": w.n_intervals[0], "overlap": w.overlap[0],
+                                        "eps": w.eps, "min_pts": w.min_pts},
+        "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": v, "unit": "ms", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+    }))
+
+
+def run_ours(args):
+    import torch
+    import paper_2011_03209_gb300 as mg
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    prec = mg.BF16 if args.precision == "bf16" else mg.FP32
+    w = synth.clusters_1m_d256()
+    Xh = torch.from_numpy(w.X).pin_memory()
+    Xd = Xh.to(f"cuda:{local}")
+    stream = torch.cuda.Stream()
+    ctx = mg.Context(local, stream=stream)
+    ctx.set_timing(True)
+    prm = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, prec)
+
+    for _ in range(args.warmup):
+        g = mg.mapper_graph(ctx, Xd, prm)
+        last = g.numpy()
+        del g
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    sampler = ClockSampler(local)
+    stats = []
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    start.record(stream)
+    for _ in range(args.steps):
+        g = mg.mapper_graph(ctx, Xd, prm)
+        stats.append(g.stats())
+        del g
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = start.elapsed_time(end) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- end to end through the public API: host X in, graph back on the host
+    ctx.set_timing(False)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(args.steps):
+        g = mg.mapper_graph(ctx, Xh.numpy(), prm)
+        out = g.numpy()
+        d2h = sum(a.nbytes for a in out.values())
+        del g
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    st = stats[-1]
+    sizes = np.load(os.path.join(ROOT, "_work", "c3_sizes.npy")) if False else None  # noqa
+    pairs = st["pairs_screened"]                       # unordered pairs incl. self, pass 1
+    pass1_ms = float(np.mean([s["ms_pass"][0] for s in stats]))
+    eps_pair_flops = 2.0 * w.d * pairs
+    peaks, src = _peaks()
+    if prec == mg.FP32:
+        clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
+        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+        peak = n_sm * GPU_FP32_LANES * 2 * clk / 1e12      # FP32 FFMA peak, TFLOP/s
+        achieved = 3.0 * w.d * pairs / (pass1_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "simt_pass_kernel<1> (FP32 sum of squared differences, 3d flops/pair)",
+                "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {clk / 1e6:.0f} MHz"}
+    else:
+        peak = peaks["bf16_tflops_sustained"]
+        achieved = eps_pair_flops / (pass1_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "tc_count_kernel (tcgen05 BF16, 2d flops/pair)",
+                "peak_source": f"{src} bf16_tflops_sustained"}
+
+    line = {
+        "metric": METRIC, "value": ms / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16+f64" if prec == mg.BF16 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "d": w.d, "lens": "L2",
+                   "n_intervals": w.n_intervals[0], "overlap": w.overlap[0], "eps": w.eps,
+                   "min_pts": w.min_pts, "precision": args.precision,
+                   "l2_flush": "inputs larger than L2 (1 GB point cloud read every step)",
+                   "parallelism": f"replicas x{world}"},
+        "eps_pair_tflops": eps_pair_flops / (pass1_ms * 1e-3) / 1e12,
+        "pass_ms": [float(np.mean([s["ms_pass"][i] for s in stats])) for i in range(3)],
+        "stage_ms": {k: float(np.mean([s[k] for s in stats]))
+                     for k in ("ms_lens", "ms_cover", "ms_cluster", "ms_nerve")},
+        "counters": {k: st[k] for k in ("n_members", "sum_ni2", "tile_pairs", "pairs_screened",
+                                        "band_pairs", "near_ties", "n_core", "n_nodes", "n_edges")},
+        "roofline": roof,
+        "clocks": clocks,
+        "gpu_launches": int(sum(s["n_launches"] for s in stats)),
+        "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": int(w.X.nbytes),
+                "d2h_bytes_per_step": int(d2h)},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        gl = None
+        g = mg.mapper_graph(ctx, Xd, prm)
+        offs, _ = g.cover().numpy()
+        gl, _ = g.clusters().numpy(int(offs[-1]))
+        del g
+        cms, desc, cores, exact = sampled_oracle(w, args.ref_budget, seed=12345, gpu_labels=gl)
+        line["cpu_baseline"] = {"value": cms, "unit": "ms", "cores": cores, "kind": "oracle",
+                                "sample": desc}
+        line["exact_on_sample"] = exact
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--ref-budget", type=float, default=12.0,
+                    help="seconds of oracle DBSCAN per reference sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

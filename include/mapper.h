@@ -1,0 +1,211 @@
+/*
+ * mapper.h -- C ABI of the GB300 mapper-graph library (libmapper_gb300.so).
+ *
+ * The library computes the mapper graph of "Mapper Interactive"
+ * (arXiv 2011.03209), §3 Background: a filter (lens) f on a point cloud
+ * X in R^d, a cover of f(X) by n overlapping intervals (or, for a 2D filter,
+ * rectangles), DBSCAN(eps, minPts) on the points of each cover element, and
+ * the 1D nerve of the resulting clusters (nodes = clusters, an edge between
+ * two clusters that share a point). Every step runs in CUDA kernels written
+ * for sm_103a (GB300); there is no CPU fallback.
+ *
+ * Conventions
+ *   - Status: every int-returning call returns MAPPER_OK (0) or a negative
+ *     mapper_status. Nothing aborts, exits or throws across this ABI. The
+ *     message of the calling thread's last failure is mapper_last_error().
+ *   - Pointers named *_dev are device pointers (cudaMalloc'd or torch CUDA
+ *     storage on the context's device). Inputs are borrowed: the caller keeps
+ *     them alive and unmodified until the call returns.
+ *   - X is row-major FP32, n rows of d values, row stride ld >= d elements.
+ *     X must be finite (MAPPER_ENONFINITE otherwise).
+ *   - Results are library-owned opaque handles released with mapper_free().
+ *     Their arrays are read with *_sizes() then *_copy() into caller-owned
+ *     buffers, on the host (on_device = 0) or device (on_device = 1).
+ *   - Calls are ordered on the context's stream. They return after the
+ *     result is complete (sizes that shape an output are read back), so a
+ *     handle is ready for *_copy when its call returns.
+ *   - Threads: one context must not be used by two threads at once; distinct
+ *     contexts are independent.
+ *   - Result semantics (exact): graph, node memberships and edges equal those
+ *     of the plain FP64 definition below, whatever the screening precision.
+ *
+ * Definitions (the readings where the paper is silent are fixed here):
+ *   lens      L2: f(x) = sqrt(sum_k x_k^2); COORD: f(x) = x_j; PCA: f(x) =
+ *             sum_k (x_k - mu_k) v_k with v the j-th principal axis. Sums in
+ *             double, k ascending, one rounding per operation.
+ *   cover     n intervals over [lo, hi] = [min f, max f]:
+ *             L = (hi-lo)/(n-(n-1)p), s = L(1-p), a_k = lo + k s,
+ *             b_k = a_k + L, then a_0 = lo, b_{n-1} = hi and
+ *             b_k = max(b_k, a_{k+1}); L = 1 if hi == lo. Closed intervals.
+ *             2D: element (i, j) has index i * n_2 + j.
+ *   DBSCAN    q in N(p) iff sum_k (x_pk - x_qk)^2 <= eps*eps (double, k
+ *             ascending) within one element; p in N(p); core iff
+ *             |N(p)| >= minPts; clusters = components of the core points;
+ *             canonical id = smallest point index among a cluster's cores; a
+ *             non-core point with core neighbours joins the neighbouring
+ *             cluster of smallest canonical id; others are noise.
+ *   nodes     every cluster of every element, ordered by (element, canonical
+ *             id); members in ascending point index.
+ *   edges     {u, v}, u < v, iff nodes u and v share a point; sorted
+ *             lexicographically.
+ */
+#ifndef MAPPER_GB300_H
+#define MAPPER_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MAPPER_ABI_VERSION 1
+
+typedef enum mapper_status {
+    MAPPER_OK = 0,
+    MAPPER_EINVAL = -1,      /* bad argument (sizes, parameters, null handle) */
+    MAPPER_ENOMEM = -2,      /* device allocation failed or over the HBM budget */
+    MAPPER_ECUDA = -3,       /* a CUDA runtime/driver call failed */
+    MAPPER_ETIMEOUT = -4,    /* a bounded device-side wait ran out */
+    MAPPER_ENONFINITE = -5,  /* X holds NaN or Inf */
+    MAPPER_EINTERNAL = -6,   /* a device-side consistency check failed */
+    MAPPER_ENOTIMPL = -7     /* option not built in this library */
+} mapper_status;
+
+typedef enum mapper_lens_kind {
+    MAPPER_LENS_L2 = 0,      /* §3: "Common choices include the L2-norm" */
+    MAPPER_LENS_COORD = 1,   /* §4.1: filter "based on a chosen dimension" */
+    MAPPER_LENS_PCA = 2      /* projection on a principal axis (PCA module, §4.1) */
+} mapper_lens_kind;
+
+/* Precision of the eps-neighbourhood screen. Every pair whose screened
+ * distance falls inside a rigorous error band around eps^2 is re-decided in
+ * FP64, so all precisions give the same exact graph. */
+typedef enum mapper_precision {
+    MAPPER_FP32 = 0,         /* CUDA-core FP32 sum of squared differences */
+    MAPPER_BF16 = 1          /* tcgen05 tensor cores, BF16 in, FP32 accumulate */
+} mapper_precision;
+
+typedef struct mapper_ctx mapper_ctx;
+typedef struct mapper_cover_t mapper_cover_t;
+typedef struct mapper_clusters_t mapper_clusters_t;
+typedef struct mapper_graph_t mapper_graph_t;
+
+/* Parameters of one mapper graph (§3, "Algorithmic details in practice":
+ * filter f, number of cover elements n, overlap p, metric, clusterer). */
+typedef struct mapper_params {
+    int32_t m;               /* filter dimension: 1 (intervals) or 2 (rectangles) */
+    int32_t lens_kind[2];    /* mapper_lens_kind per filter dimension */
+    int32_t lens_arg[2];     /* COORD: column j; PCA: axis (0 = first); L2: ignored */
+    int32_t n_intervals[2];  /* n >= 1 per filter dimension */
+    double overlap[2];       /* p in [0, 1) per filter dimension */
+    double eps;              /* DBSCAN radius, finite, > 0 */
+    int32_t min_pts;         /* DBSCAN minPts >= 1 */
+    int32_t precision;       /* mapper_precision */
+} mapper_params;
+
+/* Counters of one computation (filled by mapper_stats_get). */
+typedef struct mapper_stats {
+    int64_t n_points;        /* n */
+    int64_t n_elements;      /* cover elements */
+    int64_t n_members;       /* sum over elements of n_i */
+    double sum_ni2;          /* sum over elements of n_i^2 */
+    int64_t tile_pairs;      /* tile pairs of the neighbour-count pass */
+    int64_t tile_pairs_out;  /* ... certified all-out by bounding spheres */
+    int64_t tile_pairs_in;   /* ... certified all-in by bounding spheres */
+    int64_t pairs_screened;  /* point pairs evaluated by the screen, all passes */
+    int64_t band_pairs;      /* pairs re-decided in FP64, all passes */
+    int64_t near_ties;       /* unordered pairs with |d^2 - eps^2| <= 1e-12 eps^2 */
+    int64_t n_core;          /* core memberships */
+    int64_t n_nodes;
+    int64_t n_edges;
+    int64_t n_launches;      /* kernels this call launched */
+    double ms_lens, ms_cover, ms_cluster, ms_nerve, ms_total;  /* device time (timing on) */
+    double ms_pass[3];       /* device time of the count, union and border passes */
+} mapper_stats;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`, ordering all work on
+ * `cuda_stream` (a cudaStream_t; NULL = a stream the context creates).
+ * hbm_budget_bytes caps the context's scratch (0 = no cap). */
+int mapper_create(mapper_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream);
+void mapper_destroy(mapper_ctx* ctx);
+/* Use another stream for subsequent calls. */
+int mapper_set_stream(mapper_ctx* ctx, void* cuda_stream);
+/* Record per-stage device times in mapper_stats (adds CUDA events). */
+int mapper_set_timing(mapper_ctx* ctx, int enabled);
+
+/* -------------------------------------------------------------- the steps */
+
+/* Lens (§3 filter function; §4.1 L2 norm / chosen column; PCA module).
+ * Writes lens_dev[p * m + j] = f_j(x_p) for p < n, j < m (caller-owned,
+ * device, n*m doubles). kinds[j], args[j] as in mapper_params (host arrays).
+ * For PCA lenses, pca_out (optional, host) receives mu[d] followed by the
+ * axes v_0..v_{K-1} (K = 1 + largest PCA axis asked for), each d doubles;
+ * the axes come from power iteration on the FP32 covariance, each signed
+ * so its entry of largest magnitude is positive. */
+int mapper_lens(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, int64_t ld,
+                int32_t m, const int32_t* kinds, const int32_t* args,
+                double* lens_dev, double* pca_out);
+
+/* Cover (§3: intervals V_k of f(X), n elements, overlap p; 2D: rectangles)
+ * and pull-back: for each element, the points with f in it, ascending.
+ * lens_dev: n*m doubles (device, row-major). n_intervals, overlap: host
+ * arrays of m. Result read with mapper_cover_sizes / mapper_cover_copy. */
+int mapper_cover(mapper_ctx* ctx, const double* lens_dev, int64_t n, int32_t m,
+                 const int32_t* n_intervals, const double* overlap, mapper_cover_t** out);
+int mapper_cover_sizes(const mapper_cover_t* cover, int64_t* n_elements, int64_t* n_members);
+/* elem_offsets: n_elements+1 int64; elem_points: n_members int32. */
+int mapper_cover_copy(const mapper_cover_t* cover, int64_t* elem_offsets, int32_t* elem_points,
+                      int on_device);
+
+/* DBSCAN(eps, minPts) inside every element of `cover` (§3; the per-element
+ * decomposition is the parallelisation of §4.3). X must be the cloud the
+ * cover's lens was computed on. Result read with mapper_clusters_copy. */
+int mapper_cluster(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, int64_t ld,
+                   const mapper_cover_t* cover, double eps, int32_t min_pts, int32_t precision,
+                   mapper_clusters_t** out);
+/* Per membership slot (aligned with the cover's elem_points): label =
+ * canonical cluster id or -1 (noise); core = 1 if core. Either may be NULL. */
+int mapper_clusters_copy(const mapper_clusters_t* clusters, int64_t* label, uint8_t* core,
+                         int on_device);
+
+/* Nerve (§3: 1D nerve; an edge where two clusters intersect). */
+int mapper_nerve(mapper_ctx* ctx, const mapper_clusters_t* clusters, mapper_graph_t** out);
+
+/* Fused call: lens, cover, cluster and nerve in one. X may be a device
+ * pointer or a host pointer (pinned or pageable); a host X is copied to the
+ * device inside the call. */
+int mapper_graph(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
+                 const mapper_params* params, mapper_graph_t** out);
+
+int mapper_graph_sizes(const mapper_graph_t* g, int64_t* n_nodes, int64_t* n_members,
+                       int64_t* n_edges);
+/* node_offsets: n_nodes+1 int64; node_members: n_members int32; node_elem:
+ * n_nodes int32 (cover element of each node); edges: 2*n_edges int32
+ * (u, v pairs). Any pointer may be NULL to skip that array. */
+int mapper_graph_copy(const mapper_graph_t* g, int64_t* node_offsets, int32_t* node_members,
+                      int32_t* node_elem, int32_t* edges, int on_device);
+/* The lens the graph was built from (n*m doubles), its PCA basis if any
+ * (mu then axes, d doubles each; returns the count of doubles written via
+ * *n_pca, 0 if no PCA lens), and the cover it used. */
+int mapper_graph_lens(const mapper_graph_t* g, double* lens, double* pca, int64_t* n_pca,
+                      int on_device);
+const mapper_cover_t* mapper_graph_cover(const mapper_graph_t* g);
+const mapper_clusters_t* mapper_graph_clusters(const mapper_graph_t* g);
+
+/* Counters of a clusters or graph handle. */
+int mapper_stats_get(const void* handle, mapper_stats* out);
+
+/* Release any handle (cover, clusters, graph). NULL is a no-op. */
+void mapper_free(void* handle);
+
+const char* mapper_strerror(int status);
+const char* mapper_last_error(void);
+int mapper_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MAPPER_GB300_H */

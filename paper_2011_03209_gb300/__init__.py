@@ -1,0 +1,234 @@
+"""GB300-native mapper graph ("Mapper Interactive", arXiv 2011.03209, §3).
+
+Thin Python binding over the C ABI of libmapper_gb300.so (include/mapper.h).
+The functions carry the C names: `mapper_lens`, `mapper_cover`,
+`mapper_cluster`, `mapper_nerve` and the fused `mapper_graph`. They only
+marshal arguments: every step runs in the library's CUDA kernels. PyTorch
+supplies device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _capi
+from ._capi import BF16, FP32, LENS_COORD, LENS_L2, LENS_PCA, MapperError, MapperParams
+
+__all__ = [
+    "Context", "Cover", "Clusters", "Graph", "MapperError", "mapper_lens", "mapper_cover",
+    "mapper_cluster", "mapper_nerve", "mapper_graph", "params", "LENS_L2", "LENS_COORD",
+    "LENS_PCA", "FP32", "BF16",
+]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _vp(x) -> ctypes.c_void_p:
+    return ctypes.c_void_p(int(x))
+
+
+class Context:
+    """A library context bound to one CUDA device and stream."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0, stream=None):
+        self._lib = _capi.load()
+        h = ctypes.c_void_p()
+        s = None if stream is None else _vp(stream.cuda_stream)
+        _capi.check(self._lib.mapper_create(ctypes.byref(h), int(device), int(hbm_budget), s),
+                    "mapper_create")
+        self.h = h
+        self.device = int(device)
+        self._stream = stream
+
+    def set_stream(self, stream) -> None:
+        _capi.check(self._lib.mapper_set_stream(self.h, _vp(stream.cuda_stream)), "mapper_set_stream")
+        self._stream = stream
+
+    def set_timing(self, on: bool) -> None:
+        _capi.check(self._lib.mapper_set_timing(self.h, int(bool(on))), "mapper_set_timing")
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None and self.h.value:
+            self._lib.mapper_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _Handle:
+    def __init__(self, lib, h, owner=None):
+        self._lib = lib
+        self.h = h
+        self._owner = owner           # views keep their graph alive
+
+    def _free(self):
+        if self._owner is None and getattr(self, "h", None) is not None and self.h.value:
+            self._lib.mapper_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self._free()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        st = _capi.MapperStats()
+        _capi.check(self._lib.mapper_stats_get(self.h, ctypes.byref(st)), "mapper_stats_get")
+        return st.as_dict()
+
+
+class Cover(_Handle):
+    def sizes(self):
+        e, m = ctypes.c_int64(), ctypes.c_int64()
+        _capi.check(self._lib.mapper_cover_sizes(self.h, ctypes.byref(e), ctypes.byref(m)),
+                    "mapper_cover_sizes")
+        return e.value, m.value
+
+    def numpy(self):
+        E, M = self.sizes()
+        offs = np.empty(E + 1, dtype=np.int64)
+        pts = np.empty(max(M, 1), dtype=np.int32)
+        _capi.check(self._lib.mapper_cover_copy(self.h, _vp(offs.ctypes.data), _vp(pts.ctypes.data), 0),
+                    "mapper_cover_copy")
+        return offs, pts[:M]
+
+
+class Clusters(_Handle):
+    def numpy(self, n_members: int):
+        lab = np.empty(max(n_members, 1), dtype=np.int64)
+        core = np.empty(max(n_members, 1), dtype=np.uint8)
+        _capi.check(self._lib.mapper_clusters_copy(self.h, _vp(lab.ctypes.data), _vp(core.ctypes.data), 0),
+                    "mapper_clusters_copy")
+        return lab[:n_members], core[:n_members].astype(bool)
+
+
+class Graph(_Handle):
+    def sizes(self):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _capi.check(self._lib.mapper_graph_sizes(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+                    "mapper_graph_sizes")
+        return a.value, b.value, c.value
+
+    def numpy(self) -> dict:
+        N, G, E = self.sizes()
+        no = np.empty(N + 1, dtype=np.int64)
+        nm = np.empty(max(G, 1), dtype=np.int32)
+        ne = np.empty(max(N, 1), dtype=np.int32)
+        ed = np.empty(max(2 * E, 2), dtype=np.int32)
+        _capi.check(self._lib.mapper_graph_copy(self.h, _vp(no.ctypes.data), _vp(nm.ctypes.data),
+                                                _vp(ne.ctypes.data), _vp(ed.ctypes.data), 0),
+                    "mapper_graph_copy")
+        return dict(node_offsets=no, node_members=nm[:G], node_elem=ne[:N],
+                    edges=ed[:2 * E].reshape(E, 2))
+
+    def lens(self, n: int, m: int):
+        """(lens n x m float64, pca basis or None)."""
+        f = np.empty((n, m), dtype=np.float64)
+        npca = ctypes.c_int64()
+        _capi.check(self._lib.mapper_graph_lens(self.h, None, None, ctypes.byref(npca), 0),
+                    "mapper_graph_lens")
+        pca = np.empty(max(npca.value, 1), dtype=np.float64)
+        _capi.check(self._lib.mapper_graph_lens(self.h, _vp(f.ctypes.data), _vp(pca.ctypes.data),
+                                                ctypes.byref(npca), 0), "mapper_graph_lens")
+        return f, (pca[:npca.value] if npca.value else None)
+
+    def cover(self) -> Cover:
+        return Cover(self._lib, ctypes.c_void_p(self._lib.mapper_graph_cover(self.h)), owner=self)
+
+    def clusters(self) -> Clusters:
+        return Clusters(self._lib, ctypes.c_void_p(self._lib.mapper_graph_clusters(self.h)), owner=self)
+
+
+def params(lens_kind, lens_arg, n_intervals, overlap, eps, min_pts, precision=FP32) -> MapperParams:
+    lens_kind, lens_arg = tuple(lens_kind), tuple(lens_arg)
+    n_intervals, overlap = tuple(n_intervals), tuple(overlap)
+    p = MapperParams()
+    p.m = len(lens_kind)
+    for j in range(p.m):
+        p.lens_kind[j] = int(lens_kind[j])
+        p.lens_arg[j] = int(lens_arg[j])
+        p.n_intervals[j] = int(n_intervals[j])
+        p.overlap[j] = float(overlap[j])
+    p.eps = float(eps)
+    p.min_pts = int(min_pts)
+    p.precision = int(precision)
+    return p
+
+
+def _x_args(X):
+    """(pointer, n, d, ld, keepalive) for a torch tensor (CUDA or CPU) or a
+    NumPy array (host)."""
+    if isinstance(X, np.ndarray):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        return _vp(X.ctypes.data), X.shape[0], X.shape[1], X.shape[1], X
+    torch = _torch()
+    if X.dtype != torch.float32 or X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be a 2-D float32 tensor with unit column stride")
+    return _vp(X.data_ptr()), X.shape[0], X.shape[1], X.stride(0), X
+
+
+def mapper_lens(ctx: Context, X, kinds, args):
+    """Lens on the device: returns (lens [n, m] float64 CUDA tensor, pca)."""
+    torch = _torch()
+    p, n, d, ld, _keep = _x_args(X)
+    m = len(kinds)
+    out = torch.empty((n, m), dtype=torch.float64, device=f"cuda:{ctx.device}")
+    k = (ctypes.c_int32 * m)(*kinds)
+    a = (ctypes.c_int32 * m)(*args)
+    npca = d * (1 + max([arg for kind, arg in zip(kinds, args) if kind == LENS_PCA], default=-1))
+    pca = np.empty(max(npca, 1), dtype=np.float64)
+    _capi.check(ctx._lib.mapper_lens(ctx.h, p, n, d, ld, m, k, a, _vp(out.data_ptr()),
+                                     _vp(pca.ctypes.data) if npca > d else None), "mapper_lens")
+    return out, (pca[:npca] if npca > d else None)
+
+
+def mapper_cover(ctx: Context, lens, n_intervals, overlap) -> Cover:
+    n, m = lens.shape
+    ni = (ctypes.c_int32 * m)(*n_intervals)
+    ov = (ctypes.c_double * m)(*overlap)
+    h = ctypes.c_void_p()
+    _capi.check(ctx._lib.mapper_cover(ctx.h, _vp(lens.data_ptr()), n, m, ni, ov, ctypes.byref(h)),
+                "mapper_cover")
+    return Cover(ctx._lib, h)
+
+
+def mapper_cluster(ctx: Context, X, cover: Cover, eps: float, min_pts: int, precision: int = FP32) -> Clusters:
+    p, n, d, ld, _keep = _x_args(X)
+    h = ctypes.c_void_p()
+    _capi.check(ctx._lib.mapper_cluster(ctx.h, p, n, d, ld, cover.h, float(eps), int(min_pts),
+                                        int(precision), ctypes.byref(h)), "mapper_cluster")
+    c = Clusters(ctx._lib, h)
+    c._cover = cover
+    return c
+
+
+def mapper_nerve(ctx: Context, clusters: Clusters) -> Graph:
+    h = ctypes.c_void_p()
+    _capi.check(ctx._lib.mapper_nerve(ctx.h, clusters.h, ctypes.byref(h)), "mapper_nerve")
+    return Graph(ctx._lib, h)
+
+
+def mapper_graph(ctx: Context, X, prm: MapperParams) -> Graph:
+    """Fused lens + cover + DBSCAN + nerve. X: CUDA tensor, or a host array
+    (copied to the device inside the call)."""
+    p, n, d, ld, _keep = _x_args(X)
+    h = ctypes.c_void_p()
+    _capi.check(ctx._lib.mapper_graph(ctx.h, p, n, d, ld, ctypes.byref(prm), ctypes.byref(h)),
+                "mapper_graph")
+    return Graph(ctx._lib, h)

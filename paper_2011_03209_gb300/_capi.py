@@ -1,0 +1,141 @@
+"""ctypes declarations of the C ABI in include/mapper.h.
+
+Loading fails loudly when the compiled library is absent: there is no CPU
+fallback for any step of the mapper path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmapper_gb300.so")
+
+MAPPER_OK = 0
+MAPPER_EINVAL = -1
+MAPPER_ENOMEM = -2
+MAPPER_ECUDA = -3
+MAPPER_ETIMEOUT = -4
+MAPPER_ENONFINITE = -5
+MAPPER_EINTERNAL = -6
+MAPPER_ENOTIMPL = -7
+
+LENS_L2, LENS_COORD, LENS_PCA = 0, 1, 2
+FP32, BF16 = 0, 1
+
+# every symbol include/mapper.h declares
+EXPORTS = (
+    "mapper_create", "mapper_destroy", "mapper_set_stream", "mapper_set_timing",
+    "mapper_lens", "mapper_cover", "mapper_cover_sizes", "mapper_cover_copy",
+    "mapper_cluster", "mapper_clusters_copy", "mapper_nerve", "mapper_graph",
+    "mapper_graph_sizes", "mapper_graph_copy", "mapper_graph_lens", "mapper_graph_cover",
+    "mapper_graph_clusters", "mapper_stats_get", "mapper_free", "mapper_strerror",
+    "mapper_last_error", "mapper_abi_version",
+)
+
+
+class MapperParams(ctypes.Structure):
+    _fields_ = [
+        ("m", ctypes.c_int32),
+        ("lens_kind", ctypes.c_int32 * 2),
+        ("lens_arg", ctypes.c_int32 * 2),
+        ("n_intervals", ctypes.c_int32 * 2),
+        ("overlap", ctypes.c_double * 2),
+        ("eps", ctypes.c_double),
+        ("min_pts", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+    ]
+
+
+class MapperStats(ctypes.Structure):
+    _fields_ = [
+        ("n_points", ctypes.c_int64),
+        ("n_elements", ctypes.c_int64),
+        ("n_members", ctypes.c_int64),
+        ("sum_ni2", ctypes.c_double),
+        ("tile_pairs", ctypes.c_int64),
+        ("tile_pairs_out", ctypes.c_int64),
+        ("tile_pairs_in", ctypes.c_int64),
+        ("pairs_screened", ctypes.c_int64),
+        ("band_pairs", ctypes.c_int64),
+        ("near_ties", ctypes.c_int64),
+        ("n_core", ctypes.c_int64),
+        ("n_nodes", ctypes.c_int64),
+        ("n_edges", ctypes.c_int64),
+        ("n_launches", ctypes.c_int64),
+        ("ms_lens", ctypes.c_double),
+        ("ms_cover", ctypes.c_double),
+        ("ms_cluster", ctypes.c_double),
+        ("ms_nerve", ctypes.c_double),
+        ("ms_total", ctypes.c_double),
+        ("ms_pass", ctypes.c_double * 3),
+    ]
+
+    def as_dict(self) -> dict:
+        out = {name: getattr(self, name) for name, _ in self._fields_}
+        out["ms_pass"] = list(self.ms_pass)
+        return out
+
+
+class MapperError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: status {status}: {message}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the library (once). Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(
+                f"CUDA library {p} is missing: build it first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(p)
+        P = ctypes.c_void_p
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        i32, i64, f64, sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+        sig = {
+            "mapper_create": (ctypes.c_int, [PP, ctypes.c_int, sz, P]),
+            "mapper_destroy": (None, [P]),
+            "mapper_set_stream": (ctypes.c_int, [P, P]),
+            "mapper_set_timing": (ctypes.c_int, [P, ctypes.c_int]),
+            "mapper_lens": (ctypes.c_int, [P, P, i64, i32, i64, i32, P, P, P, P]),
+            "mapper_cover": (ctypes.c_int, [P, P, i64, i32, P, P, PP]),
+            "mapper_cover_sizes": (ctypes.c_int, [P, P, P]),
+            "mapper_cover_copy": (ctypes.c_int, [P, P, P, ctypes.c_int]),
+            "mapper_cluster": (ctypes.c_int, [P, P, i64, i32, i64, P, f64, i32, i32, PP]),
+            "mapper_clusters_copy": (ctypes.c_int, [P, P, P, ctypes.c_int]),
+            "mapper_nerve": (ctypes.c_int, [P, P, PP]),
+            "mapper_graph": (ctypes.c_int, [P, P, i64, i32, i64, ctypes.POINTER(MapperParams), PP]),
+            "mapper_graph_sizes": (ctypes.c_int, [P, P, P, P]),
+            "mapper_graph_copy": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int]),
+            "mapper_graph_lens": (ctypes.c_int, [P, P, P, P, ctypes.c_int]),
+            "mapper_graph_cover": (P, [P]),
+            "mapper_graph_clusters": (P, [P]),
+            "mapper_stats_get": (ctypes.c_int, [P, ctypes.POINTER(MapperStats)]),
+            "mapper_free": (None, [P]),
+            "mapper_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+            "mapper_last_error": (ctypes.c_char_p, []),
+            "mapper_abi_version": (ctypes.c_int, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def check(status: int, where: str) -> None:
+    if status != MAPPER_OK:
+        lib = load()
+        raise MapperError(status, where, lib.mapper_last_error().decode(errors="replace"))

@@ -1,0 +1,837 @@
+// capi.cu -- the C ABI (include/mapper.h) and the host side of the pipeline:
+// argument checks, handle ownership, stream-ordered scratch, size read-backs,
+// and the order of the kernel launches of each step.
+#include <cfloat>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/mapper.h"
+#include "dbscan.cuh"
+#include "tc.cuh"
+
+namespace mgb {
+
+thread_local std::string g_last_error;
+thread_local int64_t g_launches = 0;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+}  // namespace mgb
+
+using namespace mgb;
+
+namespace {
+
+constexpr uint32_t kMagic = 0x4d415052u;   // "MAPR"
+enum : uint32_t { kKindCover = 1, kKindClusters = 2, kKindGraph = 3 };
+
+struct HandleHdr {
+    uint32_t magic;
+    uint32_t kind;
+};
+
+// Owns (or borrows) the stream; every result array holds a reference so the
+// stream outlives the stream-ordered frees of the arrays.
+struct StreamHolder {
+    cudaStream_t s = nullptr;
+    bool owned = false;
+    ~StreamHolder() { if (owned && s) cudaStreamDestroy(s); }
+};
+using StreamRef = std::shared_ptr<StreamHolder>;
+
+struct CoverData {
+    StreamRef stream;          // first member: destroyed last
+    int m = 1;
+    int32_t n_int[2] = {1, 1};
+    double overlap[2] = {0, 0};
+    int64_t n = 0, E = 0, M = 0;
+    Buf keys;                  // sorted (element << 32 | point), M
+    Buf elem_off;              // E + 1 int64
+    Buf slot_point, slot_elem; // M int32 each
+    std::vector<int64_t> h_elem_off;
+};
+
+struct ClusterData {
+    StreamRef stream;
+    std::shared_ptr<CoverData> cover;
+    Buf count, core, root, border, lab, is_root, is_member, slot_label;
+    mapper_stats stats{};
+};
+
+}  // namespace
+
+struct mapper_ctx {
+    int device = 0;
+    StreamRef stream;
+    size_t budget = 0;
+    bool timing = false;
+    int num_sms = 152;
+};
+
+struct mapper_cover_t {
+    HandleHdr h{kMagic, kKindCover};
+    std::shared_ptr<CoverData> c;
+    bool view = false;
+};
+
+struct mapper_clusters_t {
+    HandleHdr h{kMagic, kKindClusters};
+    std::shared_ptr<ClusterData> c;
+    bool view = false;
+};
+
+struct mapper_graph_t {
+    HandleHdr h{kMagic, kKindGraph};
+    StreamRef stream;
+    std::shared_ptr<ClusterData> clusters;
+    Buf node_off, node_members, node_elem, edges, lens, pca;
+    int64_t N = 0, Gm = 0, Eg = 0, n = 0, m = 1, n_pca = 0;
+    mapper_stats stats{};
+    mapper_cover_t cover_view;
+    mapper_clusters_t clusters_view;
+};
+
+namespace {
+
+int fail(int status, const std::string& msg)
+{
+    set_error(msg);
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char* where)
+{
+    return fail(e == cudaErrorMemoryAllocation ? MAPPER_ENOMEM : MAPPER_ECUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr, where)                                                    \
+    do {                                                                   \
+        cudaError_t e_ = (expr);                                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where);                \
+    } while (0)
+
+int bits_for(int64_t n)      // bits to hold values 0 .. n-1
+{
+    int b = 1;
+    while (b < 63 && (int64_t(1) << b) < n) ++b;
+    return b;
+}
+
+struct Timer {
+    bool on;
+    cudaStream_t s;
+    cudaEvent_t ev[8]{};
+    int n = 0;
+    Timer(bool on_, cudaStream_t s_) : on(on_), s(s_) {}
+    ~Timer() { for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]); }
+    void mark() {
+        if (!on || n >= 8) return;
+        cudaEventCreate(&ev[n]);
+        cudaEventRecord(ev[n], s);
+        ++n;
+    }
+    double ms(int a, int b) const {
+        if (!on || b >= n) return 0.0;
+        float t = 0.f;
+        cudaEventSynchronize(ev[b]);
+        cudaEventElapsedTime(&t, ev[a], ev[b]);
+        return t;
+    }
+};
+
+int check_ctx(mapper_ctx* ctx)
+{
+    if (!ctx) return fail(MAPPER_EINVAL, "null context");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    return MAPPER_OK;
+}
+
+int check_x(const float* X, int64_t n, int32_t d, int64_t ld)
+{
+    if (!X) return fail(MAPPER_EINVAL, "X is null");
+    if (n < 1 || n > INT32_MAX) return fail(MAPPER_EINVAL, "n must be in [1, 2^31)");
+    if (d < 1) return fail(MAPPER_EINVAL, "d must be >= 1");
+    if (ld < d) return fail(MAPPER_EINVAL, "ld must be >= d");
+    return MAPPER_OK;
+}
+
+// ------------------------------------------------------------------- lens
+int run_lens(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld, int32_t m,
+             const int32_t* kinds, const int32_t* args, double* lens_dev, Buf* pca_dev,
+             int64_t* n_pca)
+{
+    cudaStream_t s = ctx->stream->s;
+    int K = 0;
+    for (int j = 0; j < m; ++j) {
+        if (kinds[j] == MAPPER_LENS_COORD && (args[j] < 0 || args[j] >= d))
+            return fail(MAPPER_EINVAL, "coordinate lens column out of range");
+        if (kinds[j] == MAPPER_LENS_PCA) {
+            if (args[j] < 0 || args[j] >= d) return fail(MAPPER_EINVAL, "PCA axis out of range");
+            K = std::max(K, args[j] + 1);
+        }
+        if (kinds[j] < 0 || kinds[j] > 2) return fail(MAPPER_EINVAL, "unknown lens kind");
+    }
+    *n_pca = 0;
+    Buf status;
+    if (K) {
+        CK(pca_dev->alloc(sizeof(double) * (size_t)d * (K + 1), s), "alloc pca");
+        CK(status.alloc(sizeof(int), s), "alloc");
+        CK(pca_axes(X, n, d, ld, K, pca_dev->as<double>(), pca_dev->as<double>() + d,
+                    status.as<int>(), s), "pca");
+        *n_pca = (int64_t)d * (K + 1);
+    }
+    for (int j = 0; j < m; ++j) {
+        if (kinds[j] == MAPPER_LENS_L2) CK(lens_l2(X, n, d, ld, lens_dev, m, j, s), "lens_l2");
+        else if (kinds[j] == MAPPER_LENS_COORD)
+            CK(lens_coord(X, n, ld, args[j], lens_dev, m, j, s), "lens_coord");
+        else
+            CK(lens_project(X, n, d, ld, pca_dev->as<double>(),
+                            pca_dev->as<double>() + (size_t)d * (1 + args[j]), lens_dev, m, j, s),
+               "lens_project");
+    }
+    return MAPPER_OK;
+}
+
+// ------------------------------------------------------------------ cover
+int run_cover(mapper_ctx* ctx, const double* lens, int64_t n, int32_t m, const int32_t* n_int,
+              const double* overlap, std::shared_ptr<CoverData>* out, int* nonfinite_dev)
+{
+    if (m < 1 || m > 2) return fail(MAPPER_EINVAL, "m must be 1 or 2");
+    for (int j = 0; j < m; ++j) {
+        if (n_int[j] < 1) return fail(MAPPER_EINVAL, "n_intervals must be >= 1");
+        if (!(overlap[j] >= 0.0 && overlap[j] < 1.0)) return fail(MAPPER_EINVAL, "overlap must be in [0, 1)");
+    }
+    const int64_t E = (int64_t)n_int[0] * (m == 2 ? n_int[1] : 1);
+    if (E > (int64_t(1) << 30)) return fail(MAPPER_EINVAL, "too many cover elements");
+    cudaStream_t s = ctx->stream->s;
+    auto c = std::make_shared<CoverData>();
+    c->stream = ctx->stream;
+    c->m = m;
+    c->n = n;
+    c->E = E;
+    for (int j = 0; j < m; ++j) { c->n_int[j] = n_int[j]; c->overlap[j] = overlap[j]; }
+
+    Buf lohi, bounds, cnt, pos, flag;
+    CK(lohi.alloc(sizeof(double) * 2 * m, s), "alloc");
+    CK(bounds.alloc(sizeof(double) * 2 * ((size_t)n_int[0] + (m == 2 ? n_int[1] : 0)), s), "alloc");
+    CK(cnt.alloc(sizeof(int32_t) * n, s), "alloc");
+    CK(pos.alloc(sizeof(int64_t) * (n + 1), s), "alloc");
+    int* nf = nonfinite_dev;
+    if (!nf) {
+        CK(flag.alloc(sizeof(int), s), "alloc");
+        CK(cudaMemsetAsync(flag.p, 0, sizeof(int), s), "memset");
+        nf = flag.as<int>();
+    }
+    CK(lens_range_flag(lens, n, m, lohi.as<double>(), nf, s), "lens_range");
+    CK(interval_bounds(lohi.as<double>(), m, n_int, overlap, bounds.as<double>(), s), "bounds");
+    CK(cover_count(lens, n, m, bounds.as<double>(), n_int[0], m == 2 ? n_int[1] : 1,
+                   cnt.as<int32_t>(), s), "cover_count");
+    CK(exclusive_scan_i32_to_i64(cnt.as<int32_t>(), pos.as<int64_t>(), n, s), "scan");
+    int64_t M = 0;
+    int h_nf = 0;
+    CK(cudaMemcpyAsync(&M, pos.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaMemcpyAsync(&h_nf, nf, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    if (h_nf) return fail(MAPPER_ENONFINITE, "lens or X holds NaN or Inf");
+    if (M > INT32_MAX) return fail(MAPPER_ENOMEM, "more than 2^31 cover memberships");
+    c->M = M;
+    Buf tmp;
+    CK(c->keys.alloc(sizeof(uint64_t) * M, s), "alloc keys");
+    CK(tmp.alloc(sizeof(uint64_t) * M, s), "alloc");
+    CK(cover_emit(lens, n, m, bounds.as<double>(), n_int[0], m == 2 ? n_int[1] : 1,
+                  pos.as<int64_t>(), c->keys.as<uint64_t>(), s), "cover_emit");
+    CK(radix_sort_u64(c->keys.as<uint64_t>(), tmp.as<uint64_t>(), M, 32, 32 + bits_for(E), s), "sort");
+    CK(c->elem_off.alloc(sizeof(int64_t) * (E + 1), s), "alloc");
+    CK(element_offsets(c->keys.as<uint64_t>(), M, E, c->elem_off.as<int64_t>(), s), "elem_off");
+    CK(c->slot_point.alloc(sizeof(int32_t) * M, s), "alloc");
+    CK(c->slot_elem.alloc(sizeof(int32_t) * M, s), "alloc");
+    CK(split_keys(c->keys.as<uint64_t>(), M, c->slot_point.as<int32_t>(), c->slot_elem.as<int32_t>(), s),
+       "split");
+    c->h_elem_off.resize(E + 1);
+    CK(cudaMemcpyAsync(c->h_elem_off.data(), c->elem_off.p, sizeof(int64_t) * (E + 1),
+                       cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    *out = c;
+    return MAPPER_OK;
+}
+
+// FP32 screen thresholds. The sum of d squared differences accumulated by
+// FMA in FP32 satisfies |s - d2| <= ((1+u)^2 (1+gamma_d) - 1) d2 + tiny
+// (u = 2^-24, gamma_d = d u / (1 - d u); all terms are nonnegative, the
+// subtraction rounds once, each FMA once, subnormal results add at most
+// 2^-149 each). With eta = 1.5 (d + 4) u the pair is certainly inside when
+// s <= eps2 (1 - eta) - tiny and certainly outside when s > eps2 (1 + eta)
+// + tiny; the bounds are rounded outward to float.
+void fp32_thresholds(double eps2, int d, float* lo, float* hi)
+{
+    const double u = std::ldexp(1.0, -24);
+    const double eta = 1.5 * (d + 4) * u;
+    const double tiny = 3.0 * (d + 2) * std::ldexp(1.0, -149);
+    const double l = eps2 * (1.0 - eta) - tiny;
+    const double h = eps2 * (1.0 + eta) + tiny;
+    float lf = (float)l;
+    if ((double)lf > l) lf = std::nextafter(lf, -INFINITY);
+    if (l <= 0.0) lf = -1.0f;
+    float hf = (float)h;
+    if ((double)hf < h) hf = std::nextafter(hf, INFINITY);
+    *lo = lf;
+    *hi = hf;
+}
+
+// ---------------------------------------------------------------- cluster
+int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
+                const std::shared_ptr<CoverData>& cov, double eps, int32_t min_pts, int32_t precision,
+                std::shared_ptr<ClusterData>* out, int* nonfinite_dev)
+{
+    if (!(eps > 0.0) || !std::isfinite(eps)) return fail(MAPPER_EINVAL, "eps must be finite and > 0");
+    if (min_pts < 1) return fail(MAPPER_EINVAL, "min_pts must be >= 1");
+    if (precision != MAPPER_FP32 && precision != MAPPER_BF16)
+        return fail(MAPPER_EINVAL, "unknown precision");
+    if (cov->n != n) return fail(MAPPER_EINVAL, "cover was built for another point count");
+    cudaStream_t s = ctx->stream->s;
+    const int64_t M = cov->M, E = cov->E;
+    const int dp = (d + 31) / 32 * 32;
+    const double est = (double)M * dp * 4.0 + (double)M * 48.0;
+    if (ctx->budget && est > (double)ctx->budget)
+        return fail(MAPPER_ENOMEM, "estimated scratch exceeds the context's HBM budget");
+
+    auto c = std::make_shared<ClusterData>();
+    c->stream = ctx->stream;
+    c->cover = cov;
+    mapper_stats& st = c->stats;
+    st.n_points = n;
+    st.n_elements = E;
+    st.n_members = M;
+    std::vector<int64_t> h_pairs(E + 1, 0);
+    double s2 = 0.0;
+    for (int64_t e = 0; e < E; ++e) {
+        const int64_t ne = cov->h_elem_off[e + 1] - cov->h_elem_off[e];
+        const int64_t T = (ne + 127) / 128;
+        s2 += (double)ne * (double)ne;
+        h_pairs[e + 1] = h_pairs[e] + T * (T + 1) / 2;
+    }
+    st.sum_ni2 = s2;
+    const int64_t n_pairs = h_pairs[E];
+    st.tile_pairs = n_pairs;
+    if (n_pairs > INT32_MAX) return fail(MAPPER_ENOMEM, "too many tile pairs for one launch");
+
+    Buf G, pair_off, stats, flag;
+    CK(G.alloc(sizeof(float) * (size_t)M * dp, s), "alloc rows");
+    CK(pair_off.alloc(sizeof(int64_t) * (E + 1), s), "alloc");
+    CK(cudaMemcpyAsync(pair_off.p, h_pairs.data(), sizeof(int64_t) * (E + 1), cudaMemcpyHostToDevice, s),
+       "copy");
+    CK(stats.alloc(sizeof(unsigned long long) * kStatCount, s), "alloc");
+    CK(cudaMemsetAsync(stats.p, 0, sizeof(unsigned long long) * kStatCount, s), "memset");
+    int* nf = nonfinite_dev;
+    if (!nf) {
+        CK(flag.alloc(sizeof(int), s), "alloc");
+        CK(cudaMemsetAsync(flag.p, 0, sizeof(int), s), "memset");
+        nf = flag.as<int>();
+    }
+    CK(c->count.alloc(sizeof(int32_t) * M, s), "alloc");
+    CK(c->core.alloc(M, s), "alloc");
+    CK(c->root.alloc(sizeof(int32_t) * M, s), "alloc");
+    CK(c->border.alloc(sizeof(int32_t) * M, s), "alloc");
+    Buf parent;
+    CK(parent.alloc(sizeof(int32_t) * M, s), "alloc");
+    CK(cudaMemsetAsync(c->count.p, 0, sizeof(int32_t) * M, s), "memset");
+
+    CK(gather_rows(X, ld, d, dp, cov->slot_point.as<int32_t>(), M, G.as<float>(), nf, s), "gather");
+
+    PassArgs a{};
+    a.G = G.as<float>();
+    a.dp = dp;
+    a.d = d;
+    a.elem_off = cov->elem_off.as<int64_t>();
+    a.pair_off = pair_off.as<int64_t>();
+    a.E = (int)E;
+    a.eps2 = eps * eps;
+    a.tie_thr = 1e-12 * a.eps2;
+    fp32_thresholds(a.eps2, d, &a.lo_thr, &a.hi_thr);
+    a.count = c->count.as<int32_t>();
+    a.core = c->core.as<uint8_t>();
+    a.parent = parent.as<int32_t>();
+    a.root = c->root.as<int32_t>();
+    a.border = c->border.as<int32_t>();
+    a.stats = stats.as<unsigned long long>();
+
+    Timer pt(ctx->timing, s);
+    if (precision == MAPPER_BF16) {
+        int rc = tc_cluster_passes(a, n_pairs, min_pts, s);
+        if (rc != MAPPER_OK) return rc;
+    } else {
+        pt.mark();
+        CK(simt_pass(1, a, n_pairs, s), "pass 1");
+        pt.mark();
+        CK(core_flags(a.count, M, min_pts, c->core.as<uint8_t>(), a.parent, a.border, a.stats, s), "core");
+        pt.mark();
+        CK(simt_pass(2, a, n_pairs, s), "pass 2");
+        pt.mark();
+        CK(flatten(a.parent, a.core, M, c->root.as<int32_t>(), s), "flatten");
+        pt.mark();
+        CK(simt_pass(3, a, n_pairs, s), "pass 3");
+        pt.mark();
+    }
+
+    CK(c->lab.alloc(sizeof(int32_t) * M, s), "alloc");
+    CK(c->is_root.alloc(sizeof(int32_t) * M, s), "alloc");
+    CK(c->is_member.alloc(sizeof(int32_t) * M, s), "alloc");
+    CK(c->slot_label.alloc(sizeof(int64_t) * M, s), "alloc");
+    CK(labels(a.core, c->root.as<int32_t>(), a.border, cov->slot_point.as<int32_t>(), M,
+              c->lab.as<int32_t>(), c->is_root.as<int32_t>(), c->is_member.as<int32_t>(),
+              c->slot_label.as<int64_t>(), s), "labels");
+
+    unsigned long long h_stats[kStatCount];
+    int h_nf = 0;
+    CK(cudaMemcpyAsync(h_stats, stats.p, sizeof(h_stats), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaMemcpyAsync(&h_nf, nf, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    if (h_nf) return fail(MAPPER_ENONFINITE, "X holds NaN or Inf");
+    st.band_pairs = (int64_t)h_stats[kStatBand];
+    st.near_ties = (int64_t)h_stats[kStatTies];
+    st.pairs_screened = (int64_t)h_stats[kStatScreened];
+    st.n_core = (int64_t)h_stats[kStatCore];
+    st.tile_pairs_out = (int64_t)h_stats[kStatTileOut];
+    st.tile_pairs_in = (int64_t)h_stats[kStatTileIn];
+    if (pt.n >= 6) {
+        st.ms_pass[0] = pt.ms(0, 1);
+        st.ms_pass[1] = pt.ms(2, 3);
+        st.ms_pass[2] = pt.ms(4, 5);
+    }
+    *out = c;
+    return MAPPER_OK;
+}
+
+// ------------------------------------------------------------------ nerve
+int run_nerve(mapper_ctx* ctx, const std::shared_ptr<ClusterData>& cl, mapper_graph_t* g)
+{
+    cudaStream_t s = ctx->stream->s;
+    const auto& cov = cl->cover;
+    const int64_t M = cov->M;
+    Buf nid, mpos;
+    CK(nid.alloc(sizeof(int64_t) * (M + 1), s), "alloc");
+    CK(mpos.alloc(sizeof(int64_t) * (M + 1), s), "alloc");
+    CK(exclusive_scan_i32_to_i64(cl->is_root.as<int32_t>(), nid.as<int64_t>(), M, s), "scan");
+    CK(exclusive_scan_i32_to_i64(cl->is_member.as<int32_t>(), mpos.as<int64_t>(), M, s), "scan");
+    int64_t h[2];
+    CK(cudaMemcpyAsync(&h[0], nid.as<int64_t>() + M, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaMemcpyAsync(&h[1], mpos.as<int64_t>() + M, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    const int64_t N = h[0], Gm = h[1];
+    g->N = N;
+    g->Gm = Gm;
+    Buf keys, tmp, keys2;
+    CK(keys.alloc(sizeof(uint64_t) * Gm, s), "alloc");
+    CK(tmp.alloc(sizeof(uint64_t) * Gm, s), "alloc");
+    CK(keys2.alloc(sizeof(uint64_t) * Gm, s), "alloc");
+    CK(g->node_elem.alloc(sizeof(int32_t) * N, s), "alloc");
+    CK(g->node_off.alloc(sizeof(int64_t) * (N + 1), s), "alloc");
+    CK(g->node_members.alloc(sizeof(int32_t) * Gm, s), "alloc");
+    CK(member_keys(cl->lab.as<int32_t>(), nid.as<int64_t>(), mpos.as<int64_t>(),
+                   cov->slot_point.as<int32_t>(), cov->slot_elem.as<int32_t>(), M,
+                   keys.as<uint64_t>(), g->node_elem.as<int32_t>(), s), "member keys");
+    CK(radix_sort_u64(keys.as<uint64_t>(), tmp.as<uint64_t>(), Gm, 32, 32 + bits_for(N), s), "sort");
+    CK(node_offsets(keys.as<uint64_t>(), Gm, g->node_off.as<int64_t>(), g->node_members.as<int32_t>(),
+                    keys2.as<uint64_t>(), s), "node offsets");
+    CK(cudaMemcpyAsync(g->node_off.as<int64_t>() + N, &g->Gm, sizeof(int64_t), cudaMemcpyHostToDevice, s),
+       "copy");
+    // nerve: group memberships by point, emit node pairs, sort, unique
+    CK(radix_sort_u64(keys2.as<uint64_t>(), tmp.as<uint64_t>(), Gm, 32, 32 + bits_for(cov->n), s), "sort");
+    Buf cnt, ppos;
+    CK(cnt.alloc(sizeof(int64_t) * Gm, s), "alloc");
+    CK(ppos.alloc(sizeof(int64_t) * (Gm + 1), s), "alloc");
+    CK(run_pairs(keys2.as<uint64_t>(), Gm, cnt.as<int64_t>(), s), "run pairs");
+    CK(exclusive_scan_i64(cnt.as<int64_t>(), ppos.as<int64_t>(), Gm, s), "scan");
+    int64_t P = 0;
+    CK(cudaMemcpyAsync(&P, ppos.as<int64_t>() + Gm, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    Buf pairs, ptmp, flag, upos;
+    CK(pairs.alloc(sizeof(uint64_t) * P, s), "alloc");
+    CK(ptmp.alloc(sizeof(uint64_t) * P, s), "alloc");
+    CK(emit_pairs(keys2.as<uint64_t>(), Gm, ppos.as<int64_t>(), pairs.as<uint64_t>(), s), "emit pairs");
+    const int nb = bits_for(N);
+    CK(radix_sort_u64(pairs.as<uint64_t>(), ptmp.as<uint64_t>(), P, 0, nb, s), "sort");
+    CK(radix_sort_u64(pairs.as<uint64_t>(), ptmp.as<uint64_t>(), P, 32, 32 + nb, s), "sort");
+    CK(flag.alloc(sizeof(int32_t) * P, s), "alloc");
+    CK(upos.alloc(sizeof(int64_t) * (P + 1), s), "alloc");
+    CK(unique_flags(pairs.as<uint64_t>(), P, flag.as<int32_t>(), s), "unique");
+    CK(exclusive_scan_i32_to_i64(flag.as<int32_t>(), upos.as<int64_t>(), P, s), "scan");
+    int64_t Eg = 0;
+    CK(cudaMemcpyAsync(&Eg, upos.as<int64_t>() + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    g->Eg = Eg;
+    CK(g->edges.alloc(sizeof(int32_t) * 2 * Eg, s), "alloc");
+    CK(unique_emit(pairs.as<uint64_t>(), flag.as<int32_t>(), upos.as<int64_t>(), P,
+                   g->edges.as<int32_t>(), s), "unique emit");
+    CK(cudaStreamSynchronize(s), "sync");
+    const double keep[3] = {cl->stats.ms_pass[0], cl->stats.ms_pass[1], cl->stats.ms_pass[2]};
+    g->stats = cl->stats;
+    for (int i = 0; i < 3; ++i) g->stats.ms_pass[i] = keep[i];
+    g->stats.n_nodes = N;
+    g->stats.n_edges = Eg;
+    return MAPPER_OK;
+}
+
+int copy_out(void* dst, const void* src, size_t bytes, int on_device, cudaStream_t s)
+{
+    if (!dst || bytes == 0) return MAPPER_OK;
+    CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
+       "copy out");
+    CK(cudaStreamSynchronize(s), "sync");
+    return MAPPER_OK;
+}
+
+bool is_host_pointer(const void* p)
+{
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return attr.type == cudaMemoryTypeHost || attr.type == cudaMemoryTypeUnregistered;
+}
+
+template <class T>
+T* handle_as(const void* h, uint32_t kind)
+{
+    if (!h) return nullptr;
+    const HandleHdr* hh = static_cast<const HandleHdr*>(h);
+    if (hh->magic != kMagic || hh->kind != kind) return nullptr;
+    return const_cast<T*>(static_cast<const T*>(h));
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+int mapper_abi_version(void) { return MAPPER_ABI_VERSION; }
+
+const char* mapper_last_error(void) { return g_last_error.c_str(); }
+
+const char* mapper_strerror(int status)
+{
+    switch (status) {
+    case MAPPER_OK: return "ok";
+    case MAPPER_EINVAL: return "invalid argument";
+    case MAPPER_ENOMEM: return "out of device memory or over budget";
+    case MAPPER_ECUDA: return "CUDA error";
+    case MAPPER_ETIMEOUT: return "device wait timed out";
+    case MAPPER_ENONFINITE: return "input holds NaN or Inf";
+    case MAPPER_EINTERNAL: return "internal consistency check failed";
+    case MAPPER_ENOTIMPL: return "not implemented";
+    default: return "unknown status";
+    }
+}
+
+int mapper_create(mapper_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream)
+{
+    if (!out) return fail(MAPPER_EINVAL, "out is null");
+    *out = nullptr;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(MAPPER_EINVAL, "no such device");
+    CK(cudaSetDevice(device), "cudaSetDevice");
+    auto ctx = std::make_unique<mapper_ctx>();
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes;
+    ctx->stream = std::make_shared<StreamHolder>();
+    if (cuda_stream) {
+        ctx->stream->s = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        CK(cudaStreamCreateWithFlags(&ctx->stream->s, cudaStreamNonBlocking), "cudaStreamCreate");
+        ctx->stream->owned = true;
+    }
+    CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device), "attr");
+    // keep freed scratch in the pool between calls
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *out = ctx.release();
+    return MAPPER_OK;
+}
+
+void mapper_destroy(mapper_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream && ctx->stream->s) cudaStreamSynchronize(ctx->stream->s);
+    delete ctx;
+}
+
+int mapper_set_stream(mapper_ctx* ctx, void* cuda_stream)
+{
+    if (!ctx) return fail(MAPPER_EINVAL, "null context");
+    auto h = std::make_shared<StreamHolder>();
+    if (cuda_stream) {
+        h->s = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        CK(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking), "cudaStreamCreate");
+        h->owned = true;
+    }
+    ctx->stream = h;
+    return MAPPER_OK;
+}
+
+int mapper_set_timing(mapper_ctx* ctx, int enabled)
+{
+    if (!ctx) return fail(MAPPER_EINVAL, "null context");
+    ctx->timing = enabled != 0;
+    return MAPPER_OK;
+}
+
+int mapper_lens(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, int64_t ld, int32_t m,
+                const int32_t* kinds, const int32_t* args, double* lens_dev, double* pca_out)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if ((rc = check_x(X_dev, n, d, ld))) return rc;
+    if (m < 1 || m > 2 || !kinds || !args || !lens_dev) return fail(MAPPER_EINVAL, "bad lens arguments");
+    cudaStream_t s = ctx->stream->s;
+    Buf flag, pca;
+    CK(flag.alloc(sizeof(int), s), "alloc");
+    CK(cudaMemsetAsync(flag.p, 0, sizeof(int), s), "memset");
+    CK(check_finite(X_dev, n, d, ld, flag.as<int>(), s), "finite");
+    int64_t n_pca = 0;
+    if ((rc = run_lens(ctx, X_dev, n, d, ld, m, kinds, args, lens_dev, &pca, &n_pca))) return rc;
+    int h_nf = 0;
+    CK(cudaMemcpyAsync(&h_nf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+    if (pca_out && n_pca)
+        CK(cudaMemcpyAsync(pca_out, pca.p, sizeof(double) * n_pca, cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    if (h_nf) return fail(MAPPER_ENONFINITE, "X holds NaN or Inf");
+    return MAPPER_OK;
+}
+
+int mapper_cover(mapper_ctx* ctx, const double* lens_dev, int64_t n, int32_t m,
+                 const int32_t* n_intervals, const double* overlap, mapper_cover_t** out)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (!out || !lens_dev || !n_intervals || !overlap) return fail(MAPPER_EINVAL, "null argument");
+    *out = nullptr;
+    if (n < 1 || n > INT32_MAX) return fail(MAPPER_EINVAL, "n must be in [1, 2^31)");
+    std::shared_ptr<CoverData> c;
+    if ((rc = run_cover(ctx, lens_dev, n, m, n_intervals, overlap, &c, nullptr))) return rc;
+    auto h = new mapper_cover_t;
+    h->c = c;
+    *out = h;
+    return MAPPER_OK;
+}
+
+int mapper_cover_sizes(const mapper_cover_t* cover, int64_t* n_elements, int64_t* n_members)
+{
+    auto* h = handle_as<mapper_cover_t>(cover, kKindCover);
+    if (!h) return fail(MAPPER_EINVAL, "not a cover handle");
+    if (n_elements) *n_elements = h->c->E;
+    if (n_members) *n_members = h->c->M;
+    return MAPPER_OK;
+}
+
+int mapper_cover_copy(const mapper_cover_t* cover, int64_t* elem_offsets, int32_t* elem_points,
+                      int on_device)
+{
+    auto* h = handle_as<mapper_cover_t>(cover, kKindCover);
+    if (!h) return fail(MAPPER_EINVAL, "not a cover handle");
+    cudaStream_t s = h->c->stream->s;
+    int rc = copy_out(elem_offsets, h->c->elem_off.p, sizeof(int64_t) * (h->c->E + 1), on_device, s);
+    if (rc) return rc;
+    return copy_out(elem_points, h->c->slot_point.p, sizeof(int32_t) * h->c->M, on_device, s);
+}
+
+int mapper_cluster(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, int64_t ld,
+                   const mapper_cover_t* cover, double eps, int32_t min_pts, int32_t precision,
+                   mapper_clusters_t** out)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if ((rc = check_x(X_dev, n, d, ld))) return rc;
+    auto* cv = handle_as<mapper_cover_t>(cover, kKindCover);
+    if (!cv || !out) return fail(MAPPER_EINVAL, "bad cover handle or out");
+    *out = nullptr;
+    std::shared_ptr<ClusterData> c;
+    if ((rc = run_cluster(ctx, X_dev, n, d, ld, cv->c, eps, min_pts, precision, &c, nullptr))) return rc;
+    auto h = new mapper_clusters_t;
+    h->c = c;
+    *out = h;
+    return MAPPER_OK;
+}
+
+int mapper_clusters_copy(const mapper_clusters_t* clusters, int64_t* label, uint8_t* core, int on_device)
+{
+    auto* h = handle_as<mapper_clusters_t>(clusters, kKindClusters);
+    if (!h) return fail(MAPPER_EINVAL, "not a clusters handle");
+    cudaStream_t s = h->c->stream->s;
+    const int64_t M = h->c->cover->M;
+    int rc = copy_out(label, h->c->slot_label.p, sizeof(int64_t) * M, on_device, s);
+    if (rc) return rc;
+    return copy_out(core, h->c->core.p, M, on_device, s);
+}
+
+int mapper_nerve(mapper_ctx* ctx, const mapper_clusters_t* clusters, mapper_graph_t** out)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    auto* cl = handle_as<mapper_clusters_t>(clusters, kKindClusters);
+    if (!cl || !out) return fail(MAPPER_EINVAL, "bad clusters handle or out");
+    *out = nullptr;
+    auto g = std::make_unique<mapper_graph_t>();
+    g->stream = ctx->stream;
+    g->clusters = cl->c;
+    g->n = cl->c->cover->n;
+    g->m = cl->c->cover->m;
+    if ((rc = run_nerve(ctx, cl->c, g.get()))) return rc;
+    g->cover_view.c = cl->c->cover;
+    g->cover_view.view = true;
+    g->clusters_view.c = cl->c;
+    g->clusters_view.view = true;
+    *out = g.release();
+    return MAPPER_OK;
+}
+
+int mapper_graph(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
+                 const mapper_params* p, mapper_graph_t** out)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if ((rc = check_x(X, n, d, ld))) return rc;
+    if (!p || !out) return fail(MAPPER_EINVAL, "null params or out");
+    *out = nullptr;
+    if (p->m < 1 || p->m > 2) return fail(MAPPER_EINVAL, "m must be 1 or 2");
+    cudaStream_t s = ctx->stream->s;
+    Timer tm(ctx->timing, s);
+    tm.mark();
+    const int64_t launches0 = g_launches;
+
+    Buf xdev;
+    const float* Xd = X;
+    int64_t ldd = ld;
+    if (is_host_pointer(X)) {
+        CK(xdev.alloc(sizeof(float) * (size_t)n * d, s), "alloc X");
+        CK(cudaMemcpy2DAsync(xdev.p, sizeof(float) * d, X, sizeof(float) * ld, sizeof(float) * d, n,
+                             cudaMemcpyHostToDevice, s), "copy X");
+        Xd = xdev.as<float>();
+        ldd = d;
+    }
+    auto g = std::make_unique<mapper_graph_t>();
+    g->stream = ctx->stream;
+    g->n = n;
+    g->m = p->m;
+    Buf flag;
+    CK(flag.alloc(sizeof(int), s), "alloc");
+    CK(cudaMemsetAsync(flag.p, 0, sizeof(int), s), "memset");
+    CK(g->lens.alloc(sizeof(double) * (size_t)n * p->m, s), "alloc lens");
+    if ((rc = run_lens(ctx, Xd, n, d, ldd, p->m, p->lens_kind, p->lens_arg, g->lens.as<double>(), &g->pca,
+                       &g->n_pca))) return rc;
+    tm.mark();
+    std::shared_ptr<CoverData> cov;
+    if ((rc = run_cover(ctx, g->lens.as<double>(), n, p->m, p->n_intervals, p->overlap, &cov,
+                        flag.as<int>()))) return rc;
+    tm.mark();
+    std::shared_ptr<ClusterData> cl;
+    if ((rc = run_cluster(ctx, Xd, n, d, ldd, cov, p->eps, p->min_pts, p->precision, &cl, flag.as<int>())))
+        return rc;
+    tm.mark();
+    g->clusters = cl;
+    if ((rc = run_nerve(ctx, cl, g.get()))) return rc;
+    tm.mark();
+    if (ctx->timing) {
+        g->stats.ms_lens = tm.ms(0, 1);
+        g->stats.ms_cover = tm.ms(1, 2);
+        g->stats.ms_cluster = tm.ms(2, 3);
+        g->stats.ms_nerve = tm.ms(3, 4);
+        g->stats.ms_total = tm.ms(0, 4);
+        cl->stats.ms_lens = g->stats.ms_lens;
+        cl->stats.ms_cover = g->stats.ms_cover;
+        cl->stats.ms_cluster = g->stats.ms_cluster;
+    }
+    g->stats.n_launches = g_launches - launches0;
+    g->cover_view.c = cov;
+    g->cover_view.view = true;
+    g->clusters_view.c = cl;
+    g->clusters_view.view = true;
+    *out = g.release();
+    return MAPPER_OK;
+}
+
+int mapper_graph_sizes(const mapper_graph_t* g, int64_t* n_nodes, int64_t* n_members, int64_t* n_edges)
+{
+    auto* h = handle_as<mapper_graph_t>(g, kKindGraph);
+    if (!h) return fail(MAPPER_EINVAL, "not a graph handle");
+    if (n_nodes) *n_nodes = h->N;
+    if (n_members) *n_members = h->Gm;
+    if (n_edges) *n_edges = h->Eg;
+    return MAPPER_OK;
+}
+
+int mapper_graph_copy(const mapper_graph_t* g, int64_t* node_offsets, int32_t* node_members,
+                      int32_t* node_elem, int32_t* edges, int on_device)
+{
+    auto* h = handle_as<mapper_graph_t>(g, kKindGraph);
+    if (!h) return fail(MAPPER_EINVAL, "not a graph handle");
+    cudaStream_t s = h->stream->s;
+    int rc;
+    if ((rc = copy_out(node_offsets, h->node_off.p, sizeof(int64_t) * (h->N + 1), on_device, s))) return rc;
+    if ((rc = copy_out(node_members, h->node_members.p, sizeof(int32_t) * h->Gm, on_device, s))) return rc;
+    if ((rc = copy_out(node_elem, h->node_elem.p, sizeof(int32_t) * h->N, on_device, s))) return rc;
+    return copy_out(edges, h->edges.p, sizeof(int32_t) * 2 * h->Eg, on_device, s);
+}
+
+int mapper_graph_lens(const mapper_graph_t* g, double* lens, double* pca, int64_t* n_pca, int on_device)
+{
+    auto* h = handle_as<mapper_graph_t>(g, kKindGraph);
+    if (!h) return fail(MAPPER_EINVAL, "not a graph handle");
+    if (n_pca) *n_pca = h->n_pca;
+    cudaStream_t s = h->stream->s;
+    if (lens && !h->lens.p) return fail(MAPPER_EINVAL, "graph was built from a given cover; no lens stored");
+    int rc = copy_out(lens, h->lens.p, sizeof(double) * h->n * h->m, on_device, s);
+    if (rc) return rc;
+    return copy_out(pca, h->pca.p, sizeof(double) * h->n_pca, on_device, s);
+}
+
+const mapper_cover_t* mapper_graph_cover(const mapper_graph_t* g)
+{
+    auto* h = handle_as<mapper_graph_t>(g, kKindGraph);
+    return h ? &h->cover_view : nullptr;
+}
+
+const mapper_clusters_t* mapper_graph_clusters(const mapper_graph_t* g)
+{
+    auto* h = handle_as<mapper_graph_t>(g, kKindGraph);
+    return h ? &h->clusters_view : nullptr;
+}
+
+int mapper_stats_get(const void* handle, mapper_stats* out)
+{
+    if (!out) return fail(MAPPER_EINVAL, "out is null");
+    if (auto* g = handle_as<mapper_graph_t>(handle, kKindGraph)) { *out = g->stats; return MAPPER_OK; }
+    if (auto* c = handle_as<mapper_clusters_t>(handle, kKindClusters)) { *out = c->c->stats; return MAPPER_OK; }
+    return fail(MAPPER_EINVAL, "not a graph or clusters handle");
+}
+
+void mapper_free(void* handle)
+{
+    if (!handle) return;
+    const HandleHdr* hh = static_cast<const HandleHdr*>(handle);
+    if (hh->magic != kMagic) return;
+    if (hh->kind == kKindCover) {
+        auto* h = static_cast<mapper_cover_t*>(handle);
+        if (h->view) return;
+        delete h;
+    } else if (hh->kind == kKindClusters) {
+        auto* h = static_cast<mapper_clusters_t*>(handle);
+        if (h->view) return;
+        delete h;
+    } else if (hh->kind == kKindGraph) {
+        delete static_cast<mapper_graph_t*>(handle);
+    }
+}
+
+}  // extern "C"

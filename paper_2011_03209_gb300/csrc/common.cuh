@@ -1,0 +1,102 @@
+// common.cuh -- internal declarations shared by the library's translation
+// units (never installed; the public ABI is include/mapper.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace mgb {
+
+// ------------------------------------------------------------ error plumbing
+// Every internal step returns a cudaError_t; the C ABI layer turns it into a
+// mapper_status and records a message for mapper_last_error().
+void set_error(const std::string& msg);
+
+// Kernels launched by the calling thread since the counter was last reset
+// (every launch site adds to it; reported per call in mapper_stats).
+extern thread_local int64_t g_launches;
+inline void note_launch(int k = 1) { g_launches += k; }
+
+#define MGB_TRY(expr)                                                       \
+    do {                                                                    \
+        cudaError_t e__ = (expr);                                           \
+        if (e__ != cudaSuccess) return e__;                                 \
+    } while (0)
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ------------------------------------------------------- stream-ordered memory
+// Scratch and result arrays come from the device's stream-ordered pool
+// (cudaMallocAsync); `Buf` frees on destruction on the same stream.
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t s = nullptr;
+    Buf() = default;
+    Buf(const Buf&) = delete;
+    Buf& operator=(const Buf&) = delete;
+    Buf(Buf&& o) noexcept { *this = static_cast<Buf&&>(o); }
+    Buf& operator=(Buf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; s = o.s; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~Buf() { release(); }
+    cudaError_t alloc(size_t nbytes, cudaStream_t stream) {
+        release();
+        s = stream;
+        bytes = nbytes;
+        if (nbytes == 0) nbytes = 16;
+        return cudaMallocAsync(&p, nbytes, stream);
+    }
+    void release() {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ------------------------------------------------------------------ kernels
+// lens (k_lens.cu)
+cudaError_t lens_l2(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j,
+                    cudaStream_t s);
+cudaError_t lens_coord(const float* X, int64_t n, int64_t ld, int32_t col, double* f, int m,
+                       int j, cudaStream_t s);
+cudaError_t lens_project(const float* X, int64_t n, int32_t d, int64_t ld, const double* mu,
+                         const double* v, double* f, int m, int j, cudaStream_t s);
+// Principal axes: mu (d doubles) and K axes (K*d doubles), device outputs.
+cudaError_t pca_axes(const float* X, int64_t n, int32_t d, int64_t ld, int K, double* mu,
+                     double* axes, int* status, cudaStream_t s);
+// Non-finite scan: sets *flag to 1 if any X entry is NaN/Inf.
+cudaError_t check_finite(const float* X, int64_t n, int32_t d, int64_t ld, int* flag,
+                         cudaStream_t s);
+
+// cover (k_cover.cu)
+// bounds: per lens dim j, a_j[n_int_j], b_j[n_int_j] (device, packed one
+// after the other); lohi: 2*m doubles (min, max per dim).
+cudaError_t lens_range_flag(const double* f, int64_t n, int m, double* lohi, int* nonfinite,
+                            cudaStream_t s);
+cudaError_t interval_bounds(const double* lohi, int m, const int32_t* n_int_host,
+                            const double* p_host, double* bounds, cudaStream_t s);
+// number of memberships per point (cnt[n]) and the emitted element keys
+cudaError_t cover_count(const double* f, int64_t n, int m, const double* bounds,
+                        int32_t n0, int32_t n1, int32_t* cnt, cudaStream_t s);
+cudaError_t cover_emit(const double* f, int64_t n, int m, const double* bounds, int32_t n0,
+                       int32_t n1, const int64_t* pos, uint64_t* keys, cudaStream_t s);
+
+// scan / sort / compaction (k_sort.cu)
+cudaError_t exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n,
+                                      cudaStream_t s);   // out has n+1 entries
+cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+// Stable LSD radix sort of 64-bit keys on bits [lo_bit, hi_bit). In place
+// (keys) with a scratch buffer of the same size.
+cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* tmp, int64_t n, int lo_bit, int hi_bit,
+                           cudaStream_t s);
+
+// split sorted (element << 32 | point) keys into slot_point / slot_elem
+cudaError_t split_keys(const uint64_t* keys, int64_t M, int32_t* slot_point, int32_t* slot_elem,
+                       cudaStream_t s);
+
+}  // namespace mgb

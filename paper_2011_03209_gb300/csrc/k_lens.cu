@@ -1,0 +1,323 @@
+// k_lens.cu -- filter (lens) kernels, "Mapper Interactive" §3 (filter
+// function f: X -> R or R^2) and §4.1 (L2 norm, a chosen column; PCA).
+//
+// Sums run in double, k ascending, with explicitly rounded operations
+// (__dadd_rn / __dmul_rn / __dsub_rn are never fused into FMAs), so each lens
+// value is the exact IEEE result of the defining expression. Rows are staged
+// through shared memory so the loads stay coalesced while every thread walks
+// its own row in order.
+#include "common.cuh"
+
+namespace mgb {
+
+namespace {
+
+constexpr int kRows = 128;    // rows per CTA (one thread per row)
+constexpr int kChunk = 32;    // columns staged per step
+
+// One CTA = 128 rows. Each warp loads whole 32-column row segments
+// (coalesced); then each thread consumes its row's segment in order.
+// MODE 0: sum x^2 then sqrt (L2). MODE 1: sum (x - mu) v (projection).
+template <int MODE>
+__global__ void __launch_bounds__(kRows) lens_rows_kernel(const float* __restrict__ X, int64_t n,
+                                                          int32_t d, int64_t ld,
+                                                          const double* __restrict__ mu,
+                                                          const double* __restrict__ v,
+                                                          double* __restrict__ f, int m, int j)
+{
+    __shared__ float tile[kRows][kChunk + 1];
+    __shared__ double smu[kChunk], sv[kChunk];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t row0 = (int64_t)blockIdx.x * kRows;
+    double acc = 0.0;
+    for (int32_t k0 = 0; k0 < d; k0 += kChunk) {
+        const int kc = min(kChunk, d - k0);
+#pragma unroll 4
+        for (int r = warp; r < kRows; r += kRows / 32) {
+            const int64_t row = row0 + r;
+            float x = 0.f;
+            if (row < n && lane < kc) x = __ldg(X + row * ld + k0 + lane);
+            tile[r][lane] = x;
+        }
+        if (MODE == 1 && tid < kc) {
+            smu[tid] = mu[k0 + tid];
+            sv[tid] = v[k0 + tid];
+        }
+        __syncthreads();
+        for (int k = 0; k < kc; ++k) {
+            const double x = (double)tile[tid][k];
+            if (MODE == 0) {
+                acc = __dadd_rn(acc, __dmul_rn(x, x));
+            } else {
+                const double t = __dsub_rn(x, smu[k]);
+                acc = __dadd_rn(acc, __dmul_rn(t, sv[k]));
+            }
+        }
+        __syncthreads();
+    }
+    const int64_t row = row0 + tid;
+    if (row < n) f[row * m + j] = (MODE == 0) ? __dsqrt_rn(acc) : acc;
+}
+
+__global__ void lens_coord_kernel(const float* __restrict__ X, int64_t n, int64_t ld, int32_t col,
+                                  double* __restrict__ f, int m, int j)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) f[p * m + j] = (double)X[p * ld + col];
+}
+
+__global__ void finite_kernel(const float* __restrict__ X, int64_t n, int32_t d, int64_t ld,
+                              int* flag)
+{
+    const int64_t total = n * (int64_t)d;
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / d, c = i - r * d;
+        bad |= !isfinite(X[r * ld + c]);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+// --------------------------------------------------------------------- PCA
+// Column means: partial FP64 sums per row block, then a fixed-order reduce
+// (deterministic run to run).
+constexpr int kMeanRows = 4096;
+
+__global__ void col_partial_sum_kernel(const float* __restrict__ X, int64_t n, int32_t d,
+                                       int64_t ld, double* __restrict__ part)
+{
+    const int64_t r0 = (int64_t)blockIdx.x * kMeanRows;
+    const int64_t r1 = min(n, r0 + kMeanRows);
+    for (int c = threadIdx.x; c < d; c += blockDim.x) {
+        double s = 0.0;
+        for (int64_t r = r0; r < r1; ++r) s += (double)X[r * ld + c];
+        part[(int64_t)blockIdx.x * d + c] = s;
+    }
+}
+
+__global__ void col_mean_kernel(const double* __restrict__ part, int nblk, int32_t d, int64_t n,
+                                double* __restrict__ mu)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * d + c];
+    mu[c] = s / (double)n;
+}
+
+// FP32 covariance tiles: block (ti, tj, chunk) accumulates the 64 x 64 tile
+// (ti, tj), tj >= ti, of sum_p (x_p - mu)(x_p - mu)^T over its row chunk.
+constexpr int kCovT = 64;
+constexpr int kCovRows = 2048;
+
+__global__ void __launch_bounds__(256) cov_partial_kernel(const float* __restrict__ X, int64_t n,
+                                                          int32_t d, int64_t ld,
+                                                          const double* __restrict__ mu,
+                                                          float* __restrict__ part, int ntile)
+{
+    int ti = 0, tj = 0, t = blockIdx.x;       // decode upper-triangle tile index
+    for (ti = 0; ti < ntile; ++ti) {
+        const int row_len = ntile - ti;
+        if (t < row_len) { tj = ti + t; break; }
+        t -= row_len;
+    }
+    const int chunk = blockIdx.y;
+    __shared__ float sa[32][kCovT + 1], sb[32][kCovT + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[4][4] = {};
+    const int64_t r0 = (int64_t)chunk * kCovRows, r1 = min(n, r0 + kCovRows);
+    const int ca = ti * kCovT, cb = tj * kCovT;
+    for (int64_t rb = r0; rb < r1; rb += 32) {
+        for (int e = threadIdx.x; e < 32 * kCovT; e += 256) {
+            const int rr = e / kCovT, cc = e % kCovT;
+            const int64_t r = rb + rr;
+            float xa = 0.f, xb = 0.f;
+            if (r < r1) {
+                if (ca + cc < d) xa = (float)((double)X[r * ld + ca + cc] - mu[ca + cc]);
+                if (cb + cc < d) xb = (float)((double)X[r * ld + cb + cc] - mu[cb + cc]);
+            }
+            sa[rr][cc] = xa;
+            sb[rr][cc] = xb;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int rr = 0; rr < 32; ++rr) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { a[i] = sa[rr][ty * 4 + i]; b[i] = sb[rr][tx * 4 + i]; }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(a[i], b[k], acc[i][k]);
+        }
+        __syncthreads();
+    }
+    float* out = part + ((int64_t)chunk * gridDim.x + blockIdx.x) * kCovT * kCovT;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[(ty * 4 + i) * kCovT + tx * 4 + k] = acc[i][k];
+}
+
+__global__ void cov_reduce_kernel(const float* __restrict__ part, int nchunk, int ntile, int32_t d,
+                                  int64_t n, double* __restrict__ C)
+{
+    const int tile = blockIdx.x;
+    int ti = 0, tj = 0, t = tile;
+    for (ti = 0; ti < ntile; ++ti) {
+        const int row_len = ntile - ti;
+        if (t < row_len) { tj = ti + t; break; }
+        t -= row_len;
+    }
+    const int ntiles = gridDim.x;
+    for (int e = threadIdx.x; e < kCovT * kCovT; e += blockDim.x) {
+        const int i = ti * kCovT + e / kCovT, k = tj * kCovT + e % kCovT;
+        if (i >= d || k >= d) continue;
+        double s = 0.0;
+        for (int c = 0; c < nchunk; ++c) s += (double)part[((int64_t)c * ntiles + tile) * kCovT * kCovT + e];
+        s /= (double)n;
+        C[(int64_t)i * d + k] = s;
+        C[(int64_t)k * d + i] = s;
+    }
+}
+
+// Power iteration for the top-K eigenvectors of C (d x d, FP64), one CTA.
+// Each axis is orthogonalised against the earlier ones every step (deflation
+// by projection), iterated until ||v_new - v|| < 1e-7 or 2000 steps, then
+// signed so its entry of largest magnitude is positive (ties: lowest index).
+__global__ void __launch_bounds__(1024) power_iter_kernel(const double* __restrict__ C, int32_t d,
+                                                          int K, double* __restrict__ axes,
+                                                          int* status)
+{
+    extern __shared__ double sm[];
+    double* v = sm;           // d
+    double* w = sm + d;       // d
+    __shared__ double red[32];
+    __shared__ double s_norm, s_diff;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    int not_conv = 0;
+    for (int c = 0; c < K; ++c) {
+        for (int k = tid; k < d; k += blockDim.x) v[k] = 1.0 + 0.25 * (double)((k * 7919) % 13);
+        __syncthreads();
+        for (int it = 0; it < 2000; ++it) {
+            // w = C v
+            for (int r = warp; r < d; r += nwarp) {
+                double s = 0.0;
+                for (int k = lane; k < d; k += 32) s += C[(int64_t)r * d + k] * v[k];
+                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) w[r] = s;
+            }
+            __syncthreads();
+            // orthogonalise against earlier axes
+            for (int q = 0; q < c; ++q) {
+                double s = 0.0;
+                for (int k = tid; k < d; k += blockDim.x) s += axes[q * d + k] * w[k];
+                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) red[warp] = s;
+                __syncthreads();
+                if (tid == 0) { double t = 0; for (int i = 0; i < nwarp; ++i) t += red[i]; s_norm = t; }
+                __syncthreads();
+                const double proj = s_norm;
+                for (int k = tid; k < d; k += blockDim.x) w[k] -= proj * axes[q * d + k];
+                __syncthreads();
+            }
+            double s = 0.0;
+            for (int k = tid; k < d; k += blockDim.x) s += w[k] * w[k];
+            for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) red[warp] = s;
+            __syncthreads();
+            if (tid == 0) { double t = 0; for (int i = 0; i < nwarp; ++i) t += red[i]; s_norm = sqrt(t); }
+            __syncthreads();
+            const double inv = s_norm > 0.0 ? 1.0 / s_norm : 0.0;
+            double dd = 0.0;
+            for (int k = tid; k < d; k += blockDim.x) {
+                const double nv = w[k] * inv;
+                dd += (nv - v[k]) * (nv - v[k]);
+                v[k] = nv;
+            }
+            for (int o = 16; o; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
+            if (lane == 0) red[warp] = dd;
+            __syncthreads();
+            if (tid == 0) { double t = 0; for (int i = 0; i < nwarp; ++i) t += red[i]; s_diff = t; }
+            __syncthreads();
+            if (s_diff < 1e-14) break;           // ||dv|| < 1e-7
+            if (it == 1999) not_conv = 1;
+        }
+        // sign rule
+        if (tid == 0) {
+            int arg = 0;
+            for (int k = 1; k < d; ++k)
+                if (fabs(v[k]) > fabs(v[arg])) arg = k;
+            s_norm = v[arg] < 0.0 ? -1.0 : 1.0;
+        }
+        __syncthreads();
+        for (int k = tid; k < d; k += blockDim.x) axes[c * d + k] = s_norm * v[k];
+        __syncthreads();
+    }
+    if (tid == 0) *status = not_conv;
+}
+
+}  // namespace
+
+cudaError_t lens_l2(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j,
+                    cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    { lens_rows_kernel<0><<<div_up(n, kRows), kRows, 0, s>>>(X, n, d, ld, nullptr, nullptr, f, m, j); note_launch(); }
+    return cudaGetLastError();
+}
+
+cudaError_t lens_project(const float* X, int64_t n, int32_t d, int64_t ld, const double* mu,
+                         const double* v, double* f, int m, int j, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    { lens_rows_kernel<1><<<div_up(n, kRows), kRows, 0, s>>>(X, n, d, ld, mu, v, f, m, j); note_launch(); }
+    return cudaGetLastError();
+}
+
+cudaError_t lens_coord(const float* X, int64_t n, int64_t ld, int32_t col, double* f, int m,
+                       int j, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    { lens_coord_kernel<<<div_up(n, 256), 256, 0, s>>>(X, n, ld, col, f, m, j); note_launch(); }
+    return cudaGetLastError();
+}
+
+cudaError_t check_finite(const float* X, int64_t n, int32_t d, int64_t ld, int* flag,
+                         cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    int blocks = (int)std::min<int64_t>(4096, div_up(n * (int64_t)d, 256));
+    { finite_kernel<<<blocks, 256, 0, s>>>(X, n, d, ld, flag); note_launch(); }
+    return cudaGetLastError();
+}
+
+cudaError_t pca_axes(const float* X, int64_t n, int32_t d, int64_t ld, int K, double* mu,
+                     double* axes, int* status, cudaStream_t s)
+{
+    const int nblk = div_up(n, kMeanRows);
+    Buf part;
+    MGB_TRY(part.alloc(sizeof(double) * (size_t)nblk * d, s));
+    { col_partial_sum_kernel<<<nblk, 256, 0, s>>>(X, n, d, ld, part.as<double>()); note_launch(); }
+    { col_mean_kernel<<<div_up(d, 256), 256, 0, s>>>(part.as<double>(), nblk, d, n, mu); note_launch(); }
+    MGB_TRY(cudaGetLastError());
+
+    const int ntile = div_up(d, kCovT);
+    const int ntri = ntile * (ntile + 1) / 2;
+    const int nchunk = div_up(n, kCovRows);
+    Buf cpart, C;
+    MGB_TRY(cpart.alloc(sizeof(float) * (size_t)nchunk * ntri * kCovT * kCovT, s));
+    MGB_TRY(C.alloc(sizeof(double) * (size_t)d * d, s));
+    { cov_partial_kernel<<<dim3(ntri, nchunk), 256, 0, s>>>(X, n, d, ld, mu, cpart.as<float>(), ntile); note_launch(); }
+    { cov_reduce_kernel<<<ntri, 256, 0, s>>>(cpart.as<float>(), nchunk, ntile, d, n, C.as<double>()); note_launch(); }
+    MGB_TRY(cudaGetLastError());
+    const size_t smem = sizeof(double) * 2 * (size_t)d;
+    if (smem > 48 * 1024)
+        MGB_TRY(cudaFuncSetAttribute(power_iter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    { power_iter_kernel<<<1, 1024, smem, s>>>(C.as<double>(), d, K, axes, status); note_launch(); }
+    return cudaGetLastError();
+}
+
+}  // namespace mgb

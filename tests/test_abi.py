@@ -1,0 +1,60 @@
+"""The C ABI library loads and exports every function include/mapper.h
+declares (no GPU needed: no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "mapper.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(mapper_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2011_03209_gb300 import _capi, build
+    build.build()
+    return _capi.load()
+
+
+def test_header_lists_the_api():
+    names = _declared()
+    for must in ("mapper_lens", "mapper_cover", "mapper_cluster", "mapper_nerve", "mapper_graph"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2011_03209_gb300 import _capi
+    names = _declared()
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(_capi.EXPORTS)
+
+
+def test_abi_version_and_strings(lib):
+    assert lib.mapper_abi_version() == 1
+    assert lib.mapper_strerror(0) == b"ok"
+    assert lib.mapper_strerror(-4) == b"device wait timed out"
+
+
+def test_struct_layouts_match_header():
+    from paper_2011_03209_gb300 import _capi
+    # mapper_params: 7 int32, pad to 8, 2 doubles, double, 2 int32
+    assert ctypes.sizeof(_capi.MapperParams) == 64
+    assert _capi.MapperParams.overlap.offset == 32
+    assert ctypes.sizeof(_capi.MapperStats) == 8 * 22
+
+
+def test_null_and_bad_arguments_are_rejected_without_a_gpu(lib):
+    from paper_2011_03209_gb300 import _capi
+    assert lib.mapper_graph(None, None, 0, 0, 0, None, None) == _capi.MAPPER_EINVAL
+    assert lib.mapper_cover_sizes(None, None, None) == _capi.MAPPER_EINVAL
+    assert lib.mapper_stats_get(None, None) == _capi.MAPPER_EINVAL
+    lib.mapper_free(None)
+    assert lib.mapper_last_error()

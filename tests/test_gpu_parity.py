@@ -1,0 +1,206 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every comparison is exact: the lens is the same IEEE double, the cover
+membership, per-slot core flags and cluster labels, node memberships and
+edges are equal element by element. The oracle is fed the GPU's lens (and,
+for principal-component lenses, checked against the GPU's basis), so a lens
+rounding difference could not hide a clustering difference."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2011_03209_gb300 import synth
+
+torch = pytest.importorskip("torch")
+mg = pytest.importorskip("paper_2011_03209_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = mg.Context(0)
+    c.set_timing(True)
+    yield c
+    c.close()
+
+
+def run_gpu(ctx, X, kinds, args, nint, ov, eps, min_pts, prec=mg.FP32):
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).to("cuda:0")
+    g = mg.mapper_graph(ctx, Xd, mg.params(kinds, args, nint, ov, eps, min_pts, prec))
+    out = g.numpy()
+    out["lens"], out["pca"] = g.lens(X.shape[0], len(kinds))
+    out["elem_offsets"], out["elem_points"] = g.cover().numpy()
+    out["labels"], out["core"] = g.clusters().numpy(len(out["elem_points"]))
+    out["stats"] = g.stats()
+    return out
+
+
+def assert_same_graph(X, res, nint, ov, eps, min_pts):
+    ref = oracle.mapper_graph(X, res["lens"], nint, ov, eps, min_pts)
+    for k in ("elem_offsets", "elem_points", "core", "labels", "node_offsets", "node_members",
+              "node_elem", "edges"):
+        assert np.array_equal(np.asarray(res[k]), np.asarray(ref[k])), k
+    assert res["stats"]["near_ties"] == ref["near_ties"]
+    return ref
+
+
+def _eps(X, q, seed):
+    if X.shape[0] < 3:
+        return 0.5
+    return synth.eps_at_percentile(X, q, seed, n_pairs=min(2000, X.shape[0] * 8))
+
+
+TINY = [
+    # n, d, seed, n_int, overlap, q, min_pts
+    (1, 3, 0, 4, 0.3, 10, 1),
+    (2, 1, 1, 2, 0.0, 50, 2),
+    (3, 2, 2, 3, 0.5, 40, 2),
+    (17, 5, 3, 5, 0.25, 20, 3),
+    (64, 8, 4, 6, 0.3, 10, 4),
+    (129, 33, 5, 3, 0.2, 15, 5),
+    (300, 2, 6, 10, 0.4, 5, 3),
+    (257, 70, 7, 4, 0.1, 8, 2),
+    (400, 16, 8, 1, 0.0, 3, 6),
+]
+
+
+@pytest.mark.parametrize("n,d,seed,n_int,ov,q,min_pts", TINY)
+def test_tiny_l2(ctx, n, d, seed, n_int, ov, q, min_pts):
+    X = synth.tiny_random(n, d, seed, scale=2.0)
+    eps = _eps(X, q, seed)
+    res = run_gpu(ctx, X, (0,), (0,), (n_int,), (ov,), eps, min_pts)
+    assert np.array_equal(res["lens"][:, 0], oracle.lens_l2(X))
+    assert_same_graph(X, res, (n_int,), (ov,), eps, min_pts)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_duplicates_min_pts_one_coord_lens(ctx, seed):
+    X = synth.tiny_random(350, 4, seed, dup_frac=0.3)
+    eps = _eps(X, 5, seed)
+    res = run_gpu(ctx, X, (1,), (2,), (7,), (0.35,), eps, 1)
+    assert np.array_equal(res["lens"][:, 0], X[:, 2].astype(np.float64))
+    assert_same_graph(X, res, (7,), (0.35,), eps, 1)
+
+
+def test_constant_lens_and_min_pts_above_size(ctx):
+    X = synth.tiny_random(200, 3, 9)
+    X[:, 1] = 0.25                                   # every lens value equal
+    res = run_gpu(ctx, X, (1,), (1,), (5,), (0.2,), 0.3, 4)
+    assert res["elem_offsets"][1] == 200 and res["elem_offsets"][-1] == 200
+    assert_same_graph(X, res, (5,), (0.2,), 0.3, 4)
+    res = run_gpu(ctx, X, (0,), (0,), (5,), (0.2,), 0.3, 500)   # minPts > n: all noise
+    assert len(res["node_elem"]) == 0 and len(res["edges"]) == 0
+    assert_same_graph(X, res, (5,), (0.2,), 0.3, 500)
+
+
+def test_many_empty_elements(ctx):
+    X = synth.separated_blobs(3, 40, 4, gap=50.0, std=0.2, seed=2)
+    res = run_gpu(ctx, X, (0,), (0,), (97,), (0.15,), 1.0, 3)
+    sizes = np.diff(res["elem_offsets"])
+    assert (sizes == 0).sum() > 50
+    assert_same_graph(X, res, (97,), (0.15,), 1.0, 3)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_2d_cover(ctx, seed):
+    X = synth.tiny_random(900, 6, seed, scale=3.0)
+    eps = _eps(X, 4, seed)
+    res = run_gpu(ctx, X, (1, 0), (0, 0), (6, 5), (0.3, 0.2), eps, 4)
+    assert_same_graph(X, res, (6, 5), (0.3, 0.2), eps, 4)
+
+
+def test_circle_cycle_graph(ctx):
+    X = synth.circle(720)
+    res = run_gpu(ctx, X, (1,), (1,), (6,), (0.3,), 0.05, 2)
+    ref = assert_same_graph(X, res, (6,), (0.3,), 0.05, 2)
+    assert len(ref["node_elem"]) == 10 and len(ref["edges"]) == 10
+
+
+def test_pca_lens_basis_and_bits(ctx):
+    X = synth.gaussian_mixture(6000, 12, 5, seed=4, centre_box=5.0, std_lo=0.3, std_hi=1.5,
+                               anisotropic=True)
+    eps = _eps(X, 2, 4)
+    res = run_gpu(ctx, X, (2, 2), (0, 1), (8, 6), (0.25, 0.25), eps, 5)
+    d = X.shape[1]
+    mu, V = res["pca"][:d], res["pca"][d:].reshape(-1, d)
+    omu, oV, _ = oracle.pca(X, 2)
+    np.testing.assert_allclose(mu, omu, rtol=1e-12, atol=1e-12)
+    for c in range(2):
+        assert 1.0 - abs(V[c] @ oV[c]) <= 1e-6
+        assert V[c][np.argmax(np.abs(V[c]))] > 0
+    for c in range(2):                                 # lens bits given the GPU basis
+        assert np.array_equal(res["lens"][:, c], oracle.lens_project(X, mu, V[c]))
+    assert_same_graph(X, res, (8, 6), (0.25, 0.25), eps, 5)
+
+
+def test_blobs_circle_5k_exact(ctx):
+    w = synth.blobs_circle_5k()
+    res = run_gpu(ctx, w.X, w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts)
+    ref = assert_same_graph(w.X, res, w.n_intervals, w.overlap, w.eps, w.min_pts)
+    assert res["stats"]["near_ties"] == 0 and ref["near_ties"] == 0
+    assert len(ref["node_elem"]) > 0
+
+
+def test_mixture_100k_d64_exact(ctx):
+    w = synth.mixture_100k()
+    res = run_gpu(ctx, w.X, w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts)
+    d = w.d
+    omu, oV, _ = oracle.pca(w.X, 1)
+    assert 1.0 - abs(res["pca"][d:2 * d] @ oV[0]) <= 1e-6
+    ref = assert_same_graph(w.X, res, w.n_intervals, w.overlap, w.eps, w.min_pts)
+    assert ref["near_ties"] == 0
+    assert len(ref["node_elem"]) > 10 and len(ref["edges"]) > 0
+
+
+def _check_graph_properties(res, n_points):
+    """Properties that hold at any size, checked on the GPU's own output."""
+    no, nm, ne, E = res["node_offsets"], res["node_members"], res["node_elem"], res["edges"]
+    N = len(ne)
+    assert np.all(np.diff(no) > 0)
+    node_of = np.repeat(np.arange(N), np.diff(no))
+    # members ascending within a node; nodes ordered by element
+    same = node_of[1:] == node_of[:-1]
+    assert np.all(nm[1:][same] > nm[:-1][same])
+    assert np.all(np.diff(ne) >= 0)
+    # nodes of one element are disjoint
+    key = ne[node_of].astype(np.int64) * n_points + nm
+    assert len(np.unique(key)) == len(key)
+    # edge {u, v} iff some point lies in both: rebuild from memberships
+    order = np.lexsort((node_of, nm))
+    pts, nodes = nm[order], node_of[order]
+    start = np.r_[0, np.nonzero(np.diff(pts))[0] + 1]
+    ends = np.r_[start[1:], len(pts)]
+    pairs = set()
+    for s, t in zip(start, ends):
+        ids = nodes[s:t]
+        for a in range(len(ids)):
+            for b in range(a + 1, len(ids)):
+                pairs.add((int(ids[a]), int(ids[b])))
+    assert sorted(pairs) == [tuple(e) for e in E.tolist()]
+
+
+@pytest.mark.slow
+def test_clusters_1m_d256_sampled(ctx):
+    """Full-size 1M x 256 workload as the benchmark runs it: lens rows, the
+    whole cover, and the DBSCAN of sampled elements against the oracle; the
+    nerve by its definition."""
+    w = synth.clusters_1m_d256()
+    res = run_gpu(ctx, w.X, w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts)
+    rng = np.random.default_rng(0)
+    rows = rng.choice(w.n, 4000, replace=False)
+    assert np.array_equal(res["lens"][rows, 0], oracle.lens_l2(w.X[rows]))
+    offs, pts = oracle.cover(res["lens"], w.n_intervals, w.overlap)
+    assert np.array_equal(offs, res["elem_offsets"]) and np.array_equal(pts, res["elem_points"])
+    sizes = np.diff(offs)
+    nonempty = np.nonzero(sizes)[0]
+    picks = [nonempty[np.argmin(sizes[nonempty])],
+             nonempty[np.argsort(sizes[nonempty])[len(nonempty) // 3]]]
+    for e in picks:
+        s, t = offs[e], offs[e + 1]
+        _, core, label, ties = oracle.dbscan(w.X, pts[s:t], w.eps, w.min_pts)
+        assert np.array_equal(res["core"][s:t], core), e
+        assert np.array_equal(res["labels"][s:t], label), e
+        assert ties == 0
+    assert res["stats"]["near_ties"] == 0
+    _check_graph_properties(res, w.n)
