@@ -95,11 +95,14 @@ def test_constant_lens_and_min_pts_above_size(ctx):
 
 
 def test_many_empty_elements(ctx):
-    X = synth.separated_blobs(3, 40, 4, gap=50.0, std=0.2, seed=2)
-    res = run_gpu(ctx, X, (0,), (0,), (97,), (0.15,), 1.0, 3)
+    # three tight blobs 50 apart along axis 0, coordinate lens on that axis:
+    # most of the 97 intervals hold no point
+    X = synth.tiny_random(120, 4, 2, scale=0.4)
+    X[:, 0] += np.repeat(np.array([0.0, 50.0, 100.0], dtype=np.float32), 40)
+    res = run_gpu(ctx, X, (1,), (0,), (97,), (0.15,), 0.5, 3)
     sizes = np.diff(res["elem_offsets"])
-    assert (sizes == 0).sum() > 50
-    assert_same_graph(X, res, (97,), (0.15,), 1.0, 3)
+    assert (sizes == 0).sum() > 80
+    assert_same_graph(X, res, (97,), (0.15,), 0.5, 3)
 
 
 @pytest.mark.parametrize("seed", [0, 1])
