@@ -201,6 +201,43 @@ int mapper_stats_get(const void* handle, mapper_stats* out);
 /* Release any handle (cover, clusters, graph). NULL is a no-op. */
 void mapper_free(void* handle);
 
+/* ----------------------------------------------- allocation-free variant */
+
+/* DBSCAN(eps, minPts) of one point set, allocating no device memory.
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * call cudaMalloc -- code hosted by a framework that owns every device
+ * allocation through a fixed memory plan and forbids its plug-ins to
+ * allocate, or latency-critical code that must never let an allocation
+ * synchronise the device or fail half way through.
+ *
+ * Computes the same per-element DBSCAN as mapper_cluster (FP32 screen, FP64
+ * re-decision of the error band, so results equal the FP64 definition
+ * above) with the n rows of X_dev as the single element:
+ *   label_dev[p] (device, n int64): canonical cluster id = smallest row index
+ *                among the cluster's core points, or -1 for noise;
+ *   core_dev[p]  (device, n uint8, may be NULL): 1 if row p is a core point.
+ * X_dev, label_dev and core_dev are caller-owned device memory on the
+ * calling thread's current device; work is ordered on cuda_stream (a
+ * cudaStream_t, NULL = the legacy default stream) and the call returns after
+ * it completes.
+ *
+ * Scratch lives in one fixed device array inside the library (about 8.5 MB,
+ * held by every GPU that loads the library until the process exits), so
+ * sizes are limited: n <= MAPPER_NOALLOC_MAX_POINTS and
+ * d <= MAPPER_NOALLOC_MAX_DIM; larger inputs return MAPPER_EINVAL before any
+ * GPU work. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it: make that first call before any
+ * stream capture on that device. Every call shares the array and clears what
+ * must start at zero itself; calls that overlap on the GPU (two streams, two
+ * threads) race on it and must be ordered by the caller.
+ * Errors: MAPPER_EINVAL (sizes, eps, minPts, null or non-device pointers),
+ * MAPPER_ENONFINITE (X holds NaN/Inf), MAPPER_ECUDA. */
+#define MAPPER_NOALLOC_MAX_POINTS 8192
+#define MAPPER_NOALLOC_MAX_DIM 256
+int mapper_dbscan_noalloc(const float* X_dev, int64_t n, int32_t d, int64_t ld, double eps,
+                          int32_t min_pts, int64_t* label_dev, uint8_t* core_dev,
+                          void* cuda_stream);
+
 const char* mapper_strerror(int status);
 const char* mapper_last_error(void);
 int mapper_abi_version(void);

@@ -19,7 +19,7 @@ from ._capi import BF16, FP32, LENS_COORD, LENS_L2, LENS_PCA, MapperError, Mappe
 __all__ = [
     "Context", "Cover", "Clusters", "Graph", "MapperError", "mapper_lens", "mapper_cover",
     "mapper_cluster", "mapper_nerve", "mapper_graph", "params", "LENS_L2", "LENS_COORD",
-    "LENS_PCA", "FP32", "BF16",
+    "LENS_PCA", "FP32", "BF16", "mapper_dbscan_noalloc",
 ]
 
 
@@ -232,3 +232,23 @@ def mapper_graph(ctx: Context, X, prm: MapperParams) -> Graph:
     _capi.check(ctx._lib.mapper_graph(ctx.h, p, n, d, ld, ctypes.byref(prm), ctypes.byref(h)),
                 "mapper_graph")
     return Graph(ctx._lib, h)
+
+
+def mapper_dbscan_noalloc(X, eps: float, min_pts: int, label=None, core=None, stream=None):
+    """DBSCAN of the rows of one CUDA tensor X (n <= 8192, d <= 256) through
+    the allocation-free entry point: the library allocates no device memory
+    for it (its scratch is a fixed array inside the library). `label` (int64)
+    and `core` (uint8) are caller-owned CUDA tensors of n entries, created
+    here when not given. Returns (label, core)."""
+    torch = _torch()
+    p, n, d, ld, _keep = _x_args(X)
+    if label is None:
+        label = torch.empty(n, dtype=torch.int64, device=X.device)
+    if core is None:
+        core = torch.empty(n, dtype=torch.uint8, device=X.device)
+    s = torch.cuda.current_stream(X.device) if stream is None else stream
+    lib = _capi.load()
+    _capi.check(lib.mapper_dbscan_noalloc(p, n, d, ld, float(eps), int(min_pts), _vp(label.data_ptr()),
+                                          _vp(core.data_ptr()), _vp(s.cuda_stream)),
+                "mapper_dbscan_noalloc")
+    return label, core

@@ -31,8 +31,11 @@ EXPORTS = (
     "mapper_cluster", "mapper_clusters_copy", "mapper_nerve", "mapper_graph",
     "mapper_graph_sizes", "mapper_graph_copy", "mapper_graph_lens", "mapper_graph_cover",
     "mapper_graph_clusters", "mapper_stats_get", "mapper_free", "mapper_strerror",
-    "mapper_last_error", "mapper_abi_version",
+    "mapper_last_error", "mapper_abi_version", "mapper_dbscan_noalloc",
 )
+
+NOALLOC_MAX_POINTS = 8192
+NOALLOC_MAX_DIM = 256
 
 
 class MapperParams(ctypes.Structure):
@@ -126,6 +129,7 @@ def load(path: str | None = None):
             "mapper_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "mapper_last_error": (ctypes.c_char_p, []),
             "mapper_abi_version": (ctypes.c_int, []),
+            "mapper_dbscan_noalloc": (ctypes.c_int, [P, i64, i32, i64, f64, i32, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)

@@ -259,29 +259,6 @@ int run_cover(mapper_ctx* ctx, const double* lens, int64_t n, int32_t m, const i
     return MAPPER_OK;
 }
 
-// FP32 screen thresholds. The sum of d squared differences accumulated by
-// FMA in FP32 satisfies |s - d2| <= ((1+u)^2 (1+gamma_d) - 1) d2 + tiny
-// (u = 2^-24, gamma_d = d u / (1 - d u); all terms are nonnegative, the
-// subtraction rounds once, each FMA once, subnormal results add at most
-// 2^-149 each). With eta = 1.5 (d + 4) u the pair is certainly inside when
-// s <= eps2 (1 - eta) - tiny and certainly outside when s > eps2 (1 + eta)
-// + tiny; the bounds are rounded outward to float.
-void fp32_thresholds(double eps2, int d, float* lo, float* hi)
-{
-    const double u = std::ldexp(1.0, -24);
-    const double eta = 1.5 * (d + 4) * u;
-    const double tiny = 3.0 * (d + 2) * std::ldexp(1.0, -149);
-    const double l = eps2 * (1.0 - eta) - tiny;
-    const double h = eps2 * (1.0 + eta) + tiny;
-    float lf = (float)l;
-    if ((double)lf > l) lf = std::nextafter(lf, -INFINITY);
-    if (l <= 0.0) lf = -1.0f;
-    float hf = (float)h;
-    if ((double)hf < h) hf = std::nextafter(hf, INFINITY);
-    *lo = lf;
-    *hi = hf;
-}
-
 // ---------------------------------------------------------------- cluster
 int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
                 const std::shared_ptr<CoverData>& cov, double eps, int32_t min_pts, int32_t precision,

@@ -28,6 +28,10 @@ struct PassArgs {
     unsigned long long* stats;   // kStat* counters
 };
 
+// FP32 screen thresholds for eps2 at dimension d: a pair is certainly a
+// neighbour when the FP32 screen value is <= *lo, certainly not when > *hi.
+void fp32_thresholds(double eps2, int d, float* lo, float* hi);
+
 cudaError_t gather_rows(const float* X, int64_t ld, int d, int dp, const int32_t* slot_point,
                         int64_t M, float* G, int* nonfinite, cudaStream_t s);
 cudaError_t element_offsets(const uint64_t* keys, int64_t M, int64_t E, int64_t* elem_off,

@@ -15,6 +15,7 @@
 // it is re-decided in FP64 with the defining expression (k ascending, one
 // rounding per operation), so decisions equal the FP64 definition exactly.
 #include <cfloat>
+#include <cmath>
 #include <climits>
 
 #include "dbscan.cuh"
@@ -469,6 +470,29 @@ __global__ void unique_emit_kernel(const uint64_t* __restrict__ k, const int32_t
 inline unsigned grid_for(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, div_up(n, t)); }
 
 }  // namespace
+
+// FP32 screen thresholds. The sum of d squared differences accumulated by
+// FMA in FP32 satisfies |s - d2| <= ((1+u)^2 (1+gamma_d) - 1) d2 + tiny
+// (u = 2^-24, gamma_d = d u / (1 - d u); all terms are nonnegative, the
+// subtraction rounds once, each FMA once, subnormal results add at most
+// 2^-149 each). With eta = 1.5 (d + 4) u the pair is certainly inside when
+// s <= eps2 (1 - eta) - tiny and certainly outside when s > eps2 (1 + eta)
+// + tiny; the bounds are rounded outward to float.
+void fp32_thresholds(double eps2, int d, float* lo, float* hi)
+{
+    const double u = std::ldexp(1.0, -24);
+    const double eta = 1.5 * (d + 4) * u;
+    const double tiny = 3.0 * (d + 2) * std::ldexp(1.0, -149);
+    const double l = eps2 * (1.0 - eta) - tiny;
+    const double h = eps2 * (1.0 + eta) + tiny;
+    float lf = (float)l;
+    if ((double)lf > l) lf = std::nextafter(lf, -INFINITY);
+    if (l <= 0.0) lf = -1.0f;
+    float hf = (float)h;
+    if ((double)hf < h) hf = std::nextafter(hf, INFINITY);
+    *lo = lf;
+    *hi = hf;
+}
 
 cudaError_t gather_rows(const float* X, int64_t ld, int d, int dp, const int32_t* slot_point,
                         int64_t M, float* G, int* nonfinite, cudaStream_t s)
