@@ -110,9 +110,9 @@ typedef struct mapper_stats {
     int64_t n_elements;      /* cover elements */
     int64_t n_members;       /* sum over elements of n_i */
     double sum_ni2;          /* sum over elements of n_i^2 */
-    int64_t tile_pairs;      /* tile pairs of the neighbour-count pass */
-    int64_t tile_pairs_out;  /* ... certified all-out by bounding spheres */
-    int64_t tile_pairs_in;   /* ... certified all-in by bounding spheres */
+    int64_t tile_pairs;      /* candidate tile pairs (both tiles in one element) */
+    int64_t tile_pairs_out;  /* ... certified all-out by bounding spheres (skipped) */
+    int64_t tile_pairs_in;   /* ... certified all-in by bounding spheres (no distances) */
     int64_t pairs_screened;  /* point pairs evaluated by the screen, all passes */
     int64_t band_pairs;      /* pairs re-decided in FP64, all passes */
     int64_t near_ties;       /* unordered pairs with |d^2 - eps^2| <= 1e-12 eps^2 */
@@ -122,6 +122,12 @@ typedef struct mapper_stats {
     int64_t n_launches;      /* kernels this call launched */
     double ms_lens, ms_cover, ms_cluster, ms_nerve, ms_total;  /* device time (timing on) */
     double ms_pass[3];       /* device time of the count, union and border passes */
+    double ms_tiles;         /* device time of tile layout and tile-pair classification */
+    int64_t tile_pairs_tc;   /* mixed tile pairs screened on tensor cores */
+    int64_t tile_pairs_simt; /* mixed tile pairs screened on CUDA cores (FP32) */
+    int64_t union_skipped;   /* union-pass tile pairs skipped: their cores already joined */
+    int64_t n_groups;        /* pivot groups of the tile layout */
+    int64_t n_rows;          /* rows of the tile layout (memberships + tile padding) */
 } mapper_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -221,7 +227,7 @@ void mapper_free(void* handle);
  * cudaStream_t, NULL = the legacy default stream) and the call returns after
  * it completes.
  *
- * Scratch lives in one fixed device array inside the library (about 8.5 MB,
+ * Scratch lives in one fixed device array inside the library (about 8.6 MB,
  * held by every GPU that loads the library until the process exits), so
  * sizes are limited: n <= MAPPER_NOALLOC_MAX_POINTS and
  * d <= MAPPER_NOALLOC_MAX_DIM; larger inputs return MAPPER_EINVAL before any

@@ -73,6 +73,12 @@ class MapperStats(ctypes.Structure):
         ("ms_nerve", ctypes.c_double),
         ("ms_total", ctypes.c_double),
         ("ms_pass", ctypes.c_double * 3),
+        ("ms_tiles", ctypes.c_double),
+        ("tile_pairs_tc", ctypes.c_int64),
+        ("tile_pairs_simt", ctypes.c_int64),
+        ("union_skipped", ctypes.c_int64),
+        ("n_groups", ctypes.c_int64),
+        ("n_rows", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:

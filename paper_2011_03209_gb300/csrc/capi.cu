@@ -57,7 +57,7 @@ struct CoverData {
 struct ClusterData {
     StreamRef stream;
     std::shared_ptr<CoverData> cover;
-    Buf count, core, root, border, lab, is_root, is_member, slot_label;
+    Buf core, lab, is_root, is_member, slot_label;    // per cover slot
     mapper_stats stats{};
 };
 
@@ -260,6 +260,10 @@ int run_cover(mapper_ctx* ctx, const double* lens, int64_t n, int32_t m, const i
 }
 
 // ---------------------------------------------------------------- cluster
+// Per-element DBSCAN: tiles ordered by pivot group (k_tiles.cu), tile pairs
+// classified by bounding spheres, then the passes over the three lists:
+// all-in pairs need no distance, mixed pairs of one group go to the
+// tensor-core screen (BF16) and all others to the CUDA-core FP32 screen.
 int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
                 const std::shared_ptr<CoverData>& cov, double eps, int32_t min_pts, int32_t precision,
                 std::shared_ptr<ClusterData>* out, int* nonfinite_dev)
@@ -272,7 +276,10 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     cudaStream_t s = ctx->stream->s;
     const int64_t M = cov->M, E = cov->E;
     const int dp = (d + 31) / 32 * 32;
-    const double est = (double)M * dp * 4.0 + (double)M * 48.0;
+    const bool use_tc = precision == MAPPER_BF16;
+    const int cap = (min_pts >= 2 && min_pts - 1 <= 64) ? min_pts - 1 : 0;
+    const double rows_est = (double)M + 128.0 * (double)E;
+    const double est = rows_est * dp * (use_tc ? 8.0 : 4.0) + rows_est * (40.0 + 4.0 * cap);
     if (ctx->budget && est > (double)ctx->budget)
         return fail(MAPPER_ENOMEM, "estimated scratch exceeds the context's HBM budget");
 
@@ -283,24 +290,14 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     st.n_points = n;
     st.n_elements = E;
     st.n_members = M;
-    std::vector<int64_t> h_pairs(E + 1, 0);
     double s2 = 0.0;
     for (int64_t e = 0; e < E; ++e) {
-        const int64_t ne = cov->h_elem_off[e + 1] - cov->h_elem_off[e];
-        const int64_t T = (ne + 127) / 128;
-        s2 += (double)ne * (double)ne;
-        h_pairs[e + 1] = h_pairs[e] + T * (T + 1) / 2;
+        const double ne = (double)(cov->h_elem_off[e + 1] - cov->h_elem_off[e]);
+        s2 += ne * ne;
     }
     st.sum_ni2 = s2;
-    const int64_t n_pairs = h_pairs[E];
-    st.tile_pairs = n_pairs;
-    if (n_pairs > INT32_MAX) return fail(MAPPER_ENOMEM, "too many tile pairs for one launch");
 
-    Buf G, pair_off, stats, flag;
-    CK(G.alloc(sizeof(float) * (size_t)M * dp, s), "alloc rows");
-    CK(pair_off.alloc(sizeof(int64_t) * (E + 1), s), "alloc");
-    CK(cudaMemcpyAsync(pair_off.p, h_pairs.data(), sizeof(int64_t) * (E + 1), cudaMemcpyHostToDevice, s),
-       "copy");
+    Buf stats, flag;
     CK(stats.alloc(sizeof(unsigned long long) * kStatCount, s), "alloc");
     CK(cudaMemsetAsync(stats.p, 0, sizeof(unsigned long long) * kStatCount, s), "memset");
     int* nf = nonfinite_dev;
@@ -309,58 +306,95 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         CK(cudaMemsetAsync(flag.p, 0, sizeof(int), s), "memset");
         nf = flag.as<int>();
     }
-    CK(c->count.alloc(sizeof(int32_t) * M, s), "alloc");
-    CK(c->core.alloc(M, s), "alloc");
-    CK(c->root.alloc(sizeof(int32_t) * M, s), "alloc");
-    CK(c->border.alloc(sizeof(int32_t) * M, s), "alloc");
-    Buf parent;
-    CK(parent.alloc(sizeof(int32_t) * M, s), "alloc");
-    CK(cudaMemsetAsync(c->count.p, 0, sizeof(int32_t) * M, s), "memset");
 
-    CK(gather_rows(X, ld, d, dp, cov->slot_point.as<int32_t>(), M, G.as<float>(), nf, s), "gather");
+    Timer pt(ctx->timing, s);
+    pt.mark();                                                    // 0
+    TileLayout L;
+    int rc = build_tiles(X, n, d, ld, dp, cov->slot_point.as<int32_t>(), cov->slot_elem.as<int32_t>(), M, E,
+                         4.0 * eps, use_tc, &L, nf, s);
+    if (rc) return rc;
+    PairLists PL;
+    if ((rc = classify_pairs(L, dp, E, eps, use_tc, &PL, s))) return rc;
+    const int64_t R = L.R;
+    st.tile_pairs = PL.n_candidates;
+    st.tile_pairs_out = PL.n_out;
+    st.tile_pairs_in = PL.n[kListAllIn];
+    st.tile_pairs_tc = PL.n[kListTC];
+    st.tile_pairs_simt = PL.n[kListSimt];
+    st.n_groups = L.n_groups;
+    if (PL.n[kListSimt] > INT32_MAX || PL.n[kListTC] > INT32_MAX || PL.n[kListAllIn] > INT32_MAX)
+        return fail(MAPPER_ENOMEM, "too many tile pairs for one launch");
+
+    Buf count, nbr, core, parent, root, border;
+    CK(count.alloc(sizeof(int32_t) * R, s), "alloc");
+    CK(core.alloc(R, s), "alloc");
+    CK(parent.alloc(sizeof(int32_t) * R, s), "alloc");
+    CK(root.alloc(sizeof(int32_t) * R, s), "alloc");
+    CK(border.alloc(sizeof(unsigned long long) * R, s), "alloc");
+    if (cap) CK(nbr.alloc(sizeof(int32_t) * (size_t)R * cap, s), "alloc");
+    CK(cudaMemsetAsync(count.p, 0, sizeof(int32_t) * R, s), "memset");
 
     PassArgs a{};
-    a.G = G.as<float>();
+    a.G = L.G.as<float>();
     a.dp = dp;
     a.d = d;
-    a.elem_off = cov->elem_off.as<int64_t>();
-    a.pair_off = pair_off.as<int64_t>();
-    a.E = (int)E;
+    a.tile_n = L.tile_n.as<int32_t>();
     a.eps2 = eps * eps;
     a.tie_thr = 1e-12 * a.eps2;
     fp32_thresholds(a.eps2, d, &a.lo_thr, &a.hi_thr);
-    a.count = c->count.as<int32_t>();
-    a.core = c->core.as<uint8_t>();
+    a.row_pt = L.row_pt.as<int32_t>();
+    a.count = count.as<int32_t>();
+    a.nbr = nbr.as<int32_t>();
+    a.cap = cap;
+    a.core = core.as<uint8_t>();
     a.parent = parent.as<int32_t>();
-    a.root = c->root.as<int32_t>();
-    a.border = c->border.as<int32_t>();
+    a.root = root.as<int32_t>();
+    a.border = border.as<unsigned long long>();
     a.stats = stats.as<unsigned long long>();
-
-    Timer pt(ctx->timing, s);
-    if (precision == MAPPER_BF16) {
-        int rc = tc_cluster_passes(a, n_pairs, min_pts, s);
-        if (rc != MAPPER_OK) return rc;
-    } else {
-        pt.mark();
-        CK(simt_pass(1, a, n_pairs, s), "pass 1");
-        pt.mark();
-        CK(core_flags(a.count, M, min_pts, c->core.as<uint8_t>(), a.parent, a.border, a.stats, s), "core");
-        pt.mark();
-        CK(simt_pass(2, a, n_pairs, s), "pass 2");
-        pt.mark();
-        CK(flatten(a.parent, a.core, M, c->root.as<int32_t>(), s), "flatten");
-        pt.mark();
-        CK(simt_pass(3, a, n_pairs, s), "pass 3");
-        pt.mark();
+    PassArgs a_in = a, a_tc = a, a_simt = a;
+    a_in.pairs = PL.list[kListAllIn].as<int2>();
+    a_tc.pairs = PL.list[kListTC].as<int2>();
+    a_simt.pairs = PL.list[kListSimt].as<int2>();
+    TcArgs t{};
+    if (use_tc) {
+        t.Ah = L.Ah.p;
+        t.Al = L.Al.p;
+        t.rn2 = L.rn2.as<float>();
+        t.rn = L.rn.as<float>();
+        t.R = R;
     }
 
+    pt.mark();                                                    // 1
+    CK(allin_pass(1, a_in, PL.n[kListAllIn], s), "pass 1 all-in");
+    if (use_tc) { if ((rc = tc_pass(1, a_tc, t, PL.n[kListTC], s))) return rc; }
+    else CK(simt_pass(1, a_tc, PL.n[kListTC], s), "pass 1 tc list");
+    CK(simt_pass(1, a_simt, PL.n[kListSimt], s), "pass 1");
+    pt.mark();                                                    // 2
+    CK(core_flags(a.count, R, min_pts, core.as<uint8_t>(), a.parent, a.border, a.stats, s), "core");
+    pt.mark();                                                    // 3
+    CK(allin_pass(2, a_in, PL.n[kListAllIn], s), "pass 2 all-in");
+    if (use_tc) { if ((rc = tc_pass(2, a_tc, t, PL.n[kListTC], s))) return rc; }
+    else CK(simt_pass(2, a_tc, PL.n[kListTC], s), "pass 2 tc list");
+    CK(simt_pass(2, a_simt, PL.n[kListSimt], s), "pass 2");
+    pt.mark();                                                    // 4
+    CK(flatten(a.parent, a.core, R, root.as<int32_t>(), s), "flatten");
+    if (cap) {
+        CK(border_from_lists(a.count, a.nbr, cap, a.core, a.root, a.row_pt, R, a.border, s), "border");
+    } else if (min_pts > 1) {
+        CK(allin_pass(3, a_in, PL.n[kListAllIn], s), "pass 3 all-in");
+        CK(simt_pass(3, a_tc, PL.n[kListTC], s), "pass 3 tc list");
+        CK(simt_pass(3, a_simt, PL.n[kListSimt], s), "pass 3");
+    }
+    pt.mark();                                                    // 5
+
+    CK(c->core.alloc(M, s), "alloc");
     CK(c->lab.alloc(sizeof(int32_t) * M, s), "alloc");
     CK(c->is_root.alloc(sizeof(int32_t) * M, s), "alloc");
     CK(c->is_member.alloc(sizeof(int32_t) * M, s), "alloc");
     CK(c->slot_label.alloc(sizeof(int64_t) * M, s), "alloc");
-    CK(labels(a.core, c->root.as<int32_t>(), a.border, cov->slot_point.as<int32_t>(), M,
-              c->lab.as<int32_t>(), c->is_root.as<int32_t>(), c->is_member.as<int32_t>(),
-              c->slot_label.as<int64_t>(), s), "labels");
+    CK(rows_to_slots(L.row_slot.as<int32_t>(), a.row_pt, a.core, a.root, a.border, R, c->lab.as<int32_t>(),
+                     c->is_root.as<int32_t>(), c->is_member.as<int32_t>(), c->slot_label.as<int64_t>(),
+                     c->core.as<uint8_t>(), s), "labels");
 
     unsigned long long h_stats[kStatCount];
     int h_nf = 0;
@@ -372,11 +406,12 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     st.near_ties = (int64_t)h_stats[kStatTies];
     st.pairs_screened = (int64_t)h_stats[kStatScreened];
     st.n_core = (int64_t)h_stats[kStatCore];
-    st.tile_pairs_out = (int64_t)h_stats[kStatTileOut];
-    st.tile_pairs_in = (int64_t)h_stats[kStatTileIn];
+    st.union_skipped = (int64_t)h_stats[kStatSkipped];
+    st.n_rows = R;
     if (pt.n >= 6) {
-        st.ms_pass[0] = pt.ms(0, 1);
-        st.ms_pass[1] = pt.ms(2, 3);
+        st.ms_tiles = pt.ms(0, 1);
+        st.ms_pass[0] = pt.ms(1, 2);
+        st.ms_pass[1] = pt.ms(3, 4);
         st.ms_pass[2] = pt.ms(4, 5);
     }
     *out = c;
@@ -445,9 +480,7 @@ int run_nerve(mapper_ctx* ctx, const std::shared_ptr<ClusterData>& cl, mapper_gr
     CK(unique_emit(pairs.as<uint64_t>(), flag.as<int32_t>(), upos.as<int64_t>(), P,
                    g->edges.as<int32_t>(), s), "unique emit");
     CK(cudaStreamSynchronize(s), "sync");
-    const double keep[3] = {cl->stats.ms_pass[0], cl->stats.ms_pass[1], cl->stats.ms_pass[2]};
     g->stats = cl->stats;
-    for (int i = 0; i < 3; ++i) g->stats.ms_pass[i] = keep[i];
     g->stats.n_nodes = N;
     g->stats.n_edges = Eg;
     return MAPPER_OK;

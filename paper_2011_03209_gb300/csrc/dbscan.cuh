@@ -1,30 +1,46 @@
-// dbscan.cuh -- internal interface of the per-element DBSCAN passes and of
-// graph assembly (k_dbscan.cu, k_tc.cu).
+// dbscan.cuh -- internal interface of the per-element DBSCAN stage: tile
+// layout (k_tiles.cu), screening passes (k_dbscan.cu, k_tc.cu) and graph
+// assembly (k_nerve.cu).
 #pragma once
 
 #include "common.cuh"
 
 namespace mgb {
 
-enum : int { kStatBand = 0, kStatTies = 1, kStatScreened = 2, kStatCore = 3, kStatTileOut = 4,
-             kStatTileIn = 5, kStatCount = 8 };
+constexpr int kTile = 128;          // rows per tile (one tcgen05 M block)
 
-// Arguments of one screening pass over all tile pairs of all elements.
+enum : int { kStatBand = 0, kStatTies = 1, kStatScreened = 2, kStatCore = 3, kStatTileOut = 4,
+             kStatTileIn = 5, kStatSkipped = 6, kStatCount = 8 };
+
+// Work lists of tile pairs, classified by bounding spheres.
+enum : int { kListAllIn = 0, kListTC = 1, kListSimt = 2, kListCount = 3 };
+
+// Arguments of one screening pass. Rows are points of one element laid out
+// in tiles of kTile rows; a tile pair (a, b), a <= b, belongs to one element.
+//   explicit mode (pairs != nullptr): tile pair q is pairs[q] (tile indices),
+//     tile t spans rows [t*kTile, t*kTile + tile_n[t]);
+//   implicit mode: every tile pair of every element, elements given by
+//     elem_off (rows) and pair_off (tile pairs), rows = cover slots.
 struct PassArgs {
-    const float* G;              // gathered rows, one per membership slot, pitch dp floats
-    int dp;                      // row pitch (multiple of 32, zero padded)
+    const float* G;              // FP32 rows, pitch dp floats (zero padded)
+    int dp;                      // row pitch (multiple of 32)
     int d;                       // true dimension
-    const int64_t* elem_off;     // [E+1] slot offsets of the elements
-    const int64_t* pair_off;     // [E+1] tile-pair offsets of the elements
+    const int2* pairs;           // explicit list, or nullptr
+    const int32_t* tile_n;       // valid rows per tile (explicit mode)
+    const int64_t* elem_off;     // implicit mode: [E+1] row offsets of the elements
+    const int64_t* pair_off;     // implicit mode: [E+1] tile-pair offsets
     int E;
     float lo_thr, hi_thr;        // FP32 screen: in if s <= lo_thr, out if s > hi_thr
     double eps2;                 // eps * eps in double
     double tie_thr;              // 1e-12 * eps2
-    int32_t* count;              // pass 1 output
+    const int32_t* row_pt;       // point index of each row (nullptr: the row index)
+    int32_t* count;              // pass 1 output, per row
+    int32_t* nbr;                // pass 1: first `cap` neighbour rows of each row
+    int cap;                     //   (0: no lists)
     const uint8_t* core;         // passes 2, 3
-    int32_t* parent;             // pass 2 union-find
+    int32_t* parent;             // pass 2 union-find over rows
     const int32_t* root;         // pass 3 (flattened)
-    int32_t* border;             // pass 3 output (root slot or INT_MAX)
+    unsigned long long* border;  // pass 3 output: (canonical point << 32 | root row), min
     unsigned long long* stats;   // kStat* counters
 };
 
@@ -32,19 +48,27 @@ struct PassArgs {
 // neighbour when the FP32 screen value is <= *lo, certainly not when > *hi.
 void fp32_thresholds(double eps2, int d, float* lo, float* hi);
 
-cudaError_t gather_rows(const float* X, int64_t ld, int d, int dp, const int32_t* slot_point,
-                        int64_t M, float* G, int* nonfinite, cudaStream_t s);
+// --- screening passes (k_dbscan.cu)
+cudaError_t simt_pass(int mode, const PassArgs& a, int64_t n_pairs, cudaStream_t s);
+cudaError_t allin_pass(int mode, const PassArgs& a, int64_t n_pairs, cudaStream_t s);
+cudaError_t core_flags(const int32_t* count, int64_t R, int32_t min_pts, uint8_t* core,
+                       int32_t* parent, unsigned long long* border, unsigned long long* stats,
+                       cudaStream_t s);
+cudaError_t flatten(const int32_t* parent, const uint8_t* core, int64_t R, int32_t* root,
+                    cudaStream_t s);
+cudaError_t border_from_lists(const int32_t* count, const int32_t* nbr, int cap,
+                              const uint8_t* core, const int32_t* root, const int32_t* row_pt,
+                              int64_t R, unsigned long long* border, cudaStream_t s);
+// Row space -> cover-slot space: per slot the root slot of its node (or -1),
+// canonical point id (or -1), root flag, member flag and core flag.
+cudaError_t rows_to_slots(const int32_t* row_slot, const int32_t* row_pt, const uint8_t* core,
+                          const int32_t* root, const unsigned long long* border, int64_t R,
+                          int32_t* lab, int32_t* is_root, int32_t* is_member,
+                          int64_t* slot_label, uint8_t* slot_core, cudaStream_t s);
 cudaError_t element_offsets(const uint64_t* keys, int64_t M, int64_t E, int64_t* elem_off,
                             cudaStream_t s);
-cudaError_t tile_pair_offsets(const int64_t* elem_off, int64_t E, int64_t* pair_off, cudaStream_t s);
-cudaError_t simt_pass(int mode, const PassArgs& a, int64_t n_pairs, cudaStream_t s);
-cudaError_t core_flags(const int32_t* count, int64_t M, int32_t min_pts, uint8_t* core,
-                       int32_t* parent, int32_t* border, unsigned long long* stats, cudaStream_t s);
-cudaError_t flatten(const int32_t* parent, const uint8_t* core, int64_t M, int32_t* root,
-                    cudaStream_t s);
-cudaError_t labels(const uint8_t* core, const int32_t* root, const int32_t* border,
-                   const int32_t* slot_point, int64_t M, int32_t* lab, int32_t* is_root,
-                   int32_t* is_member, int64_t* slot_label, cudaStream_t s);
+
+// --- nodes and nerve (k_nerve.cu)
 cudaError_t member_keys(const int32_t* lab, const int64_t* nid, const int64_t* mpos,
                         const int32_t* slot_point, const int32_t* slot_elem, int64_t M,
                         uint64_t* keys, int32_t* node_elem, cudaStream_t s);
@@ -56,5 +80,41 @@ cudaError_t emit_pairs(const uint64_t* keys2, int64_t G, const int64_t* pos, uin
 cudaError_t unique_flags(const uint64_t* k, int64_t P, int32_t* flag, cudaStream_t s);
 cudaError_t unique_emit(const uint64_t* k, const int32_t* flag, const int64_t* pos, int64_t P,
                         int32_t* edges, cudaStream_t s);
+
+// --- tile layout (k_tiles.cu)
+struct TileLayout {
+    int64_t R = 0;               // rows (multiple of kTile)
+    int64_t T = 0;               // tiles
+    int64_t n_seg = 0;           // (element, group) segments
+    int n_groups = 0;            // pivot groups (outliers form group n_groups)
+    Buf row_slot;                // [R] int32 cover slot, -1 for padding
+    Buf row_pt;                  // [R] int32 point, INT32_MAX for padding
+    Buf G;                       // [R x dp] FP32 rows
+    Buf tile_n, tile_seg, tile_elem;      // [T] int32
+    Buf tile_cent;               // [T x dp] FP64 centroid
+    Buf tile_rad;                // [T] FP64 radius about the centroid (rounded up)
+    Buf seg_cent;                // [n_seg x dp] FP64 centroid of each segment
+    Buf seg_outlier;             // [n_seg] int32: 1 if the segment holds outliers
+    Buf Ah, Al;                  // [R x dp] BF16 centred rows (hi and lo parts)
+    Buf rn2, rn;                 // [R] FP32 |a|^2 and |a| (rounded up)
+};
+
+struct PairLists {
+    Buf list[kListCount];        // int2 tile pairs
+    int64_t n[kListCount] = {0, 0, 0};
+    int64_t n_candidates = 0, n_out = 0;
+};
+
+// Orders every element's points by pivot group, lays them out in tiles
+// (a tile never mixes groups) and gathers rows. tau: distance under which two
+// pivots join a group and beyond which a point is an outlier.
+int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const int32_t* slot_point,
+                const int32_t* slot_elem, int64_t M, int64_t E, double tau, bool bf16,
+                TileLayout* L, int* nonfinite, cudaStream_t s);
+// Classifies every tile pair of every element by bounding spheres: out (no
+// pair within eps), all-in, or mixed (to the tensor-core list when both tiles
+// are one non-outlier segment and use_tc, else to the CUDA-core list).
+int classify_pairs(const TileLayout& L, int dp, int64_t E, double eps, bool use_tc,
+                   PairLists* P, cudaStream_t s);
 
 }  // namespace mgb

@@ -1,22 +1,26 @@
-// k_dbscan.cu -- per-cover-element DBSCAN and graph assembly.
+// k_dbscan.cu -- per-cover-element DBSCAN on CUDA cores.
 //
 // "Mapper Interactive" §3: DBSCAN(eps, minPts) clusters the points of each
 // cover element; §4.3 parallelises over elements and precomputes each
-// element's distance matrix. Here the distance matrix is never stored: every
-// element's membership slots are cut into 128-row tiles and each pair of
-// tiles (a <= b) is one CTA that recomputes the tile's squared distances and
+// element's distance matrix. Here the distance matrix is never stored: the
+// rows of an element are cut into tiles of 128 and each tile pair (a <= b) is
+// one CTA that recomputes the pair's squared distances in registers and
 // consumes them at once:
-//   pass 1  neighbour counts      count[s] = |N(s)|           (core: >= minPts)
-//   pass 2  core-core unions      lock-free union-find, root = smallest slot
-//   pass 3  border assignment     smallest root among core neighbours
-// Screen: the FP32 sum of squared differences has a rigorous relative error
-// bound eta (see pass thresholds in capi.cu); a pair is "in" when the screen
-// value is <= eps^2 (1 - eta), "out" when > eps^2 (1 + eta), and otherwise
-// it is re-decided in FP64 with the defining expression (k ascending, one
-// rounding per operation), so decisions equal the FP64 definition exactly.
+//   pass 1  neighbour counts (and the first minPts-1 neighbours of each row,
+//           enough to hold every neighbour of a non-core row)
+//   pass 2  core-core unions: lock-free union-find whose roots are the
+//           component's smallest point index (the canonical id)
+//   pass 3  border rows: the smallest canonical id among core neighbours,
+//           from the stored neighbours (or a third contraction when minPts
+//           is too large to store them)
+// Screen: the FP32 sum of squared differences s has |s - d2| <= eta d2 + tiny
+// (fp32_thresholds); a pair is in when s <= eps^2(1-eta) - tiny, out when
+// s > eps^2(1+eta) + tiny, else it is re-decided in FP64 by the defining
+// expression (k ascending, one rounding per operation), so every decision
+// equals the FP64 definition.
 #include <cfloat>
-#include <cmath>
 #include <climits>
+#include <cmath>
 
 #include "dbscan.cuh"
 
@@ -24,7 +28,7 @@ namespace mgb {
 
 namespace {
 
-constexpr int kT = 128;        // tile rows
+constexpr int kT = kTile;      // tile rows
 constexpr int kK = 32;         // k chunk
 constexpr int kPad = 132;      // smem row pitch (floats)
 
@@ -38,10 +42,11 @@ __device__ __forceinline__ int64_t upper_bound_i64(const int64_t* a, int64_t n, 
     return l;
 }
 
-// q-th entry of the upper triangle (a <= b) of a T x T grid, row-major
+// q-th entry of the upper triangle of a T x T grid: rows of cum(a) = aT -
+// a(a-1)/2 entries (a, a), (a, a+1), ...
 __device__ __forceinline__ void decode_pair(int64_t q, int64_t T, int* ta, int* tb)
 {
-    int64_t l = 0, r = T - 1;                  // largest a with cum(a) <= q
+    int64_t l = 0, r = T - 1;
     while (l < r) {
         const int64_t m = (l + r + 1) >> 1;
         const int64_t cum = m * T - m * (m - 1) / 2;
@@ -62,35 +67,49 @@ __device__ __forceinline__ double exact_sqdist(const float* __restrict__ x, cons
     return s;
 }
 
+__device__ __forceinline__ int key_of(const int32_t* row_pt, int row)
+{
+    return row_pt ? __ldg(row_pt + row) : row;
+}
+
+// Global union-find over rows. Parents always carry a smaller key (point
+// index) than their child, so every chain ends and a root is the smallest
+// key of its component. Path halving only ever points a node at an ancestor.
 __device__ __forceinline__ int gfind(int32_t* parent, int x)
 {
     volatile int32_t* par = parent;
     int p = par[x];
     while (p != x) {
         const int gp = par[p];
-        if (gp != p) par[x] = gp;             // path halving: any ancestor is a valid parent
+        if (gp != p) par[x] = gp;
         x = p;
         p = par[x];
     }
     return x;
 }
 
-__device__ __forceinline__ void gunion(int32_t* parent, int a, int b)
+__device__ __forceinline__ void gunion(int32_t* parent, const int32_t* row_pt, int a, int b)
 {
     while (true) {
         a = gfind(parent, a);
         b = gfind(parent, b);
         if (a == b) return;
-        if (a < b) { const int t = a; a = b; b = t; }
-        // link the larger root under the smaller: roots stay component minima
+        if (key_of(row_pt, a) < key_of(row_pt, b)) { const int t = a; a = b; b = t; }
         if (atomicCAS(&parent[a], a, b) == a) return;
     }
 }
 
+// Shared-memory union-find over the 256 rows of a tile pair, same rules with
+// the local index as key.
 __device__ __forceinline__ int lfind(volatile int* par, int x)
 {
     int p = par[x];
-    while (p != x) { x = p; p = par[x]; }
+    while (p != x) {
+        const int gp = par[p];
+        if (gp != p) par[x] = gp;
+        x = p;
+        p = par[x];
+    }
     return x;
 }
 
@@ -108,63 +127,116 @@ __device__ __forceinline__ void lunion(int* par, int a, int b)
 
 struct Decider {
     const PassArgs& A;
-    __device__ __forceinline__ bool operator()(float s, int64_t slot_a, int64_t slot_b,
+    __device__ __forceinline__ bool operator()(float s, int64_t row_a, int64_t row_b,
                                                bool count_tie) const
     {
         if (s <= A.lo_thr) return true;
         if (s > A.hi_thr && s <= FLT_MAX) return false;
-        const double d2 = exact_sqdist(A.G + slot_a * A.dp, A.G + slot_b * A.dp, A.d);
+        const double d2 = exact_sqdist(A.G + row_a * A.dp, A.G + row_b * A.dp, A.d);
         atomicAdd(&A.stats[kStatBand], 1ull);
         if (count_tie && fabs(d2 - A.eps2) <= A.tie_thr) atomicAdd(&A.stats[kStatTies], 1ull);
         return d2 <= A.eps2;
     }
 };
 
+// Rows, sizes and diagonal flag of this CTA's tile pair.
+struct PairRows {
+    int64_t sa, sb;
+    int na, nb;
+    bool diag;
+};
+
+__device__ __forceinline__ PairRows pair_rows(const PassArgs& A, int64_t q)
+{
+    PairRows P;
+    if (A.pairs) {
+        const int2 p = A.pairs[q];
+        P.sa = (int64_t)p.x * kT;
+        P.sb = (int64_t)p.y * kT;
+        P.na = A.tile_n[p.x];
+        P.nb = A.tile_n[p.y];
+        P.diag = p.x == p.y;
+    } else {
+        const int64_t e = upper_bound_i64(A.pair_off, (int64_t)A.E + 1, q) - 1;
+        const int64_t qq = q - A.pair_off[e];
+        const int64_t base = A.elem_off[e], ne = A.elem_off[e + 1] - base;
+        const int64_t T = (ne + kT - 1) / kT;
+        int ta, tb;
+        decode_pair(qq, T, &ta, &tb);
+        P.sa = base + (int64_t)ta * kT;
+        P.sb = base + (int64_t)tb * kT;
+        P.na = (int)(ne - (int64_t)ta * kT < kT ? ne - (int64_t)ta * kT : kT);
+        P.nb = (int)(ne - (int64_t)tb * kT < kT ? ne - (int64_t)tb * kT : kT);
+        P.diag = ta == tb;
+    }
+    return P;
+}
+
+__device__ __forceinline__ unsigned long long root_code(const PassArgs& A, int row)
+{
+    const int r = A.root[row];
+    return ((unsigned long long)(unsigned)key_of(A.row_pt, r) << 32) | (unsigned)r;
+}
+
+// Before a union pass on a tile pair: how many core rows each side holds,
+// and whether all of them already share one root (nothing left to join).
+// Fills s_core. Must be reached by all threads.
+__device__ __forceinline__ bool union_prologue(const PassArgs& A, const PairRows& P,
+                                               unsigned char* s_core, int* s_mm)
+{
+    const int tid = threadIdx.x;
+    const bool valid = tid < kT ? tid < P.na : (!P.diag && tid - kT < P.nb);
+    const int64_t row = tid < kT ? P.sa + tid : P.sb + (tid - kT);
+    const bool c = valid && A.core[row];
+    s_core[tid] = c;
+    if (tid == 0) { s_mm[0] = INT_MAX; s_mm[1] = -1; }
+    const int nca = __syncthreads_count(tid < kT && c);
+    const int ncb = __syncthreads_count(tid >= kT && c);
+    const bool work = P.diag ? nca >= 2 : (nca > 0 && ncb > 0);
+    if (!work) return false;
+    if (c) {
+        const int r = gfind(A.parent, (int)row);
+        atomicMin(&s_mm[0], r);
+        atomicMax(&s_mm[1], r);
+    }
+    __syncthreads();
+    const bool joined = s_mm[0] == s_mm[1];
+    if (joined && tid == 0) atomicAdd(&A.stats[kStatSkipped], 1ull);
+    return !joined;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256, 2) simt_pass_kernel(const PassArgs A)
 {
     __shared__ __align__(16) float As[kK][kPad];
     __shared__ __align__(16) float Bs[kK][kPad];
-    __shared__ int s_aux[2 * kT];              // pass 1: column counts; 2: local parents; 3: best roots
-    __shared__ int s_root[2 * kT];             // pass 3: roots of A (0..127) and B (128..255)
+    __shared__ int s_aux[2 * kT];                  // 1: column counts; 2: local parents
+    __shared__ int s_old[kT];                      // 1: count of each column before this pair
+    __shared__ unsigned long long s_code[2 * kT];  // 3: root code of each core row, then best
     __shared__ unsigned char s_core[2 * kT];
+    __shared__ int s_mm[2];
 
     const int tid = threadIdx.x;
-    const int64_t e = upper_bound_i64(A.pair_off, (int64_t)A.E + 1, (int64_t)blockIdx.x) - 1;
-    const int64_t q = (int64_t)blockIdx.x - A.pair_off[e];
-    const int64_t base = A.elem_off[e], ne = A.elem_off[e + 1] - base;
-    const int64_t T = (ne + kT - 1) / kT;
-    int ta, tb;
-    decode_pair(q, T, &ta, &tb);
-    const bool diag = ta == tb;
-    const int64_t sa = base + (int64_t)ta * kT, sb = base + (int64_t)tb * kT;
-    const int na = (int)(ne - (int64_t)ta * kT < kT ? ne - (int64_t)ta * kT : kT);
-    const int nb = (int)(ne - (int64_t)tb * kT < kT ? ne - (int64_t)tb * kT : kT);
+    const PairRows P = pair_rows(A, blockIdx.x);
+    const int64_t sa = P.sa, sb = P.sb;
+    const int na = P.na, nb = P.nb;
+    const bool diag = P.diag;
 
     if (MODE == 1) {
         if (tid < kT) s_aux[tid] = 0;
+    } else if (MODE == 2) {
+        if (!union_prologue(A, P, s_core, s_mm)) return;
+        s_aux[tid] = tid;
     } else {
-        bool ca = false, cb = false;
-        if (tid < kT) {
-            ca = tid < na && A.core[sa + tid];
-            s_core[tid] = ca;
-        } else {
-            const int c = tid - kT;
-            cb = c < nb && A.core[sb + c];
-            s_core[tid] = cb;
-        }
-        const int n_core_a = __syncthreads_count(tid < kT && ca);
-        const int n_core_b = __syncthreads_count(tid >= kT && cb);
-        if (MODE == 2) {
-            if (n_core_a == 0 || n_core_b == 0) return;
-            s_aux[tid] = tid;
-        } else {
-            const bool work = (n_core_b > 0 && n_core_a < na) || (!diag && n_core_a > 0 && n_core_b < nb);
-            if (!work) return;
-            s_aux[tid] = INT_MAX;
-            if (tid < kT) s_root[tid] = (tid < na && ca) ? A.root[sa + tid] : INT_MAX;
-            else s_root[tid] = (tid - kT < nb && cb) ? A.root[sb + tid - kT] : INT_MAX;
-        }
+        const bool valid = tid < kT ? tid < na : tid - kT < nb;
+        const int64_t row = tid < kT ? sa + tid : sb + (tid - kT);
+        const bool c = valid && A.core[row];
+        s_core[tid] = c;
+        const int nca = __syncthreads_count(tid < kT && c);
+        const int ncb = __syncthreads_count(tid >= kT && c);
+        const bool work = (ncb > 0 && nca < na) || (!diag && nca > 0 && ncb < nb);
+        if (!work) return;
+        s_code[tid] = c ? root_code(A, (int)row) : ~0ull;
     }
 
     const int tx = tid & 15, ty = tid >> 4;
@@ -207,41 +279,78 @@ __global__ void __launch_bounds__(256, 2) simt_pass_kernel(const PassArgs A)
 
     const Decider decide{A};
     if (MODE == 1) {
-        int rc[8], cc[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) cc[j] = 0;
+        // decide every pair once; bit (i*8 + j) = pair (row i, column j) is in
+        unsigned long long inb = 0ull;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            rc[i] = 0;
             const int r = i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4;
-            if (r >= na) continue;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int c = j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4;
-                if (c >= nb) continue;
-                const bool in = decide(acc[i][j], sa + r, sb + c, !diag || r < c);
-                rc[i] += in;
-                cc[j] += in;
+                if (r < na && c < nb && decide(acc[i][j], sa + r, sb + c, !diag || r < c))
+                    inb |= 1ull << (i * 8 + j);
             }
         }
+        // rows: counts and list positions from a scan over the 16 lanes of a row
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            int v = rc[i];
-            v += __shfl_xor_sync(0xffffffffu, v, 1);
-            v += __shfl_xor_sync(0xffffffffu, v, 2);
-            v += __shfl_xor_sync(0xffffffffu, v, 4);
-            v += __shfl_xor_sync(0xffffffffu, v, 8);
+            const unsigned bits = (unsigned)(inb >> (i * 8)) & 0xffu;
+            const int own = __popc(bits);
+            int incl = own;
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o, 16);
+                if (tx >= o) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 15, 16);
             const int r = i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4;
-            if (tx == 0 && r < na && v) atomicAdd(&A.count[sa + r], v);
+            int old = 0;
+            if (tx == 0 && total > 0) old = atomicAdd(&A.count[sa + r], total);
+            old = __shfl_sync(0xffffffffu, old, 0, 16);
+            if (A.cap > 0 && total > 0 && old < A.cap && bits) {
+                int pos = old + incl - own;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (!((bits >> j) & 1u)) continue;
+                    if (pos < A.cap) {
+                        const int c = j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4;
+                        A.nbr[(sa + r) * A.cap + pos] = (int32_t)(sb + c);
+                    }
+                    ++pos;
+                }
+            }
         }
         if (!diag) {
+            // columns: counts gathered in shared memory, then one atomic each
+            int pos_local[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
+                unsigned colbits = 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) colbits |= (unsigned)((inb >> (i * 8 + j)) & 1ull) << i;
                 const int c = j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4;
-                if (c < nb && cc[j]) atomicAdd(&s_aux[c], cc[j]);
+                pos_local[j] = colbits ? atomicAdd(&s_aux[c], __popc(colbits)) : 0;
             }
             __syncthreads();
-            if (tid < nb && s_aux[tid]) atomicAdd(&A.count[sb + tid], s_aux[tid]);
+            if (tid < kT) s_old[tid] = (tid < nb && s_aux[tid]) ? atomicAdd(&A.count[sb + tid], s_aux[tid]) : 0;
+            __syncthreads();
+            if (A.cap > 0) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int c = j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4;
+                    int pos = s_old[c] + pos_local[j];
+                    if (pos >= A.cap) continue;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        if (!((inb >> (i * 8 + j)) & 1ull)) continue;
+                        if (pos < A.cap) {
+                            const int r = i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4;
+                            A.nbr[(sb + c) * A.cap + pos] = (int32_t)(sa + r);
+                        }
+                        ++pos;
+                    }
+                }
+            }
         }
         if (tid == 0) {
             const int64_t pairs = diag ? (int64_t)na * (na + 1) / 2 : (int64_t)na * nb;
@@ -255,25 +364,30 @@ __global__ void __launch_bounds__(256, 2) simt_pass_kernel(const PassArgs A)
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int c = j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4;
-                if (c >= nb || !s_core[kT + c]) continue;
-                if (diag && c <= r) continue;
-                if (decide(acc[i][j], sa + r, sb + c, false)) lunion(s_aux, r, diag ? c : kT + c);
+                if (diag) {
+                    if (c <= r || c >= na || !s_core[c]) continue;
+                } else if (c >= nb || !s_core[kT + c]) {
+                    continue;
+                }
+                const int lr = r, lc = diag ? c : kT + c;
+                if (lfind(s_aux, lr) == lfind(s_aux, lc)) continue;
+                if (decide(acc[i][j], sa + r, sb + c, false)) lunion(s_aux, lr, lc);
             }
         }
         __syncthreads();
-        {
-            const int x = tid;
-            const bool live = x < kT ? (x < na && s_core[x]) : (!diag && x - kT < nb && s_core[x]);
-            if (live) {
-                const int rx = lfind(s_aux, x);
-                if (rx != x) {
-                    const int64_t slot_x = x < kT ? sa + x : sb + (x - kT);
-                    const int64_t slot_r = rx < kT ? sa + rx : sb + (rx - kT);
-                    gunion(A.parent, (int)slot_x, (int)slot_r);
-                }
+        const int x = tid;
+        if (s_core[x]) {
+            const int rx = lfind(s_aux, x);
+            if (rx != x) {
+                const int64_t row_x = x < kT ? sa + x : sb + (x - kT);
+                const int64_t row_r = rx < kT ? sa + rx : sb + (rx - kT);
+                gunion(A.parent, A.row_pt, (int)row_x, (int)row_r);
             }
         }
     } else {
+        __shared__ unsigned long long s_best[2 * kT];
+        s_best[tid] = ~0ull;
+        __syncthreads();
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int r = i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4;
@@ -286,41 +400,141 @@ __global__ void __launch_bounds__(256, 2) simt_pass_kernel(const PassArgs A)
                 const bool need_b = !diag && !s_core[kT + c] && s_core[r];
                 if (!(need_a || need_b)) continue;
                 if (decide(acc[i][j], sa + r, sb + c, false)) {
-                    if (need_a) atomicMin(&s_aux[r], s_root[kT + c]);
-                    if (need_b) atomicMin(&s_aux[kT + c], s_root[r]);
+                    if (need_a) atomicMin(&s_best[r], s_code[kT + c]);
+                    if (need_b) atomicMin(&s_best[kT + c], s_code[r]);
                 }
             }
         }
         __syncthreads();
         const int x = tid;
-        if (s_aux[x] != INT_MAX) {
-            const int64_t slot_x = x < kT ? sa + x : sb + (x - kT);
-            atomicMin(&A.border[slot_x], s_aux[x]);
+        if (s_best[x] != ~0ull) {
+            const int64_t row_x = x < kT ? sa + x : sb + (x - kT);
+            atomicMin(&A.border[row_x], s_best[x]);
         }
     }
 }
 
-// ------------------------------------------------------------- small kernels
-__global__ void gather_kernel(const float* __restrict__ X, int64_t ld, int d, int dp,
-                              const int32_t* __restrict__ slot_point, int64_t M,
-                              float* __restrict__ G, int* nonfinite)
+// Tile pairs certified all-in by bounding spheres: every pair is a
+// neighbour pair, nothing to screen.
+template <int MODE>
+__global__ void __launch_bounds__(256) allin_kernel(const PassArgs A)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    bool bad = false;
-    for (int64_t s = warp; s < M; s += nwarp) {
-        const int64_t p = slot_point[s];
-        for (int k = lane; k < dp; k += 32) {
-            float v = 0.f;
-            if (k < d) {
-                v = X[p * ld + k];
-                bad |= !isfinite(v);
-            }
-            G[s * dp + k] = v;
+    __shared__ unsigned char s_core[2 * kT];
+    __shared__ int s_mm[2];
+    __shared__ int s_first;
+    __shared__ unsigned long long s_min[2];
+    const int tid = threadIdx.x;
+    const PairRows P = pair_rows(A, blockIdx.x);
+    const bool side_b = tid >= kT;
+    const int x = side_b ? tid - kT : tid;
+    const bool valid = side_b ? (!P.diag && x < P.nb) : x < P.na;
+    const int64_t row = side_b ? P.sb + x : P.sa + x;
+    if (MODE == 1) {
+        if (!valid) return;
+        const int k = side_b ? P.na : (P.diag ? P.na : P.nb);
+        const int old = atomicAdd(&A.count[row], k);
+        if (A.cap > 0 && old < A.cap) {
+            const int64_t other = side_b ? P.sa : (P.diag ? P.sa : P.sb);
+            for (int i = 0; i < k && old + i < A.cap; ++i)
+                A.nbr[row * A.cap + old + i] = (int32_t)(other + i);
+        }
+        if (tid == 0) {
+            const int64_t pairs = P.diag ? (int64_t)P.na * (P.na + 1) / 2 : (int64_t)P.na * P.nb;
+            atomicAdd(&A.stats[kStatScreened], (unsigned long long)pairs);
+        }
+    } else if (MODE == 2) {
+        if (!union_prologue(A, P, s_core, s_mm)) return;
+        if (tid == 0) s_first = INT_MAX;
+        __syncthreads();
+        if (s_core[tid]) atomicMin(&s_first, tid);
+        __syncthreads();
+        const int f = s_first;
+        if (s_core[tid] && tid != f) {
+            const int64_t row_f = f < kT ? P.sa + f : P.sb + (f - kT);
+            gunion(A.parent, A.row_pt, (int)row, (int)row_f);
+        }
+    } else {
+        const bool c = valid && A.core[row];
+        if (tid < 2) s_min[tid] = ~0ull;
+        __syncthreads();
+        if (c) atomicMin(&s_min[side_b ? 1 : 0], root_code(A, (int)row));
+        __syncthreads();
+        if (valid && !c) {
+            const unsigned long long best = P.diag ? s_min[0] : s_min[side_b ? 0 : 1];
+            if (best != ~0ull) atomicMin(&A.border[row], best);
         }
     }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(nonfinite, 1);
+}
+
+__global__ void core_kernel(const int32_t* __restrict__ count, int64_t R, int32_t min_pts,
+                            uint8_t* __restrict__ core, int32_t* __restrict__ parent,
+                            unsigned long long* __restrict__ border, unsigned long long* stats)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool c = false;
+    if (s < R) {
+        c = count[s] >= min_pts;
+        core[s] = c;
+        parent[s] = (int32_t)s;
+        border[s] = ~0ull;
+    }
+    const int nc = __syncthreads_count(c);
+    if (threadIdx.x == 0 && nc) atomicAdd(&stats[kStatCore], (unsigned long long)nc);
+}
+
+__global__ void flatten_kernel(const int32_t* __restrict__ parent, const uint8_t* __restrict__ core,
+                               int64_t R, int32_t* __restrict__ root)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= R) return;
+    int r = (int)s;
+    if (core[s])
+        while (parent[r] != r) r = parent[r];
+    root[s] = r;
+}
+
+// A non-core row holds fewer than minPts neighbours, all of them stored by
+// pass 1: its label is the smallest canonical id among its core neighbours.
+__global__ void border_lists_kernel(const int32_t* __restrict__ count, const int32_t* __restrict__ nbr,
+                                    int cap, const uint8_t* __restrict__ core,
+                                    const int32_t* __restrict__ root, const int32_t* __restrict__ row_pt,
+                                    int64_t R, unsigned long long* __restrict__ border)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= R || core[s]) return;
+    const int k = min(count[s], cap);
+    unsigned long long best = ~0ull;
+    for (int i = 0; i < k; ++i) {
+        const int q = nbr[s * cap + i];
+        if (!core[q]) continue;
+        const int r = root[q];
+        const unsigned long long code =
+            ((unsigned long long)(unsigned)(row_pt ? row_pt[r] : r) << 32) | (unsigned)r;
+        best = code < best ? code : best;
+    }
+    border[s] = best;
+}
+
+__global__ void rows_to_slots_kernel(const int32_t* __restrict__ row_slot, const int32_t* __restrict__ row_pt,
+                                     const uint8_t* __restrict__ core, const int32_t* __restrict__ root,
+                                     const unsigned long long* __restrict__ border, int64_t R,
+                                     int32_t* __restrict__ lab, int32_t* __restrict__ is_root,
+                                     int32_t* __restrict__ is_member, int64_t* __restrict__ slot_label,
+                                     uint8_t* __restrict__ slot_core)
+{
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= R) return;
+    const int slot = row_slot[row];
+    if (slot < 0) return;
+    const bool c = core[row];
+    int l = -1;
+    if (c) l = root[row];
+    else if (border[row] != ~0ull) l = (int)(unsigned)(border[row] & 0xffffffffull);
+    lab[slot] = l >= 0 ? row_slot[l] : -1;
+    slot_label[slot] = l >= 0 ? (int64_t)row_pt[l] : -1;
+    is_root[slot] = c && root[row] == (int32_t)row;
+    is_member[slot] = l >= 0;
+    slot_core[slot] = c;
 }
 
 __global__ void elem_offsets_kernel(const uint64_t* __restrict__ keys, int64_t M, int64_t E,
@@ -328,143 +542,12 @@ __global__ void elem_offsets_kernel(const uint64_t* __restrict__ keys, int64_t M
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e > E) return;
-    // first slot whose element >= e
-    int64_t l = 0, r = M;
+    int64_t l = 0, r = M;                      // first slot whose element >= e
     while (l < r) {
         const int64_t m = (l + r) >> 1;
         if ((int64_t)(keys[m] >> 32) < e) l = m + 1; else r = m;
     }
     elem_off[e] = l;
-}
-
-__global__ void pair_counts_kernel(const int64_t* __restrict__ elem_off, int64_t E,
-                                   int64_t* __restrict__ pairs)
-{
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= E) return;
-    const int64_t T = (elem_off[e + 1] - elem_off[e] + kT - 1) / kT;
-    pairs[e] = T * (T + 1) / 2;
-}
-
-__global__ void core_kernel(const int32_t* __restrict__ count, int64_t M, int32_t min_pts,
-                            uint8_t* __restrict__ core, int32_t* __restrict__ parent,
-                            int32_t* __restrict__ border, unsigned long long* stats)
-{
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool c = false;
-    if (s < M) {
-        c = count[s] >= min_pts;
-        core[s] = c;
-        parent[s] = (int32_t)s;
-        border[s] = INT_MAX;
-    }
-    const int nc = __syncthreads_count(c);
-    if (threadIdx.x == 0 && nc) atomicAdd(&stats[kStatCore], (unsigned long long)nc);
-}
-
-__global__ void flatten_kernel(const int32_t* __restrict__ parent, const uint8_t* __restrict__ core,
-                               int64_t M, int32_t* __restrict__ root)
-{
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= M) return;
-    int r = (int)s;
-    if (core[s])
-        while (parent[r] != r) r = parent[r];
-    root[s] = r;
-}
-
-// label[s] = root slot of the node holding s, or -1
-__global__ void label_kernel(const uint8_t* __restrict__ core, const int32_t* __restrict__ root,
-                             const int32_t* __restrict__ border, const int32_t* __restrict__ slot_point,
-                             int64_t M, int32_t* __restrict__ lab, int32_t* __restrict__ is_root,
-                             int32_t* __restrict__ is_member, int64_t* __restrict__ slot_label)
-{
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= M) return;
-    int l = -1;
-    if (core[s]) l = root[s];
-    else if (border[s] != INT_MAX) l = border[s];
-    lab[s] = l;
-    slot_label[s] = l >= 0 ? (int64_t)slot_point[l] : -1;
-    is_root[s] = core[s] && root[s] == (int32_t)s;
-    is_member[s] = l >= 0;
-}
-
-__global__ void member_keys_kernel(const int32_t* __restrict__ lab, const int64_t* __restrict__ nid,
-                                   const int64_t* __restrict__ mpos,
-                                   const int32_t* __restrict__ slot_point,
-                                   const int32_t* __restrict__ slot_elem, int64_t M,
-                                   uint64_t* __restrict__ keys, int32_t* __restrict__ node_elem)
-{
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= M) return;
-    const int l = lab[s];
-    if (l < 0) return;
-    const int64_t node = nid[l];
-    keys[mpos[s]] = ((uint64_t)node << 32) | (uint64_t)(uint32_t)slot_point[s];
-    if (l == (int)s) node_elem[node] = slot_elem[s];
-}
-
-__global__ void node_offsets_kernel(const uint64_t* __restrict__ keys, int64_t G,
-                                    int64_t* __restrict__ node_off, int32_t* __restrict__ members,
-                                    uint64_t* __restrict__ keys2)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= G) return;
-    const uint64_t k = keys[i];
-    const int64_t node = (int64_t)(k >> 32);
-    members[i] = (int32_t)(uint32_t)k;
-    keys2[i] = ((k & 0xffffffffull) << 32) | (uint64_t)node;
-    if (i == 0 || (int64_t)(keys[i - 1] >> 32) != node) node_off[node] = i;
-}
-
-__global__ void run_pairs_kernel(const uint64_t* __restrict__ keys2, int64_t G,
-                                 int64_t* __restrict__ cnt)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= G) return;
-    const uint64_t pt = keys2[i] >> 32;
-    int64_t c = 0;
-    if (i == 0 || (keys2[i - 1] >> 32) != pt) {
-        int64_t len = 1;
-        while (i + len < G && (keys2[i + len] >> 32) == pt) ++len;
-        c = len * (len - 1) / 2;
-    }
-    cnt[i] = c;
-}
-
-__global__ void emit_pairs_kernel(const uint64_t* __restrict__ keys2, int64_t G,
-                                  const int64_t* __restrict__ pos, uint64_t* __restrict__ out)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= G) return;
-    const uint64_t pt = keys2[i] >> 32;
-    if (!(i == 0 || (keys2[i - 1] >> 32) != pt)) return;
-    int64_t len = 1;
-    while (i + len < G && (keys2[i + len] >> 32) == pt) ++len;
-    int64_t o = pos[i];
-    for (int64_t a = 0; a < len; ++a)
-        for (int64_t b = a + 1; b < len; ++b)
-            out[o++] = ((keys2[i + a] & 0xffffffffull) << 32) | (keys2[i + b] & 0xffffffffull);
-}
-
-__global__ void unique_flags_kernel(const uint64_t* __restrict__ k, int64_t P,
-                                    int32_t* __restrict__ flag)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P) return;
-    flag[i] = (i == 0 || k[i] != k[i - 1]);
-}
-
-__global__ void unique_emit_kernel(const uint64_t* __restrict__ k, const int32_t* __restrict__ flag,
-                                   const int64_t* __restrict__ pos, int64_t P,
-                                   int32_t* __restrict__ edges)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P || !flag[i]) return;
-    const int64_t o = pos[i];
-    edges[2 * o] = (int32_t)(k[i] >> 32);
-    edges[2 * o + 1] = (int32_t)(uint32_t)k[i];
 }
 
 inline unsigned grid_for(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, div_up(n, t)); }
@@ -494,111 +577,72 @@ void fp32_thresholds(double eps2, int d, float* lo, float* hi)
     *hi = hf;
 }
 
-cudaError_t gather_rows(const float* X, int64_t ld, int d, int dp, const int32_t* slot_point,
-                        int64_t M, float* G, int* nonfinite, cudaStream_t s)
+cudaError_t simt_pass(int mode, const PassArgs& a, int64_t n_pairs, cudaStream_t s)
 {
-    if (M == 0) return cudaSuccess;
-    const int64_t blocks = std::min<int64_t>(div_up(M, 8), 152 * 16);
-    { gather_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, ld, d, dp, slot_point, M, G, nonfinite); note_launch(); }
+    if (n_pairs == 0) return cudaSuccess;
+    if (mode == 1) simt_pass_kernel<1><<<(unsigned)n_pairs, 256, 0, s>>>(a);
+    else if (mode == 2) simt_pass_kernel<2><<<(unsigned)n_pairs, 256, 0, s>>>(a);
+    else simt_pass_kernel<3><<<(unsigned)n_pairs, 256, 0, s>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t allin_pass(int mode, const PassArgs& a, int64_t n_pairs, cudaStream_t s)
+{
+    if (n_pairs == 0) return cudaSuccess;
+    if (mode == 1) allin_kernel<1><<<(unsigned)n_pairs, 256, 0, s>>>(a);
+    else if (mode == 2) allin_kernel<2><<<(unsigned)n_pairs, 256, 0, s>>>(a);
+    else allin_kernel<3><<<(unsigned)n_pairs, 256, 0, s>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t core_flags(const int32_t* count, int64_t R, int32_t min_pts, uint8_t* core,
+                       int32_t* parent, unsigned long long* border, unsigned long long* stats,
+                       cudaStream_t s)
+{
+    if (R == 0) return cudaSuccess;
+    core_kernel<<<grid_for(R), 256, 0, s>>>(count, R, min_pts, core, parent, border, stats);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t flatten(const int32_t* parent, const uint8_t* core, int64_t R, int32_t* root,
+                    cudaStream_t s)
+{
+    if (R == 0) return cudaSuccess;
+    flatten_kernel<<<grid_for(R), 256, 0, s>>>(parent, core, R, root);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t border_from_lists(const int32_t* count, const int32_t* nbr, int cap,
+                              const uint8_t* core, const int32_t* root, const int32_t* row_pt,
+                              int64_t R, unsigned long long* border, cudaStream_t s)
+{
+    if (R == 0 || cap <= 0) return cudaSuccess;
+    border_lists_kernel<<<grid_for(R), 256, 0, s>>>(count, nbr, cap, core, root, row_pt, R, border);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t rows_to_slots(const int32_t* row_slot, const int32_t* row_pt, const uint8_t* core,
+                          const int32_t* root, const unsigned long long* border, int64_t R,
+                          int32_t* lab, int32_t* is_root, int32_t* is_member,
+                          int64_t* slot_label, uint8_t* slot_core, cudaStream_t s)
+{
+    if (R == 0) return cudaSuccess;
+    rows_to_slots_kernel<<<grid_for(R), 256, 0, s>>>(row_slot, row_pt, core, root, border, R, lab,
+                                                     is_root, is_member, slot_label, slot_core);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t element_offsets(const uint64_t* keys, int64_t M, int64_t E, int64_t* elem_off,
                             cudaStream_t s)
 {
-    { elem_offsets_kernel<<<grid_for(E + 1), 256, 0, s>>>(keys, M, E, elem_off); note_launch(); }
-    return cudaGetLastError();
-}
-
-cudaError_t tile_pair_offsets(const int64_t* elem_off, int64_t E, int64_t* pair_off, cudaStream_t s)
-{
-    Buf cnt;
-    MGB_TRY(cnt.alloc(sizeof(int64_t) * std::max<int64_t>(E, 1), s));
-    if (E) { pair_counts_kernel<<<grid_for(E), 256, 0, s>>>(elem_off, E, cnt.as<int64_t>()); note_launch(); }
-    MGB_TRY(cudaGetLastError());
-    return exclusive_scan_i64(cnt.as<int64_t>(), pair_off, E, s);
-}
-
-cudaError_t simt_pass(int mode, const PassArgs& a, int64_t n_pairs, cudaStream_t s)
-{
-    if (n_pairs == 0) return cudaSuccess;
-    if (mode == 1) { simt_pass_kernel<1><<<(unsigned)n_pairs, 256, 0, s>>>(a); note_launch(); }
-    else if (mode == 2) { simt_pass_kernel<2><<<(unsigned)n_pairs, 256, 0, s>>>(a); note_launch(); }
-    else { simt_pass_kernel<3><<<(unsigned)n_pairs, 256, 0, s>>>(a); note_launch(); }
-    return cudaGetLastError();
-}
-
-cudaError_t core_flags(const int32_t* count, int64_t M, int32_t min_pts, uint8_t* core,
-                       int32_t* parent, int32_t* border, unsigned long long* stats, cudaStream_t s)
-{
-    if (M == 0) return cudaSuccess;
-    { core_kernel<<<grid_for(M), 256, 0, s>>>(count, M, min_pts, core, parent, border, stats); note_launch(); }
-    return cudaGetLastError();
-}
-
-cudaError_t flatten(const int32_t* parent, const uint8_t* core, int64_t M, int32_t* root,
-                    cudaStream_t s)
-{
-    if (M == 0) return cudaSuccess;
-    { flatten_kernel<<<grid_for(M), 256, 0, s>>>(parent, core, M, root); note_launch(); }
-    return cudaGetLastError();
-}
-
-cudaError_t labels(const uint8_t* core, const int32_t* root, const int32_t* border,
-                   const int32_t* slot_point, int64_t M, int32_t* lab, int32_t* is_root,
-                   int32_t* is_member, int64_t* slot_label, cudaStream_t s)
-{
-    if (M == 0) return cudaSuccess;
-    { label_kernel<<<grid_for(M), 256, 0, s>>>(core, root, border, slot_point, M, lab, is_root,
-                                             is_member, slot_label); note_launch(); }
-    return cudaGetLastError();
-}
-
-cudaError_t member_keys(const int32_t* lab, const int64_t* nid, const int64_t* mpos,
-                        const int32_t* slot_point, const int32_t* slot_elem, int64_t M,
-                        uint64_t* keys, int32_t* node_elem, cudaStream_t s)
-{
-    if (M == 0) return cudaSuccess;
-    { member_keys_kernel<<<grid_for(M), 256, 0, s>>>(lab, nid, mpos, slot_point, slot_elem, M, keys,
-                                                   node_elem); note_launch(); }
-    return cudaGetLastError();
-}
-
-cudaError_t node_offsets(const uint64_t* keys, int64_t G, int64_t* node_off, int32_t* members,
-                         uint64_t* keys2, cudaStream_t s)
-{
-    if (G == 0) return cudaSuccess;
-    { node_offsets_kernel<<<grid_for(G), 256, 0, s>>>(keys, G, node_off, members, keys2); note_launch(); }
-    return cudaGetLastError();
-}
-
-cudaError_t run_pairs(const uint64_t* keys2, int64_t G, int64_t* cnt, cudaStream_t s)
-{
-    if (G == 0) return cudaSuccess;
-    { run_pairs_kernel<<<grid_for(G), 256, 0, s>>>(keys2, G, cnt); note_launch(); }
-    return cudaGetLastError();
-}
-
-cudaError_t emit_pairs(const uint64_t* keys2, int64_t G, const int64_t* pos, uint64_t* out,
-                       cudaStream_t s)
-{
-    if (G == 0) return cudaSuccess;
-    { emit_pairs_kernel<<<grid_for(G), 256, 0, s>>>(keys2, G, pos, out); note_launch(); }
-    return cudaGetLastError();
-}
-
-cudaError_t unique_flags(const uint64_t* k, int64_t P, int32_t* flag, cudaStream_t s)
-{
-    if (P == 0) return cudaSuccess;
-    { unique_flags_kernel<<<grid_for(P), 256, 0, s>>>(k, P, flag); note_launch(); }
-    return cudaGetLastError();
-}
-
-cudaError_t unique_emit(const uint64_t* k, const int32_t* flag, const int64_t* pos, int64_t P,
-                        int32_t* edges, cudaStream_t s)
-{
-    if (P == 0) return cudaSuccess;
-    { unique_emit_kernel<<<grid_for(P), 256, 0, s>>>(k, flag, pos, P, edges); note_launch(); }
+    elem_offsets_kernel<<<grid_for(E + 1), 256, 0, s>>>(keys, M, E, elem_off);
+    note_launch();
     return cudaGetLastError();
 }
 

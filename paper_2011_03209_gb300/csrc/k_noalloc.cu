@@ -7,7 +7,7 @@
 // and forbids its plug-ins from allocating, or a latency-critical caller that
 // must never let an allocation synchronise the device or fail half way. For
 // them, mapper_dbscan_noalloc runs the same three screening passes on scratch
-// held in one file-scope device array of fixed size (about 8.5 MB, held by
+// held in one file-scope device array of fixed size (about 8.6 MB, held by
 // every GPU that loads the library until the process exits).
 //
 // Use: the first call on a device (from the thread that makes it current)
@@ -36,7 +36,7 @@ constexpr size_t kNaCountOff = kNaRowsOff + sizeof(float) * kNaPoints * kNaDim;
 constexpr size_t kNaParentOff = kNaCountOff + sizeof(int32_t) * kNaPoints;
 constexpr size_t kNaRootOff = kNaParentOff + sizeof(int32_t) * kNaPoints;
 constexpr size_t kNaBorderOff = kNaRootOff + sizeof(int32_t) * kNaPoints;
-constexpr size_t kNaCoreOff = kNaBorderOff + sizeof(int32_t) * kNaPoints;
+constexpr size_t kNaCoreOff = kNaBorderOff + sizeof(unsigned long long) * kNaPoints;
 constexpr size_t kNaMetaOff = kNaCoreOff + kNaPoints;                // offsets, stats, flag
 constexpr size_t kNaBytes = kNaMetaOff + 256;
 static_assert(kNaCoreOff % 256 == 0 && kNaMetaOff % 256 == 0, "scratch layout alignment");
@@ -102,14 +102,14 @@ __global__ void na_setup_kernel(const float* __restrict__ X, int64_t n, int d, i
 
 // label = canonical id (row of the cluster's smallest core point) or -1
 __global__ void na_labels_kernel(const uint8_t* __restrict__ core, const int32_t* __restrict__ root,
-                                 const int32_t* __restrict__ border, int64_t n,
+                                 const unsigned long long* __restrict__ border, int64_t n,
                                  int64_t* __restrict__ label, uint8_t* __restrict__ core_out)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     int64_t l = -1;
     if (core[s]) l = root[s];
-    else if (border[s] != INT_MAX) l = border[s];
+    else if (border[s] != ~0ull) l = (int64_t)(border[s] & 0xffffffffull);
     if (label) label[s] = l;
     if (core_out) core_out[s] = core[s];
 }
@@ -164,7 +164,7 @@ extern "C" int mapper_dbscan_noalloc(const float* X_dev, int64_t n, int32_t d, i
     int32_t* count = reinterpret_cast<int32_t*>(base + kNaCountOff);
     int32_t* parent = reinterpret_cast<int32_t*>(base + kNaParentOff);
     int32_t* root = reinterpret_cast<int32_t*>(base + kNaRootOff);
-    int32_t* border = reinterpret_cast<int32_t*>(base + kNaBorderOff);
+    unsigned long long* border = reinterpret_cast<unsigned long long*>(base + kNaBorderOff);
     uint8_t* core = base + kNaCoreOff;
     NaMeta* meta = reinterpret_cast<NaMeta*>(base + kNaMetaOff);
 

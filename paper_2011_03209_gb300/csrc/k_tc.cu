@@ -4,7 +4,7 @@
 
 namespace mgb {
 
-int tc_cluster_passes(const PassArgs&, int64_t, int32_t, cudaStream_t)
+int tc_pass(int, const PassArgs&, const TcArgs&, int64_t, cudaStream_t)
 {
     set_error("BF16 tensor-core screen not built yet");
     return MAPPER_ENOTIMPL;

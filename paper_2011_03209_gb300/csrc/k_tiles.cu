@@ -1,0 +1,609 @@
+// k_tiles.cu -- spatially coherent tiles for the per-element DBSCAN passes,
+// and bounding-sphere classification of their tile pairs.
+//
+// The per-element DBSCAN of "Mapper Interactive" (§3; parallel per interval
+// in §4.3) needs, for each element, every point pair within eps. Points of an
+// element sit in a few dense regions far apart; if consecutive rows of a tile
+// come from one region, most tile pairs are provably all-out (or all-in) by
+// the triangle inequality and need no distance at all. The layout:
+//   1. K pivots (points floor(k n / K)); every point goes to its nearest
+//      pivot; pivots closer than tau join one group (connected components);
+//      a point farther than tau from every pivot is an outlier.
+//   2. Each element's slots are sorted by (group, pivot), stably, so points
+//      stay ascending inside a pivot; each (element, group) segment is cut
+//      into tiles of 128 rows (the last one padded), so no tile mixes groups.
+//   3. Per tile: rows gathered (FP32, zero padded), FP64 centroid and radius.
+//      Per segment: FP64 centroid; rows centred on it are split into BF16
+//      hi + lo parts with |a|^2 and |a| for the tensor-core screen.
+// Only speed depends on this ordering; every decision stays exact.
+#include <cuda_bf16.h>
+
+#include <cfloat>
+#include <climits>
+#include <cmath>
+#include <vector>
+
+#include "../../include/mapper.h"
+#include "dbscan.cuh"
+
+namespace mgb {
+
+namespace {
+
+constexpr int kPiv = 256;      // most pivots
+constexpr int kT = kTile;
+
+inline unsigned grid_for(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, div_up(n, t)); }
+
+int bits_for(int64_t n)        // bits to hold values 0 .. n-1
+{
+    int b = 1;
+    while (b < 63 && (int64_t(1) << b) < n) ++b;
+    return b;
+}
+
+__global__ void pivot_gather_kernel(const float* __restrict__ X, int64_t n, int d, int64_t ld, int dp,
+                                    int K, float* __restrict__ Pv)
+{
+    const int k = blockIdx.x;
+    const int64_t p = (int64_t)k * n / K;
+    for (int j = threadIdx.x; j < dp; j += blockDim.x) Pv[(int64_t)k * dp + j] = j < d ? X[p * ld + j] : 0.f;
+}
+
+// Nearest pivot of every point (FP32 distances; ties to the lower index).
+// CTA: 128 points x 128 pivots per step, 32 dimensions staged at a time.
+__global__ void __launch_bounds__(256, 2) assign_kernel(const float* __restrict__ X, int64_t n, int d,
+                                                        int64_t ld, const float* __restrict__ Pv, int dp,
+                                                        int K, int32_t* __restrict__ piv,
+                                                        float* __restrict__ pd2)
+{
+    __shared__ __align__(16) float As[32][132];
+    __shared__ __align__(16) float Bs[32][132];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t p0 = (int64_t)blockIdx.x * kT;
+    float best[8];
+    int bidx[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { best[i] = FLT_MAX; bidx[i] = INT_MAX; }
+    for (int c0 = 0; c0 < K; c0 += kT) {
+        float acc[8][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        for (int k0 = 0; k0 < d; k0 += 32) {
+#pragma unroll 4
+            for (int v = 0; v < 16; ++v) {
+                const int idx = tid + 256 * v;
+                const int r = idx >> 5, k = idx & 31;
+                float x = 0.f;
+                if (p0 + r < n && k0 + k < d) x = X[(p0 + r) * ld + k0 + k];
+                As[k][r] = x;
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int idx = tid + 256 * v;
+                const int r = idx >> 3, k4 = (idx & 7) * 4;
+                float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (c0 + r < K) b = *reinterpret_cast<const float4*>(Pv + (int64_t)(c0 + r) * dp + k0 + k4);
+                Bs[k4 + 0][r] = b.x; Bs[k4 + 1][r] = b.y; Bs[k4 + 2][r] = b.z; Bs[k4 + 3][r] = b.w;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) {
+                const float4 a0 = *reinterpret_cast<const float4*>(&As[k][ty * 4]);
+                const float4 a1 = *reinterpret_cast<const float4*>(&As[k][64 + ty * 4]);
+                const float4 b0 = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
+                const float4 b1 = *reinterpret_cast<const float4*>(&Bs[k][64 + tx * 4]);
+                const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float t = a[i] - b[j];
+                        acc[i][j] = fmaf(t, t, acc[i][j]);
+                    }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = c0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+                if (c < K && (acc[i][j] < best[i] || (acc[i][j] == best[i] && c < bidx[i]))) {
+                    best[i] = acc[i][j];
+                    bidx[i] = c;
+                }
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, best[i], o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bidx[i], o);
+            if (ov < best[i] || (ov == best[i] && oi < bidx[i])) { best[i] = ov; bidx[i] = oi; }
+        }
+        const int r = i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4;
+        if (tx == 0 && p0 + r < n) {
+            piv[p0 + r] = bidx[i] == INT_MAX ? 0 : bidx[i];       // NaN rows: any pivot
+            pd2[p0 + r] = best[i];
+        }
+    }
+}
+
+// Pivot groups: connected components of the pivots under |p - q| <= tau,
+// numbered 0.. in order of their smallest pivot. One CTA.
+__global__ void __launch_bounds__(1024) group_kernel(const float* __restrict__ Pv, int dp, int d, int K,
+                                                     float tau2, int32_t* __restrict__ gid,
+                                                     int32_t* __restrict__ n_groups)
+{
+    __shared__ unsigned adj[kPiv][kPiv / 32];
+    __shared__ int lab[kPiv];
+    __shared__ int changed;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < kPiv * kPiv / 32; e += blockDim.x) (&adj[0][0])[e] = 0u;
+    __syncthreads();
+    for (int e = tid; e < K * K; e += blockDim.x) {
+        const int i = e / K, j = e - i * K;
+        if (j < i) continue;
+        float s = 0.f;
+        for (int k = 0; k < d; ++k) {
+            const float t = Pv[(int64_t)i * dp + k] - Pv[(int64_t)j * dp + k];
+            s = fmaf(t, t, s);
+        }
+        if (s <= tau2) {
+            atomicOr(&adj[i][j >> 5], 1u << (j & 31));
+            atomicOr(&adj[j][i >> 5], 1u << (i & 31));
+        }
+    }
+    if (tid < K) lab[tid] = tid;
+    __syncthreads();
+    for (int it = 0; it <= K; ++it) {
+        if (tid == 0) changed = 0;
+        __syncthreads();
+        if (tid < K) {
+            int m = lab[tid];
+            for (int w = 0; w < (K + 31) / 32; ++w) {
+                unsigned bits = adj[tid][w];
+                while (bits) {
+                    const int j = w * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    m = min(m, lab[j]);
+                }
+            }
+            if (m < lab[tid]) { lab[tid] = m; changed = 1; }
+        }
+        __syncthreads();
+        if (!changed) break;
+        __syncthreads();
+    }
+    if (tid < K) {
+        const int l = lab[tid];
+        int g = 0;
+        for (int j = 0; j < l; ++j) g += lab[j] == j;
+        gid[tid] = g;
+        if (tid == K - 1) {
+            int ng = 0;
+            for (int j = 0; j < K; ++j) ng += lab[j] == j;
+            *n_groups = ng;
+        }
+    }
+}
+
+// Sort key of a slot: (element, group, pivot) above the slot index.
+__global__ void key_kernel(const int32_t* __restrict__ slot_point, const int32_t* __restrict__ slot_elem,
+                           int64_t M, const int32_t* __restrict__ piv, const float* __restrict__ pd2,
+                           const int32_t* __restrict__ gid, float tau2, int K, int gbits, int pbits,
+                           uint64_t* __restrict__ keys)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= M) return;
+    const int pt = slot_point[s];
+    const int pv = piv[pt];
+    const bool outlier = !(pd2[pt] <= tau2);
+    uint64_t g = 0, pf = 0;
+    if (gbits) g = outlier ? (uint64_t)K : (uint64_t)gid[pv];
+    if (pbits && !outlier) pf = (uint64_t)pv;
+    const uint64_t hi = ((uint64_t)slot_elem[s] << (gbits + pbits)) | (g << pbits) | pf;
+    keys[s] = (hi << 32) | (uint64_t)(uint32_t)s;
+}
+
+__global__ void seg_flag_kernel(const uint64_t* __restrict__ keys, int64_t M, int shift,
+                                int32_t* __restrict__ flag)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    flag[i] = i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift);
+}
+
+// seg_start[nseg+1], seg_elem, seg_out (outlier segment) from the flags' scan
+__global__ void seg_start_kernel(const uint64_t* __restrict__ keys, const int32_t* __restrict__ flag,
+                                 const int64_t* __restrict__ segpos, int64_t M, int gbits, int pbits,
+                                 int K, int64_t* __restrict__ seg_start, int32_t* __restrict__ seg_elem,
+                                 int32_t* __restrict__ seg_out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    if (flag[i]) {
+        const int64_t sg = segpos[i];
+        const uint64_t hi = keys[i] >> 32;
+        seg_start[sg] = i;
+        seg_elem[sg] = (int32_t)(hi >> (gbits + pbits));
+        seg_out[sg] = gbits ? (int32_t)(((hi >> pbits) & ((1ull << gbits) - 1)) == (uint64_t)K) : 0;
+    }
+    if (i == M - 1) seg_start[segpos[M]] = M;
+}
+
+__global__ void seg_tiles_kernel(const int64_t* __restrict__ seg_start, int64_t nseg,
+                                 int64_t* __restrict__ seg_tiles)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nseg) return;
+    seg_tiles[g] = (seg_start[g + 1] - seg_start[g] + kT - 1) / kT;
+}
+
+__global__ void row_map_kernel(const uint64_t* __restrict__ keys, const int64_t* __restrict__ segpos,
+                               const int64_t* __restrict__ seg_start, const int64_t* __restrict__ seg_toff,
+                               int64_t M, int32_t* __restrict__ row_slot)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int64_t sg = segpos[i + 1] - 1;
+    const int64_t row = seg_toff[sg] * kT + (i - seg_start[sg]);
+    row_slot[row] = (int32_t)(uint32_t)keys[i];
+}
+
+__global__ void tile_info_kernel(const int64_t* __restrict__ seg_start, const int64_t* __restrict__ seg_toff,
+                                 const int32_t* __restrict__ seg_elem, int64_t nseg,
+                                 int32_t* __restrict__ tile_n, int32_t* __restrict__ tile_seg,
+                                 int32_t* __restrict__ tile_elem)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nseg) return;
+    const int64_t len = seg_start[g + 1] - seg_start[g];
+    for (int64_t t = seg_toff[g]; t < seg_toff[g + 1]; ++t) {
+        const int64_t first = (t - seg_toff[g]) * kT;
+        tile_n[t] = (int32_t)(len - first < kT ? len - first : kT);
+        tile_seg[t] = (int32_t)g;
+        tile_elem[t] = seg_elem[g];
+    }
+}
+
+// One CTA per tile: gather rows, FP64 centroid and radius.
+__global__ void __launch_bounds__(256) tile_prep_kernel(const float* __restrict__ X, int d, int64_t ld, int dp,
+                                                        const int32_t* __restrict__ slot_point,
+                                                        const int32_t* __restrict__ row_slot,
+                                                        const int32_t* __restrict__ tile_n,
+                                                        float* __restrict__ G, int32_t* __restrict__ row_pt,
+                                                        double* __restrict__ cent, double* __restrict__ rad,
+                                                        int* nonfinite)
+{
+    __shared__ unsigned long long s_rad;
+    const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t row0 = (int64_t)t * kT;
+    const int nt = tile_n[t];
+    bool bad = false;
+    for (int r = warp; r < kT; r += 8) {
+        const int64_t row = row0 + r;
+        const int slot = row_slot[row];
+        const int64_t pt = slot >= 0 ? slot_point[slot] : -1;
+        for (int k = lane; k < dp; k += 32) {
+            float v = 0.f;
+            if (pt >= 0 && k < d) {
+                v = X[pt * ld + k];
+                bad |= !isfinite(v);
+            }
+            G[row * dp + k] = v;
+        }
+        if (lane == 0) row_pt[row] = pt >= 0 ? (int32_t)pt : INT_MAX;
+    }
+    if (tid == 0) s_rad = 0ull;
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(nonfinite, 1);
+    for (int k = tid; k < dp; k += blockDim.x) {
+        double s = 0.0;
+        for (int r = 0; r < nt; ++r) s += (double)G[(row0 + r) * dp + k];
+        cent[(int64_t)t * dp + k] = s / (double)nt;
+    }
+    __syncthreads();
+    for (int r = warp; r < nt; r += 8) {
+        const int64_t row = row0 + r;
+        double s = 0.0;
+        for (int k = lane; k < d; k += 32) {
+            const double u = (double)G[row * dp + k] - cent[(int64_t)t * dp + k];
+            s += u * u;
+        }
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) atomicMax(&s_rad, (unsigned long long)__double_as_longlong(sqrt(s)));
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const double r = __longlong_as_double((long long)s_rad);
+        rad[t] = r * (1.0 + 1e-12) + 1e-300;
+    }
+}
+
+__global__ void seg_cent_kernel(const double* __restrict__ cent, const int32_t* __restrict__ tile_n,
+                                const int64_t* __restrict__ seg_toff, int dp,
+                                double* __restrict__ seg_cent)
+{
+    const int64_t g = blockIdx.x;
+    for (int k = threadIdx.x; k < dp; k += blockDim.x) {
+        double s = 0.0, w = 0.0;
+        for (int64_t t = seg_toff[g]; t < seg_toff[g + 1]; ++t) {
+            s += cent[t * dp + k] * (double)tile_n[t];
+            w += (double)tile_n[t];
+        }
+        seg_cent[g * dp + k] = s / w;
+    }
+}
+
+// BF16 operands: a = x - (segment centroid) in FP64, hi = bf16(a),
+// lo = bf16(a - hi); |a|^2 to nearest FP32 and |a| rounded up.
+__global__ void __launch_bounds__(256) operand_kernel(const float* __restrict__ G, int d, int dp,
+                                                      const int32_t* __restrict__ tile_n,
+                                                      const int32_t* __restrict__ tile_seg,
+                                                      const double* __restrict__ seg_cent,
+                                                      __nv_bfloat16* __restrict__ Ah,
+                                                      __nv_bfloat16* __restrict__ Al,
+                                                      float* __restrict__ rn2, float* __restrict__ rn)
+{
+    const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nt = tile_n[t];
+    const double* c = seg_cent + (int64_t)tile_seg[t] * dp;
+    for (int r = warp; r < kT; r += 8) {
+        const int64_t row = (int64_t)t * kT + r;
+        double s = 0.0;
+        for (int k = lane; k < dp; k += 32) {
+            double a = 0.0;
+            if (r < nt && k < d) a = (double)G[row * dp + k] - c[k];
+            const __nv_bfloat16 h = __double2bfloat16(a);
+            const __nv_bfloat16 l = __double2bfloat16(a - (double)__bfloat162float(h));
+            Ah[row * dp + k] = h;
+            if (Al) Al[row * dp + k] = l;
+            s += a * a;
+        }
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            rn2[row] = (float)s;
+            rn[row] = __double2float_ru(sqrt(s) * (1.0 + 1e-15));
+        }
+    }
+}
+
+__global__ void elem_tiles_kernel(const int32_t* __restrict__ tile_elem, int64_t T, int64_t E,
+                                  int64_t* __restrict__ etile_off)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e > E) return;
+    int64_t l = 0, r = T;                      // first tile whose element >= e
+    while (l < r) {
+        const int64_t m = (l + r) >> 1;
+        if (tile_elem[m] < e) l = m + 1; else r = m;
+    }
+    etile_off[e] = l;
+}
+
+__global__ void cand_count_kernel(const int64_t* __restrict__ etile_off, int64_t E, int64_t* __restrict__ cnt)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    const int64_t T = etile_off[e + 1] - etile_off[e];
+    cnt[e] = T * (T + 1) / 2;
+}
+
+__device__ __forceinline__ int64_t upper_bound_i64(const int64_t* a, int64_t n, int64_t v)
+{
+    int64_t l = 0, r = n;
+    while (l < r) {
+        const int64_t m = (l + r) >> 1;
+        if (a[m] <= v) l = m + 1; else r = m;
+    }
+    return l;
+}
+
+// One warp per candidate tile pair. Candidates of an element are enumerated
+// by diagonal: (i, i) for all i, then (i, i+1), ..., so near-diagonal pairs
+// (tiles of one pivot region) come first.
+__global__ void classify_kernel(const int64_t* __restrict__ cand_off, const int64_t* __restrict__ etile_off,
+                                int64_t E, int64_t C, const double* __restrict__ cent,
+                                const double* __restrict__ rad, const int32_t* __restrict__ tile_seg,
+                                const int32_t* __restrict__ seg_out, int dp, double eps_out,
+                                double eps_in, int use_tc, int2* __restrict__ l_in,
+                                int2* __restrict__ l_tc, int2* __restrict__ l_simt,
+                                unsigned long long* __restrict__ counts)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = warp; q < C; q += nwarp) {
+        const int64_t e = upper_bound_i64(cand_off, E + 1, q) - 1;
+        const int64_t qq = q - cand_off[e];
+        const int64_t t0 = etile_off[e], T = etile_off[e + 1] - t0;
+        int64_t l = 0, r = T - 1;                // diagonal offset o: largest with cum(o) <= qq
+        while (l < r) {
+            const int64_t m = (l + r + 1) >> 1;
+            if (m * T - m * (m - 1) / 2 <= qq) l = m; else r = m - 1;
+        }
+        const int64_t o = l, i = qq - (o * T - o * (o - 1) / 2);
+        const int ta = (int)(t0 + i), tb = (int)(t0 + i + o);
+        double s = 0.0;
+        if (ta != tb)
+            for (int k = lane; k < dp; k += 32) {
+                const double u = cent[(int64_t)ta * dp + k] - cent[(int64_t)tb * dp + k];
+                s += u * u;
+            }
+        for (int w = 16; w; w >>= 1) s += __shfl_xor_sync(0xffffffffu, s, w);
+        if (lane == 0) {
+            const double D = sqrt(s), ra = rad[ta], rb = rad[tb];
+            int cls;
+            if (D - ra - rb > eps_out) cls = -1;
+            else if (D + ra + rb < eps_in) cls = kListAllIn;
+            else if (use_tc && tile_seg[ta] == tile_seg[tb] && !seg_out[tile_seg[ta]]) cls = kListTC;
+            else cls = kListSimt;
+            if (cls < 0) {
+                atomicAdd(&counts[3], 1ull);
+            } else {
+                const unsigned long long at = atomicAdd(&counts[cls], 1ull);
+                int2* dst = cls == kListAllIn ? l_in : (cls == kListTC ? l_tc : l_simt);
+                dst[at] = make_int2(ta, tb);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const int32_t* slot_point,
+                const int32_t* slot_elem, int64_t M, int64_t E, double tau, bool bf16,
+                TileLayout* L, int* nonfinite, cudaStream_t s)
+{
+#define TK(expr)                                                                      \
+    do {                                                                              \
+        cudaError_t e_ = (expr);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            set_error(std::string("build_tiles: ") + cudaGetErrorString(e_));         \
+            return e_ == cudaErrorMemoryAllocation ? MAPPER_ENOMEM : MAPPER_ECUDA;    \
+        }                                                                             \
+    } while (0)
+    const int K = (int)std::min<int64_t>(kPiv, n);
+    Buf Pv, piv, pd2, gid, ngrp;
+    TK(Pv.alloc(sizeof(float) * (size_t)K * dp, s));
+    TK(piv.alloc(sizeof(int32_t) * n, s));
+    TK(pd2.alloc(sizeof(float) * n, s));
+    TK(gid.alloc(sizeof(int32_t) * kPiv, s));
+    TK(ngrp.alloc(sizeof(int32_t), s));
+    pivot_gather_kernel<<<K, 128, 0, s>>>(X, n, d, ld, dp, K, Pv.as<float>());
+    assign_kernel<<<grid_for(n, kT), 256, 0, s>>>(X, n, d, ld, Pv.as<float>(), dp, K, piv.as<int32_t>(),
+                                                 pd2.as<float>());
+    const float tau2 = (float)(tau * tau);
+    group_kernel<<<1, 1024, 0, s>>>(Pv.as<float>(), dp, d, K, tau2, gid.as<int32_t>(), ngrp.as<int32_t>());
+    note_launch(3);
+    TK(cudaGetLastError());
+
+    int ebits = bits_for(E), gbits = bits_for(K + 1), pbits = bits_for(K);
+    if (ebits + gbits + pbits > 32) pbits = 0;
+    if (ebits + gbits + pbits > 32) gbits = 0;
+    Buf keys, tmp, flag, segpos;
+    TK(keys.alloc(sizeof(uint64_t) * M, s));
+    TK(tmp.alloc(sizeof(uint64_t) * M, s));
+    key_kernel<<<grid_for(M), 256, 0, s>>>(slot_point, slot_elem, M, piv.as<int32_t>(), pd2.as<float>(),
+                                          gid.as<int32_t>(), tau2, K, gbits, pbits, keys.as<uint64_t>());
+    note_launch();
+    TK(cudaGetLastError());
+    TK(radix_sort_u64(keys.as<uint64_t>(), tmp.as<uint64_t>(), M, 32, 32 + ebits + gbits + pbits, s));
+    TK(flag.alloc(sizeof(int32_t) * M, s));
+    TK(segpos.alloc(sizeof(int64_t) * (M + 1), s));
+    seg_flag_kernel<<<grid_for(M), 256, 0, s>>>(keys.as<uint64_t>(), M, 32 + pbits, flag.as<int32_t>());
+    note_launch();
+    TK(cudaGetLastError());
+    TK(exclusive_scan_i32_to_i64(flag.as<int32_t>(), segpos.as<int64_t>(), M, s));
+    int64_t nseg = 0;
+    int32_t ng = 0;
+    TK(cudaMemcpyAsync(&nseg, segpos.as<int64_t>() + M, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TK(cudaMemcpyAsync(&ng, ngrp.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    TK(cudaStreamSynchronize(s));
+    L->n_seg = nseg;
+    L->n_groups = gbits ? ng : 1;
+
+    Buf seg_start, seg_elem, seg_tiles, seg_toff;
+    TK(seg_start.alloc(sizeof(int64_t) * (nseg + 1), s));
+    TK(seg_elem.alloc(sizeof(int32_t) * nseg, s));
+    TK(L->seg_outlier.alloc(sizeof(int32_t) * nseg, s));
+    TK(seg_tiles.alloc(sizeof(int64_t) * nseg, s));
+    TK(seg_toff.alloc(sizeof(int64_t) * (nseg + 1), s));
+    seg_start_kernel<<<grid_for(M), 256, 0, s>>>(keys.as<uint64_t>(), flag.as<int32_t>(), segpos.as<int64_t>(),
+                                                M, gbits, pbits, K, seg_start.as<int64_t>(),
+                                                seg_elem.as<int32_t>(), L->seg_outlier.as<int32_t>());
+    seg_tiles_kernel<<<grid_for(nseg), 256, 0, s>>>(seg_start.as<int64_t>(), nseg, seg_tiles.as<int64_t>());
+    note_launch(2);
+    TK(cudaGetLastError());
+    TK(exclusive_scan_i64(seg_tiles.as<int64_t>(), seg_toff.as<int64_t>(), nseg, s));
+    int64_t T = 0;
+    TK(cudaMemcpyAsync(&T, seg_toff.as<int64_t>() + nseg, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TK(cudaStreamSynchronize(s));
+    L->T = T;
+    L->R = T * kT;
+    const int64_t R = L->R;
+
+    TK(L->row_slot.alloc(sizeof(int32_t) * R, s));
+    TK(L->row_pt.alloc(sizeof(int32_t) * R, s));
+    TK(L->G.alloc(sizeof(float) * (size_t)R * dp, s));
+    TK(L->tile_n.alloc(sizeof(int32_t) * T, s));
+    TK(L->tile_seg.alloc(sizeof(int32_t) * T, s));
+    TK(L->tile_elem.alloc(sizeof(int32_t) * T, s));
+    TK(L->tile_cent.alloc(sizeof(double) * (size_t)T * dp, s));
+    TK(L->tile_rad.alloc(sizeof(double) * T, s));
+    TK(L->seg_cent.alloc(sizeof(double) * (size_t)nseg * dp, s));
+    TK(cudaMemsetAsync(L->row_slot.p, 0xff, sizeof(int32_t) * R, s));
+    row_map_kernel<<<grid_for(M), 256, 0, s>>>(keys.as<uint64_t>(), segpos.as<int64_t>(), seg_start.as<int64_t>(),
+                                              seg_toff.as<int64_t>(), M, L->row_slot.as<int32_t>());
+    tile_info_kernel<<<grid_for(nseg), 256, 0, s>>>(seg_start.as<int64_t>(), seg_toff.as<int64_t>(),
+                                                    seg_elem.as<int32_t>(), nseg, L->tile_n.as<int32_t>(),
+                                                    L->tile_seg.as<int32_t>(), L->tile_elem.as<int32_t>());
+    tile_prep_kernel<<<(unsigned)T, 256, 0, s>>>(X, d, ld, dp, slot_point, L->row_slot.as<int32_t>(),
+                                                 L->tile_n.as<int32_t>(), L->G.as<float>(),
+                                                 L->row_pt.as<int32_t>(), L->tile_cent.as<double>(),
+                                                 L->tile_rad.as<double>(), nonfinite);
+    seg_cent_kernel<<<(unsigned)nseg, 256, 0, s>>>(L->tile_cent.as<double>(), L->tile_n.as<int32_t>(),
+                                                  seg_toff.as<int64_t>(), dp, L->seg_cent.as<double>());
+    note_launch(4);
+    TK(cudaGetLastError());
+    if (bf16) {
+        TK(L->Ah.alloc(sizeof(__nv_bfloat16) * (size_t)R * dp, s));
+        TK(L->Al.alloc(sizeof(__nv_bfloat16) * (size_t)R * dp, s));
+        TK(L->rn2.alloc(sizeof(float) * R, s));
+        TK(L->rn.alloc(sizeof(float) * R, s));
+        operand_kernel<<<(unsigned)T, 256, 0, s>>>(L->G.as<float>(), d, dp, L->tile_n.as<int32_t>(),
+                                                   L->tile_seg.as<int32_t>(), L->seg_cent.as<double>(),
+                                                   L->Ah.as<__nv_bfloat16>(), L->Al.as<__nv_bfloat16>(),
+                                                   L->rn2.as<float>(), L->rn.as<float>());
+        note_launch();
+        TK(cudaGetLastError());
+    }
+    return MAPPER_OK;
+}
+
+int classify_pairs(const TileLayout& L, int dp, int64_t E, double eps, bool use_tc, PairLists* P,
+                   cudaStream_t s)
+{
+    Buf etile_off, cnt, cand_off, counts;
+    TK(etile_off.alloc(sizeof(int64_t) * (E + 1), s));
+    TK(cnt.alloc(sizeof(int64_t) * std::max<int64_t>(E, 1), s));
+    TK(cand_off.alloc(sizeof(int64_t) * (E + 1), s));
+    TK(counts.alloc(sizeof(unsigned long long) * 4, s));
+    TK(cudaMemsetAsync(counts.p, 0, sizeof(unsigned long long) * 4, s));
+    elem_tiles_kernel<<<grid_for(E + 1), 256, 0, s>>>(L.tile_elem.as<int32_t>(), L.T, E, etile_off.as<int64_t>());
+    cand_count_kernel<<<grid_for(E), 256, 0, s>>>(etile_off.as<int64_t>(), E, cnt.as<int64_t>());
+    note_launch(2);
+    TK(cudaGetLastError());
+    TK(exclusive_scan_i64(cnt.as<int64_t>(), cand_off.as<int64_t>(), E, s));
+    int64_t C = 0;
+    TK(cudaMemcpyAsync(&C, cand_off.as<int64_t>() + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TK(cudaStreamSynchronize(s));
+    P->n_candidates = C;
+    for (int k = 0; k < kListCount; ++k) TK(P->list[k].alloc(sizeof(int2) * std::max<int64_t>(C, 1), s));
+    if (C > 0) {
+        const double eps_out = eps * (1.0 + 1e-9), eps_in = eps * (1.0 - 1e-9);
+        const unsigned blocks = (unsigned)std::min<int64_t>(div_up(C, 8), 152 * 64);
+        classify_kernel<<<blocks, 256, 0, s>>>(cand_off.as<int64_t>(), etile_off.as<int64_t>(), E, C,
+                                               L.tile_cent.as<double>(), L.tile_rad.as<double>(),
+                                               L.tile_seg.as<int32_t>(), L.seg_outlier.as<int32_t>(), dp,
+                                               eps_out, eps_in, use_tc ? 1 : 0, P->list[kListAllIn].as<int2>(),
+                                               P->list[kListTC].as<int2>(), P->list[kListSimt].as<int2>(),
+                                               counts.as<unsigned long long>());
+        note_launch();
+        TK(cudaGetLastError());
+    }
+    unsigned long long h[4] = {0, 0, 0, 0};
+    TK(cudaMemcpyAsync(h, counts.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    TK(cudaStreamSynchronize(s));
+    for (int k = 0; k < kListCount; ++k) P->n[k] = (int64_t)h[k];
+    P->n_out = (int64_t)h[3];
+    return MAPPER_OK;
+#undef TK
+}
+
+}  // namespace mgb

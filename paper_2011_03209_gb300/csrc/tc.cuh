@@ -1,12 +1,23 @@
-// tc.cuh -- internal interface of the tcgen05 (tensor-core) screen passes.
+// tc.cuh -- internal interface of the tcgen05 (tensor-core) screening passes.
 #pragma once
 
 #include "dbscan.cuh"
 
 namespace mgb {
 
-// Runs passes 1-3 (count, core flags, unions, flatten, border) with the BF16
-// tensor-core screen. Returns a mapper_status.
-int tc_cluster_passes(const PassArgs& a, int64_t n_pairs, int32_t min_pts, cudaStream_t s);
+// Operands of the tensor-core screen: rows centred on their segment's
+// centroid, split into BF16 hi and lo parts (R x dp each, row-major), with
+// |a|^2 (FP32, to nearest) and |a| (FP32, rounded up) per row.
+struct TcArgs {
+    const void* Ah;
+    const void* Al;
+    const float* rn2;
+    const float* rn;
+    int64_t R;
+};
+
+// Pass `mode` (1 = counts and neighbour lists, 2 = unions) over the tile
+// pairs a.pairs[0 .. n_pairs) on tensor cores. Returns a mapper_status.
+int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaStream_t s);
 
 }  // namespace mgb
