@@ -83,7 +83,11 @@ typedef enum mapper_lens_kind {
  * FP64, so all precisions give the same exact graph. */
 typedef enum mapper_precision {
     MAPPER_FP32 = 0,         /* CUDA-core FP32 sum of squared differences */
-    MAPPER_BF16 = 1          /* tcgen05 tensor cores, BF16 in, FP32 accumulate */
+    MAPPER_BF16 = 1,         /* tcgen05 tensor cores, BF16 in, FP32 accumulate; rows
+                                centred per group and split hi + lo: three products,
+                                a narrow band */
+    MAPPER_BF16X1 = 2        /* as MAPPER_BF16 with the hi part only: one product, a
+                                band about 2^8 times wider */
 } mapper_precision;
 
 typedef struct mapper_ctx mapper_ctx;

@@ -22,7 +22,7 @@ MAPPER_EINTERNAL = -6
 MAPPER_ENOTIMPL = -7
 
 LENS_L2, LENS_COORD, LENS_PCA = 0, 1, 2
-FP32, BF16 = 0, 1
+FP32, BF16, BF16X1 = 0, 1, 2
 
 # every symbol include/mapper.h declares
 EXPORTS = (

@@ -270,13 +270,13 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
 {
     if (!(eps > 0.0) || !std::isfinite(eps)) return fail(MAPPER_EINVAL, "eps must be finite and > 0");
     if (min_pts < 1) return fail(MAPPER_EINVAL, "min_pts must be >= 1");
-    if (precision != MAPPER_FP32 && precision != MAPPER_BF16)
+    if (precision != MAPPER_FP32 && precision != MAPPER_BF16 && precision != MAPPER_BF16X1)
         return fail(MAPPER_EINVAL, "unknown precision");
     if (cov->n != n) return fail(MAPPER_EINVAL, "cover was built for another point count");
     cudaStream_t s = ctx->stream->s;
     const int64_t M = cov->M, E = cov->E;
     const int dp = (d + 31) / 32 * 32;
-    const bool use_tc = precision == MAPPER_BF16;
+    const bool use_tc = precision != MAPPER_FP32;
     const int cap = (min_pts >= 2 && min_pts - 1 <= 64) ? min_pts - 1 : 0;
     const double rows_est = (double)M + 128.0 * (double)E;
     const double est = rows_est * dp * (use_tc ? 8.0 : 4.0) + rows_est * (40.0 + 4.0 * cap);
@@ -356,12 +356,24 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     a_tc.pairs = PL.list[kListTC].as<int2>();
     a_simt.pairs = PL.list[kListSimt].as<int2>();
     TcArgs t{};
+    Buf queue, queue_n, tc_err;
     if (use_tc) {
         t.Ah = L.Ah.p;
         t.Al = L.Al.p;
         t.rn2 = L.rn2.as<float>();
         t.rn = L.rn.as<float>();
         t.R = R;
+        t.ns = precision == MAPPER_BF16X1 ? 1 : 3;
+        t.num_sms = ctx->num_sms;
+        t.queue_cap = (unsigned long long)std::min<int64_t>(
+            int64_t(1) << 25, std::max<int64_t>(int64_t(1) << 20, 128 * PL.n[kListTC]));
+        CK(queue.alloc(sizeof(uint2) * t.queue_cap, s), "alloc band queue");
+        CK(queue_n.alloc(sizeof(unsigned long long), s), "alloc");
+        CK(tc_err.alloc(sizeof(int), s), "alloc");
+        CK(cudaMemsetAsync(tc_err.p, 0, sizeof(int), s), "memset");
+        t.queue = queue.as<uint2>();
+        t.queue_n = queue_n.as<unsigned long long>();
+        t.err = tc_err.as<int>();
     }
 
     pt.mark();                                                    // 1
@@ -397,11 +409,13 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
                      c->core.as<uint8_t>(), s), "labels");
 
     unsigned long long h_stats[kStatCount];
-    int h_nf = 0;
+    int h_nf = 0, h_err = 0;
     CK(cudaMemcpyAsync(h_stats, stats.p, sizeof(h_stats), cudaMemcpyDeviceToHost, s), "copy");
     CK(cudaMemcpyAsync(&h_nf, nf, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+    if (use_tc) CK(cudaMemcpyAsync(&h_err, tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
     CK(cudaStreamSynchronize(s), "sync");
     if (h_nf) return fail(MAPPER_ENONFINITE, "X holds NaN or Inf");
+    if (h_err) return fail(MAPPER_ETIMEOUT, "a tensor-core pass gave up waiting on a barrier");
     st.band_pairs = (int64_t)h_stats[kStatBand];
     st.near_ties = (int64_t)h_stats[kStatTies];
     st.pairs_screened = (int64_t)h_stats[kStatScreened];

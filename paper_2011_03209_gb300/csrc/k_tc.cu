@@ -1,13 +1,716 @@
-// k_tc.cu -- tcgen05 tensor-core screen passes (BF16 in, FP32 accumulate).
+// k_tc.cu -- tcgen05 tensor-core screen for the per-element DBSCAN passes
+// ("Mapper Interactive" §3 DBSCAN per cover element; §4.3 names the
+// all-pairs distances the bottleneck).
+//
+// For a tile pair (A, B) of one segment, rows are centred on the segment's
+// FP64 centroid c: a = x - c, b = y - c, so d^2(x, y) = |a|^2 + |b|^2 - 2 a.b.
+// a and b are split into BF16 parts a = hi + lo (+ tiny), and the cross term
+// comes from tcgen05.mma (kind::f16, BF16 in, FP32 accumulate in TMEM):
+//   NS = 3: hi.hi + hi.lo + lo.hi      NS = 1: hi.hi only.
+// The screen value s = (|a|^2 + |b|^2) - 2 acc is certified against eps^2 by
+// a rigorous bound E(a, b) = A1 |a||b| + A2 (|a|^2 + |b|^2) + A3 (see
+// tc_bound below); pairs with |s - eps^2| <= E are queued and re-decided in
+// FP64 by the defining expression, so every decision equals FP64.
+//
+// Kernel layout (one CTA per SM, persistent over a static share of the tile
+// pairs): warp 0 issues TMA loads of 64-column K blocks (128-byte swizzle)
+// into a ring of smem stages; warp 1 issues the MMAs into one of two TMEM
+// accumulators (128 x 128 FP32 each); warps 2-5 read the accumulator rows
+// with tcgen05.ld (one row per thread) and run the pass epilogue:
+//   pass 1: neighbour counts of rows and columns (and neighbour lists),
+//   pass 2: unions of core-core neighbour pairs.
+// Every mbarrier wait is bounded in time; a wait that runs out sets an error
+// flag, stops all roles, waits (bounded) for its own copies and MMAs, frees
+// TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cfloat>
+#include <climits>
+#include <cmath>
+#include <mutex>
+
 #include "../../include/mapper.h"
 #include "tc.cuh"
 
 namespace mgb {
 
-int tc_pass(int, const PassArgs&, const TcArgs&, int64_t, cudaStream_t)
+namespace {
+
+constexpr int kT = kTile;
+constexpr int kKB = 64;                       // BF16 columns per K block (128-byte rows)
+constexpr int kBlk = kT * kKB * 2;            // bytes of one 128 x 64 BF16 block
+constexpr int kThreads = 192;                 // producer, MMA, 4 epilogue warps
+constexpr unsigned long long kWaitNs = 4000000000ull;   // 4 s per wait at most
+
+struct TcParams {
+    PassArgs A;
+    const float* rn2;
+    const float* rn;
+    int64_t n_pairs;
+    int nkb;                                  // K blocks per row
+    double A1, A2, A3;                        // bound constants
+    uint2* queue;                             // band pairs: (row a, row b | flags << 30)
+    unsigned long long* queue_n;
+    unsigned long long queue_cap;
+    int* err;                                 // 1: a wait timed out
+};
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtime()
 {
-    set_error("BF16 tensor-core screen not built yet");
-    return MAPPER_ENOTIMPL;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false (and *abort set) if the phase did not complete in time
+// or another role already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort)
+{
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = gtime();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if ((it & 255u) == 0) {
+            if (*abort) return false;
+            if (gtime() - t0 > kWaitNs) {
+                *abort = 1;
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(su32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+
+// K-major operand, 128-byte swizzle: 8-row groups 1024 bytes apart; the
+// start address moves 32 bytes per 16-column MMA step inside the atom.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kT >> 3) << 17) |
+                            ((uint32_t)(kT >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+            tmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Barrier of the 128 epilogue threads that also ORs a flag over them, so all
+// take the same branch afterwards.
+__device__ __forceinline__ bool epi_sync_or(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+
+// ------------------------------------------------------- union-find, FP64
+__device__ __forceinline__ int key_of(const int32_t* row_pt, int row) { return row_pt ? __ldg(row_pt + row) : row; }
+
+__device__ __forceinline__ int gfind(int32_t* parent, int x)
+{
+    volatile int32_t* par = parent;
+    int p = par[x];
+    while (p != x) {
+        const int gp = par[p];
+        if (gp != p) par[x] = gp;
+        x = p;
+        p = par[x];
+    }
+    return x;
+}
+
+__device__ __forceinline__ void gunion(int32_t* parent, const int32_t* row_pt, int a, int b)
+{
+    while (true) {
+        a = gfind(parent, a);
+        b = gfind(parent, b);
+        if (a == b) return;
+        if (key_of(row_pt, a) < key_of(row_pt, b)) { const int t = a; a = b; b = t; }
+        if (atomicCAS(&parent[a], a, b) == a) return;
+    }
+}
+
+__device__ __forceinline__ int lfind(volatile int* par, int x)
+{
+    int p = par[x];
+    while (p != x) {
+        const int gp = par[p];
+        if (gp != p) par[x] = gp;
+        x = p;
+        p = par[x];
+    }
+    return x;
+}
+
+__device__ __forceinline__ void lunion(int* par, int a, int b)
+{
+    volatile int* vp = par;
+    while (true) {
+        a = lfind(vp, a);
+        b = lfind(vp, b);
+        if (a == b) return;
+        if (a < b) { const int t = a; a = b; b = t; }
+        if (atomicCAS(&par[a], a, b) == a) return;
+    }
+}
+
+__device__ __forceinline__ double exact_sqdist(const float* __restrict__ x, const float* __restrict__ y, int d)
+{
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) {
+        const double t = __dsub_rn((double)x[k], (double)y[k]);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return s;
+}
+
+// Queue flags (bits 30-31 of the second row): pass 1: bit 0 = also count for
+// row b, bit 1 = count the pair as a near tie candidate.
+enum : uint32_t { kQBoth = 1u, kQTie = 2u };
+
+// Queue a band pair, or decide it here when the queue is full.
+__device__ __forceinline__ bool push_band(const TcParams& P, int ra, int rb, uint32_t flags, bool* decided)
+{
+    const unsigned long long at = atomicAdd(P.queue_n, 1ull);
+    if (at < P.queue_cap) {
+        P.queue[at] = make_uint2((uint32_t)ra, (uint32_t)rb | (flags << 30));
+        *decided = false;
+        return false;
+    }
+    const PassArgs& A = P.A;
+    const double d2 = exact_sqdist(A.G + (int64_t)ra * A.dp, A.G + (int64_t)rb * A.dp, A.d);
+    atomicAdd(&A.stats[kStatBand], 1ull);
+    if ((flags & kQTie) && fabs(d2 - A.eps2) <= A.tie_thr) atomicAdd(&A.stats[kStatTies], 1ull);
+    *decided = true;
+    return d2 <= A.eps2;
+}
+
+// ------------------------------------------------------------------ kernel
+struct SmemTail {
+    uint64_t full[4], empty[4], acc_full[2], acc_empty[2], fin;
+    uint32_t tmem_base;
+    int abort;
+    int consumed;                              // stage fills consumed by the MMA warp
+    int s_mm[2];
+    float nb2[kT], nrb[kT];
+    uint32_t colmask[4][kT];
+    int par[2 * kT];
+    unsigned char core[2 * kT];
+    float red[8];
+};
+
+template <int NS, int MODE>
+__global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__ CUtensorMap mAh,
+                                                         const __grid_constant__ CUtensorMap mAl,
+                                                         const TcParams P)
+{
+    constexpr int kOps = NS == 1 ? 2 : 4;                 // blocks per stage: Ah, Bh (, Al, Bl)
+    constexpr int kStages = NS == 1 ? 4 : 3;
+    constexpr int kStageBytes = kOps * kBlk;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    SmemTail& S = *reinterpret_cast<SmemTail*>(smem + kStages * kStageBytes);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const PassArgs& A = P.A;
+    volatile int* abort = &S.abort;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&S.tmem_base)),
+                     "r"(2 * kT));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 32) {
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&S.full[i], 1);
+            mbar_init(&S.empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&S.acc_full[i], 1);
+            mbar_init(&S.acc_empty[i], 4);
+        }
+        mbar_init(&S.fin, 1);
+        S.abort = 0;
+        S.consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem_base;
+
+    if (warp == 0) {
+        // ---------------------------------------------------- TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued = 0;
+            for (int64_t q = blockIdx.x; q < P.n_pairs && !*abort; q += gridDim.x) {
+                const int2 tp = A.pairs[q];
+                const bool diag = tp.x == tp.y;
+                const uint32_t bytes = (uint32_t)((diag ? kOps / 2 : kOps) * kBlk);
+                for (int kb = 0; kb < P.nkb; ++kb) {
+                    if (!mbar_wait(&S.empty[stage], phase ^ 1, abort)) break;
+                    unsigned char* st = smem + stage * kStageBytes;
+                    mbar_expect_tx(&S.full[stage], bytes);
+                    tma_load(st, &mAh, kb * kKB, tp.x * kT, &S.full[stage]);
+                    if (!diag) tma_load(st + kBlk, &mAh, kb * kKB, tp.y * kT, &S.full[stage]);
+                    if (NS == 3) {
+                        tma_load(st + 2 * kBlk, &mAl, kb * kKB, tp.x * kT, &S.full[stage]);
+                        if (!diag) tma_load(st + 3 * kBlk, &mAl, kb * kKB, tp.y * kT, &S.full[stage]);
+                    }
+                    ++issued;
+                    if (++stage == kStages) { stage = 0; phase ^= 1; }
+                }
+            }
+            // on abort: let the copies already issued land before the CTA exits
+            if (*abort) {
+                __threadfence_block();
+                int consumed = *(volatile int*)&S.consumed;
+                int st = consumed % kStages;
+                uint32_t ph = (uint32_t)((consumed / kStages) & 1);
+                volatile int dummy = 0;
+                for (int f = consumed; f < issued; ++f) {
+                    mbar_wait(&S.full[st], ph, &dummy);
+                    if (++st == kStages) { st = 0; ph ^= 1; }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int it = 0;
+            for (int64_t q = blockIdx.x; q < P.n_pairs && !*abort; q += gridDim.x, ++it) {
+                const int2 tp = A.pairs[q];
+                const bool diag = tp.x == tp.y;
+                const int buf = it & 1;
+                const uint32_t acc_phase = (uint32_t)((it >> 1) & 1);
+                if (!mbar_wait(&S.acc_empty[buf], acc_phase ^ 1, abort)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(buf * kT);
+                bool ok = true;
+                for (int kb = 0; kb < P.nkb; ++kb) {
+                    if (!mbar_wait(&S.full[stage], phase, abort)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t base = su32(smem + stage * kStageBytes);
+                    const uint32_t ah = base, bh = diag ? base : base + kBlk;
+                    const uint32_t al = base + 2 * kBlk, bl = diag ? al : base + 3 * kBlk;
+#pragma unroll
+                    for (int j = 0; j < kKB / 16; ++j) {
+                        const uint32_t acc0 = (kb | j) ? 1u : 0u;
+                        mma_bf16(d_tmem, smem_desc(ah + 32 * j), smem_desc(bh + 32 * j), acc0);
+                        if (NS == 3) {
+                            mma_bf16(d_tmem, smem_desc(ah + 32 * j), smem_desc(bl + 32 * j), 1u);
+                            mma_bf16(d_tmem, smem_desc(al + 32 * j), smem_desc(bh + 32 * j), 1u);
+                        }
+                    }
+                    mma_commit(&S.empty[stage]);
+                    *(volatile int*)&S.consumed = S.consumed + 1;
+                    if (++stage == kStages) { stage = 0; phase ^= 1; }
+                }
+                if (!ok) break;
+                mma_commit(&S.acc_full[buf]);
+            }
+            // all MMAs issued by this thread have completed once `fin` flips
+            mma_commit(&S.fin);
+            volatile int dummy = 0;
+            mbar_wait(&S.fin, 0, &dummy);
+        }
+    } else {
+        // ---------------------------------------------------- epilogue
+        const int et = tid - 64;                              // 0..127
+        const int quad = warp & 3;                            // TMEM lane quadrant of this warp
+        const int r = quad * 32 + lane;                       // accumulator row = A-tile row
+        int it = 0;
+        for (int64_t q = blockIdx.x; q < P.n_pairs; q += gridDim.x, ++it) {
+            const int2 tp = A.pairs[q];
+            const bool diag = tp.x == tp.y;
+            const int na = A.tile_n[tp.x], nb = A.tile_n[tp.y];
+            const int64_t sa = (int64_t)tp.x * kT, sb = (int64_t)tp.y * kT;
+            const int buf = it & 1;
+            const uint32_t acc_phase = (uint32_t)((it >> 1) & 1);
+            const bool valid_r = r < na;
+
+            // column data of this pair; per-tile maxima for the row bounds
+            epi_sync();
+            S.nb2[et] = P.rn2[sb + et];
+            S.nrb[et] = P.rn[sb + et];
+            if (MODE == 2) {
+                S.core[et] = (et < na) && A.core[sa + et];
+                S.core[kT + et] = !diag && (et < nb) && A.core[sb + et];
+                S.par[et] = et;
+                S.par[kT + et] = kT + et;
+                if (et == 0) { S.s_mm[0] = INT_MAX; S.s_mm[1] = -1; }
+            }
+            float m2 = S.nb2[et], m1 = S.nrb[et];
+            for (int o = 16; o; o >>= 1) {
+                m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+                m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+            }
+            if (lane == 0) { S.red[warp - 2] = m2; S.red[4 + warp - 2] = m1; }
+            epi_sync();
+            const float nb2max = fmaxf(fmaxf(S.red[0], S.red[1]), fmaxf(S.red[2], S.red[3]));
+            const float nrbmax = fmaxf(fmaxf(S.red[4], S.red[5]), fmaxf(S.red[6], S.red[7]));
+
+            // union pass: skip pairs whose core rows already share one root
+            bool work = true;
+            if (MODE == 2) {
+                const bool ca = S.core[et], cbb = S.core[kT + et];
+                if (ca) { const int rr = gfind(A.parent, (int)(sa + et)); atomicMin(&S.s_mm[0], rr); atomicMax(&S.s_mm[1], rr); }
+                if (cbb) { const int rr = gfind(A.parent, (int)(sb + et)); atomicMin(&S.s_mm[0], rr); atomicMax(&S.s_mm[1], rr); }
+                epi_sync();
+                work = S.s_mm[1] >= 0 && S.s_mm[0] != S.s_mm[1];
+                if (!work && S.s_mm[1] >= 0 && et == 0) atomicAdd(&A.stats[kStatSkipped], 1ull);
+            }
+
+            const float na2 = P.rn2[sa + r], nra = P.rn[sa + r];
+            const double E = P.A1 * (double)nra * (double)nrbmax + P.A2 * ((double)na2 + (double)nb2max) + P.A3;
+            const float thr_in = __double2float_rd(A.eps2 - E);
+            const float thr_out = __double2float_ru(A.eps2 + E);
+            const bool core_r = MODE == 2 ? (bool)S.core[r] : false;
+
+            // every epilogue warp reaches the barrier, then all leave together
+            const bool bad = !mbar_wait(&S.acc_full[buf], acc_phase, abort) || *abort;
+            if (epi_sync_or(bad)) break;
+            tc_fence_after();
+            uint32_t rowbits[4] = {0u, 0u, 0u, 0u};
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * kT + c * 32), v);
+                if (c == 3) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&S.acc_empty[buf]);
+                }
+                uint32_t bits = 0u, mine = 0u;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int j = c * 32 + i;
+                    const float s = fmaf(-2.f, v[i], na2 + S.nb2[j]);
+                    bool in = s <= thr_in;
+                    bool cand = valid_r && j < nb;
+                    if (MODE == 2) cand = cand && work && core_r && S.core[diag ? j : kT + j];
+                    if (MODE == 2 && diag) cand = cand && j > r;
+                    if (cand && !in && s <= thr_out) {
+                        bool decided;
+                        uint32_t fl = MODE == 1 ? ((diag ? 0u : kQBoth) | ((!diag || r < j) ? kQTie : 0u)) : 0u;
+                        in = push_band(P, (int)(sa + r), (int)(sb + j), fl, &decided);
+                        if (!decided) in = false;             // decided later by the recheck kernel
+                    }
+                    in = in && cand;
+                    bits |= (uint32_t)in << i;
+                    if (MODE == 1 && !diag) {
+                        const uint32_t col = __ballot_sync(0xffffffffu, in);
+                        if (lane == i) mine = col;
+                    }
+                }
+                rowbits[c] = bits;
+                if (MODE == 1 && !diag) S.colmask[quad][c * 32 + lane] = mine;
+            }
+
+            if (MODE == 1) {
+                const int k = __popc(rowbits[0]) + __popc(rowbits[1]) + __popc(rowbits[2]) + __popc(rowbits[3]);
+                if (k > 0) {
+                    const int old = atomicAdd(&A.count[sa + r], k);
+                    if (A.cap > 0 && old < A.cap) {
+                        int pos = old;
+                        for (int c = 0; c < 4 && pos < A.cap; ++c) {
+                            uint32_t b = rowbits[c];
+                            while (b && pos < A.cap) {
+                                const int i = __ffs(b) - 1;
+                                b &= b - 1;
+                                A.nbr[(sa + r) * A.cap + pos++] = (int32_t)(sb + c * 32 + i);
+                            }
+                        }
+                    }
+                }
+                if (!diag) {
+                    epi_sync();
+                    const int j = et;
+                    int tot = 0;
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) tot += __popc(S.colmask[w][j]);
+                    if (tot > 0) {
+                        const int old = atomicAdd(&A.count[sb + j], tot);
+                        if (A.cap > 0 && old < A.cap) {
+                            int pos = old;
+                            for (int w = 0; w < 4 && pos < A.cap; ++w) {
+                                uint32_t b = S.colmask[w][j];
+                                while (b && pos < A.cap) {
+                                    const int i = __ffs(b) - 1;
+                                    b &= b - 1;
+                                    A.nbr[(sb + j) * A.cap + pos++] = (int32_t)(sa + w * 32 + i);
+                                }
+                            }
+                        }
+                    }
+                }
+                if (et == 0) {
+                    const int64_t pairs = diag ? (int64_t)na * (na + 1) / 2 : (int64_t)na * nb;
+                    atomicAdd(&A.stats[kStatScreened], (unsigned long long)pairs);
+                }
+            } else {
+                // local unions over the pair's 256 rows, then global unions
+                if (work) {
+                    for (int c = 0; c < 4; ++c) {
+                        uint32_t b = rowbits[c];
+                        while (b) {
+                            const int i = __ffs(b) - 1;
+                            b &= b - 1;
+                            const int j = c * 32 + i;
+                            lunion(S.par, r, diag ? j : kT + j);
+                        }
+                    }
+                }
+                epi_sync();
+                if (work) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int x = h * kT + et;
+                        if (!S.core[x]) continue;
+                        const int rx = lfind(S.par, x);
+                        if (rx != x) {
+                            const int64_t row_x = x < kT ? sa + x : sb + (x - kT);
+                            const int64_t row_r = rx < kT ? sa + rx : sb + (rx - kT);
+                            gunion(A.parent, A.row_pt, (int)row_x, (int)row_r);
+                        }
+                    }
+                }
+            }
+        }
+    }
+
+    // ---------------------------------------------------------- teardown
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0 && S.abort) atomicExch(P.err, 1);
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kT));
+}
+
+// Band pairs queued by the epilogues, re-decided in FP64 (k ascending, one
+// rounding per operation: the defining expression).
+template <int MODE>
+__global__ void recheck_kernel(const PassArgs A, const uint2* __restrict__ queue,
+                               const unsigned long long* __restrict__ queue_n, unsigned long long cap)
+{
+    const unsigned long long n = min(*queue_n, cap);
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint2 e = queue[i];
+        const int ra = (int)e.x, rb = (int)(e.y & 0x3FFFFFFFu);
+        const uint32_t fl = e.y >> 30;
+        const double d2 = exact_sqdist(A.G + (int64_t)ra * A.dp, A.G + (int64_t)rb * A.dp, A.d);
+        atomicAdd(&A.stats[kStatBand], 1ull);
+        if (MODE == 1 && (fl & kQTie) && fabs(d2 - A.eps2) <= A.tie_thr) atomicAdd(&A.stats[kStatTies], 1ull);
+        if (!(d2 <= A.eps2)) continue;
+        if (MODE == 1) {
+            int old = atomicAdd(&A.count[ra], 1);
+            if (A.cap > 0 && old < A.cap) A.nbr[(int64_t)ra * A.cap + old] = rb;
+            if (fl & kQBoth) {
+                old = atomicAdd(&A.count[rb], 1);
+                if (A.cap > 0 && old < A.cap) A.nbr[(int64_t)rb * A.cap + old] = ra;
+            }
+        } else {
+            gunion(A.parent, A.row_pt, ra, rb);
+        }
+    }
+}
+
+// --------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int dp)
+{
+    auto enc = encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)dp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)dp * 2};
+    cuuint32_t box[2] = {kKB, kT};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NS>
+constexpr int smem_bytes()
+{
+    return (NS == 1 ? 4 : 3) * (NS == 1 ? 2 : 4) * kBlk + (int)sizeof(SmemTail) + 1024;
+}
+
+template <int NS, int MODE>
+cudaError_t launch(const CUtensorMap& mh, const CUtensorMap& ml, const TcParams& p, int grid, cudaStream_t s)
+{
+    const int smem = smem_bytes<NS>();
+    cudaError_t e = cudaFuncSetAttribute(tc_kernel<NS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    tc_kernel<NS, MODE><<<grid, kThreads, smem, s>>>(mh, ml, p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Error bound of the screen value s = fl(fl(|a|^2 + |b|^2) - 2 acc) against
+// d^2 = |a|^2 + |b|^2 - 2 a.b for FP64-centred a, b, with u = 2^-8 (BF16):
+//   operand rounding  NS = 1: |hi(a).hi(b) - a.b| <= (2u + u^2) S|a||b|
+//                     NS = 3: a = hi + lo + r, |r| <= u^2 |a|, |lo| <= u |a|;
+//                             dropping lo.lo and r terms costs <= 3.01 u^2 S
+//   accumulation      m MMA steps of 16 exact products each, FP32 accumulator:
+//                     <= m 2^-22 (1 + 2u)^2 S (two units per step, allowing
+//                     truncation), S = sum |a_k||b_k| <= |a||b|
+//   norms and final   |a|^2, |b|^2 to nearest FP32, one add, one fma:
+//                     <= 2^-22 (|a|^2 + |b|^2) + 2^-23 2|acc|
+// The factor 2 of the cross term and a 1.25 margin are applied to A1. The
+// FP32 rounding of eps^2 and tiny subnormal terms go into A3.
+void tc_bound(int ns, int dp, double eps2, double* A1, double* A2, double* A3)
+{
+    const double u = std::ldexp(1.0, -8);
+    const int steps = ns * ((dp + kKB - 1) / kKB) * (kKB / 16);
+    const double oper = ns == 1 ? (2.0 * u + u * u) : 3.01 * u * u;
+    const double accu = steps * std::ldexp(1.0, -22) * (1.0 + 2.0 * u) * (1.0 + 2.0 * u);
+    *A1 = 1.25 * (2.0 * (oper + accu) + 4.0 * std::ldexp(1.0, -23));
+    *A2 = 2.0 * std::ldexp(1.0, -22);
+    *A3 = std::ldexp(1.0, -40) * eps2 + 1e-30;
+}
+
+int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaStream_t s)
+{
+    if (n_pairs == 0) return MAPPER_OK;
+    if (t.R >= (int64_t(1) << 30)) {
+        set_error("tensor-core screen: more than 2^30 rows");
+        return MAPPER_ENOMEM;
+    }
+    CUtensorMap mh, ml;
+    if (!make_map(&mh, t.Ah, t.R, a.dp) || !make_map(&ml, t.ns == 3 ? t.Al : t.Ah, t.R, a.dp)) {
+        set_error("cuTensorMapEncodeTiled failed (or is unavailable)");
+        return MAPPER_ECUDA;
+    }
+    TcParams p{};
+    p.A = a;
+    p.rn2 = t.rn2;
+    p.rn = t.rn;
+    p.n_pairs = n_pairs;
+    p.nkb = (a.dp + kKB - 1) / kKB;
+    tc_bound(t.ns, a.dp, a.eps2, &p.A1, &p.A2, &p.A3);
+    p.queue = t.queue;
+    p.queue_n = t.queue_n;
+    p.queue_cap = t.queue_cap;
+    p.err = t.err;
+    cudaError_t e = cudaMemsetAsync(t.queue_n, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ECUDA; }
+    const int grid = (int)std::min<int64_t>(n_pairs, t.num_sms);
+    if (t.ns == 3)
+        e = mode == 1 ? launch<3, 1>(mh, ml, p, grid, s) : launch<3, 2>(mh, ml, p, grid, s);
+    else
+        e = mode == 1 ? launch<1, 1>(mh, ml, p, grid, s) : launch<1, 2>(mh, ml, p, grid, s);
+    note_launch();
+    if (e != cudaSuccess) {
+        set_error(std::string("tensor-core pass: ") + cudaGetErrorString(e));
+        return MAPPER_ECUDA;
+    }
+    const int rgrid = t.num_sms * 8;
+    if (mode == 1) recheck_kernel<1><<<rgrid, 256, 0, s>>>(a, t.queue, t.queue_n, t.queue_cap);
+    else recheck_kernel<2><<<rgrid, 256, 0, s>>>(a, t.queue, t.queue_n, t.queue_cap);
+    note_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("band recheck: ") + cudaGetErrorString(e));
+        return MAPPER_ECUDA;
+    }
+    return MAPPER_OK;
 }
 
 }  // namespace mgb

@@ -14,10 +14,19 @@ struct TcArgs {
     const float* rn2;
     const float* rn;
     int64_t R;
+    int ns;                          // BF16 products per pair: 3 (hi.hi + hi.lo + lo.hi) or 1
+    int num_sms;                     // persistent grid size
+    uint2* queue;                    // band pairs for the FP64 recheck
+    unsigned long long* queue_n;     // entries pushed (may exceed queue_cap)
+    unsigned long long queue_cap;
+    int* err;                        // set to 1 if a bounded wait ran out
 };
 
 // Pass `mode` (1 = counts and neighbour lists, 2 = unions) over the tile
 // pairs a.pairs[0 .. n_pairs) on tensor cores. Returns a mapper_status.
 int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaStream_t s);
+
+// Constants of the screen's error bound E = A1 |a||b| + A2 (|a|^2 + |b|^2) + A3.
+void tc_bound(int ns, int dp, double eps2, double* A1, double* A2, double* A3);
 
 }  // namespace mgb

@@ -5,6 +5,8 @@ membership, per-slot core flags and cluster labels, node memberships and
 edges are equal element by element. The oracle is fed the GPU's lens (and,
 for principal-component lenses, checked against the GPU's basis), so a lens
 rounding difference could not hide a clustering difference."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -65,20 +67,25 @@ TINY = [
 ]
 
 
+PRECISIONS = [mg.FP32, mg.BF16, mg.BF16X1]
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
 @pytest.mark.parametrize("n,d,seed,n_int,ov,q,min_pts", TINY)
-def test_tiny_l2(ctx, n, d, seed, n_int, ov, q, min_pts):
+def test_tiny_l2(ctx, n, d, seed, n_int, ov, q, min_pts, prec):
     X = synth.tiny_random(n, d, seed, scale=2.0)
     eps = _eps(X, q, seed)
-    res = run_gpu(ctx, X, (0,), (0,), (n_int,), (ov,), eps, min_pts)
+    res = run_gpu(ctx, X, (0,), (0,), (n_int,), (ov,), eps, min_pts, prec)
     assert np.array_equal(res["lens"][:, 0], oracle.lens_l2(X))
     assert_same_graph(X, res, (n_int,), (ov,), eps, min_pts)
 
 
+@pytest.mark.parametrize("prec", PRECISIONS)
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_duplicates_min_pts_one_coord_lens(ctx, seed):
+def test_duplicates_min_pts_one_coord_lens(ctx, seed, prec):
     X = synth.tiny_random(350, 4, seed, dup_frac=0.3)
     eps = _eps(X, 5, seed)
-    res = run_gpu(ctx, X, (1,), (2,), (7,), (0.35,), eps, 1)
+    res = run_gpu(ctx, X, (1,), (2,), (7,), (0.35,), eps, 1, prec)
     assert np.array_equal(res["lens"][:, 0], X[:, 2].astype(np.float64))
     assert_same_graph(X, res, (7,), (0.35,), eps, 1)
 
@@ -105,11 +112,12 @@ def test_many_empty_elements(ctx):
     assert_same_graph(X, res, (97,), (0.15,), 0.5, 3)
 
 
+@pytest.mark.parametrize("prec", PRECISIONS)
 @pytest.mark.parametrize("seed", [0, 1])
-def test_2d_cover(ctx, seed):
+def test_2d_cover(ctx, seed, prec):
     X = synth.tiny_random(900, 6, seed, scale=3.0)
     eps = _eps(X, 4, seed)
-    res = run_gpu(ctx, X, (1, 0), (0, 0), (6, 5), (0.3, 0.2), eps, 4)
+    res = run_gpu(ctx, X, (1, 0), (0, 0), (6, 5), (0.3, 0.2), eps, 4, prec)
     assert_same_graph(X, res, (6, 5), (0.3, 0.2), eps, 4)
 
 
@@ -137,23 +145,30 @@ def test_pca_lens_basis_and_bits(ctx):
     assert_same_graph(X, res, (8, 6), (0.25, 0.25), eps, 5)
 
 
-def test_blobs_circle_5k_exact(ctx):
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_blobs_circle_5k_exact(ctx, prec):
     w = synth.blobs_circle_5k()
-    res = run_gpu(ctx, w.X, w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts)
+    res = run_gpu(ctx, w.X, w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, prec)
     ref = assert_same_graph(w.X, res, w.n_intervals, w.overlap, w.eps, w.min_pts)
     assert res["stats"]["near_ties"] == 0 and ref["near_ties"] == 0
     assert len(ref["node_elem"]) > 0
 
 
-def test_mixture_100k_d64_exact(ctx):
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_mixture_100k_d64_exact(ctx, prec):
     w = synth.mixture_100k()
-    res = run_gpu(ctx, w.X, w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts)
+    res = run_gpu(ctx, w.X, w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, prec)
     d = w.d
     omu, oV, _ = oracle.pca(w.X, 1)
     assert 1.0 - abs(res["pca"][d:2 * d] @ oV[0]) <= 1e-6
     ref = assert_same_graph(w.X, res, w.n_intervals, w.overlap, w.eps, w.min_pts)
     assert ref["near_ties"] == 0
     assert len(ref["node_elem"]) > 10 and len(ref["edges"]) > 0
+
+
+@functools.lru_cache(maxsize=1)
+def _clusters_1m():
+    return synth.clusters_1m_d256()
 
 
 def _check_graph_properties(res, n_points):
@@ -184,12 +199,13 @@ def _check_graph_properties(res, n_points):
 
 
 @pytest.mark.slow
-def test_clusters_1m_d256_sampled(ctx):
+@pytest.mark.parametrize("prec", [mg.BF16, mg.FP32])
+def test_clusters_1m_d256_sampled(ctx, prec):
     """Full-size 1M x 256 workload as the benchmark runs it: lens rows, the
     whole cover, and the DBSCAN of sampled elements against the oracle; the
     nerve by its definition."""
-    w = synth.clusters_1m_d256()
-    res = run_gpu(ctx, w.X, w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts)
+    w = _clusters_1m()
+    res = run_gpu(ctx, w.X, w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, prec)
     rng = np.random.default_rng(0)
     rows = rng.choice(w.n, 4000, replace=False)
     assert np.array_equal(res["lens"][rows, 0], oracle.lens_l2(w.X[rows]))
