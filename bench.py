@@ -173,8 +173,8 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    prec = mg.BF16 if args.precision == "bf16" else mg.FP32
-    w = synth.clusters_1m_d256()
+    prec = {"bf16": mg.BF16, "bf16x1": mg.BF16X1, "fp32": mg.FP32}[args.precision]
+    w = synth.clusters_1m_d256(args.n)
     Xh = torch.from_numpy(w.X).pin_memory()
     Xd = Xh.to(f"cuda:{local}")
     stream = torch.cuda.Stream()
@@ -255,7 +255,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": ms / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16+f64" if prec == mg.BF16 else "f32+f64",
+        "vs_baseline": None, "dtype": "f32+f64" if prec == mg.FP32 else "bf16+f64",
         "data": "synthetic",
         "config": {"workload": w.name, "n": w.n, "d": w.d, "lens": "L2",
                    "n_intervals": w.n_intervals[0], "overlap": w.overlap[0], "eps": w.eps,
@@ -300,10 +300,12 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "bf16x1", "fp32"])
     ap.add_argument("--ref-budget", type=float, default=12.0,
                     help="seconds of oracle DBSCAN per reference sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=1_000_000,
+                    help="points of the clustered cloud (smaller only for profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

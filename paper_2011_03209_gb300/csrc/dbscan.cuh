@@ -67,6 +67,14 @@ cudaError_t rows_to_slots(const int32_t* row_slot, const int32_t* row_pt, const 
                           int64_t* slot_label, uint8_t* slot_core, cudaStream_t s);
 cudaError_t element_offsets(const uint64_t* keys, int64_t M, int64_t E, int64_t* elem_off,
                             cudaStream_t s);
+// Splits a tile-pair list into pairs whose tiles are at most one apart and
+// the rest; counts[0], counts[1] receive the sizes.
+cudaError_t split_near_far(const int2* pairs, int64_t n, int2* near, int2* far,
+                           unsigned long long* counts, cudaStream_t s);
+// Keeps the union-pass tile pairs whose core rows do not all share one root
+// yet; counts[0] receives the size.
+cudaError_t filter_joined(const PassArgs& a, const int2* pairs, int64_t n, int2* out,
+                          unsigned long long* counts, cudaStream_t s);
 
 // --- nodes and nerve (k_nerve.cu)
 cudaError_t member_keys(const int32_t* lab, const int64_t* nid, const int64_t* mpos,
@@ -91,9 +99,9 @@ struct TileLayout {
     Buf row_pt;                  // [R] int32 point, INT32_MAX for padding
     Buf G;                       // [R x dp] FP32 rows
     Buf tile_n, tile_seg, tile_elem;      // [T] int32
-    Buf tile_cent;               // [T x dp] FP64 centroid
-    Buf tile_rad;                // [T] FP64 radius about the centroid (rounded up)
-    Buf seg_cent;                // [n_seg x dp] FP64 centroid of each segment
+    Buf tile_cent;               // [T x dp] FP32 centre
+    Buf tile_rad;                // [T] FP64 upper bound of the rows' distance to it
+    Buf seg_cent;                // [n_seg x dp] FP32 centre of each segment
     Buf seg_outlier;             // [n_seg] int32: 1 if the segment holds outliers
     Buf Ah, Al;                  // [R x dp] BF16 centred rows (hi and lo parts)
     Buf rn2, rn;                 // [R] FP32 |a|^2 and |a| (rounded up)

@@ -550,9 +550,76 @@ __global__ void elem_offsets_kernel(const uint64_t* __restrict__ keys, int64_t M
     elem_off[e] = l;
 }
 
+__global__ void split_near_far_kernel(const int2* __restrict__ pairs, int64_t n, int2* __restrict__ near,
+                                      int2* __restrict__ far, unsigned long long* __restrict__ counts)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int2 p = pairs[i];
+    const bool is_near = p.y - p.x <= 1;
+    const unsigned long long at = atomicAdd(&counts[is_near ? 0 : 1], 1ull);
+    (is_near ? near : far)[at] = p;
+}
+
+// One warp per tile pair: roots of all core rows, kept if they differ.
+__global__ void filter_joined_kernel(const PassArgs A, const int2* __restrict__ pairs, int64_t n,
+                                     int2* __restrict__ out, unsigned long long* __restrict__ counts)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = warp; q < n; q += nwarp) {
+        const int2 p = pairs[q];
+        const bool diag = p.x == p.y;
+        const int na = A.tile_n[p.x], nb = A.tile_n[p.y];
+        int lo = INT_MAX, hi = -1, nca = 0, ncb = 0;
+        for (int x = lane; x < 2 * kT; x += 32) {
+            const bool side_b = x >= kT;
+            const int i = side_b ? x - kT : x;
+            if (side_b ? (diag || i >= nb) : i >= na) continue;
+            const int64_t row = (int64_t)(side_b ? p.y : p.x) * kT + i;
+            if (!A.core[row]) continue;
+            const int r = gfind(A.parent, (int)row);
+            lo = min(lo, r);
+            hi = max(hi, r);
+            if (side_b) ++ncb; else ++nca;
+        }
+        for (int o = 16; o; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            nca += __shfl_xor_sync(0xffffffffu, nca, o);
+            ncb += __shfl_xor_sync(0xffffffffu, ncb, o);
+        }
+        const bool work = (diag ? nca >= 2 : (nca > 0 && ncb > 0)) && lo != hi;
+        if (lane == 0) {
+            if (work) out[atomicAdd(&counts[0], 1ull)] = p;
+            else if (hi >= 0) atomicAdd(&A.stats[kStatSkipped], 1ull);
+        }
+    }
+}
+
 inline unsigned grid_for(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, div_up(n, t)); }
 
 }  // namespace
+
+cudaError_t split_near_far(const int2* pairs, int64_t n, int2* near, int2* far,
+                           unsigned long long* counts, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    split_near_far_kernel<<<grid_for(n), 256, 0, s>>>(pairs, n, near, far, counts);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t filter_joined(const PassArgs& a, const int2* pairs, int64_t n, int2* out,
+                          unsigned long long* counts, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    filter_joined_kernel<<<(unsigned)std::min<int64_t>(div_up(n, 8), 152 * 32), 256, 0, s>>>(a, pairs, n, out,
+                                                                                           counts);
+    note_launch();
+    return cudaGetLastError();
+}
 
 // FP32 screen thresholds. The sum of d squared differences accumulated by
 // FMA in FP32 satisfies |s - d2| <= ((1+u)^2 (1+gamma_d) - 1) d2 + tiny

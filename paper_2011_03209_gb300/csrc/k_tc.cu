@@ -15,8 +15,9 @@
 // Kernel layout (one CTA per SM, persistent over a static share of the tile
 // pairs): warp 0 issues TMA loads of 64-column K blocks (128-byte swizzle)
 // into a ring of smem stages; warp 1 issues the MMAs into one of two TMEM
-// accumulators (128 x 128 FP32 each); warps 2-5 read the accumulator rows
-// with tcgen05.ld (one row per thread) and run the pass epilogue:
+// accumulators (128 x 128 FP32 each); warps 2-9 read the accumulator back
+// with tcgen05.ld (two warps per TMEM lane quadrant, each thread one row and
+// 64 columns) and run the pass epilogue, branch-free per pair:
 //   pass 1: neighbour counts of rows and columns (and neighbour lists),
 //   pass 2: unions of core-core neighbour pairs.
 // Every mbarrier wait is bounded in time; a wait that runs out sets an error
@@ -41,7 +42,7 @@ namespace {
 constexpr int kT = kTile;
 constexpr int kKB = 64;                       // BF16 columns per K block (128-byte rows)
 constexpr int kBlk = kT * kKB * 2;            // bytes of one 128 x 64 BF16 block
-constexpr int kThreads = 192;                 // producer, MMA, 4 epilogue warps
+constexpr int kThreads = 320;                 // producer, MMA, 8 epilogue warps
 constexpr unsigned long long kWaitNs = 4000000000ull;   // 4 s per wait at most
 
 struct TcParams {
@@ -165,15 +166,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
-// Barrier of the 128 epilogue threads that also ORs a flag over them, so all
+// Barrier of the 256 epilogue threads that also ORs a flag over them, so all
 // take the same branch afterwards.
 __device__ __forceinline__ bool epi_sync_or(bool v)
 {
     uint32_t r;
     asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}"
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 256, p;\n selp.u32 %0, 1, 0, q;\n}"
         : "=r"(r)
         : "r"((uint32_t)v)
         : "memory");
@@ -269,11 +270,12 @@ struct SmemTail {
     int abort;
     int consumed;                              // stage fills consumed by the MMA warp
     int s_mm[2];
-    float nb2[kT], nrb[kT];
+    uint32_t colcore[4];
+    float red[8];
+    __align__(16) float nbn[kT];               // -|b|^2 of the pair's columns
     uint32_t colmask[4][kT];
     int par[2 * kT];
     unsigned char core[2 * kT];
-    float red[8];
 };
 
 template <int NS, int MODE>
@@ -303,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&S.acc_full[i], 1);
-            mbar_init(&S.acc_empty[i], 4);
+            mbar_init(&S.acc_empty[i], 8);
         }
         mbar_init(&S.fin, 1);
         S.abort = 0;
@@ -396,8 +398,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
         }
     } else {
         // ---------------------------------------------------- epilogue
-        const int et = tid - 64;                              // 0..127
-        const int quad = warp & 3;                            // TMEM lane quadrant of this warp
+        // 8 warps: warp w reads TMEM lane quadrant (w & 3) = A rows
+        // 32(w & 3) .. +31, columns 64 h .. 64 h + 63 with h = (w - 2) / 4.
+        const int et = tid - 64;                              // 0..255
+        const int quad = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int r = quad * 32 + lane;                       // accumulator row = A-tile row
         int it = 0;
         for (int64_t q = blockIdx.x; q < P.n_pairs; q += gridDim.x, ++it) {
@@ -409,116 +414,168 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             const uint32_t acc_phase = (uint32_t)((it >> 1) & 1);
             const bool valid_r = r < na;
 
-            // column data of this pair; per-tile maxima for the row bounds
+            // column data of this pair; tile maxima for the row bounds
             epi_sync();
-            S.nb2[et] = P.rn2[sb + et];
-            S.nrb[et] = P.rn[sb + et];
+            if (et < kT) {
+                const float c2 = P.rn2[sb + et], c1 = P.rn[sb + et];
+                S.nbn[et] = -c2;
+                float m2 = c2, m1 = c1;
+                for (int o = 16; o; o >>= 1) {
+                    m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+                    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+                }
+                if (lane == 0) { S.red[et >> 5] = m2; S.red[4 + (et >> 5)] = m1; }
+                if (MODE == 2) {
+                    const bool cc = et < nb && A.core[sb + et];
+                    const uint32_t m = __ballot_sync(0xffffffffu, cc);
+                    if (lane == 0) S.colcore[et >> 5] = m;
+                }
+            }
             if (MODE == 2) {
-                S.core[et] = (et < na) && A.core[sa + et];
-                S.core[kT + et] = !diag && (et < nb) && A.core[sb + et];
+                const bool ca = et < kT ? (et < na && A.core[sa + et]) : (!diag && et - kT < nb && A.core[sb + et - kT]);
+                S.core[et] = ca;
                 S.par[et] = et;
-                S.par[kT + et] = kT + et;
                 if (et == 0) { S.s_mm[0] = INT_MAX; S.s_mm[1] = -1; }
             }
-            float m2 = S.nb2[et], m1 = S.nrb[et];
-            for (int o = 16; o; o >>= 1) {
-                m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
-                m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
-            }
-            if (lane == 0) { S.red[warp - 2] = m2; S.red[4 + warp - 2] = m1; }
             epi_sync();
             const float nb2max = fmaxf(fmaxf(S.red[0], S.red[1]), fmaxf(S.red[2], S.red[3]));
             const float nrbmax = fmaxf(fmaxf(S.red[4], S.red[5]), fmaxf(S.red[6], S.red[7]));
 
-            // union pass: skip pairs whose core rows already share one root
+            // union pass: nothing to do when the pair's core rows share one root
             bool work = true;
             if (MODE == 2) {
-                const bool ca = S.core[et], cbb = S.core[kT + et];
-                if (ca) { const int rr = gfind(A.parent, (int)(sa + et)); atomicMin(&S.s_mm[0], rr); atomicMax(&S.s_mm[1], rr); }
-                if (cbb) { const int rr = gfind(A.parent, (int)(sb + et)); atomicMin(&S.s_mm[0], rr); atomicMax(&S.s_mm[1], rr); }
+                if (S.core[et]) {
+                    const int rr = gfind(A.parent, (int)(et < kT ? sa + et : sb + et - kT));
+                    atomicMin(&S.s_mm[0], rr);
+                    atomicMax(&S.s_mm[1], rr);
+                }
                 epi_sync();
                 work = S.s_mm[1] >= 0 && S.s_mm[0] != S.s_mm[1];
                 if (!work && S.s_mm[1] >= 0 && et == 0) atomicAdd(&A.stats[kStatSkipped], 1ull);
             }
 
+            // u = fl(2 acc - |b|^2) against per-row limits: in iff u >= k_in,
+            // out iff u < k_out, else the pair is in the band
             const float na2 = P.rn2[sa + r], nra = P.rn[sa + r];
             const double E = P.A1 * (double)nra * (double)nrbmax + P.A2 * ((double)na2 + (double)nb2max) + P.A3;
-            const float thr_in = __double2float_rd(A.eps2 - E);
-            const float thr_out = __double2float_ru(A.eps2 + E);
-            const bool core_r = MODE == 2 ? (bool)S.core[r] : false;
+            const float k_in = __double2float_ru((double)na2 - A.eps2 + E);
+            const float k_out = __double2float_rd((double)na2 - A.eps2 - E);
+            const bool core_r = MODE == 2 && S.core[r];
 
-            // every epilogue warp reaches the barrier, then all leave together
             const bool bad = !mbar_wait(&S.acc_full[buf], acc_phase, abort) || *abort;
             if (epi_sync_or(bad)) break;
             tc_fence_after();
-            uint32_t rowbits[4] = {0u, 0u, 0u, 0u};
-#pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
+            uint32_t inb[2], band[2];
+#pragma unroll
+            for (int c2 = 0; c2 < 2; ++c2) {
+                const int c = half * 2 + c2;
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * kT + c * 32), v);
-                if (c == 3) {
+                if (c2 == 1) {
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&S.acc_empty[buf]);
                 }
-                uint32_t bits = 0u, mine = 0u;
+                uint32_t in_bits = 0u, keep_bits = 0u;
+                const float4* nbn4 = reinterpret_cast<const float4*>(S.nbn + c * 32);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int j = c * 32 + i;
-                    const float s = fmaf(-2.f, v[i], na2 + S.nb2[j]);
-                    bool in = s <= thr_in;
-                    bool cand = valid_r && j < nb;
-                    if (MODE == 2) cand = cand && work && core_r && S.core[diag ? j : kT + j];
-                    if (MODE == 2 && diag) cand = cand && j > r;
-                    if (cand && !in && s <= thr_out) {
-                        bool decided;
-                        uint32_t fl = MODE == 1 ? ((diag ? 0u : kQBoth) | ((!diag || r < j) ? kQTie : 0u)) : 0u;
-                        in = push_band(P, (int)(sa + r), (int)(sb + j), fl, &decided);
-                        if (!decided) in = false;             // decided later by the recheck kernel
-                    }
-                    in = in && cand;
-                    bits |= (uint32_t)in << i;
-                    if (MODE == 1 && !diag) {
-                        const uint32_t col = __ballot_sync(0xffffffffu, in);
-                        if (lane == i) mine = col;
+                for (int i4 = 0; i4 < 8; ++i4) {
+                    const float4 nn = nbn4[i4];
+                    const float n4[4] = {nn.x, nn.y, nn.z, nn.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int i = i4 * 4 + k;
+                        const float u = fmaf(2.f, v[i], n4[k]);
+                        if (u >= k_in) in_bits |= 1u << i;
+                        if (u >= k_out) keep_bits |= 1u << i;
                     }
                 }
-                rowbits[c] = bits;
-                if (MODE == 1 && !diag) S.colmask[quad][c * 32 + lane] = mine;
+                // candidate columns: valid (and core-core, upper triangle for unions)
+                const int left = nb - c * 32;
+                uint32_t cand = !valid_r ? 0u : (left >= 32 ? 0xffffffffu : (left > 0 ? (1u << left) - 1u : 0u));
+                if (MODE == 2) {
+                    cand = (work && core_r) ? cand & S.colcore[c] : 0u;
+                    if (diag) {
+                        const int lo = r + 1 - c * 32;                // columns j > r
+                        cand &= lo <= 0 ? 0xffffffffu : (lo >= 32 ? 0u : ~((1u << lo) - 1u));
+                    }
+                }
+                inb[c2] = in_bits & cand;
+                band[c2] = keep_bits & ~in_bits & cand;
+                if (MODE == 1 && !diag) {
+                    // 32 x 32 bit transpose across the warp: lane k gets column c*32+k
+                    uint32_t x = inb[c2];
+#pragma unroll
+                    for (int sft = 16; sft >= 1; sft >>= 1) {
+                        const uint32_t m = sft == 16 ? 0x0000FFFFu : sft == 8 ? 0x00FF00FFu : sft == 4 ? 0x0F0F0F0Fu
+                                                                   : sft == 2 ? 0x33333333u : 0x55555555u;
+                        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, sft);
+                        x = (lane & sft) ? (((y >> sft) & m) | (x & ~m)) : ((x & m) | ((y & m) << sft));
+                    }
+                    S.colmask[quad][c * 32 + lane] = x;
+                }
+            }
+
+            // band pairs: queued for the FP64 recheck (decided here if the queue is full)
+#pragma unroll
+            for (int c2 = 0; c2 < 2; ++c2) {
+                uint32_t b = band[c2];
+                while (b) {
+                    const int i = __ffs(b) - 1;
+                    b &= b - 1;
+                    const int j = (half * 2 + c2) * 32 + i;
+                    const uint32_t fl = MODE == 1 ? ((diag ? 0u : kQBoth) | ((!diag || r < j) ? kQTie : 0u)) : 0u;
+                    bool decided;
+                    const bool in = push_band(P, (int)(sa + r), (int)(sb + j), fl, &decided);
+                    if (decided && in) {
+                        if (MODE == 1) {
+                            int old = atomicAdd(&A.count[sa + r], 1);
+                            if (A.cap > 0 && old < A.cap) A.nbr[(sa + r) * A.cap + old] = (int32_t)(sb + j);
+                            if (!diag) {
+                                old = atomicAdd(&A.count[sb + j], 1);
+                                if (A.cap > 0 && old < A.cap) A.nbr[(sb + j) * A.cap + old] = (int32_t)(sa + r);
+                            }
+                        } else {
+                            gunion(A.parent, A.row_pt, (int)(sa + r), (int)(sb + j));
+                        }
+                    }
+                }
             }
 
             if (MODE == 1) {
-                const int k = __popc(rowbits[0]) + __popc(rowbits[1]) + __popc(rowbits[2]) + __popc(rowbits[3]);
+                const int k = __popc(inb[0]) + __popc(inb[1]);
                 if (k > 0) {
                     const int old = atomicAdd(&A.count[sa + r], k);
                     if (A.cap > 0 && old < A.cap) {
                         int pos = old;
-                        for (int c = 0; c < 4 && pos < A.cap; ++c) {
-                            uint32_t b = rowbits[c];
+                        for (int c2 = 0; c2 < 2 && pos < A.cap; ++c2) {
+                            uint32_t b = inb[c2];
                             while (b && pos < A.cap) {
                                 const int i = __ffs(b) - 1;
                                 b &= b - 1;
-                                A.nbr[(sa + r) * A.cap + pos++] = (int32_t)(sb + c * 32 + i);
+                                A.nbr[(sa + r) * A.cap + pos++] = (int32_t)(sb + (half * 2 + c2) * 32 + i);
                             }
                         }
                     }
                 }
                 if (!diag) {
                     epi_sync();
-                    const int j = et;
-                    int tot = 0;
+                    if (et < kT) {
+                        const int j = et;
+                        int tot = 0;
 #pragma unroll
-                    for (int w = 0; w < 4; ++w) tot += __popc(S.colmask[w][j]);
-                    if (tot > 0) {
-                        const int old = atomicAdd(&A.count[sb + j], tot);
-                        if (A.cap > 0 && old < A.cap) {
-                            int pos = old;
-                            for (int w = 0; w < 4 && pos < A.cap; ++w) {
-                                uint32_t b = S.colmask[w][j];
-                                while (b && pos < A.cap) {
-                                    const int i = __ffs(b) - 1;
-                                    b &= b - 1;
-                                    A.nbr[(sb + j) * A.cap + pos++] = (int32_t)(sa + w * 32 + i);
+                        for (int w = 0; w < 4; ++w) tot += __popc(S.colmask[w][j]);
+                        if (tot > 0) {
+                            const int old = atomicAdd(&A.count[sb + j], tot);
+                            if (A.cap > 0 && old < A.cap) {
+                                int pos = old;
+                                for (int w = 0; w < 4 && pos < A.cap; ++w) {
+                                    uint32_t b = S.colmask[w][j];
+                                    while (b && pos < A.cap) {
+                                        const int i = __ffs(b) - 1;
+                                        b &= b - 1;
+                                        A.nbr[(sb + j) * A.cap + pos++] = (int32_t)(sa + w * 32 + i);
+                                    }
                                 }
                             }
                         }
@@ -531,28 +588,25 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             } else {
                 // local unions over the pair's 256 rows, then global unions
                 if (work) {
-                    for (int c = 0; c < 4; ++c) {
-                        uint32_t b = rowbits[c];
+#pragma unroll
+                    for (int c2 = 0; c2 < 2; ++c2) {
+                        uint32_t b = inb[c2];
                         while (b) {
                             const int i = __ffs(b) - 1;
                             b &= b - 1;
-                            const int j = c * 32 + i;
+                            const int j = (half * 2 + c2) * 32 + i;
                             lunion(S.par, r, diag ? j : kT + j);
                         }
                     }
                 }
                 epi_sync();
-                if (work) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int x = h * kT + et;
-                        if (!S.core[x]) continue;
-                        const int rx = lfind(S.par, x);
-                        if (rx != x) {
-                            const int64_t row_x = x < kT ? sa + x : sb + (x - kT);
-                            const int64_t row_r = rx < kT ? sa + rx : sb + (rx - kT);
-                            gunion(A.parent, A.row_pt, (int)row_x, (int)row_r);
-                        }
+                if (work && S.core[et]) {
+                    const int x = et;
+                    const int rx = lfind(S.par, x);
+                    if (rx != x) {
+                        const int64_t row_x = x < kT ? sa + x : sb + (x - kT);
+                        const int64_t row_r = rx < kT ? sa + rx : sb + (rx - kT);
+                        gunion(A.parent, A.row_pt, (int)row_x, (int)row_r);
                     }
                 }
             }
@@ -643,26 +697,32 @@ cudaError_t launch(const CUtensorMap& mh, const CUtensorMap& ml, const TcParams&
 
 }  // namespace
 
-// Error bound of the screen value s = fl(fl(|a|^2 + |b|^2) - 2 acc) against
-// d^2 = |a|^2 + |b|^2 - 2 a.b for FP64-centred a, b, with u = 2^-8 (BF16):
-//   operand rounding  NS = 1: |hi(a).hi(b) - a.b| <= (2u + u^2) S|a||b|
-//                     NS = 3: a = hi + lo + r, |r| <= u^2 |a|, |lo| <= u |a|;
-//                             dropping lo.lo and r terms costs <= 3.01 u^2 S
-//   accumulation      m MMA steps of 16 exact products each, FP32 accumulator:
-//                     <= m 2^-22 (1 + 2u)^2 S (two units per step, allowing
-//                     truncation), S = sum |a_k||b_k| <= |a||b|
-//   norms and final   |a|^2, |b|^2 to nearest FP32, one add, one fma:
-//                     <= 2^-22 (|a|^2 + |b|^2) + 2^-23 2|acc|
-// The factor 2 of the cross term and a 1.25 margin are applied to A1. The
-// FP32 rounding of eps^2 and tiny subnormal terms go into A3.
+// Error bound of the screen value against d^2 = |a|^2 + |b|^2 - 2 a.b, where
+// a = x - c and b = y - c exactly (c: the segment's FP32 centre), with
+// u = 2^-8 (BF16) and v = 2^-24 (FP32):
+//   operand rounding  a32 = fl(x - c), hi = bf16(a32), lo = bf16(a32 - hi):
+//                     |a - hi| <= u'|a|, |a - hi - lo| <= rho |a| with
+//                     u' = u + 2v, rho = u^2 + 2v;
+//                     NS = 1: |hi.hi - a.b| <= (2u' + u'^2) S
+//                     NS = 3: dropping lo.lo and the residuals costs
+//                             <= (u'^2 + 2 rho + rho^2) S,  S = sum |a_k||b_k|
+//   accumulation      m MMA steps of 16 exact products each into the FP32
+//                     accumulator: <= m 2^-22 (1 + 2u')^2 S (two units per
+//                     step, allowing truncation); S <= |a||b|
+//   screen            u = fl(2 acc - |b|^2): <= v (2|acc| + |b|^2)
+//   norms             FP32 sums of d squares (lane partials and a shuffle
+//                     tree): <= (dp/32 + 16) v per norm, relative
+// A1 = 1.25 (2 (operand + accumulation) + 4v); A2 = 2 (dp/32 + 16) v + 4v;
+// A3 covers subnormal terms. |a| and |b| enter through upper bounds.
 void tc_bound(int ns, int dp, double eps2, double* A1, double* A2, double* A3)
 {
-    const double u = std::ldexp(1.0, -8);
+    const double u = std::ldexp(1.0, -8), v = std::ldexp(1.0, -24);
+    const double up = u + 2.0 * v, rho = u * u + 2.0 * v;
     const int steps = ns * ((dp + kKB - 1) / kKB) * (kKB / 16);
-    const double oper = ns == 1 ? (2.0 * u + u * u) : 3.01 * u * u;
-    const double accu = steps * std::ldexp(1.0, -22) * (1.0 + 2.0 * u) * (1.0 + 2.0 * u);
-    *A1 = 1.25 * (2.0 * (oper + accu) + 4.0 * std::ldexp(1.0, -23));
-    *A2 = 2.0 * std::ldexp(1.0, -22);
+    const double oper = ns == 1 ? (2.0 * up + up * up) : (up * up + 2.0 * rho + rho * rho);
+    const double accu = steps * std::ldexp(1.0, -22) * (1.0 + 2.0 * up) * (1.0 + 2.0 * up);
+    *A1 = 1.25 * (2.0 * (oper + accu) + 4.0 * v);
+    *A2 = 2.0 * (dp / 32 + 16) * v + 4.0 * v;
     *A3 = std::ldexp(1.0, -40) * eps2 + 1e-30;
 }
 

@@ -134,31 +134,41 @@ __global__ void __launch_bounds__(256, 2) assign_kernel(const float* __restrict_
     }
 }
 
-// Pivot groups: connected components of the pivots under |p - q| <= tau,
-// numbered 0.. in order of their smallest pivot. One CTA.
-__global__ void __launch_bounds__(1024) group_kernel(const float* __restrict__ Pv, int dp, int d, int K,
-                                                     float tau2, int32_t* __restrict__ gid,
-                                                     int32_t* __restrict__ n_groups)
+// Pivot adjacency: bit j of adj[i] set when |p_i - p_j| <= tau (FP32).
+// One warp per pivot pair i <= j.
+__global__ void pivot_adj_kernel(const float* __restrict__ Pv, int dp, int K, float tau2,
+                                 unsigned* __restrict__ adj)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t npairs = (int64_t)K * K;
+    for (int64_t e = warp; e < npairs; e += nwarp) {
+        const int i = (int)(e / K), j = (int)(e - (int64_t)i * K);
+        if (j < i) continue;
+        float s = 0.f;
+        for (int k = lane; k < dp; k += 32) {
+            const float t = Pv[(int64_t)i * dp + k] - Pv[(int64_t)j * dp + k];
+            s = fmaf(t, t, s);
+        }
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0 && s <= tau2) {
+            atomicOr(&adj[i * (kPiv / 32) + (j >> 5)], 1u << (j & 31));
+            atomicOr(&adj[j * (kPiv / 32) + (i >> 5)], 1u << (i & 31));
+        }
+    }
+}
+
+// Pivot groups: connected components of the adjacency, numbered 0.. in
+// order of their smallest pivot. One CTA.
+__global__ void __launch_bounds__(256) group_kernel(const unsigned* __restrict__ adj_g, int K,
+                                                    int32_t* __restrict__ gid, int32_t* __restrict__ n_groups)
 {
     __shared__ unsigned adj[kPiv][kPiv / 32];
     __shared__ int lab[kPiv];
     __shared__ int changed;
     const int tid = threadIdx.x;
-    for (int e = tid; e < kPiv * kPiv / 32; e += blockDim.x) (&adj[0][0])[e] = 0u;
-    __syncthreads();
-    for (int e = tid; e < K * K; e += blockDim.x) {
-        const int i = e / K, j = e - i * K;
-        if (j < i) continue;
-        float s = 0.f;
-        for (int k = 0; k < d; ++k) {
-            const float t = Pv[(int64_t)i * dp + k] - Pv[(int64_t)j * dp + k];
-            s = fmaf(t, t, s);
-        }
-        if (s <= tau2) {
-            atomicOr(&adj[i][j >> 5], 1u << (j & 31));
-            atomicOr(&adj[j][i >> 5], 1u << (i & 31));
-        }
-    }
+    for (int e = tid; e < kPiv * kPiv / 32; e += blockDim.x) (&adj[0][0])[e] = adj_g[e];
     if (tid < K) lab[tid] = tid;
     __syncthreads();
     for (int it = 0; it <= K; ++it) {
@@ -272,16 +282,20 @@ __global__ void tile_info_kernel(const int64_t* __restrict__ seg_start, const in
     }
 }
 
-// One CTA per tile: gather rows, FP64 centroid and radius.
+// One CTA per tile: gather rows, FP32 centroid (any centre serves the
+// sphere test) and a radius that bounds every row's distance to it: the FP32
+// sum of d squares of rounded differences is within (d/32 + 10) 2^-24 of the
+// exact one, so sqrt(sum) (1 + (d + 64) 2^-23), rounded up, is an upper bound.
 __global__ void __launch_bounds__(256) tile_prep_kernel(const float* __restrict__ X, int d, int64_t ld, int dp,
                                                         const int32_t* __restrict__ slot_point,
                                                         const int32_t* __restrict__ row_slot,
                                                         const int32_t* __restrict__ tile_n,
                                                         float* __restrict__ G, int32_t* __restrict__ row_pt,
-                                                        double* __restrict__ cent, double* __restrict__ rad,
+                                                        float* __restrict__ cent, double* __restrict__ rad,
                                                         int* nonfinite)
 {
-    __shared__ unsigned long long s_rad;
+    __shared__ float s_c[1024];
+    __shared__ unsigned s_rad;
     const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t row0 = (int64_t)t * kT;
     const int nt = tile_n[t];
@@ -300,75 +314,84 @@ __global__ void __launch_bounds__(256) tile_prep_kernel(const float* __restrict_
         }
         if (lane == 0) row_pt[row] = pt >= 0 ? (int32_t)pt : INT_MAX;
     }
-    if (tid == 0) s_rad = 0ull;
+    if (tid == 0) s_rad = 0u;
     if (__syncthreads_or(bad) && tid == 0) atomicOr(nonfinite, 1);
     for (int k = tid; k < dp; k += blockDim.x) {
-        double s = 0.0;
-        for (int r = 0; r < nt; ++r) s += (double)G[(row0 + r) * dp + k];
-        cent[(int64_t)t * dp + k] = s / (double)nt;
+        float s = 0.f;
+        for (int r = 0; r < nt; ++r) s += G[(row0 + r) * dp + k];
+        const float c = s / (float)nt;
+        cent[(int64_t)t * dp + k] = c;
+        if (k < 1024) s_c[k] = c;
     }
     __syncthreads();
+    const float infl = 1.0f + (float)(d + 64) * 1.1920929e-7f;
     for (int r = warp; r < nt; r += 8) {
         const int64_t row = row0 + r;
-        double s = 0.0;
+        float s = 0.f;
         for (int k = lane; k < d; k += 32) {
-            const double u = (double)G[row * dp + k] - cent[(int64_t)t * dp + k];
-            s += u * u;
+            const float c = k < 1024 ? s_c[k] : cent[(int64_t)t * dp + k];
+            const float u = G[row * dp + k] - c;
+            s = fmaf(u, u, s);
         }
         for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) atomicMax(&s_rad, (unsigned long long)__double_as_longlong(sqrt(s)));
+        if (lane == 0) atomicMax(&s_rad, __float_as_uint(__fmul_ru(__fsqrt_ru(s), infl)));
     }
     __syncthreads();
-    if (tid == 0) {
-        const double r = __longlong_as_double((long long)s_rad);
-        rad[t] = r * (1.0 + 1e-12) + 1e-300;
-    }
+    if (tid == 0) rad[t] = (double)__uint_as_float(s_rad);
 }
 
-__global__ void seg_cent_kernel(const double* __restrict__ cent, const int32_t* __restrict__ tile_n,
+__global__ void seg_cent_kernel(const float* __restrict__ cent, const int32_t* __restrict__ tile_n,
                                 const int64_t* __restrict__ seg_toff, int dp,
-                                double* __restrict__ seg_cent)
+                                float* __restrict__ seg_cent)
 {
     const int64_t g = blockIdx.x;
     for (int k = threadIdx.x; k < dp; k += blockDim.x) {
         double s = 0.0, w = 0.0;
         for (int64_t t = seg_toff[g]; t < seg_toff[g + 1]; ++t) {
-            s += cent[t * dp + k] * (double)tile_n[t];
+            s += (double)cent[t * dp + k] * (double)tile_n[t];
             w += (double)tile_n[t];
         }
-        seg_cent[g * dp + k] = s / w;
+        seg_cent[g * dp + k] = (float)(s / w);
     }
 }
 
-// BF16 operands: a = x - (segment centroid) in FP64, hi = bf16(a),
-// lo = bf16(a - hi); |a|^2 to nearest FP32 and |a| rounded up.
+// BF16 operands centred on the segment centre c (FP32): a = fl(x - c),
+// hi = bf16(a), lo = bf16(a - hi) (a - hi is exact in FP32); |a|^2 summed in
+// FP32 (lane partials, then a shuffle tree) and |a| rounded up.
 __global__ void __launch_bounds__(256) operand_kernel(const float* __restrict__ G, int d, int dp,
                                                       const int32_t* __restrict__ tile_n,
                                                       const int32_t* __restrict__ tile_seg,
-                                                      const double* __restrict__ seg_cent,
+                                                      const float* __restrict__ seg_cent,
                                                       __nv_bfloat16* __restrict__ Ah,
                                                       __nv_bfloat16* __restrict__ Al,
-                                                      float* __restrict__ rn2, float* __restrict__ rn)
+                                                      float* __restrict__ rn2, float* __restrict__ rn,
+                                                      float norm_infl)
 {
     const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nt = tile_n[t];
-    const double* c = seg_cent + (int64_t)tile_seg[t] * dp;
+    const float* c = seg_cent + (int64_t)tile_seg[t] * dp;
     for (int r = warp; r < kT; r += 8) {
         const int64_t row = (int64_t)t * kT + r;
-        double s = 0.0;
-        for (int k = lane; k < dp; k += 32) {
-            double a = 0.0;
-            if (r < nt && k < d) a = (double)G[row * dp + k] - c[k];
-            const __nv_bfloat16 h = __double2bfloat16(a);
-            const __nv_bfloat16 l = __double2bfloat16(a - (double)__bfloat162float(h));
-            Ah[row * dp + k] = h;
-            if (Al) Al[row * dp + k] = l;
-            s += a * a;
+        float s = 0.f;
+        for (int k = lane * 2; k < dp; k += 64) {
+            float a0 = 0.f, a1 = 0.f;
+            if (r < nt) {
+                const float2 x = *reinterpret_cast<const float2*>(G + row * dp + k);
+                if (k < d) a0 = x.x - c[k];
+                if (k + 1 < d) a1 = x.y - c[k + 1];
+            }
+            const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(a0 - hf.x, a1 - hf.y);
+            *reinterpret_cast<__nv_bfloat162*>(Ah + row * dp + k) = h;
+            if (Al) *reinterpret_cast<__nv_bfloat162*>(Al + row * dp + k) = l;
+            s = fmaf(a0, a0, s);
+            s = fmaf(a1, a1, s);
         }
         for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
-            rn2[row] = (float)s;
-            rn[row] = __double2float_ru(sqrt(s) * (1.0 + 1e-15));
+            rn2[row] = s;
+            rn[row] = __fmul_ru(__fsqrt_ru(s), norm_infl);
         }
     }
 }
@@ -394,61 +417,47 @@ __global__ void cand_count_kernel(const int64_t* __restrict__ etile_off, int64_t
     cnt[e] = T * (T + 1) / 2;
 }
 
-__device__ __forceinline__ int64_t upper_bound_i64(const int64_t* a, int64_t n, int64_t v)
+// One CTA per tile a: its centroid in shared memory, each warp takes tiles
+// b >= a of the same element. D = |c_a - c_b| in FP64 from FP32 centres.
+__global__ void __launch_bounds__(256) classify_kernel(const int64_t* __restrict__ etile_off,
+                                                       const int32_t* __restrict__ tile_elem,
+                                                       const float* __restrict__ cent,
+                                                       const double* __restrict__ rad,
+                                                       const int32_t* __restrict__ tile_seg,
+                                                       const int32_t* __restrict__ seg_out, int dp,
+                                                       double eps_out, double eps_in, int use_tc,
+                                                       int2* __restrict__ l_in, int2* __restrict__ l_tc,
+                                                       int2* __restrict__ l_simt,
+                                                       unsigned long long* __restrict__ counts)
 {
-    int64_t l = 0, r = n;
-    while (l < r) {
-        const int64_t m = (l + r) >> 1;
-        if (a[m] <= v) l = m + 1; else r = m;
-    }
-    return l;
-}
-
-// One warp per candidate tile pair. Candidates of an element are enumerated
-// by diagonal: (i, i) for all i, then (i, i+1), ..., so near-diagonal pairs
-// (tiles of one pivot region) come first.
-__global__ void classify_kernel(const int64_t* __restrict__ cand_off, const int64_t* __restrict__ etile_off,
-                                int64_t E, int64_t C, const double* __restrict__ cent,
-                                const double* __restrict__ rad, const int32_t* __restrict__ tile_seg,
-                                const int32_t* __restrict__ seg_out, int dp, double eps_out,
-                                double eps_in, int use_tc, int2* __restrict__ l_in,
-                                int2* __restrict__ l_tc, int2* __restrict__ l_simt,
-                                unsigned long long* __restrict__ counts)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t q = warp; q < C; q += nwarp) {
-        const int64_t e = upper_bound_i64(cand_off, E + 1, q) - 1;
-        const int64_t qq = q - cand_off[e];
-        const int64_t t0 = etile_off[e], T = etile_off[e + 1] - t0;
-        int64_t l = 0, r = T - 1;                // diagonal offset o: largest with cum(o) <= qq
-        while (l < r) {
-            const int64_t m = (l + r + 1) >> 1;
-            if (m * T - m * (m - 1) / 2 <= qq) l = m; else r = m - 1;
-        }
-        const int64_t o = l, i = qq - (o * T - o * (o - 1) / 2);
-        const int ta = (int)(t0 + i), tb = (int)(t0 + i + o);
+    extern __shared__ float s_ca[];
+    const int ta = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < dp; k += blockDim.x) s_ca[k] = cent[(int64_t)ta * dp + k];
+    __syncthreads();
+    const int64_t end = etile_off[tile_elem[ta] + 1];
+    const double ra = rad[ta];
+    const int sega = tile_seg[ta];
+    for (int64_t tb = ta + warp; tb < end; tb += 8) {
         double s = 0.0;
-        if (ta != tb)
+        if (tb != ta)
             for (int k = lane; k < dp; k += 32) {
-                const double u = cent[(int64_t)ta * dp + k] - cent[(int64_t)tb * dp + k];
-                s += u * u;
+                const double u = (double)s_ca[k] - (double)cent[tb * dp + k];
+                s = fma(u, u, s);
             }
         for (int w = 16; w; w >>= 1) s += __shfl_xor_sync(0xffffffffu, s, w);
         if (lane == 0) {
-            const double D = sqrt(s), ra = rad[ta], rb = rad[tb];
+            const double D = sqrt(s), rb = rad[tb];
             int cls;
             if (D - ra - rb > eps_out) cls = -1;
             else if (D + ra + rb < eps_in) cls = kListAllIn;
-            else if (use_tc && tile_seg[ta] == tile_seg[tb] && !seg_out[tile_seg[ta]]) cls = kListTC;
+            else if (use_tc && sega == tile_seg[tb] && !seg_out[sega]) cls = kListTC;
             else cls = kListSimt;
             if (cls < 0) {
                 atomicAdd(&counts[3], 1ull);
             } else {
                 const unsigned long long at = atomicAdd(&counts[cls], 1ull);
                 int2* dst = cls == kListAllIn ? l_in : (cls == kListTC ? l_tc : l_simt);
-                dst[at] = make_int2(ta, tb);
+                dst[at] = make_int2(ta, (int)tb);
             }
         }
     }
@@ -469,18 +478,22 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
         }                                                                             \
     } while (0)
     const int K = (int)std::min<int64_t>(kPiv, n);
-    Buf Pv, piv, pd2, gid, ngrp;
+    Buf Pv, piv, pd2, gid, ngrp, adj;
     TK(Pv.alloc(sizeof(float) * (size_t)K * dp, s));
     TK(piv.alloc(sizeof(int32_t) * n, s));
     TK(pd2.alloc(sizeof(float) * n, s));
     TK(gid.alloc(sizeof(int32_t) * kPiv, s));
     TK(ngrp.alloc(sizeof(int32_t), s));
+    TK(adj.alloc(sizeof(unsigned) * kPiv * (kPiv / 32), s));
+    TK(cudaMemsetAsync(adj.p, 0, sizeof(unsigned) * kPiv * (kPiv / 32), s));
     pivot_gather_kernel<<<K, 128, 0, s>>>(X, n, d, ld, dp, K, Pv.as<float>());
     assign_kernel<<<grid_for(n, kT), 256, 0, s>>>(X, n, d, ld, Pv.as<float>(), dp, K, piv.as<int32_t>(),
                                                  pd2.as<float>());
     const float tau2 = (float)(tau * tau);
-    group_kernel<<<1, 1024, 0, s>>>(Pv.as<float>(), dp, d, K, tau2, gid.as<int32_t>(), ngrp.as<int32_t>());
-    note_launch(3);
+    pivot_adj_kernel<<<grid_for((int64_t)K * K * 32, 256), 256, 0, s>>>(Pv.as<float>(), dp, K, tau2,
+                                                                       adj.as<unsigned>());
+    group_kernel<<<1, 256, 0, s>>>(adj.as<unsigned>(), K, gid.as<int32_t>(), ngrp.as<int32_t>());
+    note_launch(4);
     TK(cudaGetLastError());
 
     int ebits = bits_for(E), gbits = bits_for(K + 1), pbits = bits_for(K);
@@ -534,9 +547,9 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
     TK(L->tile_n.alloc(sizeof(int32_t) * T, s));
     TK(L->tile_seg.alloc(sizeof(int32_t) * T, s));
     TK(L->tile_elem.alloc(sizeof(int32_t) * T, s));
-    TK(L->tile_cent.alloc(sizeof(double) * (size_t)T * dp, s));
+    TK(L->tile_cent.alloc(sizeof(float) * (size_t)T * dp, s));
     TK(L->tile_rad.alloc(sizeof(double) * T, s));
-    TK(L->seg_cent.alloc(sizeof(double) * (size_t)nseg * dp, s));
+    TK(L->seg_cent.alloc(sizeof(float) * (size_t)nseg * dp, s));
     TK(cudaMemsetAsync(L->row_slot.p, 0xff, sizeof(int32_t) * R, s));
     row_map_kernel<<<grid_for(M), 256, 0, s>>>(keys.as<uint64_t>(), segpos.as<int64_t>(), seg_start.as<int64_t>(),
                                               seg_toff.as<int64_t>(), M, L->row_slot.as<int32_t>());
@@ -545,10 +558,10 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
                                                     L->tile_seg.as<int32_t>(), L->tile_elem.as<int32_t>());
     tile_prep_kernel<<<(unsigned)T, 256, 0, s>>>(X, d, ld, dp, slot_point, L->row_slot.as<int32_t>(),
                                                  L->tile_n.as<int32_t>(), L->G.as<float>(),
-                                                 L->row_pt.as<int32_t>(), L->tile_cent.as<double>(),
+                                                 L->row_pt.as<int32_t>(), L->tile_cent.as<float>(),
                                                  L->tile_rad.as<double>(), nonfinite);
-    seg_cent_kernel<<<(unsigned)nseg, 256, 0, s>>>(L->tile_cent.as<double>(), L->tile_n.as<int32_t>(),
-                                                  seg_toff.as<int64_t>(), dp, L->seg_cent.as<double>());
+    seg_cent_kernel<<<(unsigned)nseg, 256, 0, s>>>(L->tile_cent.as<float>(), L->tile_n.as<int32_t>(),
+                                                  seg_toff.as<int64_t>(), dp, L->seg_cent.as<float>());
     note_launch(4);
     TK(cudaGetLastError());
     if (bf16) {
@@ -556,10 +569,11 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
         TK(L->Al.alloc(sizeof(__nv_bfloat16) * (size_t)R * dp, s));
         TK(L->rn2.alloc(sizeof(float) * R, s));
         TK(L->rn.alloc(sizeof(float) * R, s));
+        const float norm_infl = 1.0f + (float)(dp / 32 + 16) * 5.9604645e-8f;
         operand_kernel<<<(unsigned)T, 256, 0, s>>>(L->G.as<float>(), d, dp, L->tile_n.as<int32_t>(),
-                                                   L->tile_seg.as<int32_t>(), L->seg_cent.as<double>(),
+                                                   L->tile_seg.as<int32_t>(), L->seg_cent.as<float>(),
                                                    L->Ah.as<__nv_bfloat16>(), L->Al.as<__nv_bfloat16>(),
-                                                   L->rn2.as<float>(), L->rn.as<float>());
+                                                   L->rn2.as<float>(), L->rn.as<float>(), norm_infl);
         note_launch();
         TK(cudaGetLastError());
     }
@@ -587,13 +601,15 @@ int classify_pairs(const TileLayout& L, int dp, int64_t E, double eps, bool use_
     for (int k = 0; k < kListCount; ++k) TK(P->list[k].alloc(sizeof(int2) * std::max<int64_t>(C, 1), s));
     if (C > 0) {
         const double eps_out = eps * (1.0 + 1e-9), eps_in = eps * (1.0 - 1e-9);
-        const unsigned blocks = (unsigned)std::min<int64_t>(div_up(C, 8), 152 * 64);
-        classify_kernel<<<blocks, 256, 0, s>>>(cand_off.as<int64_t>(), etile_off.as<int64_t>(), E, C,
-                                               L.tile_cent.as<double>(), L.tile_rad.as<double>(),
-                                               L.tile_seg.as<int32_t>(), L.seg_outlier.as<int32_t>(), dp,
-                                               eps_out, eps_in, use_tc ? 1 : 0, P->list[kListAllIn].as<int2>(),
-                                               P->list[kListTC].as<int2>(), P->list[kListSimt].as<int2>(),
-                                               counts.as<unsigned long long>());
+        const size_t smem = sizeof(float) * dp;
+        if (smem > 48 * 1024)
+            TK(cudaFuncSetAttribute(classify_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        classify_kernel<<<(unsigned)L.T, 256, smem, s>>>(etile_off.as<int64_t>(), L.tile_elem.as<int32_t>(),
+                                                         L.tile_cent.as<float>(), L.tile_rad.as<double>(),
+                                                         L.tile_seg.as<int32_t>(), L.seg_outlier.as<int32_t>(), dp,
+                                                         eps_out, eps_in, use_tc ? 1 : 0,
+                                                         P->list[kListAllIn].as<int2>(), P->list[kListTC].as<int2>(),
+                                                         P->list[kListSimt].as<int2>(), counts.as<unsigned long long>());
         note_launch();
         TK(cudaGetLastError());
     }
