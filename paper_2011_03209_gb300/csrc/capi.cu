@@ -385,36 +385,42 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     CK(core_flags(a.count, R, min_pts, core.as<uint8_t>(), a.parent, a.border, a.stats, s), "core");
     pt.mark();                                                    // 3
     CK(allin_pass(2, a_in, PL.n[kListAllIn], s), "pass 2 all-in");
-    if (use_tc && PL.n[kListTC] > 0) {
-        // unions in two rounds: pairs of tiles at most one apart join most
-        // of each group; the other pairs are then kept only if their core
-        // rows are not all joined yet
-        const int64_t ntc = PL.n[kListTC];
+    // Unions in two rounds: pairs of tiles at most one apart join most of
+    // each group; the other pairs are then kept only if their core rows are
+    // not all joined yet.
+    auto union_rounds = [&](const PassArgs& base, int64_t n, bool tc) -> int {
+        if (n == 0) return MAPPER_OK;
         Buf near, far, far2, cnt;
-        CK(near.alloc(sizeof(int2) * ntc, s), "alloc");
-        CK(far.alloc(sizeof(int2) * ntc, s), "alloc");
-        CK(far2.alloc(sizeof(int2) * ntc, s), "alloc");
+        CK(near.alloc(sizeof(int2) * n, s), "alloc");
+        CK(far.alloc(sizeof(int2) * n, s), "alloc");
+        CK(far2.alloc(sizeof(int2) * n, s), "alloc");
         CK(cnt.alloc(sizeof(unsigned long long) * 3, s), "alloc");
         CK(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * 3, s), "memset");
-        CK(split_near_far(a_tc.pairs, ntc, near.as<int2>(), far.as<int2>(), cnt.as<unsigned long long>(), s),
-           "split");
+        CK(split_near_far(base.pairs, n, near.as<int2>(), far.as<int2>(), cnt.as<unsigned long long>(), s), "split");
         unsigned long long hc[3] = {0, 0, 0};
         CK(cudaMemcpyAsync(hc, cnt.p, sizeof(hc), cudaMemcpyDeviceToHost, s), "copy");
         CK(cudaStreamSynchronize(s), "sync");
-        PassArgs a_near = a, a_far = a;
+        PassArgs a_near = base, a_far = base;
         a_near.pairs = near.as<int2>();
         a_far.pairs = far2.as<int2>();
-        if ((rc = tc_pass(2, a_near, t, (int64_t)hc[0], s))) return rc;
-        CK(filter_joined(a, far.as<int2>(), (int64_t)hc[1], far2.as<int2>(), cnt.as<unsigned long long>() + 2, s),
+        int r2;
+        if (tc) { if ((r2 = tc_pass(2, a_near, t, (int64_t)hc[0], s))) return r2; }
+        else CK(simt_pass(2, a_near, (int64_t)hc[0], s), "pass 2 near");
+        CK(filter_joined(base, far.as<int2>(), (int64_t)hc[1], far2.as<int2>(), cnt.as<unsigned long long>() + 2, s),
            "filter");
         CK(cudaMemcpyAsync(&hc[2], cnt.as<unsigned long long>() + 2, sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, s), "copy");
         CK(cudaStreamSynchronize(s), "sync");
-        if ((rc = tc_pass(2, a_far, t, (int64_t)hc[2], s))) return rc;
-    } else if (!use_tc) {
-        CK(simt_pass(2, a_tc, PL.n[kListTC], s), "pass 2 tc list");
+        if (tc) { if ((r2 = tc_pass(2, a_far, t, (int64_t)hc[2], s))) return r2; }
+        else CK(simt_pass(2, a_far, (int64_t)hc[2], s), "pass 2 far");
+        return MAPPER_OK;
+    };
+    if (use_tc) {
+        if ((rc = union_rounds(a_tc, PL.n[kListTC], true))) return rc;
+        CK(simt_pass(2, a_simt, PL.n[kListSimt], s), "pass 2");
+    } else {
+        if ((rc = union_rounds(a_simt, PL.n[kListSimt], false))) return rc;
     }
-    CK(simt_pass(2, a_simt, PL.n[kListSimt], s), "pass 2");
     pt.mark();                                                    // 4
     CK(flatten(a.parent, a.core, R, root.as<int32_t>(), s), "flatten");
     if (cap) {

@@ -103,6 +103,9 @@ struct TileLayout {
     Buf tile_rad;                // [T] FP64 upper bound of the rows' distance to it
     Buf seg_cent;                // [n_seg x dp] FP32 centre of each segment
     Buf seg_outlier;             // [n_seg] int32: 1 if the segment holds outliers
+    Buf seg_elem;                // [n_seg] int32 element of each segment
+    Buf seg_toff;                // [n_seg + 1] int64 first tile of each segment
+    Buf seg_rad;                 // [n_seg] FP64 upper bound of its rows' distance to its centre
     Buf Ah, Al;                  // [R x dp] BF16 centred rows (hi and lo parts)
     Buf rn2, rn;                 // [R] FP32 |a|^2 and |a| (rounded up)
 };

@@ -52,6 +52,8 @@ struct TcParams {
     int64_t n_pairs;
     int nkb;                                  // K blocks per row
     double A1, A2, A3;                        // bound constants
+    float A1f, A2f, A3f;                      // ... rounded up to FP32
+    float eps2_lo, eps2_hi;                   // eps^2 rounded down / up to FP32
     uint2* queue;                             // band pairs: (row a, row b | flags << 30)
     unsigned long long* queue_n;
     unsigned long long queue_cap;
@@ -264,18 +266,21 @@ __device__ __forceinline__ bool push_band(const TcParams& P, int ra, int rb, uin
 }
 
 // ------------------------------------------------------------------ kernel
+// Per-pair epilogue data is double-buffered (index: pair counter & 1): a
+// pair's buffer is written before the barrier that follows the accumulator
+// wait and read after it, so the next pair can be staged meanwhile.
 struct SmemTail {
     uint64_t full[4], empty[4], acc_full[2], acc_empty[2], fin;
     uint32_t tmem_base;
     int abort;
     int consumed;                              // stage fills consumed by the MMA warp
-    int s_mm[2];
-    uint32_t colcore[4];
-    float red[8];
-    __align__(16) float nbn[kT];               // -|b|^2 of the pair's columns
-    uint32_t colmask[4][kT];
-    int par[2 * kT];
-    unsigned char core[2 * kT];
+    int s_mm[2][2];                            // union pass: min / max root of the core rows
+    uint32_t colcore[2][4];                    // union pass: core columns, bit per column
+    float red[2][8];                           // max |b|^2 and |b| of the columns, per warp
+    __align__(16) float nbn[2][kT];            // -|b|^2 of the pair's columns
+    uint32_t colmask[4][kT];                   // count pass: neighbour bits per column
+    int par[2][2 * kT];                        // union pass: local union-find
+    unsigned char core[2][2 * kT];             // union pass: core flags of A rows, B rows
 };
 
 template <int NS, int MODE>
@@ -400,71 +405,96 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
         // ---------------------------------------------------- epilogue
         // 8 warps: warp w reads TMEM lane quadrant (w & 3) = A rows
         // 32(w & 3) .. +31, columns 64 h .. 64 h + 63 with h = (w - 2) / 4.
+        // Each pair's norms (and core flags) are loaded one pair ahead.
         const int et = tid - 64;                              // 0..255
         const int quad = warp & 3;
         const int half = (warp - 2) >> 2;
         const int r = quad * 32 + lane;                       // accumulator row = A-tile row
+        struct Pre {
+            int2 tp;
+            int na, nb;
+            float na2, nra;                                   // row r
+            float c2, c1;                                     // column et (et < 128)
+            bool core_et;                                     // union pass: row et of A | B
+        };
+        auto prefetch = [&](int64_t q, Pre& f) {
+            f.tp = A.pairs[q];
+            f.na = A.tile_n[f.tp.x];
+            f.nb = A.tile_n[f.tp.y];
+            const int64_t sa = (int64_t)f.tp.x * kT, sb = (int64_t)f.tp.y * kT;
+            f.na2 = P.rn2[sa + r];
+            f.nra = P.rn[sa + r];
+            if (et < kT) {
+                f.c2 = P.rn2[sb + et];
+                f.c1 = P.rn[sb + et];
+            }
+            if (MODE == 2) {
+                const bool diag = f.tp.x == f.tp.y;
+                f.core_et = et < kT ? (et < f.na && A.core[sa + et])
+                                    : (!diag && et - kT < f.nb && A.core[sb + et - kT]);
+            }
+        };
+        Pre cur{};
+        if ((int64_t)blockIdx.x < P.n_pairs) prefetch(blockIdx.x, cur);
         int it = 0;
         for (int64_t q = blockIdx.x; q < P.n_pairs; q += gridDim.x, ++it) {
-            const int2 tp = A.pairs[q];
+            const int2 tp = cur.tp;
             const bool diag = tp.x == tp.y;
-            const int na = A.tile_n[tp.x], nb = A.tile_n[tp.y];
+            const int na = cur.na, nb = cur.nb;
             const int64_t sa = (int64_t)tp.x * kT, sb = (int64_t)tp.y * kT;
             const int buf = it & 1;
             const uint32_t acc_phase = (uint32_t)((it >> 1) & 1);
             const bool valid_r = r < na;
+            const float na2 = cur.na2, nra = cur.nra;
 
-            // column data of this pair; tile maxima for the row bounds
-            epi_sync();
+            // (1) stage this pair's column data (and core rows, roots) in buffer `buf`
             if (et < kT) {
-                const float c2 = P.rn2[sb + et], c1 = P.rn[sb + et];
-                S.nbn[et] = -c2;
-                float m2 = c2, m1 = c1;
+                S.nbn[buf][et] = -cur.c2;
+                float m2 = cur.c2, m1 = cur.c1;
                 for (int o = 16; o; o >>= 1) {
                     m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
                     m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
                 }
-                if (lane == 0) { S.red[et >> 5] = m2; S.red[4 + (et >> 5)] = m1; }
-                if (MODE == 2) {
-                    const bool cc = et < nb && A.core[sb + et];
-                    const uint32_t m = __ballot_sync(0xffffffffu, cc);
-                    if (lane == 0) S.colcore[et >> 5] = m;
-                }
+                if (lane == 0) { S.red[buf][et >> 5] = m2; S.red[buf][4 + (et >> 5)] = m1; }
             }
             if (MODE == 2) {
-                const bool ca = et < kT ? (et < na && A.core[sa + et]) : (!diag && et - kT < nb && A.core[sb + et - kT]);
-                S.core[et] = ca;
-                S.par[et] = et;
-                if (et == 0) { S.s_mm[0] = INT_MAX; S.s_mm[1] = -1; }
+                const bool cc = cur.core_et;
+                S.core[buf][et] = cc;
+                S.par[buf][et] = et;
+                // column core bits: B rows (diagonal pair: A rows)
+                const bool colc = diag ? (et < kT && cc) : (et >= kT && cc);
+                const uint32_t m = __ballot_sync(0xffffffffu, colc);
+                if (lane == 0 && (diag ? et < kT : et >= kT)) S.colcore[buf][(et & (kT - 1)) >> 5] = m;
+                if (et == 0) { S.s_mm[buf][0] = INT_MAX; S.s_mm[buf][1] = -1; }
             }
-            epi_sync();
-            const float nb2max = fmaxf(fmaxf(S.red[0], S.red[1]), fmaxf(S.red[2], S.red[3]));
-            const float nrbmax = fmaxf(fmaxf(S.red[4], S.red[5]), fmaxf(S.red[6], S.red[7]));
-
-            // union pass: nothing to do when the pair's core rows share one root
-            bool work = true;
-            if (MODE == 2) {
-                if (S.core[et]) {
-                    const int rr = gfind(A.parent, (int)(et < kT ? sa + et : sb + et - kT));
-                    atomicMin(&S.s_mm[0], rr);
-                    atomicMax(&S.s_mm[1], rr);
-                }
-                epi_sync();
-                work = S.s_mm[1] >= 0 && S.s_mm[0] != S.s_mm[1];
-                if (!work && S.s_mm[1] >= 0 && et == 0) atomicAdd(&A.stats[kStatSkipped], 1ull);
+            if (MODE == 2) epi_sync();                          // s_mm initialised
+            if (MODE == 2 && cur.core_et) {
+                const int rr = gfind(A.parent, (int)(et < kT ? sa + et : sb + et - kT));
+                atomicMin(&S.s_mm[buf][0], rr);
+                atomicMax(&S.s_mm[buf][1], rr);
             }
 
-            // u = fl(2 acc - |b|^2) against per-row limits: in iff u >= k_in,
-            // out iff u < k_out, else the pair is in the band
-            const float na2 = P.rn2[sa + r], nra = P.rn[sa + r];
-            const double E = P.A1 * (double)nra * (double)nrbmax + P.A2 * ((double)na2 + (double)nb2max) + P.A3;
-            const float k_in = __double2float_ru((double)na2 - A.eps2 + E);
-            const float k_out = __double2float_rd((double)na2 - A.eps2 - E);
-            const bool core_r = MODE == 2 && S.core[r];
-
+            // (2) wait for the accumulator; the barrier also publishes (1)
             const bool bad = !mbar_wait(&S.acc_full[buf], acc_phase, abort) || *abort;
             if (epi_sync_or(bad)) break;
             tc_fence_after();
+            if (q + gridDim.x < P.n_pairs) prefetch(q + gridDim.x, cur);
+
+            // (3) per-row limits: in iff u >= k_in, out iff u < k_out, where
+            //     u = fl(2 acc - |b|^2); all FP32 with outward rounding
+            const float nb2max = fmaxf(fmaxf(S.red[buf][0], S.red[buf][1]), fmaxf(S.red[buf][2], S.red[buf][3]));
+            const float nrbmax = fmaxf(fmaxf(S.red[buf][4], S.red[buf][5]), fmaxf(S.red[buf][6], S.red[buf][7]));
+            const float E = __fmaf_ru(P.A1f, __fmul_ru(nra, nrbmax), __fmaf_ru(P.A2f, __fadd_ru(na2, nb2max), P.A3f));
+            const float k_in = __fadd_ru(__fsub_ru(na2, P.eps2_lo), E);
+            const float k_out = __fsub_rd(__fsub_rd(na2, P.eps2_hi), E);
+            bool work = true;
+            if (MODE == 2) {
+                work = S.s_mm[buf][1] >= 0 && S.s_mm[buf][0] != S.s_mm[buf][1];
+                if (!work && S.s_mm[buf][1] >= 0 && et == 0) atomicAdd(&A.stats[kStatSkipped], 1ull);
+            }
+            const bool core_r = MODE == 2 && S.core[buf][r];
+
+            // (4) accumulator rows -> neighbour bits
             uint32_t inb[2], band[2];
 #pragma unroll
             for (int c2 = 0; c2 < 2; ++c2) {
@@ -477,7 +507,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                     if (lane == 0) mbar_arrive(&S.acc_empty[buf]);
                 }
                 uint32_t in_bits = 0u, keep_bits = 0u;
-                const float4* nbn4 = reinterpret_cast<const float4*>(S.nbn + c * 32);
+                const float4* nbn4 = reinterpret_cast<const float4*>(S.nbn[buf] + c * 32);
 #pragma unroll
                 for (int i4 = 0; i4 < 8; ++i4) {
                     const float4 nn = nbn4[i4];
@@ -494,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 const int left = nb - c * 32;
                 uint32_t cand = !valid_r ? 0u : (left >= 32 ? 0xffffffffu : (left > 0 ? (1u << left) - 1u : 0u));
                 if (MODE == 2) {
-                    cand = (work && core_r) ? cand & S.colcore[c] : 0u;
+                    cand = (work && core_r) ? cand & S.colcore[buf][c] : 0u;
                     if (diag) {
                         const int lo = r + 1 - c * 32;                // columns j > r
                         cand &= lo <= 0 ? 0xffffffffu : (lo >= 32 ? 0u : ~((1u << lo) - 1u));
@@ -516,7 +546,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 }
             }
 
-            // band pairs: queued for the FP64 recheck (decided here if the queue is full)
+            // (5) band pairs: queued for the FP64 recheck (decided here if the queue is full)
 #pragma unroll
             for (int c2 = 0; c2 < 2; ++c2) {
                 uint32_t b = band[c2];
@@ -542,11 +572,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 }
             }
 
+            // (6) counts and lists, or unions
             if (MODE == 1) {
                 const int k = __popc(inb[0]) + __popc(inb[1]);
-                if (k > 0) {
+                if (k > A.cap) {
+                    atomicAdd(&A.count[sa + r], k);               // core for sure: no list needed
+                } else if (k > 0) {
                     const int old = atomicAdd(&A.count[sa + r], k);
-                    if (A.cap > 0 && old < A.cap) {
+                    if (old < A.cap) {
                         int pos = old;
                         for (int c2 = 0; c2 < 2 && pos < A.cap; ++c2) {
                             uint32_t b = inb[c2];
@@ -565,9 +598,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                         int tot = 0;
 #pragma unroll
                         for (int w = 0; w < 4; ++w) tot += __popc(S.colmask[w][j]);
-                        if (tot > 0) {
+                        if (tot > A.cap) {
+                            atomicAdd(&A.count[sb + j], tot);
+                        } else if (tot > 0) {
                             const int old = atomicAdd(&A.count[sb + j], tot);
-                            if (A.cap > 0 && old < A.cap) {
+                            if (old < A.cap) {
                                 int pos = old;
                                 for (int w = 0; w < 4 && pos < A.cap; ++w) {
                                     uint32_t b = S.colmask[w][j];
@@ -595,14 +630,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                             const int i = __ffs(b) - 1;
                             b &= b - 1;
                             const int j = (half * 2 + c2) * 32 + i;
-                            lunion(S.par, r, diag ? j : kT + j);
+                            lunion(S.par[buf], r, diag ? j : kT + j);
                         }
                     }
                 }
                 epi_sync();
-                if (work && S.core[et]) {
+                if (work && S.core[buf][et]) {
                     const int x = et;
-                    const int rx = lfind(S.par, x);
+                    const int rx = lfind(S.par[buf], x);
                     if (rx != x) {
                         const int64_t row_x = x < kT ? sa + x : sb + (x - kT);
                         const int64_t row_r = rx < kT ? sa + rx : sb + (rx - kT);
@@ -745,6 +780,13 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
     p.n_pairs = n_pairs;
     p.nkb = (a.dp + kKB - 1) / kKB;
     tc_bound(t.ns, a.dp, a.eps2, &p.A1, &p.A2, &p.A3);
+    p.A1f = std::nextafter((float)p.A1, INFINITY);
+    p.A2f = std::nextafter((float)p.A2, INFINITY);
+    p.A3f = std::nextafter((float)p.A3, INFINITY);
+    p.eps2_lo = (float)a.eps2;
+    if ((double)p.eps2_lo > a.eps2) p.eps2_lo = std::nextafter(p.eps2_lo, -INFINITY);
+    p.eps2_hi = (float)a.eps2;
+    if ((double)p.eps2_hi < a.eps2) p.eps2_hi = std::nextafter(p.eps2_hi, INFINITY);
     p.queue = t.queue;
     p.queue_n = t.queue_n;
     p.queue_cap = t.queue_cap;

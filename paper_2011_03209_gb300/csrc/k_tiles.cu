@@ -417,50 +417,134 @@ __global__ void cand_count_kernel(const int64_t* __restrict__ etile_off, int64_t
     cnt[e] = T * (T + 1) / 2;
 }
 
-// One CTA per tile a: its centroid in shared memory, each warp takes tiles
-// b >= a of the same element. D = |c_a - c_b| in FP64 from FP32 centres.
-__global__ void __launch_bounds__(256) classify_kernel(const int64_t* __restrict__ etile_off,
-                                                       const int32_t* __restrict__ tile_elem,
+// Upper bound of the distance between two centres from an FP32 sum of
+// squares s: the sum of d rounded squares of rounded differences (lane
+// partials, then a shuffle tree) is within (d/32 + 12) 2^-23 of the exact one.
+__device__ __forceinline__ float dist_sum32(const float* __restrict__ x, const float* __restrict__ y, int dp,
+                                            int lane)
+{
+    float s = 0.f;
+    for (int k = lane; k < dp; k += 32) {
+        const float u = x[k] - y[k];
+        s = fmaf(u, u, s);
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Segment radius: max over its tiles of |c_t - c_seg| + r_t (upper bounds).
+__global__ void __launch_bounds__(256) seg_rad_kernel(const float* __restrict__ cent,
+                                                      const double* __restrict__ rad,
+                                                      const float* __restrict__ seg_cent,
+                                                      const int64_t* __restrict__ seg_toff, int dp,
+                                                      double rel, double* __restrict__ seg_rad)
+{
+    __shared__ double s_max[8];
+    const int64_t g = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double m = 0.0;
+    for (int64_t t = seg_toff[g] + warp; t < seg_toff[g + 1]; t += 8) {
+        const float ssum = dist_sum32(cent + t * dp, seg_cent + g * dp, dp, lane);
+        m = fmax(m, sqrt((double)ssum * (1.0 + rel)) * (1.0 + 1e-15) + rad[t]);
+    }
+    if (lane == 0) s_max[warp] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = fmax(m, s_max[w]);
+        seg_rad[g] = m * (1.0 + 1e-15);
+    }
+}
+
+__global__ void elem_segs_kernel(const int32_t* __restrict__ seg_elem, int64_t nseg, int64_t E,
+                                 int64_t* __restrict__ eseg_off)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e > E) return;
+    int64_t l = 0, r = nseg;                   // first segment whose element >= e
+    while (l < r) {
+        const int64_t m = (l + r) >> 1;
+        if (seg_elem[m] < e) l = m + 1; else r = m;
+    }
+    eseg_off[e] = l;
+}
+
+// One CTA per tile a. Its centre is staged in shared memory; the segments of
+// its element that cannot hold a point within eps of the segment of a (by
+// segment spheres) are skipped whole; every tile b >= a of the others is
+// classified by tile spheres: out, all-in, or mixed (tensor-core list when
+// a and b share a non-outlier segment, else CUDA-core list).
+constexpr int kMaxSegList = 1024;
+
+__global__ void __launch_bounds__(256) classify_kernel(const int64_t* __restrict__ eseg_off,
+                                                       const int64_t* __restrict__ seg_toff,
+                                                       const int32_t* __restrict__ seg_elem,
+                                                       const float* __restrict__ seg_cent,
+                                                       const double* __restrict__ seg_rad,
                                                        const float* __restrict__ cent,
                                                        const double* __restrict__ rad,
                                                        const int32_t* __restrict__ tile_seg,
-                                                       const int32_t* __restrict__ seg_out, int dp,
+                                                       const int32_t* __restrict__ seg_out, int dp, double rel,
                                                        double eps_out, double eps_in, int use_tc,
                                                        int2* __restrict__ l_in, int2* __restrict__ l_tc,
                                                        int2* __restrict__ l_simt,
                                                        unsigned long long* __restrict__ counts)
 {
     extern __shared__ float s_ca[];
+    __shared__ int s_seg[kMaxSegList];
+    __shared__ int s_nseg;
+    __shared__ unsigned long long s_out;
     const int ta = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = threadIdx.x; k < dp; k += blockDim.x) s_ca[k] = cent[(int64_t)ta * dp + k];
+    const int ga = tile_seg[ta];
+    const int64_t g_end = eseg_off[seg_elem[ga] + 1];
+    if (threadIdx.x == 0) { s_nseg = 0; s_out = 0ull; }
     __syncthreads();
-    const int64_t end = etile_off[tile_elem[ta] + 1];
-    const double ra = rad[ta];
-    const int sega = tile_seg[ta];
-    for (int64_t tb = ta + warp; tb < end; tb += 8) {
-        double s = 0.0;
-        if (tb != ta)
-            for (int k = lane; k < dp; k += 32) {
-                const double u = (double)s_ca[k] - (double)cent[tb * dp + k];
-                s = fma(u, u, s);
-            }
-        for (int w = 16; w; w >>= 1) s += __shfl_xor_sync(0xffffffffu, s, w);
+    // surviving segments gb >= ga (the own segment always survives)
+    const bool listed = g_end - ga <= kMaxSegList;
+    for (int64_t gb = ga + warp; gb < g_end && listed; gb += 8) {
+        bool keep = gb == ga;
+        if (!keep) {
+            const float ssum = dist_sum32(seg_cent + (int64_t)ga * dp, seg_cent + gb * dp, dp, lane);
+            const double Dlo = sqrt((double)ssum * (1.0 - rel)) * (1.0 - 1e-15);
+            keep = !(Dlo - seg_rad[ga] - seg_rad[gb] > eps_out);
+        }
         if (lane == 0) {
-            const double D = sqrt(s), rb = rad[tb];
-            int cls;
-            if (D - ra - rb > eps_out) cls = -1;
-            else if (D + ra + rb < eps_in) cls = kListAllIn;
-            else if (use_tc && sega == tile_seg[tb] && !seg_out[sega]) cls = kListTC;
-            else cls = kListSimt;
-            if (cls < 0) {
-                atomicAdd(&counts[3], 1ull);
-            } else {
-                const unsigned long long at = atomicAdd(&counts[cls], 1ull);
-                int2* dst = cls == kListAllIn ? l_in : (cls == kListTC ? l_tc : l_simt);
-                dst[at] = make_int2(ta, (int)tb);
+            if (keep) s_seg[atomicAdd(&s_nseg, 1)] = (int)gb;
+            else atomicAdd(&s_out, (unsigned long long)(seg_toff[gb + 1] - seg_toff[gb]));
+        }
+    }
+    __syncthreads();
+    const int nlist = listed ? s_nseg : (int)(g_end - ga);
+    const double ra = rad[ta];
+    int64_t n_out = 0;
+    for (int li = 0; li < nlist; ++li) {
+        const int64_t gb = listed ? s_seg[li] : ga + li;
+        const int64_t t0 = gb == ga ? ta : seg_toff[gb], t1 = seg_toff[gb + 1];
+        for (int64_t tb = t0 + warp; tb < t1; tb += 8) {
+            float ssum = 0.f;
+            if (tb != ta) ssum = dist_sum32(s_ca, cent + tb * dp, dp, lane);
+            if (lane == 0) {
+                const double Dlo = sqrt((double)ssum * (1.0 - rel)) * (1.0 - 1e-15);
+                const double Dhi = sqrt((double)ssum * (1.0 + rel)) * (1.0 + 1e-15);
+                const double rb = rad[tb];
+                int cls;
+                if (Dlo - ra - rb > eps_out) cls = -1;
+                else if (Dhi + ra + rb < eps_in) cls = kListAllIn;
+                else if (use_tc && ga == tile_seg[tb] && !seg_out[ga]) cls = kListTC;
+                else cls = kListSimt;
+                if (cls < 0) {
+                    ++n_out;
+                } else {
+                    const unsigned long long at = atomicAdd(&counts[cls], 1ull);
+                    int2* dst = cls == kListAllIn ? l_in : (cls == kListTC ? l_tc : l_simt);
+                    dst[at] = make_int2(ta, (int)tb);
+                }
             }
         }
     }
+    if (lane == 0 && n_out) atomicAdd(&s_out, (unsigned long long)n_out);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_out) atomicAdd(&counts[3], s_out);
 }
 
 }  // namespace
@@ -521,7 +605,9 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
     L->n_seg = nseg;
     L->n_groups = gbits ? ng : 1;
 
-    Buf seg_start, seg_elem, seg_tiles, seg_toff;
+    Buf seg_start, seg_tiles;
+    Buf& seg_elem = L->seg_elem;
+    Buf& seg_toff = L->seg_toff;
     TK(seg_start.alloc(sizeof(int64_t) * (nseg + 1), s));
     TK(seg_elem.alloc(sizeof(int32_t) * nseg, s));
     TK(L->seg_outlier.alloc(sizeof(int32_t) * nseg, s));
@@ -564,6 +650,13 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
                                                   seg_toff.as<int64_t>(), dp, L->seg_cent.as<float>());
     note_launch(4);
     TK(cudaGetLastError());
+    TK(L->seg_rad.alloc(sizeof(double) * nseg, s));
+    const double rel = (double)(dp / 32 + 12) * std::ldexp(1.0, -23);
+    seg_rad_kernel<<<(unsigned)nseg, 256, 0, s>>>(L->tile_cent.as<float>(), L->tile_rad.as<double>(),
+                                                 L->seg_cent.as<float>(), seg_toff.as<int64_t>(), dp, rel,
+                                                 L->seg_rad.as<double>());
+    note_launch();
+    TK(cudaGetLastError());
     if (bf16) {
         TK(L->Ah.alloc(sizeof(__nv_bfloat16) * (size_t)R * dp, s));
         TK(L->Al.alloc(sizeof(__nv_bfloat16) * (size_t)R * dp, s));
@@ -583,15 +676,17 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
 int classify_pairs(const TileLayout& L, int dp, int64_t E, double eps, bool use_tc, PairLists* P,
                    cudaStream_t s)
 {
-    Buf etile_off, cnt, cand_off, counts;
+    Buf etile_off, cnt, cand_off, counts, eseg_off;
     TK(etile_off.alloc(sizeof(int64_t) * (E + 1), s));
+    TK(eseg_off.alloc(sizeof(int64_t) * (E + 1), s));
     TK(cnt.alloc(sizeof(int64_t) * std::max<int64_t>(E, 1), s));
     TK(cand_off.alloc(sizeof(int64_t) * (E + 1), s));
     TK(counts.alloc(sizeof(unsigned long long) * 4, s));
     TK(cudaMemsetAsync(counts.p, 0, sizeof(unsigned long long) * 4, s));
     elem_tiles_kernel<<<grid_for(E + 1), 256, 0, s>>>(L.tile_elem.as<int32_t>(), L.T, E, etile_off.as<int64_t>());
+    elem_segs_kernel<<<grid_for(E + 1), 256, 0, s>>>(L.seg_elem.as<int32_t>(), L.n_seg, E, eseg_off.as<int64_t>());
     cand_count_kernel<<<grid_for(E), 256, 0, s>>>(etile_off.as<int64_t>(), E, cnt.as<int64_t>());
-    note_launch(2);
+    note_launch(3);
     TK(cudaGetLastError());
     TK(exclusive_scan_i64(cnt.as<int64_t>(), cand_off.as<int64_t>(), E, s));
     int64_t C = 0;
@@ -601,15 +696,15 @@ int classify_pairs(const TileLayout& L, int dp, int64_t E, double eps, bool use_
     for (int k = 0; k < kListCount; ++k) TK(P->list[k].alloc(sizeof(int2) * std::max<int64_t>(C, 1), s));
     if (C > 0) {
         const double eps_out = eps * (1.0 + 1e-9), eps_in = eps * (1.0 - 1e-9);
+        const double rel = (double)(dp / 32 + 12) * std::ldexp(1.0, -23);
         const size_t smem = sizeof(float) * dp;
-        if (smem > 48 * 1024)
+        if (smem > 32 * 1024)
             TK(cudaFuncSetAttribute(classify_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        classify_kernel<<<(unsigned)L.T, 256, smem, s>>>(etile_off.as<int64_t>(), L.tile_elem.as<int32_t>(),
-                                                         L.tile_cent.as<float>(), L.tile_rad.as<double>(),
-                                                         L.tile_seg.as<int32_t>(), L.seg_outlier.as<int32_t>(), dp,
-                                                         eps_out, eps_in, use_tc ? 1 : 0,
-                                                         P->list[kListAllIn].as<int2>(), P->list[kListTC].as<int2>(),
-                                                         P->list[kListSimt].as<int2>(), counts.as<unsigned long long>());
+        classify_kernel<<<(unsigned)L.T, 256, smem, s>>>(
+            eseg_off.as<int64_t>(), L.seg_toff.as<int64_t>(), L.seg_elem.as<int32_t>(), L.seg_cent.as<float>(),
+            L.seg_rad.as<double>(), L.tile_cent.as<float>(), L.tile_rad.as<double>(), L.tile_seg.as<int32_t>(),
+            L.seg_outlier.as<int32_t>(), dp, rel, eps_out, eps_in, use_tc ? 1 : 0, P->list[kListAllIn].as<int2>(),
+            P->list[kListTC].as<int2>(), P->list[kListSimt].as<int2>(), counts.as<unsigned long long>());
         note_launch();
         TK(cudaGetLastError());
     }
