@@ -132,6 +132,10 @@ typedef struct mapper_stats {
     int64_t union_skipped;   /* union-pass tile pairs skipped: their cores already joined */
     int64_t n_groups;        /* pivot groups of the tile layout */
     int64_t n_rows;          /* rows of the tile layout (memberships + tile padding) */
+    int64_t count_kernel_pairs;  /* point pairs screened by the main count kernel: the
+                                    tensor-core one (BF16 precisions) or the CUDA-core
+                                    one (FP32) */
+    double ms_count_kernel;  /* device time of that kernel's launch (timing on) */
 } mapper_stats;
 
 /* ---------------------------------------------------------------- context */

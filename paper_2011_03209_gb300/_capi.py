@@ -79,6 +79,8 @@ class MapperStats(ctypes.Structure):
         ("union_skipped", ctypes.c_int64),
         ("n_groups", ctypes.c_int64),
         ("n_rows", ctypes.c_int64),
+        ("count_kernel_pairs", ctypes.c_int64),
+        ("ms_count_kernel", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:

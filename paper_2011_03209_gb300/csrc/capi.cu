@@ -378,9 +378,25 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
 
     pt.mark();                                                    // 1
     CK(allin_pass(1, a_in, PL.n[kListAllIn], s), "pass 1 all-in");
-    if (use_tc) { if ((rc = tc_pass(1, a_tc, t, PL.n[kListTC], s))) return rc; }
+    cudaEvent_t tev[2] = {nullptr, nullptr};
+    if (ctx->timing) {
+        CK(cudaEventCreate(&tev[0]), "event");
+        CK(cudaEventCreate(&tev[1]), "event");
+    }
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard() { for (int i = 0; i < 2; ++i) if (e[i]) cudaEventDestroy(e[i]); }
+    } tev_guard{tev};
+    if (use_tc) {
+        TcArgs t1 = t;
+        t1.ev_begin = tev[0];
+        t1.ev_end = tev[1];
+        if ((rc = tc_pass(1, a_tc, t1, PL.n[kListTC], s))) return rc;
+    }
     else CK(simt_pass(1, a_tc, PL.n[kListTC], s), "pass 1 tc list");
+    if (!use_tc && tev[0]) CK(cudaEventRecord(tev[0], s), "event");
     CK(simt_pass(1, a_simt, PL.n[kListSimt], s), "pass 1");
+    if (!use_tc && tev[1]) CK(cudaEventRecord(tev[1], s), "event");
     pt.mark();                                                    // 2
     CK(core_flags(a.count, R, min_pts, core.as<uint8_t>(), a.parent, a.border, a.stats, s), "core");
     pt.mark();                                                    // 3
@@ -455,6 +471,12 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     st.n_core = (int64_t)h_stats[kStatCore];
     st.union_skipped = (int64_t)h_stats[kStatSkipped];
     st.n_rows = R;
+    if (tev[0] && PL.n[use_tc ? kListTC : kListSimt] > 0) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, tev[0], tev[1]), "event time");
+        st.ms_count_kernel = ms;
+    }
+    st.count_kernel_pairs = (int64_t)h_stats[use_tc ? kStatTcPairs : kStatSimtPairs];
     if (pt.n >= 6) {
         st.ms_tiles = pt.ms(0, 1);
         st.ms_pass[0] = pt.ms(1, 2);

@@ -10,7 +10,7 @@ namespace mgb {
 constexpr int kTile = 128;          // rows per tile (one tcgen05 M block)
 
 enum : int { kStatBand = 0, kStatTies = 1, kStatScreened = 2, kStatCore = 3, kStatTileOut = 4,
-             kStatTileIn = 5, kStatSkipped = 6, kStatCount = 8 };
+             kStatTileIn = 5, kStatSkipped = 6, kStatTcPairs = 7, kStatSimtPairs = 8, kStatCount = 9 };
 
 // Work lists of tile pairs, classified by bounding spheres.
 enum : int { kListAllIn = 0, kListTC = 1, kListSimt = 2, kListCount = 3 };

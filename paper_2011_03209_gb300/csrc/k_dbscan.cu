@@ -355,6 +355,7 @@ __global__ void __launch_bounds__(256, 2) simt_pass_kernel(const PassArgs A)
         if (tid == 0) {
             const int64_t pairs = diag ? (int64_t)na * (na + 1) / 2 : (int64_t)na * nb;
             atomicAdd(&A.stats[kStatScreened], (unsigned long long)pairs);
+            atomicAdd(&A.stats[kStatSimtPairs], (unsigned long long)pairs);
         }
     } else if (MODE == 2) {
 #pragma unroll

@@ -47,7 +47,9 @@ __global__ void __launch_bounds__(kRows) lens_rows_kernel(const float* __restric
         for (int k = 0; k < kc; ++k) {
             const double x = (double)tile[tid][k];
             if (MODE == 0) {
-                acc = __dadd_rn(acc, __dmul_rn(x, x));
+                // x * x is exact in double (24-bit significands), so one
+                // fused rounding equals the separate multiply and add
+                acc = __fma_rn(x, x, acc);
             } else {
                 const double t = __dsub_rn(x, smu[k]);
                 acc = __dadd_rn(acc, __dmul_rn(t, sv[k]));

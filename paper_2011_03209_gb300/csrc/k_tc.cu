@@ -619,6 +619,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 if (et == 0) {
                     const int64_t pairs = diag ? (int64_t)na * (na + 1) / 2 : (int64_t)na * nb;
                     atomicAdd(&A.stats[kStatScreened], (unsigned long long)pairs);
+                    atomicAdd(&A.stats[kStatTcPairs], (unsigned long long)pairs);
                 }
             } else {
                 // local unions over the pair's 256 rows, then global unions
@@ -668,10 +669,33 @@ __global__ void recheck_kernel(const PassArgs A, const uint2* __restrict__ queue
         const uint2 e = queue[i];
         const int ra = (int)e.x, rb = (int)(e.y & 0x3FFFFFFFu);
         const uint32_t fl = e.y >> 30;
-        const double d2 = exact_sqdist(A.G + (int64_t)ra * A.dp, A.G + (int64_t)rb * A.dp, A.d);
+        // FP32 screen first (bounded as in fp32_thresholds), FP64 only in its band
+        const float4* xa = reinterpret_cast<const float4*>(A.G + (int64_t)ra * A.dp);
+        const float4* xb = reinterpret_cast<const float4*>(A.G + (int64_t)rb * A.dp);
+        float s32 = 0.f;
+        for (int k = 0; k < A.dp / 4; ++k) {
+            const float4 p = xa[k], q = xb[k];
+            float t = p.x - q.x;
+            s32 = fmaf(t, t, s32);
+            t = p.y - q.y;
+            s32 = fmaf(t, t, s32);
+            t = p.z - q.z;
+            s32 = fmaf(t, t, s32);
+            t = p.w - q.w;
+            s32 = fmaf(t, t, s32);
+        }
         atomicAdd(&A.stats[kStatBand], 1ull);
-        if (MODE == 1 && (fl & kQTie) && fabs(d2 - A.eps2) <= A.tie_thr) atomicAdd(&A.stats[kStatTies], 1ull);
-        if (!(d2 <= A.eps2)) continue;
+        bool in;
+        if (s32 <= A.lo_thr) {
+            in = true;
+        } else if (s32 > A.hi_thr) {
+            in = false;
+        } else {
+            const double d2 = exact_sqdist(A.G + (int64_t)ra * A.dp, A.G + (int64_t)rb * A.dp, A.d);
+            if (MODE == 1 && (fl & kQTie) && fabs(d2 - A.eps2) <= A.tie_thr) atomicAdd(&A.stats[kStatTies], 1ull);
+            in = d2 <= A.eps2;
+        }
+        if (!in) continue;
         if (MODE == 1) {
             int old = atomicAdd(&A.count[ra], 1);
             if (A.cap > 0 && old < A.cap) A.nbr[(int64_t)ra * A.cap + old] = rb;
@@ -794,10 +818,12 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
     cudaError_t e = cudaMemsetAsync(t.queue_n, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ECUDA; }
     const int grid = (int)std::min<int64_t>(n_pairs, t.num_sms);
+    if (t.ev_begin) cudaEventRecord(t.ev_begin, s);
     if (t.ns == 3)
         e = mode == 1 ? launch<3, 1>(mh, ml, p, grid, s) : launch<3, 2>(mh, ml, p, grid, s);
     else
         e = mode == 1 ? launch<1, 1>(mh, ml, p, grid, s) : launch<1, 2>(mh, ml, p, grid, s);
+    if (t.ev_end) cudaEventRecord(t.ev_end, s);
     note_launch();
     if (e != cudaSuccess) {
         set_error(std::string("tensor-core pass: ") + cudaGetErrorString(e));

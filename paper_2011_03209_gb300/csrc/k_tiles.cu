@@ -472,7 +472,7 @@ __global__ void elem_segs_kernel(const int32_t* __restrict__ seg_elem, int64_t n
 // its element that cannot hold a point within eps of the segment of a (by
 // segment spheres) are skipped whole; every tile b >= a of the others is
 // classified by tile spheres: out, all-in, or mixed (tensor-core list when
-// a and b share a non-outlier segment, else CUDA-core list).
+// a and b share a segment, hence a centre, else CUDA-core list).
 constexpr int kMaxSegList = 1024;
 
 __global__ void __launch_bounds__(256) classify_kernel(const int64_t* __restrict__ eseg_off,
@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(256) classify_kernel(const int64_t* __restrict
                 int cls;
                 if (Dlo - ra - rb > eps_out) cls = -1;
                 else if (Dhi + ra + rb < eps_in) cls = kListAllIn;
-                else if (use_tc && ga == tile_seg[tb] && !seg_out[ga]) cls = kListTC;
+                else if (use_tc && ga == tile_seg[tb]) cls = kListTC;
                 else cls = kListSimt;
                 if (cls < 0) {
                     ++n_out;

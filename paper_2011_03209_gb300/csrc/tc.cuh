@@ -20,6 +20,7 @@ struct TcArgs {
     unsigned long long* queue_n;     // entries pushed (may exceed queue_cap)
     unsigned long long queue_cap;
     int* err;                        // set to 1 if a bounded wait ran out
+    cudaEvent_t ev_begin, ev_end;    // if set: recorded around the tensor-core kernel
 };
 
 // Pass `mode` (1 = counts and neighbour lists, 2 = unions) over the tile
