@@ -311,7 +311,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     pt.mark();                                                    // 0
     TileLayout L;
     int rc = build_tiles(X, n, d, ld, dp, cov->slot_point.as<int32_t>(), cov->slot_elem.as<int32_t>(), M, E,
-                         4.0 * eps, use_tc, &L, nf, s);
+                         4.0 * eps, use_tc, ctx->num_sms, &L, nf, s);
     if (rc) return rc;
     PairLists PL;
     if ((rc = classify_pairs(L, dp, E, eps, use_tc, &PL, s))) return rc;

@@ -118,9 +118,10 @@ struct PairLists {
 
 // Orders every element's points by pivot group, lays them out in tiles
 // (a tile never mixes groups) and gathers rows. tau: distance under which two
-// pivots join a group and beyond which a point is an outlier.
+// pivots join a group and beyond which a point is an outlier. bf16: also
+// build the tensor-core operands (and assign pivots on tensor cores).
 int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const int32_t* slot_point,
-                const int32_t* slot_elem, int64_t M, int64_t E, double tau, bool bf16,
+                const int32_t* slot_elem, int64_t M, int64_t E, double tau, bool bf16, int num_sms,
                 TileLayout* L, int* nonfinite, cudaStream_t s);
 // Classifies every tile pair of every element by bounding spheres: out (no
 // pair within eps), all-in, or mixed (to the tensor-core list when both tiles

@@ -657,6 +657,202 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kT));
 }
 
+// ------------------------------------------------ nearest pivot (layout)
+// Point tiles (128 rows) against all pivots (up to 256) in one MMA of
+// N = 256: rows and pivots centred on the pivots' mean c and split into BF16
+// hi + lo (three products), so |x - p|^2 = |x - c|^2 + |p - c|^2 - 2 acc
+// with error ~2^-13 |x - c||p - c|. The nearest pivot only orders points
+// for the tile layout; no decision of the method depends on it.
+constexpr int kPivN = 256;
+constexpr int kAsgStages = 2;
+constexpr int kAsgStageBytes = 2 * kBlk + 2 * (kPivN * kKB * 2);    // x hi, lo; pivots hi, lo
+
+struct AssignParams {
+    int64_t n, n_tiles;
+    int nkb;
+    const float* xn2;                         // |x - c|^2 per point
+    const float* pn2;                         // |p - c|^2 per pivot, +inf past the last
+    int32_t* piv;
+    float* pd2;
+    int* err;
+};
+
+struct AsgTail {
+    uint64_t full[kAsgStages], empty[kAsgStages], acc_full[2], acc_empty[2], fin;
+    uint32_t tmem_base;
+    int abort;
+    float pn2[kPivN];
+};
+
+// kind::f16, BF16 in, F32 out, K-major, M = 128, N = 256
+constexpr uint32_t kIdescN256 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kPivN >> 3) << 17) |
+                                ((uint32_t)(kT >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16_n256(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+            tmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdescN256), "r"(acc));
+}
+
+__global__ void __launch_bounds__(192, 1) assign_tc_kernel(const __grid_constant__ CUtensorMap mXh,
+                                                           const __grid_constant__ CUtensorMap mXl,
+                                                           const __grid_constant__ CUtensorMap mPh,
+                                                           const __grid_constant__ CUtensorMap mPl,
+                                                           const AssignParams P)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    AsgTail& S = *reinterpret_cast<AsgTail*>(smem + kAsgStages * kAsgStageBytes);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    volatile int* abort = &S.abort;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&S.tmem_base)),
+                     "r"(2 * kPivN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 32) {
+        for (int i = 0; i < kAsgStages; ++i) {
+            mbar_init(&S.full[i], 1);
+            mbar_init(&S.empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&S.acc_full[i], 1);
+            mbar_init(&S.acc_empty[i], 4);
+        }
+        mbar_init(&S.fin, 1);
+        S.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int j = tid; j < kPivN; j += blockDim.x) S.pn2[j] = P.pn2[j];
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            for (int64_t t = blockIdx.x; t < P.n_tiles && !*abort; t += gridDim.x) {
+                for (int kb = 0; kb < P.nkb; ++kb) {
+                    if (!mbar_wait(&S.empty[stage], phase ^ 1, abort)) break;
+                    unsigned char* st = smem + stage * kAsgStageBytes;
+                    mbar_expect_tx(&S.full[stage], (uint32_t)kAsgStageBytes);
+                    tma_load(st, &mXh, kb * kKB, (int)(t * kT), &S.full[stage]);
+                    tma_load(st + kBlk, &mXl, kb * kKB, (int)(t * kT), &S.full[stage]);
+                    tma_load(st + 2 * kBlk, &mPh, kb * kKB, 0, &S.full[stage]);
+                    tma_load(st + 2 * kBlk + kPivN * kKB * 2, &mPl, kb * kKB, 0, &S.full[stage]);
+                    if (++stage == kAsgStages) { stage = 0; phase ^= 1; }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int it = 0;
+            for (int64_t t = blockIdx.x; t < P.n_tiles && !*abort; t += gridDim.x, ++it) {
+                const int buf = it & 1;
+                if (!mbar_wait(&S.acc_empty[buf], (uint32_t)(((it >> 1) & 1) ^ 1), abort)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(buf * kPivN);
+                bool ok = true;
+                for (int kb = 0; kb < P.nkb; ++kb) {
+                    if (!mbar_wait(&S.full[stage], phase, abort)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t base = su32(smem + stage * kAsgStageBytes);
+                    const uint32_t xh = base, xl = base + kBlk, ph = base + 2 * kBlk, pl = ph + kPivN * kKB * 2;
+#pragma unroll
+                    for (int j = 0; j < kKB / 16; ++j) {
+                        mma_bf16_n256(d_tmem, smem_desc(xh + 32 * j), smem_desc(ph + 32 * j), (kb | j) ? 1u : 0u);
+                        mma_bf16_n256(d_tmem, smem_desc(xh + 32 * j), smem_desc(pl + 32 * j), 1u);
+                        mma_bf16_n256(d_tmem, smem_desc(xl + 32 * j), smem_desc(ph + 32 * j), 1u);
+                    }
+                    mma_commit(&S.empty[stage]);
+                    if (++stage == kAsgStages) { stage = 0; phase ^= 1; }
+                }
+                if (!ok) break;
+                mma_commit(&S.acc_full[buf]);
+            }
+            mma_commit(&S.fin);
+            volatile int dummy = 0;
+            mbar_wait(&S.fin, 0, &dummy);
+        }
+    } else {
+        const int quad = warp & 3;
+        const int r = quad * 32 + lane;
+        int it = 0;
+        for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, ++it) {
+            const int buf = it & 1;
+            const bool bad = !mbar_wait(&S.acc_full[buf], (uint32_t)((it >> 1) & 1), abort) || *abort;
+            if (__any_sync(0xffffffffu, bad)) break;
+            tc_fence_after();
+            float best = INFINITY;
+            int bidx = 0;
+#pragma unroll 1
+            for (int c = 0; c < kPivN / 32; ++c) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * kPivN + c * 32), v);
+                if (c == kPivN / 32 - 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&S.acc_empty[buf]);
+                }
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const float val = fmaf(-2.f, v[i], S.pn2[c * 32 + i]);
+                    if (val < best) { best = val; bidx = c * 32 + i; }
+                }
+            }
+            const int64_t p = t * kT + r;
+            if (p < P.n) {
+                P.piv[p] = bidx;
+                P.pd2[p] = fmaxf(0.f, P.xn2[p] + best);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0 && S.abort) atomicExch(P.err, 1);
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kPivN));
+}
+
+// Rows of `src` (n rows, stride ld, d values) minus c, split into BF16 hi
+// and lo (rows_out rows of pitch dp, zero padded) with |row - c|^2 in FP32.
+__global__ void split_rows_kernel(const float* __restrict__ src, int64_t n, int d, int64_t ld, int dp,
+                                  const float* __restrict__ c, int64_t rows_out, __nv_bfloat16* __restrict__ hi,
+                                  __nv_bfloat16* __restrict__ lo, float* __restrict__ n2, float pad_n2)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp; r < rows_out; r += nwarp) {
+        float s = 0.f;
+        for (int k = lane; k < dp; k += 32) {
+            float a = 0.f;
+            if (r < n && k < d) a = src[r * ld + k] - c[k];
+            const __nv_bfloat16 h = __float2bfloat16_rn(a);
+            hi[r * dp + k] = h;
+            lo[r * dp + k] = __float2bfloat16_rn(a - __bfloat162float(h));
+            s = fmaf(a, a, s);
+        }
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0 && n2) n2[r] = r < n ? s : pad_n2;
+    }
+}
+
+__global__ void mean_rows_kernel(const float* __restrict__ rows, int K, int dp, float* __restrict__ c)
+{
+    for (int k = threadIdx.x; k < dp; k += blockDim.x) {
+        float s = 0.f;
+        for (int i = 0; i < K; ++i) s += rows[(int64_t)i * dp + k];
+        c[k] = s / (float)K;
+    }
+}
+
 // Band pairs queued by the epilogues, re-decided in FP64 (k ascending, one
 // rounding per operation: the defining expression).
 template <int MODE>
@@ -725,13 +921,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder()
     return fn;
 }
 
-bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int dp)
+bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int dp, int box_rows = kT)
 {
     auto enc = encoder();
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)dp, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)dp * 2};
-    cuuint32_t box[2] = {kKB, kT};
+    cuuint32_t box[2] = {kKB, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -755,6 +951,64 @@ cudaError_t launch(const CUtensorMap& mh, const CUtensorMap& ml, const TcParams&
 }
 
 }  // namespace
+
+int assign_pivots_tc(const float* X, int64_t n, int d, int64_t ld, int dp, const float* Pv, int K,
+                     int num_sms, int32_t* piv, float* pd2, cudaStream_t s)
+{
+    if (K > kPivN) { set_error("assign_pivots_tc: more than 256 pivots"); return MAPPER_EINVAL; }
+    const int64_t n_tiles = (n + kT - 1) / kT, rows = n_tiles * kT;
+    Buf c, xh, xl, xn2, ph, pl, pn2, err;
+#define AK(expr)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            set_error(std::string("assign_pivots_tc: ") + cudaGetErrorString(e_));       \
+            return e_ == cudaErrorMemoryAllocation ? MAPPER_ENOMEM : MAPPER_ECUDA;       \
+        }                                                                                \
+    } while (0)
+    AK(c.alloc(sizeof(float) * dp, s));
+    AK(xh.alloc(sizeof(__nv_bfloat16) * (size_t)rows * dp, s));
+    AK(xl.alloc(sizeof(__nv_bfloat16) * (size_t)rows * dp, s));
+    AK(xn2.alloc(sizeof(float) * rows, s));
+    AK(ph.alloc(sizeof(__nv_bfloat16) * (size_t)kPivN * dp, s));
+    AK(pl.alloc(sizeof(__nv_bfloat16) * (size_t)kPivN * dp, s));
+    AK(pn2.alloc(sizeof(float) * kPivN, s));
+    AK(err.alloc(sizeof(int), s));
+    AK(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    mean_rows_kernel<<<1, 256, 0, s>>>(Pv, K, dp, c.as<float>());
+    split_rows_kernel<<<num_sms * 8, 256, 0, s>>>(X, n, d, ld, dp, c.as<float>(), rows, xh.as<__nv_bfloat16>(),
+                                                  xl.as<__nv_bfloat16>(), xn2.as<float>(), 0.f);
+    split_rows_kernel<<<8, 256, 0, s>>>(Pv, K, d, dp, dp, c.as<float>(), kPivN, ph.as<__nv_bfloat16>(),
+                                        pl.as<__nv_bfloat16>(), pn2.as<float>(), INFINITY);
+    note_launch(3);
+    AK(cudaGetLastError());
+    CUtensorMap mxh, mxl, mph, mpl;
+    if (!make_map(&mxh, xh.p, rows, dp) || !make_map(&mxl, xl.p, rows, dp) ||
+        !make_map(&mph, ph.p, kPivN, dp, kPivN) || !make_map(&mpl, pl.p, kPivN, dp, kPivN)) {
+        set_error("cuTensorMapEncodeTiled failed (or is unavailable)");
+        return MAPPER_ECUDA;
+    }
+    AssignParams p{};
+    p.n = n;
+    p.n_tiles = n_tiles;
+    p.nkb = (dp + kKB - 1) / kKB;
+    p.xn2 = xn2.as<float>();
+    p.pn2 = pn2.as<float>();
+    p.piv = piv;
+    p.pd2 = pd2;
+    p.err = err.as<int>();
+    const int smem = kAsgStages * kAsgStageBytes + (int)sizeof(AsgTail) + 1024;
+    AK(cudaFuncSetAttribute(assign_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    assign_tc_kernel<<<(int)std::min<int64_t>(n_tiles, num_sms), 192, smem, s>>>(mxh, mxl, mph, mpl, p);
+    note_launch();
+    AK(cudaGetLastError());
+    int h_err = 0;
+    AK(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AK(cudaStreamSynchronize(s));
+#undef AK
+    if (h_err) { set_error("pivot assignment gave up waiting on a barrier"); return MAPPER_ETIMEOUT; }
+    return MAPPER_OK;
+}
 
 // Error bound of the screen value against d^2 = |a|^2 + |b|^2 - 2 a.b, where
 // a = x - c and b = y - c exactly (c: the segment's FP32 centre), with

@@ -24,7 +24,7 @@
 #include <vector>
 
 #include "../../include/mapper.h"
-#include "dbscan.cuh"
+#include "tc.cuh"
 
 namespace mgb {
 
@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(256) classify_kernel(const int64_t* __restrict
 }  // namespace
 
 int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const int32_t* slot_point,
-                const int32_t* slot_elem, int64_t M, int64_t E, double tau, bool bf16,
+                const int32_t* slot_elem, int64_t M, int64_t E, double tau, bool bf16, int num_sms,
                 TileLayout* L, int* nonfinite, cudaStream_t s)
 {
 #define TK(expr)                                                                      \
@@ -571,13 +571,21 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
     TK(adj.alloc(sizeof(unsigned) * kPiv * (kPiv / 32), s));
     TK(cudaMemsetAsync(adj.p, 0, sizeof(unsigned) * kPiv * (kPiv / 32), s));
     pivot_gather_kernel<<<K, 128, 0, s>>>(X, n, d, ld, dp, K, Pv.as<float>());
-    assign_kernel<<<grid_for(n, kT), 256, 0, s>>>(X, n, d, ld, Pv.as<float>(), dp, K, piv.as<int32_t>(),
-                                                 pd2.as<float>());
+    note_launch();
+    if (bf16) {
+        const int rc = assign_pivots_tc(X, n, d, ld, dp, Pv.as<float>(), K, num_sms, piv.as<int32_t>(),
+                                        pd2.as<float>(), s);
+        if (rc) return rc;
+    } else {
+        assign_kernel<<<grid_for(n, kT), 256, 0, s>>>(X, n, d, ld, Pv.as<float>(), dp, K, piv.as<int32_t>(),
+                                                     pd2.as<float>());
+        note_launch();
+    }
     const float tau2 = (float)(tau * tau);
     pivot_adj_kernel<<<grid_for((int64_t)K * K * 32, 256), 256, 0, s>>>(Pv.as<float>(), dp, K, tau2,
                                                                        adj.as<unsigned>());
     group_kernel<<<1, 256, 0, s>>>(adj.as<unsigned>(), K, gid.as<int32_t>(), ngrp.as<int32_t>());
-    note_launch(4);
+    note_launch(2);
     TK(cudaGetLastError());
 
     int ebits = bits_for(E), gbits = bits_for(K + 1), pbits = bits_for(K);

@@ -27,6 +27,12 @@ struct TcArgs {
 // pairs a.pairs[0 .. n_pairs) on tensor cores. Returns a mapper_status.
 int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaStream_t s);
 
+// Nearest of K <= 256 pivots (rows of Pv, pitch dp) for every point of X, on
+// tensor cores (BF16 hi + lo split, one MMA of N = 256 per 16 columns).
+// Returns a mapper_status.
+int assign_pivots_tc(const float* X, int64_t n, int d, int64_t ld, int dp, const float* Pv, int K,
+                     int num_sms, int32_t* piv, float* pd2, cudaStream_t s);
+
 // Constants of the screen's error bound E = A1 |a||b| + A2 (|a|^2 + |b|^2) + A3.
 void tc_bound(int ns, int dp, double eps2, double* A1, double* A2, double* A3);
 
