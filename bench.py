@@ -290,8 +290,8 @@ def run_ours(args):
                      for k in ("ms_lens", "ms_cover", "ms_cluster", "ms_nerve")},
         "counters": {k: st[k] for k in ("n_members", "n_rows", "n_groups", "sum_ni2", "tile_pairs",
                                         "tile_pairs_out", "tile_pairs_in", "tile_pairs_tc",
-                                        "tile_pairs_simt", "union_skipped", "pairs_screened",
-                                        "band_pairs", "near_ties", "n_core", "n_nodes", "n_edges")},
+                                        "tile_pairs_simt", "union_pairs", "union_skipped", "pairs_screened",
+                                        "band_pairs", "fp64_pairs", "near_ties", "n_core", "n_nodes", "n_edges")},
         "ms_tiles": float(np.mean([s["ms_tiles"] for s in stats])),
         "roofline": roof,
         "clocks": clocks,

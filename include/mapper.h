@@ -118,7 +118,7 @@ typedef struct mapper_stats {
     int64_t tile_pairs_out;  /* ... certified all-out by bounding spheres (skipped) */
     int64_t tile_pairs_in;   /* ... certified all-in by bounding spheres (no distances) */
     int64_t pairs_screened;  /* point pairs evaluated by the screen, all passes */
-    int64_t band_pairs;      /* pairs re-decided in FP64, all passes */
+    int64_t band_pairs;      /* pairs in the band of the first screen, all passes */
     int64_t near_ties;       /* unordered pairs with |d^2 - eps^2| <= 1e-12 eps^2 */
     int64_t n_core;          /* core memberships */
     int64_t n_nodes;
@@ -136,6 +136,9 @@ typedef struct mapper_stats {
                                     tensor-core one (BF16 precisions) or the CUDA-core
                                     one (FP32) */
     double ms_count_kernel;  /* device time of that kernel's launch (timing on) */
+    int64_t union_pairs;     /* screened tile pairs with a neighbour pair, given to the union
+                                pass (before its rounds skip joined ones) */
+    int64_t fp64_pairs;      /* pairs decided by the FP64 defining expression, all passes */
 } mapper_stats;
 
 /* ---------------------------------------------------------------- context */

@@ -81,6 +81,8 @@ class MapperStats(ctypes.Structure):
         ("n_rows", ctypes.c_int64),
         ("count_kernel_pairs", ctypes.c_int64),
         ("ms_count_kernel", ctypes.c_double),
+        ("union_pairs", ctypes.c_int64),
+        ("fp64_pairs", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:

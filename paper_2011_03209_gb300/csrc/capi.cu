@@ -351,10 +351,19 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     a.root = root.as<int32_t>();
     a.border = border.as<unsigned long long>();
     a.stats = stats.as<unsigned long long>();
+    // pass 1 flags the screened tile pairs holding a neighbour pair; only
+    // those can matter to the union pass
+    Buf hit_tc, hit_simt;
+    CK(hit_tc.alloc(std::max<int64_t>(PL.n[kListTC], 1), s), "alloc");
+    CK(hit_simt.alloc(std::max<int64_t>(PL.n[kListSimt], 1), s), "alloc");
+    CK(cudaMemsetAsync(hit_tc.p, 0, std::max<int64_t>(PL.n[kListTC], 1), s), "memset");
+    CK(cudaMemsetAsync(hit_simt.p, 0, std::max<int64_t>(PL.n[kListSimt], 1), s), "memset");
     PassArgs a_in = a, a_tc = a, a_simt = a;
     a_in.pairs = PL.list[kListAllIn].as<int2>();
     a_tc.pairs = PL.list[kListTC].as<int2>();
+    a_tc.pair_hit = hit_tc.as<uint8_t>();
     a_simt.pairs = PL.list[kListSimt].as<int2>();
+    a_simt.pair_hit = hit_simt.as<uint8_t>();
     TcArgs t{};
     Buf queue, queue_n, tc_err;
     if (use_tc) {
@@ -401,42 +410,57 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     CK(core_flags(a.count, R, min_pts, core.as<uint8_t>(), a.parent, a.border, a.stats, s), "core");
     pt.mark();                                                    // 3
     CK(allin_pass(2, a_in, PL.n[kListAllIn], s), "pass 2 all-in");
-    // Unions in two rounds: pairs of tiles at most one apart join most of
-    // each group; the other pairs are then kept only if their core rows are
-    // not all joined yet.
+    // Unions in rounds of growing tile distance b - a (tiles of one pivot
+    // region are adjacent): from the second round on, a pair is kept only if
+    // its core rows are not all joined yet, and pairs whose two sides are each
+    // already one component only need one neighbour pair.
+    int64_t union_pairs = 0;
     auto union_rounds = [&](const PassArgs& base, int64_t n, bool tc) -> int {
         if (n == 0) return MAPPER_OK;
-        Buf near, far, far2, cnt;
-        CK(near.alloc(sizeof(int2) * n, s), "alloc");
-        CK(far.alloc(sizeof(int2) * n, s), "alloc");
-        CK(far2.alloc(sizeof(int2) * n, s), "alloc");
-        CK(cnt.alloc(sizeof(unsigned long long) * 3, s), "alloc");
-        CK(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * 3, s), "memset");
-        CK(split_near_far(base.pairs, n, near.as<int2>(), far.as<int2>(), cnt.as<unsigned long long>(), s), "split");
-        unsigned long long hc[3] = {0, 0, 0};
-        CK(cudaMemcpyAsync(hc, cnt.p, sizeof(hc), cudaMemcpyDeviceToHost, s), "copy");
+        static const int kBounds[] = {-1, 1, 4, 16, 64, INT_MAX};
+        Buf hits, sel, kept, cnt;
+        CK(hits.alloc(sizeof(int2) * n, s), "alloc");
+        CK(sel.alloc(sizeof(int2) * n, s), "alloc");
+        CK(kept.alloc(sizeof(int2) * n, s), "alloc");
+        CK(cnt.alloc(sizeof(unsigned long long) * 2, s), "alloc");
+        CK(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s), "memset");
+        CK(select_hit(base.pairs, base.pair_hit, n, hits.as<int2>(), cnt.as<unsigned long long>(), s), "select");
+        unsigned long long nh = 0;
+        CK(cudaMemcpyAsync(&nh, cnt.p, sizeof(nh), cudaMemcpyDeviceToHost, s), "copy");
         CK(cudaStreamSynchronize(s), "sync");
-        PassArgs a_near = base, a_far = base;
-        a_near.pairs = near.as<int2>();
-        a_far.pairs = far2.as<int2>();
-        int r2;
-        if (tc) { if ((r2 = tc_pass(2, a_near, t, (int64_t)hc[0], s))) return r2; }
-        else CK(simt_pass(2, a_near, (int64_t)hc[0], s), "pass 2 near");
-        CK(filter_joined(base, far.as<int2>(), (int64_t)hc[1], far2.as<int2>(), cnt.as<unsigned long long>() + 2, s),
-           "filter");
-        CK(cudaMemcpyAsync(&hc[2], cnt.as<unsigned long long>() + 2, sizeof(unsigned long long),
-                           cudaMemcpyDeviceToHost, s), "copy");
-        CK(cudaStreamSynchronize(s), "sync");
-        if (tc) { if ((r2 = tc_pass(2, a_far, t, (int64_t)hc[2], s))) return r2; }
-        else CK(simt_pass(2, a_far, (int64_t)hc[2], s), "pass 2 far");
+        union_pairs += (int64_t)nh;
+        for (int k = 0; k + 1 < (int)(sizeof(kBounds) / sizeof(kBounds[0])); ++k) {
+            CK(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * 2, s), "memset");
+            CK(select_delta(hits.as<int2>(), (int64_t)nh, kBounds[k], kBounds[k + 1], sel.as<int2>(),
+                            cnt.as<unsigned long long>(), s), "select");
+            const int2* list = sel.as<int2>();
+            unsigned long long hc[2] = {0, 0};
+            if (k > 0) {
+                CK(cudaMemcpyAsync(hc, cnt.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s), "copy");
+                CK(cudaStreamSynchronize(s), "sync");
+                CK(filter_joined(base, sel.as<int2>(), (int64_t)hc[0], kept.as<int2>(),
+                                 cnt.as<unsigned long long>() + 1, s), "filter");
+                list = kept.as<int2>();
+            }
+            CK(cudaMemcpyAsync(hc, cnt.p, sizeof(hc), cudaMemcpyDeviceToHost, s), "copy");
+            CK(cudaStreamSynchronize(s), "sync");
+            const int64_t m = (int64_t)(k > 0 ? hc[1] : hc[0]);
+            PassArgs ar = base;
+            ar.pairs = list;
+            ar.pair_hit = nullptr;
+            int r2;
+            if (tc) { if ((r2 = tc_pass(2, ar, t, m, s))) return r2; }
+            else CK(simt_pass(2, ar, m, s), "pass 2");
+        }
         return MAPPER_OK;
     };
     if (use_tc) {
         if ((rc = union_rounds(a_tc, PL.n[kListTC], true))) return rc;
-        CK(simt_pass(2, a_simt, PL.n[kListSimt], s), "pass 2");
+        if ((rc = union_rounds(a_simt, PL.n[kListSimt], false))) return rc;
     } else {
         if ((rc = union_rounds(a_simt, PL.n[kListSimt], false))) return rc;
     }
+    st.union_pairs = union_pairs;
     pt.mark();                                                    // 4
     CK(flatten(a.parent, a.core, R, root.as<int32_t>(), s), "flatten");
     if (cap) {
@@ -470,6 +494,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     st.pairs_screened = (int64_t)h_stats[kStatScreened];
     st.n_core = (int64_t)h_stats[kStatCore];
     st.union_skipped = (int64_t)h_stats[kStatSkipped];
+    st.fp64_pairs = (int64_t)h_stats[kStatFp64];
     st.n_rows = R;
     if (tev[0] && PL.n[use_tc ? kListTC : kListSimt] > 0) {
         float ms = 0.f;

@@ -9,8 +9,15 @@ namespace mgb {
 
 constexpr int kTile = 128;          // rows per tile (one tcgen05 M block)
 
+// A union-pass list entry may carry a flag in bit 30 of its second tile:
+// the A-tile cores already share one root and the B-tile cores another, so
+// one neighbour pair between them is enough (no per-pair unions).
+constexpr int kPairOneEach = 1 << 30;
+constexpr int kPairTileMask = kPairOneEach - 1;
+
 enum : int { kStatBand = 0, kStatTies = 1, kStatScreened = 2, kStatCore = 3, kStatTileOut = 4,
-             kStatTileIn = 5, kStatSkipped = 6, kStatTcPairs = 7, kStatSimtPairs = 8, kStatCount = 9 };
+             kStatTileIn = 5, kStatSkipped = 6, kStatTcPairs = 7, kStatSimtPairs = 8, kStatFp64 = 9,
+             kStatCount = 10 };
 
 // Work lists of tile pairs, classified by bounding spheres.
 enum : int { kListAllIn = 0, kListTC = 1, kListSimt = 2, kListCount = 3 };
@@ -37,6 +44,8 @@ struct PassArgs {
     int32_t* count;              // pass 1 output, per row
     int32_t* nbr;                // pass 1: first `cap` neighbour rows of each row
     int cap;                     //   (0: no lists)
+    uint8_t* pair_hit;           // pass 1 (explicit mode, optional): set to 1 for each tile
+                                 //   pair with a neighbour pair, or one left to the recheck
     const uint8_t* core;         // passes 2, 3
     int32_t* parent;             // pass 2 union-find over rows
     const int32_t* root;         // pass 3 (flattened)
@@ -67,12 +76,16 @@ cudaError_t rows_to_slots(const int32_t* row_slot, const int32_t* row_pt, const 
                           int64_t* slot_label, uint8_t* slot_core, cudaStream_t s);
 cudaError_t element_offsets(const uint64_t* keys, int64_t M, int64_t E, int64_t* elem_off,
                             cudaStream_t s);
-// Splits a tile-pair list into pairs whose tiles are at most one apart and
-// the rest; counts[0], counts[1] receive the sizes.
-cudaError_t split_near_far(const int2* pairs, int64_t n, int2* near, int2* far,
-                           unsigned long long* counts, cudaStream_t s);
+// Appends to `out` the tile pairs of `pairs` whose hit flag is set; *count
+// receives the size.
+cudaError_t select_hit(const int2* pairs, const uint8_t* hit, int64_t n, int2* out,
+                       unsigned long long* count, cudaStream_t s);
+// Appends to `out` the tile pairs (a, b) of `pairs` with lo < b - a <= hi;
+// *count receives the size.
+cudaError_t select_delta(const int2* pairs, int64_t n, int lo, int hi, int2* out,
+                         unsigned long long* count, cudaStream_t s);
 // Keeps the union-pass tile pairs whose core rows do not all share one root
-// yet; counts[0] receives the size.
+// yet (flagging kPairOneEach pairs); counts[0] receives the size.
 cudaError_t filter_joined(const PassArgs& a, const int2* pairs, int64_t n, int2* out,
                           unsigned long long* counts, cudaStream_t s);
 

@@ -134,6 +134,7 @@ struct Decider {
         if (s > A.hi_thr && s <= FLT_MAX) return false;
         const double d2 = exact_sqdist(A.G + row_a * A.dp, A.G + row_b * A.dp, A.d);
         atomicAdd(&A.stats[kStatBand], 1ull);
+        atomicAdd(&A.stats[kStatFp64], 1ull);
         if (count_tie && fabs(d2 - A.eps2) <= A.tie_thr) atomicAdd(&A.stats[kStatTies], 1ull);
         return d2 <= A.eps2;
     }
@@ -151,11 +152,12 @@ __device__ __forceinline__ PairRows pair_rows(const PassArgs& A, int64_t q)
     PairRows P;
     if (A.pairs) {
         const int2 p = A.pairs[q];
+        const int tb = p.y & kPairTileMask;
         P.sa = (int64_t)p.x * kT;
-        P.sb = (int64_t)p.y * kT;
+        P.sb = (int64_t)tb * kT;
         P.na = A.tile_n[p.x];
-        P.nb = A.tile_n[p.y];
-        P.diag = p.x == p.y;
+        P.nb = A.tile_n[tb];
+        P.diag = p.x == tb;
     } else {
         const int64_t e = upper_bound_i64(A.pair_off, (int64_t)A.E + 1, q) - 1;
         const int64_t qq = q - A.pair_off[e];
@@ -352,6 +354,7 @@ __global__ void __launch_bounds__(256, 2) simt_pass_kernel(const PassArgs A)
                 }
             }
         }
+        if (A.pair_hit && inb && A.pairs) A.pair_hit[blockIdx.x] = 1;
         if (tid == 0) {
             const int64_t pairs = diag ? (int64_t)na * (na + 1) / 2 : (int64_t)na * nb;
             atomicAdd(&A.stats[kStatScreened], (unsigned long long)pairs);
@@ -551,18 +554,28 @@ __global__ void elem_offsets_kernel(const uint64_t* __restrict__ keys, int64_t M
     elem_off[e] = l;
 }
 
-__global__ void split_near_far_kernel(const int2* __restrict__ pairs, int64_t n, int2* __restrict__ near,
-                                      int2* __restrict__ far, unsigned long long* __restrict__ counts)
+__global__ void select_hit_kernel(const int2* __restrict__ pairs, const uint8_t* __restrict__ hit, int64_t n,
+                                  int2* __restrict__ out, unsigned long long* __restrict__ count)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !hit[i]) return;
+    out[atomicAdd(count, 1ull)] = pairs[i];
+}
+
+// Tile pairs whose tile distance b - a lies in (lo, hi].
+__global__ void select_delta_kernel(const int2* __restrict__ pairs, int64_t n, int lo, int hi,
+                                    int2* __restrict__ out, unsigned long long* __restrict__ count)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int2 p = pairs[i];
-    const bool is_near = p.y - p.x <= 1;
-    const unsigned long long at = atomicAdd(&counts[is_near ? 0 : 1], 1ull);
-    (is_near ? near : far)[at] = p;
+    const int delta = p.y - p.x;
+    if (delta > lo && delta <= hi) out[atomicAdd(count, 1ull)] = p;
 }
 
-// One warp per tile pair: roots of all core rows, kept if they differ.
+// One warp per tile pair: roots of all core rows. Kept if they differ; an
+// off-diagonal pair whose A cores share one root and whose B cores share
+// another is flagged (kPairOneEach): one neighbour pair joins them.
 __global__ void filter_joined_kernel(const PassArgs A, const int2* __restrict__ pairs, int64_t n,
                                      int2* __restrict__ out, unsigned long long* __restrict__ counts)
 {
@@ -573,7 +586,7 @@ __global__ void filter_joined_kernel(const PassArgs A, const int2* __restrict__ 
         const int2 p = pairs[q];
         const bool diag = p.x == p.y;
         const int na = A.tile_n[p.x], nb = A.tile_n[p.y];
-        int lo = INT_MAX, hi = -1, nca = 0, ncb = 0;
+        int loA = INT_MAX, hiA = -1, loB = INT_MAX, hiB = -1;
         for (int x = lane; x < 2 * kT; x += 32) {
             const bool side_b = x >= kT;
             const int i = side_b ? x - kT : x;
@@ -581,20 +594,25 @@ __global__ void filter_joined_kernel(const PassArgs A, const int2* __restrict__ 
             const int64_t row = (int64_t)(side_b ? p.y : p.x) * kT + i;
             if (!A.core[row]) continue;
             const int r = gfind(A.parent, (int)row);
-            lo = min(lo, r);
-            hi = max(hi, r);
-            if (side_b) ++ncb; else ++nca;
+            if (side_b) { loB = min(loB, r); hiB = max(hiB, r); }
+            else { loA = min(loA, r); hiA = max(hiA, r); }
         }
         for (int o = 16; o; o >>= 1) {
-            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-            nca += __shfl_xor_sync(0xffffffffu, nca, o);
-            ncb += __shfl_xor_sync(0xffffffffu, ncb, o);
+            loA = min(loA, __shfl_xor_sync(0xffffffffu, loA, o));
+            hiA = max(hiA, __shfl_xor_sync(0xffffffffu, hiA, o));
+            loB = min(loB, __shfl_xor_sync(0xffffffffu, loB, o));
+            hiB = max(hiB, __shfl_xor_sync(0xffffffffu, hiB, o));
         }
-        const bool work = (diag ? nca >= 2 : (nca > 0 && ncb > 0)) && lo != hi;
+        bool work, one_each = false;
+        if (diag) {
+            work = hiA >= 0 && loA != hiA;
+        } else {
+            work = hiA >= 0 && hiB >= 0 && (loA != hiA || loB != hiB || loA != loB);
+            one_each = work && loA == hiA && loB == hiB;
+        }
         if (lane == 0) {
-            if (work) out[atomicAdd(&counts[0], 1ull)] = p;
-            else if (hi >= 0) atomicAdd(&A.stats[kStatSkipped], 1ull);
+            if (work) out[atomicAdd(&counts[0], 1ull)] = make_int2(p.x, p.y | (one_each ? kPairOneEach : 0));
+            else if (hiA >= 0) atomicAdd(&A.stats[kStatSkipped], 1ull);
         }
     }
 }
@@ -603,11 +621,20 @@ inline unsigned grid_for(int64_t n, int t = 256) { return (unsigned)std::max<int
 
 }  // namespace
 
-cudaError_t split_near_far(const int2* pairs, int64_t n, int2* near, int2* far,
-                           unsigned long long* counts, cudaStream_t s)
+cudaError_t select_hit(const int2* pairs, const uint8_t* hit, int64_t n, int2* out,
+                       unsigned long long* count, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    split_near_far_kernel<<<grid_for(n), 256, 0, s>>>(pairs, n, near, far, counts);
+    select_hit_kernel<<<grid_for(n), 256, 0, s>>>(pairs, hit, n, out, count);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t select_delta(const int2* pairs, int64_t n, int lo, int hi, int2* out,
+                         unsigned long long* count, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    select_delta_kernel<<<grid_for(n), 256, 0, s>>>(pairs, n, lo, hi, out, count);
     note_launch();
     return cudaGetLastError();
 }

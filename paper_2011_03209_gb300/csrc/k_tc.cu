@@ -329,7 +329,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             uint32_t phase = 0;
             int issued = 0;
             for (int64_t q = blockIdx.x; q < P.n_pairs && !*abort; q += gridDim.x) {
-                const int2 tp = A.pairs[q];
+                int2 tp = A.pairs[q];
+                tp.y &= kPairTileMask;
                 const bool diag = tp.x == tp.y;
                 const uint32_t bytes = (uint32_t)((diag ? kOps / 2 : kOps) * kBlk);
                 for (int kb = 0; kb < P.nkb; ++kb) {
@@ -366,7 +367,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             uint32_t phase = 0;
             int it = 0;
             for (int64_t q = blockIdx.x; q < P.n_pairs && !*abort; q += gridDim.x, ++it) {
-                const int2 tp = A.pairs[q];
+                int2 tp = A.pairs[q];
+                tp.y &= kPairTileMask;
                 const bool diag = tp.x == tp.y;
                 const int buf = it & 1;
                 const uint32_t acc_phase = (uint32_t)((it >> 1) & 1);
@@ -412,6 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
         const int r = quad * 32 + lane;                       // accumulator row = A-tile row
         struct Pre {
             int2 tp;
+            bool one_each;                                    // union pass: see kPairOneEach
             int na, nb;
             float na2, nra;                                   // row r
             float c2, c1;                                     // column et (et < 128)
@@ -419,6 +422,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
         };
         auto prefetch = [&](int64_t q, Pre& f) {
             f.tp = A.pairs[q];
+            f.one_each = (f.tp.y & kPairOneEach) != 0;
+            f.tp.y &= kPairTileMask;
             f.na = A.tile_n[f.tp.x];
             f.nb = A.tile_n[f.tp.y];
             const int64_t sa = (int64_t)f.tp.x * kT, sb = (int64_t)f.tp.y * kT;
@@ -440,6 +445,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
         for (int64_t q = blockIdx.x; q < P.n_pairs; q += gridDim.x, ++it) {
             const int2 tp = cur.tp;
             const bool diag = tp.x == tp.y;
+            const bool one_each = MODE == 2 && cur.one_each;
             const int na = cur.na, nb = cur.nb;
             const int64_t sa = (int64_t)tp.x * kT, sb = (int64_t)tp.y * kT;
             const int buf = it & 1;
@@ -546,9 +552,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 }
             }
 
-            // (5) band pairs: queued for the FP64 recheck (decided here if the queue is full)
+            // (5) band pairs: queued for the FP64 recheck (decided here if the queue is full);
+            //     a one-each union pair needs none once any pair is certainly in
+            bool any_in = false;
+            if (one_each) any_in = epi_sync_or((inb[0] | inb[1]) != 0u);
 #pragma unroll
-            for (int c2 = 0; c2 < 2; ++c2) {
+            for (int c2 = 0; c2 < 2 && !any_in; ++c2) {
                 uint32_t b = band[c2];
                 while (b) {
                     const int i = __ffs(b) - 1;
@@ -575,6 +584,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             // (6) counts and lists, or unions
             if (MODE == 1) {
                 const int k = __popc(inb[0]) + __popc(inb[1]);
+                if (A.pair_hit && (k > 0 || (band[0] | band[1]) != 0u)) A.pair_hit[q] = 1;
                 if (k > A.cap) {
                     atomicAdd(&A.count[sa + r], k);               // core for sure: no list needed
                 } else if (k > 0) {
@@ -620,6 +630,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                     const int64_t pairs = diag ? (int64_t)na * (na + 1) / 2 : (int64_t)na * nb;
                     atomicAdd(&A.stats[kStatScreened], (unsigned long long)pairs);
                     atomicAdd(&A.stats[kStatTcPairs], (unsigned long long)pairs);
+                }
+            } else if (one_each) {
+                // both sides are single components: join them through any neighbour pair
+                if (work && (inb[0] | inb[1])) {
+                    const int c2 = inb[0] ? 0 : 1;
+                    const int j = (half * 2 + c2) * 32 + __ffs(inb[c2]) - 1;
+                    gunion(A.parent, A.row_pt, (int)(sa + r), (int)(sb + j));
                 }
             } else {
                 // local unions over the pair's 256 rows, then global unions
@@ -853,56 +870,101 @@ __global__ void mean_rows_kernel(const float* __restrict__ rows, int K, int dp, 
     }
 }
 
-// Band pairs queued by the epilogues, re-decided in FP64 (k ascending, one
-// rounding per operation: the defining expression).
+// Band pairs queued by the epilogues, 8 lanes per pair (4 pairs per warp in
+// flight), decided in three steps that each keep the FP64 decision:
+//   1. FP32: each lane sums dp/8 squared differences with FMA, then a
+//      3-level shuffle tree: |s - d^2| <= (2 + dp/8 + 3) 2^-24 d^2 (+ tiny),
+//      certified in/out outside that band (thresholds lo32, hi32);
+//   2. FP64, same split: |s - d^2| <= (dp/8 + 5) 2^-53 d^2, so outside
+//      4e-12 eps^2 of eps^2 it decides like the defining expression;
+//   3. else the defining expression itself (k ascending, one rounding per
+//      operation) on the group's first lane, which also counts near ties.
 template <int MODE>
-__global__ void recheck_kernel(const PassArgs A, const uint2* __restrict__ queue,
-                               const unsigned long long* __restrict__ queue_n, unsigned long long cap)
+__global__ void __launch_bounds__(256) recheck_kernel(const PassArgs A, const uint2* __restrict__ queue,
+                                                      const unsigned long long* __restrict__ queue_n,
+                                                      unsigned long long cap, float lo32, float hi32)
 {
-    const unsigned long long n = min(*queue_n, cap);
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint2 e = queue[i];
+    const long long n = (long long)min(*queue_n, cap);
+    const int lane = threadIdx.x & 31, sub = lane & 7;
+    const long long group = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const long long ngroup = ((long long)gridDim.x * blockDim.x) >> 3;
+    const long long rounds = (n + ngroup - 1) / ngroup;         // same trip count for the whole warp
+    for (long long rd = 0; rd < rounds; ++rd) {
+        const long long i = group + rd * ngroup;
+        const bool live = i < n;
+        uint2 e = make_uint2(0u, 0u);
+        if (live) e = queue[i];
         const int ra = (int)e.x, rb = (int)(e.y & 0x3FFFFFFFu);
         const uint32_t fl = e.y >> 30;
-        // FP32 screen first (bounded as in fp32_thresholds), FP64 only in its band
         const float4* xa = reinterpret_cast<const float4*>(A.G + (int64_t)ra * A.dp);
         const float4* xb = reinterpret_cast<const float4*>(A.G + (int64_t)rb * A.dp);
         float s32 = 0.f;
-        for (int k = 0; k < A.dp / 4; ++k) {
-            const float4 p = xa[k], q = xb[k];
-            float t = p.x - q.x;
-            s32 = fmaf(t, t, s32);
-            t = p.y - q.y;
-            s32 = fmaf(t, t, s32);
-            t = p.z - q.z;
-            s32 = fmaf(t, t, s32);
-            t = p.w - q.w;
-            s32 = fmaf(t, t, s32);
-        }
-        atomicAdd(&A.stats[kStatBand], 1ull);
-        bool in;
-        if (s32 <= A.lo_thr) {
-            in = true;
-        } else if (s32 > A.hi_thr) {
-            in = false;
-        } else {
-            const double d2 = exact_sqdist(A.G + (int64_t)ra * A.dp, A.G + (int64_t)rb * A.dp, A.d);
-            if (MODE == 1 && (fl & kQTie) && fabs(d2 - A.eps2) <= A.tie_thr) atomicAdd(&A.stats[kStatTies], 1ull);
-            in = d2 <= A.eps2;
-        }
-        if (!in) continue;
-        if (MODE == 1) {
-            int old = atomicAdd(&A.count[ra], 1);
-            if (A.cap > 0 && old < A.cap) A.nbr[(int64_t)ra * A.cap + old] = rb;
-            if (fl & kQBoth) {
-                old = atomicAdd(&A.count[rb], 1);
-                if (A.cap > 0 && old < A.cap) A.nbr[(int64_t)rb * A.cap + old] = ra;
+        if (live) {
+#pragma unroll 4
+            for (int k = sub; k < A.dp / 4; k += 8) {
+                const float4 p = xa[k], q = xb[k];
+                float t = p.x - q.x;
+                s32 = fmaf(t, t, s32);
+                t = p.y - q.y;
+                s32 = fmaf(t, t, s32);
+                t = p.z - q.z;
+                s32 = fmaf(t, t, s32);
+                t = p.w - q.w;
+                s32 = fmaf(t, t, s32);
             }
-        } else {
-            gunion(A.parent, A.row_pt, ra, rb);
         }
+        s32 += __shfl_xor_sync(0xffffffffu, s32, 1);
+        s32 += __shfl_xor_sync(0xffffffffu, s32, 2);
+        s32 += __shfl_xor_sync(0xffffffffu, s32, 4);
+        int state = !live ? 3 : (s32 <= lo32 ? 1 : (s32 > hi32 ? 0 : 2));   // 2: undecided
+        if (__any_sync(0xffffffffu, state == 2)) {
+            double s64 = 0.0;
+            if (state == 2) {
+                for (int k = sub; k < A.dp / 4; k += 8) {
+                    const float4 p = xa[k], q = xb[k];
+                    double t = (double)p.x - (double)q.x;
+                    s64 = fma(t, t, s64);
+                    t = (double)p.y - (double)q.y;
+                    s64 = fma(t, t, s64);
+                    t = (double)p.z - (double)q.z;
+                    s64 = fma(t, t, s64);
+                    t = (double)p.w - (double)q.w;
+                    s64 = fma(t, t, s64);
+                }
+            }
+            s64 += __shfl_xor_sync(0xffffffffu, s64, 1);
+            s64 += __shfl_xor_sync(0xffffffffu, s64, 2);
+            s64 += __shfl_xor_sync(0xffffffffu, s64, 4);
+            if (state == 2) {
+                if (fabs(s64 - A.eps2) > 4e-12 * A.eps2) state = s64 <= A.eps2 ? 1 : 0;
+                else state = 4;                                        // the defining expression decides
+            }
+        }
+        if (live && sub == 0) {
+            bool in = state == 1;
+            if (state == 4) {
+                const double d2 = exact_sqdist(A.G + (int64_t)ra * A.dp, A.G + (int64_t)rb * A.dp, A.d);
+                if (MODE == 1 && (fl & kQTie) && fabs(d2 - A.eps2) <= A.tie_thr)
+                    atomicAdd(&A.stats[kStatTies], 1ull);
+                atomicAdd(&A.stats[kStatFp64], 1ull);
+                in = d2 <= A.eps2;
+            }
+            if (in) {
+                if (MODE == 1) {
+                    int old = atomicAdd(&A.count[ra], 1);
+                    if (A.cap > 0 && old < A.cap) A.nbr[(int64_t)ra * A.cap + old] = rb;
+                    if (fl & kQBoth) {
+                        old = atomicAdd(&A.count[rb], 1);
+                        if (A.cap > 0 && old < A.cap) A.nbr[(int64_t)rb * A.cap + old] = ra;
+                    }
+                } else {
+                    gunion(A.parent, A.row_pt, ra, rb);
+                }
+            }
+        }
+        __syncwarp();
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&A.stats[kStatBand], (unsigned long long)n);
 }
 
 // --------------------------------------------------------------- host side
@@ -1083,9 +1145,15 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
         set_error(std::string("tensor-core pass: ") + cudaGetErrorString(e));
         return MAPPER_ECUDA;
     }
-    const int rgrid = t.num_sms * 8;
-    if (mode == 1) recheck_kernel<1><<<rgrid, 256, 0, s>>>(a, t.queue, t.queue_n, t.queue_cap);
-    else recheck_kernel<2><<<rgrid, 256, 0, s>>>(a, t.queue, t.queue_n, t.queue_cap);
+    // FP32 limits of the recheck's lane-split sum (relative error (dp/8 + 5) 2^-24)
+    const double eta = 1.5 * (a.dp / 8 + 5) * std::ldexp(1.0, -24);
+    const double tiny = 3.0 * (a.d + 2) * std::ldexp(1.0, -149);
+    float lo32 = (float)(a.eps2 * (1.0 - eta) - tiny), hi32 = (float)(a.eps2 * (1.0 + eta) + tiny);
+    if ((double)lo32 > a.eps2 * (1.0 - eta) - tiny) lo32 = std::nextafter(lo32, -INFINITY);
+    if ((double)hi32 < a.eps2 * (1.0 + eta) + tiny) hi32 = std::nextafter(hi32, INFINITY);
+    const int rgrid = t.num_sms * 16;
+    if (mode == 1) recheck_kernel<1><<<rgrid, 256, 0, s>>>(a, t.queue, t.queue_n, t.queue_cap, lo32, hi32);
+    else recheck_kernel<2><<<rgrid, 256, 0, s>>>(a, t.queue, t.queue_n, t.queue_cap, lo32, hi32);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) {

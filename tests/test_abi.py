@@ -48,7 +48,7 @@ def test_struct_layouts_match_header():
     # mapper_params: 7 int32, pad to 8, 2 doubles, double, 2 int32
     assert ctypes.sizeof(_capi.MapperParams) == 64
     assert _capi.MapperParams.overlap.offset == 32
-    assert ctypes.sizeof(_capi.MapperStats) == 8 * 30
+    assert ctypes.sizeof(_capi.MapperStats) == 8 * 32
 
 
 def test_null_and_bad_arguments_are_rejected_without_a_gpu(lib):
