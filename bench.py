@@ -316,6 +316,61 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_serving(args):
+    """Serving mix: nine device-resident clouds, a seeded Poisson request
+    stream (mean `rate` per second), requests admitted by device-memory
+    footprint into `slots` concurrent slots. Reports graphs/s and the
+    p50/p99 latency from submission to a finished graph."""
+    import torch
+    import paper_2011_03209_gb300 as mg
+
+    torch.cuda.set_device(0)
+    Xs = synth.serving_datasets(seed=4)
+    samples = [synth.pair_sample(X, 4 + i) for i, X in enumerate(Xs)]
+    reqs = synth.serving_requests(samples, args.requests + args.warmup, args.rate, seed=4)
+    Xd = [torch.from_numpy(X).to("cuda:0") for X in Xs]
+    prec = {"bf16": mg.BF16, "bf16x1": mg.BF16X1, "fp32": mg.FP32}[args.precision]
+
+    def prm(r):
+        return mg.params(r["lens_kind"], r["lens_arg"], r["n_intervals"], r["overlap"], r["eps"],
+                         r["min_pts"], prec)
+
+    with mg.Server(0, n_slots=args.slots) as srv:
+        ids = [srv.add_dataset(X) for X in Xd]
+        for r in reqs[:args.warmup]:                      # untimed: first calls, pool growth
+            srv.wait(srv.submit(ids[r["dataset"]], prm(r)))
+        timed = reqs[args.warmup:]
+        t_base = timed[0]["t"]
+        sampler = ClockSampler(0)
+        sampler.start()
+        t0 = time.perf_counter()
+        tickets = []
+        for r in timed:
+            delay = (r["t"] - t_base) - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(ids[r["dataset"]], prm(r)))
+        lat, runs, nodes = [], [], 0
+        for t in tickets:
+            g, info = srv.wait(t)
+            lat.append(info["latency_s"] * 1e3)
+            runs.append(info["run_s"] * 1e3)
+            nodes += g.sizes()[0]
+        wall = time.perf_counter() - t0
+        clocks = sampler.stop()
+    lat = np.asarray(lat)
+    print(json.dumps({
+        "metric": "serving graphs/s (9 resident clouds, Poisson stream)", "value": len(timed) / wall,
+        "unit": "graphs/s", "n_gpus": 1, "steps": len(timed), "warmup": args.warmup,
+        "higher_is_better": True, "dtype": "f32+f64" if prec == mg.FP32 else "bf16+f64", "data": "synthetic",
+        "config": {"workload": "serving_mix_9_clouds", "rate_per_s": args.rate, "slots": args.slots,
+                   "datasets": [list(X.shape) for X in Xs], "precision": args.precision},
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "mean_run_ms": float(np.mean(runs)), "max_ms": float(lat.max()), "nodes": int(nodes),
+        "wall_s": wall, "clocks": clocks,
+    }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -326,11 +381,18 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=12.0,
                     help="seconds of oracle DBSCAN per reference sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="clusters", choices=["clusters", "serving"],
+                    help="clusters: the 1M x 256 graph (default); serving: the request mix")
+    ap.add_argument("--requests", type=int, default=200, help="serving: timed requests")
+    ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
+    ap.add_argument("--slots", type=int, default=4, help="serving: concurrent slots")
     ap.add_argument("--n", type=int, default=1_000_000,
                     help="points of the clustered cloud (smaller only for profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -218,6 +218,46 @@ int mapper_stats_get(const void* handle, mapper_stats* out);
 /* Release any handle (cover, clusters, graph). NULL is a no-op. */
 void mapper_free(void* handle);
 
+/* ------------------------------------------------------------- serving */
+
+/* Estimated device bytes one mapper_graph call on an n x d cloud with these
+ * parameters holds at its peak (for admission control; not a guarantee). */
+int mapper_graph_footprint(int64_t n, int32_t d, const mapper_params* params, size_t* bytes);
+
+/* A request server (§4.1: the interface recomputes the graph whenever a
+ * parameter changes; §4.4: parameter ranges computed offline). Datasets stay
+ * resident on the device; requests (dataset, parameters) are queued in
+ * arrival order and start as soon as one of n_slots worker slots is free and
+ * their estimated footprint fits in hbm_budget_bytes beside the running ones
+ * (0 = 80 % of the device's free memory at creation; a request that alone
+ * exceeds the budget runs when nothing else does). Each slot is a host thread
+ * with its own context and CUDA stream, so running requests overlap on the
+ * device. Results are the exact graphs of mapper_graph. Thread-safe. */
+typedef struct mapper_server mapper_server;
+
+typedef struct mapper_request_info {
+    double queue_s;          /* submit -> start of work */
+    double run_s;            /* start of work -> graph ready */
+    double latency_s;        /* submit -> graph ready */
+    size_t footprint;        /* the admission estimate it ran under */
+    int32_t status;          /* mapper_status of the computation */
+} mapper_request_info;
+
+int mapper_server_create(mapper_server** out, int device, int n_slots, size_t hbm_budget_bytes);
+/* Stops the slots after their running requests; queued ones are dropped. */
+void mapper_server_destroy(mapper_server* server);
+/* X_dev: device FP32 cloud (n rows, stride ld), borrowed until destroy. */
+int mapper_server_add_dataset(mapper_server* server, const float* X_dev, int64_t n, int32_t d, int64_t ld,
+                              int32_t* dataset_id);
+int mapper_server_submit(mapper_server* server, int32_t dataset_id, const mapper_params* params,
+                         int64_t* request_id);
+/* Waits for a request (timeout_s < 0: no limit; MAPPER_ETIMEOUT otherwise)
+ * and hands its graph to the caller (release with mapper_free). info may be
+ * NULL. A request is collected once. */
+int mapper_server_wait(mapper_server* server, int64_t request_id, double timeout_s, mapper_graph_t** out,
+                       mapper_request_info* info);
+int mapper_server_load(mapper_server* server, int* running, int* queued, size_t* bytes_in_use);
+
 /* ----------------------------------------------- allocation-free variant */
 
 /* DBSCAN(eps, minPts) of one point set, allocating no device memory.

@@ -19,7 +19,7 @@ from ._capi import BF16, BF16X1, FP32, LENS_COORD, LENS_L2, LENS_PCA, MapperErro
 __all__ = [
     "Context", "Cover", "Clusters", "Graph", "MapperError", "mapper_lens", "mapper_cover",
     "mapper_cluster", "mapper_nerve", "mapper_graph", "params", "LENS_L2", "LENS_COORD",
-    "LENS_PCA", "FP32", "BF16", "BF16X1", "mapper_dbscan_noalloc",
+    "LENS_PCA", "FP32", "BF16", "BF16X1", "mapper_dbscan_noalloc", "Server", "graph_footprint",
 ]
 
 
@@ -252,3 +252,71 @@ def mapper_dbscan_noalloc(X, eps: float, min_pts: int, label=None, core=None, st
                                           _vp(core.data_ptr()), _vp(s.cuda_stream)),
                 "mapper_dbscan_noalloc")
     return label, core
+
+
+def graph_footprint(n: int, d: int, prm: MapperParams) -> int:
+    """Estimated peak device bytes of one mapper_graph call (admission control)."""
+    out = ctypes.c_size_t()
+    lib = _capi.load()
+    _capi.check(lib.mapper_graph_footprint(int(n), int(d), ctypes.byref(prm), ctypes.byref(out)),
+                "mapper_graph_footprint")
+    return out.value
+
+
+class Server:
+    """Request server over device-resident datasets: requests start as soon as
+    a worker slot is free and their footprint fits in the budget; running
+    requests overlap on the device (see mapper_server_* in include/mapper.h)."""
+
+    def __init__(self, device: int = 0, n_slots: int = 4, hbm_budget: int = 0):
+        self._lib = _capi.load()
+        h = ctypes.c_void_p()
+        _capi.check(self._lib.mapper_server_create(ctypes.byref(h), int(device), int(n_slots), int(hbm_budget)),
+                    "mapper_server_create")
+        self.h = h
+        self._keep = []
+
+    def add_dataset(self, X) -> int:
+        p, n, d, ld, keep = _x_args(X)
+        self._keep.append(keep)
+        out = ctypes.c_int32()
+        _capi.check(self._lib.mapper_server_add_dataset(self.h, p, n, d, ld, ctypes.byref(out)),
+                    "mapper_server_add_dataset")
+        return out.value
+
+    def submit(self, dataset: int, prm: MapperParams) -> int:
+        out = ctypes.c_int64()
+        _capi.check(self._lib.mapper_server_submit(self.h, int(dataset), ctypes.byref(prm), ctypes.byref(out)),
+                    "mapper_server_submit")
+        return out.value
+
+    def wait(self, request: int, timeout: float = -1.0):
+        """(Graph, info dict) of a finished request."""
+        g = ctypes.c_void_p()
+        info = _capi.RequestInfo()
+        _capi.check(self._lib.mapper_server_wait(self.h, int(request), float(timeout), ctypes.byref(g),
+                                                 ctypes.byref(info)), "mapper_server_wait")
+        return Graph(self._lib, g), {k: getattr(info, k) for k, _ in info._fields_}
+
+    def load(self):
+        r, q, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        _capi.check(self._lib.mapper_server_load(self.h, ctypes.byref(r), ctypes.byref(q), ctypes.byref(b)),
+                    "mapper_server_load")
+        return r.value, q.value, b.value
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self._lib.mapper_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -31,7 +31,9 @@ EXPORTS = (
     "mapper_cluster", "mapper_clusters_copy", "mapper_nerve", "mapper_graph",
     "mapper_graph_sizes", "mapper_graph_copy", "mapper_graph_lens", "mapper_graph_cover",
     "mapper_graph_clusters", "mapper_stats_get", "mapper_free", "mapper_strerror",
-    "mapper_last_error", "mapper_abi_version", "mapper_dbscan_noalloc",
+    "mapper_last_error", "mapper_abi_version", "mapper_dbscan_noalloc", "mapper_graph_footprint",
+    "mapper_server_create", "mapper_server_destroy", "mapper_server_add_dataset", "mapper_server_submit",
+    "mapper_server_wait", "mapper_server_load",
 )
 
 NOALLOC_MAX_POINTS = 8192
@@ -91,6 +93,16 @@ class MapperStats(ctypes.Structure):
         return out
 
 
+class RequestInfo(ctypes.Structure):
+    _fields_ = [
+        ("queue_s", ctypes.c_double),
+        ("run_s", ctypes.c_double),
+        ("latency_s", ctypes.c_double),
+        ("footprint", ctypes.c_size_t),
+        ("status", ctypes.c_int32),
+    ]
+
+
 class MapperError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         super().__init__(f"{where}: status {status}: {message}")
@@ -140,6 +152,13 @@ def load(path: str | None = None):
             "mapper_last_error": (ctypes.c_char_p, []),
             "mapper_abi_version": (ctypes.c_int, []),
             "mapper_dbscan_noalloc": (ctypes.c_int, [P, i64, i32, i64, f64, i32, P, P, P]),
+            "mapper_graph_footprint": (ctypes.c_int, [i64, i32, ctypes.POINTER(MapperParams), P]),
+            "mapper_server_create": (ctypes.c_int, [PP, ctypes.c_int, ctypes.c_int, sz]),
+            "mapper_server_destroy": (None, [P]),
+            "mapper_server_add_dataset": (ctypes.c_int, [P, P, i64, i32, i64, P]),
+            "mapper_server_submit": (ctypes.c_int, [P, i32, ctypes.POINTER(MapperParams), P]),
+            "mapper_server_wait": (ctypes.c_int, [P, i64, f64, PP, ctypes.POINTER(RequestInfo)]),
+            "mapper_server_load": (ctypes.c_int, [P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)

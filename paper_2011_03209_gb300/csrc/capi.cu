@@ -865,6 +865,31 @@ int mapper_graph(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t 
     return MAPPER_OK;
 }
 
+int mapper_graph_footprint(int64_t n, int32_t d, const mapper_params* p, size_t* bytes)
+{
+    if (!p || !bytes) return fail(MAPPER_EINVAL, "null argument");
+    if (n < 1 || d < 1 || p->m < 1 || p->m > 2) return fail(MAPPER_EINVAL, "bad sizes or filter dimension");
+    double mult = 1.0, E = 1.0;
+    for (int j = 0; j < p->m; ++j) {
+        if (p->n_intervals[j] < 1 || !(p->overlap[j] >= 0.0 && p->overlap[j] < 1.0))
+            return fail(MAPPER_EINVAL, "bad cover parameters");
+        // a point lies in at most floor(1/(1-p)) + 1 intervals, one more on exact ties
+        mult *= std::min<double>(p->n_intervals[j], std::floor(1.0 / (1.0 - p->overlap[j])) + 2.0);
+        E *= p->n_intervals[j];
+    }
+    const double dp = (double)((d + 31) / 32 * 32);
+    const double M = (double)n * mult;
+    const double rows = 1.1 * M + 128.0 * E;
+    const int cap = (p->min_pts >= 2 && p->min_pts - 1 <= 64) ? p->min_pts - 1 : 0;
+    const bool tc = p->precision != MAPPER_FP32;
+    double b = rows * dp * (tc ? 8.0 : 4.0);                 // FP32 rows (+ BF16 hi, lo)
+    b += tc ? (double)n * dp * 4.0 : 0.0;                     // pivot assignment operands
+    b += rows * (29.0 + 4.0 * cap) + M * 40.0 + (double)n * 24.0 * p->m;
+    b += 3.0 * 8.0 * rows * rows / (128.0 * 128.0) / std::max(1.0, E);   // tile-pair lists
+    *bytes = (size_t)(b * 1.1) + (size_t)(64u << 20);
+    return MAPPER_OK;
+}
+
 int mapper_graph_sizes(const mapper_graph_t* g, int64_t* n_nodes, int64_t* n_members, int64_t* n_edges)
 {
     auto* h = handle_as<mapper_graph_t>(g, kKindGraph);

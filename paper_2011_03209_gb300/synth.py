@@ -206,3 +206,63 @@ def tiny_random(n: int, d: int, seed: int, scale: float = 1.0, dup_frac: float =
         dst = rng.integers(0, n, size=n_dup)
         X[dst] = X[src]
     return X
+
+
+# --------------------------------------------------------------------------
+# Serving mix: resident clouds and a seeded Poisson request stream.
+# --------------------------------------------------------------------------
+
+def pair_sample(X: np.ndarray, seed: int, n_pairs: int = 100_000) -> np.ndarray:
+    """Sorted squared distances of n_pairs uniformly drawn pairs i != j."""
+    rng = np.random.default_rng([seed, 0x5E7])
+    n = X.shape[0]
+    i = rng.integers(0, n, size=n_pairs)
+    j = rng.integers(0, n - 1, size=n_pairs)
+    j = j + (j >= i)
+    sq = np.empty(n_pairs, dtype=np.float64)
+    for s in range(0, n_pairs, 8192):
+        diff = X[i[s:s + 8192]].astype(np.float64) - X[j[s:s + 8192]].astype(np.float64)
+        sq[s:s + 8192] = np.einsum("ij,ij->i", diff, diff)
+    sq.sort()
+    return sq
+
+
+def eps_from_sample(sq: np.ndarray, q: float) -> float:
+    """Radius halfway (in squared distance) between the sampled values around
+    the q-th percentile, as in eps_at_percentile."""
+    k = min(max(int(math.ceil(q * len(sq) / 100.0)) - 1, 0), len(sq) - 2)
+    return float(math.sqrt(0.5 * (sq[k] + sq[k + 1])))
+
+
+def serving_datasets(seed: int = 4, big_n: int = 1_000_000):
+    """Nine resident clouds: the 1,000,000 x 256 clustered cloud and eight
+    Gaussian mixtures (16 clusters) with n log-uniform in [1e4, 5e5] and d in
+    {32, 64, 128, 256}."""
+    rng = np.random.default_rng(seed)
+    out = [clusters_1m_d256(big_n).X]
+    for k in range(8):
+        n = int(round(10 ** rng.uniform(4.0, math.log10(5e5))))
+        d = int(rng.choice([32, 64, 128, 256]))
+        out.append(gaussian_mixture(n, d, 16, seed=100 + k, centre_box=10.0, std_lo=0.3, std_hi=1.5,
+                                    anisotropic=True))
+    return out
+
+
+def serving_requests(samples, n_requests: int, rate: float, seed: int = 4):
+    """Poisson arrivals (mean `rate` per second); each request draws a
+    dataset, lens in {L2, PC1}, n_intervals in [10, 200], overlap in
+    [0.1, 0.5], eps at a percentile in [0.5, 4] and minPts in [3, 20].
+    `samples` are the datasets' pair_sample arrays. Returns a list of dicts
+    with arrival time `t` (seconds) and the mapper parameters."""
+    rng = np.random.default_rng([seed, 0x5E4])
+    t = 0.0
+    reqs = []
+    for _ in range(n_requests):
+        t += rng.exponential(1.0 / rate)
+        ds = int(rng.integers(0, len(samples)))
+        lens = LENS_L2 if rng.random() < 0.5 else LENS_PCA
+        reqs.append(dict(t=t, dataset=ds, lens_kind=(lens,), lens_arg=(0,),
+                         n_intervals=(int(rng.integers(10, 201)),), overlap=(float(rng.uniform(0.1, 0.5)),),
+                         eps=eps_from_sample(samples[ds], float(rng.uniform(0.5, 4.0))),
+                         min_pts=int(rng.integers(3, 21))))
+    return reqs

@@ -1,0 +1,90 @@
+"""The request server: graphs computed while other requests run beside them
+on the device equal the graphs computed alone (exact integer outputs), and
+equal the FP64 oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2011_03209_gb300 import synth
+
+torch = pytest.importorskip("torch")
+mg = pytest.importorskip("paper_2011_03209_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+def _datasets():
+    return [
+        synth.gaussian_mixture(6000, 32, 8, seed=21, centre_box=8.0, std_lo=0.3, std_hi=1.2, anisotropic=True),
+        synth.gaussian_mixture(15000, 64, 12, seed=22, centre_box=10.0, std_lo=0.3, std_hi=1.5,
+                               anisotropic=True),
+        synth.blobs_circle_5k().X,
+    ]
+
+
+def _requests(samples, n):
+    reqs = synth.serving_requests(samples, n, rate=1000.0, seed=7)
+    for k, r in enumerate(reqs):
+        r["n_intervals"] = (10 + (r["n_intervals"][0] % 30),)    # keep elements several tiles wide
+        r["precision"] = mg.FP32 if k % 5 == 4 else mg.BF16
+    return reqs
+
+
+def _params(r):
+    return mg.params(r["lens_kind"], r["lens_arg"], r["n_intervals"], r["overlap"], r["eps"], r["min_pts"],
+                     r["precision"])
+
+
+def _same(a, b):
+    for k in ("node_offsets", "node_members", "node_elem", "edges"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.fixture(scope="module")
+def data():
+    Xs = _datasets()
+    samples = [synth.pair_sample(X, 3 + i, 20000) for i, X in enumerate(Xs)]
+    Xd = [torch.from_numpy(X).to("cuda:0") for X in Xs]
+    return Xs, Xd, _requests(samples, 16)
+
+
+def test_server_results_equal_alone_and_oracle(data):
+    Xs, Xd, reqs = data
+    with mg.Server(0, n_slots=4) as srv:
+        ids = [srv.add_dataset(X) for X in Xd]
+        tickets = [srv.submit(ids[r["dataset"]], _params(r)) for r in reqs]
+        mixed = []
+        for t in tickets:
+            g, info = srv.wait(t, timeout=120.0)
+            assert info["status"] == 0 and info["latency_s"] >= info["run_s"] >= 0.0
+            mixed.append(g.numpy())
+    with mg.Context(0) as ctx:
+        for k, (r, got) in enumerate(zip(reqs, mixed)):
+            alone = mg.mapper_graph(ctx, Xd[r["dataset"]], _params(r))
+            _same(got, alone.numpy())
+            if k < 4:                                    # and the oracle, on the GPU's lens
+                lens, _ = alone.lens(Xs[r["dataset"]].shape[0], 1)
+                ref = oracle.mapper_graph(Xs[r["dataset"]], lens, r["n_intervals"], r["overlap"], r["eps"],
+                                          r["min_pts"])
+                _same(got, ref)
+
+
+def test_tiny_budget_runs_one_at_a_time_and_stays_exact(data):
+    Xs, Xd, reqs = data
+    with mg.Server(0, n_slots=3, hbm_budget=1) as srv:
+        ids = [srv.add_dataset(X) for X in Xd]
+        tickets = [srv.submit(ids[r["dataset"]], _params(r)) for r in reqs[:6]]
+        got = [srv.wait(t, timeout=120.0)[0].numpy() for t in tickets]
+    with mg.Context(0) as ctx:
+        for r, g in zip(reqs[:6], got):
+            _same(g, mg.mapper_graph(ctx, Xd[r["dataset"]], _params(r)).numpy())
+
+
+def test_server_rejects_unknown_dataset_and_request(data):
+    _, Xd, reqs = data
+    with mg.Server(0, n_slots=1) as srv:
+        srv.add_dataset(Xd[0])
+        with pytest.raises(mg.MapperError):
+            srv.submit(5, _params(reqs[0]))
+        with pytest.raises(mg.MapperError):
+            srv.wait(12345, timeout=0.1)
