@@ -371,6 +371,56 @@ def run_serving(args):
     }))
 
 
+def run_sweep(args):
+    """The 2D-lens sweep: 16 graphs (eps at 4 percentiles x 4 overlaps) of
+    the 500,000 x 128 Zipf mixture with a (PC1, PC2) lens on a 30 x 30 grid,
+    as one mapper_graph_sweep call; also timed as 16 mapper_graph calls."""
+    import torch
+    import paper_2011_03209_gb300 as mg
+
+    torch.cuda.set_device(0)
+    w, eps, ov = synth.zipf_sweep()
+    prec = {"bf16": mg.BF16, "bf16x1": mg.BF16X1, "fp32": mg.FP32}[args.precision]
+    Xd = torch.from_numpy(w.X).to("cuda:0")
+    stream = torch.cuda.Stream()
+    with mg.Context(0, stream=stream) as ctx:
+        base = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, eps[0], w.min_pts, prec)
+        for _ in range(args.warmup):
+            gs = mg.mapper_graph_sweep(ctx, Xd, base, eps, ov)
+            del gs
+        torch.cuda.synchronize()
+        sampler = ClockSampler(0)
+        sampler.start()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(args.steps):
+            gs = mg.mapper_graph_sweep(ctx, Xd, base, eps, ov)
+            nodes = [g.sizes()[0] for g in gs]
+            del gs
+        end.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        sweep_ms = start.elapsed_time(end) / args.steps
+        start.record(stream)
+        for _ in range(args.steps):
+            for e, p in zip(eps, ov):
+                g = mg.mapper_graph(ctx, Xd, mg.params(w.lens_kind, w.lens_arg, w.n_intervals, (p, p), e,
+                                                       w.min_pts, prec))
+                del g
+        end.record(stream)
+        torch.cuda.synchronize()
+        single_ms = start.elapsed_time(end) / args.steps
+    print(json.dumps({
+        "metric": "sweep ms (16 graphs, 500k x 128, 2D lens, 30 x 30 grid)", "value": sweep_ms, "unit": "ms",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+        "dtype": "f32+f64" if prec == mg.FP32 else "bf16+f64", "data": "synthetic",
+        "config": {"workload": w.name + "_sweep16", "n": w.n, "d": w.d, "lens": "(PC1, PC2)", "grid": [30, 30],
+                   "eps": eps, "overlap": ov, "min_pts": w.min_pts, "precision": args.precision},
+        "ms_per_graph": sweep_ms / len(eps), "single_calls_ms": single_ms,
+        "sweep_speedup": single_ms / sweep_ms, "nodes": nodes, "clocks": clocks,
+    }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,8 +431,9 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=12.0,
                     help="seconds of oracle DBSCAN per reference sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="clusters", choices=["clusters", "serving"],
-                    help="clusters: the 1M x 256 graph (default); serving: the request mix")
+    ap.add_argument("--workload", default="clusters", choices=["clusters", "serving", "sweep"],
+                    help="clusters: the 1M x 256 graph (default); serving: the request mix; "
+                         "sweep: 16 graphs of the 500k x 128 2D-lens cloud")
     ap.add_argument("--requests", type=int, default=200, help="serving: timed requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent slots")
@@ -393,6 +444,8 @@ def main():
         run_reference(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_ours(args)
 

@@ -197,6 +197,16 @@ int mapper_nerve(mapper_ctx* ctx, const mapper_clusters_t* clusters, mapper_grap
 int mapper_graph(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
                  const mapper_params* params, mapper_graph_t** out);
 
+/* Parameter sweep (§4.4: the command line computes graphs over ranges of
+ * parameters): n_sweep graphs of one cloud, graph i with radius eps[i] and
+ * overlap[i] (for every filter dimension), the other parameters from
+ * `params`. The lens is computed once, the cover and the tile layout once per
+ * distinct overlap and shared by its radii. out: n_sweep handles (each
+ * released with mapper_free). Results equal n_sweep mapper_graph calls. */
+int mapper_graph_sweep(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
+                       const mapper_params* params, int32_t n_sweep, const double* eps, const double* overlap,
+                       mapper_graph_t** out);
+
 int mapper_graph_sizes(const mapper_graph_t* g, int64_t* n_nodes, int64_t* n_members,
                        int64_t* n_edges);
 /* node_offsets: n_nodes+1 int64; node_members: n_members int32; node_elem:

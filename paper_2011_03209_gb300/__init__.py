@@ -20,6 +20,7 @@ __all__ = [
     "Context", "Cover", "Clusters", "Graph", "MapperError", "mapper_lens", "mapper_cover",
     "mapper_cluster", "mapper_nerve", "mapper_graph", "params", "LENS_L2", "LENS_COORD",
     "LENS_PCA", "FP32", "BF16", "BF16X1", "mapper_dbscan_noalloc", "Server", "graph_footprint",
+    "mapper_graph_sweep",
 ]
 
 
@@ -320,3 +321,19 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def mapper_graph_sweep(ctx: Context, X, prm: MapperParams, eps, overlap):
+    """Graphs for the radii eps[i] with overlaps overlap[i] (all filter
+    dimensions), sharing the lens, and the cover and tile layout of each
+    distinct overlap. Returns a list of Graph."""
+    p, n, d, ld, _keep = _x_args(X)
+    k = len(eps)
+    if len(overlap) != k:
+        raise ValueError("eps and overlap differ in length")
+    e = (ctypes.c_double * k)(*[float(x) for x in eps])
+    o = (ctypes.c_double * k)(*[float(x) for x in overlap])
+    hs = (ctypes.c_void_p * k)()
+    _capi.check(ctx._lib.mapper_graph_sweep(ctx.h, p, n, d, ld, ctypes.byref(prm), k, e, o, hs),
+                "mapper_graph_sweep")
+    return [Graph(ctx._lib, ctypes.c_void_p(h)) for h in hs]

@@ -33,7 +33,7 @@ EXPORTS = (
     "mapper_graph_clusters", "mapper_stats_get", "mapper_free", "mapper_strerror",
     "mapper_last_error", "mapper_abi_version", "mapper_dbscan_noalloc", "mapper_graph_footprint",
     "mapper_server_create", "mapper_server_destroy", "mapper_server_add_dataset", "mapper_server_submit",
-    "mapper_server_wait", "mapper_server_load",
+    "mapper_server_wait", "mapper_server_load", "mapper_graph_sweep",
 )
 
 NOALLOC_MAX_POINTS = 8192
@@ -153,6 +153,8 @@ def load(path: str | None = None):
             "mapper_abi_version": (ctypes.c_int, []),
             "mapper_dbscan_noalloc": (ctypes.c_int, [P, i64, i32, i64, f64, i32, P, P, P]),
             "mapper_graph_footprint": (ctypes.c_int, [i64, i32, ctypes.POINTER(MapperParams), P]),
+            "mapper_graph_sweep": (ctypes.c_int, [P, P, i64, i32, i64, ctypes.POINTER(MapperParams), i32, P, P,
+                                                  P]),
             "mapper_server_create": (ctypes.c_int, [PP, ctypes.c_int, ctypes.c_int, sz]),
             "mapper_server_destroy": (None, [P]),
             "mapper_server_add_dataset": (ctypes.c_int, [P, P, i64, i32, i64, P]),

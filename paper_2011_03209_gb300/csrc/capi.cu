@@ -264,9 +264,11 @@ int run_cover(mapper_ctx* ctx, const double* lens, int64_t n, int32_t m, const i
 // classified by bounding spheres, then the passes over the three lists:
 // all-in pairs need no distance, mixed pairs of one group go to the
 // tensor-core screen (BF16) and all others to the CUDA-core FP32 screen.
+// `layout` (optional): a tile layout of this cover built beforehand with
+// operands for this precision, shared by several radii (a sweep).
 int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
                 const std::shared_ptr<CoverData>& cov, double eps, int32_t min_pts, int32_t precision,
-                std::shared_ptr<ClusterData>* out, int* nonfinite_dev)
+                std::shared_ptr<ClusterData>* out, int* nonfinite_dev, const TileLayout* layout = nullptr)
 {
     if (!(eps > 0.0) || !std::isfinite(eps)) return fail(MAPPER_EINVAL, "eps must be finite and > 0");
     if (min_pts < 1) return fail(MAPPER_EINVAL, "min_pts must be >= 1");
@@ -309,10 +311,15 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
 
     Timer pt(ctx->timing, s);
     pt.mark();                                                    // 0
-    TileLayout L;
-    int rc = build_tiles(X, n, d, ld, dp, cov->slot_point.as<int32_t>(), cov->slot_elem.as<int32_t>(), M, E,
-                         4.0 * eps, use_tc, ctx->num_sms, &L, nf, s);
-    if (rc) return rc;
+    TileLayout own;
+    int rc = MAPPER_OK;
+    if (!layout) {
+        rc = build_tiles(X, n, d, ld, dp, cov->slot_point.as<int32_t>(), cov->slot_elem.as<int32_t>(), M, E,
+                         4.0 * eps, use_tc, ctx->num_sms, &own, nf, s);
+        if (rc) return rc;
+        layout = &own;
+    }
+    const TileLayout& L = *layout;
     PairLists PL;
     if ((rc = classify_pairs(L, dp, E, eps, use_tc, &PL, s))) return rc;
     const int64_t R = L.R;
@@ -887,6 +894,87 @@ int mapper_graph_footprint(int64_t n, int32_t d, const mapper_params* p, size_t*
     b += rows * (29.0 + 4.0 * cap) + M * 40.0 + (double)n * 24.0 * p->m;
     b += 3.0 * 8.0 * rows * rows / (128.0 * 128.0) / std::max(1.0, E);   // tile-pair lists
     *bytes = (size_t)(b * 1.1) + (size_t)(64u << 20);
+    return MAPPER_OK;
+}
+
+int mapper_graph_sweep(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld, const mapper_params* p,
+                       int32_t n_sweep, const double* eps, const double* overlap, mapper_graph_t** out)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if ((rc = check_x(X, n, d, ld))) return rc;
+    if (!p || !out || !eps || !overlap || n_sweep < 1) return fail(MAPPER_EINVAL, "bad sweep arguments");
+    if (p->m < 1 || p->m > 2) return fail(MAPPER_EINVAL, "m must be 1 or 2");
+    for (int i = 0; i < n_sweep; ++i) out[i] = nullptr;
+    cudaStream_t s = ctx->stream->s;
+    const int64_t launches0 = g_launches;
+    Buf xdev;
+    const float* Xd = X;
+    int64_t ldd = ld;
+    if (is_host_pointer(X)) {
+        CK(xdev.alloc(sizeof(float) * (size_t)n * d, s), "alloc X");
+        CK(cudaMemcpy2DAsync(xdev.p, sizeof(float) * d, X, sizeof(float) * ld, sizeof(float) * d, n,
+                             cudaMemcpyHostToDevice, s), "copy X");
+        Xd = xdev.as<float>();
+        ldd = d;
+    }
+    Buf lens, pca, flag;
+    int64_t n_pca = 0;
+    CK(flag.alloc(sizeof(int), s), "alloc");
+    CK(cudaMemsetAsync(flag.p, 0, sizeof(int), s), "memset");
+    CK(lens.alloc(sizeof(double) * (size_t)n * p->m, s), "alloc lens");
+    if ((rc = run_lens(ctx, Xd, n, d, ldd, p->m, p->lens_kind, p->lens_arg, lens.as<double>(), &pca, &n_pca)))
+        return rc;
+    std::vector<std::unique_ptr<mapper_graph_t>> graphs(n_sweep);
+    std::vector<char> done(n_sweep, 0);
+    const int dp = (d + 31) / 32 * 32;
+    const bool use_tc = p->precision != MAPPER_FP32;
+    // one cover and one tile layout per distinct overlap, shared by its radii
+    for (int i = 0; i < n_sweep; ++i) {
+        if (done[i]) continue;
+        double ov[2] = {overlap[i], overlap[i]};
+        std::shared_ptr<CoverData> cov;
+        if ((rc = run_cover(ctx, lens.as<double>(), n, p->m, p->n_intervals, ov, &cov, flag.as<int>()))) return rc;
+        double eps_max = 0.0;
+        for (int j = i; j < n_sweep; ++j)
+            if (overlap[j] == overlap[i]) eps_max = std::max(eps_max, eps[j]);
+        if (!(eps_max > 0.0) || !std::isfinite(eps_max)) return fail(MAPPER_EINVAL, "eps must be finite and > 0");
+        TileLayout L;
+        if ((rc = build_tiles(Xd, n, d, ldd, dp, cov->slot_point.as<int32_t>(), cov->slot_elem.as<int32_t>(), cov->M,
+                              cov->E, 4.0 * eps_max, use_tc, ctx->num_sms, &L, flag.as<int>(), s)))
+            return rc;
+        for (int j = i; j < n_sweep; ++j) {
+            if (done[j] || overlap[j] != overlap[i]) continue;
+            std::shared_ptr<ClusterData> cl;
+            if ((rc = run_cluster(ctx, Xd, n, d, ldd, cov, eps[j], p->min_pts, p->precision, &cl, flag.as<int>(), &L)))
+                return rc;
+            auto g = std::make_unique<mapper_graph_t>();
+            g->stream = ctx->stream;
+            g->n = n;
+            g->m = p->m;
+            g->clusters = cl;
+            CK(g->lens.alloc(sizeof(double) * (size_t)n * p->m, s), "alloc lens");
+            CK(cudaMemcpyAsync(g->lens.p, lens.p, sizeof(double) * (size_t)n * p->m, cudaMemcpyDeviceToDevice, s),
+               "copy lens");
+            if (n_pca) {
+                CK(g->pca.alloc(sizeof(double) * n_pca, s), "alloc");
+                CK(cudaMemcpyAsync(g->pca.p, pca.p, sizeof(double) * n_pca, cudaMemcpyDeviceToDevice, s), "copy");
+                g->n_pca = n_pca;
+            }
+            if ((rc = run_nerve(ctx, cl, g.get()))) return rc;
+            g->cover_view.c = cov;
+            g->cover_view.view = true;
+            g->clusters_view.c = cl;
+            g->clusters_view.view = true;
+            graphs[j] = std::move(g);
+            done[j] = 1;
+        }
+    }
+    const int64_t launches = g_launches - launches0;
+    for (int i = 0; i < n_sweep; ++i) {
+        graphs[i]->stats.n_launches = launches / n_sweep;
+        out[i] = graphs[i].release();
+    }
     return MAPPER_OK;
 }
 

@@ -15,9 +15,9 @@
 // Kernel layout (one CTA per SM, persistent over a static share of the tile
 // pairs): warp 0 issues TMA loads of 64-column K blocks (128-byte swizzle)
 // into a ring of smem stages; warp 1 issues the MMAs into one of two TMEM
-// accumulators (128 x 128 FP32 each); warps 2-9 read the accumulator back
-// with tcgen05.ld (two warps per TMEM lane quadrant, each thread one row and
-// 64 columns) and run the pass epilogue, branch-free per pair:
+// accumulators (128 x 128 FP32 each); 16 warps read the accumulator back
+// with tcgen05.ld (four warps per TMEM lane quadrant, each thread one row and
+// 32 columns) and run the pass epilogue, branch-free per pair:
 //   pass 1: neighbour counts of rows and columns (and neighbour lists),
 //   pass 2: unions of core-core neighbour pairs.
 // Every mbarrier wait is bounded in time; a wait that runs out sets an error
@@ -42,7 +42,10 @@ namespace {
 constexpr int kT = kTile;
 constexpr int kKB = 64;                       // BF16 columns per K block (128-byte rows)
 constexpr int kBlk = kT * kKB * 2;            // bytes of one 128 x 64 BF16 block
-constexpr int kThreads = 320;                 // producer, MMA, 8 epilogue warps
+constexpr int kEpiWarps = 16;                 // epilogue warps: 4 per TMEM lane quadrant
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kChunks = 128 / (kEpiWarps / 4) / 32;   // 32-column chunks per epilogue thread
+constexpr int kThreads = 64 + kEpiThreads;    // producer, MMA, epilogue warps
 constexpr unsigned long long kWaitNs = 4000000000ull;   // 4 s per wait at most
 
 struct TcParams {
@@ -168,17 +171,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
-// Barrier of the 256 epilogue threads that also ORs a flag over them, so all
+// Barrier of the epilogue threads that also ORs a flag over them, so all
 // take the same branch afterwards.
 __device__ __forceinline__ bool epi_sync_or(bool v)
 {
     uint32_t r;
     asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 256, p;\n selp.u32 %0, 1, 0, q;\n}"
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
         : "=r"(r)
-        : "r"((uint32_t)v)
+        : "r"((uint32_t)v), "n"(kEpiThreads)
         : "memory");
     return r != 0;
 }
@@ -278,7 +281,8 @@ struct SmemTail {
     uint32_t colcore[2][4];                    // union pass: core columns, bit per column
     float red[2][8];                           // max |b|^2 and |b| of the columns, per warp
     __align__(16) float nbn[2][kT];            // -|b|^2 of the pair's columns
-    uint32_t colmask[4][kT];                   // count pass: neighbour bits per column
+    uint32_t colmask[4][kT];                   // count pass: neighbour bits per column (by row quadrant)
+    uint32_t rowmask[4 * kChunks][kT];         // count pass: neighbour bits per row (by 32-column chunk)
     int par[2][2 * kT];                        // union pass: local union-find
     unsigned char core[2][2 * kT];             // union pass: core flags of A rows, B rows
 };
@@ -310,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&S.acc_full[i], 1);
-            mbar_init(&S.acc_empty[i], 8);
+            mbar_init(&S.acc_empty[i], kEpiWarps);
         }
         mbar_init(&S.fin, 1);
         S.abort = 0;
@@ -405,12 +409,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
         }
     } else {
         // ---------------------------------------------------- epilogue
-        // 8 warps: warp w reads TMEM lane quadrant (w & 3) = A rows
-        // 32(w & 3) .. +31, columns 64 h .. 64 h + 63 with h = (w - 2) / 4.
+        // kEpiWarps warps: warp w reads TMEM lane quadrant (w & 3) = A rows
+        // 32(w & 3) .. +31 and the 32 kChunks columns of part (w - 2) / 4.
         // Each pair's norms (and core flags) are loaded one pair ahead.
-        const int et = tid - 64;                              // 0..255
+        const int et = tid - 64;                              // 0 .. kEpiThreads-1
         const int quad = warp & 3;
-        const int half = (warp - 2) >> 2;
+        const int half = (warp - 2) >> 2;                     // column part
         const int r = quad * 32 + lane;                       // accumulator row = A-tile row
         struct Pre {
             int2 tp;
@@ -419,6 +423,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             float na2, nra;                                   // row r
             float c2, c1;                                     // column et (et < 128)
             bool core_et;                                     // union pass: row et of A | B
+            int count_et;                                     // count pass: count of row / column et
         };
         auto prefetch = [&](int64_t q, Pre& f) {
             f.tp = A.pairs[q];
@@ -436,12 +441,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             if (MODE == 2) {
                 const bool diag = f.tp.x == f.tp.y;
                 f.core_et = et < kT ? (et < f.na && A.core[sa + et])
-                                    : (!diag && et - kT < f.nb && A.core[sb + et - kT]);
+                                    : (et < 2 * kT && !diag && et - kT < f.nb && A.core[sb + et - kT]);
+            } else if (et < 2 * kT) {
+                f.count_et = et < kT ? A.count[sa + et] : A.count[sb + et - kT];
             }
         };
         Pre cur{};
         if ((int64_t)blockIdx.x < P.n_pairs) prefetch(blockIdx.x, cur);
         int it = 0;
+        int64_t screened = 0;
         for (int64_t q = blockIdx.x; q < P.n_pairs; q += gridDim.x, ++it) {
             const int2 tp = cur.tp;
             const bool diag = tp.x == tp.y;
@@ -452,6 +460,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             const uint32_t acc_phase = (uint32_t)((it >> 1) & 1);
             const bool valid_r = r < na;
             const float na2 = cur.na2, nra = cur.nra;
+            const int pre_count = cur.count_et;
 
             // (1) stage this pair's column data (and core rows, roots) in buffer `buf`
             if (et < kT) {
@@ -463,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 }
                 if (lane == 0) { S.red[buf][et >> 5] = m2; S.red[buf][4 + (et >> 5)] = m1; }
             }
-            if (MODE == 2) {
+            if (MODE == 2 && et < 2 * kT) {
                 const bool cc = cur.core_et;
                 S.core[buf][et] = cc;
                 S.par[buf][et] = et;
@@ -474,7 +483,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 if (et == 0) { S.s_mm[buf][0] = INT_MAX; S.s_mm[buf][1] = -1; }
             }
             if (MODE == 2) epi_sync();                          // s_mm initialised
-            if (MODE == 2 && cur.core_et) {
+            if (MODE == 2 && et < 2 * kT && cur.core_et) {
                 const int rr = gfind(A.parent, (int)(et < kT ? sa + et : sb + et - kT));
                 atomicMin(&S.s_mm[buf][0], rr);
                 atomicMax(&S.s_mm[buf][1], rr);
@@ -501,13 +510,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             const bool core_r = MODE == 2 && S.core[buf][r];
 
             // (4) accumulator rows -> neighbour bits
-            uint32_t inb[2], band[2];
+            uint32_t inb[kChunks], band[kChunks];
 #pragma unroll
-            for (int c2 = 0; c2 < 2; ++c2) {
-                const int c = half * 2 + c2;
+            for (int c2 = 0; c2 < kChunks; ++c2) {
+                const int c = half * kChunks + c2;
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * kT + c * 32), v);
-                if (c2 == 1) {
+                if (c2 == kChunks - 1) {
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&S.acc_empty[buf]);
@@ -538,6 +547,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 }
                 inb[c2] = in_bits & cand;
                 band[c2] = keep_bits & ~in_bits & cand;
+                if (MODE == 1) S.rowmask[c][r] = inb[c2];
                 if (MODE == 1 && !diag) {
                     // 32 x 32 bit transpose across the warp: lane k gets column c*32+k
                     uint32_t x = inb[c2];
@@ -555,14 +565,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             // (5) band pairs: queued for the FP64 recheck (decided here if the queue is full);
             //     a one-each union pair needs none once any pair is certainly in
             bool any_in = false;
-            if (one_each) any_in = epi_sync_or((inb[0] | inb[1]) != 0u);
+            uint32_t all_in = 0u;
 #pragma unroll
-            for (int c2 = 0; c2 < 2 && !any_in; ++c2) {
+            for (int c2 = 0; c2 < kChunks; ++c2) all_in |= inb[c2];
+            if (one_each) any_in = epi_sync_or(all_in != 0u);
+#pragma unroll
+            for (int c2 = 0; c2 < kChunks && !any_in; ++c2) {
                 uint32_t b = band[c2];
                 while (b) {
                     const int i = __ffs(b) - 1;
                     b &= b - 1;
-                    const int j = (half * 2 + c2) * 32 + i;
+                    const int j = (half * kChunks + c2) * 32 + i;
                     const uint32_t fl = MODE == 1 ? ((diag ? 0u : kQBoth) | ((!diag || r < j) ? kQTie : 0u)) : 0u;
                     bool decided;
                     const bool in = push_band(P, (int)(sa + r), (int)(sb + j), fl, &decided);
@@ -583,77 +596,74 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
 
             // (6) counts and lists, or unions
             if (MODE == 1) {
-                const int k = __popc(inb[0]) + __popc(inb[1]);
-                if (A.pair_hit && (k > 0 || (band[0] | band[1]) != 0u)) A.pair_hit[q] = 1;
-                if (k > A.cap) {
-                    atomicAdd(&A.count[sa + r], k);               // core for sure: no list needed
-                } else if (k > 0) {
-                    const int old = atomicAdd(&A.count[sa + r], k);
-                    if (old < A.cap) {
-                        int pos = old;
-                        for (int c2 = 0; c2 < 2 && pos < A.cap; ++c2) {
-                            uint32_t b = inb[c2];
-                            while (b && pos < A.cap) {
-                                const int i = __ffs(b) - 1;
-                                b &= b - 1;
-                                A.nbr[(sa + r) * A.cap + pos++] = (int32_t)(sb + (half * 2 + c2) * 32 + i);
-                            }
-                        }
-                    }
-                }
-                if (!diag) {
-                    epi_sync();
-                    if (et < kT) {
-                        const int j = et;
-                        int tot = 0;
+                // one thread per row (et < 128) and per column (128 <= et < 256) adds the
+                // pair's neighbours to the count; lists are written only while a count may
+                // still be below cap (the count read one pair ahead is a lower bound)
+                int k = 0;
+                uint32_t any_band = 0u;
 #pragma unroll
-                        for (int w = 0; w < 4; ++w) tot += __popc(S.colmask[w][j]);
-                        if (tot > A.cap) {
-                            atomicAdd(&A.count[sb + j], tot);
-                        } else if (tot > 0) {
-                            const int old = atomicAdd(&A.count[sb + j], tot);
-                            if (old < A.cap) {
-                                int pos = old;
-                                for (int w = 0; w < 4 && pos < A.cap; ++w) {
-                                    uint32_t b = S.colmask[w][j];
-                                    while (b && pos < A.cap) {
-                                        const int i = __ffs(b) - 1;
-                                        b &= b - 1;
-                                        A.nbr[(sb + j) * A.cap + pos++] = (int32_t)(sa + w * 32 + i);
-                                    }
+                for (int c2 = 0; c2 < kChunks; ++c2) {
+                    k += __popc(inb[c2]);
+                    any_band |= band[c2];
+                }
+                const bool hit = epi_sync_or(k > 0 || any_band != 0u);
+                if (et == 0 && hit && A.pair_hit) A.pair_hit[q] = 1;
+                const bool is_row = et < kT, is_col = !diag && et >= kT && et < 2 * kT;
+                if (is_row || is_col) {
+                    const int x = is_row ? et : et - kT;
+                    const int64_t row = (is_row ? sa : sb) + x;
+                    const int64_t other = is_row ? sb : sa;
+                    int tot = 0;
+                    if (is_row) {
+#pragma unroll
+                        for (int w = 0; w < 4 * kChunks; ++w) tot += __popc(S.rowmask[w][x]);
+                    } else {
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) tot += __popc(S.colmask[w][x]);
+                    }
+                    if (tot > 0) {
+                        if (tot > A.cap || pre_count >= A.cap) {
+                            atomicAdd(&A.count[row], tot);          // no list entry can be due
+                        } else {
+                            const int old = atomicAdd(&A.count[row], tot);
+                            int pos = old;
+                            for (int w = 0; w < 4 * kChunks && pos < A.cap; ++w) {
+                                uint32_t bm = is_row ? S.rowmask[w][x] : S.colmask[w & 3][x];
+                                if (!is_row && w >= 4) bm = 0u;
+                                while (bm && pos < A.cap) {
+                                    const int i = __ffs(bm) - 1;
+                                    bm &= bm - 1;
+                                    A.nbr[row * A.cap + pos++] = (int32_t)(other + w * 32 + i);
                                 }
                             }
                         }
                     }
                 }
-                if (et == 0) {
-                    const int64_t pairs = diag ? (int64_t)na * (na + 1) / 2 : (int64_t)na * nb;
-                    atomicAdd(&A.stats[kStatScreened], (unsigned long long)pairs);
-                    atomicAdd(&A.stats[kStatTcPairs], (unsigned long long)pairs);
-                }
+                if (et == 0) screened += diag ? (int64_t)na * (na + 1) / 2 : (int64_t)na * nb;
             } else if (one_each) {
                 // both sides are single components: join them through any neighbour pair
-                if (work && (inb[0] | inb[1])) {
-                    const int c2 = inb[0] ? 0 : 1;
-                    const int j = (half * 2 + c2) * 32 + __ffs(inb[c2]) - 1;
+                if (work && all_in) {
+                    int c2 = 0;
+                    while (!inb[c2]) ++c2;
+                    const int j = (half * kChunks + c2) * 32 + __ffs(inb[c2]) - 1;
                     gunion(A.parent, A.row_pt, (int)(sa + r), (int)(sb + j));
                 }
             } else {
                 // local unions over the pair's 256 rows, then global unions
                 if (work) {
 #pragma unroll
-                    for (int c2 = 0; c2 < 2; ++c2) {
+                    for (int c2 = 0; c2 < kChunks; ++c2) {
                         uint32_t b = inb[c2];
                         while (b) {
                             const int i = __ffs(b) - 1;
                             b &= b - 1;
-                            const int j = (half * 2 + c2) * 32 + i;
+                            const int j = (half * kChunks + c2) * 32 + i;
                             lunion(S.par[buf], r, diag ? j : kT + j);
                         }
                     }
                 }
                 epi_sync();
-                if (work && S.core[buf][et]) {
+                if (work && et < 2 * kT && S.core[buf][et]) {
                     const int x = et;
                     const int rx = lfind(S.par[buf], x);
                     if (rx != x) {
@@ -663,6 +673,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                     }
                 }
             }
+        }
+        if (MODE == 1 && et == 0 && screened) {
+            atomicAdd(&A.stats[kStatScreened], (unsigned long long)screened);
+            atomicAdd(&A.stats[kStatTcPairs], (unsigned long long)screened);
         }
     }
 

@@ -266,3 +266,18 @@ def serving_requests(samples, n_requests: int, rate: float, seed: int = 4):
                          eps=eps_from_sample(samples[ds], float(rng.uniform(0.5, 4.0))),
                          min_pts=int(rng.integers(3, 21))))
     return reqs
+
+
+def zipf_sweep(n: int = 500_000):
+    """The 2D-lens sweep: the Zipf(1.2) mixture of 24 clusters (n x 128),
+    (PC1, PC2) lens on a 30 x 30 grid, minPts 10, and 16 (eps, overlap)
+    points: eps at the 0.5/1/2/4th percentile of sampled distances times
+    overlap 0.1/0.2/0.3/0.4. Returns (workload, eps list, overlap list)."""
+    w = zipf_mixture_500k(n)
+    sq = pair_sample(w.X, 3)
+    eps, ov = [], []
+    for q in (0.5, 1.0, 2.0, 4.0):
+        for p in (0.1, 0.2, 0.3, 0.4):
+            eps.append(eps_from_sample(sq, q))
+            ov.append(p)
+    return w, eps, ov
