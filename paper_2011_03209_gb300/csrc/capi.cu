@@ -358,6 +358,16 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     a.root = root.as<int32_t>();
     a.border = border.as<unsigned long long>();
     a.stats = stats.as<unsigned long long>();
+    // tensor-core pairs in (b, a) order: consecutive pairs, which run on
+    // neighbouring SMs at the same time, share a tile in L2
+    if (PL.n[kListTC] > 1) {
+        Buf tmp;
+        CK(tmp.alloc(sizeof(uint64_t) * PL.n[kListTC], s), "alloc");
+        uint64_t* keys = PL.list[kListTC].as<uint64_t>();
+        const int tb = bits_for(L.T);
+        CK(radix_sort_u64(keys, tmp.as<uint64_t>(), PL.n[kListTC], 0, tb, s), "sort pairs");
+        CK(radix_sort_u64(keys, tmp.as<uint64_t>(), PL.n[kListTC], 32, 32 + tb, s), "sort pairs");
+    }
     // pass 1 flags the screened tile pairs holding a neighbour pair; only
     // those can matter to the union pass
     Buf hit_tc, hit_simt;

@@ -213,6 +213,8 @@ __device__ __forceinline__ void gunion(int32_t* parent, const int32_t* row_pt, i
     }
 }
 
+// Shared-memory union-find over the 256 rows of a tile pair (local index as
+// key; parents always smaller), for sparse pairs.
 __device__ __forceinline__ int lfind(volatile int* par, int x)
 {
     int p = par[x];
@@ -283,9 +285,97 @@ struct SmemTail {
     __align__(16) float nbn[2][kT];            // -|b|^2 of the pair's columns
     uint32_t colmask[4][kT];                   // count pass: neighbour bits per column (by row quadrant)
     uint32_t rowmask[4 * kChunks][kT];         // count pass: neighbour bits per row (by 32-column chunk)
-    int par[2][2 * kT];                        // union pass: local union-find
+    int par[2][2 * kT];                        // union pass: local union-find / component
+    int groot[2][2 * kT];                      // union pass: global root of each core row
+    int edges[2];                              // union pass: certain core-core pairs
     unsigned char core[2][2 * kT];             // union pass: core flags of A rows, B rows
 };
+
+// Connected components of a tile pair's core-core neighbour graph, on one
+// warp. Nodes: A rows 0..127 and (off-diagonal pairs) B rows 128..255; edges:
+// S.rowmask[c][r] (columns c*32.. of row r) and S.colmask[q][j] (rows
+// q*32.. of column j), both already restricted to core-core pairs. Writes
+// S.par[buf][x] = the first node of x's component (for every node).
+__device__ __forceinline__ void bfs_components(SmemTail& S, int buf, bool diag, int lane)
+{
+    const unsigned char* core = S.core[buf];
+    int* rep = S.par[buf];
+    uint32_t vis_r[4], vis_c[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        vis_r[w] = ~__ballot_sync(0xffffffffu, core[w * 32 + lane] != 0);
+        vis_c[w] = diag ? 0xffffffffu : ~__ballot_sync(0xffffffffu, core[kT + w * 32 + lane] != 0);
+    }
+    for (int x = lane; x < 2 * kT; x += 32) rep[x] = x;
+    __syncwarp();
+    while (true) {
+        int w0 = 0;
+        while (w0 < 4 && vis_r[w0] == 0xffffffffu) ++w0;
+        if (w0 == 4) break;
+        const int r0 = w0 * 32 + __ffs(~vis_r[w0]) - 1;
+        uint32_t comp_r[4] = {0u, 0u, 0u, 0u}, comp_c[4] = {0u, 0u, 0u, 0u}, front[4] = {0u, 0u, 0u, 0u};
+        front[w0] = 1u << (r0 & 31);
+        comp_r[w0] = front[w0];
+        vis_r[w0] |= front[w0];
+        for (int step = 0; step < 2 * kT; ++step) {
+            // neighbours of the frontier rows: columns (or, diagonal pair, rows)
+            uint32_t acc[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                if ((front[w] >> lane) & 1u) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[c] |= S.rowmask[c][w * 32 + lane];
+                }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[c] = __reduce_or_sync(0xffffffffu, acc[c]);
+            bool grew = false;
+            if (diag) {
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    front[w] = acc[w] & ~vis_r[w];
+                    vis_r[w] |= front[w];
+                    comp_r[w] |= front[w];
+                    grew |= front[w] != 0u;
+                }
+            } else {
+                uint32_t newc[4];
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    newc[w] = acc[w] & ~vis_c[w];
+                    vis_c[w] |= newc[w];
+                    comp_c[w] |= newc[w];
+                }
+                // rows adjacent to the new columns
+                uint32_t accr[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                for (int w = 0; w < 4; ++w)
+                    if ((newc[w] >> lane) & 1u) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) accr[q] |= q == 0 ? S.colmask[0][w * 32 + lane]
+                                                              : q == 1 ? S.colmask[1][w * 32 + lane]
+                                                              : q == 2 ? S.colmask[2][w * 32 + lane]
+                                                                       : S.colmask[3][w * 32 + lane];
+                    }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    accr[q] = __reduce_or_sync(0xffffffffu, accr[q]);
+                    front[q] = accr[q] & ~vis_r[q];
+                    vis_r[q] |= front[q];
+                    comp_r[q] |= front[q];
+                    grew |= front[q] != 0u;
+                }
+            }
+            if (!grew) break;
+        }
+        // every node of the component points at r0
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            if ((comp_r[w] >> lane) & 1u) rep[w * 32 + lane] = r0;
+            if ((comp_c[w] >> lane) & 1u) rep[kT + w * 32 + lane] = r0;
+        }
+        __syncwarp();
+    }
+}
 
 template <int NS, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__ CUtensorMap mAh,
@@ -482,9 +572,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 if (lane == 0 && (diag ? et < kT : et >= kT)) S.colcore[buf][(et & (kT - 1)) >> 5] = m;
                 if (et == 0) { S.s_mm[buf][0] = INT_MAX; S.s_mm[buf][1] = -1; }
             }
-            if (MODE == 2) epi_sync();                          // s_mm initialised
+            if (MODE == 2) {
+                if (et == 0) S.edges[buf] = 0;
+                epi_sync();                                     // s_mm, edges initialised
+            }
             if (MODE == 2 && et < 2 * kT && cur.core_et) {
                 const int rr = gfind(A.parent, (int)(et < kT ? sa + et : sb + et - kT));
+                S.groot[buf][et] = rr;
                 atomicMin(&S.s_mm[buf][0], rr);
                 atomicMax(&S.s_mm[buf][1], rr);
             }
@@ -538,17 +632,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 // candidate columns: valid (and core-core, upper triangle for unions)
                 const int left = nb - c * 32;
                 uint32_t cand = !valid_r ? 0u : (left >= 32 ? 0xffffffffu : (left > 0 ? (1u << left) - 1u : 0u));
+                uint32_t cand_band = cand;
                 if (MODE == 2) {
                     cand = (work && core_r) ? cand & S.colcore[buf][c] : 0u;
-                    if (diag) {
-                        const int lo = r + 1 - c * 32;                // columns j > r
-                        cand &= lo <= 0 ? 0xffffffffu : (lo >= 32 ? 0u : ~((1u << lo) - 1u));
+                    cand_band = cand;
+                    if (diag) {                                       // band pairs once: j > r
+                        const int lo = r + 1 - c * 32;
+                        cand_band &= lo <= 0 ? 0xffffffffu : (lo >= 32 ? 0u : ~((1u << lo) - 1u));
                     }
                 }
                 inb[c2] = in_bits & cand;
-                band[c2] = keep_bits & ~in_bits & cand;
-                if (MODE == 1) S.rowmask[c][r] = inb[c2];
-                if (MODE == 1 && !diag) {
+                band[c2] = keep_bits & ~in_bits & cand_band;
+                S.rowmask[c][r] = inb[c2];
+                if (MODE == 2 && inb[c2]) atomicAdd(&S.edges[buf], __popc(inb[c2]));
+                if (!diag) {
                     // 32 x 32 bit transpose across the warp: lane k gets column c*32+k
                     uint32_t x = inb[c2];
 #pragma unroll
@@ -649,8 +746,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                     gunion(A.parent, A.row_pt, (int)(sa + r), (int)(sb + j));
                 }
             } else {
-                // local unions over the pair's 256 rows, then global unions
-                if (work) {
+                // components of the pair's core-core neighbour graph: dense pairs by a
+                // bitset breadth-first search on one warp (each row's and column's
+                // mask is OR-ed once), sparse ones by shared-memory unions per pair.
+                // Then each core row whose global root (read before) differs from its
+                // component head's joins it globally.
+                epi_sync();                                   // masks and edge count ready
+                const bool dense = S.edges[buf] > 1024;
+                if (work && dense && warp == 2) bfs_components(S, buf, diag, lane);
+                if (work && !dense) {
 #pragma unroll
                     for (int c2 = 0; c2 < kChunks; ++c2) {
                         uint32_t b = inb[c2];
@@ -665,12 +769,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 epi_sync();
                 if (work && et < 2 * kT && S.core[buf][et]) {
                     const int x = et;
-                    const int rx = lfind(S.par[buf], x);
-                    if (rx != x) {
-                        const int64_t row_x = x < kT ? sa + x : sb + (x - kT);
-                        const int64_t row_r = rx < kT ? sa + rx : sb + (rx - kT);
-                        gunion(A.parent, A.row_pt, (int)row_x, (int)row_r);
-                    }
+                    const int rx = dense ? S.par[buf][x] : lfind(S.par[buf], x);
+                    if (rx != x && S.groot[buf][x] != S.groot[buf][rx])
+                        gunion(A.parent, A.row_pt, S.groot[buf][x], S.groot[buf][rx]);
                 }
             }
         }
