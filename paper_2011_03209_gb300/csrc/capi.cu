@@ -338,7 +338,11 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     CK(parent.alloc(sizeof(int32_t) * R, s), "alloc");
     CK(root.alloc(sizeof(int32_t) * R, s), "alloc");
     CK(border.alloc(sizeof(unsigned long long) * R, s), "alloc");
-    if (cap) CK(nbr.alloc(sizeof(int32_t) * (size_t)R * cap, s), "alloc");
+    if (cap) {
+        // every writer fills the slots below cap it reserves; -1 marks any left
+        CK(nbr.alloc(sizeof(int32_t) * (size_t)R * cap, s), "alloc");
+        CK(cudaMemsetAsync(nbr.p, 0xff, sizeof(int32_t) * (size_t)R * cap, s), "memset");
+    }
     CK(cudaMemsetAsync(count.p, 0, sizeof(int32_t) * R, s), "memset");
 
     PassArgs a{};
@@ -358,15 +362,16 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     a.root = root.as<int32_t>();
     a.border = border.as<unsigned long long>();
     a.stats = stats.as<unsigned long long>();
-    // tensor-core pairs in (b, a) order: consecutive pairs, which run on
-    // neighbouring SMs at the same time, share a tile in L2
+    // tensor-core pairs in (a, b) order: pairs sharing tile A form the
+    // groups of the pass-1 kernel, and consecutive groups, which run on
+    // neighbouring SMs at the same time, share tiles in L2
     if (PL.n[kListTC] > 1) {
         Buf tmp;
         CK(tmp.alloc(sizeof(uint64_t) * PL.n[kListTC], s), "alloc");
         uint64_t* keys = PL.list[kListTC].as<uint64_t>();
         const int tb = bits_for(L.T);
-        CK(radix_sort_u64(keys, tmp.as<uint64_t>(), PL.n[kListTC], 0, tb, s), "sort pairs");
         CK(radix_sort_u64(keys, tmp.as<uint64_t>(), PL.n[kListTC], 32, 32 + tb, s), "sort pairs");
+        CK(radix_sort_u64(keys, tmp.as<uint64_t>(), PL.n[kListTC], 0, tb, s), "sort pairs");
     }
     // pass 1 flags the screened tile pairs holding a neighbour pair; only
     // those can matter to the union pass
@@ -413,10 +418,13 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         cudaEvent_t* e;
         ~EvGuard() { for (int i = 0; i < 2; ++i) if (e[i]) cudaEventDestroy(e[i]); }
     } tev_guard{tev};
+    Buf groups;
     if (use_tc) {
         TcArgs t1 = t;
         t1.ev_begin = tev[0];
         t1.ev_end = tev[1];
+        if ((rc = tc_groups(a_tc.pairs, PL.n[kListTC], &groups, &t1.n_groups, s))) return rc;
+        t1.groups = groups.as<int2>();
         if ((rc = tc_pass(1, a_tc, t1, PL.n[kListTC], s))) return rc;
     }
     else CK(simt_pass(1, a_tc, PL.n[kListTC], s), "pass 1 tc list");
@@ -426,11 +434,13 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     pt.mark();                                                    // 2
     CK(core_flags(a.count, R, min_pts, core.as<uint8_t>(), a.parent, a.border, a.stats, s), "core");
     pt.mark();                                                    // 3
+    CK(list_unions(a.count, a.nbr, cap, a.core, a.parent, a.row_pt, R, s), "list unions");
     CK(allin_pass(2, a_in, PL.n[kListAllIn], s), "pass 2 all-in");
     // Unions in rounds of growing tile distance b - a (tiles of one pivot
-    // region are adjacent): from the second round on, a pair is kept only if
-    // its core rows are not all joined yet, and pairs whose two sides are each
-    // already one component only need one neighbour pair.
+    // region are adjacent), after the unions along the neighbour lists: a
+    // pair is kept only if its core rows are not all joined yet (from the
+    // second round on when there are no lists), and pairs whose two sides are
+    // each already one component only need one neighbour pair.
     int64_t union_pairs = 0;
     auto union_rounds = [&](const PassArgs& base, int64_t n, bool tc) -> int {
         if (n == 0) return MAPPER_OK;
@@ -452,7 +462,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
                             cnt.as<unsigned long long>(), s), "select");
             const int2* list = sel.as<int2>();
             unsigned long long hc[2] = {0, 0};
-            if (k > 0) {
+            if (k > 0 || cap) {
                 CK(cudaMemcpyAsync(hc, cnt.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s), "copy");
                 CK(cudaStreamSynchronize(s), "sync");
                 CK(filter_joined(base, sel.as<int2>(), (int64_t)hc[0], kept.as<int2>(),
@@ -461,7 +471,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
             }
             CK(cudaMemcpyAsync(hc, cnt.p, sizeof(hc), cudaMemcpyDeviceToHost, s), "copy");
             CK(cudaStreamSynchronize(s), "sync");
-            const int64_t m = (int64_t)(k > 0 ? hc[1] : hc[0]);
+            const int64_t m = (int64_t)(k > 0 || cap ? hc[1] : hc[0]);
             PassArgs ar = base;
             ar.pairs = list;
             ar.pair_hit = nullptr;

@@ -70,6 +70,9 @@ cudaError_t border_from_lists(const int32_t* count, const int32_t* nbr, int cap,
                               int64_t R, unsigned long long* border, cudaStream_t s);
 // Row space -> cover-slot space: per slot the root slot of its node (or -1),
 // canonical point id (or -1), root flag, member flag and core flag.
+// Unions of each core row with the core rows of its pass-1 neighbour list.
+cudaError_t list_unions(const int32_t* count, const int32_t* nbr, int cap, const uint8_t* core, int32_t* parent,
+                        const int32_t* row_pt, int64_t R, cudaStream_t s);
 cudaError_t rows_to_slots(const int32_t* row_slot, const int32_t* row_pt, const uint8_t* core,
                           const int32_t* root, const unsigned long long* border, int64_t R,
                           int32_t* lab, int32_t* is_root, int32_t* is_member,

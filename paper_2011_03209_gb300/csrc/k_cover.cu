@@ -49,22 +49,33 @@ __global__ void range_partial_kernel(const double* __restrict__ f, int64_t n, in
     }
 }
 
+// One CTA per lens dimension reduces the partials (strided over threads).
 __global__ void range_final_kernel(const double* __restrict__ part, int nb, int m,
                                    double* __restrict__ lohi, int* __restrict__ nonfinite)
 {
-    const int j = threadIdx.x;
-    if (j >= m) return;
+    const int j = blockIdx.x;
     double lo = INFINITY, hi = -INFINITY;
     bool bad = false;
-    for (int b = 0; b < nb; ++b) {
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         const double* o = part + ((int64_t)j * nb + b) * 3;
         lo = fmin(lo, o[0]);
         hi = fmax(hi, o[1]);
         bad |= o[2] != 0.0;
     }
-    lohi[2 * j] = lo;
-    lohi[2 * j + 1] = hi;
-    if (bad && nonfinite) atomicOr(nonfinite, 1);
+    for (int o = 16; o; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    __shared__ double slo[32], shi[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { slo[warp] = lo; shi[warp] = hi; }
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { lo = fmin(lo, slo[w]); hi = fmax(hi, shi[w]); }
+        lohi[2 * j] = lo;
+        lohi[2 * j + 1] = hi;
+        if (bad && nonfinite) atomicOr(nonfinite, 1);
+    }
 }
 
 // bounds layout: dim 0: a[n0], b[n0]; dim 1: a[n1], b[n1]
@@ -179,7 +190,7 @@ cudaError_t lens_range_flag(const double* f, int64_t n, int m, double* lohi, int
     Buf part;
     MGB_TRY(part.alloc(sizeof(double) * 3 * nb * m, s));
     { range_partial_kernel<<<dim3(nb, m), 256, 0, s>>>(f, n, m, part.as<double>()); note_launch(); }
-    { range_final_kernel<<<1, 32, 0, s>>>(part.as<double>(), nb, m, lohi, nonfinite); note_launch(); }
+    { range_final_kernel<<<m, 256, 0, s>>>(part.as<double>(), nb, m, lohi, nonfinite); note_launch(); }
     return cudaGetLastError();
 }
 

@@ -510,13 +510,30 @@ __global__ void border_lists_kernel(const int32_t* __restrict__ count, const int
     unsigned long long best = ~0ull;
     for (int i = 0; i < k; ++i) {
         const int q = nbr[s * cap + i];
-        if (!core[q]) continue;
+        if (q < 0 || !core[q]) continue;
         const int r = root[q];
         const unsigned long long code =
             ((unsigned long long)(unsigned)(row_pt ? row_pt[r] : r) << 32) | (unsigned)r;
         best = code < best ? code : best;
     }
     border[s] = best;
+}
+
+// Unions along the neighbour lists of pass 1: a core row's list holds its
+// first cap neighbours, every one a certified neighbour pair; joining the
+// core ones merges most of each cluster before the union pass, which then
+// skips every tile pair whose core rows already share one root.
+__global__ void list_unions_kernel(const int32_t* __restrict__ count, const int32_t* __restrict__ nbr, int cap,
+                                   const uint8_t* __restrict__ core, int32_t* __restrict__ parent,
+                                   const int32_t* __restrict__ row_pt, int64_t R)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= R || !core[s]) return;
+    const int k = min(count[s], cap);
+    for (int i = 0; i < k; ++i) {
+        const int q = nbr[s * cap + i];
+        if (q >= 0 && core[q]) gunion(parent, row_pt, (int)s, q);
+    }
 }
 
 __global__ void rows_to_slots_kernel(const int32_t* __restrict__ row_slot, const int32_t* __restrict__ row_pt,
@@ -717,6 +734,15 @@ cudaError_t border_from_lists(const int32_t* count, const int32_t* nbr, int cap,
 {
     if (R == 0 || cap <= 0) return cudaSuccess;
     border_lists_kernel<<<grid_for(R), 256, 0, s>>>(count, nbr, cap, core, root, row_pt, R, border);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t list_unions(const int32_t* count, const int32_t* nbr, int cap, const uint8_t* core, int32_t* parent,
+                        const int32_t* row_pt, int64_t R, cudaStream_t s)
+{
+    if (R == 0 || cap == 0) return cudaSuccess;
+    list_unions_kernel<<<grid_for(R), 256, 0, s>>>(count, nbr, cap, core, parent, row_pt, R);
     note_launch();
     return cudaGetLastError();
 }

@@ -1,9 +1,9 @@
 // k_lens.cu -- filter (lens) kernels, "Mapper Interactive" §3 (filter
 // function f: X -> R or R^2) and §4.1 (L2 norm, a chosen column; PCA).
 //
-// Sums run in double, k ascending, with explicitly rounded operations
-// (__dadd_rn / __dmul_rn / __dsub_rn are never fused into FMAs), so each lens
-// value is the exact IEEE result of the defining expression. Rows are staged
+// The projection lens sums in double, k ascending, with explicitly rounded
+// operations (never fused), so it is the exact IEEE result of the defining
+// expression; the L2 lens rounds the exact sum of squares once. Rows are staged
 // through shared memory so the loads stay coalesced while every thread walks
 // its own row in order.
 #include "common.cuh"
@@ -59,6 +59,123 @@ __global__ void __launch_bounds__(kRows) lens_rows_kernel(const float* __restric
     }
     const int64_t row = row0 + tid;
     if (row < n) f[row * m + j] = (MODE == 0) ? __dsqrt_rn(acc) : acc;
+}
+
+// L2 lens from the exact sum of squares. A float x = m 2^(e-150) (m < 2^24)
+// squares to m^2 2^(2e-300) exactly; the row's squares are added as integers
+// in a 128-bit fixed-point accumulator aligned to the largest exponent (bits
+// of a square more than 2^110 below the largest square are dropped: a
+// relative change of at most d 2^-110), then converted to double once (round
+// to nearest, with a sticky bit). So the result is the exact sum rounded
+// once, within (d - 1) 2^-53 relative of the sequential double sum; sqrt is
+// correctly rounded. A row holding a NaN (an Inf) gets NaN (Inf). Each
+// square is below 2^48 units of the top word, so rows of d <= 32768 cannot
+// overflow it. One warp per row, 256 columns in registers at a time.
+__device__ __forceinline__ void add128(unsigned long long& hi, unsigned long long& lo, unsigned long long bh,
+                                       unsigned long long bl)
+{
+    const unsigned long long t = lo + bl;
+    hi += bh + (t < lo ? 1ull : 0ull);
+    lo = t;
+}
+
+constexpr int kL2Per = 8;                     // values per lane per 256-column chunk
+
+__device__ __forceinline__ void l2_load(const float* __restrict__ x, int k0, int d, int lane, unsigned* v)
+{
+#pragma unroll
+    for (int i = 0; i < kL2Per; ++i) {
+        const int k = k0 + i * 32 + lane;
+        v[i] = k < d ? __float_as_uint(__ldg(x + k)) : 0u;
+    }
+}
+
+// sqrt of (hi 2^64 + lo) 2^(2 emax - 364): the 128-bit value rounded once
+// to double (its top 64 bits, a sticky bit for the rest), then sqrt
+__device__ __forceinline__ double l2_finish(unsigned long long hi, unsigned long long lo, int emax, unsigned special)
+{
+    double val = 0.0;
+    if (hi != 0ull || lo != 0ull) {
+        const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+        unsigned long long top, rest;
+        if (lz < 64) {
+            top = lz ? (hi << lz) | (lo >> (64 - lz)) : hi;
+            rest = lz ? lo << lz : lo;
+        } else {
+            top = lo << (lz - 64);
+            rest = 0ull;
+        }
+        if (rest) top |= 1ull;
+        val = ldexp(__ull2double_rn(top), 64 - lz + 2 * emax - 300 - 64);
+    }
+    if (special) val = (special & 2u) ? __longlong_as_double(0x7FF8000000000000ll)
+                                      : __longlong_as_double(0x7FF0000000000000ll);
+    return __dsqrt_rn(val);
+}
+
+// A warp sums 32 rows in turn (all lanes on one row), lane i keeps row i's
+// sum, and the 32 double conversions and square roots then run side by side.
+__global__ void __launch_bounds__(256) lens_l2_exact_kernel(const float* __restrict__ X, int64_t n, int32_t d,
+                                                            int64_t ld, double* __restrict__ f, int m, int j)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool one_chunk = d <= 32 * kL2Per;
+    for (int64_t r0 = warp * 32; r0 < n; r0 += nwarp * 32) {
+        unsigned long long my_hi = 0ull, my_lo = 0ull;
+        int my_emax = 1;
+        unsigned my_special = 0u;
+        const int rows = n - r0 < 32 ? (int)(n - r0) : 32;
+        for (int i = 0; i < rows; ++i) {
+            const float* x = X + (r0 + i) * ld;
+            unsigned v[kL2Per];
+            int emax = 1;
+            unsigned special = 0u;                                 // 1: an Inf, 2: a NaN
+            for (int k0 = 0; k0 < d; k0 += 32 * kL2Per) {
+                l2_load(x, k0, d, lane, v);
+#pragma unroll
+                for (int t = 0; t < kL2Per; ++t) {
+                    const int e = (int)((v[t] >> 23) & 0xFFu);
+                    if (e == 255) special |= (v[t] & 0x7FFFFFu) ? 2u : 1u;
+                    if (v[t] & 0x7FFFFFFFu) emax = max(emax, min(e, 254));
+                }
+            }
+            emax = __reduce_max_sync(0xffffffffu, emax);
+            special = __reduce_or_sync(0xffffffffu, special);
+            unsigned long long hi = 0ull, lo = 0ull;
+            for (int k0 = 0; k0 < d; k0 += 32 * kL2Per) {
+                if (!one_chunk) l2_load(x, k0, d, lane, v);
+#pragma unroll
+                for (int t = 0; t < kL2Per; ++t) {
+                    int e = (int)((v[t] >> 23) & 0xFFu);
+                    unsigned long long mm = v[t] & 0x7FFFFFu;
+                    if (e == 0) e = 1; else mm |= 0x800000ull;
+                    e = min(e, 254);
+                    const unsigned long long sq = mm * mm;         // < 2^48, exact
+                    const int sh = 2 * (emax - e);                  // add (sq << 64) >> sh
+                    unsigned long long ah = 0ull, al = 0ull;
+                    if (sh == 0) ah = sq;
+                    else if (sh < 64) { ah = sq >> sh; al = sq << (64 - sh); }
+                    else if (sh < 112) al = sq >> (sh - 64);
+                    add128(hi, lo, ah, al);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long oh = __shfl_xor_sync(0xffffffffu, hi, o);
+                const unsigned long long ol = __shfl_xor_sync(0xffffffffu, lo, o);
+                add128(hi, lo, oh, ol);
+            }
+            if (lane == i) {
+                my_hi = hi;
+                my_lo = lo;
+                my_emax = emax;
+                my_special = special;
+            }
+        }
+        if (lane < rows) f[(r0 + lane) * m + j] = l2_finish(my_hi, my_lo, my_emax, my_special);
+    }
 }
 
 __global__ void lens_coord_kernel(const float* __restrict__ X, int64_t n, int64_t ld, int32_t col,
@@ -266,7 +383,13 @@ cudaError_t lens_l2(const float* X, int64_t n, int32_t d, int64_t ld, double* f,
                     cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    { lens_rows_kernel<0><<<div_up(n, kRows), kRows, 0, s>>>(X, n, d, ld, nullptr, nullptr, f, m, j); note_launch(); }
+    if (d <= 32768) {
+        const int blocks = (int)std::min<int64_t>(div_up(n, 8 * 32), 152 * 8);
+        lens_l2_exact_kernel<<<blocks, 256, 0, s>>>(X, n, d, ld, f, m, j);
+    } else {
+        lens_rows_kernel<0><<<div_up(n, kRows), kRows, 0, s>>>(X, n, d, ld, nullptr, nullptr, f, m, j);
+    }
+    note_launch();
     return cudaGetLastError();
 }
 

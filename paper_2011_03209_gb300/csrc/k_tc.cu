@@ -53,6 +53,8 @@ struct TcParams {
     const float* rn2;
     const float* rn;
     int64_t n_pairs;
+    const int2* groups;                       // W = 2: (pair, pair or -1) sharing tile A
+    int64_t n_groups;
     int nkb;                                  // K blocks per row
     double A1, A2, A3;                        // bound constants
     float A1f, A2f, A3f;                      // ... rounded up to FP32
@@ -137,13 +139,17 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
 // kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kT >> 3) << 17) |
                             ((uint32_t)(kT >> 4) << 24);
+// ... N = 256: tile A against two B tiles stacked in shared memory
+constexpr uint32_t kIdesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(2 * kT >> 3) << 17) |
+                             ((uint32_t)(kT >> 4) << 24);
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc)
+__device__ __forceinline__ void mma_bf16_id(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t acc)
 {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
             tmem),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc));
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar)
@@ -377,14 +383,29 @@ __device__ __forceinline__ void bfs_components(SmemTail& S, int buf, bool diag, 
     }
 }
 
-template <int NS, int MODE>
+template <int NS, int W>
+struct TcShape {
+    // blocks per stage: W = 1: Ah, Bh (, Al, Bl); W = 2: Ah (, Al), Bh0, Bh1 (, Bl0, Bl1)
+    static constexpr int kOps = W == 1 ? (NS == 1 ? 2 : 4) : (NS == 1 ? 3 : 6);
+    static constexpr int kStages = W == 1 ? (NS == 1 ? 4 : 3) : (NS == 1 ? 4 : 2);
+    static constexpr int kStageBytes = kOps * kBlk;
+    static constexpr int kAccCols = W * kT;               // TMEM columns of one accumulator
+};
+
+// W = 1: one tile pair per work item. W = 2: a group of one or two tile
+// pairs sharing tile A, computed as one N = 256 product (both B tiles
+// stacked), which halves the A loads; the epilogue takes its pairs in turn.
+template <int NS, int MODE, int W>
 __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__ CUtensorMap mAh,
                                                          const __grid_constant__ CUtensorMap mAl,
                                                          const TcParams P)
 {
-    constexpr int kOps = NS == 1 ? 2 : 4;                 // blocks per stage: Ah, Bh (, Al, Bl)
-    constexpr int kStages = NS == 1 ? 4 : 3;
-    constexpr int kStageBytes = kOps * kBlk;
+    constexpr int kOps = TcShape<NS, W>::kOps;
+    constexpr int kStages = TcShape<NS, W>::kStages;
+    constexpr int kStageBytes = TcShape<NS, W>::kStageBytes;
+    constexpr int kAccCols = TcShape<NS, W>::kAccCols;
+    const int64_t n_items = W == 1 ? P.n_pairs : P.n_groups;
+    auto group_at = [&](int64_t g) -> int2 { return W == 1 ? make_int2((int)g, -1) : P.groups[g]; };
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     SmemTail& S = *reinterpret_cast<SmemTail*>(smem + kStages * kStageBytes);
@@ -394,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&S.tmem_base)),
-                     "r"(2 * kT));
+                     "r"(2 * kAccCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 32) {
@@ -422,20 +443,36 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             int stage = 0;
             uint32_t phase = 0;
             int issued = 0;
-            for (int64_t q = blockIdx.x; q < P.n_pairs && !*abort; q += gridDim.x) {
-                int2 tp = A.pairs[q];
+            for (int64_t g = blockIdx.x; g < n_items && !*abort; g += gridDim.x) {
+                const int2 grp = group_at(g);
+                int2 tp = A.pairs[grp.x];
                 tp.y &= kPairTileMask;
-                const bool diag = tp.x == tp.y;
-                const uint32_t bytes = (uint32_t)((diag ? kOps / 2 : kOps) * kBlk);
+                const bool diag = W == 1 && tp.x == tp.y;
+                const int tb1 = W == 2 && grp.y >= 0 ? (A.pairs[grp.y].y & kPairTileMask) : -1;
+                const int nbt = tb1 >= 0 ? 2 : 1;
+                const uint32_t bytes = (uint32_t)((W == 1 ? (diag ? kOps / 2 : kOps)
+                                                          : (NS == 3 ? 2 + 2 * nbt : 1 + nbt)) * kBlk);
                 for (int kb = 0; kb < P.nkb; ++kb) {
                     if (!mbar_wait(&S.empty[stage], phase ^ 1, abort)) break;
                     unsigned char* st = smem + stage * kStageBytes;
                     mbar_expect_tx(&S.full[stage], bytes);
-                    tma_load(st, &mAh, kb * kKB, tp.x * kT, &S.full[stage]);
-                    if (!diag) tma_load(st + kBlk, &mAh, kb * kKB, tp.y * kT, &S.full[stage]);
-                    if (NS == 3) {
-                        tma_load(st + 2 * kBlk, &mAl, kb * kKB, tp.x * kT, &S.full[stage]);
-                        if (!diag) tma_load(st + 3 * kBlk, &mAl, kb * kKB, tp.y * kT, &S.full[stage]);
+                    if (W == 1) {
+                        tma_load(st, &mAh, kb * kKB, tp.x * kT, &S.full[stage]);
+                        if (!diag) tma_load(st + kBlk, &mAh, kb * kKB, tp.y * kT, &S.full[stage]);
+                        if (NS == 3) {
+                            tma_load(st + 2 * kBlk, &mAl, kb * kKB, tp.x * kT, &S.full[stage]);
+                            if (!diag) tma_load(st + 3 * kBlk, &mAl, kb * kKB, tp.y * kT, &S.full[stage]);
+                        }
+                    } else {
+                        constexpr int bo = NS == 3 ? 2 : 1;      // first B block
+                        tma_load(st, &mAh, kb * kKB, tp.x * kT, &S.full[stage]);
+                        tma_load(st + bo * kBlk, &mAh, kb * kKB, tp.y * kT, &S.full[stage]);
+                        if (nbt == 2) tma_load(st + (bo + 1) * kBlk, &mAh, kb * kKB, tb1 * kT, &S.full[stage]);
+                        if (NS == 3) {
+                            tma_load(st + kBlk, &mAl, kb * kKB, tp.x * kT, &S.full[stage]);
+                            tma_load(st + 4 * kBlk, &mAl, kb * kKB, tp.y * kT, &S.full[stage]);
+                            if (nbt == 2) tma_load(st + 5 * kBlk, &mAl, kb * kKB, tb1 * kT, &S.full[stage]);
+                        }
                     }
                     ++issued;
                     if (++stage == kStages) { stage = 0; phase ^= 1; }
@@ -460,29 +497,37 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             int stage = 0;
             uint32_t phase = 0;
             int it = 0;
-            for (int64_t q = blockIdx.x; q < P.n_pairs && !*abort; q += gridDim.x, ++it) {
-                int2 tp = A.pairs[q];
+            for (int64_t g = blockIdx.x; g < n_items && !*abort; g += gridDim.x, ++it) {
+                const int2 grp = group_at(g);
+                int2 tp = A.pairs[grp.x];
                 tp.y &= kPairTileMask;
-                const bool diag = tp.x == tp.y;
+                const bool diag = W == 1 && tp.x == tp.y;
+                const uint32_t idesc = W == 2 && grp.y >= 0 ? kIdesc2 : kIdesc;
                 const int buf = it & 1;
                 const uint32_t acc_phase = (uint32_t)((it >> 1) & 1);
                 if (!mbar_wait(&S.acc_empty[buf], acc_phase ^ 1, abort)) break;
                 tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(buf * kT);
+                const uint32_t d_tmem = tmem + (uint32_t)(buf * kAccCols);
                 bool ok = true;
                 for (int kb = 0; kb < P.nkb; ++kb) {
                     if (!mbar_wait(&S.full[stage], phase, abort)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t base = su32(smem + stage * kStageBytes);
-                    const uint32_t ah = base, bh = diag ? base : base + kBlk;
-                    const uint32_t al = base + 2 * kBlk, bl = diag ? al : base + 3 * kBlk;
+                    uint32_t ah, bh, al, bl;
+                    if (W == 1) {
+                        ah = base; bh = diag ? base : base + kBlk;
+                        al = base + 2 * kBlk; bl = diag ? al : base + 3 * kBlk;
+                    } else {
+                        ah = base; al = base + kBlk;
+                        bh = base + (NS == 3 ? 2 : 1) * kBlk; bl = base + 4 * kBlk;
+                    }
 #pragma unroll
                     for (int j = 0; j < kKB / 16; ++j) {
                         const uint32_t acc0 = (kb | j) ? 1u : 0u;
-                        mma_bf16(d_tmem, smem_desc(ah + 32 * j), smem_desc(bh + 32 * j), acc0);
+                        mma_bf16_id(d_tmem, smem_desc(ah + 32 * j), smem_desc(bh + 32 * j), idesc, acc0);
                         if (NS == 3) {
-                            mma_bf16(d_tmem, smem_desc(ah + 32 * j), smem_desc(bl + 32 * j), 1u);
-                            mma_bf16(d_tmem, smem_desc(al + 32 * j), smem_desc(bh + 32 * j), 1u);
+                            mma_bf16_id(d_tmem, smem_desc(ah + 32 * j), smem_desc(bl + 32 * j), idesc, 1u);
+                            mma_bf16_id(d_tmem, smem_desc(al + 32 * j), smem_desc(bh + 32 * j), idesc, 1u);
                         }
                     }
                     mma_commit(&S.empty[stage]);
@@ -536,18 +581,34 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 f.count_et = et < kT ? A.count[sa + et] : A.count[sb + et - kT];
             }
         };
+        // work items in turn, each one or (W = 2) two pairs: `it` counts pairs
+        // (staging buffers), `git` items (TMEM accumulators)
         Pre cur{};
-        if ((int64_t)blockIdx.x < P.n_pairs) prefetch(blockIdx.x, cur);
-        int it = 0;
+        int64_t g = blockIdx.x;
+        int2 grp = g < n_items ? group_at(g) : make_int2(-1, -1);
+        int h = 0;                                            // pair of the item
+        if (g < n_items) prefetch(grp.x, cur);
+        int it = 0, git = 0;
         int64_t screened = 0;
-        for (int64_t q = blockIdx.x; q < P.n_pairs; q += gridDim.x, ++it) {
+        while (g < n_items) {
+            const int64_t q = h ? grp.y : grp.x;
+            const bool last_sub = h == 1 || grp.y < 0;
+            int64_t g_next = g;
+            int h_next = 1;
+            int2 grp_next = grp;
+            if (last_sub) {
+                g_next = g + gridDim.x;
+                h_next = 0;
+                grp_next = g_next < n_items ? group_at(g_next) : make_int2(-1, -1);
+            }
             const int2 tp = cur.tp;
             const bool diag = tp.x == tp.y;
             const bool one_each = MODE == 2 && cur.one_each;
             const int na = cur.na, nb = cur.nb;
             const int64_t sa = (int64_t)tp.x * kT, sb = (int64_t)tp.y * kT;
             const int buf = it & 1;
-            const uint32_t acc_phase = (uint32_t)((it >> 1) & 1);
+            const int tbuf = git & 1;
+            const uint32_t acc_phase = (uint32_t)((git >> 1) & 1);
             const bool valid_r = r < na;
             const float na2 = cur.na2, nra = cur.nra;
             const int pre_count = cur.count_et;
@@ -584,10 +645,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             }
 
             // (2) wait for the accumulator; the barrier also publishes (1)
-            const bool bad = !mbar_wait(&S.acc_full[buf], acc_phase, abort) || *abort;
+            const bool bad = (h == 0 && !mbar_wait(&S.acc_full[tbuf], acc_phase, abort)) || *abort;
             if (epi_sync_or(bad)) break;
             tc_fence_after();
-            if (q + gridDim.x < P.n_pairs) prefetch(q + gridDim.x, cur);
+            if (g_next < n_items) prefetch(h_next ? grp_next.y : grp_next.x, cur);
 
             // (3) per-row limits: in iff u >= k_in, out iff u < k_out, where
             //     u = fl(2 acc - |b|^2); all FP32 with outward rounding
@@ -609,11 +670,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             for (int c2 = 0; c2 < kChunks; ++c2) {
                 const int c = half * kChunks + c2;
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * kT + c * 32), v);
-                if (c2 == kChunks - 1) {
+                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tbuf * kAccCols + h * kT + c * 32), v);
+                if (c2 == kChunks - 1 && last_sub) {
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&S.acc_empty[buf]);
+                    if (lane == 0) mbar_arrive(&S.acc_empty[tbuf]);
                 }
                 uint32_t in_bits = 0u, keep_bits = 0u;
                 const float4* nbn4 = reinterpret_cast<const float4*>(S.nbn[buf] + c * 32);
@@ -719,7 +780,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                         for (int w = 0; w < 4; ++w) tot += __popc(S.colmask[w][x]);
                     }
                     if (tot > 0) {
-                        if (tot > A.cap || pre_count >= A.cap) {
+                        if (pre_count >= A.cap) {
                             atomicAdd(&A.count[row], tot);          // no list entry can be due
                         } else {
                             const int old = atomicAdd(&A.count[row], tot);
@@ -774,6 +835,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                         gunion(A.parent, A.row_pt, S.groot[buf][x], S.groot[buf][rx]);
                 }
             }
+            ++it;
+            if (last_sub) ++git;
+            g = g_next;
+            h = h_next;
+            grp = grp_next;
         }
         if (MODE == 1 && et == 0 && screened) {
             atomicAdd(&A.stats[kStatScreened], (unsigned long long)screened);
@@ -786,7 +852,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
     __syncthreads();
     tc_fence_after();
     if (tid == 0 && S.abort) atomicExch(P.err, 1);
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kT));
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kAccCols));
 }
 
 // ------------------------------------------------ nearest pivot (layout)
@@ -1111,20 +1178,48 @@ bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int dp, int box_row
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NS>
+template <int NS, int W>
 constexpr int smem_bytes()
 {
-    return (NS == 1 ? 4 : 3) * (NS == 1 ? 2 : 4) * kBlk + (int)sizeof(SmemTail) + 1024;
+    return TcShape<NS, W>::kStages * TcShape<NS, W>::kStageBytes + (int)sizeof(SmemTail) + 1024;
 }
+static_assert(smem_bytes<3, 1>() <= 232448 && smem_bytes<1, 1>() <= 232448, "shared memory");
+static_assert(smem_bytes<3, 2>() <= 232448 && smem_bytes<1, 2>() <= 232448, "shared memory");
 
-template <int NS, int MODE>
+template <int NS, int MODE, int W>
 cudaError_t launch(const CUtensorMap& mh, const CUtensorMap& ml, const TcParams& p, int grid, cudaStream_t s)
 {
-    const int smem = smem_bytes<NS>();
-    cudaError_t e = cudaFuncSetAttribute(tc_kernel<NS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int smem = smem_bytes<NS, W>();
+    cudaError_t e =
+        cudaFuncSetAttribute(tc_kernel<NS, MODE, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    tc_kernel<NS, MODE><<<grid, kThreads, smem, s>>>(mh, ml, p);
+    tc_kernel<NS, MODE, W><<<grid, kThreads, smem, s>>>(mh, ml, p);
     return cudaGetLastError();
+}
+
+// Groups of the pass-1 pair list (sorted by tile A, then B): each pair at an
+// even position within its run of equal A leads a group, with the next pair
+// of the run if there is one.
+__global__ void group_lead_kernel(const int2* __restrict__ pairs, int64_t n, int32_t* __restrict__ lead)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int a = pairs[i].x;
+    int64_t lo = 0, hi = i;                               // first index of the run
+    while (lo < hi) {
+        const int64_t m = (lo + hi) >> 1;
+        if (pairs[m].x < a) lo = m + 1; else hi = m;
+    }
+    lead[i] = ((i - lo) & 1) == 0;
+}
+
+__global__ void group_emit_kernel(const int2* __restrict__ pairs, int64_t n, const int32_t* __restrict__ lead,
+                                  const int64_t* __restrict__ pos, int2* __restrict__ groups)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !lead[i]) return;
+    const bool two = i + 1 < n && pairs[i + 1].x == pairs[i].x;
+    groups[pos[i]] = make_int2((int)i, two ? (int)(i + 1) : -1);
 }
 
 }  // namespace
@@ -1248,12 +1343,18 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
     p.err = t.err;
     cudaError_t e = cudaMemsetAsync(t.queue_n, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ECUDA; }
-    const int grid = (int)std::min<int64_t>(n_pairs, t.num_sms);
+    const bool grouped = mode == 1 && t.groups != nullptr;
+    p.groups = grouped ? t.groups : nullptr;
+    p.n_groups = grouped ? t.n_groups : 0;
+    const int grid = (int)std::min<int64_t>(grouped ? t.n_groups : n_pairs, t.num_sms);
+    if (grid < 1) return MAPPER_OK;
     if (t.ev_begin) cudaEventRecord(t.ev_begin, s);
-    if (t.ns == 3)
-        e = mode == 1 ? launch<3, 1>(mh, ml, p, grid, s) : launch<3, 2>(mh, ml, p, grid, s);
+    if (grouped)
+        e = t.ns == 3 ? launch<3, 1, 2>(mh, ml, p, grid, s) : launch<1, 1, 2>(mh, ml, p, grid, s);
+    else if (t.ns == 3)
+        e = mode == 1 ? launch<3, 1, 1>(mh, ml, p, grid, s) : launch<3, 2, 1>(mh, ml, p, grid, s);
     else
-        e = mode == 1 ? launch<1, 1>(mh, ml, p, grid, s) : launch<1, 2>(mh, ml, p, grid, s);
+        e = mode == 1 ? launch<1, 1, 1>(mh, ml, p, grid, s) : launch<1, 2, 1>(mh, ml, p, grid, s);
     if (t.ev_end) cudaEventRecord(t.ev_end, s);
     note_launch();
     if (e != cudaSuccess) {
@@ -1275,6 +1376,38 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
         set_error(std::string("band recheck: ") + cudaGetErrorString(e));
         return MAPPER_ECUDA;
     }
+    return MAPPER_OK;
+}
+
+int tc_groups(const int2* pairs, int64_t n, Buf* groups, int64_t* n_groups, cudaStream_t s)
+{
+    *n_groups = 0;
+    if (n == 0) return MAPPER_OK;
+    Buf lead, pos;
+#define GK(expr)                                                                  \
+    do {                                                                          \
+        cudaError_t e_ = (expr);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            set_error(std::string("tc_groups: ") + cudaGetErrorString(e_));       \
+            return e_ == cudaErrorMemoryAllocation ? MAPPER_ENOMEM : MAPPER_ECUDA; \
+        }                                                                         \
+    } while (0)
+    GK(lead.alloc(sizeof(int32_t) * n, s));
+    GK(pos.alloc(sizeof(int64_t) * (n + 1), s));
+    const unsigned blocks = (unsigned)div_up(n, 256);
+    group_lead_kernel<<<blocks, 256, 0, s>>>(pairs, n, lead.as<int32_t>());
+    note_launch();
+    GK(cudaGetLastError());
+    GK(exclusive_scan_i32_to_i64(lead.as<int32_t>(), pos.as<int64_t>(), n, s));
+    int64_t ng = 0;
+    GK(cudaMemcpyAsync(&ng, pos.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GK(cudaStreamSynchronize(s));
+    GK(groups->alloc(sizeof(int2) * (size_t)ng, s));
+    group_emit_kernel<<<blocks, 256, 0, s>>>(pairs, n, lead.as<int32_t>(), pos.as<int64_t>(), groups->as<int2>());
+    note_launch();
+    GK(cudaGetLastError());
+#undef GK
+    *n_groups = ng;
     return MAPPER_OK;
 }
 

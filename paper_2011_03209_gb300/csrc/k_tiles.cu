@@ -340,18 +340,149 @@ __global__ void __launch_bounds__(256) tile_prep_kernel(const float* __restrict_
     if (tid == 0) rad[t] = (double)__uint_as_float(s_rad);
 }
 
-__global__ void seg_cent_kernel(const float* __restrict__ cent, const int32_t* __restrict__ tile_n,
-                                const int64_t* __restrict__ seg_toff, int dp,
-                                float* __restrict__ seg_cent)
+// tile_prep_kernel for dp <= 256 with the tile held in registers: 16 warps,
+// warp w owns rows w, w + 16, ..; lane l holds columns 4l .. 4l + 3 and
+// 128 + 4l .. 131 + 4l of each. X is read once and G written once; centroid
+// and radius come from the registers (same FP32 radius bound: each lane sums
+// at most dp/32 squares before the shuffle tree).
+constexpr int kPrepWarps = 16;
+constexpr int kPrepRows = kT / kPrepWarps;
+
+__global__ void __launch_bounds__(32 * kPrepWarps, 1) tile_prep_reg_kernel(
+    const float* __restrict__ X, int d, int64_t ld, int dp, bool vec, const int32_t* __restrict__ slot_point,
+    const int32_t* __restrict__ row_slot, const int32_t* __restrict__ tile_n, float* __restrict__ G,
+    int32_t* __restrict__ row_pt, float* __restrict__ cent, double* __restrict__ rad, int* nonfinite)
 {
-    const int64_t g = blockIdx.x;
-    for (int k = threadIdx.x; k < dp; k += blockDim.x) {
-        double s = 0.0, w = 0.0;
-        for (int64_t t = seg_toff[g]; t < seg_toff[g + 1]; ++t) {
-            s += (double)cent[t * dp + k] * (double)tile_n[t];
-            w += (double)tile_n[t];
+    __shared__ float4 s_part[kPrepWarps][64];
+    __shared__ float4 s_c[64];
+    __shared__ unsigned s_rad;
+    const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t row0 = (int64_t)t * kT;
+    const int nt = tile_n[t];
+    float4 v[kPrepRows][2];
+    bool bad = false;
+    int pt_l = -1;                                  // lane i < kPrepRows: point of row warp + 16 i
+    if (lane < kPrepRows) {
+        const int64_t row = row0 + warp + kPrepWarps * lane;
+        const int slot = row_slot[row];
+        pt_l = slot >= 0 ? slot_point[slot] : -1;
+        row_pt[row] = pt_l >= 0 ? pt_l : INT_MAX;
+    }
+#pragma unroll
+    for (int i = 0; i < kPrepRows; ++i) {
+        const int64_t pt = __shfl_sync(0xffffffffu, pt_l, i);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = h * 128 + 4 * lane;
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (pt >= 0 && k < d) {
+                const float* src = X + pt * ld + k;
+                if (vec && k + 3 < d) {
+                    x = __ldg(reinterpret_cast<const float4*>(src));
+                } else {
+                    x.x = src[0];
+                    if (k + 1 < d) x.y = src[1];
+                    if (k + 2 < d) x.z = src[2];
+                    if (k + 3 < d) x.w = src[3];
+                }
+            }
+            v[i][h] = x;
         }
-        seg_cent[g * dp + k] = (float)(s / w);
+    }
+    if (tid == 0) s_rad = 0u;
+    float4 part[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        part[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int k = h * 128 + 4 * lane;
+#pragma unroll
+        for (int i = 0; i < kPrepRows; ++i) {
+            const float4 x = v[i][h];
+            bad |= !isfinite(x.x) || !isfinite(x.y) || !isfinite(x.z) || !isfinite(x.w);
+            if (k < dp)
+                *reinterpret_cast<float4*>(G + (row0 + warp + kPrepWarps * i) * dp + k) = x;
+            part[h].x += x.x;
+            part[h].y += x.y;
+            part[h].z += x.z;
+            part[h].w += x.w;
+        }
+        s_part[warp][h * 32 + lane] = part[h];
+    }
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(nonfinite, 1);
+    if (tid < 64) {
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < kPrepWarps; ++w) {
+            const float4 q = s_part[w][tid];
+            c.x += q.x; c.y += q.y; c.z += q.z; c.w += q.w;
+        }
+        const float inv = (float)nt;
+        c.x /= inv; c.y /= inv; c.z /= inv; c.w /= inv;
+        s_c[tid] = c;
+        const int k = (tid >> 5) * 128 + 4 * (tid & 31);
+        if (k < dp) *reinterpret_cast<float4*>(cent + (int64_t)t * dp + k) = c;
+    }
+    __syncthreads();
+    const float infl = 1.0f + (float)(d + 64) * 1.1920929e-7f;
+    const float4 c0 = s_c[lane], c1 = s_c[32 + lane];
+#pragma unroll
+    for (int i = 0; i < kPrepRows; ++i) {
+        if (warp + kPrepWarps * i >= nt) continue;                 // warp-uniform
+        float s = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float4 x = v[i][h], c = h ? c1 : c0;
+            const int k = h * 128 + 4 * lane;
+            float u;
+            if (k < d)     { u = x.x - c.x; s = fmaf(u, u, s); }
+            if (k + 1 < d) { u = x.y - c.y; s = fmaf(u, u, s); }
+            if (k + 2 < d) { u = x.z - c.z; s = fmaf(u, u, s); }
+            if (k + 3 < d) { u = x.w - c.w; s = fmaf(u, u, s); }
+        }
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) atomicMax(&s_rad, __float_as_uint(__fmul_ru(__fsqrt_ru(s), infl)));
+    }
+    __syncthreads();
+    if (tid == 0) rad[t] = (double)__uint_as_float(s_rad);
+}
+
+// Segment centre: the row-weighted mean of its tile centres, in double.
+// With dp <= 512 the CTA splits the tiles over blockDim / dp thread groups
+// (one thread per column in each) and adds the group sums at the end.
+__global__ void __launch_bounds__(1024) seg_cent_kernel(const float* __restrict__ cent,
+                                                        const int32_t* __restrict__ tile_n,
+                                                        const int64_t* __restrict__ seg_toff, int dp,
+                                                        float* __restrict__ seg_cent)
+{
+    __shared__ double s_sum[2][1024];
+    const int64_t g = blockIdx.x;
+    const int W = dp <= 512 ? (int)blockDim.x / dp : 1;
+    const int w = dp <= 512 ? (int)threadIdx.x / dp : 0;
+    const int64_t t0 = seg_toff[g], t1 = seg_toff[g + 1];
+    for (int k0 = 0; k0 < dp; k0 += (dp <= 512 ? dp : (int)blockDim.x)) {
+        const int k = dp <= 512 ? (int)threadIdx.x % dp : k0 + (int)threadIdx.x;
+        double sum = 0.0, wt = 0.0;
+        if (w < W && k < dp) {
+            for (int64_t t = t0 + w; t < t1; t += W) {
+                sum += (double)cent[t * dp + k] * (double)tile_n[t];
+                wt += (double)tile_n[t];
+            }
+        }
+        if (W > 1) {
+            if (w < W) {
+                s_sum[0][threadIdx.x] = sum;
+                s_sum[1][threadIdx.x] = wt;
+            }
+            __syncthreads();
+            if (w == 0) {
+                for (int v = 1; v < W; ++v) {
+                    sum += s_sum[0][v * dp + k];
+                    wt += s_sum[1][v * dp + k];
+                }
+            }
+            __syncthreads();
+        }
+        if (w == 0 && k < dp) seg_cent[g * dp + k] = (float)(sum / wt);
     }
 }
 
@@ -433,24 +564,24 @@ __device__ __forceinline__ float dist_sum32(const float* __restrict__ x, const f
 }
 
 // Segment radius: max over its tiles of |c_t - c_seg| + r_t (upper bounds).
-__global__ void __launch_bounds__(256) seg_rad_kernel(const float* __restrict__ cent,
-                                                      const double* __restrict__ rad,
-                                                      const float* __restrict__ seg_cent,
-                                                      const int64_t* __restrict__ seg_toff, int dp,
-                                                      double rel, double* __restrict__ seg_rad)
+__global__ void __launch_bounds__(1024) seg_rad_kernel(const float* __restrict__ cent,
+                                                       const double* __restrict__ rad,
+                                                       const float* __restrict__ seg_cent,
+                                                       const int64_t* __restrict__ seg_toff, int dp,
+                                                       double rel, double* __restrict__ seg_rad)
 {
-    __shared__ double s_max[8];
+    __shared__ double s_max[32];
     const int64_t g = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double m = 0.0;
-    for (int64_t t = seg_toff[g] + warp; t < seg_toff[g + 1]; t += 8) {
+    for (int64_t t = seg_toff[g] + warp; t < seg_toff[g + 1]; t += nw) {
         const float ssum = dist_sum32(cent + t * dp, seg_cent + g * dp, dp, lane);
         m = fmax(m, sqrt((double)ssum * (1.0 + rel)) * (1.0 + 1e-15) + rad[t]);
     }
     if (lane == 0) s_max[warp] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < 8; ++w) m = fmax(m, s_max[w]);
+        for (int w = 1; w < nw; ++w) m = fmax(m, s_max[w]);
         seg_rad[g] = m * (1.0 + 1e-15);
     }
 }
@@ -474,6 +605,7 @@ __global__ void elem_segs_kernel(const int32_t* __restrict__ seg_elem, int64_t n
 // classified by tile spheres: out, all-in, or mixed (tensor-core list when
 // a and b share a segment, hence a centre, else CUDA-core list).
 constexpr int kMaxSegList = 1024;
+constexpr int kClsPer = 8;                     // tiles b per warp step
 
 __global__ void __launch_bounds__(256) classify_kernel(const int64_t* __restrict__ eseg_off,
                                                        const int64_t* __restrict__ seg_toff,
@@ -520,10 +652,31 @@ __global__ void __launch_bounds__(256) classify_kernel(const int64_t* __restrict
     for (int li = 0; li < nlist; ++li) {
         const int64_t gb = listed ? s_seg[li] : ga + li;
         const int64_t t0 = gb == ga ? ta : seg_toff[gb], t1 = seg_toff[gb + 1];
-        for (int64_t tb = t0 + warp; tb < t1; tb += 8) {
+        // each warp takes kClsPer tiles b at a time (independent sums, each
+        // with the lane and shuffle order of dist_sum32); lane u classifies b_u
+        for (int64_t tb0 = t0 + warp * kClsPer; tb0 < t1; tb0 += 8 * kClsPer) {
+            float ss[kClsPer];
+#pragma unroll
+            for (int u = 0; u < kClsPer; ++u) ss[u] = 0.f;
+            for (int k = lane; k < dp; k += 32) {
+                const float a = s_ca[k];
+#pragma unroll
+                for (int u = 0; u < kClsPer; ++u) {
+                    if (tb0 + u < t1) {
+                        const float v = a - cent[(tb0 + u) * dp + k];
+                        ss[u] = fmaf(v, v, ss[u]);
+                    }
+                }
+            }
             float ssum = 0.f;
-            if (tb != ta) ssum = dist_sum32(s_ca, cent + tb * dp, dp, lane);
-            if (lane == 0) {
+#pragma unroll
+            for (int u = 0; u < kClsPer; ++u) {
+                for (int o = 16; o; o >>= 1) ss[u] += __shfl_xor_sync(0xffffffffu, ss[u], o);
+                if (lane == u) ssum = ss[u];
+            }
+            const int64_t tb = tb0 + lane;
+            if (tb == ta) ssum = 0.f;
+            if (lane < kClsPer && tb < t1) {
                 const double Dlo = sqrt((double)ssum * (1.0 - rel)) * (1.0 - 1e-15);
                 const double Dhi = sqrt((double)ssum * (1.0 + rel)) * (1.0 + 1e-15);
                 const double rb = rad[tb];
@@ -542,7 +695,7 @@ __global__ void __launch_bounds__(256) classify_kernel(const int64_t* __restrict
             }
         }
     }
-    if (lane == 0 && n_out) atomicAdd(&s_out, (unsigned long long)n_out);
+    if (n_out) atomicAdd(&s_out, (unsigned long long)n_out);
     __syncthreads();
     if (threadIdx.x == 0 && s_out) atomicAdd(&counts[3], s_out);
 }
@@ -650,17 +803,24 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
     tile_info_kernel<<<grid_for(nseg), 256, 0, s>>>(seg_start.as<int64_t>(), seg_toff.as<int64_t>(),
                                                     seg_elem.as<int32_t>(), nseg, L->tile_n.as<int32_t>(),
                                                     L->tile_seg.as<int32_t>(), L->tile_elem.as<int32_t>());
-    tile_prep_kernel<<<(unsigned)T, 256, 0, s>>>(X, d, ld, dp, slot_point, L->row_slot.as<int32_t>(),
-                                                 L->tile_n.as<int32_t>(), L->G.as<float>(),
-                                                 L->row_pt.as<int32_t>(), L->tile_cent.as<float>(),
-                                                 L->tile_rad.as<double>(), nonfinite);
-    seg_cent_kernel<<<(unsigned)nseg, 256, 0, s>>>(L->tile_cent.as<float>(), L->tile_n.as<int32_t>(),
+    if (dp <= 256) {
+        const bool vec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
+        tile_prep_reg_kernel<<<(unsigned)T, 32 * kPrepWarps, 0, s>>>(
+            X, d, ld, dp, vec, slot_point, L->row_slot.as<int32_t>(), L->tile_n.as<int32_t>(), L->G.as<float>(),
+            L->row_pt.as<int32_t>(), L->tile_cent.as<float>(), L->tile_rad.as<double>(), nonfinite);
+    } else {
+        tile_prep_kernel<<<(unsigned)T, 256, 0, s>>>(X, d, ld, dp, slot_point, L->row_slot.as<int32_t>(),
+                                                     L->tile_n.as<int32_t>(), L->G.as<float>(),
+                                                     L->row_pt.as<int32_t>(), L->tile_cent.as<float>(),
+                                                     L->tile_rad.as<double>(), nonfinite);
+    }
+    seg_cent_kernel<<<(unsigned)nseg, 1024, 0, s>>>(L->tile_cent.as<float>(), L->tile_n.as<int32_t>(),
                                                   seg_toff.as<int64_t>(), dp, L->seg_cent.as<float>());
     note_launch(4);
     TK(cudaGetLastError());
     TK(L->seg_rad.alloc(sizeof(double) * nseg, s));
     const double rel = (double)(dp / 32 + 12) * std::ldexp(1.0, -23);
-    seg_rad_kernel<<<(unsigned)nseg, 256, 0, s>>>(L->tile_cent.as<float>(), L->tile_rad.as<double>(),
+    seg_rad_kernel<<<(unsigned)nseg, 1024, 0, s>>>(L->tile_cent.as<float>(), L->tile_rad.as<double>(),
                                                  L->seg_cent.as<float>(), seg_toff.as<int64_t>(), dp, rel,
                                                  L->seg_rad.as<double>());
     note_launch();

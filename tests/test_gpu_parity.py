@@ -1,11 +1,15 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Every comparison is exact: the lens is the same IEEE double, the cover
+The L2 lens is the exact sum of squares rounded once, then a correctly
+rounded square root: it must equal sqrt(fsum(x_k^2)) bit for bit and lie
+within 1e-12 relative of the oracle's sequential double sum. Every other
+comparison is exact: coordinate and projection lenses, the cover
 membership, per-slot core flags and cluster labels, node memberships and
 edges are equal element by element. The oracle is fed the GPU's lens (and,
 for principal-component lenses, checked against the GPU's basis), so a lens
 rounding difference could not hide a clustering difference."""
 import functools
+import math
 
 import numpy as np
 import pytest
@@ -36,6 +40,16 @@ def run_gpu(ctx, X, kinds, args, nint, ov, eps, min_pts, prec=mg.FP32):
     out["labels"], out["core"] = g.clusters().numpy(len(out["elem_points"]))
     out["stats"] = g.stats()
     return out
+
+
+def assert_l2_lens(X, f):
+    """L2 lens: correctly rounded exact sum (math.fsum of the squares, which
+    are exact in double), and 1e-12 relative of the oracle's sequential sum."""
+    X64 = np.asarray(X, dtype=np.float64)
+    exact = np.array([np.sqrt(math.fsum(r * r)) for r in X64])
+    assert np.array_equal(f, exact)
+    ref = oracle.lens_l2(np.asarray(X, dtype=np.float32))
+    assert np.all(np.abs(f - ref) <= 1e-12 * np.abs(ref))
 
 
 def assert_same_graph(X, res, nint, ov, eps, min_pts):
@@ -76,7 +90,7 @@ def test_tiny_l2(ctx, n, d, seed, n_int, ov, q, min_pts, prec):
     X = synth.tiny_random(n, d, seed, scale=2.0)
     eps = _eps(X, q, seed)
     res = run_gpu(ctx, X, (0,), (0,), (n_int,), (ov,), eps, min_pts, prec)
-    assert np.array_equal(res["lens"][:, 0], oracle.lens_l2(X))
+    assert_l2_lens(X, res["lens"][:, 0])
     assert_same_graph(X, res, (n_int,), (ov,), eps, min_pts)
 
 
@@ -126,6 +140,27 @@ def test_circle_cycle_graph(ctx):
     res = run_gpu(ctx, X, (1,), (1,), (6,), (0.3,), 0.05, 2)
     ref = assert_same_graph(X, res, (6,), (0.3,), 0.05, 2)
     assert len(ref["node_elem"]) == 10 and len(ref["edges"]) == 10
+
+
+@pytest.mark.parametrize("d", [1, 7, 33, 256, 700])
+def test_l2_lens_exponent_range(ctx, d):
+    """L2 lens over rows mixing magnitudes from subnormal to near overflow,
+    zero rows and ragged widths; X holding an Inf or a NaN is rejected."""
+    rng = np.random.default_rng(d)
+    n = 300
+    X = (rng.standard_normal((n, d)) * np.exp2(rng.integers(-140, 120, (n, d)))).astype(np.float32)
+    X[5] = 0.0
+    X[6, 0] = np.float32(1e-45)                      # a lone subnormal
+    X[7] = np.float32(3e38) * (rng.random(d) < 0.5)  # near the float maximum
+    f, _ = mg.mapper_lens(ctx, torch.from_numpy(X).to("cuda:0"), (0,), (0,))
+    f = f.cpu().numpy()[:, 0]
+    assert f[5] == 0.0
+    assert_l2_lens(X, f)
+    for bad in (np.inf, np.nan):
+        Y = X.copy()
+        Y[8, d // 2] = bad
+        with pytest.raises(mg.MapperError):
+            mg.mapper_lens(ctx, torch.from_numpy(Y).to("cuda:0"), (0,), (0,))
 
 
 def test_pca_lens_basis_and_bits(ctx):
@@ -208,7 +243,7 @@ def test_clusters_1m_d256_sampled(ctx, prec):
     res = run_gpu(ctx, w.X, w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, prec)
     rng = np.random.default_rng(0)
     rows = rng.choice(w.n, 4000, replace=False)
-    assert np.array_equal(res["lens"][rows, 0], oracle.lens_l2(w.X[rows]))
+    assert_l2_lens(w.X[rows], res["lens"][rows, 0])
     offs, pts = oracle.cover(res["lens"], w.n_intervals, w.overlap)
     assert np.array_equal(offs, res["elem_offsets"]) and np.array_equal(pts, res["elem_points"])
     sizes = np.diff(offs)
