@@ -245,7 +245,6 @@ def run_ours(args):
         e2e_ms = float(t.item())
 
     st = stats[-1]
-    sizes = np.load(os.path.join(ROOT, "_work", "c3_sizes.npy")) if False else None  # noqa
     pairs = st["pairs_screened"]                       # unordered pairs incl. self, pass 1
     kpairs = st["count_kernel_pairs"]                  # ... of them screened by the main kernel
     kms = float(np.mean([s["ms_count_kernel"] for s in stats]))

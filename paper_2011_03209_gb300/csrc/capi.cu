@@ -347,6 +347,9 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
 
     PassArgs a{};
     a.G = L.G.as<float>();
+    a.X = X;
+    a.ld = ld;
+    a.xvec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
     a.dp = dp;
     a.d = d;
     a.tile_n = L.tile_n.as<int32_t>();
@@ -846,8 +849,11 @@ int mapper_graph(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t 
     int64_t ldd = ld;
     if (is_host_pointer(X)) {
         CK(xdev.alloc(sizeof(float) * (size_t)n * d, s), "alloc X");
-        CK(cudaMemcpy2DAsync(xdev.p, sizeof(float) * d, X, sizeof(float) * ld, sizeof(float) * d, n,
-                             cudaMemcpyHostToDevice, s), "copy X");
+        if (ld == d)
+            CK(cudaMemcpyAsync(xdev.p, X, sizeof(float) * (size_t)n * d, cudaMemcpyHostToDevice, s), "copy X");
+        else
+            CK(cudaMemcpy2DAsync(xdev.p, sizeof(float) * d, X, sizeof(float) * ld, sizeof(float) * d, n,
+                                 cudaMemcpyHostToDevice, s), "copy X");
         Xd = xdev.as<float>();
         ldd = d;
     }
@@ -933,8 +939,11 @@ int mapper_graph_sweep(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, in
     int64_t ldd = ld;
     if (is_host_pointer(X)) {
         CK(xdev.alloc(sizeof(float) * (size_t)n * d, s), "alloc X");
-        CK(cudaMemcpy2DAsync(xdev.p, sizeof(float) * d, X, sizeof(float) * ld, sizeof(float) * d, n,
-                             cudaMemcpyHostToDevice, s), "copy X");
+        if (ld == d)
+            CK(cudaMemcpyAsync(xdev.p, X, sizeof(float) * (size_t)n * d, cudaMemcpyHostToDevice, s), "copy X");
+        else
+            CK(cudaMemcpy2DAsync(xdev.p, sizeof(float) * d, X, sizeof(float) * ld, sizeof(float) * d, n,
+                                 cudaMemcpyHostToDevice, s), "copy X");
         Xd = xdev.as<float>();
         ldd = d;
     }

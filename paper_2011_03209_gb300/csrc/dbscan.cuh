@@ -29,7 +29,10 @@ enum : int { kListAllIn = 0, kListTC = 1, kListSimt = 2, kListCount = 3 };
 //   implicit mode: every tile pair of every element, elements given by
 //     elem_off (rows) and pair_off (tile pairs), rows = cover slots.
 struct PassArgs {
-    const float* G;              // FP32 rows, pitch dp floats (zero padded)
+    const float* G;              // FP32 rows, pitch dp floats (zero padded), or nullptr:
+    const float* X;              //   then row r is X + row_pt[r] * ld (d columns)
+    int64_t ld;
+    bool xvec;                   //   X rows 16-byte aligned (float4 loads)
     int dp;                      // row pitch (multiple of 32)
     int d;                       // true dimension
     const int2* pairs;           // explicit list, or nullptr
@@ -52,6 +55,26 @@ struct PassArgs {
     unsigned long long* border;  // pass 3 output: (canonical point << 32 | root row), min
     unsigned long long* stats;   // kStat* counters
 };
+
+// Row `row` of a pass (the tile layout's FP32 rows, or the input rows).
+__device__ __forceinline__ const float* pass_row(const PassArgs& A, int64_t row)
+{
+    return A.G ? A.G + row * A.dp : A.X + (int64_t)A.row_pt[row] * A.ld;
+}
+
+// Columns 4 k4 .. 4 k4 + 3 of a row from pass_row (zero from column d on).
+__device__ __forceinline__ float4 pass_ld4(const PassArgs& A, const float* p, int k4)
+{
+    if (A.G) return reinterpret_cast<const float4*>(p)[k4];
+    const int k = 4 * k4;
+    if (A.xvec && k + 3 < A.d) return *reinterpret_cast<const float4*>(p + k);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k < A.d) v.x = p[k];
+    if (k + 1 < A.d) v.y = p[k + 1];
+    if (k + 2 < A.d) v.z = p[k + 2];
+    if (k + 3 < A.d) v.w = p[k + 3];
+    return v;
+}
 
 // FP32 screen thresholds for eps2 at dimension d: a pair is certainly a
 // neighbour when the FP32 screen value is <= *lo, certainly not when > *hi.
@@ -113,7 +136,7 @@ struct TileLayout {
     int n_groups = 0;            // pivot groups (outliers form group n_groups)
     Buf row_slot;                // [R] int32 cover slot, -1 for padding
     Buf row_pt;                  // [R] int32 point, INT32_MAX for padding
-    Buf G;                       // [R x dp] FP32 rows
+    Buf G;                       // [R x dp] FP32 rows (unset on the tensor-core path for dp <= 256)
     Buf tile_n, tile_seg, tile_elem;      // [T] int32
     Buf tile_cent;               // [T x dp] FP32 centre
     Buf tile_rad;                // [T] FP64 upper bound of the rows' distance to it

@@ -132,7 +132,7 @@ struct Decider {
     {
         if (s <= A.lo_thr) return true;
         if (s > A.hi_thr && s <= FLT_MAX) return false;
-        const double d2 = exact_sqdist(A.G + row_a * A.dp, A.G + row_b * A.dp, A.d);
+        const double d2 = exact_sqdist(pass_row(A, row_a), pass_row(A, row_b), A.d);
         atomicAdd(&A.stats[kStatBand], 1ull);
         atomicAdd(&A.stats[kStatFp64], 1ull);
         if (count_tie && fabs(d2 - A.eps2) <= A.tie_thr) atomicAdd(&A.stats[kStatTies], 1ull);
@@ -254,8 +254,8 @@ __global__ void __launch_bounds__(256, 2) simt_pass_kernel(const PassArgs A)
             const int idx = tid + 256 * v;       // float4 index in the 128 x 32 chunk
             const int r = idx >> 3, k4 = (idx & 7) * 4;
             float4 xa = make_float4(0.f, 0.f, 0.f, 0.f), xb = xa;
-            if (r < na) xa = *reinterpret_cast<const float4*>(A.G + (sa + r) * A.dp + k0 + k4);
-            if (r < nb) xb = *reinterpret_cast<const float4*>(A.G + (sb + r) * A.dp + k0 + k4);
+            if (r < na) xa = pass_ld4(A, pass_row(A, sa + r), (k0 + k4) >> 2);
+            if (r < nb) xb = pass_ld4(A, pass_row(A, sb + r), (k0 + k4) >> 2);
             As[k4 + 0][r] = xa.x; As[k4 + 1][r] = xa.y; As[k4 + 2][r] = xa.z; As[k4 + 3][r] = xa.w;
             Bs[k4 + 0][r] = xb.x; Bs[k4 + 1][r] = xb.y; Bs[k4 + 2][r] = xb.z; Bs[k4 + 3][r] = xb.w;
         }

@@ -63,20 +63,41 @@ __global__ void __launch_bounds__(kRows) lens_rows_kernel(const float* __restric
 
 // L2 lens from the exact sum of squares. A float x = m 2^(e-150) (m < 2^24)
 // squares to m^2 2^(2e-300) exactly; the row's squares are added as integers
-// in a 128-bit fixed-point accumulator aligned to the largest exponent (bits
-// of a square more than 2^110 below the largest square are dropped: a
-// relative change of at most d 2^-110), then converted to double once (round
-// to nearest, with a sticky bit). So the result is the exact sum rounded
-// once, within (d - 1) 2^-53 relative of the sequential double sum; sqrt is
-// correctly rounded. A row holding a NaN (an Inf) gets NaN (Inf). Each
-// square is below 2^48 units of the top word, so rows of d <= 32768 cannot
-// overflow it. One warp per row, 256 columns in registers at a time.
+// and the exact sum is rounded to double once, then a correctly rounded sqrt.
+// Per lane and 256-column chunk, with el the lane's largest exponent:
+//   e >= el - 6:       (m << (e - el + 6))^2 into a 64-bit sum (unit 2^(2el-312))
+//   el - 13 <= e < ..: (m << (e - el + 13))^2 into a second one (2^(2el-326))
+// (one multiply-add each, at most 8 terms below 2^60); rarer small values
+// and subnormals go to a 128-bit fixed-point sum whose unit is 2^(2emax-364)
+// (emax: the row's largest exponent), where the two 64-bit sums also land at
+// the end of each chunk. Bits of that sum below its unit are dropped: a
+// relative change of at most d 2^-110, so the result is the exact sum rounded
+// once up to that, within (d - 1) 2^-53 relative of a sequential double sum.
+// A row holding a NaN (an Inf) gets NaN (Inf); d <= 32768 keeps the 128-bit
+// sum below 2^127. One warp per row, 256 columns in registers at a time.
 __device__ __forceinline__ void add128(unsigned long long& hi, unsigned long long& lo, unsigned long long bh,
                                        unsigned long long bl)
 {
     const unsigned long long t = lo + bl;
     hi += bh + (t < lo ? 1ull : 0ull);
     lo = t;
+}
+
+// (hi, lo) += v 2^f, bits below 2^0 dropped (f < 64)
+__device__ __forceinline__ void add128_shifted(unsigned long long& hi, unsigned long long& lo, unsigned long long v,
+                                               int f)
+{
+    if (v == 0ull) return;
+    if (f > 0) add128(hi, lo, v >> (64 - f), v << f);
+    else if (f == 0) add128(hi, lo, 0ull, v);
+    else if (f > -64) add128(hi, lo, 0ull, v >> -f);
+}
+
+__device__ __forceinline__ unsigned long long mad_wide(uint32_t a, unsigned long long acc)
+{
+    unsigned long long r;
+    asm("mad.wide.u32 %0, %1, %1, %2;" : "=l"(r) : "r"(a), "l"(acc));
+    return r;
 }
 
 constexpr int kL2Per = 8;                     // values per lane per 256-column chunk
@@ -113,6 +134,17 @@ __device__ __forceinline__ double l2_finish(unsigned long long hi, unsigned long
     return __dsqrt_rn(val);
 }
 
+// the largest biased exponent of the lane's values (254 for Inf/NaN, which
+// are flagged separately), at least 1
+__device__ __forceinline__ int lane_emax(const unsigned* v, int* raw)
+{
+    int el = 1;
+#pragma unroll
+    for (int t = 0; t < kL2Per; ++t) el = max(el, (int)((v[t] >> 23) & 0xFFu));
+    *raw = el;
+    return min(el, 254);
+}
+
 // A warp sums 32 rows in turn (all lanes on one row), lane i keeps row i's
 // sum, and the 32 double conversions and square roots then run side by side.
 __global__ void __launch_bounds__(256) lens_l2_exact_kernel(const float* __restrict__ X, int64_t n, int32_t d,
@@ -130,36 +162,49 @@ __global__ void __launch_bounds__(256) lens_l2_exact_kernel(const float* __restr
         for (int i = 0; i < rows; ++i) {
             const float* x = X + (r0 + i) * ld;
             unsigned v[kL2Per];
-            int emax = 1;
-            unsigned special = 0u;                                 // 1: an Inf, 2: a NaN
+            int emax = 1, raw_max = 0;
             for (int k0 = 0; k0 < d; k0 += 32 * kL2Per) {
                 l2_load(x, k0, d, lane, v);
+                int raw;
+                emax = max(emax, lane_emax(v, &raw));
+                raw_max = max(raw_max, raw);
+            }
+            emax = __reduce_max_sync(0xffffffffu, emax);
+            unsigned special = 0u;                                 // 1: an Inf, 2: a NaN
+            if (__any_sync(0xffffffffu, raw_max == 255)) {
+                for (int k0 = 0; k0 < d; k0 += 32 * kL2Per) {
+                    l2_load(x, k0, d, lane, v);
+#pragma unroll
+                    for (int t = 0; t < kL2Per; ++t)
+                        if (((v[t] >> 23) & 0xFFu) == 0xFFu) special |= (v[t] & 0x7FFFFFu) ? 2u : 1u;
+                }
+                special = __reduce_or_sync(0xffffffffu, special);
+            }
+            unsigned long long hi = 0ull, lo = 0ull;
+            for (int k0 = 0; k0 < d && !special; k0 += 32 * kL2Per) {
+                if (!one_chunk) l2_load(x, k0, d, lane, v);
+                int raw;
+                const int el = lane_emax(v, &raw);
+                unsigned long long s1 = 0ull, s2 = 0ull;
 #pragma unroll
                 for (int t = 0; t < kL2Per; ++t) {
                     const int e = (int)((v[t] >> 23) & 0xFFu);
-                    if (e == 255) special |= (v[t] & 0x7FFFFFu) ? 2u : 1u;
-                    if (v[t] & 0x7FFFFFFFu) emax = max(emax, min(e, 254));
+                    const int sh1 = e - el + 6;
+                    if (e != 0 && sh1 >= 0) {
+                        s1 = mad_wide(((v[t] | 0x800000u) & 0xFFFFFFu) << sh1, s1);
+                    } else if (e != 0 && sh1 >= -7) {
+                        s2 = mad_wide(((v[t] | 0x800000u) & 0xFFFFFFu) << (sh1 + 7), s2);
+                    } else if (v[t] & 0x7FFFFFFFu) {
+                        // small or subnormal: (m^2 << 64) >> 2 (emax - e) into the 128-bit sum
+                        const unsigned mm = e ? ((v[t] | 0x800000u) & 0xFFFFFFu) : (v[t] & 0x7FFFFFu);
+                        const int sh = 2 * (emax - (e ? e : 1));
+                        const unsigned long long sq = (unsigned long long)mm * mm;
+                        if (sh < 64) add128(hi, lo, sq >> sh, sh ? sq << (64 - sh) : 0ull);
+                        else if (sh < 112) add128(hi, lo, 0ull, sq >> (sh - 64));
+                    }
                 }
-            }
-            emax = __reduce_max_sync(0xffffffffu, emax);
-            special = __reduce_or_sync(0xffffffffu, special);
-            unsigned long long hi = 0ull, lo = 0ull;
-            for (int k0 = 0; k0 < d; k0 += 32 * kL2Per) {
-                if (!one_chunk) l2_load(x, k0, d, lane, v);
-#pragma unroll
-                for (int t = 0; t < kL2Per; ++t) {
-                    int e = (int)((v[t] >> 23) & 0xFFu);
-                    unsigned long long mm = v[t] & 0x7FFFFFu;
-                    if (e == 0) e = 1; else mm |= 0x800000ull;
-                    e = min(e, 254);
-                    const unsigned long long sq = mm * mm;         // < 2^48, exact
-                    const int sh = 2 * (emax - e);                  // add (sq << 64) >> sh
-                    unsigned long long ah = 0ull, al = 0ull;
-                    if (sh == 0) ah = sq;
-                    else if (sh < 64) { ah = sq >> sh; al = sq << (64 - sh); }
-                    else if (sh < 112) al = sq >> (sh - 64);
-                    add128(hi, lo, ah, al);
-                }
+                add128_shifted(hi, lo, s1, 52 - 2 * (emax - el));
+                add128_shifted(hi, lo, s2, 38 - 2 * (emax - el));
             }
 #pragma unroll
             for (int o = 16; o; o >>= 1) {

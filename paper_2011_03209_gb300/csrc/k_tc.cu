@@ -269,7 +269,7 @@ __device__ __forceinline__ bool push_band(const TcParams& P, int ra, int rb, uin
         return false;
     }
     const PassArgs& A = P.A;
-    const double d2 = exact_sqdist(A.G + (int64_t)ra * A.dp, A.G + (int64_t)rb * A.dp, A.d);
+    const double d2 = exact_sqdist(pass_row(A, ra), pass_row(A, rb), A.d);
     atomicAdd(&A.stats[kStatBand], 1ull);
     if ((flags & kQTie) && fabs(d2 - A.eps2) <= A.tie_thr) atomicAdd(&A.stats[kStatTies], 1ull);
     *decided = true;
@@ -858,13 +858,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
 
 // ------------------------------------------------ nearest pivot (layout)
 // Point tiles (128 rows) against all pivots (up to 256) in one MMA of
-// N = 256: rows and pivots centred on the pivots' mean c and split into BF16
-// hi + lo (three products), so |x - p|^2 = |x - c|^2 + |p - c|^2 - 2 acc
-// with error ~2^-13 |x - c||p - c|. The nearest pivot only orders points
-// for the tile layout; no decision of the method depends on it.
+// N = 256: rows and pivots centred on the pivots' mean c and rounded to BF16
+// (one product), so |x - p|^2 = |x - c|^2 + |p - c|^2 - 2 acc with error
+// ~2^-7 |x - c||p - c|. The nearest pivot only orders points for the tile
+// layout (a near tie may go either way); no decision of the method depends
+// on it.
 constexpr int kPivN = 256;
-constexpr int kAsgStages = 2;
-constexpr int kAsgStageBytes = 2 * kBlk + 2 * (kPivN * kKB * 2);    // x hi, lo; pivots hi, lo
+constexpr int kAsgStages = 4;
+constexpr int kAsgStageBytes = kBlk + kPivN * kKB * 2;               // x, pivots
 
 struct AssignParams {
     int64_t n, n_tiles;
@@ -896,9 +897,7 @@ __device__ __forceinline__ void mma_bf16_n256(uint32_t tmem, uint64_t adesc, uin
 }
 
 __global__ void __launch_bounds__(192, 1) assign_tc_kernel(const __grid_constant__ CUtensorMap mXh,
-                                                           const __grid_constant__ CUtensorMap mXl,
                                                            const __grid_constant__ CUtensorMap mPh,
-                                                           const __grid_constant__ CUtensorMap mPl,
                                                            const AssignParams P)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -940,9 +939,7 @@ __global__ void __launch_bounds__(192, 1) assign_tc_kernel(const __grid_constant
                     unsigned char* st = smem + stage * kAsgStageBytes;
                     mbar_expect_tx(&S.full[stage], (uint32_t)kAsgStageBytes);
                     tma_load(st, &mXh, kb * kKB, (int)(t * kT), &S.full[stage]);
-                    tma_load(st + kBlk, &mXl, kb * kKB, (int)(t * kT), &S.full[stage]);
-                    tma_load(st + 2 * kBlk, &mPh, kb * kKB, 0, &S.full[stage]);
-                    tma_load(st + 2 * kBlk + kPivN * kKB * 2, &mPl, kb * kKB, 0, &S.full[stage]);
+                    tma_load(st + kBlk, &mPh, kb * kKB, 0, &S.full[stage]);
                     if (++stage == kAsgStages) { stage = 0; phase ^= 1; }
                 }
             }
@@ -962,13 +959,10 @@ __global__ void __launch_bounds__(192, 1) assign_tc_kernel(const __grid_constant
                     if (!mbar_wait(&S.full[stage], phase, abort)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t base = su32(smem + stage * kAsgStageBytes);
-                    const uint32_t xh = base, xl = base + kBlk, ph = base + 2 * kBlk, pl = ph + kPivN * kKB * 2;
+                    const uint32_t xh = base, ph = base + kBlk;
 #pragma unroll
-                    for (int j = 0; j < kKB / 16; ++j) {
+                    for (int j = 0; j < kKB / 16; ++j)
                         mma_bf16_n256(d_tmem, smem_desc(xh + 32 * j), smem_desc(ph + 32 * j), (kb | j) ? 1u : 0u);
-                        mma_bf16_n256(d_tmem, smem_desc(xh + 32 * j), smem_desc(pl + 32 * j), 1u);
-                        mma_bf16_n256(d_tmem, smem_desc(xl + 32 * j), smem_desc(ph + 32 * j), 1u);
-                    }
                     mma_commit(&S.empty[stage]);
                     if (++stage == kAsgStages) { stage = 0; phase ^= 1; }
                 }
@@ -1019,24 +1013,43 @@ __global__ void __launch_bounds__(192, 1) assign_tc_kernel(const __grid_constant
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kPivN));
 }
 
-// Rows of `src` (n rows, stride ld, d values) minus c, split into BF16 hi
-// and lo (rows_out rows of pitch dp, zero padded) with |row - c|^2 in FP32.
+// Rows of `src` (n rows, stride ld, d values) minus c, rounded to BF16
+// (rows_out rows of pitch dp, zero padded) with |row - c|^2 in FP32. A lane
+// converts 8 consecutive columns (one 16-byte store).
 __global__ void split_rows_kernel(const float* __restrict__ src, int64_t n, int d, int64_t ld, int dp,
                                   const float* __restrict__ c, int64_t rows_out, __nv_bfloat16* __restrict__ hi,
-                                  __nv_bfloat16* __restrict__ lo, float* __restrict__ n2, float pad_n2)
+                                  float* __restrict__ n2, float pad_n2, bool vec)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = warp; r < rows_out; r += nwarp) {
         float s = 0.f;
-        for (int k = lane; k < dp; k += 32) {
-            float a = 0.f;
-            if (r < n && k < d) a = src[r * ld + k] - c[k];
-            const __nv_bfloat16 h = __float2bfloat16_rn(a);
-            hi[r * dp + k] = h;
-            lo[r * dp + k] = __float2bfloat16_rn(a - __bfloat162float(h));
-            s = fmaf(a, a, s);
+        for (int k0 = 0; k0 < dp; k0 += 256) {
+            const int k = k0 + lane * 8;
+            if (k >= dp) continue;
+            float a[8];
+            const float* x = src + r * ld + k;
+            if (r < n && vec && k + 7 < d) {
+                const float4 x0 = *reinterpret_cast<const float4*>(x);
+                const float4 x1 = *reinterpret_cast<const float4*>(x + 4);
+                a[0] = x0.x; a[1] = x0.y; a[2] = x0.z; a[3] = x0.w;
+                a[4] = x1.x; a[5] = x1.y; a[6] = x1.z; a[7] = x1.w;
+            } else {
+#pragma unroll
+                for (int t = 0; t < 8; ++t) a[t] = (r < n && k + t < d) ? x[t] : 0.f;
+            }
+            uint32_t w[4];
+#pragma unroll
+            for (int t = 0; t < 8; t += 2) {
+                const float a0 = (r < n && k + t < d) ? a[t] - c[k + t] : 0.f;
+                const float a1 = (r < n && k + t + 1 < d) ? a[t + 1] - c[k + t + 1] : 0.f;
+                const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+                w[t >> 1] = *reinterpret_cast<const uint32_t*>(&h);
+                s = fmaf(a0, a0, s);
+                s = fmaf(a1, a1, s);
+            }
+            *reinterpret_cast<uint4*>(hi + r * dp + k) = make_uint4(w[0], w[1], w[2], w[3]);
         }
         for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0 && n2) n2[r] = r < n ? s : pad_n2;
@@ -1078,13 +1091,13 @@ __global__ void __launch_bounds__(256) recheck_kernel(const PassArgs A, const ui
         if (live) e = queue[i];
         const int ra = (int)e.x, rb = (int)(e.y & 0x3FFFFFFFu);
         const uint32_t fl = e.y >> 30;
-        const float4* xa = reinterpret_cast<const float4*>(A.G + (int64_t)ra * A.dp);
-        const float4* xb = reinterpret_cast<const float4*>(A.G + (int64_t)rb * A.dp);
+        const float* xa = live ? pass_row(A, ra) : nullptr;
+        const float* xb = live ? pass_row(A, rb) : nullptr;
         float s32 = 0.f;
         if (live) {
 #pragma unroll 4
             for (int k = sub; k < A.dp / 4; k += 8) {
-                const float4 p = xa[k], q = xb[k];
+                const float4 p = pass_ld4(A, xa, k), q = pass_ld4(A, xb, k);
                 float t = p.x - q.x;
                 s32 = fmaf(t, t, s32);
                 t = p.y - q.y;
@@ -1103,7 +1116,7 @@ __global__ void __launch_bounds__(256) recheck_kernel(const PassArgs A, const ui
             double s64 = 0.0;
             if (state == 2) {
                 for (int k = sub; k < A.dp / 4; k += 8) {
-                    const float4 p = xa[k], q = xb[k];
+                    const float4 p = pass_ld4(A, xa, k), q = pass_ld4(A, xb, k);
                     double t = (double)p.x - (double)q.x;
                     s64 = fma(t, t, s64);
                     t = (double)p.y - (double)q.y;
@@ -1125,7 +1138,7 @@ __global__ void __launch_bounds__(256) recheck_kernel(const PassArgs A, const ui
         if (live && sub == 0) {
             bool in = state == 1;
             if (state == 4) {
-                const double d2 = exact_sqdist(A.G + (int64_t)ra * A.dp, A.G + (int64_t)rb * A.dp, A.d);
+                const double d2 = exact_sqdist(xa, xb, A.d);
                 if (MODE == 1 && (fl & kQTie) && fabs(d2 - A.eps2) <= A.tie_thr)
                     atomicAdd(&A.stats[kStatTies], 1ull);
                 atomicAdd(&A.stats[kStatFp64], 1ull);
@@ -1229,7 +1242,7 @@ int assign_pivots_tc(const float* X, int64_t n, int d, int64_t ld, int dp, const
 {
     if (K > kPivN) { set_error("assign_pivots_tc: more than 256 pivots"); return MAPPER_EINVAL; }
     const int64_t n_tiles = (n + kT - 1) / kT, rows = n_tiles * kT;
-    Buf c, xh, xl, xn2, ph, pl, pn2, err;
+    Buf c, xh, xn2, ph, pn2, err;
 #define AK(expr)                                                                         \
     do {                                                                                 \
         cudaError_t e_ = (expr);                                                         \
@@ -1240,23 +1253,21 @@ int assign_pivots_tc(const float* X, int64_t n, int d, int64_t ld, int dp, const
     } while (0)
     AK(c.alloc(sizeof(float) * dp, s));
     AK(xh.alloc(sizeof(__nv_bfloat16) * (size_t)rows * dp, s));
-    AK(xl.alloc(sizeof(__nv_bfloat16) * (size_t)rows * dp, s));
     AK(xn2.alloc(sizeof(float) * rows, s));
     AK(ph.alloc(sizeof(__nv_bfloat16) * (size_t)kPivN * dp, s));
-    AK(pl.alloc(sizeof(__nv_bfloat16) * (size_t)kPivN * dp, s));
     AK(pn2.alloc(sizeof(float) * kPivN, s));
     AK(err.alloc(sizeof(int), s));
     AK(cudaMemsetAsync(err.p, 0, sizeof(int), s));
     mean_rows_kernel<<<1, 256, 0, s>>>(Pv, K, dp, c.as<float>());
+    const bool vec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
     split_rows_kernel<<<num_sms * 8, 256, 0, s>>>(X, n, d, ld, dp, c.as<float>(), rows, xh.as<__nv_bfloat16>(),
-                                                  xl.as<__nv_bfloat16>(), xn2.as<float>(), 0.f);
+                                                  xn2.as<float>(), 0.f, vec);
     split_rows_kernel<<<8, 256, 0, s>>>(Pv, K, d, dp, dp, c.as<float>(), kPivN, ph.as<__nv_bfloat16>(),
-                                        pl.as<__nv_bfloat16>(), pn2.as<float>(), INFINITY);
+                                        pn2.as<float>(), INFINITY, true);
     note_launch(3);
     AK(cudaGetLastError());
-    CUtensorMap mxh, mxl, mph, mpl;
-    if (!make_map(&mxh, xh.p, rows, dp) || !make_map(&mxl, xl.p, rows, dp) ||
-        !make_map(&mph, ph.p, kPivN, dp, kPivN) || !make_map(&mpl, pl.p, kPivN, dp, kPivN)) {
+    CUtensorMap mxh, mph;
+    if (!make_map(&mxh, xh.p, rows, dp) || !make_map(&mph, ph.p, kPivN, dp, kPivN)) {
         set_error("cuTensorMapEncodeTiled failed (or is unavailable)");
         return MAPPER_ECUDA;
     }
@@ -1271,7 +1282,7 @@ int assign_pivots_tc(const float* X, int64_t n, int d, int64_t ld, int dp, const
     p.err = err.as<int>();
     const int smem = kAsgStages * kAsgStageBytes + (int)sizeof(AsgTail) + 1024;
     AK(cudaFuncSetAttribute(assign_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    assign_tc_kernel<<<(int)std::min<int64_t>(n_tiles, num_sms), 192, smem, s>>>(mxh, mxl, mph, mpl, p);
+    assign_tc_kernel<<<(int)std::min<int64_t>(n_tiles, num_sms), 192, smem, s>>>(mxh, mph, p);
     note_launch();
     AK(cudaGetLastError());
     int h_err = 0;

@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(32 * kPrepWarps, 1) tile_prep_reg_kernel(
         for (int i = 0; i < kPrepRows; ++i) {
             const float4 x = v[i][h];
             bad |= !isfinite(x.x) || !isfinite(x.y) || !isfinite(x.z) || !isfinite(x.w);
-            if (k < dp)
+            if (G && k < dp)
                 *reinterpret_cast<float4*>(G + (row0 + warp + kPrepWarps * i) * dp + k) = x;
             part[h].x += x.x;
             part[h].y += x.y;
@@ -488,9 +488,12 @@ __global__ void __launch_bounds__(1024) seg_cent_kernel(const float* __restrict_
 
 // BF16 operands centred on the segment centre c (FP32): a = fl(x - c),
 // hi = bf16(a), lo = bf16(a - hi) (a - hi is exact in FP32); |a|^2 summed in
-// FP32 (lane partials, then a shuffle tree) and |a| rounded up.
-__global__ void __launch_bounds__(256) operand_kernel(const float* __restrict__ G, int d, int dp,
-                                                      const int32_t* __restrict__ tile_n,
+// FP32 (lane partials of at most dp/32 squares, then a shuffle tree) and |a|
+// rounded up. A warp per row, a lane per 8 consecutive columns (16-byte
+// stores); rows come from G when it is set, else from X.
+__global__ void __launch_bounds__(256) operand_kernel(const float* __restrict__ G, const float* __restrict__ X,
+                                                      int64_t ld, bool xvec, const int32_t* __restrict__ row_pt,
+                                                      int d, int dp, const int32_t* __restrict__ tile_n,
                                                       const int32_t* __restrict__ tile_seg,
                                                       const float* __restrict__ seg_cent,
                                                       __nv_bfloat16* __restrict__ Ah,
@@ -501,23 +504,47 @@ __global__ void __launch_bounds__(256) operand_kernel(const float* __restrict__ 
     const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nt = tile_n[t];
     const float* c = seg_cent + (int64_t)tile_seg[t] * dp;
+    const bool vec = G ? true : xvec;
     for (int r = warp; r < kT; r += 8) {
         const int64_t row = (int64_t)t * kT + r;
+        const bool valid = r < nt;
+        const float* xr = !valid ? nullptr : (G ? G + row * dp : X + (int64_t)row_pt[row] * ld);
         float s = 0.f;
-        for (int k = lane * 2; k < dp; k += 64) {
-            float a0 = 0.f, a1 = 0.f;
-            if (r < nt) {
-                const float2 x = *reinterpret_cast<const float2*>(G + row * dp + k);
-                if (k < d) a0 = x.x - c[k];
-                if (k + 1 < d) a1 = x.y - c[k + 1];
+        for (int k0 = 0; k0 < dp; k0 += 256) {
+            const int k = k0 + lane * 8;
+            if (k >= dp) continue;
+            float a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] = 0.f;
+            if (valid) {
+                if (vec && k + 7 < d) {
+                    const float4 x0 = *reinterpret_cast<const float4*>(xr + k);
+                    const float4 x1 = *reinterpret_cast<const float4*>(xr + k + 4);
+                    a[0] = x0.x; a[1] = x0.y; a[2] = x0.z; a[3] = x0.w;
+                    a[4] = x1.x; a[5] = x1.y; a[6] = x1.z; a[7] = x1.w;
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) if (k + u < d) a[u] = xr[k + u];
+                }
+                const float4 c0 = *reinterpret_cast<const float4*>(c + k);
+                const float4 c1 = *reinterpret_cast<const float4*>(c + k + 4);
+                const float cc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+                for (int u = 0; u < 8; ++u) a[u] = k + u < d ? a[u] - cc[u] : 0.f;
             }
-            const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
-            const float2 hf = __bfloat1622float2(h);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(a0 - hf.x, a1 - hf.y);
-            *reinterpret_cast<__nv_bfloat162*>(Ah + row * dp + k) = h;
-            if (Al) *reinterpret_cast<__nv_bfloat162*>(Al + row * dp + k) = l;
-            s = fmaf(a0, a0, s);
-            s = fmaf(a1, a1, s);
+            uint32_t wh[4], wl[4];
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(a[u], a[u + 1]);
+                const float2 hf = __bfloat1622float2(h);
+                const __nv_bfloat162 l = __floats2bfloat162_rn(a[u] - hf.x, a[u + 1] - hf.y);
+                wh[u >> 1] = *reinterpret_cast<const uint32_t*>(&h);
+                wl[u >> 1] = *reinterpret_cast<const uint32_t*>(&l);
+                s = fmaf(a[u], a[u], s);
+                s = fmaf(a[u + 1], a[u + 1], s);
+            }
+            *reinterpret_cast<uint4*>(Ah + row * dp + k) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+            if (Al) *reinterpret_cast<uint4*>(Al + row * dp + k) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
         }
         for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
@@ -790,7 +817,10 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
 
     TK(L->row_slot.alloc(sizeof(int32_t) * R, s));
     TK(L->row_pt.alloc(sizeof(int32_t) * R, s));
-    TK(L->G.alloc(sizeof(float) * (size_t)R * dp, s));
+    // FP32 rows gathered in layout order for the CUDA-core passes (and the
+    // tile statistics of rows wider than 256); the tensor-core path reads the
+    // few rows it rechecks from X instead
+    if (!bf16 || dp > 256) TK(L->G.alloc(sizeof(float) * (size_t)R * dp, s));
     TK(L->tile_n.alloc(sizeof(int32_t) * T, s));
     TK(L->tile_seg.alloc(sizeof(int32_t) * T, s));
     TK(L->tile_elem.alloc(sizeof(int32_t) * T, s));
@@ -831,7 +861,9 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
         TK(L->rn2.alloc(sizeof(float) * R, s));
         TK(L->rn.alloc(sizeof(float) * R, s));
         const float norm_infl = 1.0f + (float)(dp / 32 + 16) * 5.9604645e-8f;
-        operand_kernel<<<(unsigned)T, 256, 0, s>>>(L->G.as<float>(), d, dp, L->tile_n.as<int32_t>(),
+        const bool xvec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
+        operand_kernel<<<(unsigned)T, 256, 0, s>>>(L->G.as<float>(), X, ld, xvec, L->row_pt.as<int32_t>(), d, dp,
+                                                   L->tile_n.as<int32_t>(),
                                                    L->tile_seg.as<int32_t>(), L->seg_cent.as<float>(),
                                                    L->Ah.as<__nv_bfloat16>(), L->Al.as<__nv_bfloat16>(),
                                                    L->rn2.as<float>(), L->rn.as<float>(), norm_infl);

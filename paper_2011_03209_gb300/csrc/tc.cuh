@@ -35,7 +35,8 @@ int tc_groups(const int2* pairs, int64_t n, Buf* groups, int64_t* n_groups, cuda
 int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaStream_t s);
 
 // Nearest of K <= 256 pivots (rows of Pv, pitch dp) for every point of X, on
-// tensor cores (BF16 hi + lo split, one MMA of N = 256 per 16 columns).
+// tensor cores (rows centred and rounded to BF16, one MMA of N = 256 per 16
+// columns); near ties may resolve either way, which only orders the layout.
 // Returns a mapper_status.
 int assign_pivots_tc(const float* X, int64_t n, int d, int64_t ld, int dp, const float* Pv, int K,
                      int num_sms, int32_t* piv, float* pd2, cudaStream_t s);
