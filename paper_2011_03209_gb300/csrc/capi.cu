@@ -421,13 +421,15 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         cudaEvent_t* e;
         ~EvGuard() { for (int i = 0; i < 2; ++i) if (e[i]) cudaEventDestroy(e[i]); }
     } tev_guard{tev};
-    Buf groups;
+    Buf groups, group_pos;
     if (use_tc) {
         TcArgs t1 = t;
         t1.ev_begin = tev[0];
         t1.ev_end = tev[1];
-        if ((rc = tc_groups(a_tc.pairs, PL.n[kListTC], &groups, &t1.n_groups, s))) return rc;
+        if ((rc = tc_groups(a_tc.pairs, PL.n[kListTC], &groups, &group_pos, s))) return rc;
         t1.groups = groups.as<int2>();
+        t1.n_groups = PL.n[kListTC];
+        t1.groups_dev = reinterpret_cast<const unsigned long long*>(group_pos.as<int64_t>() + PL.n[kListTC]);
         if ((rc = tc_pass(1, a_tc, t1, PL.n[kListTC], s))) return rc;
     }
     else CK(simt_pass(1, a_tc, PL.n[kListTC], s), "pass 1 tc list");
@@ -444,43 +446,46 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     // pair is kept only if its core rows are not all joined yet (from the
     // second round on when there are no lists), and pairs whose two sides are
     // each already one component only need one neighbour pair.
-    int64_t union_pairs = 0;
     auto union_rounds = [&](const PassArgs& base, int64_t n, bool tc) -> int {
         if (n == 0) return MAPPER_OK;
+        // every count stays on the device: each launch covers the list's
+        // capacity n and reads its length there, so the rounds need no host
+        // round trip
         static const int kBounds[] = {-1, 1, 4, 16, 64, INT_MAX};
         Buf hits, sel, kept, cnt;
         CK(hits.alloc(sizeof(int2) * n, s), "alloc");
         CK(sel.alloc(sizeof(int2) * n, s), "alloc");
         CK(kept.alloc(sizeof(int2) * n, s), "alloc");
-        CK(cnt.alloc(sizeof(unsigned long long) * 2, s), "alloc");
-        CK(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s), "memset");
-        CK(select_hit(base.pairs, base.pair_hit, n, hits.as<int2>(), cnt.as<unsigned long long>(), s), "select");
-        unsigned long long nh = 0;
-        CK(cudaMemcpyAsync(&nh, cnt.p, sizeof(nh), cudaMemcpyDeviceToHost, s), "copy");
-        CK(cudaStreamSynchronize(s), "sync");
-        union_pairs += (int64_t)nh;
+        CK(cnt.alloc(sizeof(unsigned long long) * 3, s), "alloc");
+        unsigned long long* c_hit = cnt.as<unsigned long long>();
+        unsigned long long* c_sel = c_hit + 1;
+        unsigned long long* c_kept = c_hit + 2;
+        CK(cudaMemsetAsync(c_hit, 0, sizeof(unsigned long long), s), "memset");
+        CK(select_hit(base.pairs, base.pair_hit, n, hits.as<int2>(), c_hit, s), "select");
+        CK(add_counter(base.stats + kStatUnion, c_hit, s), "count");
         for (int k = 0; k + 1 < (int)(sizeof(kBounds) / sizeof(kBounds[0])); ++k) {
-            CK(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * 2, s), "memset");
-            CK(select_delta(hits.as<int2>(), (int64_t)nh, kBounds[k], kBounds[k + 1], sel.as<int2>(),
-                            cnt.as<unsigned long long>(), s), "select");
+            CK(cudaMemsetAsync(c_sel, 0, sizeof(unsigned long long) * 2, s), "memset");
+            CK(select_delta(hits.as<int2>(), n, c_hit, kBounds[k], kBounds[k + 1], sel.as<int2>(), c_sel, s),
+               "select");
             const int2* list = sel.as<int2>();
-            unsigned long long hc[2] = {0, 0};
+            const unsigned long long* c_list = c_sel;
             if (k > 0 || cap) {
-                CK(cudaMemcpyAsync(hc, cnt.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s), "copy");
-                CK(cudaStreamSynchronize(s), "sync");
-                CK(filter_joined(base, sel.as<int2>(), (int64_t)hc[0], kept.as<int2>(),
-                                 cnt.as<unsigned long long>() + 1, s), "filter");
+                CK(filter_joined(base, sel.as<int2>(), n, c_sel, kept.as<int2>(), c_kept, s), "filter");
                 list = kept.as<int2>();
+                c_list = c_kept;
             }
-            CK(cudaMemcpyAsync(hc, cnt.p, sizeof(hc), cudaMemcpyDeviceToHost, s), "copy");
-            CK(cudaStreamSynchronize(s), "sync");
-            const int64_t m = (int64_t)(k > 0 || cap ? hc[1] : hc[0]);
             PassArgs ar = base;
             ar.pairs = list;
+            ar.n_dev = c_list;
             ar.pair_hit = nullptr;
             int r2;
-            if (tc) { if ((r2 = tc_pass(2, ar, t, m, s))) return r2; }
-            else CK(simt_pass(2, ar, m, s), "pass 2");
+            if (tc) {
+                TcArgs t2 = t;
+                t2.n_dev = c_list;
+                if ((r2 = tc_pass(2, ar, t2, n, s))) return r2;
+            } else {
+                CK(simt_pass(2, ar, n, s), "pass 2");
+            }
         }
         return MAPPER_OK;
     };
@@ -490,7 +495,6 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     } else {
         if ((rc = union_rounds(a_simt, PL.n[kListSimt], false))) return rc;
     }
-    st.union_pairs = union_pairs;
     pt.mark();                                                    // 4
     CK(flatten(a.parent, a.core, R, root.as<int32_t>(), s), "flatten");
     if (cap) {
@@ -525,6 +529,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     st.n_core = (int64_t)h_stats[kStatCore];
     st.union_skipped = (int64_t)h_stats[kStatSkipped];
     st.fp64_pairs = (int64_t)h_stats[kStatFp64];
+    st.union_pairs = (int64_t)h_stats[kStatUnion];
     st.n_rows = R;
     if (tev[0] && PL.n[use_tc ? kListTC : kListSimt] > 0) {
         float ms = 0.f;

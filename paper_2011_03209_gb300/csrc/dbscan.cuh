@@ -17,7 +17,7 @@ constexpr int kPairTileMask = kPairOneEach - 1;
 
 enum : int { kStatBand = 0, kStatTies = 1, kStatScreened = 2, kStatCore = 3, kStatTileOut = 4,
              kStatTileIn = 5, kStatSkipped = 6, kStatTcPairs = 7, kStatSimtPairs = 8, kStatFp64 = 9,
-             kStatCount = 10 };
+             kStatUnion = 10, kStatCount = 11 };
 
 // Work lists of tile pairs, classified by bounding spheres.
 enum : int { kListAllIn = 0, kListTC = 1, kListSimt = 2, kListCount = 3 };
@@ -36,6 +36,8 @@ struct PassArgs {
     int dp;                      // row pitch (multiple of 32)
     int d;                       // true dimension
     const int2* pairs;           // explicit list, or nullptr
+    const unsigned long long* n_dev;   // explicit list: its length on the device, if set
+                                       //   (launches cover an upper bound; the rest exit)
     const int32_t* tile_n;       // valid rows per tile (explicit mode)
     const int64_t* elem_off;     // implicit mode: [E+1] row offsets of the elements
     const int64_t* pair_off;     // implicit mode: [E+1] tile-pair offsets
@@ -106,14 +108,17 @@ cudaError_t element_offsets(const uint64_t* keys, int64_t M, int64_t E, int64_t*
 // receives the size.
 cudaError_t select_hit(const int2* pairs, const uint8_t* hit, int64_t n, int2* out,
                        unsigned long long* count, cudaStream_t s);
-// Appends to `out` the tile pairs (a, b) of `pairs` with lo < b - a <= hi;
-// *count receives the size.
-cudaError_t select_delta(const int2* pairs, int64_t n, int lo, int hi, int2* out,
+// *dst += *src (one device counter into another).
+cudaError_t add_counter(unsigned long long* dst, const unsigned long long* src, cudaStream_t s);
+// Appends to `out` the tile pairs (a, b) of pairs[0 .. *n_dev) (at most n)
+// with lo < b - a <= hi; *count receives the size.
+cudaError_t select_delta(const int2* pairs, int64_t n, const unsigned long long* n_dev, int lo, int hi, int2* out,
                          unsigned long long* count, cudaStream_t s);
-// Keeps the union-pass tile pairs whose core rows do not all share one root
-// yet (flagging kPairOneEach pairs); counts[0] receives the size.
-cudaError_t filter_joined(const PassArgs& a, const int2* pairs, int64_t n, int2* out,
-                          unsigned long long* counts, cudaStream_t s);
+// Keeps the union-pass tile pairs of pairs[0 .. *n_dev) (at most n) whose
+// core rows do not all share one root yet (flagging kPairOneEach pairs);
+// *count receives the size.
+cudaError_t filter_joined(const PassArgs& a, const int2* pairs, int64_t n, const unsigned long long* n_dev,
+                          int2* out, unsigned long long* count, cudaStream_t s);
 
 // --- nodes and nerve (k_nerve.cu)
 cudaError_t member_keys(const int32_t* lab, const int64_t* nid, const int64_t* mpos,

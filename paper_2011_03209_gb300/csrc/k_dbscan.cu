@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(256, 2) simt_pass_kernel(const PassArgs A)
     __shared__ int s_mm[2];
 
     const int tid = threadIdx.x;
+    if (A.n_dev && (unsigned long long)blockIdx.x >= *A.n_dev) return;
     const PairRows P = pair_rows(A, blockIdx.x);
     const int64_t sa = P.sa, sb = P.sb;
     const int na = P.na, nb = P.nb;
@@ -580,11 +581,12 @@ __global__ void select_hit_kernel(const int2* __restrict__ pairs, const uint8_t*
 }
 
 // Tile pairs whose tile distance b - a lies in (lo, hi].
-__global__ void select_delta_kernel(const int2* __restrict__ pairs, int64_t n, int lo, int hi,
+__global__ void select_delta_kernel(const int2* __restrict__ pairs, int64_t n,
+                                    const unsigned long long* __restrict__ n_dev, int lo, int hi,
                                     int2* __restrict__ out, unsigned long long* __restrict__ count)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || (n_dev && (unsigned long long)i >= *n_dev)) return;
     const int2 p = pairs[i];
     const int delta = p.y - p.x;
     if (delta > lo && delta <= hi) out[atomicAdd(count, 1ull)] = p;
@@ -594,8 +596,10 @@ __global__ void select_delta_kernel(const int2* __restrict__ pairs, int64_t n, i
 // off-diagonal pair whose A cores share one root and whose B cores share
 // another is flagged (kPairOneEach): one neighbour pair joins them.
 __global__ void filter_joined_kernel(const PassArgs A, const int2* __restrict__ pairs, int64_t n,
-                                     int2* __restrict__ out, unsigned long long* __restrict__ counts)
+                                     const unsigned long long* __restrict__ n_dev, int2* __restrict__ out,
+                                     unsigned long long* __restrict__ count)
 {
+    if (n_dev) n = min(n, (int64_t)*n_dev);
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -628,7 +632,7 @@ __global__ void filter_joined_kernel(const PassArgs A, const int2* __restrict__ 
             one_each = work && loA == hiA && loB == hiB;
         }
         if (lane == 0) {
-            if (work) out[atomicAdd(&counts[0], 1ull)] = make_int2(p.x, p.y | (one_each ? kPairOneEach : 0));
+            if (work) out[atomicAdd(count, 1ull)] = make_int2(p.x, p.y | (one_each ? kPairOneEach : 0));
             else if (hiA >= 0) atomicAdd(&A.stats[kStatSkipped], 1ull);
         }
     }
@@ -647,21 +651,30 @@ cudaError_t select_hit(const int2* pairs, const uint8_t* hit, int64_t n, int2* o
     return cudaGetLastError();
 }
 
-cudaError_t select_delta(const int2* pairs, int64_t n, int lo, int hi, int2* out,
-                         unsigned long long* count, cudaStream_t s)
+__global__ void add_counter_kernel(unsigned long long* dst, const unsigned long long* src) { *dst += *src; }
+
+cudaError_t add_counter(unsigned long long* dst, const unsigned long long* src, cudaStream_t s)
 {
-    if (n == 0) return cudaSuccess;
-    select_delta_kernel<<<grid_for(n), 256, 0, s>>>(pairs, n, lo, hi, out, count);
+    add_counter_kernel<<<1, 1, 0, s>>>(dst, src);
     note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t filter_joined(const PassArgs& a, const int2* pairs, int64_t n, int2* out,
-                          unsigned long long* counts, cudaStream_t s)
+cudaError_t select_delta(const int2* pairs, int64_t n, const unsigned long long* n_dev, int lo, int hi, int2* out,
+                         unsigned long long* count, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    filter_joined_kernel<<<(unsigned)std::min<int64_t>(div_up(n, 8), 152 * 32), 256, 0, s>>>(a, pairs, n, out,
-                                                                                           counts);
+    select_delta_kernel<<<grid_for(n), 256, 0, s>>>(pairs, n, n_dev, lo, hi, out, count);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t filter_joined(const PassArgs& a, const int2* pairs, int64_t n, const unsigned long long* n_dev,
+                          int2* out, unsigned long long* count, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    filter_joined_kernel<<<(unsigned)std::min<int64_t>(div_up(n, 8), 152 * 32), 256, 0, s>>>(a, pairs, n, n_dev,
+                                                                                           out, count);
     note_launch();
     return cudaGetLastError();
 }

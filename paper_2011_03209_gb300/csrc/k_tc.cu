@@ -55,6 +55,7 @@ struct TcParams {
     int64_t n_pairs;
     const int2* groups;                       // W = 2: (pair, pair or -1) sharing tile A
     int64_t n_groups;
+    const unsigned long long* n_dev;          // if set: work items on the device (<= n_pairs or n_groups)
     int nkb;                                  // K blocks per row
     double A1, A2, A3;                        // bound constants
     float A1f, A2f, A3f;                      // ... rounded up to FP32
@@ -404,7 +405,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
     constexpr int kStages = TcShape<NS, W>::kStages;
     constexpr int kStageBytes = TcShape<NS, W>::kStageBytes;
     constexpr int kAccCols = TcShape<NS, W>::kAccCols;
-    const int64_t n_items = W == 1 ? P.n_pairs : P.n_groups;
+    const int64_t n_cap = W == 1 ? P.n_pairs : P.n_groups;
+    const int64_t n_items = P.n_dev ? min(n_cap, (int64_t)*P.n_dev) : n_cap;
     auto group_at = [&](int64_t g) -> int2 { return W == 1 ? make_int2((int)g, -1) : P.groups[g]; };
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -1357,6 +1359,7 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
     const bool grouped = mode == 1 && t.groups != nullptr;
     p.groups = grouped ? t.groups : nullptr;
     p.n_groups = grouped ? t.n_groups : 0;
+    p.n_dev = grouped ? t.groups_dev : t.n_dev;
     const int grid = (int)std::min<int64_t>(grouped ? t.n_groups : n_pairs, t.num_sms);
     if (grid < 1) return MAPPER_OK;
     if (t.ev_begin) cudaEventRecord(t.ev_begin, s);
@@ -1390,11 +1393,10 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
     return MAPPER_OK;
 }
 
-int tc_groups(const int2* pairs, int64_t n, Buf* groups, int64_t* n_groups, cudaStream_t s)
+int tc_groups(const int2* pairs, int64_t n, Buf* groups, Buf* pos, cudaStream_t s)
 {
-    *n_groups = 0;
     if (n == 0) return MAPPER_OK;
-    Buf lead, pos;
+    Buf lead;
 #define GK(expr)                                                                  \
     do {                                                                          \
         cudaError_t e_ = (expr);                                                  \
@@ -1404,21 +1406,17 @@ int tc_groups(const int2* pairs, int64_t n, Buf* groups, int64_t* n_groups, cuda
         }                                                                         \
     } while (0)
     GK(lead.alloc(sizeof(int32_t) * n, s));
-    GK(pos.alloc(sizeof(int64_t) * (n + 1), s));
+    GK(pos->alloc(sizeof(int64_t) * (n + 1), s));
     const unsigned blocks = (unsigned)div_up(n, 256);
     group_lead_kernel<<<blocks, 256, 0, s>>>(pairs, n, lead.as<int32_t>());
     note_launch();
     GK(cudaGetLastError());
-    GK(exclusive_scan_i32_to_i64(lead.as<int32_t>(), pos.as<int64_t>(), n, s));
-    int64_t ng = 0;
-    GK(cudaMemcpyAsync(&ng, pos.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    GK(cudaStreamSynchronize(s));
-    GK(groups->alloc(sizeof(int2) * (size_t)ng, s));
-    group_emit_kernel<<<blocks, 256, 0, s>>>(pairs, n, lead.as<int32_t>(), pos.as<int64_t>(), groups->as<int2>());
+    GK(exclusive_scan_i32_to_i64(lead.as<int32_t>(), pos->as<int64_t>(), n, s));
+    GK(groups->alloc(sizeof(int2) * (size_t)n, s));
+    group_emit_kernel<<<blocks, 256, 0, s>>>(pairs, n, lead.as<int32_t>(), pos->as<int64_t>(), groups->as<int2>());
     note_launch();
     GK(cudaGetLastError());
 #undef GK
-    *n_groups = ng;
     return MAPPER_OK;
 }
 

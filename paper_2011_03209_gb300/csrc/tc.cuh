@@ -22,13 +22,17 @@ struct TcArgs {
     int* err;                        // set to 1 if a bounded wait ran out
     cudaEvent_t ev_begin, ev_end;    // if set: recorded around the tensor-core kernel
     const int2* groups;              // pass 1, if set: pair groups sharing tile A (tc_groups)
-    int64_t n_groups;
+    int64_t n_groups;                //   capacity of groups
+    const unsigned long long* groups_dev;   // ... and their number on the device
+    const unsigned long long* n_dev; // ungrouped, if set: the pair count on the device
+                                     //   (n_pairs then bounds it)
 };
 
 // Groups the pair list (sorted by tile A, then tile B) into work items of
 // one or two pairs sharing tile A: groups[k] = (pair index, pair index or -1).
-// Allocates *groups on stream s. Returns a mapper_status.
-int tc_groups(const int2* pairs, int64_t n, Buf* groups, int64_t* n_groups, cudaStream_t s);
+// Allocates *groups (capacity n) and *pos ([n + 1] int64; pos[n] = the number
+// of groups) on stream s, without a host round trip. Returns a mapper_status.
+int tc_groups(const int2* pairs, int64_t n, Buf* groups, Buf* pos, cudaStream_t s);
 
 // Pass `mode` (1 = counts and neighbour lists, 2 = unions) over the tile
 // pairs a.pairs[0 .. n_pairs) on tensor cores. Returns a mapper_status.
