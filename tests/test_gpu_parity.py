@@ -181,6 +181,43 @@ def test_pca_lens_basis_and_bits(ctx):
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("d", [300, 520])
+def test_wide_rows_exact(ctx, d, prec):
+    """Rows wider than 256 columns: the tile statistics go through the
+    gathered FP32 rows, the tensor-core operands span more K blocks."""
+    X = synth.gaussian_mixture(3000, d, 6, seed=40 + d, centre_box=4.0, std_lo=0.4, std_hi=1.0,
+                               anisotropic=True, noise_frac=0.05)
+    eps = _eps(X, 4, d)
+    res = run_gpu(ctx, X, (0,), (0,), (6,), (0.3,), eps, 6, prec)
+    assert_l2_lens(X, res["lens"][:, 0])
+    ref = assert_same_graph(X, res, (6,), (0.3,), eps, 6)
+    assert ref["near_ties"] == 0 and len(ref["node_elem"]) > 0
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("d,pad", [(37, 3), (64, 1), (130, 6)])
+def test_strided_rows_exact(ctx, d, pad, prec):
+    """X as a column slice of a wider array (row stride ld = d + pad): rows
+    re-decided from X use unaligned scalar loads."""
+    X = synth.gaussian_mixture(4000, d, 5, seed=50 + d, centre_box=5.0, std_lo=0.5, std_hi=1.2,
+                               anisotropic=False, noise_frac=0.05)
+    wide = np.zeros((X.shape[0], d + pad), dtype=np.float32)
+    wide[:, :d] = X
+    wide[:, d:] = 7.0                                  # never read
+    Xd = torch.from_numpy(wide).to("cuda:0")[:, :d]
+    assert Xd.stride(0) == d + pad
+    eps = _eps(X, 5, d)
+    g = mg.mapper_graph(ctx, Xd, mg.params((0,), (0,), (8,), (0.25,), eps, 5, prec))
+    res = g.numpy()
+    res["lens"], _ = g.lens(X.shape[0], 1)
+    res["elem_offsets"], res["elem_points"] = g.cover().numpy()
+    res["labels"], res["core"] = g.clusters().numpy(len(res["elem_points"]))
+    res["stats"] = g.stats()
+    assert_l2_lens(X, res["lens"][:, 0])
+    assert_same_graph(X, res, (8,), (0.25,), eps, 5)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
 def test_blobs_circle_5k_exact(ctx, prec):
     w = synth.blobs_circle_5k()
     res = run_gpu(ctx, w.X, w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, prec)
