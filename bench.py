@@ -290,7 +290,8 @@ def run_ours(args):
         "counters": {k: st[k] for k in ("n_members", "n_rows", "n_groups", "sum_ni2", "tile_pairs",
                                         "tile_pairs_out", "tile_pairs_in", "tile_pairs_tc",
                                         "tile_pairs_simt", "union_pairs", "union_skipped", "pairs_screened",
-                                        "band_pairs", "fp64_pairs", "near_ties", "n_core", "n_nodes", "n_edges")},
+                                        "band_pairs", "fp64_pairs", "near_ties", "n_core", "n_nodes", "n_edges",
+                                        "pass1_tile_n")},
         "ms_tiles": float(np.mean([s["ms_tiles"] for s in stats])),
         "roofline": roof,
         "clocks": clocks,
@@ -395,6 +396,7 @@ def run_sweep(args):
         for _ in range(args.steps):
             gs = mg.mapper_graph_sweep(ctx, Xd, base, eps, ov)
             nodes = [g.sizes()[0] for g in gs]
+            tile_n = gs[0].stats()["pass1_tile_n"]
             del gs
         end.record(stream)
         torch.cuda.synchronize()
@@ -416,7 +418,7 @@ def run_sweep(args):
         "config": {"workload": w.name + "_sweep16", "n": w.n, "d": w.d, "lens": "(PC1, PC2)", "grid": [30, 30],
                    "eps": eps, "overlap": ov, "min_pts": w.min_pts, "precision": args.precision},
         "ms_per_graph": sweep_ms / len(eps), "single_calls_ms": single_ms,
-        "sweep_speedup": single_ms / sweep_ms, "nodes": nodes, "clocks": clocks,
+        "sweep_speedup": single_ms / sweep_ms, "pass1_tile_n": tile_n, "nodes": nodes, "clocks": clocks,
     }))
 
 

@@ -59,7 +59,7 @@
 extern "C" {
 #endif
 
-#define MAPPER_ABI_VERSION 1
+#define MAPPER_ABI_VERSION 2
 
 typedef enum mapper_status {
     MAPPER_OK = 0,
@@ -139,6 +139,9 @@ typedef struct mapper_stats {
     int64_t union_pairs;     /* screened tile pairs with a neighbour pair, given to the union
                                 pass (before its rounds skip joined ones) */
     int64_t fp64_pairs;      /* pairs decided by the FP64 defining expression, all passes */
+    int64_t pass1_tile_n;    /* N of the pass-1 tensor-core product, picked by the context's
+                                autotuner: 128 (one tile pair per work item) or 256 (two tile
+                                pairs sharing tile A); 0 off the tensor cores */
 } mapper_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -152,6 +155,12 @@ void mapper_destroy(mapper_ctx* ctx);
 int mapper_set_stream(mapper_ctx* ctx, void* cuda_stream);
 /* Record per-stage device times in mapper_stats (adds CUDA events). */
 int mapper_set_timing(mapper_ctx* ctx, int enabled);
+/* Shape of the pass-1 tensor-core product (a tuning knob; the paper has no
+ * counterpart and results do not depend on it): 0 = let the context's
+ * autotuner pick per row pitch and screen (default), 128 = one tile pair per
+ * work item, 256 = two tile pairs sharing their first tile. Other values:
+ * MAPPER_EINVAL. */
+int mapper_set_pass1_tile_n(mapper_ctx* ctx, int tile_n);
 
 /* -------------------------------------------------------------- the steps */
 

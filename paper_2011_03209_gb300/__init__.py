@@ -53,6 +53,10 @@ class Context:
     def set_timing(self, on: bool) -> None:
         _capi.check(self._lib.mapper_set_timing(self.h, int(bool(on))), "mapper_set_timing")
 
+    def set_pass1_tile_n(self, tile_n: int) -> None:
+        """0: autotuned (default); 128 or 256: fixed pass-1 product shape."""
+        _capi.check(self._lib.mapper_set_pass1_tile_n(self.h, int(tile_n)), "mapper_set_pass1_tile_n")
+
     def close(self) -> None:
         if getattr(self, "h", None) is not None and self.h.value:
             self._lib.mapper_destroy(self.h)

@@ -5,6 +5,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <string>
 #include <vector>
@@ -69,6 +70,8 @@ struct mapper_ctx {
     size_t budget = 0;
     bool timing = false;
     int num_sms = 152;
+    std::map<uint64_t, int> pass1_tile_n;      // autotuner: (row pitch, products) -> N
+    int pass1_forced = 0;                      // 128 or 256: fixed by the caller
 };
 
 struct mapper_cover_t {
@@ -259,6 +262,88 @@ int run_cover(mapper_ctx* ctx, const double* lens, int64_t n, int32_t m, const i
     return MAPPER_OK;
 }
 
+// Pass-1 autotuner. The tensor-core count kernel runs its tile pairs as work
+// items of one pair (an M = 128, N = 128 product) or of two pairs sharing
+// tile A (N = 256, tile A loaded once); which is faster depends on the row
+// pitch (MMA work per pair against the fixed epilogue work) and the number of
+// products. The first call for a (pitch, products) key times both shapes on
+// a prefix of its own pair list, into scratch outputs, and the context keeps
+// the faster; lists too short to time take N = 256 without caching.
+int tune_pass1(mapper_ctx* ctx, const PassArgs& a, const TcArgs& t, int64_t n_pairs, int64_t R, int cap,
+               cudaStream_t s, int* tile_n)
+{
+    if (ctx->pass1_forced) {
+        *tile_n = ctx->pass1_forced;
+        return MAPPER_OK;
+    }
+    const uint64_t key = ((uint64_t)a.dp << 8) | (uint64_t)t.ns;
+    auto it = ctx->pass1_tile_n.find(key);
+    if (it != ctx->pass1_tile_n.end()) {
+        *tile_n = it->second;
+        return MAPPER_OK;
+    }
+    *tile_n = 256;
+    const int64_t n_t = std::min<int64_t>(n_pairs, (int64_t)ctx->num_sms * 32);
+    if (n_t < (int64_t)ctx->num_sms * 8) return MAPPER_OK;
+    const unsigned long long qcap = 1ull << 20;
+    Buf cnt, nbr, hit, q, qn, st, err, grp, gpos;
+    CK(cnt.alloc(sizeof(int32_t) * R, s), "alloc");
+    if (cap) CK(nbr.alloc(sizeof(int32_t) * (size_t)R * cap, s), "alloc");
+    CK(hit.alloc(n_t, s), "alloc");
+    CK(q.alloc(sizeof(uint2) * qcap, s), "alloc");
+    CK(qn.alloc(sizeof(unsigned long long), s), "alloc");
+    CK(st.alloc(sizeof(unsigned long long) * kStatCount, s), "alloc");
+    CK(err.alloc(sizeof(int), s), "alloc");
+    CK(cudaMemsetAsync(err.p, 0, sizeof(int), s), "memset");
+    PassArgs as = a;
+    as.count = cnt.as<int32_t>();
+    as.nbr = nbr.as<int32_t>();
+    as.pair_hit = hit.as<uint8_t>();
+    as.stats = st.as<unsigned long long>();
+    TcArgs ts = t;
+    ts.queue = q.as<uint2>();
+    ts.queue_n = qn.as<unsigned long long>();
+    ts.queue_cap = qcap;
+    ts.err = err.as<int>();
+    ts.groups = nullptr;
+    ts.groups_dev = nullptr;
+    ts.n_dev = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    struct Guard {
+        cudaEvent_t* e;
+        ~Guard() { for (int i = 0; i < 4; ++i) if (e[i]) cudaEventDestroy(e[i]); }
+    } guard{ev};
+    for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&ev[i]), "event");
+    for (int v = 0; v < 2; ++v) {
+        CK(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * R, s), "memset");
+        if (cap) CK(cudaMemsetAsync(nbr.p, 0xff, sizeof(int32_t) * (size_t)R * cap, s), "memset");
+        CK(cudaMemsetAsync(hit.p, 0, n_t, s), "memset");
+        CK(cudaMemsetAsync(st.p, 0, sizeof(unsigned long long) * kStatCount, s), "memset");
+        TcArgs tv = ts;
+        tv.ev_begin = ev[2 * v];
+        tv.ev_end = ev[2 * v + 1];
+        if (v == 1) {
+            int rc = tc_groups(a.pairs, n_t, &grp, &gpos, s);
+            if (rc) return rc;
+            tv.groups = grp.as<int2>();
+            tv.n_groups = n_t;
+            tv.groups_dev = reinterpret_cast<const unsigned long long*>(gpos.as<int64_t>() + n_t);
+        }
+        int rc = tc_pass(1, as, tv, n_t, s);
+        if (rc) return rc;
+    }
+    int h_err = 0;
+    CK(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    if (h_err) return fail(MAPPER_ETIMEOUT, "a tensor-core pass gave up waiting on a barrier (autotuning)");
+    float ms[2] = {0.f, 0.f};
+    CK(cudaEventElapsedTime(&ms[0], ev[0], ev[1]), "event time");
+    CK(cudaEventElapsedTime(&ms[1], ev[2], ev[3]), "event time");
+    *tile_n = ms[1] <= ms[0] ? 256 : 128;
+    ctx->pass1_tile_n[key] = *tile_n;
+    return MAPPER_OK;
+}
+
 // ---------------------------------------------------------------- cluster
 // Per-element DBSCAN: tiles ordered by pivot group (k_tiles.cu), tile pairs
 // classified by bounding spheres, then the passes over the three lists:
@@ -410,6 +495,9 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         t.err = tc_err.as<int>();
     }
 
+    int tile_n = 0;
+    if (use_tc && PL.n[kListTC] > 0 && (rc = tune_pass1(ctx, a_tc, t, PL.n[kListTC], R, cap, s, &tile_n)))
+        return rc;
     pt.mark();                                                    // 1
     CK(allin_pass(1, a_in, PL.n[kListAllIn], s), "pass 1 all-in");
     cudaEvent_t tev[2] = {nullptr, nullptr};
@@ -426,10 +514,12 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         TcArgs t1 = t;
         t1.ev_begin = tev[0];
         t1.ev_end = tev[1];
-        if ((rc = tc_groups(a_tc.pairs, PL.n[kListTC], &groups, &group_pos, s))) return rc;
-        t1.groups = groups.as<int2>();
-        t1.n_groups = PL.n[kListTC];
-        t1.groups_dev = reinterpret_cast<const unsigned long long*>(group_pos.as<int64_t>() + PL.n[kListTC]);
+        if (tile_n == 256) {
+            if ((rc = tc_groups(a_tc.pairs, PL.n[kListTC], &groups, &group_pos, s))) return rc;
+            t1.groups = groups.as<int2>();
+            t1.n_groups = PL.n[kListTC];
+            t1.groups_dev = reinterpret_cast<const unsigned long long*>(group_pos.as<int64_t>() + PL.n[kListTC]);
+        }
         if ((rc = tc_pass(1, a_tc, t1, PL.n[kListTC], s))) return rc;
     }
     else CK(simt_pass(1, a_tc, PL.n[kListTC], s), "pass 1 tc list");
@@ -530,6 +620,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     st.union_skipped = (int64_t)h_stats[kStatSkipped];
     st.fp64_pairs = (int64_t)h_stats[kStatFp64];
     st.union_pairs = (int64_t)h_stats[kStatUnion];
+    st.pass1_tile_n = tile_n;
     st.n_rows = R;
     if (tev[0] && PL.n[use_tc ? kListTC : kListSimt] > 0) {
         float ms = 0.f;
@@ -723,6 +814,14 @@ int mapper_set_timing(mapper_ctx* ctx, int enabled)
 {
     if (!ctx) return fail(MAPPER_EINVAL, "null context");
     ctx->timing = enabled != 0;
+    return MAPPER_OK;
+}
+
+int mapper_set_pass1_tile_n(mapper_ctx* ctx, int tile_n)
+{
+    if (!ctx) return fail(MAPPER_EINVAL, "null context");
+    if (tile_n != 0 && tile_n != 128 && tile_n != 256) return fail(MAPPER_EINVAL, "tile_n must be 0, 128 or 256");
+    ctx->pass1_forced = tile_n;
     return MAPPER_OK;
 }
 

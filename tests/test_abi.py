@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version_and_strings(lib):
-    assert lib.mapper_abi_version() == 1
+    assert lib.mapper_abi_version() == 2
     assert lib.mapper_strerror(0) == b"ok"
     assert lib.mapper_strerror(-4) == b"device wait timed out"
 
@@ -48,7 +48,7 @@ def test_struct_layouts_match_header():
     # mapper_params: 7 int32, pad to 8, 2 doubles, double, 2 int32
     assert ctypes.sizeof(_capi.MapperParams) == 64
     assert _capi.MapperParams.overlap.offset == 32
-    assert ctypes.sizeof(_capi.MapperStats) == 8 * 32
+    assert ctypes.sizeof(_capi.MapperStats) == 8 * 33
 
 
 def test_null_and_bad_arguments_are_rejected_without_a_gpu(lib):

@@ -270,6 +270,38 @@ def _check_graph_properties(res, n_points):
     assert sorted(pairs) == [tuple(e) for e in E.tolist()]
 
 
+@pytest.mark.parametrize("prec", [mg.BF16, mg.BF16X1])
+def test_pass1_shapes_agree(prec):
+    """Both pass-1 product shapes (one tile pair per item, N = 128; two pairs
+    sharing tile A, N = 256) and the autotuner's pick give the same exact
+    graph, equal to the oracle's."""
+    w = synth.mixture_100k()
+    Xd = torch.from_numpy(w.X).to("cuda:0")
+    prm = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, prec)
+    outs = []
+    for tile_n in (128, 256, 0):
+        with mg.Context(0) as c:
+            c.set_pass1_tile_n(tile_n)
+            g = c_graph = mg.mapper_graph(c, Xd, prm)
+            st = g.stats()
+            assert st["tile_pairs_tc"] > 0
+            assert st["pass1_tile_n"] in ((128, 256) if tile_n == 0 else (tile_n,))
+            out = g.numpy()
+            out["lens"], out["pca"] = g.lens(w.n, 1)
+            out["elem_offsets"], out["elem_points"] = g.cover().numpy()
+            out["labels"], out["core"] = g.clusters().numpy(len(out["elem_points"]))
+            out["stats"] = st
+            outs.append(out)
+            del g, c_graph
+    for o in outs[1:]:
+        for k in ("elem_points", "core", "labels", "node_offsets", "node_members", "node_elem", "edges"):
+            assert np.array_equal(o[k], outs[0][k]), k
+    assert_same_graph(w.X, outs[0], w.n_intervals, w.overlap, w.eps, w.min_pts)
+    with mg.Context(0) as c:
+        with pytest.raises(mg.MapperError):
+            c.set_pass1_tile_n(64)
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("prec", [mg.BF16, mg.FP32])
 def test_clusters_1m_d256_sampled(ctx, prec):
