@@ -542,7 +542,8 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         // capacity n and reads its length there, so the rounds need no host
         // round trip
         static const int kBounds[] = {-1, 1, 4, 16, 64, INT_MAX};
-        Buf hits, sel, kept, cnt;
+        Buf hits, sel, kept, cnt, troots;
+        CK(troots.alloc(sizeof(int2) * std::max<int64_t>(L.T, 1), s), "alloc");
         CK(hits.alloc(sizeof(int2) * n, s), "alloc");
         CK(sel.alloc(sizeof(int2) * n, s), "alloc");
         CK(kept.alloc(sizeof(int2) * n, s), "alloc");
@@ -560,7 +561,8 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
             const int2* list = sel.as<int2>();
             const unsigned long long* c_list = c_sel;
             if (k > 0 || cap) {
-                CK(filter_joined(base, sel.as<int2>(), n, c_sel, kept.as<int2>(), c_kept, s), "filter");
+                CK(filter_joined(base, L.T, troots.as<int2>(), sel.as<int2>(), n, c_sel, kept.as<int2>(), c_kept, s),
+                   "filter");
                 list = kept.as<int2>();
                 c_list = c_kept;
             }

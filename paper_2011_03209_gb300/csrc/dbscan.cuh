@@ -116,9 +116,10 @@ cudaError_t select_delta(const int2* pairs, int64_t n, const unsigned long long*
                          unsigned long long* count, cudaStream_t s);
 // Keeps the union-pass tile pairs of pairs[0 .. *n_dev) (at most n) whose
 // core rows do not all share one root yet (flagging kPairOneEach pairs);
-// *count receives the size.
-cudaError_t filter_joined(const PassArgs& a, const int2* pairs, int64_t n, const unsigned long long* n_dev,
-                          int2* out, unsigned long long* count, cudaStream_t s);
+// *count receives the size. tile_roots: scratch of T entries (the current
+// root range of each of the T tiles).
+cudaError_t filter_joined(const PassArgs& a, int64_t T, int2* tile_roots, const int2* pairs, int64_t n,
+                          const unsigned long long* n_dev, int2* out, unsigned long long* count, cudaStream_t s);
 
 // --- nodes and nerve (k_nerve.cu)
 cudaError_t member_keys(const int32_t* lab, const int64_t* nid, const int64_t* mpos,

@@ -592,50 +592,66 @@ __global__ void select_delta_kernel(const int2* __restrict__ pairs, int64_t n,
     if (delta > lo && delta <= hi) out[atomicAdd(count, 1ull)] = p;
 }
 
-// One warp per tile pair: roots of all core rows. Kept if they differ; an
-// off-diagonal pair whose A cores share one root and whose B cores share
-// another is flagged (kPairOneEach): one neighbour pair joins them.
-__global__ void filter_joined_kernel(const PassArgs A, const int2* __restrict__ pairs, int64_t n,
-                                     const unsigned long long* __restrict__ n_dev, int2* __restrict__ out,
-                                     unsigned long long* __restrict__ count)
+// Smallest and largest current root over each tile's core rows (INT_MAX,
+// -1 for a tile without core rows); one warp per tile.
+__global__ void tile_roots_kernel(const PassArgs A, int64_t T, int2* __restrict__ tr)
 {
-    if (n_dev) n = min(n, (int64_t)*n_dev);
     const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t q = warp; q < n; q += nwarp) {
-        const int2 p = pairs[q];
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= T) return;
+    const int nt = A.tile_n[t];
+    int lo = INT_MAX, hi = -1;
+    for (int x = lane; x < nt; x += 32) {
+        const int64_t row = t * kT + x;
+        if (!A.core[row]) continue;
+        const int r = gfind(A.parent, (int)row);
+        lo = min(lo, r);
+        hi = max(hi, r);
+    }
+    for (int o = 16; o; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) tr[t] = make_int2(lo, hi);
+}
+
+// A tile pair is kept if the roots of its core rows differ (read from the
+// tiles' root ranges); an off-diagonal pair whose A cores share one root and
+// whose B cores share another is flagged (kPairOneEach): one neighbour pair
+// joins them. One thread per pair.
+__global__ void filter_joined_kernel(const int2* __restrict__ pairs, int64_t n,
+                                     const unsigned long long* __restrict__ n_dev, const int2* __restrict__ tr,
+                                     int2* __restrict__ out, unsigned long long* __restrict__ count,
+                                     unsigned long long* __restrict__ stats)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n_dev) n = min(n, (int64_t)*n_dev);
+    bool keep = false, skipped = false;
+    int2 p = make_int2(0, 0);
+    if (i < n) {
+        p = pairs[i];
         const bool diag = p.x == p.y;
-        const int na = A.tile_n[p.x], nb = A.tile_n[p.y];
-        int loA = INT_MAX, hiA = -1, loB = INT_MAX, hiB = -1;
-        for (int x = lane; x < 2 * kT; x += 32) {
-            const bool side_b = x >= kT;
-            const int i = side_b ? x - kT : x;
-            if (side_b ? (diag || i >= nb) : i >= na) continue;
-            const int64_t row = (int64_t)(side_b ? p.y : p.x) * kT + i;
-            if (!A.core[row]) continue;
-            const int r = gfind(A.parent, (int)row);
-            if (side_b) { loB = min(loB, r); hiB = max(hiB, r); }
-            else { loA = min(loA, r); hiA = max(hiA, r); }
-        }
-        for (int o = 16; o; o >>= 1) {
-            loA = min(loA, __shfl_xor_sync(0xffffffffu, loA, o));
-            hiA = max(hiA, __shfl_xor_sync(0xffffffffu, hiA, o));
-            loB = min(loB, __shfl_xor_sync(0xffffffffu, loB, o));
-            hiB = max(hiB, __shfl_xor_sync(0xffffffffu, hiB, o));
-        }
+        const int2 a = tr[p.x], b = tr[p.y];
         bool work, one_each = false;
         if (diag) {
-            work = hiA >= 0 && loA != hiA;
+            work = a.y >= 0 && a.x != a.y;
         } else {
-            work = hiA >= 0 && hiB >= 0 && (loA != hiA || loB != hiB || loA != loB);
-            one_each = work && loA == hiA && loB == hiB;
+            work = a.y >= 0 && b.y >= 0 && (a.x != a.y || b.x != b.y || a.x != b.x);
+            one_each = work && a.x == a.y && b.x == b.y;
         }
-        if (lane == 0) {
-            if (work) out[atomicAdd(count, 1ull)] = make_int2(p.x, p.y | (one_each ? kPairOneEach : 0));
-            else if (hiA >= 0) atomicAdd(&A.stats[kStatSkipped], 1ull);
-        }
+        keep = work;
+        skipped = !work && a.y >= 0;
+        if (one_each) p.y |= kPairOneEach;
     }
+    // one output atomic per warp
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    unsigned long long base = 0;
+    const int lane = threadIdx.x & 31;
+    if (lane == 0 && m) base = atomicAdd(count, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (keep) out[base + __popc(m & ((1u << lane) - 1u))] = p;
+    const unsigned ms = __ballot_sync(0xffffffffu, skipped);
+    if (lane == 0 && ms) atomicAdd(&stats[kStatSkipped], (unsigned long long)__popc(ms));
 }
 
 inline unsigned grid_for(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, div_up(n, t)); }
@@ -669,13 +685,13 @@ cudaError_t select_delta(const int2* pairs, int64_t n, const unsigned long long*
     return cudaGetLastError();
 }
 
-cudaError_t filter_joined(const PassArgs& a, const int2* pairs, int64_t n, const unsigned long long* n_dev,
-                          int2* out, unsigned long long* count, cudaStream_t s)
+cudaError_t filter_joined(const PassArgs& a, int64_t T, int2* tile_roots, const int2* pairs, int64_t n,
+                          const unsigned long long* n_dev, int2* out, unsigned long long* count, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    filter_joined_kernel<<<(unsigned)std::min<int64_t>(div_up(n, 8), 152 * 32), 256, 0, s>>>(a, pairs, n, n_dev,
-                                                                                           out, count);
-    note_launch();
+    tile_roots_kernel<<<grid_for(T * 32), 256, 0, s>>>(a, T, tile_roots);
+    filter_joined_kernel<<<grid_for(n), 256, 0, s>>>(pairs, n, n_dev, tile_roots, out, count, a.stats);
+    note_launch(2);
     return cudaGetLastError();
 }
 
