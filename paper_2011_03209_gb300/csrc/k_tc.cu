@@ -291,7 +291,7 @@ struct SmemTail {
     float red[2][8];                           // max |b|^2 and |b| of the columns, per warp
     __align__(16) float nbn[2][kT];            // -|b|^2 of the pair's columns
     uint32_t colmask[4][kT];                   // count pass: neighbour bits per column (by row quadrant)
-    uint32_t rowmask[4 * kChunks][kT];         // count pass: neighbour bits per row (by 32-column chunk)
+    uint32_t rowmask[kT / 32][kT];             // neighbour bits per row (by 32-column chunk)
     int par[2][2 * kT];                        // union pass: local union-find / component
     int groot[2][2 * kT];                      // union pass: global root of each core row
     int edges[2];                              // union pass: certain core-core pairs
@@ -776,7 +776,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                     int tot = 0;
                     if (is_row) {
 #pragma unroll
-                        for (int w = 0; w < 4 * kChunks; ++w) tot += __popc(S.rowmask[w][x]);
+                        for (int w = 0; w < kT / 32; ++w) tot += __popc(S.rowmask[w][x]);
                     } else {
 #pragma unroll
                         for (int w = 0; w < 4; ++w) tot += __popc(S.colmask[w][x]);
@@ -787,7 +787,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                         } else {
                             const int old = atomicAdd(&A.count[row], tot);
                             int pos = old;
-                            for (int w = 0; w < 4 * kChunks && pos < A.cap; ++w) {
+                            for (int w = 0; w < kT / 32 && pos < A.cap; ++w) {
                                 uint32_t bm = is_row ? S.rowmask[w][x] : S.colmask[w & 3][x];
                                 if (!is_row && w >= 4) bm = 0u;
                                 while (bm && pos < A.cap) {
