@@ -200,6 +200,30 @@ int mapper_clusters_copy(const mapper_clusters_t* clusters, int64_t* label, uint
 /* Nerve (§3: 1D nerve; an edge where two clusters intersect). */
 int mapper_nerve(mapper_ctx* ctx, const mapper_clusters_t* clusters, mapper_graph_t** out);
 
+/* Element sharding across GPUs (§4.3: the clustering of each cover element
+ * is independent; §6 names distributing it across several GPUs, with the
+ * merge of results, as the next step). A rank clusters a subset of the
+ * elements, the ranks exchange their nodes, and every rank builds the nerve
+ * of the merged node list.
+ *
+ * mapper_cover_subset: a cover holding only elements[0 .. k) of `cover`
+ * (host int32 indices, distinct, in [0, n_elements)), renumbered 0 .. k-1 in
+ * the given order, each with its points ascending as before. The result is
+ * a new cover handle (release with mapper_free); MAPPER_EINVAL for an index
+ * out of range or repeated.
+ *
+ * mapper_nerve_from_nodes: a graph whose nodes are given (node u = members
+ * node_members[node_offsets[u] .. node_offsets[u+1]) of points in
+ * [0, n_points), ascending, and node_elem[u] its element) and whose edges
+ * are computed here as in mapper_nerve. The three arrays may be host or
+ * device pointers (all of one kind) and are copied; node_offsets has
+ * n_nodes + 1 entries starting at 0. The graph has no lens, cover or
+ * clusters (mapper_graph_cover / _clusters return NULL). */
+int mapper_cover_subset(mapper_ctx* ctx, const mapper_cover_t* cover, const int32_t* elements, int32_t k,
+                        mapper_cover_t** out);
+int mapper_nerve_from_nodes(mapper_ctx* ctx, int64_t n_points, int64_t n_nodes, const int64_t* node_offsets,
+                            const int32_t* node_members, const int32_t* node_elem, mapper_graph_t** out);
+
 /* Fused call: lens, cover, cluster and nerve in one. X may be a device
  * pointer or a host pointer (pinned or pageable); a host X is copied to the
  * device inside the call. */

@@ -20,7 +20,7 @@ __all__ = [
     "Context", "Cover", "Clusters", "Graph", "MapperError", "mapper_lens", "mapper_cover",
     "mapper_cluster", "mapper_nerve", "mapper_graph", "params", "LENS_L2", "LENS_COORD",
     "LENS_PCA", "FP32", "BF16", "BF16X1", "mapper_dbscan_noalloc", "Server", "graph_footprint",
-    "mapper_graph_sweep",
+    "mapper_graph_sweep", "mapper_cover_subset", "mapper_nerve_from_nodes",
 ]
 
 
@@ -226,6 +226,31 @@ def mapper_cluster(ctx: Context, X, cover: Cover, eps: float, min_pts: int, prec
 def mapper_nerve(ctx: Context, clusters: Clusters) -> Graph:
     h = ctypes.c_void_p()
     _capi.check(ctx._lib.mapper_nerve(ctx.h, clusters.h, ctypes.byref(h)), "mapper_nerve")
+    return Graph(ctx._lib, h)
+
+
+def mapper_cover_subset(ctx: Context, cover: Cover, elements) -> Cover:
+    """A cover of the given elements of `cover` (renumbered in that order)."""
+    el = np.ascontiguousarray(np.asarray(elements, dtype=np.int32))
+    h = ctypes.c_void_p()
+    _capi.check(ctx._lib.mapper_cover_subset(ctx.h, cover.h, _vp(el.ctypes.data) if el.size else None,
+                                             int(el.size), ctypes.byref(h)), "mapper_cover_subset")
+    return Cover(ctx._lib, h)
+
+
+def mapper_nerve_from_nodes(ctx: Context, n_points: int, node_offsets, node_members, node_elem) -> Graph:
+    """Graph of the given nodes (host arrays) with its nerve edges computed on
+    the device."""
+    off = np.ascontiguousarray(np.asarray(node_offsets, dtype=np.int64))
+    mem = np.ascontiguousarray(np.asarray(node_members, dtype=np.int32))
+    elm = np.ascontiguousarray(np.asarray(node_elem, dtype=np.int32))
+    N = off.size - 1
+    mem_p = mem if mem.size else np.zeros(1, dtype=np.int32)
+    elm_p = elm if elm.size else np.zeros(1, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _capi.check(ctx._lib.mapper_nerve_from_nodes(ctx.h, int(n_points), N, _vp(off.ctypes.data),
+                                                 _vp(mem_p.ctypes.data), _vp(elm_p.ctypes.data),
+                                                 ctypes.byref(h)), "mapper_nerve_from_nodes")
     return Graph(ctx._lib, h)
 
 

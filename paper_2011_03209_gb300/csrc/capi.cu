@@ -641,6 +641,8 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
 }
 
 // ------------------------------------------------------------------ nerve
+int nerve_edges(mapper_ctx* ctx, uint64_t* keys2, int64_t Gm, int64_t n_points, int64_t N, mapper_graph_t* g);
+
 int run_nerve(mapper_ctx* ctx, const std::shared_ptr<ClusterData>& cl, mapper_graph_t* g)
 {
     cudaStream_t s = ctx->stream->s;
@@ -673,12 +675,27 @@ int run_nerve(mapper_ctx* ctx, const std::shared_ptr<ClusterData>& cl, mapper_gr
                     keys2.as<uint64_t>(), s), "node offsets");
     CK(cudaMemcpyAsync(g->node_off.as<int64_t>() + N, &g->Gm, sizeof(int64_t), cudaMemcpyHostToDevice, s),
        "copy");
-    // nerve: group memberships by point, emit node pairs, sort, unique
-    CK(radix_sort_u64(keys2.as<uint64_t>(), tmp.as<uint64_t>(), Gm, 32, 32 + bits_for(cov->n), s), "sort");
+    int rc = nerve_edges(ctx, keys2.as<uint64_t>(), Gm, cov->n, N, g);
+    if (rc) return rc;
+    g->stats = cl->stats;
+    g->stats.n_nodes = N;
+    g->stats.n_edges = g->Eg;
+    return MAPPER_OK;
+}
+
+// Nerve edges from the memberships (point << 32 | node) of N nodes (the keys
+// are sorted in place): group by point, emit each point's node pairs, sort,
+// unique. Sets g->edges and g->Eg.
+int nerve_edges(mapper_ctx* ctx, uint64_t* keys2, int64_t Gm, int64_t n_points, int64_t N, mapper_graph_t* g)
+{
+    cudaStream_t s = ctx->stream->s;
+    Buf tmp;
+    CK(tmp.alloc(sizeof(uint64_t) * std::max<int64_t>(Gm, 1), s), "alloc");
+    CK(radix_sort_u64(keys2, tmp.as<uint64_t>(), Gm, 32, 32 + bits_for(n_points), s), "sort");
     Buf cnt, ppos;
     CK(cnt.alloc(sizeof(int64_t) * Gm, s), "alloc");
     CK(ppos.alloc(sizeof(int64_t) * (Gm + 1), s), "alloc");
-    CK(run_pairs(keys2.as<uint64_t>(), Gm, cnt.as<int64_t>(), s), "run pairs");
+    CK(run_pairs(keys2, Gm, cnt.as<int64_t>(), s), "run pairs");
     CK(exclusive_scan_i64(cnt.as<int64_t>(), ppos.as<int64_t>(), Gm, s), "scan");
     int64_t P = 0;
     CK(cudaMemcpyAsync(&P, ppos.as<int64_t>() + Gm, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "copy");
@@ -686,7 +703,7 @@ int run_nerve(mapper_ctx* ctx, const std::shared_ptr<ClusterData>& cl, mapper_gr
     Buf pairs, ptmp, flag, upos;
     CK(pairs.alloc(sizeof(uint64_t) * P, s), "alloc");
     CK(ptmp.alloc(sizeof(uint64_t) * P, s), "alloc");
-    CK(emit_pairs(keys2.as<uint64_t>(), Gm, ppos.as<int64_t>(), pairs.as<uint64_t>(), s), "emit pairs");
+    CK(emit_pairs(keys2, Gm, ppos.as<int64_t>(), pairs.as<uint64_t>(), s), "emit pairs");
     const int nb = bits_for(N);
     CK(radix_sort_u64(pairs.as<uint64_t>(), ptmp.as<uint64_t>(), P, 0, nb, s), "sort");
     CK(radix_sort_u64(pairs.as<uint64_t>(), ptmp.as<uint64_t>(), P, 32, 32 + nb, s), "sort");
@@ -702,9 +719,6 @@ int run_nerve(mapper_ctx* ctx, const std::shared_ptr<ClusterData>& cl, mapper_gr
     CK(unique_emit(pairs.as<uint64_t>(), flag.as<int32_t>(), upos.as<int64_t>(), P,
                    g->edges.as<int32_t>(), s), "unique emit");
     CK(cudaStreamSynchronize(s), "sync");
-    g->stats = cl->stats;
-    g->stats.n_nodes = N;
-    g->stats.n_edges = Eg;
     return MAPPER_OK;
 }
 
@@ -936,6 +950,95 @@ int mapper_nerve(mapper_ctx* ctx, const mapper_clusters_t* clusters, mapper_grap
     return MAPPER_OK;
 }
 
+int mapper_cover_subset(mapper_ctx* ctx, const mapper_cover_t* cover, const int32_t* elements, int32_t k,
+                        mapper_cover_t** out)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    auto* h = handle_as<mapper_cover_t>(cover, kKindCover);
+    if (!h || !out || (k > 0 && !elements) || k < 0) return fail(MAPPER_EINVAL, "bad cover subset arguments");
+    *out = nullptr;
+    const auto& src = *h->c;
+    std::vector<char> seen(src.E, 0);
+    auto c = std::make_shared<CoverData>();
+    c->stream = ctx->stream;
+    c->m = src.m;
+    c->n_int[0] = src.n_int[0];
+    c->n_int[1] = src.n_int[1];
+    c->overlap[0] = src.overlap[0];
+    c->overlap[1] = src.overlap[1];
+    c->n = src.n;
+    c->E = k;
+    c->h_elem_off.assign(1, 0);
+    for (int32_t j = 0; j < k; ++j) {
+        const int32_t e = elements[j];
+        if (e < 0 || e >= src.E || seen[e]) return fail(MAPPER_EINVAL, "element index out of range or repeated");
+        seen[e] = 1;
+        c->h_elem_off.push_back(c->h_elem_off.back() + (src.h_elem_off[e + 1] - src.h_elem_off[e]));
+    }
+    c->M = c->h_elem_off.back();
+    cudaStream_t s = ctx->stream->s;
+    CK(c->elem_off.alloc(sizeof(int64_t) * (k + 1), s), "alloc");
+    CK(c->slot_point.alloc(sizeof(int32_t) * std::max<int64_t>(c->M, 1), s), "alloc");
+    CK(c->slot_elem.alloc(sizeof(int32_t) * std::max<int64_t>(c->M, 1), s), "alloc");
+    CK(cudaMemcpyAsync(c->elem_off.p, c->h_elem_off.data(), sizeof(int64_t) * (k + 1), cudaMemcpyHostToDevice, s),
+       "copy");
+    for (int32_t j = 0; j < k; ++j) {
+        const int32_t e = elements[j];
+        const int64_t len = src.h_elem_off[e + 1] - src.h_elem_off[e];
+        if (len)
+            CK(cudaMemcpyAsync(c->slot_point.as<int32_t>() + c->h_elem_off[j],
+                               src.slot_point.as<int32_t>() + src.h_elem_off[e], sizeof(int32_t) * len,
+                               cudaMemcpyDeviceToDevice, s), "copy");
+    }
+    CK(fill_slot_elem(c->elem_off.as<int64_t>(), k, c->M, c->slot_elem.as<int32_t>(), s), "slot elements");
+    CK(cudaStreamSynchronize(s), "sync");                 // h_elem_off copied before it goes out of scope
+    auto o = new mapper_cover_t;
+    o->c = c;
+    *out = o;
+    return MAPPER_OK;
+}
+
+int mapper_nerve_from_nodes(mapper_ctx* ctx, int64_t n_points, int64_t n_nodes, const int64_t* node_offsets,
+                            const int32_t* node_members, const int32_t* node_elem, mapper_graph_t** out)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (!out || n_points < 1 || n_points > INT32_MAX || n_nodes < 0 || !node_offsets ||
+        (n_nodes > 0 && (!node_members || !node_elem)))
+        return fail(MAPPER_EINVAL, "bad node arguments");
+    *out = nullptr;
+    cudaStream_t s = ctx->stream->s;
+    auto g = std::make_unique<mapper_graph_t>();
+    g->stream = ctx->stream;
+    g->n = n_points;
+    g->N = n_nodes;
+    const bool host = is_host_pointer(node_offsets);
+    const cudaMemcpyKind kind = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    CK(g->node_off.alloc(sizeof(int64_t) * (n_nodes + 1), s), "alloc");
+    CK(cudaMemcpyAsync(g->node_off.p, node_offsets, sizeof(int64_t) * (n_nodes + 1), kind, s), "copy");
+    int64_t Gm = 0;
+    CK(cudaMemcpyAsync(&Gm, g->node_off.as<int64_t>() + n_nodes, sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+       "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    if (Gm < 0 || Gm > INT32_MAX) return fail(MAPPER_EINVAL, "bad node offsets");
+    g->Gm = Gm;
+    CK(g->node_members.alloc(sizeof(int32_t) * std::max<int64_t>(Gm, 1), s), "alloc");
+    CK(g->node_elem.alloc(sizeof(int32_t) * std::max<int64_t>(n_nodes, 1), s), "alloc");
+    if (Gm) CK(cudaMemcpyAsync(g->node_members.p, node_members, sizeof(int32_t) * Gm, kind, s), "copy");
+    if (n_nodes) CK(cudaMemcpyAsync(g->node_elem.p, node_elem, sizeof(int32_t) * n_nodes, kind, s), "copy");
+    Buf keys2;
+    CK(keys2.alloc(sizeof(uint64_t) * std::max<int64_t>(Gm, 1), s), "alloc");
+    CK(node_member_keys(g->node_off.as<int64_t>(), n_nodes, Gm, g->node_members.as<int32_t>(),
+                        keys2.as<uint64_t>(), s), "member keys");
+    if ((rc = nerve_edges(ctx, keys2.as<uint64_t>(), Gm, n_points, n_nodes, g.get()))) return rc;
+    g->stats.n_points = n_points;
+    g->stats.n_nodes = n_nodes;
+    g->stats.n_edges = g->Eg;
+    *out = g.release();
+    return MAPPER_OK;
+}
+
 int mapper_graph(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
                  const mapper_params* p, mapper_graph_t** out)
 {
@@ -1151,13 +1254,13 @@ int mapper_graph_lens(const mapper_graph_t* g, double* lens, double* pca, int64_
 const mapper_cover_t* mapper_graph_cover(const mapper_graph_t* g)
 {
     auto* h = handle_as<mapper_graph_t>(g, kKindGraph);
-    return h ? &h->cover_view : nullptr;
+    return h && h->cover_view.c ? &h->cover_view : nullptr;
 }
 
 const mapper_clusters_t* mapper_graph_clusters(const mapper_graph_t* g)
 {
     auto* h = handle_as<mapper_graph_t>(g, kKindGraph);
-    return h ? &h->clusters_view : nullptr;
+    return h && h->clusters_view.c ? &h->clusters_view : nullptr;
 }
 
 int mapper_stats_get(const void* handle, mapper_stats* out)

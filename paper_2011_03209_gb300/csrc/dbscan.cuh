@@ -122,6 +122,11 @@ cudaError_t filter_joined(const PassArgs& a, int64_t T, int2* tile_roots, const 
                           const unsigned long long* n_dev, int2* out, unsigned long long* count, cudaStream_t s);
 
 // --- nodes and nerve (k_nerve.cu)
+// Nerve keys (point << 32 | node) of the members of nodes given by offsets.
+cudaError_t node_member_keys(const int64_t* node_off, int64_t N, int64_t G, const int32_t* members,
+                             uint64_t* keys2, cudaStream_t s);
+// slot_elem[i] = the element e with elem_off[e] <= i < elem_off[e + 1].
+cudaError_t fill_slot_elem(const int64_t* elem_off, int32_t k, int64_t M, int32_t* slot_elem, cudaStream_t s);
 cudaError_t member_keys(const int32_t* lab, const int64_t* nid, const int64_t* mpos,
                         const int32_t* slot_point, const int32_t* slot_elem, int64_t M,
                         uint64_t* keys, int32_t* node_elem, cudaStream_t s);

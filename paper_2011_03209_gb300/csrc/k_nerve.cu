@@ -42,6 +42,35 @@ __global__ void node_offsets_kernel(const uint64_t* __restrict__ keys, int64_t G
     if (i == 0 || (int64_t)(keys[i - 1] >> 32) != node) node_off[node] = i;
 }
 
+// Nerve keys (point << 32 | node) of given nodes: member i belongs to the
+// node u with node_off[u] <= i < node_off[u + 1].
+__global__ void node_member_keys_kernel(const int64_t* __restrict__ node_off, int64_t N, int64_t G,
+                                        const int32_t* __restrict__ members, uint64_t* __restrict__ keys2)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= G) return;
+    int64_t lo = 0, hi = N;                    // last u with node_off[u] <= i
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (node_off[mid] <= i) lo = mid; else hi = mid;
+    }
+    keys2[i] = ((uint64_t)(uint32_t)members[i] << 32) | (uint64_t)lo;
+}
+
+// Slot -> element index of a cover whose element offsets are elem_off[0..k].
+__global__ void fill_slot_elem_kernel(const int64_t* __restrict__ elem_off, int32_t k, int64_t M,
+                                      int32_t* __restrict__ slot_elem)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    int32_t lo = 0, hi = k;                    // last e with elem_off[e] <= i
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (elem_off[mid] <= i) lo = mid; else hi = mid;
+    }
+    slot_elem[i] = lo;
+}
+
 __global__ void run_pairs_kernel(const uint64_t* __restrict__ keys2, int64_t G,
                                  int64_t* __restrict__ cnt)
 {
@@ -110,6 +139,21 @@ cudaError_t node_offsets(const uint64_t* keys, int64_t G, int64_t* node_off, int
 {
     if (G == 0) return cudaSuccess;
     { node_offsets_kernel<<<grid_for(G), 256, 0, s>>>(keys, G, node_off, members, keys2); note_launch(); }
+    return cudaGetLastError();
+}
+
+cudaError_t node_member_keys(const int64_t* node_off, int64_t N, int64_t G, const int32_t* members,
+                             uint64_t* keys2, cudaStream_t s)
+{
+    if (G == 0 || N == 0) return cudaSuccess;
+    { node_member_keys_kernel<<<grid_for(G), 256, 0, s>>>(node_off, N, G, members, keys2); note_launch(); }
+    return cudaGetLastError();
+}
+
+cudaError_t fill_slot_elem(const int64_t* elem_off, int32_t k, int64_t M, int32_t* slot_elem, cudaStream_t s)
+{
+    if (M == 0 || k == 0) return cudaSuccess;
+    { fill_slot_elem_kernel<<<grid_for(M), 256, 0, s>>>(elem_off, k, M, slot_elem); note_launch(); }
     return cudaGetLastError();
 }
 
