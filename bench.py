@@ -422,6 +422,69 @@ def run_sweep(args):
     }))
 
 
+def run_sharded(args):
+    """One 1M x 256 graph per step with its cover elements split over the
+    ranks (longest processing time by n_i^2 d), each rank clustering its
+    share; the ranks exchange their nodes (one all-gather) and every rank
+    builds the nerve of the merged nodes. Strong scaling: the value is the
+    time of one whole graph."""
+    import torch
+    import paper_2011_03209_gb300 as mg
+    from paper_2011_03209_gb300 import sharded
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prec = {"bf16": mg.BF16, "bf16x1": mg.BF16X1, "fp32": mg.FP32}[args.precision]
+    w = synth.clusters_1m_d256(args.n)
+    Xd = torch.from_numpy(w.X).to(f"cuda:{local}")
+    stream = torch.cuda.Stream()
+    ctx = mg.Context(local, stream=stream)
+    prm = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, prec)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            g, _ = sharded.sharded_graph(ctx, Xd, prm)
+            del g
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        sampler = ClockSampler(local)
+        sampler.start()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(args.steps):
+            g, mine = sharded.sharded_graph(ctx, Xd, prm)
+            sizes = g.sizes()
+            del g
+        end.record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        clocks = sampler.stop()
+    ms = start.elapsed_time(end) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "strong",
+            "vs_baseline": None, "dtype": "bf16+f64" if prec != mg.FP32 else "f32+f64", "data": "synthetic",
+            "config": {"workload": f"clusters_{w.n // 1000}k_d{w.d}_sharded", "n": w.n, "d": w.d,
+                       "parallelism": f"elements over {world} ranks, one node all-gather",
+                       "l2_flush": "inputs larger than L2 (1 GB point cloud read every step)"},
+            "elements_rank0": int(mine.size), "nodes": int(sizes[0]), "edges": int(sizes[2]), "clocks": clocks,
+        }))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -432,9 +495,10 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=12.0,
                     help="seconds of oracle DBSCAN per reference sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="clusters", choices=["clusters", "serving", "sweep"],
-                    help="clusters: the 1M x 256 graph (default); serving: the request mix; "
-                         "sweep: 16 graphs of the 500k x 128 2D-lens cloud")
+    ap.add_argument("--workload", default="clusters", choices=["clusters", "serving", "sweep", "sharded"],
+                    help="clusters: the 1M x 256 graph (default; N ranks = N replicas); serving: the "
+                         "request mix; sweep: 16 graphs of the 500k x 128 2D-lens cloud; sharded: the "
+                         "1M x 256 graph with its elements split over the ranks")
     ap.add_argument("--requests", type=int, default=200, help="serving: timed requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent slots")
@@ -447,6 +511,8 @@ def main():
         run_serving(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "sharded":
+        run_sharded(args)
     else:
         run_ours(args)
 
