@@ -59,6 +59,7 @@ def _load():
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
         lib.oracle_lens_l2.argtypes = [P, i64, i32, i64, P]
+        lib.oracle_lens_ecc2.argtypes = [P, i64, i32, i64, P]
         lib.oracle_lens_coord.argtypes = [P, i64, i32, i64, i32, P]
         lib.oracle_lens_project.argtypes = [P, i64, i32, i64, P, P, P]
         lib.oracle_pca.argtypes = [P, i64, i32, i64, i32, P, P, P]
@@ -97,6 +98,15 @@ def lens_l2(X) -> np.ndarray:
     X = _f32(X)
     f = np.empty(X.shape[0], dtype=np.float64)
     _load().oracle_lens_l2(_ptr(X), X.shape[0], X.shape[1], X.shape[1], _ptr(f))
+    return f
+
+
+def lens_ecc2(X) -> np.ndarray:
+    """Eccentricity with exponent 2 (root mean squared distance to the cloud),
+    O(n^2 d): small clouds only."""
+    X = _f32(X)
+    f = np.empty(X.shape[0], dtype=np.float64)
+    _load().oracle_lens_ecc2(_ptr(X), X.shape[0], X.shape[1], X.shape[1], _ptr(f))
     return f
 
 
@@ -146,6 +156,8 @@ def lens(X, kinds, args, pca_basis=None) -> np.ndarray:
                 mu, V, _ = pca(X, max(a for kk, a in zip(kinds, args) if kk == 2) + 1)
                 basis = (mu, V)
             cols.append(lens_project(X, basis[0], basis[1][arg]))
+        elif kind == 3:
+            cols.append(lens_ecc2(X))
         else:
             raise ValueError(kind)
     return np.ascontiguousarray(np.stack(cols, axis=1))

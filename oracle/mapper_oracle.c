@@ -77,6 +77,31 @@ void oracle_lens_l2(const float* X, int64_t n, int32_t d, int64_t ld, double* f)
     }
 }
 
+/* Eccentricity filter (§3 lists eccentricity among the common filters;
+ * §4.1 offers it beside the L2 norm and density), exponent 2:
+ *   f(x) = ( (1/n) sum_{y in X} d(x, y)^2 )^(1/2),
+ * d the Euclidean distance. Direct O(n^2 d) form: for each x, the squared
+ * distances summed over y ascending (each a k-ascending double sum), divided
+ * by n, square root. */
+void oracle_lens_ecc2(const float* X, int64_t n, int32_t d, int64_t ld, double* f)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t p = 0; p < n; ++p) {
+        const float* x = X + p * ld;
+        double s = 0.0;
+        for (int64_t q = 0; q < n; ++q) {
+            const float* y = X + q * ld;
+            double d2 = 0.0;
+            for (int32_t k = 0; k < d; ++k) {
+                double t = (double)x[k] - (double)y[k];
+                d2 = d2 + t * t;
+            }
+            s = s + d2;
+        }
+        f[p] = sqrt(s / (double)n);
+    }
+}
+
 /* Filter "based on a chosen dimension (column)" (§4.1): f(x) = x_j. */
 void oracle_lens_coord(const float* X, int64_t n, int32_t d, int64_t ld, int32_t j, double* f)
 {

@@ -20,6 +20,35 @@ def test_l2_lens_closed_form_and_numpy():
     np.testing.assert_allclose(oracle.lens_l2(Y), ref, rtol=1e-14, atol=0)
 
 
+def test_eccentricity_closed_forms():
+    """Eccentricity with exponent 2, pinned by hand-derived values."""
+    # two points at distance 5: each has mean squared distance 25 / 2
+    f = oracle.lens_ecc2(np.array([[0.0, 0.0], [3.0, 4.0]], dtype=np.float32))
+    np.testing.assert_allclose(f, [5.0 / np.sqrt(2.0)] * 2, rtol=1e-15)
+    # {-1, 0, 1} on a line: f(0)^2 = (1 + 0 + 1) / 3, f(+-1)^2 = (0 + 1 + 4) / 3
+    f = oracle.lens_ecc2(np.array([[-1.0], [0.0], [1.0]], dtype=np.float32))
+    np.testing.assert_allclose(f, [np.sqrt(5 / 3), np.sqrt(2 / 3), np.sqrt(5 / 3)], rtol=1e-15)
+    # the n unit vectors of R^n: every pair at distance sqrt(2), so f^2 = 2 (n - 1) / n
+    n = 7
+    f = oracle.lens_ecc2(np.eye(n, dtype=np.float32))
+    np.testing.assert_allclose(f, np.sqrt(2.0 * (n - 1) / n), rtol=1e-15)
+    # one point: zero
+    assert oracle.lens_ecc2(np.array([[2.5, -1.0, 7.0]], dtype=np.float32))[0] == 0.0
+
+
+def test_eccentricity_invariants():
+    """Translation invariance, and the parallel-axis identity
+    mean_y |x - y|^2 = |x - mu|^2 + mean_y |y - mu|^2 (mu the mean)."""
+    Y = np.round(synth.tiny_random(400, 11, seed=8, scale=3.0) * 64.0).astype(np.float32) / 64.0
+    f = oracle.lens_ecc2(Y)
+    shifted = Y + np.float32(2.0)                      # exact: multiples of 1/64 below 8
+    np.testing.assert_allclose(oracle.lens_ecc2(shifted), f, rtol=1e-12)
+    Y64 = Y.astype(np.float64)
+    mu = Y64.mean(axis=0)
+    ident = np.sqrt(((Y64 - mu) ** 2).sum(axis=1) + ((Y64 - mu) ** 2).sum(axis=1).mean())
+    np.testing.assert_allclose(f, ident, rtol=1e-12)
+
+
 def test_coord_lens_is_the_column():
     Y = synth.tiny_random(100, 5, seed=4)
     for j in range(5):
