@@ -75,7 +75,9 @@ typedef enum mapper_status {
 typedef enum mapper_lens_kind {
     MAPPER_LENS_L2 = 0,      /* §3: "Common choices include the L2-norm" */
     MAPPER_LENS_COORD = 1,   /* §4.1: filter "based on a chosen dimension" */
-    MAPPER_LENS_PCA = 2      /* projection on a principal axis (PCA module, §4.1) */
+    MAPPER_LENS_PCA = 2,     /* projection on a principal axis (PCA module, §4.1) */
+    MAPPER_LENS_ECC = 3      /* eccentricity, exponent 2: sqrt(mean over the cloud of
+                                |x - y|^2) (§3 "eccentricity", §4.1 derived filters) */
 } mapper_lens_kind;
 
 /* Precision of the eps-neighbourhood screen. Every pair whose screened

@@ -14,12 +14,12 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _capi
-from ._capi import BF16, BF16X1, FP32, LENS_COORD, LENS_L2, LENS_PCA, MapperError, MapperParams
+from ._capi import BF16, BF16X1, FP32, LENS_COORD, LENS_ECC, LENS_L2, LENS_PCA, MapperError, MapperParams
 
 __all__ = [
     "Context", "Cover", "Clusters", "Graph", "MapperError", "mapper_lens", "mapper_cover",
     "mapper_cluster", "mapper_nerve", "mapper_graph", "params", "LENS_L2", "LENS_COORD",
-    "LENS_PCA", "FP32", "BF16", "BF16X1", "mapper_dbscan_noalloc", "Server", "graph_footprint",
+    "LENS_PCA", "LENS_ECC", "FP32", "BF16", "BF16X1", "mapper_dbscan_noalloc", "Server", "graph_footprint",
     "mapper_graph_sweep", "mapper_cover_subset", "mapper_nerve_from_nodes",
 ]
 

@@ -21,7 +21,7 @@ MAPPER_ENONFINITE = -5
 MAPPER_EINTERNAL = -6
 MAPPER_ENOTIMPL = -7
 
-LENS_L2, LENS_COORD, LENS_PCA = 0, 1, 2
+LENS_L2, LENS_COORD, LENS_PCA, LENS_ECC = 0, 1, 2, 3
 FP32, BF16, BF16X1 = 0, 1, 2
 
 # every symbol include/mapper.h declares

@@ -176,7 +176,7 @@ int run_lens(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld, 
             if (args[j] < 0 || args[j] >= d) return fail(MAPPER_EINVAL, "PCA axis out of range");
             K = std::max(K, args[j] + 1);
         }
-        if (kinds[j] < 0 || kinds[j] > 2) return fail(MAPPER_EINVAL, "unknown lens kind");
+        if (kinds[j] < 0 || kinds[j] > 3) return fail(MAPPER_EINVAL, "unknown lens kind");
     }
     *n_pca = 0;
     Buf status;
@@ -191,6 +191,8 @@ int run_lens(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld, 
         if (kinds[j] == MAPPER_LENS_L2) CK(lens_l2(X, n, d, ld, lens_dev, m, j, s), "lens_l2");
         else if (kinds[j] == MAPPER_LENS_COORD)
             CK(lens_coord(X, n, ld, args[j], lens_dev, m, j, s), "lens_coord");
+        else if (kinds[j] == MAPPER_LENS_ECC)
+            CK(lens_ecc2(X, n, d, ld, lens_dev, m, j, s), "lens_ecc2");
         else
             CK(lens_project(X, n, d, ld, pca_dev->as<double>(),
                             pca_dev->as<double>() + (size_t)d * (1 + args[j]), lens_dev, m, j, s),

@@ -62,6 +62,8 @@ struct Buf {
 // lens (k_lens.cu)
 cudaError_t lens_l2(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j,
                     cudaStream_t s);
+cudaError_t lens_ecc2(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j,
+                      cudaStream_t s);
 cudaError_t lens_coord(const float* X, int64_t n, int64_t ld, int32_t col, double* f, int m,
                        int j, cudaStream_t s);
 cudaError_t lens_project(const float* X, int64_t n, int32_t d, int64_t ld, const double* mu,

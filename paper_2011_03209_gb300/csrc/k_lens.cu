@@ -18,6 +18,7 @@ constexpr int kChunk = 32;    // columns staged per step
 // One CTA = 128 rows. Each warp loads whole 32-column row segments
 // (coalesced); then each thread consumes its row's segment in order.
 // MODE 0: sum x^2 then sqrt (L2). MODE 1: sum (x - mu) v (projection).
+// MODE 2: sum (x - mu)^2 (squared distance to the mean).
 template <int MODE>
 __global__ void __launch_bounds__(kRows) lens_rows_kernel(const float* __restrict__ X, int64_t n,
                                                           int32_t d, int64_t ld,
@@ -39,9 +40,9 @@ __global__ void __launch_bounds__(kRows) lens_rows_kernel(const float* __restric
             if (row < n && lane < kc) x = __ldg(X + row * ld + k0 + lane);
             tile[r][lane] = x;
         }
-        if (MODE == 1 && tid < kc) {
+        if (MODE >= 1 && tid < kc) {
             smu[tid] = mu[k0 + tid];
-            sv[tid] = v[k0 + tid];
+            if (MODE == 1) sv[tid] = v[k0 + tid];
         }
         __syncthreads();
         for (int k = 0; k < kc; ++k) {
@@ -50,9 +51,12 @@ __global__ void __launch_bounds__(kRows) lens_rows_kernel(const float* __restric
                 // x * x is exact in double (24-bit significands), so one
                 // fused rounding equals the separate multiply and add
                 acc = __fma_rn(x, x, acc);
-            } else {
+            } else if (MODE == 1) {
                 const double t = __dsub_rn(x, smu[k]);
                 acc = __dadd_rn(acc, __dmul_rn(t, sv[k]));
+            } else {
+                const double t = __dsub_rn(x, smu[k]);
+                acc = __fma_rn(t, t, acc);
             }
         }
         __syncthreads();
@@ -221,6 +225,43 @@ __global__ void __launch_bounds__(256) lens_l2_exact_kernel(const float* __restr
         }
         if (lane < rows) f[(r0 + lane) * m + j] = l2_finish(my_hi, my_lo, my_emax, my_special);
     }
+}
+
+// Mean of f[r * m + j] over the rows: per-block sums (rows strided over the
+// threads, then a shuffle and shared-memory tree), then one block adds the
+// block sums in a fixed order (the same result run to run).
+constexpr int kMeanBlocks = 512;
+
+__global__ void __launch_bounds__(256) col_lens_partial_kernel(const double* __restrict__ f, int64_t n, int m,
+                                                               int j, double* __restrict__ part)
+{
+    __shared__ double ws[8];
+    double s = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        s += f[r * m + j];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += ws[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// f = sqrt(q + V), V = (sum of the block sums) / n
+__global__ void __launch_bounds__(256) ecc_finish_kernel(double* __restrict__ f, int64_t n, int m, int j,
+                                                         const double* __restrict__ part, int nb)
+{
+    __shared__ double V;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < nb; ++b) t += part[b];
+        V = t / (double)n;
+    }
+    __syncthreads();
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        f[r * m + j] = __dsqrt_rn(__dadd_rn(f[r * m + j], V));
 }
 
 __global__ void lens_coord_kernel(const float* __restrict__ X, int64_t n, int64_t ld, int32_t col,
@@ -443,6 +484,29 @@ cudaError_t lens_project(const float* X, int64_t n, int32_t d, int64_t ld, const
 {
     if (n == 0) return cudaSuccess;
     { lens_rows_kernel<1><<<div_up(n, kRows), kRows, 0, s>>>(X, n, d, ld, mu, v, f, m, j); note_launch(); }
+    return cudaGetLastError();
+}
+
+// Eccentricity with exponent 2 (§3 and §4.1 name eccentricity among the
+// common filters): the mean squared distance from x to the cloud equals
+// |x - mu|^2 + mean_y |y - mu|^2 (mu the column means), so f(x) =
+// sqrt(|x - mu|^2 + V) in FP64 without any pair of points: column means by
+// fixed-order block sums, |x - mu|^2 summed k ascending, V their mean.
+cudaError_t lens_ecc2(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const int nblk = div_up(n, kMeanRows);
+    Buf part, mu, vpart;
+    MGB_TRY(part.alloc(sizeof(double) * (size_t)nblk * d, s));
+    MGB_TRY(mu.alloc(sizeof(double) * d, s));
+    MGB_TRY(vpart.alloc(sizeof(double) * kMeanBlocks, s));
+    { col_partial_sum_kernel<<<nblk, 256, 0, s>>>(X, n, d, ld, part.as<double>()); note_launch(); }
+    { col_mean_kernel<<<div_up(d, 256), 256, 0, s>>>(part.as<double>(), nblk, d, n, mu.as<double>()); note_launch(); }
+    { lens_rows_kernel<2><<<div_up(n, kRows), kRows, 0, s>>>(X, n, d, ld, mu.as<double>(), nullptr, f, m, j);
+      note_launch(); }
+    { col_lens_partial_kernel<<<kMeanBlocks, 256, 0, s>>>(f, n, m, j, vpart.as<double>()); note_launch(); }
+    { ecc_finish_kernel<<<std::min(div_up(n, 256), 152 * 8), 256, 0, s>>>(f, n, m, j, vpart.as<double>(), kMeanBlocks);
+      note_launch(); }
     return cudaGetLastError();
 }
 

@@ -163,6 +163,30 @@ def test_l2_lens_exponent_range(ctx, d):
             mg.mapper_lens(ctx, torch.from_numpy(Y).to("cuda:0"), (0,), (0,))
 
 
+@pytest.mark.parametrize("prec", [mg.BF16, mg.FP32])
+@pytest.mark.parametrize("n,d,seed", [(1, 3, 0), (2, 5, 1), (300, 7, 2), (3000, 64, 3)])
+def test_eccentricity_lens(ctx, n, d, seed, prec):
+    """Eccentricity filter (exponent 2) within 1e-12 relative of the oracle's
+    direct O(n^2 d) form; the graph on it equals the oracle's."""
+    X = synth.gaussian_mixture(n, d, 3, seed=60 + seed, centre_box=4.0, std_lo=0.5, std_hi=1.0,
+                               anisotropic=False) if n > 2 else synth.tiny_random(n, d, seed, scale=3.0)
+    eps = _eps(X, 8, seed)
+    res = run_gpu(ctx, X, (mg.LENS_ECC,), (0,), (7,), (0.3,), eps, 4, prec)
+    ref = oracle.lens_ecc2(X)
+    assert np.all(np.abs(res["lens"][:, 0] - ref) <= 1e-12 * np.abs(ref))
+    assert_same_graph(X, res, (7,), (0.3,), eps, 4)
+
+
+def test_eccentricity_with_l2_2d_cover(ctx):
+    X = synth.gaussian_mixture(2500, 16, 4, seed=64, centre_box=5.0, std_lo=0.5, std_hi=1.0,
+                               anisotropic=True)
+    eps = _eps(X, 6, 64)
+    res = run_gpu(ctx, X, (mg.LENS_ECC, mg.LENS_L2), (0, 0), (5, 6), (0.25, 0.2), eps, 5, mg.BF16)
+    np.testing.assert_allclose(res["lens"][:, 0], oracle.lens_ecc2(X), rtol=1e-12, atol=0)
+    assert_l2_lens(X, res["lens"][:, 1])
+    assert_same_graph(X, res, (5, 6), (0.25, 0.2), eps, 5)
+
+
 def test_pca_lens_basis_and_bits(ctx):
     X = synth.gaussian_mixture(6000, 12, 5, seed=4, centre_box=5.0, std_lo=0.3, std_hi=1.5,
                                anisotropic=True)
