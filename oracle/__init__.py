@@ -66,7 +66,8 @@ def _load():
         lib.oracle_pca.restype = ctypes.c_int
         lib.oracle_range.argtypes = [P, i64, i32, i32, P, P]
         lib.oracle_interval_bounds.argtypes = [f64, f64, i32, f64, P, P]
-        lib.oracle_cover.argtypes = [P, i64, i32, P, P, P, P]
+        lib.oracle_cover.argtypes = [P, i64, i32, P, P, i32, P, P]
+        lib.oracle_balanced_bounds.argtypes = [P, i64, i32, i32, i32, f64, P, P]
         lib.oracle_cover.restype = i64
         lib.oracle_dbscan.argtypes = [P, i64, i32, i64, P, i64, f64, i32, P, P, P, P]
         lib.oracle_dbscan.restype = ctypes.c_int
@@ -172,8 +173,18 @@ def interval_bounds(lo: float, hi: float, n_int: int, p: float):
     return a, b
 
 
-def cover(lens_arr, n_intervals, overlap):
-    """(elem_offsets[E+1] int64, elem_points[sum n_i] int32)."""
+def balanced_bounds(lens_col, n_int: int, p: float):
+    """Interval bounds of the balanced cover of one filter column."""
+    L = np.ascontiguousarray(lens_col, dtype=np.float64).reshape(-1)
+    a = np.empty(n_int, dtype=np.float64)
+    b = np.empty(n_int, dtype=np.float64)
+    _load().oracle_balanced_bounds(_ptr(L), L.size, 1, 0, int(n_int), float(p), _ptr(a), _ptr(b))
+    return a, b
+
+
+def cover(lens_arr, n_intervals, overlap, balanced: bool = False):
+    """(elem_offsets[E+1] int64, elem_points[sum n_i] int32); `balanced`:
+    the balanced cover (uniform cover of the filter's ranks)."""
     L = np.ascontiguousarray(lens_arr, dtype=np.float64)
     if L.ndim == 1:
         L = L[:, None]
@@ -183,11 +194,11 @@ def cover(lens_arr, n_intervals, overlap):
     E = int(np.prod(ni))
     offs = np.empty(E + 1, dtype=np.int64)
     lib = _load()
-    total = lib.oracle_cover(_ptr(L), n, m, _ptr(ni), _ptr(ov), _ptr(offs), None)
+    total = lib.oracle_cover(_ptr(L), n, m, _ptr(ni), _ptr(ov), int(bool(balanced)), _ptr(offs), None)
     if total < 0:
         raise ValueError("bad cover arguments")
     pts = np.empty(max(total, 1), dtype=np.int32)
-    lib.oracle_cover(_ptr(L), n, m, _ptr(ni), _ptr(ov), _ptr(offs), _ptr(pts))
+    lib.oracle_cover(_ptr(L), n, m, _ptr(ni), _ptr(ov), int(bool(balanced)), _ptr(offs), _ptr(pts))
     return offs, pts[:total]
 
 
@@ -260,7 +271,7 @@ def nerve(node_offsets, node_members, n_points: int):
 
 
 def mapper_graph(X, lens_arr, n_intervals, overlap, eps: float, min_pts: int,
-                 elements=None):
+                 elements=None, balanced: bool = False):
     """Full mapper graph from a given lens (n x m). With `elements` (a list
     of element indices) only those elements are clustered and the nerve is
     left empty (sampled parity at large sizes).
@@ -269,7 +280,7 @@ def mapper_graph(X, lens_arr, n_intervals, overlap, eps: float, min_pts: int,
     core (per membership), counts, node_offsets, node_members, node_elem,
     edges, near_ties."""
     X = _f32(X)
-    offs, pts = cover(lens_arr, n_intervals, overlap)
+    offs, pts = cover(lens_arr, n_intervals, overlap, balanced)
     E = len(offs) - 1
     labels = np.full(len(pts), -1, dtype=np.int64)
     core = np.zeros(len(pts), dtype=bool)

@@ -253,13 +253,52 @@ void oracle_interval_bounds(double lo, double hi, int32_t n_int, double p, doubl
         if (b[k] < a[k + 1]) b[k] = a[k + 1];
 }
 
+static int cmp_double(const void* x, const void* y)
+{
+    const double a = *(const double*)x, b = *(const double*)y;
+    return (a > b) - (a < b);
+}
+
+/* Balanced cover of one filter dimension (§3: some libraries offer a
+ * "balanced" cover whose intervals hold equal numbers of points). Reading:
+ * the uniform cover of the filter's ranks. With v_0 <= ... <= v_{n-1} the
+ * sorted values, the uniform intervals [r_a, r_b] of n_int elements with
+ * overlap p over the rank range [0, n-1] give the value intervals
+ * [v_ceil(r_a), v_floor(r_b)]; an interval holding no integer rank is empty
+ * (+inf, -inf). Membership stays closed. */
+void oracle_balanced_bounds(const double* lens, int64_t n, int32_t m, int32_t j, int32_t n_int, double p,
+                            double* a, double* b)
+{
+    double* v = (double*)malloc(sizeof(double) * (size_t)n);
+    for (int64_t q = 0; q < n; ++q) v[q] = lens[q * m + j];
+    qsort(v, (size_t)n, sizeof(double), cmp_double);
+    double* ra = (double*)malloc(sizeof(double) * (size_t)n_int);
+    double* rb = (double*)malloc(sizeof(double) * (size_t)n_int);
+    oracle_interval_bounds(0.0, (double)(n - 1), n_int, p, ra, rb);
+    for (int32_t k = 0; k < n_int; ++k) {
+        double lo_r = ceil(ra[k]), hi_r = floor(rb[k]);
+        if (lo_r < 0.0) lo_r = 0.0;
+        if (hi_r > (double)(n - 1)) hi_r = (double)(n - 1);
+        if (lo_r > hi_r) {
+            a[k] = INFINITY;
+            b[k] = -INFINITY;
+        } else {
+            a[k] = v[(int64_t)lo_r];
+            b[k] = v[(int64_t)hi_r];
+        }
+    }
+    free(ra);
+    free(rb);
+    free(v);
+}
+
 /* Pull-back cover (§3: points in f^{-1}(V_k)). lens is n x m row-major.
  * Writes elem_offsets[E+1] and, when elem_points != NULL, the member
  * indices of each element in ascending order. Returns the total number of
  * memberships, or -1 on bad arguments. Brute force: every point is tested
  * against every element. */
 int64_t oracle_cover(const double* lens, int64_t n, int32_t m, const int32_t* n_int,
-                     const double* overlap, int64_t* elem_offsets, int32_t* elem_points)
+                     const double* overlap, int32_t balanced, int64_t* elem_offsets, int32_t* elem_points)
 {
     if (m < 1 || m > 2) return -1;
     double* a[2] = {0, 0};
@@ -269,7 +308,10 @@ int64_t oracle_cover(const double* lens, int64_t n, int32_t m, const int32_t* n_
         oracle_range(lens, n, m, j, &lo, &hi);
         a[j] = (double*)malloc(sizeof(double) * (size_t)n_int[j]);
         b[j] = (double*)malloc(sizeof(double) * (size_t)n_int[j]);
-        oracle_interval_bounds(lo, hi, n_int[j], overlap[j], a[j], b[j]);
+        if (balanced)
+            oracle_balanced_bounds(lens, n, m, j, n_int[j], overlap[j], a[j], b[j]);
+        else
+            oracle_interval_bounds(lo, hi, n_int[j], overlap[j], a[j], b[j]);
     }
     int32_t n2 = (m == 2) ? n_int[1] : 1;
     int64_t E = (int64_t)n_int[0] * n2;

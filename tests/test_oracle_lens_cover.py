@@ -151,3 +151,37 @@ def test_cover_2d_is_product_in_row_major_order():
             e = i * 3 + j
             ref = np.intersect1d(p1[o1[i]:o1[i + 1]], p2[o2[j]:o2[j + 1]])
             assert np.array_equal(pts[offs[e]:offs[e + 1]], ref)
+
+
+def test_balanced_cover_hand_worked():
+    """Ten distinct values 0..9, three intervals, overlap 0.2: rank range
+    [0, 9], L = 9 / 2.6, s = 0.8 L, rank intervals [0, 3.46], [2.77, 6.23],
+    [5.54, 9] -> ranks {0..3}, {3..6}, {6..9}."""
+    f = np.array([5.0, 0.0, 9.0, 3.0, 7.0, 1.0, 8.0, 2.0, 6.0, 4.0])   # a permutation of 0..9
+    offs, pts = oracle.cover(f, (3,), (0.2,), balanced=True)
+    got = [sorted(f[pts[offs[e]:offs[e + 1]]].tolist()) for e in range(3)]
+    assert got == [[0, 1, 2, 3], [3, 4, 5, 6], [6, 7, 8, 9]]
+    a, b = oracle.balanced_bounds(f, 3, 0.2)
+    assert a.tolist() == [0.0, 3.0, 6.0] and b.tolist() == [3.0, 6.0, 9.0]
+
+
+def test_balanced_cover_invariants():
+    rng = np.random.default_rng(11)
+    f = rng.standard_normal(1000) * 3.0
+    for n_int, p in [(1, 0.0), (7, 0.0), (10, 0.3), (25, 0.5)]:
+        offs, pts = oracle.cover(f, (n_int,), (p,), balanced=True)
+        # every point covered; equal counts up to one (distinct values)
+        assert set(pts.tolist()) == set(range(f.size))
+        sizes = np.diff(offs)
+        L = (f.size - 1) / (n_int - (n_int - 1) * p)
+        assert sizes.min() >= np.floor(L) and sizes.max() <= np.ceil(L) + 1
+        # invariant under a strictly increasing transform of the filter
+        offs2, pts2 = oracle.cover(np.exp(f / 4.0), (n_int,), (p,), balanced=True)
+        assert np.array_equal(offs, offs2) and np.array_equal(pts, pts2)
+    # all values equal: each element's value interval is [2, 2], so (closed
+    # membership) every element holds every point
+    offs, pts = oracle.cover(np.full(5, 2.0), (3,), (0.2,), balanced=True)
+    assert np.diff(offs).tolist() == [5, 5, 5]
+    # a single point lies in the first element only
+    offs, _ = oracle.cover(np.array([1.5]), (4,), (0.25,), balanced=True)
+    assert np.diff(offs).tolist() == [1, 0, 0, 0]
