@@ -59,7 +59,7 @@
 extern "C" {
 #endif
 
-#define MAPPER_ABI_VERSION 2
+#define MAPPER_ABI_VERSION 3
 
 typedef enum mapper_status {
     MAPPER_OK = 0,
@@ -99,6 +99,18 @@ typedef struct mapper_graph_t mapper_graph_t;
 
 /* Parameters of one mapper graph (§3, "Algorithmic details in practice":
  * filter f, number of cover elements n, overlap p, metric, clusterer). */
+/* Cover of the filter range (§3: "Each interval (cover element) typically has
+ * uniform size"; some libraries offer a "balanced" cover whose intervals hold
+ * equal numbers of points). */
+typedef enum mapper_cover_kind {
+    MAPPER_COVER_UNIFORM = 0,   /* n intervals of equal length over [min f, max f] */
+    MAPPER_COVER_BALANCED = 1   /* the uniform cover of the ranks of f: with v_0 <= ..
+                                   <= v_{n-1} the sorted values and [r_a, r_b] the uniform
+                                   intervals over [0, n-1], the element is
+                                   [v_ceil(r_a), v_min(floor(r_b), n-1)] (empty when
+                                   ceil(r_a) > n-1), membership closed */
+} mapper_cover_kind;
+
 typedef struct mapper_params {
     int32_t m;               /* filter dimension: 1 (intervals) or 2 (rectangles) */
     int32_t lens_kind[2];    /* mapper_lens_kind per filter dimension */
@@ -108,6 +120,7 @@ typedef struct mapper_params {
     double eps;              /* DBSCAN radius, finite, > 0 */
     int32_t min_pts;         /* DBSCAN minPts >= 1 */
     int32_t precision;       /* mapper_precision */
+    int32_t cover_kind;      /* mapper_cover_kind */
 } mapper_params;
 
 /* Counters of one computation (filled by mapper_stats_get). */
@@ -183,6 +196,9 @@ int mapper_lens(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, int64
  * arrays of m. Result read with mapper_cover_sizes / mapper_cover_copy. */
 int mapper_cover(mapper_ctx* ctx, const double* lens_dev, int64_t n, int32_t m,
                  const int32_t* n_intervals, const double* overlap, mapper_cover_t** out);
+/* The same with the balanced cover (mapper_cover_kind). */
+int mapper_cover_balanced(mapper_ctx* ctx, const double* lens_dev, int64_t n, int32_t m,
+                          const int32_t* n_intervals, const double* overlap, mapper_cover_t** out);
 int mapper_cover_sizes(const mapper_cover_t* cover, int64_t* n_elements, int64_t* n_members);
 /* elem_offsets: n_elements+1 int64; elem_points: n_members int32. */
 int mapper_cover_copy(const mapper_cover_t* cover, int64_t* elem_offsets, int32_t* elem_points,

@@ -264,8 +264,10 @@ static int cmp_double(const void* x, const void* y)
  * the uniform cover of the filter's ranks. With v_0 <= ... <= v_{n-1} the
  * sorted values, the uniform intervals [r_a, r_b] of n_int elements with
  * overlap p over the rank range [0, n-1] give the value intervals
- * [v_ceil(r_a), v_floor(r_b)]; an interval holding no integer rank is empty
- * (+inf, -inf). Membership stays closed. */
+ * [v_ceil(r_a), v_min(floor(r_b), n-1)]; one starting past the last rank is
+ * empty (a = +inf). Membership stays closed, so an interval with
+ * ceil(r_a) > floor(r_b) holds only points of a value tied at both ends.
+ * The bounds are nondecreasing in k. */
 void oracle_balanced_bounds(const double* lens, int64_t n, int32_t m, int32_t j, int32_t n_int, double p,
                             double* a, double* b)
 {
@@ -277,15 +279,9 @@ void oracle_balanced_bounds(const double* lens, int64_t n, int32_t m, int32_t j,
     oracle_interval_bounds(0.0, (double)(n - 1), n_int, p, ra, rb);
     for (int32_t k = 0; k < n_int; ++k) {
         double lo_r = ceil(ra[k]), hi_r = floor(rb[k]);
-        if (lo_r < 0.0) lo_r = 0.0;
         if (hi_r > (double)(n - 1)) hi_r = (double)(n - 1);
-        if (lo_r > hi_r) {
-            a[k] = INFINITY;
-            b[k] = -INFINITY;
-        } else {
-            a[k] = v[(int64_t)lo_r];
-            b[k] = v[(int64_t)hi_r];
-        }
+        b[k] = v[(int64_t)hi_r];
+        a[k] = lo_r > (double)(n - 1) ? INFINITY : v[(int64_t)lo_r];
     }
     free(ra);
     free(rb);

@@ -14,12 +14,13 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _capi
-from ._capi import BF16, BF16X1, FP32, LENS_COORD, LENS_ECC, LENS_L2, LENS_PCA, MapperError, MapperParams
+from ._capi import (BF16, BF16X1, COVER_BALANCED, COVER_UNIFORM, FP32, LENS_COORD, LENS_ECC, LENS_L2, LENS_PCA,
+                    MapperError, MapperParams)
 
 __all__ = [
     "Context", "Cover", "Clusters", "Graph", "MapperError", "mapper_lens", "mapper_cover",
     "mapper_cluster", "mapper_nerve", "mapper_graph", "params", "LENS_L2", "LENS_COORD",
-    "LENS_PCA", "LENS_ECC", "FP32", "BF16", "BF16X1", "mapper_dbscan_noalloc", "Server", "graph_footprint",
+    "LENS_PCA", "LENS_ECC", "COVER_UNIFORM", "COVER_BALANCED", "FP32", "BF16", "BF16X1", "mapper_dbscan_noalloc", "Server", "graph_footprint",
     "mapper_graph_sweep", "mapper_cover_subset", "mapper_nerve_from_nodes",
 ]
 
@@ -160,7 +161,8 @@ class Graph(_Handle):
         return Clusters(self._lib, ctypes.c_void_p(self._lib.mapper_graph_clusters(self.h)), owner=self)
 
 
-def params(lens_kind, lens_arg, n_intervals, overlap, eps, min_pts, precision=FP32) -> MapperParams:
+def params(lens_kind, lens_arg, n_intervals, overlap, eps, min_pts, precision=FP32,
+           cover_kind=COVER_UNIFORM) -> MapperParams:
     lens_kind, lens_arg = tuple(lens_kind), tuple(lens_arg)
     n_intervals, overlap = tuple(n_intervals), tuple(overlap)
     p = MapperParams()
@@ -173,6 +175,7 @@ def params(lens_kind, lens_arg, n_intervals, overlap, eps, min_pts, precision=FP
     p.eps = float(eps)
     p.min_pts = int(min_pts)
     p.precision = int(precision)
+    p.cover_kind = int(cover_kind)
     return p
 
 
@@ -203,13 +206,13 @@ def mapper_lens(ctx: Context, X, kinds, args):
     return out, (pca[:npca] if npca > d else None)
 
 
-def mapper_cover(ctx: Context, lens, n_intervals, overlap) -> Cover:
+def mapper_cover(ctx: Context, lens, n_intervals, overlap, balanced: bool = False) -> Cover:
     n, m = lens.shape
     ni = (ctypes.c_int32 * m)(*n_intervals)
     ov = (ctypes.c_double * m)(*overlap)
     h = ctypes.c_void_p()
-    _capi.check(ctx._lib.mapper_cover(ctx.h, _vp(lens.data_ptr()), n, m, ni, ov, ctypes.byref(h)),
-                "mapper_cover")
+    fn = ctx._lib.mapper_cover_balanced if balanced else ctx._lib.mapper_cover
+    _capi.check(fn(ctx.h, _vp(lens.data_ptr()), n, m, ni, ov, ctypes.byref(h)), "mapper_cover")
     return Cover(ctx._lib, h)
 
 

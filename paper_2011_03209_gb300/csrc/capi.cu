@@ -203,7 +203,7 @@ int run_lens(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld, 
 
 // ------------------------------------------------------------------ cover
 int run_cover(mapper_ctx* ctx, const double* lens, int64_t n, int32_t m, const int32_t* n_int,
-              const double* overlap, std::shared_ptr<CoverData>* out, int* nonfinite_dev)
+              const double* overlap, std::shared_ptr<CoverData>* out, int* nonfinite_dev, bool balanced = false)
 {
     if (m < 1 || m > 2) return fail(MAPPER_EINVAL, "m must be 1 or 2");
     for (int j = 0; j < m; ++j) {
@@ -232,7 +232,8 @@ int run_cover(mapper_ctx* ctx, const double* lens, int64_t n, int32_t m, const i
         nf = flag.as<int>();
     }
     CK(lens_range_flag(lens, n, m, lohi.as<double>(), nf, s), "lens_range");
-    CK(interval_bounds(lohi.as<double>(), m, n_int, overlap, bounds.as<double>(), s), "bounds");
+    if (balanced) CK(balanced_bounds(lens, n, m, n_int, overlap, bounds.as<double>(), s), "balanced bounds");
+    else CK(interval_bounds(lohi.as<double>(), m, n_int, overlap, bounds.as<double>(), s), "bounds");
     CK(cover_count(lens, n, m, bounds.as<double>(), n_int[0], m == 2 ? n_int[1] : 1,
                    cnt.as<int32_t>(), s), "cover_count");
     CK(exclusive_scan_i32_to_i64(cnt.as<int32_t>(), pos.as<int64_t>(), n, s), "scan");
@@ -866,8 +867,8 @@ int mapper_lens(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, int64
     return MAPPER_OK;
 }
 
-int mapper_cover(mapper_ctx* ctx, const double* lens_dev, int64_t n, int32_t m,
-                 const int32_t* n_intervals, const double* overlap, mapper_cover_t** out)
+static int cover_call(mapper_ctx* ctx, const double* lens_dev, int64_t n, int32_t m,
+                      const int32_t* n_intervals, const double* overlap, int balanced, mapper_cover_t** out)
 {
     int rc = check_ctx(ctx);
     if (rc) return rc;
@@ -875,11 +876,23 @@ int mapper_cover(mapper_ctx* ctx, const double* lens_dev, int64_t n, int32_t m,
     *out = nullptr;
     if (n < 1 || n > INT32_MAX) return fail(MAPPER_EINVAL, "n must be in [1, 2^31)");
     std::shared_ptr<CoverData> c;
-    if ((rc = run_cover(ctx, lens_dev, n, m, n_intervals, overlap, &c, nullptr))) return rc;
+    if ((rc = run_cover(ctx, lens_dev, n, m, n_intervals, overlap, &c, nullptr, balanced != 0))) return rc;
     auto h = new mapper_cover_t;
     h->c = c;
     *out = h;
     return MAPPER_OK;
+}
+
+int mapper_cover(mapper_ctx* ctx, const double* lens_dev, int64_t n, int32_t m,
+                 const int32_t* n_intervals, const double* overlap, mapper_cover_t** out)
+{
+    return cover_call(ctx, lens_dev, n, m, n_intervals, overlap, 0, out);
+}
+
+int mapper_cover_balanced(mapper_ctx* ctx, const double* lens_dev, int64_t n, int32_t m,
+                          const int32_t* n_intervals, const double* overlap, mapper_cover_t** out)
+{
+    return cover_call(ctx, lens_dev, n, m, n_intervals, overlap, 1, out);
 }
 
 int mapper_cover_sizes(const mapper_cover_t* cover, int64_t* n_elements, int64_t* n_members)
@@ -1080,8 +1093,10 @@ int mapper_graph(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t 
                        &g->n_pca))) return rc;
     tm.mark();
     std::shared_ptr<CoverData> cov;
+    if (p->cover_kind != MAPPER_COVER_UNIFORM && p->cover_kind != MAPPER_COVER_BALANCED)
+        return fail(MAPPER_EINVAL, "unknown cover kind");
     if ((rc = run_cover(ctx, g->lens.as<double>(), n, p->m, p->n_intervals, p->overlap, &cov,
-                        flag.as<int>()))) return rc;
+                        flag.as<int>(), p->cover_kind == MAPPER_COVER_BALANCED))) return rc;
     tm.mark();
     std::shared_ptr<ClusterData> cl;
     if ((rc = run_cluster(ctx, Xd, n, d, ldd, cov, p->eps, p->min_pts, p->precision, &cl, flag.as<int>())))
@@ -1141,6 +1156,8 @@ int mapper_graph_sweep(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, in
     if (rc) return rc;
     if ((rc = check_x(X, n, d, ld))) return rc;
     if (!p || !out || !eps || !overlap || n_sweep < 1) return fail(MAPPER_EINVAL, "bad sweep arguments");
+    if (p->cover_kind != MAPPER_COVER_UNIFORM && p->cover_kind != MAPPER_COVER_BALANCED)
+        return fail(MAPPER_EINVAL, "unknown cover kind");
     if (p->m < 1 || p->m > 2) return fail(MAPPER_EINVAL, "m must be 1 or 2");
     for (int i = 0; i < n_sweep; ++i) out[i] = nullptr;
     cudaStream_t s = ctx->stream->s;
@@ -1174,7 +1191,9 @@ int mapper_graph_sweep(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, in
         if (done[i]) continue;
         double ov[2] = {overlap[i], overlap[i]};
         std::shared_ptr<CoverData> cov;
-        if ((rc = run_cover(ctx, lens.as<double>(), n, p->m, p->n_intervals, ov, &cov, flag.as<int>()))) return rc;
+        if ((rc = run_cover(ctx, lens.as<double>(), n, p->m, p->n_intervals, ov, &cov, flag.as<int>(),
+                            p->cover_kind == MAPPER_COVER_BALANCED)))
+            return rc;
         double eps_max = 0.0;
         for (int j = i; j < n_sweep; ++j)
             if (overlap[j] == overlap[i]) eps_max = std::max(eps_max, eps[j]);

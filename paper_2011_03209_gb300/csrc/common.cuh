@@ -82,6 +82,9 @@ cudaError_t lens_range_flag(const double* f, int64_t n, int m, double* lohi, int
                             cudaStream_t s);
 cudaError_t interval_bounds(const double* lohi, int m, const int32_t* n_int_host,
                             const double* p_host, double* bounds, cudaStream_t s);
+// interval bounds of the balanced cover (same layout as interval_bounds)
+cudaError_t balanced_bounds(const double* f, int64_t n, int m, const int32_t* n_int_host, const double* p_host,
+                            double* bounds, cudaStream_t s);
 // number of memberships per point (cnt[n]) and the emitted element keys
 cudaError_t cover_count(const double* f, int64_t n, int m, const double* bounds,
                         int32_t n0, int32_t n1, int32_t* cnt, cudaStream_t s);

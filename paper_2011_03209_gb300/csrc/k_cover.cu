@@ -78,6 +78,39 @@ __global__ void range_final_kernel(const double* __restrict__ part, int nb, int 
     }
 }
 
+// Balanced cover (§3: intervals holding equal numbers of points), read as
+// the uniform cover of the filter's ranks: filter values sorted through an
+// order-preserving map of doubles to 64-bit keys; element k of dimension j
+// is [v_ceil(ra_k), v_min(floor(rb_k), n-1)] for the uniform rank intervals
+// [ra_k, rb_k] over [0, n-1], and empty (a = +inf) when it starts past the
+// last rank, so both bound arrays stay nondecreasing (the membership search
+// relies on it).
+__global__ void order_keys_kernel(const double* __restrict__ f, int64_t n, int m, int j, uint64_t* __restrict__ keys)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t b = (uint64_t)__double_as_longlong(f[i * m + j]);
+    keys[i] = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__global__ void pick_bounds_kernel(const uint64_t* __restrict__ keys, int64_t n, int32_t nk,
+                                   const double* __restrict__ rank_a, const double* __restrict__ rank_b,
+                                   double* __restrict__ a, double* __restrict__ b)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nk) return;
+    const double lo = ceil(rank_a[k]);
+    double hi = floor(rank_b[k]);
+    if (hi > (double)(n - 1)) hi = (double)(n - 1);
+    auto value = [&](int64_t r) {
+        const uint64_t key = keys[r];
+        const uint64_t bits = (key >> 63) ? (key & 0x7fffffffffffffffull) : ~key;
+        return __longlong_as_double((long long)bits);
+    };
+    b[k] = value((int64_t)hi);
+    a[k] = lo > (double)(n - 1) ? INFINITY : value((int64_t)lo);
+}
+
 // bounds layout: dim 0: a[n0], b[n0]; dim 1: a[n1], b[n1]
 __global__ void bounds_kernel(const double* __restrict__ lohi, int m, int32_t n0, int32_t n1,
                               double p0, double p1, double* __restrict__ bounds)
@@ -200,6 +233,37 @@ cudaError_t interval_bounds(const double* lohi, int m, const int32_t* n_int_host
     { bounds_kernel<<<1, 256, 0, s>>>(lohi, m, n_int_host[0], m == 2 ? n_int_host[1] : 1,
                                     p_host[0], m == 2 ? p_host[1] : 0.0, bounds); note_launch(); }
     return cudaGetLastError();
+}
+
+cudaError_t balanced_bounds(const double* f, int64_t n, int m, const int32_t* n_int_host, const double* p_host,
+                            double* bounds, cudaStream_t s)
+{
+    const int32_t n0 = n_int_host[0], n1 = m == 2 ? n_int_host[1] : 1;
+    Buf rank_lohi, rank_bounds, keys, tmp;
+    MGB_TRY(rank_lohi.alloc(sizeof(double) * 4, s));
+    MGB_TRY(rank_bounds.alloc(sizeof(double) * 2 * ((size_t)n0 + (m == 2 ? n1 : 0)), s));
+    MGB_TRY(keys.alloc(sizeof(uint64_t) * n, s));
+    MGB_TRY(tmp.alloc(sizeof(uint64_t) * n, s));
+    static thread_local double h_lohi[4];
+    h_lohi[0] = 0.0;
+    h_lohi[1] = (double)(n - 1);
+    h_lohi[2] = 0.0;
+    h_lohi[3] = (double)(n - 1);
+    MGB_TRY(cudaMemcpyAsync(rank_lohi.p, h_lohi, sizeof(double) * 4, cudaMemcpyHostToDevice, s));
+    MGB_TRY(interval_bounds(rank_lohi.as<double>(), m, n_int_host, p_host, rank_bounds.as<double>(), s));
+    for (int j = 0; j < m; ++j) {
+        const int32_t nk = j == 0 ? n0 : n1;
+        const int64_t off = j == 0 ? 0 : 2 * (int64_t)n0;
+        { order_keys_kernel<<<div_up(n, 256), 256, 0, s>>>(f, n, m, j, keys.as<uint64_t>()); note_launch(); }
+        MGB_TRY(cudaGetLastError());
+        MGB_TRY(radix_sort_u64(keys.as<uint64_t>(), tmp.as<uint64_t>(), n, 0, 64, s));
+        const double* ra = rank_bounds.as<double>() + off;
+        { pick_bounds_kernel<<<div_up(nk, 256), 256, 0, s>>>(keys.as<uint64_t>(), n, nk, ra, ra + nk,
+                                                            bounds + off, bounds + off + nk); note_launch(); }
+        MGB_TRY(cudaGetLastError());
+    }
+    MGB_TRY(cudaStreamSynchronize(s));              // h_lohi read before it is rewritten
+    return cudaSuccess;
 }
 
 cudaError_t cover_count(const double* f, int64_t n, int m, const double* bounds, int32_t n0,

@@ -38,16 +38,17 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version_and_strings(lib):
-    assert lib.mapper_abi_version() == 2
+    assert lib.mapper_abi_version() == 3
     assert lib.mapper_strerror(0) == b"ok"
     assert lib.mapper_strerror(-4) == b"device wait timed out"
 
 
 def test_struct_layouts_match_header():
     from paper_2011_03209_gb300 import _capi
-    # mapper_params: 7 int32, pad to 8, 2 doubles, double, 2 int32
-    assert ctypes.sizeof(_capi.MapperParams) == 64
+    # mapper_params: 7 int32, pad to 8, 2 doubles, double, 3 int32, pad to 8
+    assert ctypes.sizeof(_capi.MapperParams) == 72
     assert _capi.MapperParams.overlap.offset == 32
+    assert _capi.MapperParams.cover_kind.offset == 64
     assert ctypes.sizeof(_capi.MapperStats) == 8 * 33
 
 

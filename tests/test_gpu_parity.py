@@ -31,9 +31,9 @@ def ctx():
     c.close()
 
 
-def run_gpu(ctx, X, kinds, args, nint, ov, eps, min_pts, prec=mg.FP32):
+def run_gpu(ctx, X, kinds, args, nint, ov, eps, min_pts, prec=mg.FP32, cover_kind=mg.COVER_UNIFORM):
     Xd = torch.from_numpy(np.ascontiguousarray(X)).to("cuda:0")
-    g = mg.mapper_graph(ctx, Xd, mg.params(kinds, args, nint, ov, eps, min_pts, prec))
+    g = mg.mapper_graph(ctx, Xd, mg.params(kinds, args, nint, ov, eps, min_pts, prec, cover_kind))
     out = g.numpy()
     out["lens"], out["pca"] = g.lens(X.shape[0], len(kinds))
     out["elem_offsets"], out["elem_points"] = g.cover().numpy()
@@ -52,8 +52,8 @@ def assert_l2_lens(X, f):
     assert np.all(np.abs(f - ref) <= 1e-12 * np.abs(ref))
 
 
-def assert_same_graph(X, res, nint, ov, eps, min_pts):
-    ref = oracle.mapper_graph(X, res["lens"], nint, ov, eps, min_pts)
+def assert_same_graph(X, res, nint, ov, eps, min_pts, balanced=False):
+    ref = oracle.mapper_graph(X, res["lens"], nint, ov, eps, min_pts, balanced=balanced)
     for k in ("elem_offsets", "elem_points", "core", "labels", "node_offsets", "node_members",
               "node_elem", "edges"):
         assert np.array_equal(np.asarray(res[k]), np.asarray(ref[k])), k
@@ -185,6 +185,34 @@ def test_eccentricity_with_l2_2d_cover(ctx):
     np.testing.assert_allclose(res["lens"][:, 0], oracle.lens_ecc2(X), rtol=1e-12, atol=0)
     assert_l2_lens(X, res["lens"][:, 1])
     assert_same_graph(X, res, (5, 6), (0.25, 0.2), eps, 5)
+
+
+@pytest.mark.parametrize("prec", [mg.BF16, mg.FP32])
+@pytest.mark.parametrize("n,d,seed,n_int,ov", [(1, 3, 0, 4, 0.25), (2, 4, 1, 3, 0.2), (5, 2, 2, 7, 0.5),
+                                               (3000, 12, 3, 9, 0.3), (2000, 8, 4, 1, 0.0)])
+def test_balanced_cover(ctx, n, d, seed, n_int, ov, prec):
+    """Balanced cover (uniform cover of the filter's ranks): memberships equal
+    the oracle's bit for bit, and so does the graph."""
+    X = (synth.gaussian_mixture(n, d, 4, seed=70 + seed, centre_box=5.0, std_lo=0.5, std_hi=1.0,
+                                anisotropic=False) if n > 5 else synth.tiny_random(n, d, seed, scale=2.0))
+    eps = _eps(X, 6, seed)
+    res = run_gpu(ctx, X, (0,), (0,), (n_int,), (ov,), eps, 4, prec, mg.COVER_BALANCED)
+    offs, pts = oracle.cover(res["lens"], (n_int,), (ov,), balanced=True)
+    assert np.array_equal(res["elem_offsets"], offs) and np.array_equal(res["elem_points"], pts)
+    assert_same_graph(X, res, (n_int,), (ov,), eps, 4, balanced=True)
+
+
+def test_balanced_cover_2d_with_ties(ctx):
+    """2D balanced cover on a coordinate filter with many equal values (ties
+    sit on both sides of a boundary) and the L2 filter."""
+    X = synth.gaussian_mixture(2500, 6, 5, seed=77, centre_box=5.0, std_lo=0.5, std_hi=1.0, anisotropic=True)
+    X[:, 1] = np.round(X[:, 1])                      # a handful of distinct values
+    eps = _eps(X, 5, 77)
+    res = run_gpu(ctx, X, (mg.LENS_COORD, mg.LENS_L2), (1, 0), (6, 5), (0.3, 0.2), eps, 5, mg.BF16,
+                  mg.COVER_BALANCED)
+    offs, pts = oracle.cover(res["lens"], (6, 5), (0.3, 0.2), balanced=True)
+    assert np.array_equal(res["elem_offsets"], offs) and np.array_equal(res["elem_points"], pts)
+    assert_same_graph(X, res, (6, 5), (0.3, 0.2), eps, 5, balanced=True)
 
 
 def test_pca_lens_basis_and_bits(ctx):

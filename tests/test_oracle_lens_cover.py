@@ -185,3 +185,21 @@ def test_balanced_cover_invariants():
     # a single point lies in the first element only
     offs, _ = oracle.cover(np.array([1.5]), (4,), (0.25,), balanced=True)
     assert np.diff(offs).tolist() == [1, 0, 0, 0]
+
+
+def test_balanced_bounds_nondecreasing_and_covering():
+    """Bounds nondecreasing in k (the membership search relies on it) and every
+    point covered, down to one and two points."""
+    rng = np.random.default_rng(12)
+    for n in (1, 2, 3, 7, 40):
+        f = rng.standard_normal(n)
+        for n_int in (1, 2, 3, 6):
+            for p in (0.0, 0.3, 0.6):
+                a, b = oracle.balanced_bounds(f, n_int, p)
+                assert np.all(a[1:] >= a[:-1]) and np.all(b[1:] >= b[:-1])
+                offs, pts = oracle.cover(f, (n_int,), (p,), balanced=True)
+                assert set(pts.tolist()) == set(range(n))
+    # two points, four intervals of overlap 0.25: rank intervals [0, .31], [.23, .54],
+    # [.46, .77], [.69, 1] hold ranks {0}, {}, {}, {1}
+    offs, _ = oracle.cover(np.array([3.0, -1.0]), (4,), (0.25,), balanced=True)
+    assert np.diff(offs).tolist() == [1, 0, 0, 1]
