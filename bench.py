@@ -196,7 +196,8 @@ def run_ours(args):
     ctx = mg.Context(local, stream=stream)
     ctx.set_timing(True)
     lens_kind = (mg.LENS_ECC,) if args.lens == "ecc" else w.lens_kind
-    prm = mg.params(lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, prec)
+    cover_kind = mg.COVER_BALANCED if args.cover == "balanced" else mg.COVER_UNIFORM
+    prm = mg.params(lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, prec, cover_kind)
 
     for _ in range(args.warmup):
         g = mg.mapper_graph(ctx, Xd, prm)
@@ -278,8 +279,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if prec == mg.FP32 else "bf16+f64",
         "data": "synthetic",
-        "config": {"workload": w.name if args.lens == "l2" else w.name + "_ecc", "n": w.n, "d": w.d,
-                   "lens": "L2" if args.lens == "l2" else "eccentricity (exponent 2)",
+        "config": {"workload": w.name + ("" if args.lens == "l2" else "_ecc")
+                   + ("" if args.cover == "uniform" else "_balanced"), "n": w.n, "d": w.d,
+                   "lens": "L2" if args.lens == "l2" else "eccentricity (exponent 2)", "cover": args.cover,
                    "n_intervals": w.n_intervals[0], "overlap": w.overlap[0], "eps": w.eps,
                    "min_pts": w.min_pts, "precision": args.precision,
                    "l2_flush": "inputs larger than L2 (1 GB point cloud read every step)",
@@ -301,7 +303,7 @@ def run_ours(args):
         "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": int(w.X.nbytes),
                 "d2h_bytes_per_step": int(d2h)},
     }
-    if rank == 0 and not args.no_cpu_baseline and args.lens == "l2":
+    if rank == 0 and not args.no_cpu_baseline and args.lens == "l2" and args.cover == "uniform":
         gl = None
         g = mg.mapper_graph(ctx, Xd, prm)
         offs, _ = g.cover().numpy()
@@ -507,6 +509,8 @@ def main():
     ap.add_argument("--lens", default="l2", choices=["l2", "ecc"],
                     help="clusters workload filter: L2 norm (default) or eccentricity (exponent 2); "
                          "the oracle sample needs the L2 filter")
+    ap.add_argument("--cover", default="uniform", choices=["uniform", "balanced"],
+                    help="clusters workload cover: uniform intervals (default) or balanced (equal counts)")
     ap.add_argument("--n", type=int, default=1_000_000,
                     help="points of the clustered cloud (smaller only for profiling runs)")
     args = ap.parse_args()
