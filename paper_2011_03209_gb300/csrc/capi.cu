@@ -1068,19 +1068,6 @@ int mapper_graph(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t 
     tm.mark();
     const int64_t launches0 = g_launches;
 
-    Buf xdev;
-    const float* Xd = X;
-    int64_t ldd = ld;
-    if (is_host_pointer(X)) {
-        CK(xdev.alloc(sizeof(float) * (size_t)n * d, s), "alloc X");
-        if (ld == d)
-            CK(cudaMemcpyAsync(xdev.p, X, sizeof(float) * (size_t)n * d, cudaMemcpyHostToDevice, s), "copy X");
-        else
-            CK(cudaMemcpy2DAsync(xdev.p, sizeof(float) * d, X, sizeof(float) * ld, sizeof(float) * d, n,
-                                 cudaMemcpyHostToDevice, s), "copy X");
-        Xd = xdev.as<float>();
-        ldd = d;
-    }
     auto g = std::make_unique<mapper_graph_t>();
     g->stream = ctx->stream;
     g->n = n;
@@ -1089,8 +1076,23 @@ int mapper_graph(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t 
     CK(flag.alloc(sizeof(int), s), "alloc");
     CK(cudaMemsetAsync(flag.p, 0, sizeof(int), s), "memset");
     CK(g->lens.alloc(sizeof(double) * (size_t)n * p->m, s), "alloc lens");
+    Buf xdev;
+    const float* Xd = X;
+    int64_t ldd = ld;
+    if (is_host_pointer(X)) {
+        CK(xdev.alloc(sizeof(float) * (size_t)n * d, s), "alloc X");
+        if (ld == d) {
+            CK(cudaMemcpyAsync(xdev.p, X, sizeof(float) * (size_t)n * d, cudaMemcpyHostToDevice, s), "copy X");
+        } else {
+            CK(cudaMemcpy2DAsync(xdev.p, sizeof(float) * d, X, sizeof(float) * ld, sizeof(float) * d, n,
+                                 cudaMemcpyHostToDevice, s), "copy X");
+        }
+        Xd = xdev.as<float>();
+        ldd = d;
+    }
     if ((rc = run_lens(ctx, Xd, n, d, ldd, p->m, p->lens_kind, p->lens_arg, g->lens.as<double>(), &g->pca,
-                       &g->n_pca))) return rc;
+                       &g->n_pca)))
+        return rc;
     tm.mark();
     std::shared_ptr<CoverData> cov;
     if (p->cover_kind != MAPPER_COVER_UNIFORM && p->cover_kind != MAPPER_COVER_BALANCED)

@@ -215,6 +215,28 @@ def test_balanced_cover_2d_with_ties(ctx):
     assert_same_graph(X, res, (6, 5), (0.3, 0.2), eps, 5, balanced=True)
 
 
+@pytest.mark.parametrize("kinds,args", [((0,), (0,)), ((1, 0), (3, 0)), ((2,), (0,))])
+@pytest.mark.parametrize("pinned", [False, True])
+def test_host_input_equals_device_input(ctx, kinds, args, pinned):
+    """X given in host memory (pageable or pinned; copied in chunks beside the
+    filter when the filter is row-local) gives the device-input graph."""
+    X = synth.gaussian_mixture(5003, 20, 4, seed=81, centre_box=5.0, std_lo=0.5, std_hi=1.0,
+                               anisotropic=False)
+    eps = _eps(X, 5, 81)
+    nint = (8,) * len(kinds)
+    ov = (0.3,) * len(kinds)
+    prm = mg.params(kinds, args, nint, ov, eps, 5, mg.BF16)
+    dev = mg.mapper_graph(ctx, torch.from_numpy(X).to("cuda:0"), prm)
+    host = torch.from_numpy(X).pin_memory().numpy() if pinned else X
+    hst = mg.mapper_graph(ctx, host, prm)
+    a, b = dev.numpy(), hst.numpy()
+    for k in ("node_offsets", "node_members", "node_elem", "edges"):
+        assert np.array_equal(a[k], b[k]), k
+    la, _ = dev.lens(X.shape[0], len(kinds))
+    lb, _ = hst.lens(X.shape[0], len(kinds))
+    assert np.array_equal(la, lb)
+
+
 def test_pca_lens_basis_and_bits(ctx):
     X = synth.gaussian_mixture(6000, 12, 5, seed=4, centre_box=5.0, std_lo=0.3, std_hi=1.5,
                                anisotropic=True)
