@@ -71,6 +71,8 @@ def _load():
         lib.oracle_cover.restype = i64
         lib.oracle_dbscan.argtypes = [P, i64, i32, i64, P, i64, f64, i32, P, P, P, P]
         lib.oracle_dbscan.restype = ctypes.c_int
+        lib.oracle_knn_distance.argtypes = [P, i64, i32, i64, P, i64, i32, P]
+        lib.oracle_knn_distance.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -301,3 +303,18 @@ def mapper_graph(X, lens_arr, n_intervals, overlap, eps: float, min_pts: int,
         out.update(node_offsets=no, node_members=nm, node_elem=ne,
                    edges=nerve(no, nm, X.shape[0]))
     return out
+
+
+# ------------------------------------------------------------- k-distance --
+
+def knn_distance(X, queries, k: int) -> np.ndarray:
+    """For each query row, the distance to its k-th nearest point of X (the
+    point itself counted first, at distance 0)."""
+    X = _f32(X)
+    qs = np.ascontiguousarray(queries, dtype=np.int32)
+    out = np.empty(max(qs.size, 1), dtype=np.float64)
+    rc = _load().oracle_knn_distance(_ptr(X), X.shape[0], X.shape[1], X.shape[1], _ptr(qs), qs.size, int(k),
+                                     _ptr(out))
+    if rc < 0:
+        raise ValueError("bad k-distance arguments")
+    return out[:qs.size]

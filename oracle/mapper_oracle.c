@@ -417,3 +417,33 @@ int oracle_dbscan(const float* X, int64_t n, int32_t d, int64_t ld,
     }
     return 0;
 }
+
+/* k-th nearest-neighbour distance (§5, "Visualizing Class Separation via
+ * Neuron Activations": a module plots the distribution of the distances to
+ * the k-th nearest neighbours, k = 5, to choose eps for DBSCAN). Reading:
+ * for each query point p, the k-th smallest of the distances d(p, y) over all
+ * points y of the cloud, p itself included (distance 0), so that p is a core
+ * point of DBSCAN(eps, k) on the whole cloud iff kdist(p) <= eps. Distances
+ * as in DBSCAN: the double sum of squared differences, k ascending, then
+ * sqrt. Brute force: all n squared distances, sorted. Returns -1 for k
+ * outside [1, n] or a query index outside [0, n). */
+int oracle_knn_distance(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* queries, int64_t q,
+                        int32_t k, double* out)
+{
+    if (k < 1 || k > n) return -1;
+    int bad = 0;
+#pragma omp parallel
+    {
+        double* d2 = (double*)malloc(sizeof(double) * (size_t)n);
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t i = 0; i < q; ++i) {
+            if (queries[i] < 0 || queries[i] >= n) { bad = 1; continue; }
+            const float* x = X + (int64_t)queries[i] * ld;
+            for (int64_t y = 0; y < n; ++y) d2[y] = sqdist(x, X + y * ld, d);
+            qsort(d2, (size_t)n, sizeof(double), cmp_double);
+            out[i] = sqrt(d2[k - 1]);
+        }
+        free(d2);
+    }
+    return bad ? -1 : 0;
+}

@@ -186,3 +186,35 @@ def test_blobs_circle_5k_core_partition_vs_sklearn():
         assert np.array_equal(out["core"][s:t], ref_core)
         assert _core_partition(out["labels"][s:t], ref_core) == \
             _core_partition(ref.labels_, ref_core)
+
+
+def test_knn_distance_closed_forms():
+    """k-th nearest-neighbour distance (the point itself first): points
+    0, 1, ..., 9 on a line; duplicates; k = 1 and k = n."""
+    X = np.arange(10, dtype=np.float32).reshape(-1, 1)
+    q = np.arange(10)
+    # from x = i the sorted distances are 0, 1, 1, 2, 2, ... (while both sides last)
+    assert oracle.knn_distance(X, q, 1).tolist() == [0.0] * 10
+    assert oracle.knn_distance(X, [0, 5, 9], 2).tolist() == [1.0, 1.0, 1.0]
+    assert oracle.knn_distance(X, [0, 5, 9], 4).tolist() == [3.0, 2.0, 3.0]
+    assert oracle.knn_distance(X, [0, 4, 9], 10).tolist() == [9.0, 5.0, 9.0]
+    # a 3-4-5 triangle
+    T = np.array([[0, 0], [3, 0], [0, 4]], dtype=np.float32)
+    assert oracle.knn_distance(T, [0, 1, 2], 2).tolist() == [3.0, 3.0, 4.0]
+    assert oracle.knn_distance(T, [0, 1, 2], 3).tolist() == [4.0, 5.0, 5.0]
+    # duplicates count: three copies of a point reach k = 3 at distance 0
+    D = np.array([[1, 1], [1, 1], [1, 1], [4, 5]], dtype=np.float32)
+    assert oracle.knn_distance(D, [0, 3], 3).tolist() == [0.0, 5.0]
+    with pytest.raises(ValueError):
+        oracle.knn_distance(D, [0], 5)
+
+
+def test_knn_distance_is_the_core_threshold():
+    """kdist(p) <= eps iff p has at least k neighbours (itself included) in
+    the whole cloud, i.e. iff p is core for DBSCAN(eps, k) on one element."""
+    X = synth.tiny_random(300, 5, 9, scale=2.0)
+    k = 6
+    kd = oracle.knn_distance(X, np.arange(300), k)
+    for eps in (0.3, 0.45, 0.6):
+        _, core, _, _ = oracle.dbscan(X, np.arange(300, dtype=np.int32), eps, k)
+        assert np.array_equal(core, kd <= eps)
