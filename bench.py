@@ -426,6 +426,60 @@ def run_sweep(args):
     }))
 
 
+def run_knn(args):
+    """k-th nearest-neighbour distances (k = 5, as in the paper's module for
+    choosing eps) of a seeded sample of query rows against the whole 1M x 256
+    cloud; the oracle's brute force on a few of the same queries beside it."""
+    import torch
+    import paper_2011_03209_gb300 as mg
+
+    torch.cuda.set_device(0)
+    w = synth.clusters_1m_d256(args.n)
+    Xd = torch.from_numpy(w.X).to("cuda:0")
+    rng = np.random.default_rng(5)
+    q = np.sort(rng.choice(w.n, size=min(args.queries, w.n), replace=False)).astype(np.int32)
+    k = 5
+    stream = torch.cuda.Stream()
+    with mg.Context(0, stream=stream) as ctx:
+        for _ in range(args.warmup):
+            mg.mapper_knn_distance(ctx, Xd, q, k)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(0)
+        sampler.start()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(args.steps):
+            kd = mg.mapper_knn_distance(ctx, Xd, q, k)
+        end.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+    ms = start.elapsed_time(end) / args.steps
+    # FP32 screen: two passes of 3 d flops (sub, FMA) per (query, row) pair
+    tflops = 2 * 3 * w.d * float(q.size) * w.n / (ms * 1e-3) / 1e12
+    peak = 152 * 128 * 2 * 2070e6 / 1e12
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        sub = q[:4]
+        t0 = time.perf_counter()
+        ref = oracle.knn_distance(w.X, sub, k)
+        cpu_ms = (time.perf_counter() - t0) * 1e3
+        assert np.array_equal(ref, kd[:4])
+        cpu = {"value": cpu_ms / sub.size * q.size, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{sub.size} of the {q.size} queries, scaled by queries; equal to the GPU values"}
+    print(json.dumps({
+        "metric": f"k-distance ms ({q.size} queries, k = {k}, {w.n // 1000}k x {w.d})", "value": ms, "unit": "ms",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "dtype": "f32+f64",
+        "data": "synthetic", "config": {"workload": f"clusters_{w.n // 1000}k_d{w.d}_knn", "queries": int(q.size),
+                                        "k": k},
+        "queries_per_s": q.size / (ms * 1e-3),
+        "roofline": {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                     "traffic": None, "kernel": "knn_kernel<0,1>: FP32 screen, 3 d flops per pair per pass",
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max clock)"},
+        "cpu_baseline": cpu, "clocks": clocks,
+    }))
+
+
 def run_sharded(args):
     """One 1M x 256 graph per step with its cover elements split over the
     ranks (longest processing time by n_i^2 d), each rank clustering its
@@ -499,13 +553,14 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=12.0,
                     help="seconds of oracle DBSCAN per reference sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="clusters", choices=["clusters", "serving", "sweep", "sharded"],
+    ap.add_argument("--workload", default="clusters", choices=["clusters", "serving", "sweep", "sharded", "knn"],
                     help="clusters: the 1M x 256 graph (default; N ranks = N replicas); serving: the "
                          "request mix; sweep: 16 graphs of the 500k x 128 2D-lens cloud; sharded: the "
                          "1M x 256 graph with its elements split over the ranks")
     ap.add_argument("--requests", type=int, default=200, help="serving: timed requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent slots")
+    ap.add_argument("--queries", type=int, default=8192, help="knn: query rows")
     ap.add_argument("--lens", default="l2", choices=["l2", "ecc"],
                     help="clusters workload filter: L2 norm (default) or eccentricity (exponent 2); "
                          "the oracle sample needs the L2 filter")
@@ -522,6 +577,8 @@ def main():
         run_sweep(args)
     elif args.workload == "sharded":
         run_sharded(args)
+    elif args.workload == "knn":
+        run_knn(args)
     else:
         run_ours(args)
 

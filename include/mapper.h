@@ -242,6 +242,19 @@ int mapper_cover_subset(mapper_ctx* ctx, const mapper_cover_t* cover, const int3
 int mapper_nerve_from_nodes(mapper_ctx* ctx, int64_t n_points, int64_t n_nodes, const int64_t* node_offsets,
                             const int32_t* node_members, const int32_t* node_elem, mapper_graph_t** out);
 
+/* k-th nearest-neighbour distances (§5: a module plots the distribution of
+ * the distances to the k-th nearest neighbours, k = 5, to choose eps): for
+ * each query row index queries[i] (in [0, n)), the k-th smallest distance to
+ * the rows of X, the row itself counted first (distance 0), so the row is
+ * core for DBSCAN(eps, k) on the whole cloud iff the value is <= eps. The
+ * value is the FP64 distance of the defining expression (double sum of
+ * squared differences, k ascending, sqrt), found exactly through an FP32
+ * screen. X: device memory. queries (q int32) and out (q doubles): host or
+ * device memory, out filled before the call returns. k in [1, min(16, n)],
+ * d <= 1184; MAPPER_EINVAL otherwise, MAPPER_ENONFINITE if X holds NaN/Inf. */
+int mapper_knn_distance(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, int64_t ld,
+                        const int32_t* queries, int64_t q, int32_t k, double* out);
+
 /* Fused call: lens, cover, cluster and nerve in one. X may be a device
  * pointer or a host pointer (pinned or pageable); a host X is copied to the
  * device inside the call. */

@@ -21,7 +21,7 @@ __all__ = [
     "Context", "Cover", "Clusters", "Graph", "MapperError", "mapper_lens", "mapper_cover",
     "mapper_cluster", "mapper_nerve", "mapper_graph", "params", "LENS_L2", "LENS_COORD",
     "LENS_PCA", "LENS_ECC", "COVER_UNIFORM", "COVER_BALANCED", "FP32", "BF16", "BF16X1", "mapper_dbscan_noalloc", "Server", "graph_footprint",
-    "mapper_graph_sweep", "mapper_cover_subset", "mapper_nerve_from_nodes",
+    "mapper_graph_sweep", "mapper_cover_subset", "mapper_nerve_from_nodes", "mapper_knn_distance",
 ]
 
 
@@ -230,6 +230,17 @@ def mapper_nerve(ctx: Context, clusters: Clusters) -> Graph:
     h = ctypes.c_void_p()
     _capi.check(ctx._lib.mapper_nerve(ctx.h, clusters.h, ctypes.byref(h)), "mapper_nerve")
     return Graph(ctx._lib, h)
+
+
+def mapper_knn_distance(ctx: Context, X, queries, k: int) -> np.ndarray:
+    """Distance from each query row to its k-th nearest row of X (the row
+    itself first), exact in FP64. X: CUDA tensor."""
+    p, n, d, ld, _keep = _x_args(X)
+    qs = np.ascontiguousarray(np.asarray(queries, dtype=np.int32))
+    out = np.empty(max(qs.size, 1), dtype=np.float64)
+    _capi.check(ctx._lib.mapper_knn_distance(ctx.h, p, n, d, ld, _vp(qs.ctypes.data) if qs.size else None,
+                                             int(qs.size), int(k), _vp(out.ctypes.data)), "mapper_knn_distance")
+    return out[:qs.size]
 
 
 def mapper_cover_subset(ctx: Context, cover: Cover, elements) -> Cover:

@@ -28,7 +28,7 @@ FP32, BF16, BF16X1 = 0, 1, 2
 # every symbol include/mapper.h declares
 EXPORTS = (
     "mapper_create", "mapper_destroy", "mapper_set_stream", "mapper_set_timing", "mapper_set_pass1_tile_n",
-    "mapper_cover_subset", "mapper_nerve_from_nodes", "mapper_cover_balanced",
+    "mapper_cover_subset", "mapper_nerve_from_nodes", "mapper_cover_balanced", "mapper_knn_distance",
     "mapper_lens", "mapper_cover", "mapper_cover_sizes", "mapper_cover_copy",
     "mapper_cluster", "mapper_clusters_copy", "mapper_nerve", "mapper_graph",
     "mapper_graph_sizes", "mapper_graph_copy", "mapper_graph_lens", "mapper_graph_cover",
@@ -144,6 +144,7 @@ def load(path: str | None = None):
             "mapper_lens": (ctypes.c_int, [P, P, i64, i32, i64, i32, P, P, P, P]),
             "mapper_cover": (ctypes.c_int, [P, P, i64, i32, P, P, PP]),
             "mapper_cover_balanced": (ctypes.c_int, [P, P, i64, i32, P, P, PP]),
+            "mapper_knn_distance": (ctypes.c_int, [P, P, i64, i32, i64, P, i64, i32, P]),
             "mapper_cover_sizes": (ctypes.c_int, [P, P, P]),
             "mapper_cover_copy": (ctypes.c_int, [P, P, P, ctypes.c_int]),
             "mapper_cluster": (ctypes.c_int, [P, P, i64, i32, i64, P, f64, i32, i32, PP]),

@@ -1054,6 +1054,37 @@ int mapper_nerve_from_nodes(mapper_ctx* ctx, int64_t n_points, int64_t n_nodes, 
     return MAPPER_OK;
 }
 
+int mapper_knn_distance(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, int64_t ld,
+                        const int32_t* queries, int64_t q, int32_t k, double* out)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if ((rc = check_x(X_dev, n, d, ld))) return rc;
+    if (q < 0 || (q > 0 && (!queries || !out))) return fail(MAPPER_EINVAL, "bad query arguments");
+    if (q == 0) return MAPPER_OK;
+    if (is_host_pointer(X_dev)) return fail(MAPPER_EINVAL, "X must be in device memory");
+    cudaStream_t s = ctx->stream->s;
+    std::vector<int32_t> hq((size_t)q);
+    const bool q_host = is_host_pointer(queries);
+    CK(cudaMemcpyAsync(hq.data(), queries, sizeof(int32_t) * q,
+                       q_host ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost, s), "copy");
+    Buf qd, od, flag;
+    CK(flag.alloc(sizeof(int), s), "alloc");
+    CK(cudaMemsetAsync(flag.p, 0, sizeof(int), s), "memset");
+    CK(check_finite(X_dev, n, d, ld, flag.as<int>(), s), "finite");
+    int h_nf = 0;
+    CK(cudaMemcpyAsync(&h_nf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    if (h_nf) return fail(MAPPER_ENONFINITE, "X holds NaN or Inf");
+    for (int64_t i = 0; i < q; ++i)
+        if (hq[i] < 0 || hq[i] >= n) return fail(MAPPER_EINVAL, "query index out of range");
+    CK(qd.alloc(sizeof(int32_t) * q, s), "alloc");
+    CK(od.alloc(sizeof(double) * q, s), "alloc");
+    CK(cudaMemcpyAsync(qd.p, hq.data(), sizeof(int32_t) * q, cudaMemcpyHostToDevice, s), "copy");
+    if ((rc = knn_distance(X_dev, n, d, ld, qd.as<int32_t>(), q, k, od.as<double>(), s))) return rc;
+    return copy_out(out, od.p, sizeof(double) * q, !is_host_pointer(out), s);
+}
+
 int mapper_graph(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
                  const mapper_params* p, mapper_graph_t** out)
 {

@@ -1,0 +1,78 @@
+"""k-th nearest-neighbour distances on the GPU (§5's module for choosing
+eps): equal to the oracle's brute-force FP64 values bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2011_03209_gb300 import synth
+
+torch = pytest.importorskip("torch")
+mg = pytest.importorskip("paper_2011_03209_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = mg.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("n,d,k,seed", [(1, 3, 1, 0), (40, 2, 16, 1), (3001, 17, 5, 2),
+                                        (5000, 64, 1, 3), (4000, 130, 16, 4), (2500, 600, 5, 5)])
+def test_knn_distance_equals_oracle(ctx, n, d, k, seed):
+    X = (synth.gaussian_mixture(n, d, 6, seed=90 + seed, centre_box=4.0, std_lo=0.3, std_hi=1.0,
+                                anisotropic=True, noise_frac=0.05)
+         if n > 40 else synth.tiny_random(n, d, seed, scale=3.0))
+    rng = np.random.default_rng(seed)
+    q = np.unique(rng.integers(0, n, size=min(n, 300))).astype(np.int32)
+    got = mg.mapper_knn_distance(ctx, torch.from_numpy(X).to("cuda:0"), q, k)
+    ref = oracle.knn_distance(X, q, k)
+    assert np.array_equal(got, ref)
+
+
+def test_knn_distance_duplicates_and_all_points(ctx):
+    X = synth.tiny_random(64, 5, 7, dup_frac=0.5)
+    Xd = torch.from_numpy(X).to("cuda:0")
+    q = np.arange(64, dtype=np.int32)
+    for k in (1, 2, 3, 8, 16):
+        assert np.array_equal(mg.mapper_knn_distance(ctx, Xd, q, k), oracle.knn_distance(X, q, k))
+    # queries given in device memory
+    qd = torch.from_numpy(q).to("cuda:0")
+    out = np.empty(64)
+    lib = ctx._lib
+    import ctypes
+    p = ctypes.c_void_p(Xd.data_ptr())
+    assert lib.mapper_knn_distance(ctx.h, p, 64, 5, 5, ctypes.c_void_p(qd.data_ptr()), 64, 4,
+                                   ctypes.c_void_p(out.ctypes.data)) == 0
+    assert np.array_equal(out, oracle.knn_distance(X, q, 4))
+
+
+def test_knn_distance_core_threshold_matches_dbscan(ctx):
+    """kdist(p) <= eps exactly when p is core for DBSCAN(eps, k) on the whole
+    cloud (one cover element)."""
+    X = synth.gaussian_mixture(3000, 12, 5, seed=95, centre_box=4.0, std_lo=0.4, std_hi=1.0, anisotropic=False)
+    Xd = torch.from_numpy(X).to("cuda:0")
+    k = 6
+    kd = mg.mapper_knn_distance(ctx, Xd, np.arange(3000), k)
+    s = np.unique(kd)
+    i = int(0.4 * s.size)
+    eps = float((s[i] + s[i + 1]) / 2)                 # halfway between two k-distances
+    prm = mg.params((mg.LENS_COORD,), (0,), (1,), (0.0,), eps, k, mg.BF16)
+    g = mg.mapper_graph(ctx, Xd, prm)
+    offs, pts = g.cover().numpy()
+    _, core = g.clusters().numpy(len(pts))
+    assert np.array_equal(core[np.argsort(pts)], kd <= eps)
+
+
+def test_knn_distance_rejects_bad_input(ctx):
+    X = synth.tiny_random(20, 4, 1)
+    Xd = torch.from_numpy(X).to("cuda:0")
+    for q, k in (([0], 0), ([0], 21), ([0], 17), ([20], 3), ([-1], 3)):
+        with pytest.raises(mg.MapperError):
+            mg.mapper_knn_distance(ctx, Xd, q, k)
+    Y = X.copy()
+    Y[3, 2] = np.nan
+    with pytest.raises(mg.MapperError):
+        mg.mapper_knn_distance(ctx, torch.from_numpy(Y).to("cuda:0"), [0], 3)
