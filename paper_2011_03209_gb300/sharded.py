@@ -100,7 +100,8 @@ def sharded_graph(ctx, X, prm, group=None):
     args = [int(prm.lens_arg[i]) for i in range(m)]
     lens, _ = mg.mapper_lens(ctx, X, kinds, args)
     cover = mg.mapper_cover(ctx, lens, [int(prm.n_intervals[i]) for i in range(m)],
-                            [float(prm.overlap[i]) for i in range(m)])
+                            [float(prm.overlap[i]) for i in range(m)],
+                            balanced=int(prm.cover_kind) == mg.COVER_BALANCED)
     offs, _ = cover.numpy()
     d = int(X.shape[1])
     sizes = np.diff(offs).astype(np.float64)

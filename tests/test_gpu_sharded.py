@@ -42,10 +42,12 @@ def test_shares_merge_to_the_whole_graph(prec, world):
     _same(g, whole)
 
 
-def test_sharded_graph_single_process():
+@pytest.mark.parametrize("cover_kind", [mg.COVER_UNIFORM, mg.COVER_BALANCED])
+def test_sharded_graph_single_process(cover_kind):
     w = synth.blobs_circle_5k()
     Xd = torch.from_numpy(w.X).to("cuda:0")
-    prm = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, mg.BF16)
+    prm = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, mg.BF16,
+                    cover_kind=cover_kind)
     with mg.Context(0) as ctx:
         whole = mg.mapper_graph(ctx, Xd, prm).numpy()
         g, mine = sharded.sharded_graph(ctx, Xd, prm)
