@@ -61,6 +61,9 @@ def _load():
         lib.oracle_lens_l2.argtypes = [P, i64, i32, i64, P]
         lib.oracle_lens_ecc2.argtypes = [P, i64, i32, i64, P]
         lib.oracle_lens_coord.argtypes = [P, i64, i32, i64, i32, P]
+        lib.oracle_lens_linf.argtypes = [P, i64, i32, i64, P]
+        lib.oracle_lens_density.argtypes = [P, i64, i32, i64, f64, P]
+        lib.oracle_lens_ecc_inf.argtypes = [P, i64, i32, i64, P]
         lib.oracle_lens_project.argtypes = [P, i64, i32, i64, P, P, P]
         lib.oracle_pca.argtypes = [P, i64, i32, i64, i32, P, P, P]
         lib.oracle_pca.restype = ctypes.c_int
@@ -113,6 +116,32 @@ def lens_ecc2(X) -> np.ndarray:
     return f
 
 
+def lens_linf(X) -> np.ndarray:
+    """max_k |x_k| per row."""
+    X = _f32(X)
+    f = np.empty(X.shape[0], dtype=np.float64)
+    _load().oracle_lens_linf(_ptr(X), X.shape[0], X.shape[1], X.shape[1], _ptr(f))
+    return f
+
+
+def lens_density(X, r: float) -> np.ndarray:
+    """Number of points within distance r of each row (itself included),
+    O(n^2 d): small clouds only."""
+    X = _f32(X)
+    f = np.empty(X.shape[0], dtype=np.float64)
+    _load().oracle_lens_density(_ptr(X), X.shape[0], X.shape[1], X.shape[1], float(r), _ptr(f))
+    return f
+
+
+def lens_ecc_inf(X) -> np.ndarray:
+    """Largest distance from each row to the cloud, O(n^2 d): small clouds
+    only."""
+    X = _f32(X)
+    f = np.empty(X.shape[0], dtype=np.float64)
+    _load().oracle_lens_ecc_inf(_ptr(X), X.shape[0], X.shape[1], X.shape[1], _ptr(f))
+    return f
+
+
 def lens_coord(X, j: int) -> np.ndarray:
     X = _f32(X)
     f = np.empty(X.shape[0], dtype=np.float64)
@@ -142,10 +171,10 @@ def pca(X, k: int = 1):
     return mu, V, lam
 
 
-def lens(X, kinds, args, pca_basis=None) -> np.ndarray:
+def lens(X, kinds, args, pca_basis=None, radii=None) -> np.ndarray:
     """n x m lens. For principal-component lenses, `pca_basis` = (mu, V)
     fixes the projection (the GPU's own, for parity); otherwise the oracle's
-    FP64 PCA supplies it."""
+    FP64 PCA supplies it. `radii[j]` is the ball radius of a density lens."""
     X = _f32(X)
     cols = []
     basis = pca_basis
@@ -161,6 +190,12 @@ def lens(X, kinds, args, pca_basis=None) -> np.ndarray:
             cols.append(lens_project(X, basis[0], basis[1][arg]))
         elif kind == 3:
             cols.append(lens_ecc2(X))
+        elif kind == 4:
+            cols.append(lens_linf(X))
+        elif kind == 5:
+            cols.append(lens_density(X, radii[len(cols)]))
+        elif kind == 6:
+            cols.append(lens_ecc_inf(X))
         else:
             raise ValueError(kind)
     return np.ascontiguousarray(np.stack(cols, axis=1))

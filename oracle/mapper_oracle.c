@@ -102,6 +102,70 @@ void oracle_lens_ecc2(const float* X, int64_t n, int32_t d, int64_t ld, double* 
     }
 }
 
+/* L-infinity-norm filter (§5, breast-cancer use case: the first filter of
+ * both 2D mapper graphs is the "L_infinity-norm"). Reading: the norm of the
+ * point itself, f(x) = max_k |x_k|, as L2 is sqrt(sum_k x_k^2). */
+void oracle_lens_linf(const float* X, int64_t n, int32_t d, int64_t ld, double* f)
+{
+    for (int64_t p = 0; p < n; ++p) {
+        const float* x = X + p * ld;
+        double m = 0.0;
+        for (int32_t k = 0; k < d; ++k) {
+            double v = fabs((double)x[k]);
+            if (v > m) m = v;
+        }
+        f[p] = m;
+    }
+}
+
+/* Density filter (§4.1 lists density among the derived filters; no estimator
+ * is given). Reading: the number of points of the cloud within distance r of
+ * x, x itself included (a ball-count, i.e. uniform-kernel, density estimate
+ * without its constant factor): f(x) = |{y in X : d(x, y)^2 <= r * r}|, the
+ * squared distance summed in double for k ascending as in DBSCAN. */
+void oracle_lens_density(const float* X, int64_t n, int32_t d, int64_t ld, double r, double* f)
+{
+    const double r2 = r * r;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t p = 0; p < n; ++p) {
+        const float* x = X + p * ld;
+        int64_t c = 0;
+        for (int64_t q = 0; q < n; ++q) {
+            const float* y = X + q * ld;
+            double d2 = 0.0;
+            for (int32_t k = 0; k < d; ++k) {
+                double t = (double)x[k] - (double)y[k];
+                d2 = d2 + t * t;
+            }
+            if (d2 <= r2) ++c;
+        }
+        f[p] = (double)c;
+    }
+}
+
+/* L-infinity centrality, the other reading of §5's "L_infinity-norm" filter
+ * computed from the pairwise distance matrix: the largest entry of x's row,
+ * f(x) = max_{y in X} d(x, y) (eccentricity with exponent infinity). The
+ * largest squared distance (double sum, k ascending), then sqrt. */
+void oracle_lens_ecc_inf(const float* X, int64_t n, int32_t d, int64_t ld, double* f)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t p = 0; p < n; ++p) {
+        const float* x = X + p * ld;
+        double m = 0.0;
+        for (int64_t q = 0; q < n; ++q) {
+            const float* y = X + q * ld;
+            double d2 = 0.0;
+            for (int32_t k = 0; k < d; ++k) {
+                double t = (double)x[k] - (double)y[k];
+                d2 = d2 + t * t;
+            }
+            if (d2 > m) m = d2;
+        }
+        f[p] = sqrt(m);
+    }
+}
+
 /* Filter "based on a chosen dimension (column)" (§4.1): f(x) = x_j. */
 void oracle_lens_coord(const float* X, int64_t n, int32_t d, int64_t ld, int32_t j, double* f)
 {

@@ -49,6 +49,74 @@ def test_eccentricity_invariants():
     np.testing.assert_allclose(f, ident, rtol=1e-12)
 
 
+def test_linf_lens_closed_forms_and_numpy():
+    """L-infinity norm of each row: hand values, numpy's ord=inf norm, and the
+    norm inequalities |x|_inf <= |x|_2 <= sqrt(d) |x|_inf (equal on scaled unit
+    vectors)."""
+    X = np.array([[0, 0, 0], [1, -3, 2], [-0.5, 0.25, 0.5], [-7, 7, -7]], dtype=np.float32)
+    assert oracle.lens_linf(X).tolist() == [0.0, 3.0, 0.5, 7.0]
+    Y = synth.tiny_random(500, 9, seed=12, scale=5.0)
+    f = oracle.lens_linf(Y)
+    assert np.array_equal(f, np.linalg.norm(Y.astype(np.float64), ord=np.inf, axis=1))
+    l2 = oracle.lens_l2(Y)
+    assert np.all(f <= l2) and np.all(l2 <= np.sqrt(9.0) * f * (1 + 1e-15))
+    E = np.diag(np.arange(1, 6, dtype=np.float32)) * np.float32(-1.5)
+    assert np.array_equal(oracle.lens_linf(E), oracle.lens_l2(E))
+
+
+def test_density_lens_closed_forms():
+    """Ball counts (self included), pinned by hand: points 0..9 on a line with
+    r = 1.5 have 3 points within r, 2 at the ends; r below every distance
+    gives 1; r at least the diameter gives n; a hand-worked planar case."""
+    line = np.arange(10, dtype=np.float32).reshape(-1, 1)
+    assert oracle.lens_density(line, 1.5).tolist() == [2.0] + [3.0] * 8 + [2.0]
+    assert oracle.lens_density(line, 2.0).tolist() == [3.0, 4.0] + [5.0] * 6 + [4.0, 3.0]
+    assert np.all(oracle.lens_density(line, 0.5) == 1.0)
+    assert np.all(oracle.lens_density(line, 9.0) == 10.0)
+    # (0,0) (1,0) (3,0) (3,4), r = 2: the distance 2 between (1,0) and (3,0) counts
+    P = np.array([[0, 0], [1, 0], [3, 0], [3, 4]], dtype=np.float32)
+    assert oracle.lens_density(P, 2.0).tolist() == [2.0, 3.0, 2.0, 1.0]
+    # duplicates count once each
+    D = np.array([[1, 1], [1, 1], [1, 1], [5, 5]], dtype=np.float32)
+    assert oracle.lens_density(D, 0.1).tolist() == [3.0, 3.0, 3.0, 1.0]
+
+
+def test_density_lens_against_kdtree_and_pair_count():
+    """On a cloud of multiples of 1/8 every squared distance is exact in
+    double; with r^2 halfway between two multiples of 1/64 no pair is on the
+    sphere, so scipy's k-d tree ball counts are exact too, and the counts sum
+    to n + 2 x (pairs within r)."""
+    spatial = pytest.importorskip("scipy.spatial")
+    Y = np.round(synth.tiny_random(600, 5, seed=21, scale=2.0) * 8.0).astype(np.float32) / 8.0
+    r2 = 60.0 / 64.0 + 1.0 / 128.0
+    f = oracle.lens_density(Y, np.sqrt(r2))
+    Y64 = Y.astype(np.float64)
+    tree = spatial.cKDTree(Y64)
+    ref = tree.query_ball_point(Y64, np.sqrt(r2), return_length=True)
+    assert np.array_equal(f, ref.astype(np.float64))
+    pairs = int((spatial.distance.pdist(Y64, "sqeuclidean") <= r2).sum())
+    assert int(f.sum()) == Y.shape[0] + 2 * pairs
+    assert f.min() >= 1.0 and f.max() > 2.0
+
+
+def test_ecc_inf_lens_closed_forms_and_scipy():
+    """Largest distance to the cloud: on a line max(x - min, max - x); the
+    hand-worked planar case; scipy's cdist row maxima; its maximum is the
+    diameter and it bounds the exponent-2 eccentricity from above."""
+    spatial = pytest.importorskip("scipy.spatial")
+    line = np.array([[-2.0], [0.0], [1.0], [5.0]], dtype=np.float32)
+    assert oracle.lens_ecc_inf(line).tolist() == [7.0, 5.0, 4.0, 7.0]
+    P = np.array([[0, 0], [1, 0], [3, 0], [3, 4]], dtype=np.float32)
+    np.testing.assert_allclose(oracle.lens_ecc_inf(P), [5.0, np.sqrt(20.0), 4.0, 5.0], rtol=1e-15)
+    assert oracle.lens_ecc_inf(np.array([[1.0, 2.0]], dtype=np.float32)).tolist() == [0.0]
+    Y = synth.tiny_random(300, 7, seed=22, scale=3.0)
+    f = oracle.lens_ecc_inf(Y)
+    Dm = spatial.distance.cdist(Y.astype(np.float64), Y.astype(np.float64))
+    np.testing.assert_allclose(f, Dm.max(axis=1), rtol=1e-14)
+    np.testing.assert_allclose(f.max(), Dm.max(), rtol=1e-14)
+    assert np.all(f >= oracle.lens_ecc2(Y) * (1 - 1e-14))
+
+
 def test_coord_lens_is_the_column():
     Y = synth.tiny_random(100, 5, seed=4)
     for j in range(5):
