@@ -29,6 +29,8 @@ if ROOT not in sys.path:
 
 from paper_2011_03209_gb300 import synth  # noqa: E402
 
+LENS_NAMES = {"l2": "L2", "ecc": "eccentricity (exponent 2)", "linf": "L-infinity norm",
+              "density": "density (points within eps)"}
 METRIC = "mapper graph ms (1M x 256, exact graph)"
 GPU_FP32_LANES = 128                 # FP32 lanes per SM (Blackwell)
 
@@ -195,9 +197,11 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     ctx = mg.Context(local, stream=stream)
     ctx.set_timing(True)
-    lens_kind = (mg.LENS_ECC,) if args.lens == "ecc" else w.lens_kind
+    lens_kind = {"l2": w.lens_kind, "ecc": (mg.LENS_ECC,), "linf": (mg.LENS_LINF,),
+                 "density": (mg.LENS_DENSITY,)}[args.lens]
     cover_kind = mg.COVER_BALANCED if args.cover == "balanced" else mg.COVER_UNIFORM
-    prm = mg.params(lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, prec, cover_kind)
+    prm = mg.params(lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, prec, cover_kind,
+                    lens_param=(w.eps,))
 
     for _ in range(args.warmup):
         g = mg.mapper_graph(ctx, Xd, prm)
@@ -279,9 +283,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if prec == mg.FP32 else "bf16+f64",
         "data": "synthetic",
-        "config": {"workload": w.name + ("" if args.lens == "l2" else "_ecc")
+        "config": {"workload": w.name + ("" if args.lens == "l2" else "_" + args.lens)
                    + ("" if args.cover == "uniform" else "_balanced"), "n": w.n, "d": w.d,
-                   "lens": "L2" if args.lens == "l2" else "eccentricity (exponent 2)", "cover": args.cover,
+                   "lens": LENS_NAMES[args.lens], "cover": args.cover,
                    "n_intervals": w.n_intervals[0], "overlap": w.overlap[0], "eps": w.eps,
                    "min_pts": w.min_pts, "precision": args.precision,
                    "l2_flush": "inputs larger than L2 (1 GB point cloud read every step)",
@@ -295,7 +299,7 @@ def run_ours(args):
                                         "tile_pairs_out", "tile_pairs_in", "tile_pairs_tc",
                                         "tile_pairs_simt", "union_pairs", "union_skipped", "pairs_screened",
                                         "band_pairs", "fp64_pairs", "near_ties", "n_core", "n_nodes", "n_edges",
-                                        "pass1_tile_n")},
+                                        "pass1_tile_n", "tile_pairs_cross")},
         "ms_tiles": float(np.mean([s["ms_tiles"] for s in stats])),
         "roofline": roof,
         "clocks": clocks,
@@ -561,9 +565,10 @@ def main():
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent slots")
     ap.add_argument("--queries", type=int, default=8192, help="knn: query rows")
-    ap.add_argument("--lens", default="l2", choices=["l2", "ecc"],
-                    help="clusters workload filter: L2 norm (default) or eccentricity (exponent 2); "
-                         "the oracle sample needs the L2 filter")
+    ap.add_argument("--lens", default="l2", choices=sorted(LENS_NAMES),
+                    help="clusters workload filter: L2 norm (default), eccentricity (exponent 2), "
+                         "L-infinity norm, or density (points within eps); the oracle sample needs "
+                         "the L2 filter")
     ap.add_argument("--cover", default="uniform", choices=["uniform", "balanced"],
                     help="clusters workload cover: uniform intervals (default) or balanced (equal counts)")
     ap.add_argument("--n", type=int, default=1_000_000,

@@ -59,7 +59,7 @@
 extern "C" {
 #endif
 
-#define MAPPER_ABI_VERSION 3
+#define MAPPER_ABI_VERSION 4
 
 typedef enum mapper_status {
     MAPPER_OK = 0,
@@ -76,8 +76,14 @@ typedef enum mapper_lens_kind {
     MAPPER_LENS_L2 = 0,      /* §3: "Common choices include the L2-norm" */
     MAPPER_LENS_COORD = 1,   /* §4.1: filter "based on a chosen dimension" */
     MAPPER_LENS_PCA = 2,     /* projection on a principal axis (PCA module, §4.1) */
-    MAPPER_LENS_ECC = 3      /* eccentricity, exponent 2: sqrt(mean over the cloud of
+    MAPPER_LENS_ECC = 3,     /* eccentricity, exponent 2: sqrt(mean over the cloud of
                                 |x - y|^2) (§3 "eccentricity", §4.1 derived filters) */
+    MAPPER_LENS_LINF = 4,    /* L-infinity norm max_k |x_k| (§5: the breast-cancer mapper
+                                graphs filter by the "L_infinity-norm") */
+    MAPPER_LENS_DENSITY = 5  /* density (§4.1 derived filters): the number of points within
+                                distance r of x, x included, r = lens_param[j]; exact counts
+                                (the pass-1 neighbour counts of DBSCAN(r, .) on the whole
+                                cloud), returned as doubles */
 } mapper_lens_kind;
 
 /* Precision of the eps-neighbourhood screen. Every pair whose screened
@@ -121,6 +127,7 @@ typedef struct mapper_params {
     int32_t min_pts;         /* DBSCAN minPts >= 1 */
     int32_t precision;       /* mapper_precision */
     int32_t cover_kind;      /* mapper_cover_kind */
+    double lens_param[2];    /* DENSITY: ball radius r (finite, > 0); other kinds: ignored */
 } mapper_params;
 
 /* Counters of one computation (filled by mapper_stats_get). */
@@ -143,7 +150,8 @@ typedef struct mapper_stats {
     double ms_pass[3];       /* device time of the count, union and border passes */
     double ms_tiles;         /* device time of tile layout and tile-pair classification */
     int64_t tile_pairs_tc;   /* mixed tile pairs screened on tensor cores */
-    int64_t tile_pairs_simt; /* mixed tile pairs screened on CUDA cores (FP32) */
+    int64_t tile_pairs_simt; /* mixed tile pairs across two segments (two centres): CUDA cores
+                                (FP32), or tensor cores (tile_pairs_cross) */
     int64_t union_skipped;   /* union-pass tile pairs skipped: their cores already joined */
     int64_t n_groups;        /* pivot groups of the tile layout */
     int64_t n_rows;          /* rows of the tile layout (memberships + tile padding) */
@@ -157,6 +165,10 @@ typedef struct mapper_stats {
     int64_t pass1_tile_n;    /* N of the pass-1 tensor-core product, picked by the context's
                                 autotuner: 128 (one tile pair per work item) or 256 (two tile
                                 pairs sharing tile A); 0 off the tensor cores */
+    int64_t tile_pairs_cross;  /* of tile_pairs_simt (mixed pairs across two segments of one
+                                  element), those screened on the tensor cores with rows
+                                  centred per element: all of them when they are at least
+                                  1/32 of the rows (BF16 precisions), else none */
 } mapper_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -176,6 +188,12 @@ int mapper_set_timing(mapper_ctx* ctx, int enabled);
  * work item, 256 = two tile pairs sharing their first tile. Other values:
  * MAPPER_EINVAL. */
 int mapper_set_pass1_tile_n(mapper_ctx* ctx, int tile_n);
+/* Where the BF16 precisions screen mixed tile pairs across two segments of
+ * one element (a tuning knob; results do not depend on it): 0 = on the
+ * tensor cores when they are at least 1/32 of the rows, else on CUDA cores
+ * (default), 1 = always on the tensor cores (rows centred per element, a
+ * second operand set), 2 = always on CUDA cores. Other values: MAPPER_EINVAL. */
+int mapper_set_cross_screen(mapper_ctx* ctx, int mode);
 
 /* -------------------------------------------------------------- the steps */
 
@@ -189,6 +207,15 @@ int mapper_set_pass1_tile_n(mapper_ctx* ctx, int tile_n);
 int mapper_lens(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, int64_t ld,
                 int32_t m, const int32_t* kinds, const int32_t* args,
                 double* lens_dev, double* pca_out);
+/* The same with per-dimension real parameters lens_param[m] (host; the
+ * density radius; may be NULL when no lens needs one) and the screen
+ * precision of the density lens's neighbour counts (mapper_precision; the
+ * counts are exact in every precision). mapper_lens is this call with
+ * lens_param = NULL and MAPPER_BF16. A density lens without a finite radius
+ * > 0: MAPPER_EINVAL. */
+int mapper_lens_ex(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, int64_t ld,
+                   int32_t m, const int32_t* kinds, const int32_t* args, const double* lens_param,
+                   int32_t precision, double* lens_dev, double* pca_out);
 
 /* Cover (§3: intervals V_k of f(X), n elements, overlap p; 2D: rectangles)
  * and pull-back: for each element, the points with f in it, ascending.

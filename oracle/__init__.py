@@ -64,6 +64,7 @@ def _load():
         lib.oracle_lens_linf.argtypes = [P, i64, i32, i64, P]
         lib.oracle_lens_density.argtypes = [P, i64, i32, i64, f64, P]
         lib.oracle_lens_ecc_inf.argtypes = [P, i64, i32, i64, P]
+        lib.oracle_density_at.argtypes = [P, i64, i32, i64, P, i64, f64, P]
         lib.oracle_lens_project.argtypes = [P, i64, i32, i64, P, P, P]
         lib.oracle_pca.argtypes = [P, i64, i32, i64, i32, P, P, P]
         lib.oracle_pca.restype = ctypes.c_int
@@ -131,6 +132,19 @@ def lens_density(X, r: float) -> np.ndarray:
     f = np.empty(X.shape[0], dtype=np.float64)
     _load().oracle_lens_density(_ptr(X), X.shape[0], X.shape[1], X.shape[1], float(r), _ptr(f))
     return f
+
+
+def density_at(X, queries, r: float) -> np.ndarray:
+    """The density filter (points within distance r, the point included) at
+    the given rows only."""
+    X = _f32(X)
+    qs = np.ascontiguousarray(queries, dtype=np.int32)
+    out = np.empty(max(qs.size, 1), dtype=np.float64)
+    rc = _load().oracle_density_at(_ptr(X), X.shape[0], X.shape[1], X.shape[1], _ptr(qs), qs.size, float(r),
+                                   _ptr(out))
+    if rc < 0:
+        raise ValueError("query row out of range")
+    return out[:qs.size]
 
 
 def lens_ecc_inf(X) -> np.ndarray:

@@ -143,6 +143,33 @@ void oracle_lens_density(const float* X, int64_t n, int32_t d, int64_t ld, doubl
     }
 }
 
+/* The density filter at the points queries[0..q) only (sampled parity at
+ * sizes where all n^2 pairs are too many): out[i] = f(x_queries[i]) with f
+ * as in oracle_lens_density. Returns -1 for a query outside [0, n). */
+int oracle_density_at(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* queries, int64_t q,
+                      double r, double* out)
+{
+    const double r2 = r * r;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < q; ++i) {
+        if (queries[i] < 0 || queries[i] >= n) { bad = 1; continue; }
+        const float* x = X + (int64_t)queries[i] * ld;
+        int64_t c = 0;
+        for (int64_t y = 0; y < n; ++y) {
+            const float* yv = X + y * ld;
+            double d2 = 0.0;
+            for (int32_t k = 0; k < d; ++k) {
+                double t = (double)x[k] - (double)yv[k];
+                d2 = d2 + t * t;
+            }
+            if (d2 <= r2) ++c;
+        }
+        out[i] = (double)c;
+    }
+    return bad ? -1 : 0;
+}
+
 /* L-infinity centrality, the other reading of §5's "L_infinity-norm" filter
  * computed from the pairwise distance matrix: the largest entry of x's row,
  * f(x) = max_{y in X} d(x, y) (eccentricity with exponent infinity). The

@@ -14,13 +14,14 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _capi
-from ._capi import (BF16, BF16X1, COVER_BALANCED, COVER_UNIFORM, FP32, LENS_COORD, LENS_ECC, LENS_L2, LENS_PCA,
+from ._capi import (BF16, BF16X1, COVER_BALANCED, COVER_UNIFORM, FP32, LENS_COORD, LENS_DENSITY, LENS_ECC, LENS_L2,
+                    LENS_LINF, LENS_PCA,
                     MapperError, MapperParams)
 
 __all__ = [
     "Context", "Cover", "Clusters", "Graph", "MapperError", "mapper_lens", "mapper_cover",
     "mapper_cluster", "mapper_nerve", "mapper_graph", "params", "LENS_L2", "LENS_COORD",
-    "LENS_PCA", "LENS_ECC", "COVER_UNIFORM", "COVER_BALANCED", "FP32", "BF16", "BF16X1", "mapper_dbscan_noalloc", "Server", "graph_footprint",
+    "LENS_PCA", "LENS_ECC", "LENS_LINF", "LENS_DENSITY", "COVER_UNIFORM", "COVER_BALANCED", "FP32", "BF16", "BF16X1", "mapper_dbscan_noalloc", "Server", "graph_footprint",
     "mapper_graph_sweep", "mapper_cover_subset", "mapper_nerve_from_nodes", "mapper_knn_distance",
 ]
 
@@ -57,6 +58,11 @@ class Context:
     def set_pass1_tile_n(self, tile_n: int) -> None:
         """0: autotuned (default); 128 or 256: fixed pass-1 product shape."""
         _capi.check(self._lib.mapper_set_pass1_tile_n(self.h, int(tile_n)), "mapper_set_pass1_tile_n")
+
+    def set_cross_screen(self, mode: int) -> None:
+        """Mixed tile pairs across two segments: 0 auto (default), 1 tensor
+        cores, 2 CUDA cores."""
+        _capi.check(self._lib.mapper_set_cross_screen(self.h, int(mode)), "mapper_set_cross_screen")
 
     def close(self) -> None:
         if getattr(self, "h", None) is not None and self.h.value:
@@ -162,7 +168,7 @@ class Graph(_Handle):
 
 
 def params(lens_kind, lens_arg, n_intervals, overlap, eps, min_pts, precision=FP32,
-           cover_kind=COVER_UNIFORM) -> MapperParams:
+           cover_kind=COVER_UNIFORM, lens_param=None) -> MapperParams:
     lens_kind, lens_arg = tuple(lens_kind), tuple(lens_arg)
     n_intervals, overlap = tuple(n_intervals), tuple(overlap)
     p = MapperParams()
@@ -176,6 +182,9 @@ def params(lens_kind, lens_arg, n_intervals, overlap, eps, min_pts, precision=FP
     p.min_pts = int(min_pts)
     p.precision = int(precision)
     p.cover_kind = int(cover_kind)
+    if lens_param is not None:
+        for j, r in enumerate(tuple(lens_param)):
+            p.lens_param[j] = float(r)
     return p
 
 
@@ -191,18 +200,21 @@ def _x_args(X):
     return _vp(X.data_ptr()), X.shape[0], X.shape[1], X.stride(0), X
 
 
-def mapper_lens(ctx: Context, X, kinds, args):
-    """Lens on the device: returns (lens [n, m] float64 CUDA tensor, pca)."""
+def mapper_lens(ctx: Context, X, kinds, args, lens_param=None, precision: int = BF16):
+    """Lens on the device: returns (lens [n, m] float64 CUDA tensor, pca).
+    lens_param[j]: the ball radius of a density lens; precision: the screen
+    of its neighbour counts."""
     torch = _torch()
     p, n, d, ld, _keep = _x_args(X)
     m = len(kinds)
     out = torch.empty((n, m), dtype=torch.float64, device=f"cuda:{ctx.device}")
     k = (ctypes.c_int32 * m)(*kinds)
     a = (ctypes.c_int32 * m)(*args)
+    lp = (ctypes.c_double * m)(*[float(r) for r in lens_param]) if lens_param is not None else None
     npca = d * (1 + max([arg for kind, arg in zip(kinds, args) if kind == LENS_PCA], default=-1))
     pca = np.empty(max(npca, 1), dtype=np.float64)
-    _capi.check(ctx._lib.mapper_lens(ctx.h, p, n, d, ld, m, k, a, _vp(out.data_ptr()),
-                                     _vp(pca.ctypes.data) if npca > d else None), "mapper_lens")
+    _capi.check(ctx._lib.mapper_lens_ex(ctx.h, p, n, d, ld, m, k, a, lp, int(precision), _vp(out.data_ptr()),
+                                        _vp(pca.ctypes.data) if npca > d else None), "mapper_lens")
     return out, (pca[:npca] if npca > d else None)
 
 

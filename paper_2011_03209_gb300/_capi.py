@@ -21,15 +21,16 @@ MAPPER_ENONFINITE = -5
 MAPPER_EINTERNAL = -6
 MAPPER_ENOTIMPL = -7
 
-LENS_L2, LENS_COORD, LENS_PCA, LENS_ECC = 0, 1, 2, 3
+LENS_L2, LENS_COORD, LENS_PCA, LENS_ECC, LENS_LINF, LENS_DENSITY = 0, 1, 2, 3, 4, 5
 COVER_UNIFORM, COVER_BALANCED = 0, 1
 FP32, BF16, BF16X1 = 0, 1, 2
 
 # every symbol include/mapper.h declares
 EXPORTS = (
     "mapper_create", "mapper_destroy", "mapper_set_stream", "mapper_set_timing", "mapper_set_pass1_tile_n",
+    "mapper_set_cross_screen",
     "mapper_cover_subset", "mapper_nerve_from_nodes", "mapper_cover_balanced", "mapper_knn_distance",
-    "mapper_lens", "mapper_cover", "mapper_cover_sizes", "mapper_cover_copy",
+    "mapper_lens", "mapper_lens_ex", "mapper_cover", "mapper_cover_sizes", "mapper_cover_copy",
     "mapper_cluster", "mapper_clusters_copy", "mapper_nerve", "mapper_graph",
     "mapper_graph_sizes", "mapper_graph_copy", "mapper_graph_lens", "mapper_graph_cover",
     "mapper_graph_clusters", "mapper_stats_get", "mapper_free", "mapper_strerror",
@@ -53,6 +54,7 @@ class MapperParams(ctypes.Structure):
         ("min_pts", ctypes.c_int32),
         ("precision", ctypes.c_int32),
         ("cover_kind", ctypes.c_int32),
+        ("lens_param", ctypes.c_double * 2),
     ]
 
 
@@ -89,6 +91,7 @@ class MapperStats(ctypes.Structure):
         ("union_pairs", ctypes.c_int64),
         ("fp64_pairs", ctypes.c_int64),
         ("pass1_tile_n", ctypes.c_int64),
+        ("tile_pairs_cross", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -138,10 +141,12 @@ def load(path: str | None = None):
             "mapper_set_stream": (ctypes.c_int, [P, P]),
             "mapper_set_timing": (ctypes.c_int, [P, ctypes.c_int]),
             "mapper_set_pass1_tile_n": (ctypes.c_int, [P, ctypes.c_int]),
+            "mapper_set_cross_screen": (ctypes.c_int, [P, ctypes.c_int]),
             "mapper_cover_subset": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.POINTER(P)]),
             "mapper_nerve_from_nodes": (ctypes.c_int, [P, ctypes.c_int64, ctypes.c_int64, P, P, P,
                                                        ctypes.POINTER(P)]),
             "mapper_lens": (ctypes.c_int, [P, P, i64, i32, i64, i32, P, P, P, P]),
+            "mapper_lens_ex": (ctypes.c_int, [P, P, i64, i32, i64, i32, P, P, P, i32, P, P]),
             "mapper_cover": (ctypes.c_int, [P, P, i64, i32, P, P, PP]),
             "mapper_cover_balanced": (ctypes.c_int, [P, P, i64, i32, P, P, PP]),
             "mapper_knn_distance": (ctypes.c_int, [P, P, i64, i32, i64, P, i64, i32, P]),

@@ -72,6 +72,7 @@ struct mapper_ctx {
     int num_sms = 152;
     std::map<uint64_t, int> pass1_tile_n;      // autotuner: (row pitch, products) -> N
     int pass1_forced = 0;                      // 128 or 256: fixed by the caller
+    int cross_mode = 0;                        // cross-segment pairs: 0 auto, 1 tensor cores, 2 CUDA cores
 };
 
 struct mapper_cover_t {
@@ -163,20 +164,26 @@ int check_x(const float* X, int64_t n, int32_t d, int64_t ld)
 }
 
 // ------------------------------------------------------------------- lens
+int run_density(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld, double r, int32_t precision,
+                double* f, int m, int j);
+
 int run_lens(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld, int32_t m,
-             const int32_t* kinds, const int32_t* args, double* lens_dev, Buf* pca_dev,
-             int64_t* n_pca)
+             const int32_t* kinds, const int32_t* args, const double* lens_param, int32_t precision,
+             double* lens_dev, Buf* pca_dev, int64_t* n_pca)
 {
     cudaStream_t s = ctx->stream->s;
     int K = 0;
     for (int j = 0; j < m; ++j) {
+        if (kinds[j] == MAPPER_LENS_DENSITY &&
+            (!lens_param || !(lens_param[j] > 0.0) || !std::isfinite(lens_param[j])))
+            return fail(MAPPER_EINVAL, "density lens radius must be finite and > 0");
         if (kinds[j] == MAPPER_LENS_COORD && (args[j] < 0 || args[j] >= d))
             return fail(MAPPER_EINVAL, "coordinate lens column out of range");
         if (kinds[j] == MAPPER_LENS_PCA) {
             if (args[j] < 0 || args[j] >= d) return fail(MAPPER_EINVAL, "PCA axis out of range");
             K = std::max(K, args[j] + 1);
         }
-        if (kinds[j] < 0 || kinds[j] > 3) return fail(MAPPER_EINVAL, "unknown lens kind");
+        if (kinds[j] < 0 || kinds[j] > MAPPER_LENS_DENSITY) return fail(MAPPER_EINVAL, "unknown lens kind");
     }
     *n_pca = 0;
     Buf status;
@@ -193,7 +200,12 @@ int run_lens(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld, 
             CK(lens_coord(X, n, ld, args[j], lens_dev, m, j, s), "lens_coord");
         else if (kinds[j] == MAPPER_LENS_ECC)
             CK(lens_ecc2(X, n, d, ld, lens_dev, m, j, s), "lens_ecc2");
-        else
+        else if (kinds[j] == MAPPER_LENS_LINF)
+            CK(lens_linf(X, n, d, ld, lens_dev, m, j, s), "lens_linf");
+        else if (kinds[j] == MAPPER_LENS_DENSITY) {
+            const int rc = run_density(ctx, X, n, d, ld, lens_param[j], precision, lens_dev, m, j);
+            if (rc) return rc;
+        } else
             CK(lens_project(X, n, d, ld, pca_dev->as<double>(),
                             pca_dev->as<double>() + (size_t)d * (1 + args[j]), lens_dev, m, j, s),
                "lens_project");
@@ -354,9 +366,17 @@ int tune_pass1(mapper_ctx* ctx, const PassArgs& a, const TcArgs& t, int64_t n_pa
 // tensor-core screen (BF16) and all others to the CUDA-core FP32 screen.
 // `layout` (optional): a tile layout of this cover built beforehand with
 // operands for this precision, shared by several radii (a sweep).
+// Where a counts-only run (the density filter) writes its neighbour counts:
+// f[point * m + j].
+struct CountsOut {
+    double* f;
+    int m, j;
+};
+
 int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
                 const std::shared_ptr<CoverData>& cov, double eps, int32_t min_pts, int32_t precision,
-                std::shared_ptr<ClusterData>* out, int* nonfinite_dev, const TileLayout* layout = nullptr)
+                std::shared_ptr<ClusterData>* out, int* nonfinite_dev, const TileLayout* layout = nullptr,
+                const CountsOut* counts_out = nullptr)
 {
     if (!(eps > 0.0) || !std::isfinite(eps)) return fail(MAPPER_EINVAL, "eps must be finite and > 0");
     if (min_pts < 1) return fail(MAPPER_EINVAL, "min_pts must be >= 1");
@@ -367,7 +387,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     const int64_t M = cov->M, E = cov->E;
     const int dp = (d + 31) / 32 * 32;
     const bool use_tc = precision != MAPPER_FP32;
-    const int cap = (min_pts >= 2 && min_pts - 1 <= 64) ? min_pts - 1 : 0;
+    const int cap = (!counts_out && min_pts >= 2 && min_pts - 1 <= 64) ? min_pts - 1 : 0;
     const double rows_est = (double)M + 128.0 * (double)E;
     const double est = rows_est * dp * (use_tc ? 8.0 : 4.0) + rows_est * (40.0 + 4.0 * cap);
     if (ctx->budget && est > (double)ctx->budget)
@@ -453,16 +473,23 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     a.root = root.as<int32_t>();
     a.border = border.as<unsigned long long>();
     a.stats = stats.as<unsigned long long>();
+    // Mixed tile pairs across two segments of one element have no common
+    // centre; when they are many (a cover element holding scattered points,
+    // whose tiles have wide spheres), they run on the tensor cores too, with
+    // a second operand set centred per element, instead of on CUDA cores.
+    const bool cross_tc = use_tc && PL.n[kListSimt] > 0 && ctx->cross_mode != 2 &&
+                          (ctx->cross_mode == 1 || PL.n[kListSimt] * 32 >= R);
     // tensor-core pairs in (a, b) order: pairs sharing tile A form the
     // groups of the pass-1 kernel, and consecutive groups, which run on
     // neighbouring SMs at the same time, share tiles in L2
-    if (PL.n[kListTC] > 1) {
+    for (int li : {(int)kListTC, (int)kListSimt}) {
+        if (PL.n[li] <= 1 || (li == kListSimt && !cross_tc)) continue;
         Buf tmp;
-        CK(tmp.alloc(sizeof(uint64_t) * PL.n[kListTC], s), "alloc");
-        uint64_t* keys = PL.list[kListTC].as<uint64_t>();
+        CK(tmp.alloc(sizeof(uint64_t) * PL.n[li], s), "alloc");
+        uint64_t* keys = PL.list[li].as<uint64_t>();
         const int tb = bits_for(L.T);
-        CK(radix_sort_u64(keys, tmp.as<uint64_t>(), PL.n[kListTC], 32, 32 + tb, s), "sort pairs");
-        CK(radix_sort_u64(keys, tmp.as<uint64_t>(), PL.n[kListTC], 0, tb, s), "sort pairs");
+        CK(radix_sort_u64(keys, tmp.as<uint64_t>(), PL.n[li], 32, 32 + tb, s), "sort pairs");
+        CK(radix_sort_u64(keys, tmp.as<uint64_t>(), PL.n[li], 0, tb, s), "sort pairs");
     }
     // pass 1 flags the screened tile pairs holding a neighbour pair; only
     // those can matter to the union pass
@@ -498,8 +525,22 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         t.err = tc_err.as<int>();
     }
 
+    TcArgs tx{};                                                  // the cross-segment operands
+    Buf xAh, xAl, xrn2, xrn;
+    if (cross_tc) {
+        if ((rc = cross_operands(L, X, ld, d, dp, E, &xAh, &xAl, &xrn2, &xrn, s))) return rc;
+        tx = t;
+        tx.Ah = xAh.p;
+        tx.Al = xAl.p;
+        tx.rn2 = xrn2.as<float>();
+        tx.rn = xrn.as<float>();
+    }
+    st.tile_pairs_cross = cross_tc ? PL.n[kListSimt] : 0;
     int tile_n = 0;
     if (use_tc && PL.n[kListTC] > 0 && (rc = tune_pass1(ctx, a_tc, t, PL.n[kListTC], R, cap, s, &tile_n)))
+        return rc;
+    if (use_tc && PL.n[kListTC] == 0 && cross_tc &&
+        (rc = tune_pass1(ctx, a_simt, tx, PL.n[kListSimt], R, cap, s, &tile_n)))
         return rc;
     pt.mark();                                                    // 1
     CK(allin_pass(1, a_in, PL.n[kListAllIn], s), "pass 1 all-in");
@@ -512,24 +553,48 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         cudaEvent_t* e;
         ~EvGuard() { for (int i = 0; i < 2; ++i) if (e[i]) cudaEventDestroy(e[i]); }
     } tev_guard{tev};
-    Buf groups, group_pos;
-    if (use_tc) {
-        TcArgs t1 = t;
-        t1.ev_begin = tev[0];
-        t1.ev_end = tev[1];
+    Buf groups, group_pos, xgroups, xgroup_pos;
+    // pass 1 on the tensor cores of one pair list (its events bracket the
+    // count kernels: both lists' launches when the cross list runs there)
+    auto tc_count = [&](const PassArgs& pa, const TcArgs& base, int64_t np, Buf& gr, Buf& gp, bool first,
+                        bool last) -> int {
+        TcArgs t1 = base;
+        t1.ev_begin = first ? tev[0] : nullptr;
+        t1.ev_end = last ? tev[1] : nullptr;
         if (tile_n == 256) {
-            if ((rc = tc_groups(a_tc.pairs, PL.n[kListTC], &groups, &group_pos, s))) return rc;
-            t1.groups = groups.as<int2>();
-            t1.n_groups = PL.n[kListTC];
-            t1.groups_dev = reinterpret_cast<const unsigned long long*>(group_pos.as<int64_t>() + PL.n[kListTC]);
+            int r2;
+            if ((r2 = tc_groups(pa.pairs, np, &gr, &gp, s))) return r2;
+            t1.groups = gr.as<int2>();
+            t1.n_groups = np;
+            t1.groups_dev = reinterpret_cast<const unsigned long long*>(gp.as<int64_t>() + np);
         }
-        if ((rc = tc_pass(1, a_tc, t1, PL.n[kListTC], s))) return rc;
+        return tc_pass(1, pa, t1, np, s);
+    };
+    if (use_tc) {
+        const bool x_last = cross_tc && PL.n[kListSimt] > 0;
+        if (PL.n[kListTC] > 0 && (rc = tc_count(a_tc, t, PL.n[kListTC], groups, group_pos, true, !x_last)))
+            return rc;
+        if (x_last && (rc = tc_count(a_simt, tx, PL.n[kListSimt], xgroups, xgroup_pos, PL.n[kListTC] == 0, true)))
+            return rc;
     }
     else CK(simt_pass(1, a_tc, PL.n[kListTC], s), "pass 1 tc list");
     if (!use_tc && tev[0]) CK(cudaEventRecord(tev[0], s), "event");
-    CK(simt_pass(1, a_simt, PL.n[kListSimt], s), "pass 1");
+    if (!cross_tc) CK(simt_pass(1, a_simt, PL.n[kListSimt], s), "pass 1");
     if (!use_tc && tev[1]) CK(cudaEventRecord(tev[1], s), "event");
     pt.mark();                                                    // 2
+    if (counts_out) {
+        // the counts are final after pass 1 (band pairs re-decided)
+        CK(counts_to_lens(L.row_slot.as<int32_t>(), a.row_pt, a.count, R, counts_out->f, counts_out->m,
+                          counts_out->j, s), "counts");
+        int h_nf = 0, h_err = 0;
+        CK(cudaMemcpyAsync(&h_nf, nf, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+        if (use_tc) CK(cudaMemcpyAsync(&h_err, tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+        CK(cudaStreamSynchronize(s), "sync");
+        if (h_nf) return fail(MAPPER_ENONFINITE, "X holds NaN or Inf");
+        if (h_err) return fail(MAPPER_ETIMEOUT, "a tensor-core pass gave up waiting on a barrier");
+        *out = c;
+        return MAPPER_OK;
+    }
     CK(core_flags(a.count, R, min_pts, core.as<uint8_t>(), a.parent, a.border, a.stats, s), "core");
     pt.mark();                                                    // 3
     CK(list_unions(a.count, a.nbr, cap, a.core, a.parent, a.row_pt, R, s), "list unions");
@@ -539,7 +604,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     // pair is kept only if its core rows are not all joined yet (from the
     // second round on when there are no lists), and pairs whose two sides are
     // each already one component only need one neighbour pair.
-    auto union_rounds = [&](const PassArgs& base, int64_t n, bool tc) -> int {
+    auto union_rounds = [&](const PassArgs& base, const TcArgs& tbase, int64_t n, bool tc) -> int {
         if (n == 0) return MAPPER_OK;
         // every count stays on the device: each launch covers the list's
         // capacity n and reads its length there, so the rounds need no host
@@ -575,7 +640,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
             ar.pair_hit = nullptr;
             int r2;
             if (tc) {
-                TcArgs t2 = t;
+                TcArgs t2 = tbase;
                 t2.n_dev = c_list;
                 if ((r2 = tc_pass(2, ar, t2, n, s))) return r2;
             } else {
@@ -585,10 +650,10 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         return MAPPER_OK;
     };
     if (use_tc) {
-        if ((rc = union_rounds(a_tc, PL.n[kListTC], true))) return rc;
-        if ((rc = union_rounds(a_simt, PL.n[kListSimt], false))) return rc;
+        if ((rc = union_rounds(a_tc, t, PL.n[kListTC], true))) return rc;
+        if ((rc = union_rounds(a_simt, tx, PL.n[kListSimt], cross_tc))) return rc;
     } else {
-        if ((rc = union_rounds(a_simt, PL.n[kListSimt], false))) return rc;
+        if ((rc = union_rounds(a_simt, t, PL.n[kListSimt], false))) return rc;
     }
     pt.mark();                                                    // 4
     CK(flatten(a.parent, a.core, R, root.as<int32_t>(), s), "flatten");
@@ -627,7 +692,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     st.union_pairs = (int64_t)h_stats[kStatUnion];
     st.pass1_tile_n = tile_n;
     st.n_rows = R;
-    if (tev[0] && PL.n[use_tc ? kListTC : kListSimt] > 0) {
+    if (tev[0] && (PL.n[use_tc ? kListTC : kListSimt] > 0 || cross_tc)) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, tev[0], tev[1]), "event time");
         st.ms_count_kernel = ms;
@@ -641,6 +706,30 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     }
     *out = c;
     return MAPPER_OK;
+}
+
+// Density filter (§4.1 names density among the derived filters; no estimator
+// is given): the number of points within distance r of each point, itself
+// included, i.e. pass 1 of DBSCAN(r, .) on one cover element holding the
+// whole cloud. Exact: the counts are those of the FP64 definition.
+int run_density(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld, double r, int32_t precision,
+                double* f, int m, int j)
+{
+    if (n > INT32_MAX) return fail(MAPPER_EINVAL, "density lens: more than 2^31 points");
+    cudaStream_t s = ctx->stream->s;
+    auto c = std::make_shared<CoverData>();
+    c->stream = ctx->stream;
+    c->m = 1;
+    c->n = n;
+    c->E = 1;
+    c->M = n;
+    CK(c->slot_point.alloc(sizeof(int32_t) * n, s), "alloc");
+    CK(c->slot_elem.alloc(sizeof(int32_t) * n, s), "alloc");
+    CK(whole_cloud_slots(n, c->slot_point.as<int32_t>(), c->slot_elem.as<int32_t>(), s), "slots");
+    c->h_elem_off = {0, n};
+    std::shared_ptr<ClusterData> cl;
+    const CountsOut co{f, m, j};
+    return run_cluster(ctx, X, n, d, ld, c, r, 1, precision, &cl, nullptr, nullptr, &co);
 }
 
 // ------------------------------------------------------------------ nerve
@@ -836,6 +925,14 @@ int mapper_set_timing(mapper_ctx* ctx, int enabled)
     return MAPPER_OK;
 }
 
+int mapper_set_cross_screen(mapper_ctx* ctx, int mode)
+{
+    if (!ctx) return fail(MAPPER_EINVAL, "null context");
+    if (mode < 0 || mode > 2) return fail(MAPPER_EINVAL, "mode must be 0, 1 or 2");
+    ctx->cross_mode = mode;
+    return MAPPER_OK;
+}
+
 int mapper_set_pass1_tile_n(mapper_ctx* ctx, int tile_n)
 {
     if (!ctx) return fail(MAPPER_EINVAL, "null context");
@@ -847,6 +944,13 @@ int mapper_set_pass1_tile_n(mapper_ctx* ctx, int tile_n)
 int mapper_lens(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, int64_t ld, int32_t m,
                 const int32_t* kinds, const int32_t* args, double* lens_dev, double* pca_out)
 {
+    return mapper_lens_ex(ctx, X_dev, n, d, ld, m, kinds, args, nullptr, MAPPER_BF16, lens_dev, pca_out);
+}
+
+int mapper_lens_ex(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, int64_t ld, int32_t m,
+                   const int32_t* kinds, const int32_t* args, const double* lens_param, int32_t precision,
+                   double* lens_dev, double* pca_out)
+{
     int rc = check_ctx(ctx);
     if (rc) return rc;
     if ((rc = check_x(X_dev, n, d, ld))) return rc;
@@ -857,7 +961,8 @@ int mapper_lens(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, int64
     CK(cudaMemsetAsync(flag.p, 0, sizeof(int), s), "memset");
     CK(check_finite(X_dev, n, d, ld, flag.as<int>(), s), "finite");
     int64_t n_pca = 0;
-    if ((rc = run_lens(ctx, X_dev, n, d, ld, m, kinds, args, lens_dev, &pca, &n_pca))) return rc;
+    if ((rc = run_lens(ctx, X_dev, n, d, ld, m, kinds, args, lens_param, precision, lens_dev, &pca, &n_pca)))
+        return rc;
     int h_nf = 0;
     CK(cudaMemcpyAsync(&h_nf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
     if (pca_out && n_pca)
@@ -1121,8 +1226,8 @@ int mapper_graph(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t 
         Xd = xdev.as<float>();
         ldd = d;
     }
-    if ((rc = run_lens(ctx, Xd, n, d, ldd, p->m, p->lens_kind, p->lens_arg, g->lens.as<double>(), &g->pca,
-                       &g->n_pca)))
+    if ((rc = run_lens(ctx, Xd, n, d, ldd, p->m, p->lens_kind, p->lens_arg, p->lens_param, p->precision,
+                       g->lens.as<double>(), &g->pca, &g->n_pca)))
         return rc;
     tm.mark();
     std::shared_ptr<CoverData> cov;
@@ -1170,14 +1275,21 @@ int mapper_graph_footprint(int64_t n, int32_t d, const mapper_params* p, size_t*
         E *= p->n_intervals[j];
     }
     const double dp = (double)((d + 31) / 32 * 32);
-    const double M = (double)n * mult;
-    const double rows = 1.1 * M + 128.0 * E;
-    const int cap = (p->min_pts >= 2 && p->min_pts - 1 <= 64) ? p->min_pts - 1 : 0;
     const bool tc = p->precision != MAPPER_FP32;
-    double b = rows * dp * (tc ? 8.0 : 4.0);                 // FP32 rows (+ BF16 hi, lo)
-    b += tc ? (double)n * dp * 4.0 : 0.0;                     // pivot assignment operands
-    b += rows * (29.0 + 4.0 * cap) + M * 40.0 + (double)n * 24.0 * p->m;
-    b += 3.0 * 8.0 * rows * rows / (128.0 * 128.0) / std::max(1.0, E);   // tile-pair lists
+    // scratch of one clustering of M memberships in E elements
+    auto cluster_bytes = [&](double M, double E, int cap) {
+        const double rows = 1.1 * M + 128.0 * E;
+        double b = rows * dp * (tc ? 12.0 : 4.0);                // FP32 rows (+ BF16 hi, lo, twice)
+        b += tc ? (double)n * dp * 4.0 : 0.0;                     // pivot assignment operands
+        b += rows * (29.0 + 4.0 * cap) + M * 40.0;
+        b += 3.0 * 8.0 * rows * rows / (128.0 * 128.0) / std::max(1.0, E);   // tile-pair lists
+        return b;
+    };
+    const int cap = (p->min_pts >= 2 && p->min_pts - 1 <= 64) ? p->min_pts - 1 : 0;
+    double b = cluster_bytes((double)n * mult, E, cap);
+    for (int j = 0; j < p->m; ++j)                            // a density lens: one element of n points
+        if (p->lens_kind[j] == MAPPER_LENS_DENSITY) b = std::max(b, cluster_bytes((double)n, 1.0, 0));
+    b += (double)n * 24.0 * p->m;
     *bytes = (size_t)(b * 1.1) + (size_t)(64u << 20);
     return MAPPER_OK;
 }
@@ -1213,7 +1325,8 @@ int mapper_graph_sweep(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, in
     CK(flag.alloc(sizeof(int), s), "alloc");
     CK(cudaMemsetAsync(flag.p, 0, sizeof(int), s), "memset");
     CK(lens.alloc(sizeof(double) * (size_t)n * p->m, s), "alloc lens");
-    if ((rc = run_lens(ctx, Xd, n, d, ldd, p->m, p->lens_kind, p->lens_arg, lens.as<double>(), &pca, &n_pca)))
+    if ((rc = run_lens(ctx, Xd, n, d, ldd, p->m, p->lens_kind, p->lens_arg, p->lens_param, p->precision,
+                       lens.as<double>(), &pca, &n_pca)))
         return rc;
     std::vector<std::unique_ptr<mapper_graph_t>> graphs(n_sweep);
     std::vector<char> done(n_sweep, 0);

@@ -71,6 +71,8 @@ int knn_distance(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t
                  int32_t k, double* out_dev, cudaStream_t s);
 cudaError_t lens_coord(const float* X, int64_t n, int64_t ld, int32_t col, double* f, int m,
                        int j, cudaStream_t s);
+cudaError_t lens_linf(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j,
+                      cudaStream_t s);
 cudaError_t lens_project(const float* X, int64_t n, int32_t d, int64_t ld, const double* mu,
                          const double* v, double* f, int m, int j, cudaStream_t s);
 // Principal axes: mu (d doubles) and K axes (K*d doubles), device outputs.
@@ -104,6 +106,9 @@ cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaS
 // (keys) with a scratch buffer of the same size.
 cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* tmp, int64_t n, int lo_bit, int hi_bit,
                            cudaStream_t s);
+
+// slots of a cover with one element holding every point (slot i = point i)
+cudaError_t whole_cloud_slots(int64_t n, int32_t* slot_point, int32_t* slot_elem, cudaStream_t s);
 
 // split sorted (element << 32 | point) keys into slot_point / slot_elem
 cudaError_t split_keys(const uint64_t* keys, int64_t M, int32_t* slot_point, int32_t* slot_elem,

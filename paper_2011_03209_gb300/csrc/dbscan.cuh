@@ -104,6 +104,10 @@ cudaError_t rows_to_slots(const int32_t* row_slot, const int32_t* row_pt, const 
                           int64_t* slot_label, uint8_t* slot_core, cudaStream_t s);
 cudaError_t element_offsets(const uint64_t* keys, int64_t M, int64_t E, int64_t* elem_off,
                             cudaStream_t s);
+// f[row_pt[row] * m + j] = count[row] for every non-padding row (the rows of
+// a one-element cover of the whole cloud: the density filter).
+cudaError_t counts_to_lens(const int32_t* row_slot, const int32_t* row_pt, const int32_t* count, int64_t R,
+                           double* f, int m, int j, cudaStream_t s);
 // Appends to `out` the tile pairs of `pairs` whose hit flag is set; *count
 // receives the size.
 cudaError_t select_hit(const int2* pairs, const uint8_t* hit, int64_t n, int2* out,
@@ -178,5 +182,10 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
 // are one non-outlier segment and use_tc, else to the CUDA-core list).
 int classify_pairs(const TileLayout& L, int dp, int64_t E, double eps, bool use_tc,
                    PairLists* P, cudaStream_t s);
+// Tensor-core operands for the CUDA-core list (tile pairs of one element, two
+// segments): every row centred on its element's centre, BF16 hi + lo, with
+// FP32 |a|^2 and |a| rounded up (R rows each).
+int cross_operands(const TileLayout& L, const float* X, int64_t ld, int d, int dp, int64_t E, Buf* Ah, Buf* Al,
+                   Buf* rn2, Buf* rn, cudaStream_t s);
 
 }  // namespace mgb

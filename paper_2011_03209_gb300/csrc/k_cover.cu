@@ -208,6 +208,22 @@ __global__ void split_keys_kernel(const uint64_t* __restrict__ keys, int64_t M,
 
 }  // namespace
 
+// The cover of one element holding every point: slot i is point i.
+__global__ void whole_cloud_slots_kernel(int64_t n, int32_t* __restrict__ slot_point, int32_t* __restrict__ slot_elem)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    slot_point[i] = (int32_t)i;
+    slot_elem[i] = 0;
+}
+
+cudaError_t whole_cloud_slots(int64_t n, int32_t* slot_point, int32_t* slot_elem, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    { whole_cloud_slots_kernel<<<div_up(n, 256), 256, 0, s>>>(n, slot_point, slot_elem); note_launch(); }
+    return cudaGetLastError();
+}
+
 cudaError_t split_keys(const uint64_t* keys, int64_t M, int32_t* slot_point, int32_t* slot_elem,
                        cudaStream_t s)
 {

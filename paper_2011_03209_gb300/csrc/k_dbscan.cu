@@ -559,6 +559,15 @@ __global__ void rows_to_slots_kernel(const int32_t* __restrict__ row_slot, const
     slot_core[slot] = c;
 }
 
+__global__ void counts_to_lens_kernel(const int32_t* __restrict__ row_slot, const int32_t* __restrict__ row_pt,
+                                      const int32_t* __restrict__ count, int64_t R, double* __restrict__ f, int m,
+                                      int j)
+{
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= R || row_slot[row] < 0) return;
+    f[(int64_t)row_pt[row] * m + j] = (double)count[row];
+}
+
 __global__ void elem_offsets_kernel(const uint64_t* __restrict__ keys, int64_t M, int64_t E,
                                     int64_t* __restrict__ elem_off)
 {
@@ -784,6 +793,14 @@ cudaError_t rows_to_slots(const int32_t* row_slot, const int32_t* row_pt, const 
     if (R == 0) return cudaSuccess;
     rows_to_slots_kernel<<<grid_for(R), 256, 0, s>>>(row_slot, row_pt, core, root, border, R, lab,
                                                      is_root, is_member, slot_label, slot_core);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t counts_to_lens(const int32_t* row_slot, const int32_t* row_pt, const int32_t* count, int64_t R,
+                           double* f, int m, int j, cudaStream_t s)
+{
+    counts_to_lens_kernel<<<grid_for(R), 256, 0, s>>>(row_slot, row_pt, count, R, f, m, j);
     note_launch();
     return cudaGetLastError();
 }

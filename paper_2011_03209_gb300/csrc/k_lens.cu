@@ -1,5 +1,7 @@
 // k_lens.cu -- filter (lens) kernels, "Mapper Interactive" §3 (filter
-// function f: X -> R or R^2) and §4.1 (L2 norm, a chosen column; PCA).
+// function f: X -> R or R^2) and §4.1 (L2 norm, a chosen column; PCA;
+// eccentricity), §5 (L-infinity norm). The density filter is a count pass of
+// the DBSCAN kernels (capi.cu).
 //
 // The projection lens sums in double, k ascending, with explicitly rounded
 // operations (never fused), so it is the exact IEEE result of the defining
@@ -271,6 +273,30 @@ __global__ void lens_coord_kernel(const float* __restrict__ X, int64_t n, int64_
     if (p < n) f[p * m + j] = (double)X[p * ld + col];
 }
 
+// L-infinity norm max_k |x_k|: one warp per row, lanes over columns, a
+// NaN-propagating maximum (exact: no arithmetic, FP32 values widen exactly).
+__global__ void __launch_bounds__(256) lens_linf_kernel(const float* __restrict__ X, int64_t n, int32_t d,
+                                                        int64_t ld, double* __restrict__ f, int m, int j)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w0; r < n; r += nw) {
+        const float* x = X + r * ld;
+        float mx = 0.f;
+        for (int k = lane; k < d; k += 32) {
+            const float v = fabsf(__ldg(x + k));
+            if (v > mx || v != v) mx = v;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const float v = __shfl_xor_sync(0xffffffffu, mx, o);
+            if (v > mx || v != v) mx = v;
+        }
+        if (lane == 0) f[r * m + j] = (double)mx;
+    }
+}
+
 __global__ void finite_kernel(const float* __restrict__ X, int64_t n, int32_t d, int64_t ld,
                               int* flag)
 {
@@ -507,6 +533,16 @@ cudaError_t lens_ecc2(const float* X, int64_t n, int32_t d, int64_t ld, double* 
     { col_lens_partial_kernel<<<kMeanBlocks, 256, 0, s>>>(f, n, m, j, vpart.as<double>()); note_launch(); }
     { ecc_finish_kernel<<<std::min(div_up(n, 256), 152 * 8), 256, 0, s>>>(f, n, m, j, vpart.as<double>(), kMeanBlocks);
       note_launch(); }
+    return cudaGetLastError();
+}
+
+// L-infinity norm filter (§5: the breast-cancer graphs filter by the
+// "L_infinity-norm"), read as the norm of the point: f(x) = max_k |x_k|.
+cudaError_t lens_linf(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>(div_up(n, 8), 152 * 8);
+    { lens_linf_kernel<<<blocks, 256, 0, s>>>(X, n, d, ld, f, m, j); note_launch(); }
     return cudaGetLastError();
 }
 

@@ -873,6 +873,45 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
     return MAPPER_OK;
 }
 
+// Operands for tile pairs of one element but two segments (two centres):
+// rows centred on their element's centre (the row-weighted mean of its tile
+// centres), split as by operand_kernel. |a| is larger than with the segment
+// centre, so the screen's error bound, and its band, are wider; pairs far
+// apart are still decided at once.
+int cross_operands(const TileLayout& L, const float* X, int64_t ld, int d, int dp, int64_t E, Buf* Ah, Buf* Al,
+                   Buf* rn2, Buf* rn, cudaStream_t s)
+{
+#define XK(expr)                                                                      \
+    do {                                                                              \
+        cudaError_t e_ = (expr);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            set_error(std::string("cross_operands: ") + cudaGetErrorString(e_));      \
+            return e_ == cudaErrorMemoryAllocation ? MAPPER_ENOMEM : MAPPER_ECUDA;    \
+        }                                                                             \
+    } while (0)
+    const int64_t R = L.R, T = L.T;
+    Buf etile_off, ecent;
+    XK(etile_off.alloc(sizeof(int64_t) * (E + 1), s));
+    XK(ecent.alloc(sizeof(float) * (size_t)E * dp, s));
+    XK(Ah->alloc(sizeof(__nv_bfloat16) * (size_t)R * dp, s));
+    XK(Al->alloc(sizeof(__nv_bfloat16) * (size_t)R * dp, s));
+    XK(rn2->alloc(sizeof(float) * R, s));
+    XK(rn->alloc(sizeof(float) * R, s));
+    elem_tiles_kernel<<<grid_for(E + 1), 256, 0, s>>>(L.tile_elem.as<int32_t>(), T, E, etile_off.as<int64_t>());
+    seg_cent_kernel<<<(unsigned)E, 1024, 0, s>>>(L.tile_cent.as<float>(), L.tile_n.as<int32_t>(),
+                                               etile_off.as<int64_t>(), dp, ecent.as<float>());
+    const float norm_infl = 1.0f + (float)(dp / 32 + 16) * 5.9604645e-8f;
+    const bool xvec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
+    operand_kernel<<<(unsigned)T, 256, 0, s>>>(L.G.as<float>(), X, ld, xvec, L.row_pt.as<int32_t>(), d, dp,
+                                               L.tile_n.as<int32_t>(), L.tile_elem.as<int32_t>(), ecent.as<float>(),
+                                               Ah->as<__nv_bfloat16>(), Al->as<__nv_bfloat16>(), rn2->as<float>(),
+                                               rn->as<float>(), norm_infl);
+    note_launch(3);
+    XK(cudaGetLastError());
+    return MAPPER_OK;
+#undef XK
+}
+
 int classify_pairs(const TileLayout& L, int dp, int64_t E, double eps, bool use_tc, PairLists* P,
                    cudaStream_t s)
 {

@@ -38,18 +38,19 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version_and_strings(lib):
-    assert lib.mapper_abi_version() == 3
+    assert lib.mapper_abi_version() == 4
     assert lib.mapper_strerror(0) == b"ok"
     assert lib.mapper_strerror(-4) == b"device wait timed out"
 
 
 def test_struct_layouts_match_header():
     from paper_2011_03209_gb300 import _capi
-    # mapper_params: 7 int32, pad to 8, 2 doubles, double, 3 int32, pad to 8
-    assert ctypes.sizeof(_capi.MapperParams) == 72
+    # mapper_params: 7 int32, pad to 8, 2 doubles, double, 3 int32, pad to 8, 2 doubles
+    assert ctypes.sizeof(_capi.MapperParams) == 88
     assert _capi.MapperParams.overlap.offset == 32
     assert _capi.MapperParams.cover_kind.offset == 64
-    assert ctypes.sizeof(_capi.MapperStats) == 8 * 33
+    assert _capi.MapperParams.lens_param.offset == 72
+    assert ctypes.sizeof(_capi.MapperStats) == 8 * 34
 
 
 def test_null_and_bad_arguments_are_rejected_without_a_gpu(lib):

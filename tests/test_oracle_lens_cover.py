@@ -97,6 +97,10 @@ def test_density_lens_against_kdtree_and_pair_count():
     pairs = int((spatial.distance.pdist(Y64, "sqeuclidean") <= r2).sum())
     assert int(f.sum()) == Y.shape[0] + 2 * pairs
     assert f.min() >= 1.0 and f.max() > 2.0
+    rows = np.array([0, 599, 17, 17, 300])
+    assert np.array_equal(oracle.density_at(Y, rows, np.sqrt(r2)), ref[rows].astype(np.float64))
+    with pytest.raises(ValueError):
+        oracle.density_at(Y, [600], 1.0)
 
 
 def test_ecc_inf_lens_closed_forms_and_scipy():
