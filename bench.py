@@ -458,8 +458,9 @@ def run_knn(args):
         torch.cuda.synchronize()
         clocks = sampler.stop()
     ms = start.elapsed_time(end) / args.steps
-    # FP32 screen: two passes of 3 d flops (sub, FMA) per (query, row) pair
-    tflops = 2 * 3 * w.d * float(q.size) * w.n / (ms * 1e-3) / 1e12
+    # FP32 screen: 3 d flops (sub, FMA) per (query, row) pair, one pass (the
+    # exact refinement of at most 16 candidates per query is not counted)
+    tflops = 3 * w.d * float(q.size) * w.n / (ms * 1e-3) / 1e12
     peak = 152 * 128 * 2 * 2070e6 / 1e12
     cpu = None
     if not args.no_cpu_baseline:
@@ -478,7 +479,8 @@ def run_knn(args):
                                         "k": k},
         "queries_per_s": q.size / (ms * 1e-3),
         "roofline": {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
-                     "traffic": None, "kernel": "knn_kernel<0,1>: FP32 screen, 3 d flops per pair per pass",
+                     "traffic": None, "kernel": "knn_screen_kernel: register-tiled FP32 screen, 3 d flops per (query, point) "
+                               "pair (sub + FMA: at most 0.75 of the FMA peak)",
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max clock)"},
         "cpu_baseline": cpu, "clocks": clocks,
     }))

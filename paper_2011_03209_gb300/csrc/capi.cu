@@ -1186,7 +1186,7 @@ int mapper_knn_distance(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t 
     CK(qd.alloc(sizeof(int32_t) * q, s), "alloc");
     CK(od.alloc(sizeof(double) * q, s), "alloc");
     CK(cudaMemcpyAsync(qd.p, hq.data(), sizeof(int32_t) * q, cudaMemcpyHostToDevice, s), "copy");
-    if ((rc = knn_distance(X_dev, n, d, ld, qd.as<int32_t>(), q, k, od.as<double>(), s))) return rc;
+    if ((rc = knn_distance(X_dev, n, d, ld, qd.as<int32_t>(), q, k, od.as<double>(), ctx->num_sms, s))) return rc;
     return copy_out(out, od.p, sizeof(double) * q, !is_host_pointer(out), s);
 }
 

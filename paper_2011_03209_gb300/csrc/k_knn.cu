@@ -16,8 +16,16 @@
 //      of those are the k smallest overall: the k points behind T are within
 //      (T + tiny) / (1 - eta) exactly, so the true k-th D* is too, and a point
 //      with true value <= D* has an FP32 value <= (1 + eta) D* + tiny <= B.
-// One warp per query, 16 queries per CTA, 32 points per shared-memory tile
-// (one per lane, rows padded against bank conflicts).
+// Pass A runs register-tiled: a CTA screens 64 queries against tiles of 128
+// points (each thread 4 x 8 distances, columns staged 64 at a time in shared
+// memory), CTAs split the points into chunks, and every (query, chunk, part)
+// keeps its 16 smallest values with their points; a part is a 32-point slice
+// of each tile. The union of those lists holds the 16 smallest values of the
+// whole cloud, so when the 16th of them exceeds B every point below B is in
+// it, and pass B reduces to the exact distances of at most 16 candidates per
+// query. Queries whose 16th value is within B (many near ties, or k = 16 with
+// a tie at the k-th value) take the two streaming passes below: one warp per
+// query, 16 queries per CTA, 32 points per shared-memory tile.
 #include <cfloat>
 #include <cmath>
 
@@ -82,9 +90,12 @@ __device__ __forceinline__ double exact_sqdist_rows(const float* __restrict__ x,
     return s;
 }
 
+// The fallback streaming passes over the queries at positions pos[0 .. q)
+// of the query list (all of them when pos is null).
 template <int PASS>
 __global__ void __launch_bounds__(32 * kQ, 1) knn_kernel(const float* __restrict__ X, int64_t n, int d, int64_t ld,
-                                                          int dp, const int32_t* __restrict__ queries, int64_t q,
+                                                          int dp, const int32_t* __restrict__ queries,
+                                                          const int32_t* __restrict__ pos, int64_t q,
                                                           int k, float eta_lo, float eta_hi, float tiny,
                                                           float* __restrict__ thr, double* __restrict__ out)
 {
@@ -94,7 +105,8 @@ __global__ void __launch_bounds__(32 * kQ, 1) knn_kernel(const float* __restrict
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t qi = (int64_t)blockIdx.x * kQ + w;
     const bool live = qi < q;
-    const int64_t qp = live ? queries[qi] : 0;
+    const int64_t qpos = live ? (pos ? pos[qi] : qi) : 0;
+    const int64_t qp = live ? queries[qpos] : 0;
     for (int c = lane; c < dp; c += 32) qrow[w * dp + c] = (live && c < d) ? X[qp * ld + c] : 0.f;
     float bound = 0.f;
     if (PASS == 1 && live) {
@@ -141,14 +153,222 @@ __global__ void __launch_bounds__(32 * kQ, 1) knn_kernel(const float* __restrict
         if (lane == 0) thr[qi] = t;
     } else {
         const double t = warp_kth(topd, k, lane);
-        if (lane == 0) out[qi] = __dsqrt_rn(t);
+        if (lane == 0) out[qpos] = __dsqrt_rn(t);
     }
+}
+
+// ------------------------------------------------------ register-tiled pass A
+constexpr int kTQ = 64;                          // queries per CTA
+constexpr int kTP = 128;                         // points per tile
+constexpr int kKC = 64;                          // columns per staged chunk
+constexpr int kL = kKMax;                        // candidates per list
+constexpr int kParts = kTP / 32;                 // lists per query and CTA
+constexpr int kDS = kParts * 33;                 // distance-tile row stride (floats)
+constexpr int kPS = (kTP * (kKC + 1) > kTQ * kDS) ? kTP * (kKC + 1) : kTQ * kDS;
+
+// acc_i += (a - b_i)^2 for i = 0, 1 with the packed FP32 pair instructions:
+// each lane rounds as the scalar subtract and FMA do.
+__device__ __forceinline__ void sqdiff2(float& acc0, float& acc1, float a, float b0, float b1)
+{
+    asm("{.reg .b64 A, B, T, S;\n\t"
+        "mov.b64 A, {%2, %2};\n\t"
+        "mov.b64 B, {%3, %4};\n\t"
+        "sub.rn.f32x2 T, A, B;\n\t"
+        "mov.b64 S, {%0, %1};\n\t"
+        "fma.rn.f32x2 S, T, T, S;\n\t"
+        "mov.b64 {%0, %1}, S;}\n"
+        : "+f"(acc0), "+f"(acc1) : "f"(a), "f"(b0), "f"(b1));
+}
+
+// Insert (v, j) into an ascending list of kL entries (v below the last).
+__device__ __forceinline__ void list_insert(float (&lv)[kL], int (&li)[kL], float v, int j)
+{
+#pragma unroll
+    for (int i = kL - 1; i > 0; --i) {
+        const bool sh = v < lv[i - 1];
+        const bool here = !sh && v < lv[i];
+        lv[i] = sh ? lv[i - 1] : (here ? v : lv[i]);
+        li[i] = sh ? li[i - 1] : (here ? j : li[i]);
+    }
+    if (v < lv[0]) { lv[0] = v; li[0] = j; }
+}
+
+// Grid (query tiles, point chunks). Thread (tq, tp) = (tid / 16, tid % 16)
+// computes queries tq + 16 u (u < 4) against points tp + 16 v (v < 8) of each
+// tile: FP32 sums of squared differences, columns ascending (the same chain
+// as the fallback pass, so the same error bound), two points per packed
+// instruction. The tile of distances then
+// goes through shared memory to thread (qq, part) = (tid / 4, tid % 4), which
+// keeps the kL smallest of query qq over points 32 part .. 32 part + 31 of
+// every tile of the chunk.
+__global__ void __launch_bounds__(256, 2) knn_screen_kernel(const float* __restrict__ X, int64_t n, int d,
+                                                             int64_t ld, bool xvec,
+                                                             const int32_t* __restrict__ queries, int64_t q,
+                                                             int64_t chunk, float* __restrict__ cand_v,
+                                                             int32_t* __restrict__ cand_i)
+{
+    __shared__ float qs[kTQ][kKC + 1];
+    __shared__ __align__(16) float ps[kPS];
+    const int tid = threadIdx.x, tq = tid >> 4, tp = tid & 15;
+    const int qq = tid >> 2, part = tid & 3;
+    const int64_t q0 = (int64_t)blockIdx.x * kTQ;
+    const int64_t p_begin = (int64_t)blockIdx.y * chunk;
+    const int64_t p_end = p_begin + chunk < n ? p_begin + chunk : n;
+    float lv[kL];
+    int li[kL];
+#pragma unroll
+    for (int i = 0; i < kL; ++i) { lv[i] = INFINITY; li[i] = -1; }
+    for (int64_t p0 = p_begin; p0 < p_end; p0 += kTP) {
+        float acc[4][8];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+        for (int k0 = 0; k0 < d; k0 += kKC) {
+            __syncthreads();
+            // queries: thread = (row tid / 64 + 4 r, column tid % 64)
+            {
+                const int c = tid & 63;
+                for (int r = tid >> 6; r < kTQ; r += 4) {
+                    const int64_t qi = q0 + r;
+                    float x = 0.f;
+                    if (qi < q && k0 + c < d) x = __ldg(X + (int64_t)queries[qi] * ld + k0 + c);
+                    qs[r][c] = x;
+                }
+            }
+            // points: 16 float4 per row chunk
+            {
+                const int c4 = (tid & 15) * 4;
+                for (int r = tid >> 4; r < kTP; r += 16) {
+                    const int64_t j = p0 + r;
+                    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (j < p_end) {
+                        const float* src = X + j * ld + k0 + c4;
+                        if (xvec && k0 + c4 + 3 < d) {
+                            x = __ldg(reinterpret_cast<const float4*>(src));
+                        } else {
+                            if (k0 + c4 < d) x.x = __ldg(src);
+                            if (k0 + c4 + 1 < d) x.y = __ldg(src + 1);
+                            if (k0 + c4 + 2 < d) x.z = __ldg(src + 2);
+                            if (k0 + c4 + 3 < d) x.w = __ldg(src + 3);
+                        }
+                    }
+                    float* dst = ps + r * (kKC + 1) + c4;
+                    dst[0] = x.x; dst[1] = x.y; dst[2] = x.z; dst[3] = x.w;
+                }
+            }
+            __syncthreads();
+            const int kc = d - k0 < kKC ? d - k0 : kKC;
+#pragma unroll 4
+            for (int c = 0; c < kc; ++c) {
+                float a[4], b[8];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) a[u] = qs[tq + 16 * u][c];
+#pragma unroll
+                for (int v = 0; v < 8; ++v) b[v] = ps[(tp + 16 * v) * (kKC + 1) + c];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 8; v += 2) sqdiff2(acc[u][v], acc[u][v + 1], a[u], b[v], b[v + 1]);
+            }
+        }
+        __syncthreads();
+        // distance tile: row r (query), part p (32 points), column c at
+        // r * kDS + 33 p + c; +inf past the chunk's end
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                const int col = tp + 16 * v;
+                ps[(tq + 16 * u) * kDS + (col >> 5) * 33 + (col & 31)] =
+                    p0 + col < p_end ? acc[u][v] : INFINITY;
+            }
+        __syncthreads();
+        const float* row = ps + qq * kDS + part * 33;
+#pragma unroll 4
+        for (int c = 0; c < 32; ++c) {
+            const float v = row[c];
+            if (v < lv[kL - 1]) list_insert(lv, li, v, (int)(p0 + part * 32 + c));
+        }
+    }
+    const int64_t qi = q0 + qq;
+    if (qi >= q) return;
+    const int64_t base = ((qi * gridDim.y + blockIdx.y) * kParts + part) * kL;
+#pragma unroll
+    for (int i = 0; i < kL; ++i) {
+        cand_v[base + i] = lv[i];
+        cand_i[base + i] = li[i];
+    }
+}
+
+// One warp per query: the kL smallest of the query's lists (each lane keeps
+// the smallest of a strided share, then kL rounds of a warp minimum), the
+// bound B from the k-th of them, and, when the kL-th exceeds B, the exact
+// FP64 distances of the candidates below B and their k-th smallest. Else the
+// query goes to the fallback list.
+__global__ void __launch_bounds__(256) knn_merge_kernel(const float* __restrict__ X, int d, int64_t ld,
+                                                        const int32_t* __restrict__ queries, int64_t q,
+                                                        int n_lists, const float* __restrict__ cand_v,
+                                                        const int32_t* __restrict__ cand_i, int k, float eta_lo,
+                                                        float eta_hi, float tiny, double* __restrict__ out,
+                                                        int32_t* __restrict__ redo,
+                                                        unsigned long long* __restrict__ n_redo)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t qi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (qi >= q) return;                         // whole warp
+    float lv[kL];
+    int li[kL];
+#pragma unroll
+    for (int i = 0; i < kL; ++i) { lv[i] = INFINITY; li[i] = -1; }
+    const int64_t total = (int64_t)n_lists * kL;
+    const float* cv = cand_v + qi * total;
+    const int32_t* ci = cand_i + qi * total;
+    for (int64_t e = lane; e < total; e += 32) {
+        const float v = cv[e];
+        if (v < lv[kL - 1]) list_insert(lv, li, v, ci[e]);
+    }
+    // kL rounds: lane r keeps the r-th smallest (value, point)
+    float my_v = INFINITY;
+    int my_i = -1;
+    for (int r = 0; r < kL; ++r) {
+        float m = lv[0];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const unsigned owners = __ballot_sync(0xffffffffu, lv[0] == m);
+        const int src = __ffs(owners) - 1;
+        const int j = __shfl_sync(0xffffffffu, li[0], src);
+        if (lane == src) {
+#pragma unroll
+            for (int i = 0; i + 1 < kL; ++i) { lv[i] = lv[i + 1]; li[i] = li[i + 1]; }
+            lv[kL - 1] = INFINITY;
+            li[kL - 1] = -1;
+        }
+        if (lane == r) { my_v = m; my_i = j; }
+    }
+    const float t = __shfl_sync(0xffffffffu, my_v, k - 1);
+    const float last = __shfl_sync(0xffffffffu, my_v, kL - 1);
+    const float bound = __fadd_ru(__fdiv_ru(__fmul_ru(__fadd_ru(t, tiny), eta_hi), eta_lo), tiny);
+    if (!(last > bound)) {
+        if (lane == 0) redo[atomicAdd(n_redo, 1ull)] = (int32_t)qi;
+        return;
+    }
+    const bool cand = lane < kL && my_v <= bound && my_i >= 0;
+    double e = INFINITY;
+    if (cand) e = exact_sqdist_rows(X + (int64_t)queries[qi] * ld, X + (int64_t)my_i * ld, d);
+    // rank among the candidates (ties by lane)
+    int rank = 0;
+    for (int j = 0; j < kL; ++j) {
+        const double o = __shfl_sync(0xffffffffu, e, j);
+        rank += (o < e || (o == e && j < lane)) ? 1 : 0;
+    }
+    if (cand && rank == k - 1) out[qi] = __dsqrt_rn(e);
 }
 
 }  // namespace
 
 int knn_distance(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* queries_dev, int64_t q,
-                 int32_t k, double* out_dev, cudaStream_t s)
+                 int32_t k, double* out_dev, int num_sms, cudaStream_t s)
 {
     if (q == 0) return MAPPER_OK;
     if (k < 1 || k > kKMax || k > n) {
@@ -169,17 +389,49 @@ int knn_distance(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t
     if ((double)eta_hi < 1.0 + eta) eta_hi = std::nextafter(eta_hi, INFINITY);
     if ((double)eta_lo > 1.0 - eta) eta_lo = std::nextafter(eta_lo, 0.f);
     const float tiny = (float)(3.0 * (d + 2) * std::ldexp(1.0, -149)) + FLT_TRUE_MIN;
-    Buf thr;
-    cudaError_t e = thr.alloc(sizeof(float) * q, s);
+    // pass A: point chunks so that the grid fills the GPU a few times over
+    const int64_t qt = div_up(q, kTQ);
+    const int64_t want = 8LL * (num_sms > 0 ? num_sms : 152);
+    int64_t S = std::max<int64_t>(1, std::min<int64_t>(div_up(want, qt), div_up(n, 8 * kTP)));
+    S = std::min<int64_t>(S, 65535);
+    const int64_t chunk = div_up(div_up(n, S), kTP) * kTP;
+    S = div_up(n, chunk);
+    Buf cv, ci, redo, n_redo;
+    const size_t nc = (size_t)q * S * kParts * kL;
+    cudaError_t e = cv.alloc(sizeof(float) * nc, s);
+    if (e == cudaSuccess) e = ci.alloc(sizeof(int32_t) * nc, s);
+    if (e == cudaSuccess) e = redo.alloc(sizeof(int32_t) * q, s);
+    if (e == cudaSuccess) e = n_redo.alloc(sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n_redo.p, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ENOMEM; }
-    const unsigned grid = (unsigned)div_up(q, kQ);
+    const bool xvec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
+    knn_screen_kernel<<<dim3((unsigned)qt, (unsigned)S), 256, 0, s>>>(X, n, d, ld, xvec, queries_dev, q, chunk,
+                                                                      cv.as<float>(), ci.as<int32_t>());
+    knn_merge_kernel<<<(unsigned)div_up(q, 8), 256, 0, s>>>(X, d, ld, queries_dev, q, (int)(S * kParts),
+                                                            cv.as<float>(), ci.as<int32_t>(), k, eta_lo, eta_hi,
+                                                            tiny, out_dev, redo.as<int32_t>(),
+                                                            n_redo.as<unsigned long long>());
+    note_launch(2);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ECUDA; }
+    unsigned long long h_redo = 0;
+    e = cudaMemcpyAsync(&h_redo, n_redo.p, sizeof(h_redo), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ECUDA; }
+    if (h_redo == 0) return MAPPER_OK;
+    // the two streaming passes for the queries whose band reaches the 16th value
+    const int64_t qr = (int64_t)h_redo;
+    Buf thr;
+    e = thr.alloc(sizeof(float) * qr, s);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ENOMEM; }
+    const unsigned grid = (unsigned)div_up(qr, kQ);
     e = cudaFuncSetAttribute(knn_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(knn_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ECUDA; }
-    knn_kernel<0><<<grid, 32 * kQ, smem, s>>>(X, n, d, ld, dp, queries_dev, q, k, eta_lo, eta_hi, tiny,
-                                               thr.as<float>(), out_dev);
-    knn_kernel<1><<<grid, 32 * kQ, smem, s>>>(X, n, d, ld, dp, queries_dev, q, k, eta_lo, eta_hi, tiny,
-                                               thr.as<float>(), out_dev);
+    knn_kernel<0><<<grid, 32 * kQ, smem, s>>>(X, n, d, ld, dp, queries_dev, redo.as<int32_t>(), qr, k, eta_lo,
+                                               eta_hi, tiny, thr.as<float>(), out_dev);
+    knn_kernel<1><<<grid, 32 * kQ, smem, s>>>(X, n, d, ld, dp, queries_dev, redo.as<int32_t>(), qr, k, eta_lo,
+                                               eta_hi, tiny, thr.as<float>(), out_dev);
     note_launch(2);
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ECUDA; }

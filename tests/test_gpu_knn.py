@@ -76,3 +76,30 @@ def test_knn_distance_rejects_bad_input(ctx):
     Y[3, 2] = np.nan
     with pytest.raises(mg.MapperError):
         mg.mapper_knn_distance(ctx, torch.from_numpy(Y).to("cuda:0"), [0], 3)
+
+
+@pytest.mark.parametrize("k", [1, 5, 16])
+def test_knn_distance_many_chunks(ctx, k):
+    """150k points: the screen splits the points into many chunks per query
+    tile, each with its own candidate lists; the merged result is exact."""
+    X = synth.gaussian_mixture(150_000, 24, 12, seed=97, centre_box=5.0, std_lo=0.4, std_hi=1.1,
+                               anisotropic=True, noise_frac=0.05)
+    rng = np.random.default_rng(k)
+    q = rng.integers(0, X.shape[0], size=200).astype(np.int32)
+    got = mg.mapper_knn_distance(ctx, torch.from_numpy(X).to("cuda:0"), q, k)
+    assert np.array_equal(got, oracle.knn_distance(X, q, k))
+
+
+def test_knn_distance_strided_rows_and_ties(ctx):
+    """Rows with a pitch that is not a multiple of 4 floats (scalar loads) and
+    a cloud of many exact duplicates (ties at the k-th value send queries to
+    the two streaming passes)."""
+    base = synth.tiny_random(3000, 13, 11, scale=2.0, dup_frac=0.6)
+    base[100:140] = base[100]                            # 40 copies: the 16 smallest values all 0
+    X = np.concatenate([base, base[:1500]])              # every point at least twice, many more
+    wide = np.zeros((X.shape[0], 16), dtype=np.float32)
+    wide[:, :13] = X
+    Xd = torch.from_numpy(wide).to("cuda:0")[:, :13]
+    q = np.r_[np.arange(0, X.shape[0], 7), np.arange(100, 140)].astype(np.int32)
+    for k in (2, 3, 16):
+        assert np.array_equal(mg.mapper_knn_distance(ctx, Xd, q, k), oracle.knn_distance(X, q, k)), k
