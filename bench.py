@@ -30,7 +30,7 @@ if ROOT not in sys.path:
 from paper_2011_03209_gb300 import synth  # noqa: E402
 
 LENS_NAMES = {"l2": "L2", "ecc": "eccentricity (exponent 2)", "linf": "L-infinity norm",
-              "density": "density (points within eps)"}
+              "density": "density (points within eps)", "eccinf": "L-infinity centrality (max distance)"}
 METRIC = "mapper graph ms (1M x 256, exact graph)"
 GPU_FP32_LANES = 128                 # FP32 lanes per SM (Blackwell)
 
@@ -198,7 +198,7 @@ def run_ours(args):
     ctx = mg.Context(local, stream=stream)
     ctx.set_timing(True)
     lens_kind = {"l2": w.lens_kind, "ecc": (mg.LENS_ECC,), "linf": (mg.LENS_LINF,),
-                 "density": (mg.LENS_DENSITY,)}[args.lens]
+                 "density": (mg.LENS_DENSITY,), "eccinf": (mg.LENS_ECC_INF,)}[args.lens]
     cover_kind = mg.COVER_BALANCED if args.cover == "balanced" else mg.COVER_UNIFORM
     prm = mg.params(lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, prec, cover_kind,
                     lens_param=(w.eps,))
@@ -294,7 +294,9 @@ def run_ours(args):
                    "lens": LENS_NAMES[args.lens], "cover": args.cover,
                    "n_intervals": w.n_intervals[0], "overlap": w.overlap[0], "eps": w.eps,
                    "min_pts": w.min_pts, "precision": args.precision,
-                   "l2_flush": "inputs larger than L2 (1 GB point cloud read every step)",
+                   "l2_flush": (f"inputs larger than L2 ({w.X.nbytes / 1e9:.2f} GB point cloud read every step)"
+                                if w.X.nbytes > 129e6 else
+                                f"none: the {w.X.nbytes / 1e6:.0f} MB point cloud fits in L2 (profiling size)"),
                    "parallelism": f"replicas x{world}"},
         "eps_pair_tflops": eps_pair_flops / (pass1_ms * 1e-3) / 1e12,
         "count_kernel_ms": kms,

@@ -80,10 +80,14 @@ typedef enum mapper_lens_kind {
                                 |x - y|^2) (§3 "eccentricity", §4.1 derived filters) */
     MAPPER_LENS_LINF = 4,    /* L-infinity norm max_k |x_k| (§5: the breast-cancer mapper
                                 graphs filter by the "L_infinity-norm") */
-    MAPPER_LENS_DENSITY = 5  /* density (§4.1 derived filters): the number of points within
+    MAPPER_LENS_DENSITY = 5, /* density (§4.1 derived filters): the number of points within
                                 distance r of x, x included, r = lens_param[j]; exact counts
                                 (the pass-1 neighbour counts of DBSCAN(r, .) on the whole
                                 cloud), returned as doubles */
+    MAPPER_LENS_ECC_INF = 6  /* L-infinity centrality max_y |x - y| (§5 filters by the
+                                "L_infinity-norm" of the pairwise distance matrix;
+                                eccentricity with exponent infinity): the FP64 distance of the
+                                defining expression, exact; O(n^2 d) */
 } mapper_lens_kind;
 
 /* Precision of the eps-neighbourhood screen. Every pair whose screened
@@ -277,8 +281,8 @@ int mapper_nerve_from_nodes(mapper_ctx* ctx, int64_t n_points, int64_t n_nodes, 
  * value is the FP64 distance of the defining expression (double sum of
  * squared differences, k ascending, sqrt), found exactly through an FP32
  * screen. X: device memory. queries (q int32) and out (q doubles): host or
- * device memory, out filled before the call returns. k in [1, min(16, n)],
- * d <= 1184; MAPPER_EINVAL otherwise, MAPPER_ENONFINITE if X holds NaN/Inf. */
+ * device memory, out filled before the call returns. k in [1, min(16, n)];
+ * MAPPER_EINVAL otherwise, MAPPER_ENONFINITE if X holds NaN/Inf. */
 int mapper_knn_distance(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, int64_t ld,
                         const int32_t* queries, int64_t q, int32_t k, double* out);
 

@@ -14,14 +14,14 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _capi
-from ._capi import (BF16, BF16X1, COVER_BALANCED, COVER_UNIFORM, FP32, LENS_COORD, LENS_DENSITY, LENS_ECC, LENS_L2,
-                    LENS_LINF, LENS_PCA,
+from ._capi import (BF16, BF16X1, COVER_BALANCED, COVER_UNIFORM, FP32, LENS_COORD, LENS_DENSITY, LENS_ECC,
+                    LENS_ECC_INF, LENS_L2, LENS_LINF, LENS_PCA,
                     MapperError, MapperParams)
 
 __all__ = [
     "Context", "Cover", "Clusters", "Graph", "MapperError", "mapper_lens", "mapper_cover",
     "mapper_cluster", "mapper_nerve", "mapper_graph", "params", "LENS_L2", "LENS_COORD",
-    "LENS_PCA", "LENS_ECC", "LENS_LINF", "LENS_DENSITY", "COVER_UNIFORM", "COVER_BALANCED", "FP32", "BF16", "BF16X1", "mapper_dbscan_noalloc", "Server", "graph_footprint",
+    "LENS_PCA", "LENS_ECC", "LENS_LINF", "LENS_DENSITY", "LENS_ECC_INF", "COVER_UNIFORM", "COVER_BALANCED", "FP32", "BF16", "BF16X1", "mapper_dbscan_noalloc", "Server", "graph_footprint",
     "mapper_graph_sweep", "mapper_cover_subset", "mapper_nerve_from_nodes", "mapper_knn_distance",
 ]
 

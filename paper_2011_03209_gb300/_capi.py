@@ -21,7 +21,7 @@ MAPPER_ENONFINITE = -5
 MAPPER_EINTERNAL = -6
 MAPPER_ENOTIMPL = -7
 
-LENS_L2, LENS_COORD, LENS_PCA, LENS_ECC, LENS_LINF, LENS_DENSITY = 0, 1, 2, 3, 4, 5
+LENS_L2, LENS_COORD, LENS_PCA, LENS_ECC, LENS_LINF, LENS_DENSITY, LENS_ECC_INF = 0, 1, 2, 3, 4, 5, 6
 COVER_UNIFORM, COVER_BALANCED = 0, 1
 FP32, BF16, BF16X1 = 0, 1, 2
 

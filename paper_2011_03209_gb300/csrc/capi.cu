@@ -183,7 +183,7 @@ int run_lens(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld, 
             if (args[j] < 0 || args[j] >= d) return fail(MAPPER_EINVAL, "PCA axis out of range");
             K = std::max(K, args[j] + 1);
         }
-        if (kinds[j] < 0 || kinds[j] > MAPPER_LENS_DENSITY) return fail(MAPPER_EINVAL, "unknown lens kind");
+        if (kinds[j] < 0 || kinds[j] > MAPPER_LENS_ECC_INF) return fail(MAPPER_EINVAL, "unknown lens kind");
     }
     *n_pca = 0;
     Buf status;
@@ -204,6 +204,9 @@ int run_lens(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld, 
             CK(lens_linf(X, n, d, ld, lens_dev, m, j, s), "lens_linf");
         else if (kinds[j] == MAPPER_LENS_DENSITY) {
             const int rc = run_density(ctx, X, n, d, ld, lens_param[j], precision, lens_dev, m, j);
+            if (rc) return rc;
+        } else if (kinds[j] == MAPPER_LENS_ECC_INF) {
+            const int rc = lens_ecc_inf(X, n, d, ld, lens_dev, m, j, ctx->num_sms, s);
             if (rc) return rc;
         } else
             CK(lens_project(X, n, d, ld, pca_dev->as<double>(),

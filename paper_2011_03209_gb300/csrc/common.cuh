@@ -66,9 +66,12 @@ cudaError_t lens_ecc2(const float* X, int64_t n, int32_t d, int64_t ld, double* 
                       cudaStream_t s);
 // k-th nearest-neighbour distances of q query rows (device indices) over all
 // n rows, the row itself first; out: q doubles on the device. Returns a
-// mapper_status (k in [1, min(16, n)], d <= 1184).
+// mapper_status (k in [1, min(16, n)]).
 int knn_distance(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* queries_dev, int64_t q,
                  int32_t k, double* out_dev, int num_sms, cudaStream_t s);
+// L-infinity centrality f(x) = max_y |x - y| into f[p * m + j]; a mapper_status.
+int lens_ecc_inf(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j, int num_sms,
+                 cudaStream_t s);
 cudaError_t lens_coord(const float* X, int64_t n, int64_t ld, int32_t col, double* f, int m,
                        int j, cudaStream_t s);
 cudaError_t lens_linf(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j,

@@ -91,28 +91,32 @@ __device__ __forceinline__ double exact_sqdist_rows(const float* __restrict__ x,
 }
 
 // The fallback streaming passes over the queries at positions pos[0 .. q)
-// of the query list (all of them when pos is null).
-template <int PASS>
+// of the query list (all of them when pos is null); columns staged kFC at a
+// time, so any row length. FAR: the k-th largest distance instead (values
+// negated in the lists), with the lower bound of the candidates' FP32 values.
+constexpr int kFC = 192;
+
+template <int PASS, bool FAR>
 __global__ void __launch_bounds__(32 * kQ, 1) knn_kernel(const float* __restrict__ X, int64_t n, int d, int64_t ld,
-                                                          int dp, const int32_t* __restrict__ queries,
+                                                          const int32_t* __restrict__ queries,
                                                           const int32_t* __restrict__ pos, int64_t q,
                                                           int k, float eta_lo, float eta_hi, float tiny,
                                                           float* __restrict__ thr, double* __restrict__ out)
 {
-    extern __shared__ float sm[];
-    float* qrow = sm;                            // [kQ][dp]
-    float* prow = sm + kQ * dp;                  // [kP][dp + 1]
+    __shared__ float qrow[kQ][kFC];
+    __shared__ float prow[kP][kFC + 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t qi = (int64_t)blockIdx.x * kQ + w;
     const bool live = qi < q;
     const int64_t qpos = live ? (pos ? pos[qi] : qi) : 0;
     const int64_t qp = live ? queries[qpos] : 0;
-    for (int c = lane; c < dp; c += 32) qrow[w * dp + c] = (live && c < d) ? X[qp * ld + c] : 0.f;
     float bound = 0.f;
     if (PASS == 1 && live) {
-        // B = (T + tiny)(1 + eta) / (1 - eta) + tiny, each step rounded up
         const float t = thr[qi];
-        bound = __fadd_ru(__fdiv_ru(__fmul_ru(__fadd_ru(t, tiny), eta_hi), eta_lo), tiny);
+        // nearest: B = (T + tiny)(1 + eta) / (1 - eta) + tiny, each step rounded up;
+        // farthest: B = (T - tiny)(1 - eta) / (1 + eta) - tiny, each step rounded down
+        bound = FAR ? __fsub_rd(__fdiv_rd(__fmul_rd(__fsub_rd(t, tiny), eta_lo), eta_hi), tiny)
+                    : __fadd_ru(__fdiv_ru(__fmul_ru(__fadd_ru(t, tiny), eta_hi), eta_lo), tiny);
     }
     float topf[kKMax];
     double topd[kKMax];
@@ -123,37 +127,42 @@ __global__ void __launch_bounds__(32 * kQ, 1) knn_kernel(const float* __restrict
     }
     float worstf = INFINITY;
     double worstd = INFINITY;
-    const float* qv = qrow + w * dp;
     for (int64_t j0 = 0; j0 < n; j0 += kP) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < kP * dp; e += blockDim.x) {
-            const int r = e / dp, c = e - r * dp;
-            const int64_t j = j0 + r;
-            prow[r * (dp + 1) + c] = (j < n && c < d) ? X[j * ld + c] : 0.f;
-        }
-        __syncthreads();
         const int64_t j = j0 + lane;
-        if (!live || j >= n) continue;
-        const float* pv = prow + lane * (dp + 1);
+        const bool act = live && j < n;
         float s = 0.f;
-        for (int c = 0; c < d; ++c) {
-            const float t = qv[c] - pv[c];
-            s = fmaf(t, t, s);
+        for (int k0 = 0; k0 < d; k0 += kFC) {
+            const int kc = d - k0 < kFC ? d - k0 : kFC;
+            __syncthreads();
+            for (int c = lane; c < kc; c += 32) qrow[w][c] = live ? X[qp * ld + k0 + c] : 0.f;
+            for (int e = threadIdx.x; e < kP * kc; e += blockDim.x) {
+                const int r = e / kc, c = e - r * kc;
+                const int64_t jr = j0 + r;
+                prow[r][c] = jr < n ? X[jr * ld + k0 + c] : 0.f;
+            }
+            __syncthreads();
+            if (act) {
+                for (int c = 0; c < kc; ++c) {
+                    const float t = qrow[w][c] - prow[lane][c];
+                    s = fmaf(t, t, s);
+                }
+            }
         }
+        if (!act) continue;
         if (PASS == 0) {
-            topk_insert(topf, k, s, worstf);
-        } else if (s <= bound) {
+            topk_insert(topf, k, FAR ? -s : s, worstf);
+        } else if (FAR ? s >= bound : s <= bound) {
             const double e2 = exact_sqdist_rows(X + qp * ld, X + j * ld, d);
-            topk_insert(topd, k, e2, worstd);
+            topk_insert(topd, k, FAR ? -e2 : e2, worstd);
         }
     }
     if (!live) return;                           // whole warp: qi is per warp
     if (PASS == 0) {
         const float t = warp_kth(topf, k, lane);
-        if (lane == 0) thr[qi] = t;
+        if (lane == 0) thr[qi] = FAR ? -t : t;
     } else {
         const double t = warp_kth(topd, k, lane);
-        if (lane == 0) out[qpos] = __dsqrt_rn(t);
+        if (lane == 0) out[qpos] = __dsqrt_rn(FAR ? -t : t);
     }
 }
 
@@ -201,6 +210,7 @@ __device__ __forceinline__ void list_insert(float (&lv)[kL], int (&li)[kL], floa
 // goes through shared memory to thread (qq, part) = (tid / 4, tid % 4), which
 // keeps the kL smallest of query qq over points 32 part .. 32 part + 31 of
 // every tile of the chunk.
+template <bool FAR>
 __global__ void __launch_bounds__(256, 2) knn_screen_kernel(const float* __restrict__ X, int64_t n, int d,
                                                              int64_t ld, bool xvec,
                                                              const int32_t* __restrict__ queries, int64_t q,
@@ -281,7 +291,7 @@ __global__ void __launch_bounds__(256, 2) knn_screen_kernel(const float* __restr
             for (int v = 0; v < 8; ++v) {
                 const int col = tp + 16 * v;
                 ps[(tq + 16 * u) * kDS + (col >> 5) * 33 + (col & 31)] =
-                    p0 + col < p_end ? acc[u][v] : INFINITY;
+                    p0 + col < p_end ? (FAR ? -acc[u][v] : acc[u][v]) : INFINITY;
             }
         __syncthreads();
         const float* row = ps + qq * kDS + part * 33;
@@ -306,6 +316,7 @@ __global__ void __launch_bounds__(256, 2) knn_screen_kernel(const float* __restr
 // bound B from the k-th of them, and, when the kL-th exceeds B, the exact
 // FP64 distances of the candidates below B and their k-th smallest. Else the
 // query goes to the fallback list.
+template <bool FAR>
 __global__ void __launch_bounds__(256) knn_merge_kernel(const float* __restrict__ X, int d, int64_t ld,
                                                         const int32_t* __restrict__ queries, int64_t q,
                                                         int n_lists, const float* __restrict__ cand_v,
@@ -346,39 +357,53 @@ __global__ void __launch_bounds__(256) knn_merge_kernel(const float* __restrict_
         }
         if (lane == r) { my_v = m; my_i = j; }
     }
+    // the lists hold negated values when FAR: v = -s
     const float t = __shfl_sync(0xffffffffu, my_v, k - 1);
     const float last = __shfl_sync(0xffffffffu, my_v, kL - 1);
-    const float bound = __fadd_ru(__fdiv_ru(__fmul_ru(__fadd_ru(t, tiny), eta_hi), eta_lo), tiny);
-    if (!(last > bound)) {
+    bool cand, redo_q;
+    if (!FAR) {
+        const float bound = __fadd_ru(__fdiv_ru(__fmul_ru(__fadd_ru(t, tiny), eta_hi), eta_lo), tiny);
+        redo_q = !(last > bound);
+        cand = lane < kL && my_v <= bound && my_i >= 0;
+    } else {
+        const float bound = __fsub_rd(__fdiv_rd(__fmul_rd(__fsub_rd(-t, tiny), eta_lo), eta_hi), tiny);
+        redo_q = !(-last < bound);
+        cand = lane < kL && -my_v >= bound && my_i >= 0;
+    }
+    if (redo_q) {
         if (lane == 0) redo[atomicAdd(n_redo, 1ull)] = (int32_t)qi;
         return;
     }
-    const bool cand = lane < kL && my_v <= bound && my_i >= 0;
-    double e = INFINITY;
+    const double none = FAR ? -INFINITY : INFINITY;
+    double e = none;
     if (cand) e = exact_sqdist_rows(X + (int64_t)queries[qi] * ld, X + (int64_t)my_i * ld, d);
-    // rank among the candidates (ties by lane)
+    // rank among the candidates, ascending (descending when FAR), ties by lane
     int rank = 0;
     for (int j = 0; j < kL; ++j) {
         const double o = __shfl_sync(0xffffffffu, e, j);
-        rank += (o < e || (o == e && j < lane)) ? 1 : 0;
+        rank += ((FAR ? o > e : o < e) || (o == e && j < lane)) ? 1 : 0;
     }
     if (cand && rank == k - 1) out[qi] = __dsqrt_rn(e);
 }
 
 }  // namespace
 
-int knn_distance(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* queries_dev, int64_t q,
-                 int32_t k, double* out_dev, int num_sms, cudaStream_t s)
+namespace {
+
+__global__ void iota_kernel(int64_t n, int32_t* __restrict__ v)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (int32_t)i;
+}
+
+// k-th smallest (FAR: k-th largest) distance of each query row to the cloud.
+template <bool FAR>
+int knn_select(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* queries_dev, int64_t q, int32_t k,
+               double* out_dev, int num_sms, cudaStream_t s)
 {
     if (q == 0) return MAPPER_OK;
     if (k < 1 || k > kKMax || k > n) {
         set_error("k must be in [1, min(16, n)]");
-        return MAPPER_EINVAL;
-    }
-    const int dp = (d + 31) / 32 * 32;
-    const size_t smem = sizeof(float) * ((size_t)kQ * dp + (size_t)kP * (dp + 1));
-    if (smem > 227 * 1024) {
-        set_error("k-distance: rows wider than 1184 columns");
         return MAPPER_EINVAL;
     }
     // FP32 screen bound of the sum of d squared differences (as the CUDA-core
@@ -405,12 +430,12 @@ int knn_distance(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t
     if (e == cudaSuccess) e = cudaMemsetAsync(n_redo.p, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ENOMEM; }
     const bool xvec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
-    knn_screen_kernel<<<dim3((unsigned)qt, (unsigned)S), 256, 0, s>>>(X, n, d, ld, xvec, queries_dev, q, chunk,
-                                                                      cv.as<float>(), ci.as<int32_t>());
-    knn_merge_kernel<<<(unsigned)div_up(q, 8), 256, 0, s>>>(X, d, ld, queries_dev, q, (int)(S * kParts),
-                                                            cv.as<float>(), ci.as<int32_t>(), k, eta_lo, eta_hi,
-                                                            tiny, out_dev, redo.as<int32_t>(),
-                                                            n_redo.as<unsigned long long>());
+    knn_screen_kernel<FAR><<<dim3((unsigned)qt, (unsigned)S), 256, 0, s>>>(X, n, d, ld, xvec, queries_dev, q, chunk,
+                                                                           cv.as<float>(), ci.as<int32_t>());
+    knn_merge_kernel<FAR><<<(unsigned)div_up(q, 8), 256, 0, s>>>(X, d, ld, queries_dev, q, (int)(S * kParts),
+                                                                 cv.as<float>(), ci.as<int32_t>(), k, eta_lo, eta_hi,
+                                                                 tiny, out_dev, redo.as<int32_t>(),
+                                                                 n_redo.as<unsigned long long>());
     note_launch(2);
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ECUDA; }
@@ -425,15 +450,46 @@ int knn_distance(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t
     e = thr.alloc(sizeof(float) * qr, s);
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ENOMEM; }
     const unsigned grid = (unsigned)div_up(qr, kQ);
-    e = cudaFuncSetAttribute(knn_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(knn_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ECUDA; }
-    knn_kernel<0><<<grid, 32 * kQ, smem, s>>>(X, n, d, ld, dp, queries_dev, redo.as<int32_t>(), qr, k, eta_lo,
-                                               eta_hi, tiny, thr.as<float>(), out_dev);
-    knn_kernel<1><<<grid, 32 * kQ, smem, s>>>(X, n, d, ld, dp, queries_dev, redo.as<int32_t>(), qr, k, eta_lo,
-                                               eta_hi, tiny, thr.as<float>(), out_dev);
+    knn_kernel<0, FAR><<<grid, 32 * kQ, 0, s>>>(X, n, d, ld, queries_dev, redo.as<int32_t>(), qr, k, eta_lo, eta_hi,
+                                                tiny, thr.as<float>(), out_dev);
+    knn_kernel<1, FAR><<<grid, 32 * kQ, 0, s>>>(X, n, d, ld, queries_dev, redo.as<int32_t>(), qr, k, eta_lo, eta_hi,
+                                                tiny, thr.as<float>(), out_dev);
     note_launch(2);
     e = cudaGetLastError();
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ECUDA; }
+    return MAPPER_OK;
+}
+
+}  // namespace
+
+int knn_distance(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* queries_dev, int64_t q,
+                 int32_t k, double* out_dev, int num_sms, cudaStream_t s)
+{
+    return knn_select<false>(X, n, d, ld, queries_dev, q, k, out_dev, num_sms, s);
+}
+
+// L-infinity centrality filter f(x) = max_y d(x, y): the L-infinity norm of
+// x's row of the pairwise distance matrix (§5 filters by the "L_infinity-norm"
+// after computing that matrix), the largest distance of every row to the
+// cloud, exact.
+int lens_ecc_inf(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j, int num_sms,
+                 cudaStream_t s)
+{
+    if (n == 0) return MAPPER_OK;
+    if (n > INT32_MAX) {
+        set_error("L-infinity centrality: more than 2^31 points");
+        return MAPPER_EINVAL;
+    }
+    Buf qs, tmp;
+    cudaError_t e = qs.alloc(sizeof(int32_t) * n, s);
+    if (e == cudaSuccess) e = tmp.alloc(sizeof(double) * n, s);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ENOMEM; }
+    iota_kernel<<<(unsigned)div_up(n, 256), 256, 0, s>>>(n, qs.as<int32_t>());
+    note_launch();
+    const int rc = knn_select<true>(X, n, d, ld, qs.as<int32_t>(), n, 1, tmp.as<double>(), num_sms, s);
+    if (rc) return rc;
+    e = cudaMemcpy2DAsync(f + j, sizeof(double) * m, tmp.p, sizeof(double), sizeof(double), (size_t)n,
+                          cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ECUDA; }
     return MAPPER_OK;
 }

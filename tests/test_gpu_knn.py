@@ -103,3 +103,13 @@ def test_knn_distance_strided_rows_and_ties(ctx):
     q = np.r_[np.arange(0, X.shape[0], 7), np.arange(100, 140)].astype(np.int32)
     for k in (2, 3, 16):
         assert np.array_equal(mg.mapper_knn_distance(ctx, Xd, q, k), oracle.knn_distance(X, q, k)), k
+
+
+def test_knn_distance_wide_rows(ctx):
+    """1500 columns (the row length of §5's gene-expression case): the
+    streaming passes stage columns in chunks."""
+    X = synth.gaussian_mixture(300, 1500, 3, seed=98, centre_box=3.0, std_lo=0.5, std_hi=1.0, anisotropic=False)
+    Xd = torch.from_numpy(X).to("cuda:0")
+    q = np.arange(300, dtype=np.int32)
+    for k in (1, 2, 5):
+        assert np.array_equal(mg.mapper_knn_distance(ctx, Xd, q, k), oracle.knn_distance(X, q, k))

@@ -1,8 +1,9 @@
-"""Parity of the L-infinity-norm and density filters (through the C ABI) with
-the FP64 oracle. Both are exact (a maximum of magnitudes; integer counts of
-the points within distance r), so the lens columns equal the oracle's bit for
-bit in every screen precision, and the graphs built on them equal the
-oracle's."""
+"""Parity of the L-infinity-norm, density and L-infinity-centrality filters
+(through the C ABI) with the FP64 oracle. All three are exact (a maximum of
+magnitudes; integer counts of the points within distance r; the FP64 distance
+of the defining expression to the farthest point), so the lens columns equal
+the oracle's bit for bit in every screen precision, and the graphs built on
+them equal the oracle's."""
 import functools
 
 import numpy as np
@@ -149,3 +150,32 @@ def test_density_lens_1m_d256_sampled(ctx):
     rng = np.random.default_rng(4)
     rows = np.r_[rng.choice(w.n, 40, replace=False), np.argmin(f), np.argmax(f)]
     assert np.array_equal(f[rows], oracle.density_at(w.X, rows, w.eps))
+
+
+@pytest.mark.parametrize("n,d,seed", [(1, 3, 0), (2, 5, 1), (300, 1500, 2), (3000, 64, 3), (5000, 17, 4)])
+def test_ecc_inf_lens_exact(ctx, n, d, seed):
+    """L-infinity centrality max_y |x - y| equals the oracle's brute force bit
+    for bit (rows up to 1500 columns, as §5's gene-expression case)."""
+    X = _cloud(n, d, seed)
+    got = _lens(ctx, X, (mg.LENS_ECC_INF,), (0,))[:, 0]
+    assert np.array_equal(got, oracle.lens_ecc_inf(X))
+
+
+def test_ecc_inf_lens_far_duplicates_and_2d_graph(ctx):
+    """Forty copies of one far point make the 16 largest screened values tie
+    for every row (the streaming passes decide them); the 2D graph on
+    (L-infinity centrality, a column), as in §5, equals the oracle's."""
+    X = _cloud(2500, 12, 7)
+    X[100:140] = X[:, :].max(axis=0) * 3.0
+    got = _lens(ctx, X, (mg.LENS_ECC_INF, mg.LENS_COORD), (0, 2))
+    ref = oracle.lens(X, (6, 1), (0, 2))
+    assert np.array_equal(got, ref)
+    eps = _radius(X, 4, 7)
+    prm = mg.params((mg.LENS_ECC_INF, mg.LENS_COORD), (0, 2), (8, 5), (0.65, 0.5), eps, 2, mg.BF16)
+    g = mg.mapper_graph(ctx, torch.from_numpy(X).to("cuda:0"), prm)
+    res = g.numpy()
+    lens, _ = g.lens(X.shape[0], 2)
+    assert np.array_equal(lens, ref)
+    rg = oracle.mapper_graph(X, ref, (8, 5), (0.65, 0.5), eps, 2)
+    for k in ("node_offsets", "node_members", "node_elem", "edges"):
+        assert np.array_equal(np.asarray(res[k]), np.asarray(rg[k])), k
