@@ -379,7 +379,7 @@ struct CountsOut {
 int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
                 const std::shared_ptr<CoverData>& cov, double eps, int32_t min_pts, int32_t precision,
                 std::shared_ptr<ClusterData>* out, int* nonfinite_dev, const TileLayout* layout = nullptr,
-                const CountsOut* counts_out = nullptr)
+                const CountsOut* counts_out = nullptr, const PivotSet* pivots = nullptr)
 {
     if (!(eps > 0.0) || !std::isfinite(eps)) return fail(MAPPER_EINVAL, "eps must be finite and > 0");
     if (min_pts < 1) return fail(MAPPER_EINVAL, "min_pts must be >= 1");
@@ -426,7 +426,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     int rc = MAPPER_OK;
     if (!layout) {
         rc = build_tiles(X, n, d, ld, dp, cov->slot_point.as<int32_t>(), cov->slot_elem.as<int32_t>(), M, E,
-                         4.0 * eps, use_tc, ctx->num_sms, &own, nf, s);
+                         4.0 * eps, use_tc, ctx->num_sms, &own, nf, s, pivots);
         if (rc) return rc;
         layout = &own;
     }
@@ -888,6 +888,7 @@ int mapper_create(mapper_ctx** out, int device, size_t hbm_budget_bytes, void* c
         ctx->stream->owned = true;
     }
     CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device), "attr");
+
     // keep freed scratch in the pool between calls
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
@@ -1335,6 +1336,9 @@ int mapper_graph_sweep(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, in
     std::vector<char> done(n_sweep, 0);
     const int dp = (d + 31) / 32 * 32;
     const bool use_tc = p->precision != MAPPER_FP32;
+    PivotSet piv;                              // one pivot assignment for every tile layout
+    CK(pivot_alloc(n, dp, &piv, s), "alloc pivots");
+    if ((rc = pivot_assign(Xd, n, d, ldd, dp, use_tc, ctx->num_sms, &piv, s))) return rc;
     // one cover and one tile layout per distinct overlap, shared by its radii
     for (int i = 0; i < n_sweep; ++i) {
         if (done[i]) continue;
@@ -1349,7 +1353,7 @@ int mapper_graph_sweep(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, in
         if (!(eps_max > 0.0) || !std::isfinite(eps_max)) return fail(MAPPER_EINVAL, "eps must be finite and > 0");
         TileLayout L;
         if ((rc = build_tiles(Xd, n, d, ldd, dp, cov->slot_point.as<int32_t>(), cov->slot_elem.as<int32_t>(), cov->M,
-                              cov->E, 4.0 * eps_max, use_tc, ctx->num_sms, &L, flag.as<int>(), s)))
+                              cov->E, 4.0 * eps_max, use_tc, ctx->num_sms, &L, flag.as<int>(), s, &piv)))
             return rc;
         for (int j = i; j < n_sweep; ++j) {
             if (done[j] || overlap[j] != overlap[i]) continue;

@@ -170,13 +170,28 @@ struct PairLists {
     int64_t n_candidates = 0, n_out = 0;
 };
 
+// The pivots of the tile layout and every point's nearest one: K pivots
+// (points floor(k n / K)), Pv their FP32 rows (K x dp), piv[n] the nearest
+// pivot and pd2[n] an FP32 squared distance to it. They depend on X only, so
+// one set serves every layout of the cloud.
+struct PivotSet {
+    int K = 0;
+    Buf Pv, piv, pd2;
+};
+// Allocates the set on stream `alloc_s` (where it is later freed) and
+// computes it on stream `s` (which must wait for alloc_s).
+cudaError_t pivot_alloc(int64_t n, int dp, PivotSet* P, cudaStream_t alloc_s);
+int pivot_assign(const float* X, int64_t n, int32_t d, int64_t ld, int dp, bool bf16, int num_sms, PivotSet* P,
+                 cudaStream_t s);
+
 // Orders every element's points by pivot group, lays them out in tiles
 // (a tile never mixes groups) and gathers rows. tau: distance under which two
 // pivots join a group and beyond which a point is an outlier. bf16: also
 // build the tensor-core operands (and assign pivots on tensor cores).
+// pre: the pivot set, computed beforehand (stream-ordered before s), or null.
 int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const int32_t* slot_point,
                 const int32_t* slot_elem, int64_t M, int64_t E, double tau, bool bf16, int num_sms,
-                TileLayout* L, int* nonfinite, cudaStream_t s);
+                TileLayout* L, int* nonfinite, cudaStream_t s, const PivotSet* pre = nullptr);
 // Classifies every tile pair of every element by bounding spheres: out (no
 // pair within eps), all-in, or mixed (to the tensor-core list when both tiles
 // are one non-outlier segment and use_tc, else to the CUDA-core list).

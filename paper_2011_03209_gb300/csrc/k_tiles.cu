@@ -729,9 +729,41 @@ __global__ void __launch_bounds__(256) classify_kernel(const int64_t* __restrict
 
 }  // namespace
 
+cudaError_t pivot_alloc(int64_t n, int dp, PivotSet* P, cudaStream_t alloc_s)
+{
+    P->K = (int)std::min<int64_t>(kPiv, n);
+    cudaError_t e = P->Pv.alloc(sizeof(float) * (size_t)P->K * dp, alloc_s);
+    if (e == cudaSuccess) e = P->piv.alloc(sizeof(int32_t) * n, alloc_s);
+    if (e == cudaSuccess) e = P->pd2.alloc(sizeof(float) * n, alloc_s);
+    return e;
+}
+
+int pivot_assign(const float* X, int64_t n, int32_t d, int64_t ld, int dp, bool bf16, int num_sms, PivotSet* P,
+                 cudaStream_t s)
+{
+    const int K = P->K;
+    pivot_gather_kernel<<<K, 128, 0, s>>>(X, n, d, ld, dp, K, P->Pv.as<float>());
+    note_launch();
+    if (bf16) {
+        const int rc = assign_pivots_tc(X, n, d, ld, dp, P->Pv.as<float>(), K, num_sms, P->piv.as<int32_t>(),
+                                        P->pd2.as<float>(), s);
+        if (rc) return rc;
+    } else {
+        assign_kernel<<<grid_for(n, kT), 256, 0, s>>>(X, n, d, ld, P->Pv.as<float>(), dp, K, P->piv.as<int32_t>(),
+                                                     P->pd2.as<float>());
+        note_launch();
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("pivot assignment: ") + cudaGetErrorString(e));
+        return MAPPER_ECUDA;
+    }
+    return MAPPER_OK;
+}
+
 int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const int32_t* slot_point,
                 const int32_t* slot_elem, int64_t M, int64_t E, double tau, bool bf16, int num_sms,
-                TileLayout* L, int* nonfinite, cudaStream_t s)
+                TileLayout* L, int* nonfinite, cudaStream_t s, const PivotSet* pre)
 {
 #define TK(expr)                                                                      \
     do {                                                                              \
@@ -741,26 +773,22 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
             return e_ == cudaErrorMemoryAllocation ? MAPPER_ENOMEM : MAPPER_ECUDA;    \
         }                                                                             \
     } while (0)
-    const int K = (int)std::min<int64_t>(kPiv, n);
-    Buf Pv, piv, pd2, gid, ngrp, adj;
-    TK(Pv.alloc(sizeof(float) * (size_t)K * dp, s));
-    TK(piv.alloc(sizeof(int32_t) * n, s));
-    TK(pd2.alloc(sizeof(float) * n, s));
+    PivotSet own;
+    if (!pre) {
+        TK(pivot_alloc(n, dp, &own, s));
+        const int rc = pivot_assign(X, n, d, ld, dp, bf16, num_sms, &own, s);
+        if (rc) return rc;
+        pre = &own;
+    }
+    const int K = pre->K;
+    const Buf& Pv = pre->Pv;
+    const Buf& piv = pre->piv;
+    const Buf& pd2 = pre->pd2;
+    Buf gid, ngrp, adj;
     TK(gid.alloc(sizeof(int32_t) * kPiv, s));
     TK(ngrp.alloc(sizeof(int32_t), s));
     TK(adj.alloc(sizeof(unsigned) * kPiv * (kPiv / 32), s));
     TK(cudaMemsetAsync(adj.p, 0, sizeof(unsigned) * kPiv * (kPiv / 32), s));
-    pivot_gather_kernel<<<K, 128, 0, s>>>(X, n, d, ld, dp, K, Pv.as<float>());
-    note_launch();
-    if (bf16) {
-        const int rc = assign_pivots_tc(X, n, d, ld, dp, Pv.as<float>(), K, num_sms, piv.as<int32_t>(),
-                                        pd2.as<float>(), s);
-        if (rc) return rc;
-    } else {
-        assign_kernel<<<grid_for(n, kT), 256, 0, s>>>(X, n, d, ld, Pv.as<float>(), dp, K, piv.as<int32_t>(),
-                                                     pd2.as<float>());
-        note_launch();
-    }
     const float tau2 = (float)(tau * tau);
     pivot_adj_kernel<<<grid_for((int64_t)K * K * 32, 256), 256, 0, s>>>(Pv.as<float>(), dp, K, tau2,
                                                                        adj.as<unsigned>());
