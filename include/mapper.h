@@ -198,6 +198,11 @@ int mapper_set_pass1_tile_n(mapper_ctx* ctx, int tile_n);
  * (default), 1 = always on the tensor cores (rows centred per element, a
  * second operand set), 2 = always on CUDA cores. Other values: MAPPER_EINVAL. */
 int mapper_set_cross_screen(mapper_ctx* ctx, int mode);
+/* Failure-detection self-test (the paper has no counterpart): runs the
+ * bounded mbarrier wait of the tensor-core passes on a barrier that nothing
+ * completes. Returns MAPPER_ETIMEOUT after the wait's limit (4 s), the status
+ * a pass reports when a wait runs out; the context stays usable. */
+int mapper_selftest_wait(mapper_ctx* ctx);
 
 /* -------------------------------------------------------------- the steps */
 

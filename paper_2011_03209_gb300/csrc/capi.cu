@@ -929,6 +929,13 @@ int mapper_set_timing(mapper_ctx* ctx, int enabled)
     return MAPPER_OK;
 }
 
+int mapper_selftest_wait(mapper_ctx* ctx)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    return tc_wait_selftest(ctx->stream->s);
+}
+
 int mapper_set_cross_screen(mapper_ctx* ctx, int mode)
 {
     if (!ctx) return fail(MAPPER_EINVAL, "null context");

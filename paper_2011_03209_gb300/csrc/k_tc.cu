@@ -1393,6 +1393,48 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
     return MAPPER_OK;
 }
 
+namespace {
+
+// The bounded wait of the tensor-core passes, run out on purpose: one thread
+// arms an mbarrier for one arrival that nothing makes and waits on it with
+// the same helper; status = 1 when the wait gave up and raised the abort
+// flag (as a pass that lost its producer would), 0 if it completed.
+__global__ void wait_selftest_kernel(int* status)
+{
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const bool done = mbar_wait(&bar, 0, &abort_flag);
+        *status = done ? 0 : (abort_flag ? 1 : 2);
+    }
+}
+
+}  // namespace
+
+int tc_wait_selftest(cudaStream_t s)
+{
+    Buf st;
+    cudaError_t e = st.alloc(sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st.p, 0xff, sizeof(int), s);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ECUDA; }
+    wait_selftest_kernel<<<1, 32, 0, s>>>(st.as<int>());
+    note_launch();
+    int h = -1;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, st.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ECUDA; }
+    if (h == 1) {
+        set_error("bounded wait gave up as designed (self-test)");
+        return MAPPER_ETIMEOUT;
+    }
+    set_error("bounded-wait self-test: the wait did not run out");
+    return MAPPER_EINTERNAL;
+}
+
 int tc_groups(const int2* pairs, int64_t n, Buf* groups, Buf* pos, cudaStream_t s)
 {
     if (n == 0) return MAPPER_OK;

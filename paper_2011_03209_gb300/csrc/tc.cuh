@@ -45,6 +45,10 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
 int assign_pivots_tc(const float* X, int64_t n, int d, int64_t ld, int dp, const float* Pv, int K,
                      int num_sms, int32_t* piv, float* pd2, cudaStream_t s);
 
+// Runs the passes' bounded mbarrier wait on a barrier that is never
+// completed: MAPPER_ETIMEOUT once it gives up (after 4 s), as designed.
+int tc_wait_selftest(cudaStream_t s);
+
 // Constants of the screen's error bound E = A1 |a||b| + A2 (|a|^2 + |b|^2) + A3.
 void tc_bound(int ns, int dp, double eps2, double* A1, double* A2, double* A3);
 
