@@ -466,10 +466,14 @@ def run_knn(args):
         torch.cuda.synchronize()
         clocks = sampler.stop()
     ms = start.elapsed_time(end) / args.steps
-    # FP32 screen: 3 d flops (sub, FMA) per (query, row) pair, one pass (the
-    # exact refinement of at most 16 candidates per query is not counted)
-    tflops = 3 * w.d * float(q.size) * w.n / (ms * 1e-3) / 1e12
-    peak = 152 * 128 * 2 * 2070e6 / 1e12
+    # tensor-core screen: 2 d algorithmic flops per (query, point) pair (one
+    # product; the kernel executes three BF16 products), over the whole call
+    # (operands, screen, FP64 merge and the CUDA-core screen of the queries the
+    # lists do not settle)
+    peaks, src = _peaks()
+    algo = 2.0 * w.d * float(q.size) * w.n
+    tflops = algo / (ms * 1e-3) / 1e12
+    peak = peaks["bf16_tflops_sustained"]
     cpu = None
     if not args.no_cpu_baseline:
         import oracle
@@ -486,10 +490,11 @@ def run_knn(args):
         "data": "synthetic", "config": {"workload": f"clusters_{w.n // 1000}k_d{w.d}_knn", "queries": int(q.size),
                                         "k": k},
         "queries_per_s": q.size / (ms * 1e-3),
-        "roofline": {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
-                     "traffic": None, "kernel": "knn_screen_kernel: register-tiled FP32 screen, 3 d flops per (query, point) "
-                               "pair (sub + FMA: at most 0.75 of the FMA peak)",
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max clock)"},
+        "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                     "traffic": None, "executed_tflops": 3.0 * tflops,
+                     "kernel": "tc_kernel<3,3,2> (tcgen05 BF16 k-distance screen, top-8 lists per query row and "
+                               "32-column part): 2d algorithmic flops per (query, point) pair over the whole call",
+                     "peak_source": f"{src} bf16_tflops_sustained"},
         "cpu_baseline": cpu, "clocks": clocks,
     }))
 

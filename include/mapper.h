@@ -203,6 +203,10 @@ int mapper_set_cross_screen(mapper_ctx* ctx, int mode);
  * completes. Returns MAPPER_ETIMEOUT after the wait's limit (4 s), the status
  * a pass reports when a wait runs out; the context stays usable. */
 int mapper_selftest_wait(mapper_ctx* ctx);
+/* Screen of mapper_knn_distance (a tuning knob; results do not depend on
+ * it): 0 = tensor cores (default), 1 = tensor cores, 2 = the FP32 CUDA-core
+ * screen. Other values: MAPPER_EINVAL. */
+int mapper_set_knn_screen(mapper_ctx* ctx, int mode);
 
 /* -------------------------------------------------------------- the steps */
 
@@ -284,8 +288,10 @@ int mapper_nerve_from_nodes(mapper_ctx* ctx, int64_t n_points, int64_t n_nodes, 
  * the rows of X, the row itself counted first (distance 0), so the row is
  * core for DBSCAN(eps, k) on the whole cloud iff the value is <= eps. The
  * value is the FP64 distance of the defining expression (double sum of
- * squared differences, k ascending, sqrt), found exactly through an FP32
- * screen. X: device memory. queries (q int32) and out (q doubles): host or
+ * squared differences, k ascending, sqrt), found exactly through a screen
+ * (tensor cores, BF16 hi + lo products of rows centred on the column means,
+ * or FP32 CUDA cores; mapper_set_knn_screen) and an FP64 decision of its
+ * candidates. X: device memory. queries (q int32) and out (q doubles): host or
  * device memory, out filled before the call returns. k in [1, min(16, n)];
  * MAPPER_EINVAL otherwise, MAPPER_ENONFINITE if X holds NaN/Inf. */
 int mapper_knn_distance(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, int64_t ld,

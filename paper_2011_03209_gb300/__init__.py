@@ -59,6 +59,10 @@ class Context:
         """0: autotuned (default); 128 or 256: fixed pass-1 product shape."""
         _capi.check(self._lib.mapper_set_pass1_tile_n(self.h, int(tile_n)), "mapper_set_pass1_tile_n")
 
+    def set_knn_screen(self, mode: int) -> None:
+        """k-distance screen: 0 tensor cores (default), 1 tensor cores, 2 CUDA cores."""
+        _capi.check(self._lib.mapper_set_knn_screen(self.h, int(mode)), "mapper_set_knn_screen")
+
     def set_cross_screen(self, mode: int) -> None:
         """Mixed tile pairs across two segments: 0 auto (default), 1 tensor
         cores, 2 CUDA cores."""

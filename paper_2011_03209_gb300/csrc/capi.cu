@@ -73,6 +73,7 @@ struct mapper_ctx {
     std::map<uint64_t, int> pass1_tile_n;      // autotuner: (row pitch, products) -> N
     int pass1_forced = 0;                      // 128 or 256: fixed by the caller
     int cross_mode = 0;                        // cross-segment pairs: 0 auto, 1 tensor cores, 2 CUDA cores
+    int knn_mode = 0;                          // k-distance screen: 0 auto (tensor cores), 1 tensor, 2 CUDA cores
 };
 
 struct mapper_cover_t {
@@ -206,7 +207,7 @@ int run_lens(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld, 
             const int rc = run_density(ctx, X, n, d, ld, lens_param[j], precision, lens_dev, m, j);
             if (rc) return rc;
         } else if (kinds[j] == MAPPER_LENS_ECC_INF) {
-            const int rc = lens_ecc_inf(X, n, d, ld, lens_dev, m, j, ctx->num_sms, s);
+            const int rc = lens_ecc_inf(X, n, d, ld, lens_dev, m, j, ctx->num_sms, precision != MAPPER_FP32, s);
             if (rc) return rc;
         } else
             CK(lens_project(X, n, d, ld, pca_dev->as<double>(),
@@ -936,6 +937,14 @@ int mapper_selftest_wait(mapper_ctx* ctx)
     return tc_wait_selftest(ctx->stream->s);
 }
 
+int mapper_set_knn_screen(mapper_ctx* ctx, int mode)
+{
+    if (!ctx) return fail(MAPPER_EINVAL, "null context");
+    if (mode < 0 || mode > 2) return fail(MAPPER_EINVAL, "mode must be 0, 1 or 2");
+    ctx->knn_mode = mode;
+    return MAPPER_OK;
+}
+
 int mapper_set_cross_screen(mapper_ctx* ctx, int mode)
 {
     if (!ctx) return fail(MAPPER_EINVAL, "null context");
@@ -1197,7 +1206,9 @@ int mapper_knn_distance(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t 
     CK(qd.alloc(sizeof(int32_t) * q, s), "alloc");
     CK(od.alloc(sizeof(double) * q, s), "alloc");
     CK(cudaMemcpyAsync(qd.p, hq.data(), sizeof(int32_t) * q, cudaMemcpyHostToDevice, s), "copy");
-    if ((rc = knn_distance(X_dev, n, d, ld, qd.as<int32_t>(), q, k, od.as<double>(), ctx->num_sms, s))) return rc;
+    if ((rc = knn_distance(X_dev, n, d, ld, qd.as<int32_t>(), q, k, od.as<double>(), ctx->num_sms,
+                           ctx->knn_mode != 2, s)))
+        return rc;
     return copy_out(out, od.p, sizeof(double) * q, !is_host_pointer(out), s);
 }
 

@@ -67,17 +67,20 @@ cudaError_t lens_ecc2(const float* X, int64_t n, int32_t d, int64_t ld, double* 
 // k-th nearest-neighbour distances of q query rows (device indices) over all
 // n rows, the row itself first; out: q doubles on the device. Returns a
 // mapper_status (k in [1, min(16, n)]).
+// tensor_cores: screen on the tensor cores (else the FP32 CUDA-core screen).
 int knn_distance(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* queries_dev, int64_t q,
-                 int32_t k, double* out_dev, int num_sms, cudaStream_t s);
+                 int32_t k, double* out_dev, int num_sms, bool tensor_cores, cudaStream_t s);
 // L-infinity centrality f(x) = max_y |x - y| into f[p * m + j]; a mapper_status.
 int lens_ecc_inf(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j, int num_sms,
-                 cudaStream_t s);
+                 bool tensor_cores, cudaStream_t s);
 cudaError_t lens_coord(const float* X, int64_t n, int64_t ld, int32_t col, double* f, int m,
                        int j, cudaStream_t s);
 cudaError_t lens_linf(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j,
                       cudaStream_t s);
 cudaError_t lens_project(const float* X, int64_t n, int32_t d, int64_t ld, const double* mu,
                          const double* v, double* f, int m, int j, cudaStream_t s);
+// Column means of X (FP64, fixed-order block sums): mu[d] on the device.
+cudaError_t column_means(const float* X, int64_t n, int32_t d, int64_t ld, double* mu, cudaStream_t s);
 // Principal axes: mu (d doubles) and K axes (K*d doubles), device outputs.
 cudaError_t pca_axes(const float* X, int64_t n, int32_t d, int64_t ld, int K, double* mu,
                      double* axes, int* status, cudaStream_t s);

@@ -197,6 +197,12 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
 // are one non-outlier segment and use_tc, else to the CUDA-core list).
 int classify_pairs(const TileLayout& L, int dp, int64_t E, double eps, bool use_tc,
                    PairLists* P, cudaStream_t s);
+// BF16 hi + lo operands of rows row_pt[.] of X (T tiles of 128 rows, the
+// first tile_n[t] of tile t valid, the rest zero), centred on cents[tile_cent[t]]
+// (dp floats each), with FP32 |a|^2 and |a| rounded up.
+cudaError_t centred_operands(const float* X, int64_t ld, int d, int dp, const int32_t* row_pt, const int32_t* tile_n,
+                             const int32_t* tile_cent, const float* cents, int64_t T, void* Ah, void* Al, float* rn2,
+                             float* rn, cudaStream_t s);
 // Tensor-core operands for the CUDA-core list (tile pairs of one element, two
 // segments): every row centred on its element's centre, BF16 hi + lo, with
 // FP32 |a|^2 and |a| rounded up (R rows each).

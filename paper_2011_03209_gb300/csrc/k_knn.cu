@@ -31,6 +31,7 @@
 
 #include "../../include/mapper.h"
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace mgb {
 
@@ -396,6 +397,294 @@ __global__ void iota_kernel(int64_t n, int32_t* __restrict__ v)
     if (i < n) v[i] = (int32_t)i;
 }
 
+// FP32 sum of squared differences of two rows, columns ascending (the chain
+// of the CUDA-core screen: relative error at most eta, subnormals below tiny).
+__device__ __forceinline__ float fp32_sqdist_rows(const float* __restrict__ x, const float* __restrict__ y, int d)
+{
+    float s = 0.f;
+    for (int k = 0; k < d; ++k) {
+        const float t = x[k] - y[k];
+        s = fmaf(t, t, s);
+    }
+    return s;
+}
+
+// Merge for the tensor-core screen. Its lists hold lower bounds l = key - E
+// of the exact key (d^2, or -d^2 for FAR) with E = A1 |a||b| + A2 (|a|^2 +
+// |b|^2) + A3 for that pair of rows, so u = l + 2E bounds it from above. The
+// k-th smallest exact key is at most U = the k-th smallest u over the lists,
+// and every point that can reach it has l <= U. Each list (kTL smallest l of a
+// 32-point part of a chunk) holds every point of its part below its last l,
+// so when U is below every list's last l the lists hold every candidate (else
+// the query goes to the fallback list). The candidates are then screened
+// again by their FP32 sums (relative error eta): with T32 the k-th smallest
+// of those keys, only candidates within B32 = (T32 + tiny)(1 + eta) / (1 - eta)
+// + tiny (FAR: the mirror bound) can hold the k-th exact key, and those few
+// get the FP64 defining expression. One warp per query, lane i takes lists
+// i, i + 32, ..
+constexpr int kTL = kKnnList;
+
+template <bool FAR>
+__global__ void __launch_bounds__(256) knn_merge_abs_kernel(const float* __restrict__ X, int d, int64_t ld,
+                                                            const int32_t* __restrict__ queries, int64_t q,
+                                                            int n_lists, const float* __restrict__ cand_v,
+                                                            const int32_t* __restrict__ cand_i, int k,
+                                                            const float* __restrict__ rn2, const float* __restrict__ rn,
+                                                            int64_t q_row0, float A1, float A2, float A3,
+                                                            float eta_lo, float eta_hi, float tiny,
+                                                            double* __restrict__ out, int32_t* __restrict__ redo,
+                                                            unsigned long long* __restrict__ n_redo)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t qi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (qi >= q) return;                         // whole warp
+    const float* cv = cand_v + qi * (int64_t)n_lists * kTL;
+    const int32_t* ci = cand_i + qi * (int64_t)n_lists * kTL;
+    const float na2 = rn2[q_row0 + qi], nra = rn[q_row0 + qi];
+    float top[kKMax];
+#pragma unroll
+    for (int i = 0; i < kKMax; ++i) top[i] = INFINITY;
+    float worst = INFINITY, mlast = INFINITY;
+    for (int l = lane; l < n_lists; l += 32) {
+        const int64_t e0 = (int64_t)l * kTL;
+        mlast = fminf(mlast, cv[e0 + kTL - 1]);
+        for (int i = 0; i < kTL; ++i) {
+            const float lo = cv[e0 + i];
+            if (!(lo < worst)) break;            // ascending list; u >= l
+            const int j = ci[e0 + i];
+            const float E = __fmaf_ru(A1, __fmul_ru(nra, rn[j]), __fmaf_ru(A2, __fadd_ru(na2, rn2[j]), A3));
+            topk_insert(top, k, __fadd_ru(lo, __fmul_ru(2.f, E)), worst);
+        }
+    }
+    const float U = warp_kth(top, k, lane);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mlast = fminf(mlast, __shfl_xor_sync(0xffffffffu, mlast, o));
+    if (!(U < mlast)) {
+        if (lane == 0) redo[atomicAdd(n_redo, 1ull)] = (int32_t)qi;
+        return;
+    }
+    const float* xq = X + (int64_t)queries[qi] * ld;
+    // FP32 keys of the candidates: their k-th smallest
+    float topf[kKMax];
+#pragma unroll
+    for (int i = 0; i < kKMax; ++i) topf[i] = INFINITY;
+    float worstf = INFINITY;
+    for (int l = lane; l < n_lists; l += 32) {
+        for (int i = 0; i < kTL; ++i) {
+            const int64_t e = (int64_t)l * kTL + i;
+            if (!(cv[e] <= U)) break;
+            const float f = fp32_sqdist_rows(xq, X + (int64_t)ci[e] * ld, d);
+            topk_insert(topf, k, FAR ? -f : f, worstf);
+        }
+    }
+    const float t32 = warp_kth(topf, k, lane);
+    const float b_hi = __fadd_ru(__fdiv_ru(__fmul_ru(__fadd_ru(t32, tiny), eta_hi), eta_lo), tiny);
+    const float b_lo = __fsub_rd(__fdiv_rd(__fmul_rd(__fsub_rd(-t32, tiny), eta_lo), eta_hi), tiny);
+    double topd[kKMax];
+#pragma unroll
+    for (int i = 0; i < kKMax; ++i) topd[i] = INFINITY;
+    double worstd = INFINITY;
+    for (int l = lane; l < n_lists; l += 32) {
+        for (int i = 0; i < kTL; ++i) {
+            const int64_t e = (int64_t)l * kTL + i;
+            if (!(cv[e] <= U)) break;
+            const float* y = X + (int64_t)ci[e] * ld;
+            const float f = fp32_sqdist_rows(xq, y, d);
+            if (FAR ? !(f >= b_lo) : !(f <= b_hi)) continue;
+            const double e2 = exact_sqdist_rows(xq, y, d);
+            topk_insert(topd, k, FAR ? -e2 : e2, worstd);
+        }
+    }
+    const double kth = warp_kth(topd, k, lane);
+    if (lane == 0) out[qi] = __dsqrt_rn(FAR ? -kth : kth);
+}
+
+// Layout of the tensor-core screen's operand rows: points 0 .. n-1 in
+// order (tiles 0 .. Tp-1), then the queries (tiles Tp ..); one centre.
+__global__ void knn_layout_kernel(int64_t n, int64_t Tp, const int32_t* __restrict__ queries, int64_t q, int64_t T,
+                                  int32_t* __restrict__ row_pt, int32_t* __restrict__ tile_n,
+                                  int32_t* __restrict__ tile_cent)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t Rp = Tp * 128;
+    if (i < T * 128) {
+        int32_t pt = 0;
+        if (i < Rp) pt = i < n ? (int32_t)i : 0;
+        else if (i - Rp < q) pt = queries[i - Rp];
+        row_pt[i] = pt;
+    }
+    if (i < T) {
+        const int64_t left = i < Tp ? n - i * 128 : q - (i - Tp) * 128;
+        tile_n[i] = (int32_t)(left < 128 ? left : 128);
+        tile_cent[i] = 0;
+    }
+}
+
+// Centre of the screen's operands: the mean of up to 4096 evenly spaced rows
+// (any centre gives exact results; one near the data keeps |a| small).
+// Partial sums of 32-row groups (block: 32 columns x 8 row groups), then a
+// fixed-order sum per column.
+constexpr int kCentRows = 4096, kCentGroup = 32;
+
+__global__ void sample_sum_kernel(const float* __restrict__ X, int64_t n, int d, int64_t ld, int dp,
+                                  double* __restrict__ part)
+{
+    const int col = blockIdx.x * 32 + threadIdx.x;
+    const int grp = blockIdx.y * 8 + threadIdx.y;
+    const int64_t m = n < kCentRows ? n : kCentRows;
+    double sum = 0.0;
+    if (col < d)
+        for (int64_t i = (int64_t)grp * kCentGroup; i < m && i < (int64_t)(grp + 1) * kCentGroup; ++i)
+            sum += (double)X[(i * n / m) * ld + col];
+    if (col < dp) part[(int64_t)grp * dp + col] = sum;
+}
+
+__global__ void sample_centre_kernel(const double* __restrict__ part, int64_t n, int dp, float* __restrict__ c)
+{
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= dp) return;
+    const int64_t m = n < kCentRows ? n : kCentRows;
+    double sum = 0.0;
+    for (int g = 0; g < kCentRows / kCentGroup; ++g) sum += part[(int64_t)g * dp + col];
+    c[col] = (float)(sum / (double)m);
+}
+
+__global__ void gather_queries_kernel(const int32_t* __restrict__ queries, const int32_t* __restrict__ pos,
+                                      int64_t m, int32_t* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[i] = queries[pos[i]];
+}
+
+__global__ void scatter_out_kernel(const double* __restrict__ v, const int32_t* __restrict__ pos, int64_t m,
+                                   double* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[pos[i]] = v[i];
+}
+
+template <bool FAR>
+int knn_select(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* queries_dev, int64_t q, int32_t k,
+               double* out_dev, int num_sms, cudaStream_t s);
+
+#define KNN_TRY(expr)                                                                  \
+    do {                                                                               \
+        const cudaError_t e_ = (expr);                                                 \
+        if (e_ != cudaSuccess) {                                                       \
+            set_error(std::string("k-distance: ") + cudaGetErrorString(e_));           \
+            return e_ == cudaErrorMemoryAllocation ? MAPPER_ENOMEM : MAPPER_ECUDA;     \
+        }                                                                              \
+    } while (0)
+
+// The tensor-core screen: rows centred on the column means, three BF16
+// products per tile pair; per query the 16 smallest (FAR: largest) screened
+// values, a bound from the screen's absolute error, the exact FP64 distances
+// of the candidates; queries whose 16 values do not settle it go through the
+// CUDA-core screen.
+template <bool FAR>
+int knn_select_tc(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* queries_dev, int64_t q, int32_t k,
+                  double* out_dev, int num_sms, cudaStream_t s)
+{
+    const int dp = (d + 31) / 32 * 32;
+    const int64_t Tp = div_up(n, 128), Tq = div_up(q, 128), T = Tp + Tq, R = T * 128;
+    // FP32 re-screen of the candidates (the CUDA-core screen's bound)
+    const double eta = 1.5 * (d + 4) * std::ldexp(1.0, -24);
+    float eta_hi = (float)(1.0 + eta), eta_lo = (float)(1.0 - eta);
+    if ((double)eta_hi < 1.0 + eta) eta_hi = std::nextafter(eta_hi, INFINITY);
+    if ((double)eta_lo > 1.0 - eta) eta_lo = std::nextafter(eta_lo, 0.f);
+    const float tiny = (float)(3.0 * (d + 2) * std::ldexp(1.0, -149)) + FLT_TRUE_MIN;
+    const int sms = num_sms > 0 ? num_sms : 152;
+    // point chunks: fewest waves of one-CTA-per-SM tasks times items per
+    // task; nearest: lists over at most 4096 points each (a list must hold
+    // every candidate of its part), within 2 GB of lists
+    const int64_t ct_max = FAR ? Tp + 1 : 128;
+    const int64_t c_mem = std::max<int64_t>(1, (int64_t(2) << 30) / std::max<int64_t>(1, q * kParts * kTL * 8));
+    int64_t best_c = 0, best_ct = 0;
+    double best = 1e300;
+    for (int64_t c = 1; c <= std::max<int64_t>(1, std::min<int64_t>(Tp, 8192)); ++c) {
+        int64_t ct = div_up(Tp, c);
+        ct += ct & 1;
+        const int64_t cc = div_up(Tp, ct);
+        if (cc > c_mem && best_c) break;
+        const double cost = (double)div_up(Tq * cc, sms) * (double)(ct / 2 + 4) + (ct > ct_max ? 1e200 : 0.0);
+        if (cost < best) { best = cost; best_c = cc; best_ct = ct; }
+    }
+    if (Tq * best_c > INT32_MAX) {
+        set_error("k-distance: too many queries for one launch");
+        return MAPPER_EINVAL;
+    }
+    Buf cpart, cent, row_pt, tile_n, tile_cent, Ah, Al, rn2, rn, cv, ci, redo, n_redo, err;
+    KNN_TRY(cpart.alloc(sizeof(double) * (kCentRows / kCentGroup) * dp, s));
+    KNN_TRY(cent.alloc(sizeof(float) * dp, s));
+    KNN_TRY(row_pt.alloc(sizeof(int32_t) * R, s));
+    KNN_TRY(tile_n.alloc(sizeof(int32_t) * T, s));
+    KNN_TRY(tile_cent.alloc(sizeof(int32_t) * T, s));
+    KNN_TRY(Ah.alloc(sizeof(uint16_t) * (size_t)R * dp, s));
+    KNN_TRY(Al.alloc(sizeof(uint16_t) * (size_t)R * dp, s));
+    KNN_TRY(rn2.alloc(sizeof(float) * R, s));
+    KNN_TRY(rn.alloc(sizeof(float) * R, s));
+    const size_t nc = (size_t)q * best_c * kParts * kTL;
+    KNN_TRY(cv.alloc(sizeof(float) * nc, s));
+    KNN_TRY(ci.alloc(sizeof(int32_t) * nc, s));
+    KNN_TRY(redo.alloc(sizeof(int32_t) * q, s));
+    KNN_TRY(n_redo.alloc(sizeof(unsigned long long), s));
+    KNN_TRY(err.alloc(sizeof(int), s));
+    KNN_TRY(cudaMemsetAsync(n_redo.p, 0, sizeof(unsigned long long), s));
+    KNN_TRY(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    sample_sum_kernel<<<dim3((unsigned)div_up(dp, 32), kCentRows / kCentGroup / 8), dim3(32, 8), 0, s>>>(
+        X, n, d, ld, dp, cpart.as<double>());
+    sample_centre_kernel<<<div_up(dp, 128), 128, 0, s>>>(cpart.as<double>(), n, dp, cent.as<float>());
+    note_launch();
+    knn_layout_kernel<<<(unsigned)div_up(R, 256), 256, 0, s>>>(n, Tp, queries_dev, q, T, row_pt.as<int32_t>(),
+                                                               tile_n.as<int32_t>(), tile_cent.as<int32_t>());
+    note_launch(2);
+    KNN_TRY(cudaGetLastError());
+    KNN_TRY(centred_operands(X, ld, d, dp, row_pt.as<int32_t>(), tile_n.as<int32_t>(), tile_cent.as<int32_t>(),
+                             cent.as<float>(), T, Ah.p, Al.p, rn2.as<float>(), rn.as<float>(), s));
+    // error bound of s = |a|^2 + |b|^2 - 2 acc: the screen's constants, plus
+    // 4 units of the rounding of s in each term
+    double A1, A2, A3;
+    tc_bound(3, dp, 0.0, &A1, &A2, &A3);
+    const double v = std::ldexp(1.0, -24);
+    const float A1f = std::nextafter((float)(A1 + 4.0 * v), INFINITY);
+    const float A2f = std::nextafter((float)(A2 + 4.0 * v), INFINITY);
+    const float A3f = std::nextafter((float)A3, INFINITY);
+    int rc = tc_knn_screen(Ah.p, Al.p, rn2.as<float>(), rn.as<float>(), tile_n.as<int32_t>(), Tp, q, dp,
+                           (int)best_ct, (int)best_c, FAR, A1f, A2f, A3f, cv.as<float>(), ci.as<int32_t>(),
+                           err.as<int>(), s);
+    if (rc) return rc;
+    knn_merge_abs_kernel<FAR><<<(unsigned)div_up(q, 8), 256, 0, s>>>(
+        X, d, ld, queries_dev, q, (int)(best_c * kParts), cv.as<float>(), ci.as<int32_t>(), k, rn2.as<float>(),
+        rn.as<float>(), Tp * 128, A1f, A2f, A3f, eta_lo, eta_hi, tiny, out_dev, redo.as<int32_t>(),
+        n_redo.as<unsigned long long>());
+    note_launch();
+    KNN_TRY(cudaGetLastError());
+    unsigned long long h_redo = 0;
+    int h_err = 0;
+    KNN_TRY(cudaMemcpyAsync(&h_redo, n_redo.p, sizeof(h_redo), cudaMemcpyDeviceToHost, s));
+    KNN_TRY(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KNN_TRY(cudaStreamSynchronize(s));
+    if (h_err) {
+        set_error("k-distance: the tensor-core screen gave up waiting on a barrier");
+        return MAPPER_ETIMEOUT;
+    }
+    if (h_redo == 0) return MAPPER_OK;
+    // queries the 16 screened values did not settle: the CUDA-core screen
+    const int64_t m = (int64_t)h_redo;
+    Buf pts, tmp;
+    KNN_TRY(pts.alloc(sizeof(int32_t) * m, s));
+    KNN_TRY(tmp.alloc(sizeof(double) * m, s));
+    gather_queries_kernel<<<(unsigned)div_up(m, 256), 256, 0, s>>>(queries_dev, redo.as<int32_t>(), m,
+                                                                   pts.as<int32_t>());
+    note_launch();
+    KNN_TRY(cudaGetLastError());
+    if ((rc = knn_select<FAR>(X, n, d, ld, pts.as<int32_t>(), m, k, tmp.as<double>(), num_sms, s))) return rc;
+    scatter_out_kernel<<<(unsigned)div_up(m, 256), 256, 0, s>>>(tmp.as<double>(), redo.as<int32_t>(), m, out_dev);
+    note_launch();
+    KNN_TRY(cudaGetLastError());
+    return MAPPER_OK;
+}
+
 // k-th smallest (FAR: k-th largest) distance of each query row to the cloud.
 template <bool FAR>
 int knn_select(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* queries_dev, int64_t q, int32_t k,
@@ -463,9 +752,15 @@ int knn_select(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* 
 }  // namespace
 
 int knn_distance(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* queries_dev, int64_t q,
-                 int32_t k, double* out_dev, int num_sms, cudaStream_t s)
+                 int32_t k, double* out_dev, int num_sms, bool tensor_cores, cudaStream_t s)
 {
-    return knn_select<false>(X, n, d, ld, queries_dev, q, k, out_dev, num_sms, s);
+    if (q == 0) return MAPPER_OK;
+    if (k < 1 || k > kKMax || k > n) {
+        set_error("k must be in [1, min(16, n)]");
+        return MAPPER_EINVAL;
+    }
+    return tensor_cores && k <= kKnnList ? knn_select_tc<false>(X, n, d, ld, queries_dev, q, k, out_dev, num_sms, s)
+                                         : knn_select<false>(X, n, d, ld, queries_dev, q, k, out_dev, num_sms, s);
 }
 
 // L-infinity centrality filter f(x) = max_y d(x, y): the L-infinity norm of
@@ -473,7 +768,7 @@ int knn_distance(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t
 // after computing that matrix), the largest distance of every row to the
 // cloud, exact.
 int lens_ecc_inf(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j, int num_sms,
-                 cudaStream_t s)
+                 bool tensor_cores, cudaStream_t s)
 {
     if (n == 0) return MAPPER_OK;
     if (n > INT32_MAX) {
@@ -486,7 +781,8 @@ int lens_ecc_inf(const float* X, int64_t n, int32_t d, int64_t ld, double* f, in
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ENOMEM; }
     iota_kernel<<<(unsigned)div_up(n, 256), 256, 0, s>>>(n, qs.as<int32_t>());
     note_launch();
-    const int rc = knn_select<true>(X, n, d, ld, qs.as<int32_t>(), n, 1, tmp.as<double>(), num_sms, s);
+    const int rc = tensor_cores ? knn_select_tc<true>(X, n, d, ld, qs.as<int32_t>(), n, 1, tmp.as<double>(), num_sms, s)
+                                : knn_select<true>(X, n, d, ld, qs.as<int32_t>(), n, 1, tmp.as<double>(), num_sms, s);
     if (rc) return rc;
     e = cudaMemcpy2DAsync(f + j, sizeof(double) * m, tmp.p, sizeof(double), sizeof(double), (size_t)n,
                           cudaMemcpyDeviceToDevice, s);

@@ -297,15 +297,27 @@ __global__ void __launch_bounds__(256) lens_linf_kernel(const float* __restrict_
     }
 }
 
-__global__ void finite_kernel(const float* __restrict__ X, int64_t n, int32_t d, int64_t ld,
-                              int* flag)
+// One warp per row (grid-stride), lanes over columns, 16-byte loads when
+// the rows allow them.
+__global__ void __launch_bounds__(256) finite_kernel(const float* __restrict__ X, int64_t n, int32_t d, int64_t ld,
+                                                     bool vec, int* flag)
 {
-    const int64_t total = n * (int64_t)d;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     bool bad = false;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = i / d, c = i - r * d;
-        bad |= !isfinite(X[r * ld + c]);
+    for (int64_t r = w0; r < n; r += nw) {
+        const float* x = X + r * ld;
+        if (vec) {
+            const int d4 = d >> 2;
+            for (int c = lane; c < d4; c += 32) {
+                const float4 v = __ldg(reinterpret_cast<const float4*>(x) + c);
+                bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+            }
+            for (int c = 4 * d4 + lane; c < d; c += 32) bad |= !isfinite(__ldg(x + c));
+        } else {
+            for (int c = lane; c < d; c += 32) bad |= !isfinite(__ldg(x + c));
+        }
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
 }
@@ -513,6 +525,17 @@ cudaError_t lens_project(const float* X, int64_t n, int32_t d, int64_t ld, const
     return cudaGetLastError();
 }
 
+cudaError_t column_means(const float* X, int64_t n, int32_t d, int64_t ld, double* mu, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const int nblk = div_up(n, kMeanRows);
+    Buf part;
+    MGB_TRY(part.alloc(sizeof(double) * (size_t)nblk * d, s));
+    { col_partial_sum_kernel<<<nblk, 256, 0, s>>>(X, n, d, ld, part.as<double>()); note_launch(); }
+    { col_mean_kernel<<<div_up(d, 256), 256, 0, s>>>(part.as<double>(), nblk, d, n, mu); note_launch(); }
+    return cudaGetLastError();
+}
+
 // Eccentricity with exponent 2 (§3 and §4.1 name eccentricity among the
 // common filters): the mean squared distance from x to the cloud equals
 // |x - mu|^2 + mean_y |y - mu|^2 (mu the column means), so f(x) =
@@ -558,8 +581,9 @@ cudaError_t check_finite(const float* X, int64_t n, int32_t d, int64_t ld, int* 
                          cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    int blocks = (int)std::min<int64_t>(4096, div_up(n * (int64_t)d, 256));
-    { finite_kernel<<<blocks, 256, 0, s>>>(X, n, d, ld, flag); note_launch(); }
+    const int blocks = (int)std::min<int64_t>(152 * 8, div_up(n, 8));
+    const bool vec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
+    { finite_kernel<<<blocks, 256, 0, s>>>(X, n, d, ld, vec, flag); note_launch(); }
     return cudaGetLastError();
 }
 

@@ -64,6 +64,13 @@ struct TcParams {
     unsigned long long* queue_n;
     unsigned long long queue_cap;
     int* err;                                 // 1: a wait timed out
+    // k-distance screen (MODE 3): CTA t = (query tile t / kq_chunks, chunk t % kq_chunks)
+    // against point tiles chunk * kq_ct .. + kq_ct of the kq_tp point tiles; query
+    // tile u is operand tile kq_tp + u
+    int64_t kq_tp, kq_q;
+    int kq_ct, kq_chunks, kq_far;
+    float* kq_v;                              // lists: [((query * chunks + chunk) * 4 + part) * 16]
+    int32_t* kq_i;
 };
 
 // ------------------------------------------------------------------ PTX
@@ -178,6 +185,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v)
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
 // Barrier of the epilogue threads that also ORs a flag over them, so all
@@ -290,6 +308,7 @@ struct SmemTail {
     uint32_t colcore[2][4];                    // union pass: core columns, bit per column
     float red[2][8];                           // max |b|^2 and |b| of the columns, per warp
     __align__(16) float nbn[2][kT];            // -|b|^2 of the pair's columns
+    __align__(16) float nbr[2][kT];            // k-distance pass: |b| (rounded up) of the pair's columns
     uint32_t colmask[4][kT];                   // count pass: neighbour bits per column (by row quadrant)
     uint32_t rowmask[kT / 32][kT];             // neighbour bits per row (by 32-column chunk)
     int par[2][2 * kT];                        // union pass: local union-find / component
@@ -384,6 +403,20 @@ __device__ __forceinline__ void bfs_components(SmemTail& S, int buf, bool diag, 
     }
 }
 
+// k-distance lists: insert (v, j) into an ascending list (v below its last).
+constexpr int kKnnL = kKnnList;
+__device__ __forceinline__ void knn_insert(float (&lv)[kKnnL], int (&li)[kKnnL], float v, int j)
+{
+#pragma unroll
+    for (int i = kKnnL - 1; i > 0; --i) {
+        const bool sh = v < lv[i - 1];
+        const bool here = !sh && v < lv[i];
+        lv[i] = sh ? lv[i - 1] : (here ? v : lv[i]);
+        li[i] = sh ? li[i - 1] : (here ? j : li[i]);
+    }
+    if (v < lv[0]) { lv[0] = v; li[0] = j; }
+}
+
 template <int NS, int W>
 struct TcShape {
     // blocks per stage: W = 1: Ah, Bh (, Al, Bl); W = 2: Ah (, Al), Bh0, Bh1 (, Bl0, Bl1)
@@ -406,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
     constexpr int kStageBytes = TcShape<NS, W>::kStageBytes;
     constexpr int kAccCols = TcShape<NS, W>::kAccCols;
     const int64_t n_cap = W == 1 ? P.n_pairs : P.n_groups;
-    const int64_t n_items = P.n_dev ? min(n_cap, (int64_t)*P.n_dev) : n_cap;
+    const int64_t n_items = MODE == 3 ? 0 : (P.n_dev ? min(n_cap, (int64_t)*P.n_dev) : n_cap);
     auto group_at = [&](int64_t g) -> int2 { return W == 1 ? make_int2((int)g, -1) : P.groups[g]; };
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -414,6 +447,25 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const PassArgs& A = P.A;
     volatile int* abort = &S.abort;
+    // work items of this CTA: g_begin, g_begin + g_step, .. < g_end. MODE 3: the
+    // tile pairs (b, b + 1) of its chunk in order; else every gridDim-th group
+    const int64_t kq_ch = MODE == 3 ? blockIdx.x % P.kq_chunks : 0;
+    const int64_t kq_qt = MODE == 3 ? blockIdx.x / P.kq_chunks : 0;
+    const int64_t kq_bhi = MODE == 3 ? min(P.kq_tp, (kq_ch + 1) * P.kq_ct) : 0;
+    const int64_t g_begin = MODE == 3 ? 0 : blockIdx.x;
+    const int64_t g_step = MODE == 3 ? 1 : gridDim.x;
+    const int64_t g_end = MODE == 3 ? (kq_bhi > kq_ch * P.kq_ct ? (kq_bhi - kq_ch * P.kq_ct + 1) / 2 : 0) : n_items;
+    // tiles of item g: (A, B0, B1 or -1)
+    auto item = [&](int64_t g) -> int3 {
+        if (MODE == 3) {
+            const int64_t b0 = kq_ch * P.kq_ct + 2 * g;
+            return make_int3((int)(P.kq_tp + kq_qt), (int)b0, b0 + 1 < kq_bhi ? (int)(b0 + 1) : -1);
+        }
+        const int2 grp = group_at(g);
+        const int2 tp = A.pairs[grp.x];
+        const int tb1 = W == 2 && grp.y >= 0 ? (A.pairs[grp.y].y & kPairTileMask) : -1;
+        return make_int3(tp.x, tp.y & kPairTileMask, tb1);
+    };
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&S.tmem_base)),
@@ -445,12 +497,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             int stage = 0;
             uint32_t phase = 0;
             int issued = 0;
-            for (int64_t g = blockIdx.x; g < n_items && !*abort; g += gridDim.x) {
-                const int2 grp = group_at(g);
-                int2 tp = A.pairs[grp.x];
-                tp.y &= kPairTileMask;
+            for (int64_t g = g_begin; g < g_end && !*abort; g += g_step) {
+                const int3 itm = item(g);
+                const int2 tp = make_int2(itm.x, itm.y);
                 const bool diag = W == 1 && tp.x == tp.y;
-                const int tb1 = W == 2 && grp.y >= 0 ? (A.pairs[grp.y].y & kPairTileMask) : -1;
+                const int tb1 = itm.z;
                 const int nbt = tb1 >= 0 ? 2 : 1;
                 const uint32_t bytes = (uint32_t)((W == 1 ? (diag ? kOps / 2 : kOps)
                                                           : (NS == 3 ? 2 + 2 * nbt : 1 + nbt)) * kBlk);
@@ -499,12 +550,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             int stage = 0;
             uint32_t phase = 0;
             int it = 0;
-            for (int64_t g = blockIdx.x; g < n_items && !*abort; g += gridDim.x, ++it) {
-                const int2 grp = group_at(g);
-                int2 tp = A.pairs[grp.x];
-                tp.y &= kPairTileMask;
-                const bool diag = W == 1 && tp.x == tp.y;
-                const uint32_t idesc = W == 2 && grp.y >= 0 ? kIdesc2 : kIdesc;
+            for (int64_t g = g_begin; g < g_end && !*abort; g += g_step, ++it) {
+                const int3 itm = item(g);
+                const bool diag = W == 1 && itm.x == itm.y;
+                const uint32_t idesc = W == 2 && itm.z >= 0 ? kIdesc2 : kIdesc;
                 const int buf = it & 1;
                 const uint32_t acc_phase = (uint32_t)((it >> 1) & 1);
                 if (!mbar_wait(&S.acc_empty[buf], acc_phase ^ 1, abort)) break;
@@ -543,6 +592,81 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             mma_commit(&S.fin);
             volatile int dummy = 0;
             mbar_wait(&S.fin, 0, &dummy);
+        }
+    } else if constexpr (MODE == 3) {
+        // ------------------------------------- epilogue: k smallest distances
+        // Warp w holds TMEM lane quadrant (w & 3) = query rows 32 (w & 3) ..
+        // +31 and the 32-column part (w - 2) / 4 of every point tile; each
+        // thread keeps, over its part of the chunk, the kKnnL smallest lower
+        // bounds key - E of its query row with their points, where key = s =
+        // |a|^2 + |b|^2 - 2 acc (FAR: -s) and E = A1 |a||b| + A2 (|a|^2 +
+        // |b|^2) + A3 bounds |s - d^2| for this pair of rows.
+        const int et = tid - 64;
+        const int quad = warp & 3;
+        const int part = (warp - 2) >> 2;
+        const int r = quad * 32 + lane;
+        const int64_t qi = kq_qt * kT + r;
+        const bool valid_r = qi < P.kq_q;
+        const float na2 = P.rn2[(P.kq_tp + kq_qt) * kT + r];
+        const float nra = P.rn[(P.kq_tp + kq_qt) * kT + r];
+        float lv[kKnnL];
+        int li[kKnnL];
+#pragma unroll
+        for (int i = 0; i < kKnnL; ++i) { lv[i] = INFINITY; li[i] = -1; }
+        int it = 0, git = 0;
+        bool stop = false;
+        for (int64_t g = g_begin; g < g_end && !stop; g += g_step, ++git) {
+            const int3 itm = item(g);
+            const int nbt = itm.z >= 0 ? 2 : 1;
+            for (int h = 0; h < nbt; ++h, ++it) {
+                const int tb = h ? itm.z : itm.y;
+                const int64_t sb = (int64_t)tb * kT;
+                const int buf = it & 1, tbuf = git & 1;
+                const uint32_t acc_phase = (uint32_t)((git >> 1) & 1);
+                // (1) |b|^2 of the pair's columns, (2) the accumulator; the
+                // barrier also publishes (1)
+                if (et < kT) {
+                    S.nbn[buf][et] = P.rn2[sb + et];
+                    S.nbr[buf][et] = P.rn[sb + et];
+                }
+                const bool bad = (h == 0 && !mbar_wait(&S.acc_full[tbuf], acc_phase, abort)) || *abort;
+                if (epi_sync_or(bad)) { stop = true; break; }
+                tc_fence_after();
+                const int nb = A.tile_n[tb];
+                // 8 columns at a time (a compact loop body: the insertion is
+                // rare but long)
+#pragma unroll 1
+                for (int c8 = 0; c8 < 4; ++c8) {
+                    float v[8];
+                    tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) +
+                                 (uint32_t)(tbuf * kAccCols + h * kT + part * 32 + c8 * 8), v);
+                    if (c8 == 3 && h == nbt - 1) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&S.acc_empty[tbuf]);
+                    }
+                    const int j0 = part * 32 + c8 * 8;
+                    const float* nb2 = S.nbn[buf] + j0;
+                    const float* nbr = S.nbr[buf] + j0;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float sq = fmaf(-2.f, v[i], na2 + nb2[i]);
+                        const float E = __fmaf_ru(P.A1f, __fmul_ru(nra, nbr[i]),
+                                                  __fmaf_ru(P.A2f, __fadd_ru(na2, nb2[i]), P.A3f));
+                        const float key = __fsub_rd(P.kq_far ? -sq : sq, E);
+                        if (valid_r && j0 + i < nb && key < lv[kKnnL - 1])
+                            knn_insert(lv, li, key, (int)(sb + j0 + i));
+                    }
+                }
+            }
+        }
+        if (!stop && valid_r) {
+            const int64_t base = ((qi * P.kq_chunks + kq_ch) * 4 + part) * kKnnL;
+#pragma unroll
+            for (int i = 0; i < kKnnL; ++i) {
+                P.kq_v[base + i] = lv[i];
+                P.kq_i[base + i] = li[i];
+            }
         }
     } else {
         // ---------------------------------------------------- epilogue
@@ -1433,6 +1557,49 @@ int tc_wait_selftest(cudaStream_t s)
     }
     set_error("bounded-wait self-test: the wait did not run out");
     return MAPPER_EINTERNAL;
+}
+
+int tc_knn_screen(const void* Ah, const void* Al, const float* rn2, const float* rn, const int32_t* tile_n,
+                  int64_t Tp, int64_t q, int dp, int chunk_tiles, int chunks, bool far, float A1f, float A2f,
+                  float A3f, float* cand_v, int32_t* cand_i, int* err, cudaStream_t s)
+{
+    if (q == 0 || Tp == 0) return MAPPER_OK;
+    const int64_t Tq = (q + kT - 1) / kT;
+    const int64_t R = (Tp + Tq) * kT;
+    if (R >= (int64_t(1) << 30) || chunk_tiles < 2 || (chunk_tiles & 1) || chunks < 1 ||
+        Tq * chunks > INT32_MAX) {
+        set_error("k-distance tensor-core screen: sizes out of range");
+        return MAPPER_EINVAL;
+    }
+    CUtensorMap mh, ml;
+    if (!make_map(&mh, Ah, R, dp) || !make_map(&ml, Al, R, dp)) {
+        set_error("cuTensorMapEncodeTiled failed (or is unavailable)");
+        return MAPPER_ECUDA;
+    }
+    TcParams p{};
+    p.A.tile_n = tile_n;
+    p.A.dp = dp;
+    p.rn2 = rn2;
+    p.rn = rn;
+    p.nkb = (dp + kKB - 1) / kKB;
+    p.err = err;
+    p.A1f = A1f;
+    p.A2f = A2f;
+    p.A3f = A3f;
+    p.kq_tp = Tp;
+    p.kq_q = q;
+    p.kq_ct = chunk_tiles;
+    p.kq_chunks = chunks;
+    p.kq_far = far ? 1 : 0;
+    p.kq_v = cand_v;
+    p.kq_i = cand_i;
+    const cudaError_t e = launch<3, 3, 2>(mh, ml, p, (int)(Tq * chunks), s);
+    note_launch();
+    if (e != cudaSuccess) {
+        set_error(std::string("k-distance tensor-core screen: ") + cudaGetErrorString(e));
+        return MAPPER_ECUDA;
+    }
+    return MAPPER_OK;
 }
 
 int tc_groups(const int2* pairs, int64_t n, Buf* groups, Buf* pos, cudaStream_t s)

@@ -901,6 +901,20 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
     return MAPPER_OK;
 }
 
+cudaError_t centred_operands(const float* X, int64_t ld, int d, int dp, const int32_t* row_pt, const int32_t* tile_n,
+                             const int32_t* tile_cent, const float* cents, int64_t T, void* Ah, void* Al, float* rn2,
+                             float* rn, cudaStream_t s)
+{
+    if (T == 0) return cudaSuccess;
+    const float norm_infl = 1.0f + (float)(dp / 32 + 16) * 5.9604645e-8f;
+    const bool xvec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
+    operand_kernel<<<(unsigned)T, 256, 0, s>>>(nullptr, X, ld, xvec, row_pt, d, dp, tile_n, tile_cent, cents,
+                                               static_cast<__nv_bfloat16*>(Ah), static_cast<__nv_bfloat16*>(Al), rn2,
+                                               rn, norm_infl);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // Operands for tile pairs of one element but two segments (two centres):
 // rows centred on their element's centre (the row-weighted mean of its tile
 // centres), split as by operand_kernel. |a| is larger than with the segment

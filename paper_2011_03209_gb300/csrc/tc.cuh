@@ -45,6 +45,24 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
 int assign_pivots_tc(const float* X, int64_t n, int d, int64_t ld, int dp, const float* Pv, int K,
                      int num_sms, int32_t* piv, float* pd2, cudaStream_t s);
 
+// Entries per list of the k-distance tensor-core screen (k <= this).
+constexpr int kKnnList = 8;
+
+// k-distance screen on tensor cores: operand rows 0 .. 128 Tp are the points
+// (row = point index, tile_n marking the valid rows), rows 128 Tp .. the q
+// queries in order; all centred on one centre and split into BF16 hi + lo.
+// CTA (query tile u, chunk c) screens query tile u against point tiles
+// c chunk_tiles .. (c + 1) chunk_tiles - 1 (three products, N = 256 items of
+// two point tiles) and writes, per query row and 32-column part, the
+// kKnnList smallest lower bounds key - E of key = s = |a|^2 + |b|^2 - 2 acc
+// (FAR: -s), E = A1f |a||b| + A2f (|a|^2 + |b|^2) + A3f (rounded up), with
+// their points: cand_v / cand_i[((query * chunks + c) * 4 + part) * kKnnList
+// + i]. *err = 1 if a
+// bounded wait ran out. Returns a mapper_status.
+int tc_knn_screen(const void* Ah, const void* Al, const float* rn2, const float* rn, const int32_t* tile_n,
+                  int64_t Tp, int64_t q, int dp, int chunk_tiles, int chunks, bool far, float A1f, float A2f,
+                  float A3f, float* cand_v, int32_t* cand_i, int* err, cudaStream_t s);
+
 // Runs the passes' bounded mbarrier wait on a barrier that is never
 // completed: MAPPER_ETIMEOUT once it gives up (after 4 s), as designed.
 int tc_wait_selftest(cudaStream_t s);

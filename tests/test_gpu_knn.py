@@ -1,5 +1,6 @@
 """k-th nearest-neighbour distances on the GPU (§5's module for choosing
-eps): equal to the oracle's brute-force FP64 values bit for bit."""
+eps): equal to the oracle's brute-force FP64 values bit for bit, with either
+screen."""
 import numpy as np
 import pytest
 
@@ -12,9 +13,12 @@ mg = pytest.importorskip("paper_2011_03209_gb300")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=[1, 2], ids=["tensor-cores", "cuda-cores"])
+def ctx(request):
+    """Every test runs with both screens: BF16 tensor-core products (three per
+    tile pair) and the FP32 CUDA-core sums."""
     c = mg.Context(0)
+    c.set_knn_screen(request.param)
     yield c
     c.close()
 
@@ -113,3 +117,10 @@ def test_knn_distance_wide_rows(ctx):
     q = np.arange(300, dtype=np.int32)
     for k in (1, 2, 5):
         assert np.array_equal(mg.mapper_knn_distance(ctx, Xd, q, k), oracle.knn_distance(X, q, k))
+
+
+def test_knn_screen_rejects_bad_mode():
+    with mg.Context(0) as c:
+        for mode in (-1, 3):
+            with pytest.raises(mg.MapperError):
+                c.set_knn_screen(mode)

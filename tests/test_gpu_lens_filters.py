@@ -152,12 +152,14 @@ def test_density_lens_1m_d256_sampled(ctx):
     assert np.array_equal(f[rows], oracle.density_at(w.X, rows, w.eps))
 
 
+@pytest.mark.parametrize("prec", [mg.BF16, mg.FP32])
 @pytest.mark.parametrize("n,d,seed", [(1, 3, 0), (2, 5, 1), (300, 1500, 2), (3000, 64, 3), (5000, 17, 4)])
-def test_ecc_inf_lens_exact(ctx, n, d, seed):
+def test_ecc_inf_lens_exact(ctx, n, d, seed, prec):
     """L-infinity centrality max_y |x - y| equals the oracle's brute force bit
-    for bit (rows up to 1500 columns, as §5's gene-expression case)."""
+    for bit (rows up to 1500 columns, as §5's gene-expression case), through
+    the tensor-core screen (BF16) and the CUDA-core one (FP32)."""
     X = _cloud(n, d, seed)
-    got = _lens(ctx, X, (mg.LENS_ECC_INF,), (0,))[:, 0]
+    got = _lens(ctx, X, (mg.LENS_ECC_INF,), (0,), prec=prec)[:, 0]
     assert np.array_equal(got, oracle.lens_ecc_inf(X))
 
 
@@ -167,9 +169,10 @@ def test_ecc_inf_lens_far_duplicates_and_2d_graph(ctx):
     (L-infinity centrality, a column), as in §5, equals the oracle's."""
     X = _cloud(2500, 12, 7)
     X[100:140] = X[:, :].max(axis=0) * 3.0
-    got = _lens(ctx, X, (mg.LENS_ECC_INF, mg.LENS_COORD), (0, 2))
     ref = oracle.lens(X, (6, 1), (0, 2))
-    assert np.array_equal(got, ref)
+    for prec in (mg.BF16, mg.FP32):
+        got = _lens(ctx, X, (mg.LENS_ECC_INF, mg.LENS_COORD), (0, 2), prec=prec)
+        assert np.array_equal(got, ref)
     eps = _radius(X, 4, 7)
     prm = mg.params((mg.LENS_ECC_INF, mg.LENS_COORD), (0, 2), (8, 5), (0.65, 0.5), eps, 2, mg.BF16)
     g = mg.mapper_graph(ctx, torch.from_numpy(X).to("cuda:0"), prm)
