@@ -41,12 +41,12 @@ constexpr int kQ = 16;            // queries per CTA (one warp each)
 constexpr int kP = 32;            // points per tile (one per lane)
 constexpr int kKMax = 16;         // largest k
 
-template <class T>
-__device__ __forceinline__ void topk_insert(T (&top)[kKMax], int k, T v, T& worst)
+template <class T, int N>
+__device__ __forceinline__ void topk_insert(T (&top)[N], int k, T v, T& worst)
 {
     if (!(v < worst)) return;
 #pragma unroll
-    for (int i = 0; i < kKMax; ++i) {
+    for (int i = 0; i < N; ++i) {
         if (i < k && v < top[i]) {
             const T t = top[i];
             top[i] = v;
@@ -54,13 +54,13 @@ __device__ __forceinline__ void topk_insert(T (&top)[kKMax], int k, T v, T& wors
         }
     }
 #pragma unroll
-    for (int i = 0; i < kKMax; ++i)
+    for (int i = 0; i < N; ++i)
         if (i == k - 1) worst = top[i];
 }
 
 // k-th smallest of the warp's lane lists (each ascending, k entries)
-template <class T>
-__device__ __forceinline__ T warp_kth(T (&top)[kKMax], int k, int lane)
+template <class T, int N>
+__device__ __forceinline__ T warp_kth(T (&top)[N], int k, int lane)
 {
     T v = top[0];
     for (int r = 0; r < k; ++r) {
@@ -73,12 +73,31 @@ __device__ __forceinline__ T warp_kth(T (&top)[kKMax], int k, int lane)
         const unsigned owners = __ballot_sync(0xffffffffu, top[0] == m);
         if (lane == __ffs(owners) - 1) {
 #pragma unroll
-            for (int i = 0; i + 1 < kKMax; ++i) top[i] = top[i + 1];
-            top[kKMax - 1] = (T)INFINITY;
+            for (int i = 0; i + 1 < N; ++i) top[i] = top[i + 1];
+            top[N - 1] = (T)INFINITY;
         }
         v = m;
     }
     return v;
+}
+
+// The same sums with 16-byte loads (rows 16-byte aligned, d a multiple of 4):
+// columns still ascending, one rounding per operation.
+__device__ __forceinline__ double exact_sqdist_rows4(const float* __restrict__ x, const float* __restrict__ y, int d)
+{
+    double s = 0.0;
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    const float4* y4 = reinterpret_cast<const float4*>(y);
+    for (int k = 0; k < d / 4; ++k) {
+        const float4 a = x4[k], b = __ldg(y4 + k);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const double t = __dsub_rn((double)av[u], (double)bv[u]);
+            s = __dadd_rn(s, __dmul_rn(t, t));
+        }
+    }
+    return s;
 }
 
 __device__ __forceinline__ double exact_sqdist_rows(const float* __restrict__ x, const float* __restrict__ y, int d)
@@ -399,6 +418,25 @@ __global__ void iota_kernel(int64_t n, int32_t* __restrict__ v)
 
 // FP32 sum of squared differences of two rows, columns ascending (the chain
 // of the CUDA-core screen: relative error at most eta, subnormals below tiny).
+__device__ __forceinline__ float fp32_sqdist_rows4(const float* __restrict__ x, const float* __restrict__ y, int d)
+{
+    float s = 0.f;
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    const float4* y4 = reinterpret_cast<const float4*>(y);
+    for (int k = 0; k < d / 4; ++k) {
+        const float4 a = x4[k], b = __ldg(y4 + k);
+        float t = a.x - b.x;
+        s = fmaf(t, t, s);
+        t = a.y - b.y;
+        s = fmaf(t, t, s);
+        t = a.z - b.z;
+        s = fmaf(t, t, s);
+        t = a.w - b.w;
+        s = fmaf(t, t, s);
+    }
+    return s;
+}
+
 __device__ __forceinline__ float fp32_sqdist_rows(const float* __restrict__ x, const float* __restrict__ y, int d)
 {
     float s = 0.f;
@@ -414,9 +452,10 @@ __device__ __forceinline__ float fp32_sqdist_rows(const float* __restrict__ x, c
 // |b|^2) + A3 for that pair of rows, so u = l + 2E bounds it from above. The
 // k-th smallest exact key is at most U = the k-th smallest u over the lists,
 // and every point that can reach it has l <= U. Each list (kTL smallest l of a
-// 32-point part of a chunk) holds every point of its part below its last l,
-// so when U is below every list's last l the lists hold every candidate (else
-// the query goes to the fallback list). The candidates are then screened
+// 32-point part of a chunk) holds every point of its part below its last l;
+// the candidates are the entries below U of the lists whose last l exceeds U,
+// and every point of the parts whose list does not (the warp screens those
+// together). The candidates are then screened
 // again by their FP32 sums (relative error eta): with T32 the k-th smallest
 // of those keys, only candidates within B32 = (T32 + tiny)(1 + eta) / (1 - eta)
 // + tiny (FAR: the mirror bound) can hold the k-th exact key, and those few
@@ -431,9 +470,9 @@ __global__ void __launch_bounds__(256) knn_merge_abs_kernel(const float* __restr
                                                             const int32_t* __restrict__ cand_i, int k,
                                                             const float* __restrict__ rn2, const float* __restrict__ rn,
                                                             int64_t q_row0, float A1, float A2, float A3,
-                                                            float eta_lo, float eta_hi, float tiny,
-                                                            double* __restrict__ out, int32_t* __restrict__ redo,
-                                                            unsigned long long* __restrict__ n_redo)
+                                                            float eta_lo, float eta_hi, float tiny, int64_t n,
+                                                            int64_t Tp, int chunk_tiles, bool vec4,
+                                                            double* __restrict__ out)
 {
     const int lane = threadIdx.x & 31;
     const int64_t qi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -441,9 +480,9 @@ __global__ void __launch_bounds__(256) knn_merge_abs_kernel(const float* __restr
     const float* cv = cand_v + qi * (int64_t)n_lists * kTL;
     const int32_t* ci = cand_i + qi * (int64_t)n_lists * kTL;
     const float na2 = rn2[q_row0 + qi], nra = rn[q_row0 + qi];
-    float top[kKMax];
+    float top[kTL];
 #pragma unroll
-    for (int i = 0; i < kKMax; ++i) top[i] = INFINITY;
+    for (int i = 0; i < kTL; ++i) top[i] = INFINITY;
     float worst = INFINITY, mlast = INFINITY;
     for (int l = lane; l < n_lists; l += 32) {
         const int64_t e0 = (int64_t)l * kTL;
@@ -459,42 +498,55 @@ __global__ void __launch_bounds__(256) knn_merge_abs_kernel(const float* __restr
     const float U = warp_kth(top, k, lane);
 #pragma unroll
     for (int o = 16; o; o >>= 1) mlast = fminf(mlast, __shfl_xor_sync(0xffffffffu, mlast, o));
-    if (!(U < mlast)) {
-        if (lane == 0) redo[atomicAdd(n_redo, 1ull)] = (int32_t)qi;
-        return;
-    }
+    const bool all_complete = U < mlast;
     const float* xq = X + (int64_t)queries[qi] * ld;
-    // FP32 keys of the candidates: their k-th smallest
-    float topf[kKMax];
-#pragma unroll
-    for (int i = 0; i < kKMax; ++i) topf[i] = INFINITY;
-    float worstf = INFINITY;
-    for (int l = lane; l < n_lists; l += 32) {
-        for (int i = 0; i < kTL; ++i) {
-            const int64_t e = (int64_t)l * kTL + i;
-            if (!(cv[e] <= U)) break;
-            const float f = fp32_sqdist_rows(xq, X + (int64_t)ci[e] * ld, d);
-            topk_insert(topf, k, FAR ? -f : f, worstf);
+    // Visits every candidate once: entries below U of complete lists (lane
+    // by list), then all points of the incomplete lists' parts (the warp
+    // together, part by part).
+    auto for_candidates = [&](auto&& visit) {
+        for (int l = lane; l < n_lists; l += 32) {
+            if (!(cv[(int64_t)l * kTL + kTL - 1] > U)) continue;
+            for (int i = 0; i < kTL; ++i) {
+                const int64_t e = (int64_t)l * kTL + i;
+                if (!(cv[e] <= U)) break;
+                visit((int64_t)ci[e]);
+            }
         }
-    }
+        if (all_complete) return;
+        for (int l = 0; l < n_lists; ++l) {
+            if (cv[(int64_t)l * kTL + kTL - 1] > U) continue;
+            const int64_t c = l / kParts, part = l % kParts;
+            const int64_t b0 = c * chunk_tiles, b1 = min(Tp, b0 + chunk_tiles);
+            for (int64_t t = lane; t < (b1 - b0) * 32; t += 32) {
+                const int64_t j = (b0 + t / 32) * 128 + part * 32 + (t & 31);
+                if (j < n) visit(j);
+            }
+        }
+    };
+    // FP32 keys of the candidates: their k-th smallest
+    float topf[kTL];
+#pragma unroll
+    for (int i = 0; i < kTL; ++i) topf[i] = INFINITY;
+    float worstf = INFINITY;
+    for_candidates([&](int64_t j) {
+        const float* y = X + j * ld;
+        const float f = vec4 ? fp32_sqdist_rows4(xq, y, d) : fp32_sqdist_rows(xq, y, d);
+        topk_insert(topf, k, FAR ? -f : f, worstf);
+    });
     const float t32 = warp_kth(topf, k, lane);
     const float b_hi = __fadd_ru(__fdiv_ru(__fmul_ru(__fadd_ru(t32, tiny), eta_hi), eta_lo), tiny);
     const float b_lo = __fsub_rd(__fdiv_rd(__fmul_rd(__fsub_rd(-t32, tiny), eta_lo), eta_hi), tiny);
-    double topd[kKMax];
+    double topd[kTL];
 #pragma unroll
-    for (int i = 0; i < kKMax; ++i) topd[i] = INFINITY;
+    for (int i = 0; i < kTL; ++i) topd[i] = INFINITY;
     double worstd = INFINITY;
-    for (int l = lane; l < n_lists; l += 32) {
-        for (int i = 0; i < kTL; ++i) {
-            const int64_t e = (int64_t)l * kTL + i;
-            if (!(cv[e] <= U)) break;
-            const float* y = X + (int64_t)ci[e] * ld;
-            const float f = fp32_sqdist_rows(xq, y, d);
-            if (FAR ? !(f >= b_lo) : !(f <= b_hi)) continue;
-            const double e2 = exact_sqdist_rows(xq, y, d);
-            topk_insert(topd, k, FAR ? -e2 : e2, worstd);
-        }
-    }
+    for_candidates([&](int64_t j) {
+        const float* y = X + j * ld;
+        const float f = vec4 ? fp32_sqdist_rows4(xq, y, d) : fp32_sqdist_rows(xq, y, d);
+        if (FAR ? !(f >= b_lo) : !(f <= b_hi)) return;
+        const double e2 = vec4 ? exact_sqdist_rows4(xq, y, d) : exact_sqdist_rows(xq, y, d);
+        topk_insert(topd, k, FAR ? -e2 : e2, worstd);
+    });
     const double kth = warp_kth(topd, k, lane);
     if (lane == 0) out[qi] = __dsqrt_rn(FAR ? -kth : kth);
 }
@@ -549,23 +601,7 @@ __global__ void sample_centre_kernel(const double* __restrict__ part, int64_t n,
     c[col] = (float)(sum / (double)m);
 }
 
-__global__ void gather_queries_kernel(const int32_t* __restrict__ queries, const int32_t* __restrict__ pos,
-                                      int64_t m, int32_t* __restrict__ out)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) out[i] = queries[pos[i]];
-}
 
-__global__ void scatter_out_kernel(const double* __restrict__ v, const int32_t* __restrict__ pos, int64_t m,
-                                   double* __restrict__ out)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) out[pos[i]] = v[i];
-}
-
-template <bool FAR>
-int knn_select(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* queries_dev, int64_t q, int32_t k,
-               double* out_dev, int num_sms, cudaStream_t s);
 
 #define KNN_TRY(expr)                                                                  \
     do {                                                                               \
@@ -613,7 +649,7 @@ int knn_select_tc(const float* X, int64_t n, int32_t d, int64_t ld, const int32_
         set_error("k-distance: too many queries for one launch");
         return MAPPER_EINVAL;
     }
-    Buf cpart, cent, row_pt, tile_n, tile_cent, Ah, Al, rn2, rn, cv, ci, redo, n_redo, err;
+    Buf cpart, cent, row_pt, tile_n, tile_cent, Ah, Al, rn2, rn, cv, ci, err;
     KNN_TRY(cpart.alloc(sizeof(double) * (kCentRows / kCentGroup) * dp, s));
     KNN_TRY(cent.alloc(sizeof(float) * dp, s));
     KNN_TRY(row_pt.alloc(sizeof(int32_t) * R, s));
@@ -626,10 +662,7 @@ int knn_select_tc(const float* X, int64_t n, int32_t d, int64_t ld, const int32_
     const size_t nc = (size_t)q * best_c * kParts * kTL;
     KNN_TRY(cv.alloc(sizeof(float) * nc, s));
     KNN_TRY(ci.alloc(sizeof(int32_t) * nc, s));
-    KNN_TRY(redo.alloc(sizeof(int32_t) * q, s));
-    KNN_TRY(n_redo.alloc(sizeof(unsigned long long), s));
     KNN_TRY(err.alloc(sizeof(int), s));
-    KNN_TRY(cudaMemsetAsync(n_redo.p, 0, sizeof(unsigned long long), s));
     KNN_TRY(cudaMemsetAsync(err.p, 0, sizeof(int), s));
     sample_sum_kernel<<<dim3((unsigned)div_up(dp, 32), kCentRows / kCentGroup / 8), dim3(32, 8), 0, s>>>(
         X, n, d, ld, dp, cpart.as<double>());
@@ -655,33 +688,17 @@ int knn_select_tc(const float* X, int64_t n, int32_t d, int64_t ld, const int32_
     if (rc) return rc;
     knn_merge_abs_kernel<FAR><<<(unsigned)div_up(q, 8), 256, 0, s>>>(
         X, d, ld, queries_dev, q, (int)(best_c * kParts), cv.as<float>(), ci.as<int32_t>(), k, rn2.as<float>(),
-        rn.as<float>(), Tp * 128, A1f, A2f, A3f, eta_lo, eta_hi, tiny, out_dev, redo.as<int32_t>(),
-        n_redo.as<unsigned long long>());
+        rn.as<float>(), Tp * 128, A1f, A2f, A3f, eta_lo, eta_hi, tiny, n, Tp, (int)best_ct,
+        d % 4 == 0 && ld % 4 == 0 && ((uintptr_t)X & 15) == 0, out_dev);
     note_launch();
     KNN_TRY(cudaGetLastError());
-    unsigned long long h_redo = 0;
     int h_err = 0;
-    KNN_TRY(cudaMemcpyAsync(&h_redo, n_redo.p, sizeof(h_redo), cudaMemcpyDeviceToHost, s));
     KNN_TRY(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     KNN_TRY(cudaStreamSynchronize(s));
     if (h_err) {
         set_error("k-distance: the tensor-core screen gave up waiting on a barrier");
         return MAPPER_ETIMEOUT;
     }
-    if (h_redo == 0) return MAPPER_OK;
-    // queries the 16 screened values did not settle: the CUDA-core screen
-    const int64_t m = (int64_t)h_redo;
-    Buf pts, tmp;
-    KNN_TRY(pts.alloc(sizeof(int32_t) * m, s));
-    KNN_TRY(tmp.alloc(sizeof(double) * m, s));
-    gather_queries_kernel<<<(unsigned)div_up(m, 256), 256, 0, s>>>(queries_dev, redo.as<int32_t>(), m,
-                                                                   pts.as<int32_t>());
-    note_launch();
-    KNN_TRY(cudaGetLastError());
-    if ((rc = knn_select<FAR>(X, n, d, ld, pts.as<int32_t>(), m, k, tmp.as<double>(), num_sms, s))) return rc;
-    scatter_out_kernel<<<(unsigned)div_up(m, 256), 256, 0, s>>>(tmp.as<double>(), redo.as<int32_t>(), m, out_dev);
-    note_launch();
-    KNN_TRY(cudaGetLastError());
     return MAPPER_OK;
 }
 
