@@ -631,8 +631,9 @@ int knn_select_tc(const float* X, int64_t n, int32_t d, int64_t ld, const int32_
     const float tiny = (float)(3.0 * (d + 2) * std::ldexp(1.0, -149)) + FLT_TRUE_MIN;
     const int sms = num_sms > 0 ? num_sms : 152;
     // point chunks: fewest waves of one-CTA-per-SM tasks times items per
-    // task; nearest: lists over at most 4096 points each (a list must hold
-    // every candidate of its part), within 2 GB of lists
+    // task; nearest: lists over at most 4096 points each (longer chunks cut
+    // the epilogue's insertions but leave more parts whose list may miss a
+    // candidate, which the merge then screens whole), within 2 GB of lists
     const int64_t ct_max = FAR ? Tp + 1 : 128;
     const int64_t c_mem = std::max<int64_t>(1, (int64_t(2) << 30) / std::max<int64_t>(1, q * kParts * kTL * 8));
     int64_t best_c = 0, best_ct = 0;
