@@ -197,6 +197,8 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     ctx = mg.Context(local, stream=stream)
     ctx.set_timing(True)
+    if args.pass1_tile_n:
+        ctx.set_pass1_tile_n(args.pass1_tile_n)
     lens_kind = {"l2": w.lens_kind, "ecc": (mg.LENS_ECC,), "linf": (mg.LENS_LINF,),
                  "density": (mg.LENS_DENSITY,), "eccinf": (mg.LENS_ECC_INF,)}[args.lens]
     cover_kind = mg.COVER_BALANCED if args.cover == "balanced" else mg.COVER_UNIFORM
@@ -586,6 +588,9 @@ def main():
                          "the L2 filter")
     ap.add_argument("--cover", default="uniform", choices=["uniform", "balanced"],
                     help="clusters workload cover: uniform intervals (default) or balanced (equal counts)")
+    ap.add_argument("--pass1-tile-n", type=int, default=0, choices=[0, 128, 256],
+                    help="clusters workload: fix the pass-1 tensor-core product shape (0: the context's "
+                         "autotuner picks; a fixed shape keeps profiler runs on the same kernel)")
     ap.add_argument("--n", type=int, default=1_000_000,
                     help="points of the clustered cloud (smaller only for profiling runs)")
     args = ap.parse_args()
