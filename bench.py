@@ -50,6 +50,29 @@ def _traffic(kpairs, tile_pairs):
     return rec["bytes_per_tile_pair"] * tile_pairs
 
 
+def _bind_local_cpus(device: int):
+    """Run on the CPUs local to the GPU (sysfs local_cpulist of its PCI
+    device), so pinned host buffers land in the memory next to it and the
+    end-to-end copies run at that link's rate. Returns the CPU list, or None
+    when the topology is not readable."""
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(device)
+        path = "/sys/bus/pci/devices/%04x:%02x:%02x.0/local_cpulist" % (
+            getattr(p, "pci_domain_id", 0), p.pci_bus_id, p.pci_device_id)
+        cpus = set()
+        for part in open(path).read().strip().split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return sorted(cpus)
+    except (OSError, AttributeError, ValueError):
+        return None
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -192,6 +215,7 @@ def run_ours(args):
 
     prec = {"bf16": mg.BF16, "bf16x1": mg.BF16X1, "fp32": mg.FP32}[args.precision]
     w = synth.clusters_1m_d256(args.n)
+    local_cpus = _bind_local_cpus(local)
     Xh = torch.from_numpy(w.X).pin_memory()
     Xd = Xh.to(f"cuda:{local}")
     stream = torch.cuda.Stream()
@@ -315,7 +339,9 @@ def run_ours(args):
         "clocks": clocks,
         "gpu_launches": int(sum(s["n_launches"] for s in stats)),
         "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": int(w.X.nbytes),
-                "d2h_bytes_per_step": int(d2h)},
+                "d2h_bytes_per_step": int(d2h),
+                "host": (f"pinned input, process bound to the {len(local_cpus)} CPUs local to the GPU"
+                         if local_cpus else "pinned input, CPU placement left to the system")},
     }
     if rank == 0 and not args.no_cpu_baseline and args.lens == "l2" and args.cover == "uniform":
         gl = None
