@@ -124,3 +124,23 @@ def test_knn_screen_rejects_bad_mode():
         for mode in (-1, 3):
             with pytest.raises(mg.MapperError):
                 c.set_knn_screen(mode)
+
+
+@pytest.mark.parametrize("k", [7, 8, 9])
+def test_knn_distance_list_length_boundary(ctx, k):
+    """k up to 8 runs on the tensor-core screen's 8-entry lists, k = 9 on the
+    CUDA-core screen: both exact on either side of the switch."""
+    X = synth.gaussian_mixture(20_000, 40, 8, seed=99, centre_box=4.0, std_lo=0.3, std_hi=0.9,
+                               anisotropic=True, noise_frac=0.05)
+    q = np.random.default_rng(k).integers(0, X.shape[0], size=257).astype(np.int32)
+    got = mg.mapper_knn_distance(ctx, torch.from_numpy(X).to("cuda:0"), q, k)
+    assert np.array_equal(got, oracle.knn_distance(X, q, k))
+
+
+def test_knn_distance_k_equals_n(ctx):
+    """k = n: the largest distance from each point (the L-infinity centrality)."""
+    X = synth.tiny_random(16, 6, 12, scale=2.0)
+    q = np.arange(16, dtype=np.int32)
+    got = mg.mapper_knn_distance(ctx, torch.from_numpy(X).to("cuda:0"), q, 16)
+    assert np.array_equal(got, oracle.knn_distance(X, q, 16))
+    assert np.array_equal(got, oracle.lens_ecc_inf(X))
