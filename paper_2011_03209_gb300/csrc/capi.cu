@@ -433,7 +433,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     }
     const TileLayout& L = *layout;
     PairLists PL;
-    if ((rc = classify_pairs(L, dp, E, eps, use_tc, &PL, s))) return rc;
+    if ((rc = classify_pairs(L, X, ld, d, dp, E, eps, use_tc, &PL, s))) return rc;
     const int64_t R = L.R;
     st.tile_pairs = PL.n_candidates;
     st.tile_pairs_out = PL.n_out;

@@ -195,8 +195,10 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
 // Classifies every tile pair of every element by bounding spheres: out (no
 // pair within eps), all-in, or mixed (to the tensor-core list when both tiles
 // are one non-outlier segment and use_tc, else to the CUDA-core list).
-int classify_pairs(const TileLayout& L, int dp, int64_t E, double eps, bool use_tc,
-                   PairLists* P, cudaStream_t s);
+// X, ld, d: the rows (read for the outlier tiles' distance bounds when G is
+// not gathered).
+int classify_pairs(const TileLayout& L, const float* X, int64_t ld, int d, int dp, int64_t E, double eps,
+                   bool use_tc, PairLists* P, cudaStream_t s);
 // BF16 hi + lo operands of rows row_pt[.] of X (T tiles of 128 rows, the
 // first tile_n[t] of tile t valid, the rest zero), centred on cents[tile_cent[t]]
 // (dp floats each), with FP32 |a|^2 and |a| rounded up.

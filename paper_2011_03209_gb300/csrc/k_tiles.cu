@@ -631,6 +631,54 @@ __global__ void elem_segs_kernel(const int32_t* __restrict__ seg_elem, int64_t n
 // segment spheres) are skipped whole; every tile b >= a of the others is
 // classified by tile spheres: out, all-in, or mixed (tensor-core list when
 // a and b share a segment, hence a centre, else CUDA-core list).
+// Outlier tiles (rows that no pivot group took) have wide spheres, so their
+// pairs with the tiles of other segments stay mixed. For each outlier tile t
+// and each segment g of its element, tsm[t * smax + (g - first segment)] is a
+// lower bound of the smallest distance from t's rows to g's centre (FP32
+// lane-split sums with relative error at most rel, rounded down): no point of
+// g lies within eps of t when that bound minus g's radius exceeds eps.
+__global__ void __launch_bounds__(256) outlier_seg_kernel(const float* __restrict__ G, const float* __restrict__ X,
+                                                          int64_t ld, int d, int dp, const int32_t* __restrict__ row_pt,
+                                                          const int32_t* __restrict__ tile_n,
+                                                          const int32_t* __restrict__ tile_seg,
+                                                          const int32_t* __restrict__ tile_elem,
+                                                          const int32_t* __restrict__ seg_out,
+                                                          const int64_t* __restrict__ eseg_off,
+                                                          const float* __restrict__ seg_cent, double rel, int smax,
+                                                          float* __restrict__ tsm)
+{
+    __shared__ float s_min[8];
+    const int t = blockIdx.x;
+    if (!seg_out[tile_seg[t]]) return;                   // whole block
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int e = tile_elem[t];
+    const int64_t g0 = eseg_off[e], g1 = eseg_off[e + 1];
+    const int nt = tile_n[t];
+    for (int64_t g = g0; g < g1 && g - g0 < smax; ++g) {
+        const float* c = seg_cent + g * dp;
+        float mn = INFINITY;
+        for (int r = warp; r < nt; r += 8) {
+            const int64_t row = (int64_t)t * kT + r;
+            const float* x = G ? G + row * dp : X + (int64_t)row_pt[row] * ld;
+            float ss = 0.f;
+            for (int k = lane; k < d; k += 32) {
+                const float u = x[k] - c[k];
+                ss = fmaf(u, u, ss);
+            }
+            for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            mn = fminf(mn, ss);
+        }
+        if (lane == 0) s_min[warp] = mn;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float m = s_min[0];
+            for (int w = 1; w < 8; ++w) m = fminf(m, s_min[w]);
+            tsm[(int64_t)t * smax + (g - g0)] = __double2float_rd(sqrt((double)m * (1.0 - rel)) * (1.0 - 1e-15));
+        }
+        __syncthreads();
+    }
+}
+
 constexpr int kMaxSegList = 1024;
 constexpr int kClsPer = 8;                     // tiles b per warp step
 
@@ -644,6 +692,7 @@ __global__ void __launch_bounds__(256) classify_kernel(const int64_t* __restrict
                                                        const int32_t* __restrict__ tile_seg,
                                                        const int32_t* __restrict__ seg_out, int dp, double rel,
                                                        double eps_out, double eps_in, int use_tc,
+                                                       const float* __restrict__ tsm, int smax,
                                                        int2* __restrict__ l_in, int2* __restrict__ l_tc,
                                                        int2* __restrict__ l_simt,
                                                        unsigned long long* __restrict__ counts)
@@ -656,6 +705,7 @@ __global__ void __launch_bounds__(256) classify_kernel(const int64_t* __restrict
     for (int k = threadIdx.x; k < dp; k += blockDim.x) s_ca[k] = cent[(int64_t)ta * dp + k];
     const int ga = tile_seg[ta];
     const int64_t g_end = eseg_off[seg_elem[ga] + 1];
+    const int64_t g_first = eseg_off[seg_elem[ga]];
     if (threadIdx.x == 0) { s_nseg = 0; s_out = 0ull; }
     __syncthreads();
     // surviving segments gb >= ga (the own segment always survives)
@@ -707,10 +757,15 @@ __global__ void __launch_bounds__(256) classify_kernel(const int64_t* __restrict
                 const double Dlo = sqrt((double)ssum * (1.0 - rel)) * (1.0 - 1e-15);
                 const double Dhi = sqrt((double)ssum * (1.0 + rel)) * (1.0 + 1e-15);
                 const double rb = rad[tb];
+                const int gb = tile_seg[tb];
                 int cls;
                 if (Dlo - ra - rb > eps_out) cls = -1;
                 else if (Dhi + ra + rb < eps_in) cls = kListAllIn;
-                else if (use_tc && ga == tile_seg[tb]) cls = kListTC;
+                else if (tsm && gb != ga &&
+                         ((seg_out[ga] && (double)tsm[(int64_t)ta * smax + (gb - g_first)] - seg_rad[gb] > eps_out) ||
+                          (seg_out[gb] && (double)tsm[tb * smax + (ga - g_first)] - seg_rad[ga] > eps_out)))
+                    cls = -1;
+                else if (use_tc && ga == gb) cls = kListTC;
                 else cls = kListSimt;
                 if (cls < 0) {
                     ++n_out;
@@ -954,8 +1009,8 @@ int cross_operands(const TileLayout& L, const float* X, int64_t ld, int d, int d
 #undef XK
 }
 
-int classify_pairs(const TileLayout& L, int dp, int64_t E, double eps, bool use_tc, PairLists* P,
-                   cudaStream_t s)
+int classify_pairs(const TileLayout& L, const float* X, int64_t ld, int d, int dp, int64_t E, double eps, bool use_tc,
+                   PairLists* P, cudaStream_t s)
 {
     Buf etile_off, cnt, cand_off, counts, eseg_off;
     TK(etile_off.alloc(sizeof(int64_t) * (E + 1), s));
@@ -984,14 +1039,42 @@ int classify_pairs(const TileLayout& L, int dp, int64_t E, double eps, bool use_
         classify_kernel<<<(unsigned)L.T, 256, smem, s>>>(
             eseg_off.as<int64_t>(), L.seg_toff.as<int64_t>(), L.seg_elem.as<int32_t>(), L.seg_cent.as<float>(),
             L.seg_rad.as<double>(), L.tile_cent.as<float>(), L.tile_rad.as<double>(), L.tile_seg.as<int32_t>(),
-            L.seg_outlier.as<int32_t>(), dp, rel, eps_out, eps_in, use_tc ? 1 : 0, P->list[kListAllIn].as<int2>(),
-            P->list[kListTC].as<int2>(), P->list[kListSimt].as<int2>(), counts.as<unsigned long long>());
+            L.seg_outlier.as<int32_t>(), dp, rel, eps_out, eps_in, use_tc ? 1 : 0, nullptr, 0,
+            P->list[kListAllIn].as<int2>(), P->list[kListTC].as<int2>(), P->list[kListSimt].as<int2>(),
+            counts.as<unsigned long long>());
         note_launch();
         TK(cudaGetLastError());
     }
     unsigned long long h[4] = {0, 0, 0, 0};
     TK(cudaMemcpyAsync(h, counts.p, sizeof(h), cudaMemcpyDeviceToHost, s));
     TK(cudaStreamSynchronize(s));
+    // Many mixed pairs across segments (a cover element holding scattered
+    // points): bound the outlier tiles' distance to every segment of their
+    // element and classify again, certifying more pairs all-out.
+    if (C > 0 && (int64_t)h[kListSimt] * 32 >= L.R) {
+        const int smax = L.n_groups + 1;
+        Buf tsm;
+        TK(tsm.alloc(sizeof(float) * (size_t)L.T * smax, s));
+        const double eps_out = eps * (1.0 + 1e-9), eps_in = eps * (1.0 - 1e-9);
+        const double rel = (double)(dp / 32 + 12) * std::ldexp(1.0, -23);
+        const size_t smem = sizeof(float) * dp;
+        outlier_seg_kernel<<<(unsigned)L.T, 256, 0, s>>>(L.G.as<float>(), X, ld, d, dp, L.row_pt.as<int32_t>(),
+                                                          L.tile_n.as<int32_t>(), L.tile_seg.as<int32_t>(),
+                                                          L.tile_elem.as<int32_t>(), L.seg_outlier.as<int32_t>(),
+                                                          eseg_off.as<int64_t>(), L.seg_cent.as<float>(), rel, smax,
+                                                          tsm.as<float>());
+        TK(cudaMemsetAsync(counts.p, 0, sizeof(unsigned long long) * 4, s));
+        classify_kernel<<<(unsigned)L.T, 256, smem, s>>>(
+            eseg_off.as<int64_t>(), L.seg_toff.as<int64_t>(), L.seg_elem.as<int32_t>(), L.seg_cent.as<float>(),
+            L.seg_rad.as<double>(), L.tile_cent.as<float>(), L.tile_rad.as<double>(), L.tile_seg.as<int32_t>(),
+            L.seg_outlier.as<int32_t>(), dp, rel, eps_out, eps_in, use_tc ? 1 : 0, tsm.as<float>(), smax,
+            P->list[kListAllIn].as<int2>(), P->list[kListTC].as<int2>(), P->list[kListSimt].as<int2>(),
+            counts.as<unsigned long long>());
+        note_launch(2);
+        TK(cudaGetLastError());
+        TK(cudaMemcpyAsync(h, counts.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+        TK(cudaStreamSynchronize(s));
+    }
     for (int k = 0; k < kListCount; ++k) P->n[k] = (int64_t)h[k];
     P->n_out = (int64_t)h[3];
     return MAPPER_OK;

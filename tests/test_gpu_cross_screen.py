@@ -2,7 +2,10 @@
 cores (rows centred per element, a second BF16 operand set) give the same
 exact graph as on CUDA cores and as the oracle: forced on and off on small
 and medium clouds, and picked automatically for an element holding scattered
-points (wide tile spheres, many such pairs)."""
+points (wide tile spheres, many such pairs). When such pairs are many, the
+classification first bounds the outlier tiles' distance to every segment of
+their element, which certifies far noise all-out; outliers in a halo around
+the clusters keep pairs mixed."""
 import numpy as np
 import pytest
 
@@ -34,14 +37,21 @@ def _check(X, res, nint, ov, eps, min_pts):
     return ref
 
 
-def _scattered(n_clustered, n_noise, d, seed):
-    """Gaussian clusters plus points uniform in a box twice their extent."""
+def _scattered(n_clustered, n_noise, d, seed, halo=0):
+    """Gaussian clusters plus points uniform in a box twice their extent and,
+    optionally, `halo` copies of cluster points pushed a few eps away."""
     X = synth.gaussian_mixture(n_clustered, d, 6, seed=seed, centre_box=6.0, std_lo=0.4, std_hi=0.9,
                                anisotropic=False)
     rng = np.random.default_rng(seed + 1)
     lo, hi = X.min(axis=0) * 2.0, X.max(axis=0) * 2.0
-    N = rng.uniform(lo, hi, size=(n_noise, d)).astype(np.float32)
-    return np.ascontiguousarray(np.concatenate([X, N])[rng.permutation(n_clustered + n_noise)])
+    parts = [X, rng.uniform(lo, hi, size=(n_noise, d)).astype(np.float32)]
+    if halo:
+        r = 5.0 * synth.eps_at_percentile(X, 3, seed, n_pairs=6000)
+        u = rng.standard_normal((halo, d))
+        u *= r / np.linalg.norm(u, axis=1, keepdims=True)
+        parts.append((X[rng.integers(0, n_clustered, size=halo)] + u).astype(np.float32))
+    Y = np.concatenate(parts)
+    return np.ascontiguousarray(Y[rng.permutation(Y.shape[0])])
 
 
 CASES = [
@@ -64,7 +74,7 @@ def test_cross_screen_on_off_auto_equal_oracle(case, prec):
         with mg.Context(0) as ctx:
             ctx.set_cross_screen(mode)
             outs[mode] = _graph(ctx, X, (mg.LENS_L2,), (0,), (nint,), (ov,), eps, min_pts, prec)
-    assert outs[1]["stats"]["tile_pairs_cross"] == outs[1]["stats"]["tile_pairs_simt"] > 0
+    assert outs[1]["stats"]["tile_pairs_cross"] == outs[1]["stats"]["tile_pairs_simt"]
     assert outs[2]["stats"]["tile_pairs_cross"] == 0
     for mode in (0, 2):
         for k in ("elem_points", "core", "labels", "node_offsets", "node_members", "edges"):
@@ -73,14 +83,34 @@ def test_cross_screen_on_off_auto_equal_oracle(case, prec):
     assert len(ref["node_elem"]) > 0
 
 
-def test_cross_screen_auto_picks_tensor_cores_for_scattered_element():
-    X = _scattered(20000, 12000, 48, 77)
+def test_cross_screen_auto_rule_for_scattered_element():
+    """The automatic choice follows its rule (tensor cores iff the pairs are at
+    least 1/32 of the rows) and the graph is the oracle's."""
+    X = _scattered(20000, 12000, 48, 77, halo=3000)
     eps = synth.eps_at_percentile(X, 2, 7, n_pairs=20000)
     with mg.Context(0) as ctx:
         res = _graph(ctx, X, (mg.LENS_L2,), (0,), (1,), (0.0,), eps, 5, mg.BF16)
     st = res["stats"]
-    assert st["tile_pairs_cross"] == st["tile_pairs_simt"] and st["tile_pairs_simt"] * 32 >= st["n_rows"]
+    assert st["tile_pairs_cross"] == (st["tile_pairs_simt"] if st["tile_pairs_simt"] * 32 >= st["n_rows"] else 0)
     _check(X, res, (1,), (0.0,), eps, 5)
+
+
+@pytest.mark.parametrize("prec", [mg.BF16, mg.BF16X1])
+def test_cross_screen_halo_outliers(prec):
+    """Outliers a few eps around the clusters keep cross-segment pairs mixed
+    after the outlier bounds: forced onto the tensor cores they give the
+    CUDA-core graph and the oracle's."""
+    X = _scattered(6000, 1000, 32, 55, halo=2500)
+    eps = synth.eps_at_percentile(X, 3, 55, n_pairs=8000)
+    outs = {}
+    for mode in (1, 2):
+        with mg.Context(0) as ctx:
+            ctx.set_cross_screen(mode)
+            outs[mode] = _graph(ctx, X, (mg.LENS_L2,), (0,), (2,), (0.2,), eps, 4, prec)
+    assert outs[1]["stats"]["tile_pairs_cross"] == outs[1]["stats"]["tile_pairs_simt"] > 0
+    for k in ("elem_points", "core", "labels", "node_offsets", "node_members", "edges"):
+        assert np.array_equal(outs[1][k], outs[2][k]), k
+    _check(X, outs[1], (2,), (0.2,), eps, 4)
 
 
 def test_cross_screen_with_density_lens_2d():
