@@ -1,16 +1,28 @@
 // k_knn.cu -- k-th nearest-neighbour distances ("Mapper Interactive" §5,
 // "Visualizing Class Separation via Neuron Activations": a module plots the
 // distribution of the distances to the k-th nearest neighbours, k = 5, to
-// choose eps for DBSCAN).
+// choose eps for DBSCAN), and the farthest-point distance of the
+// L-infinity-centrality filter (§5), the same computation with the largest
+// distance.
 //
 // For each query point p, the k-th smallest distance d(p, y) over all points
 // y of the cloud, p itself included (distance 0): p is a core point of
 // DBSCAN(eps, k) on the whole cloud iff that distance is <= eps. The result is
 // the FP64 distance of the defining expression (double sum of squared
-// differences, k ascending, then sqrt), found in two streaming passes:
-//   A. FP32 squared distances (FMA sum of squared differences, relative error
-//      at most eta = 1.5 (d + 4) 2^-24 plus a subnormal term); each lane keeps
-//      its k smallest, the warp merges them: T = the k-th smallest FP32 value.
+// differences, k ascending, then sqrt). Two screens find it exactly:
+//
+// Tensor cores (k <= 8, knn_select_tc): rows centred on a sampled mean and
+// split into BF16 hi + lo, three products per tile pair in the count pass's
+// kernel (tc_kernel, MODE 3), whose epilogue keeps per query row and 32-point
+// part of each chunk the 8 smallest lower bounds s - E of the squared
+// distance (E bounds the screen's error for that pair of rows);
+// knn_merge_abs_kernel settles each query from those lists (its comment gives
+// the argument).
+//
+// CUDA cores (knn_select): FP32 squared distances (FMA sum of squared
+// differences, relative error at most eta = 1.5 (d + 4) 2^-24 plus a
+// subnormal term), then
+//   A. the k-th smallest FP32 value T;
 //   B. every point with FP32 value <= B = (T + tiny)(1 + eta) / (1 - eta) +
 //      tiny (rounded up) gets its exact FP64 squared distance; the k smallest
 //      of those are the k smallest overall: the k points behind T are within
@@ -24,8 +36,8 @@
 // whole cloud, so when the 16th of them exceeds B every point below B is in
 // it, and pass B reduces to the exact distances of at most 16 candidates per
 // query. Queries whose 16th value is within B (many near ties, or k = 16 with
-// a tie at the k-th value) take the two streaming passes below: one warp per
-// query, 16 queries per CTA, 32 points per shared-memory tile.
+// a tie at the k-th value) take the two streaming passes: one warp per query,
+// 16 queries per CTA, 32 points per shared-memory tile.
 #include <cfloat>
 #include <cmath>
 
