@@ -30,9 +30,13 @@
  *     of the plain FP64 definition below, whatever the screening precision.
  *
  * Definitions (the readings where the paper is silent are fixed here):
- *   lens      L2: f(x) = sqrt(sum_k x_k^2); COORD: f(x) = x_j; PCA: f(x) =
- *             sum_k (x_k - mu_k) v_k with v the j-th principal axis. Sums in
- *             double, k ascending, one rounding per operation.
+ *   lens      L2: f(x) = sqrt(sum_k x_k^2), the exact sum rounded once to
+ *             double, then a correctly rounded square root; COORD: f(x) = x_j;
+ *             PCA: f(x) = sum_k (x_k - mu_k) v_k with v the j-th principal
+ *             axis (double, k ascending, one rounding per operation); ECC:
+ *             sqrt(mean_y |x - y|^2); LINF: max_k |x_k|; DENSITY: the number
+ *             of points y with |x - y|^2 <= r*r (DBSCAN's distance); ECC_INF:
+ *             max_y |x - y| (the DBSCAN distance, exact).
  *   cover     n intervals over [lo, hi] = [min f, max f]:
  *             L = (hi-lo)/(n-(n-1)p), s = L(1-p), a_k = lo + k s,
  *             b_k = a_k + L, then a_0 = lo, b_{n-1} = hi and
