@@ -486,7 +486,10 @@ __global__ void __launch_bounds__(256) knn_merge_abs_kernel(const float* __restr
                                                             int64_t Tp, int chunk_tiles, bool vec4,
                                                             double* __restrict__ out)
 {
-    const int lane = threadIdx.x & 31;
+    constexpr int kCache = 8;                    // candidates cached per lane
+    __shared__ float c_f[8][kCache][32];
+    __shared__ int c_j[8][kCache][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t qi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (qi >= q) return;                         // whole warp
     const float* cv = cand_v + qi * (int64_t)n_lists * kTL;
@@ -540,10 +543,19 @@ __global__ void __launch_bounds__(256) knn_merge_abs_kernel(const float* __restr
 #pragma unroll
     for (int i = 0; i < kTL; ++i) topf[i] = INFINITY;
     float worstf = INFINITY;
+    int n_cached = 0;                            // this lane's candidates, kept for the last pass
+    bool spilled = false;
     for_candidates([&](int64_t j) {
         const float* y = X + j * ld;
         const float f = vec4 ? fp32_sqdist_rows4(xq, y, d) : fp32_sqdist_rows(xq, y, d);
         topk_insert(topf, k, FAR ? -f : f, worstf);
+        if (n_cached < kCache) {
+            c_f[wib][n_cached][lane] = f;
+            c_j[wib][n_cached][lane] = (int)j;
+            ++n_cached;
+        } else {
+            spilled = true;
+        }
     });
     const float t32 = warp_kth(topf, k, lane);
     const float b_hi = __fadd_ru(__fdiv_ru(__fmul_ru(__fadd_ru(t32, tiny), eta_hi), eta_lo), tiny);
@@ -552,13 +564,20 @@ __global__ void __launch_bounds__(256) knn_merge_abs_kernel(const float* __restr
 #pragma unroll
     for (int i = 0; i < kTL; ++i) topd[i] = INFINITY;
     double worstd = INFINITY;
-    for_candidates([&](int64_t j) {
-        const float* y = X + j * ld;
-        const float f = vec4 ? fp32_sqdist_rows4(xq, y, d) : fp32_sqdist_rows(xq, y, d);
+    auto decide = [&](int64_t j, float f) {
         if (FAR ? !(f >= b_lo) : !(f <= b_hi)) return;
+        const float* y = X + j * ld;
         const double e2 = vec4 ? exact_sqdist_rows4(xq, y, d) : exact_sqdist_rows(xq, y, d);
         topk_insert(topd, k, FAR ? -e2 : e2, worstd);
-    });
+    };
+    if (__any_sync(0xffffffffu, spilled)) {      // some lane's candidates did not fit: all again
+        for_candidates([&](int64_t j) {
+            const float* y = X + j * ld;
+            decide(j, vec4 ? fp32_sqdist_rows4(xq, y, d) : fp32_sqdist_rows(xq, y, d));
+        });
+    } else {
+        for (int t = 0; t < n_cached; ++t) decide(c_j[wib][t][lane], c_f[wib][t][lane]);
+    }
     const double kth = warp_kth(topd, k, lane);
     if (lane == 0) out[qi] = __dsqrt_rn(FAR ? -kth : kth);
 }
