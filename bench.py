@@ -69,7 +69,7 @@ def _bind_local_cpus(device: int):
             return None
         os.sched_setaffinity(0, cpus)
         return sorted(cpus)
-    except (OSError, AttributeError, ValueError):
+    except Exception:                            # no CUDA device, sysfs or attribute: leave placement alone
         return None
 
 
