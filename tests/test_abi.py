@@ -60,3 +60,31 @@ def test_null_and_bad_arguments_are_rejected_without_a_gpu(lib):
     assert lib.mapper_stats_get(None, None) == _capi.MAPPER_EINVAL
     lib.mapper_free(None)
     assert lib.mapper_last_error()
+
+
+def test_knobs_and_new_calls_reject_a_null_context_without_a_gpu(lib):
+    """The tuning knobs, the failure self-test and the extended lens call
+    validate their context before touching a device."""
+    from paper_2011_03209_gb300 import _capi
+    assert lib.mapper_set_pass1_tile_n(None, 0) == _capi.MAPPER_EINVAL
+    assert lib.mapper_set_cross_screen(None, 0) == _capi.MAPPER_EINVAL
+    assert lib.mapper_set_knn_screen(None, 0) == _capi.MAPPER_EINVAL
+    assert lib.mapper_selftest_wait(None) == _capi.MAPPER_EINVAL
+    assert lib.mapper_lens_ex(None, None, 0, 0, 0, 1, None, None, None, 1, None, None) == _capi.MAPPER_EINVAL
+    assert lib.mapper_knn_distance(None, None, 0, 0, 0, None, 0, 1, None) == _capi.MAPPER_EINVAL
+    assert lib.mapper_set_timing(None, 1) == _capi.MAPPER_EINVAL
+
+
+def test_footprint_counts_a_density_lens_without_a_gpu(lib):
+    """The footprint of a graph with a density filter covers the one-element
+    clustering of the whole cloud that computes it."""
+    import ctypes
+    from paper_2011_03209_gb300 import _capi
+    import paper_2011_03209_gb300 as mg
+    n, d = 1_000_000, 256
+    l2 = mg.params((mg.LENS_L2,), (0,), (100,), (0.2,), 20.0, 5, mg.BF16)
+    den = mg.params((mg.LENS_DENSITY,), (0,), (100,), (0.2,), 20.0, 5, mg.BF16, lens_param=(20.0,))
+    b_l2, b_den = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.mapper_graph_footprint(n, d, ctypes.byref(l2), ctypes.byref(b_l2)) == _capi.MAPPER_OK
+    assert lib.mapper_graph_footprint(n, d, ctypes.byref(den), ctypes.byref(b_den)) == _capi.MAPPER_OK
+    assert b_den.value >= b_l2.value > n * d * 4
