@@ -88,3 +88,41 @@ def test_footprint_counts_a_density_lens_without_a_gpu(lib):
     assert lib.mapper_graph_footprint(n, d, ctypes.byref(l2), ctypes.byref(b_l2)) == _capi.MAPPER_OK
     assert lib.mapper_graph_footprint(n, d, ctypes.byref(den), ctypes.byref(b_den)) == _capi.MAPPER_OK
     assert b_den.value >= b_l2.value > n * d * 4
+
+
+def test_header_compiles_as_c_and_links(lib, tmp_path):
+    """A plain C99 program includes include/mapper.h, links the library and
+    calls it without a GPU (version, error strings, argument checks): the
+    boundary is C, not C++."""
+    import shutil
+    import subprocess
+    from paper_2011_03209_gb300 import _capi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_abi.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include "mapper.h"
+int main(void) {
+    mapper_stats st;
+    size_t bytes = 0;
+    mapper_params p = {0};
+    if (mapper_abi_version() != MAPPER_ABI_VERSION) return 1;
+    if (mapper_graph(NULL, NULL, 0, 0, 0, NULL, NULL) != MAPPER_EINVAL) return 2;
+    if (mapper_stats_get(NULL, &st) != MAPPER_EINVAL) return 3;
+    p.m = 1; p.lens_kind[0] = MAPPER_LENS_L2; p.n_intervals[0] = 10; p.overlap[0] = 0.25;
+    p.eps = 1.0; p.min_pts = 5; p.precision = MAPPER_BF16; p.cover_kind = MAPPER_COVER_UNIFORM;
+    if (mapper_graph_footprint(1000, 16, &p, &bytes) != MAPPER_OK || bytes == 0) return 4;
+    printf("%s|%s\n", mapper_strerror(MAPPER_OK), mapper_strerror(MAPPER_ETIMEOUT));
+    return 0;
+}
+""")
+    exe = tmp_path / "use_abi"
+    libdir = os.path.dirname(_capi.LIB_PATH)
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-o", str(exe), "-L", libdir, "-lmapper_gb300", "-Wl,-rpath," + libdir],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    assert out.stdout.strip() == "ok|device wait timed out"
