@@ -12,6 +12,9 @@
  *   3. DBSCAN(eps, minPts) on the points of each cover element   (§3)
  *   4. the 1D nerve: nodes = clusters, edge iff two share a point (§3)
  * Steps 1-3 live here; step 4 and node numbering are in oracle/__init__.py.
+ * Beside the graph: further filters (eccentricity, L-infinity norm and
+ * centrality, density; §3, §4.1, §5) and the k-th nearest-neighbour distance
+ * of §5's module for choosing eps.
  *
  * Every step is written in its most direct form: brute-force O(n_i^2)
  * distances in double precision, breadth-first search for connected
