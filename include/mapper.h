@@ -202,6 +202,13 @@ int mapper_set_pass1_tile_n(mapper_ctx* ctx, int tile_n);
  * (default), 1 = always on the tensor cores (rows centred per element, a
  * second operand set), 2 = always on CUDA cores. Other values: MAPPER_EINVAL. */
 int mapper_set_cross_screen(mapper_ctx* ctx, int mode);
+/* Capacity of the tensor-core screen's band queue, in pairs (a tuning and
+ * testing knob; the paper has no counterpart and results do not depend on
+ * it): band pairs past the capacity are decided in FP64 inside the screen
+ * kernel instead of by the separate recheck. 0 = sized from the tile pairs
+ * (2^20 to 2^25 entries, the default); 1 .. 2^30 = that many entries.
+ * Other values: MAPPER_EINVAL. */
+int mapper_set_band_queue_cap(mapper_ctx* ctx, int64_t entries);
 /* Failure-detection self-test (the paper has no counterpart): runs the
  * bounded mbarrier wait of the tensor-core passes on a barrier that nothing
  * completes. Returns MAPPER_ETIMEOUT after the wait's limit (4 s), the status
@@ -402,13 +409,19 @@ int mapper_server_load(mapper_server* server, int* running, int* queued, size_t*
  * held by every GPU that loads the library until the process exits), so
  * sizes are limited: n <= MAPPER_NOALLOC_MAX_POINTS and
  * d <= MAPPER_NOALLOC_MAX_DIM; larger inputs return MAPPER_EINVAL before any
- * GPU work. The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it: make that first call before any
- * stream capture on that device. Every call shares the array and clears what
- * must start at zero itself; calls that overlap on the GPU (two streams, two
- * threads) race on it and must be ordered by the caller.
- * Errors: MAPPER_EINVAL (sizes, eps, minPts, null or non-device pointers),
- * MAPPER_ENONFINITE (X holds NaN/Inf), MAPPER_ECUDA. */
+ * GPU work. The first call in a CUDA context (normally the device's primary
+ * context) looks up the array's device address there (cudaGetSymbolAddress)
+ * and caches it under the context's unique id, so the address is valid for
+ * that context's lifetime and a context created again gets a new lookup:
+ * make the first call in a context before any stream capture. The call waits
+ * for its stream (it reads a status word back before returning). Every call
+ * shares the array and clears what must start at zero itself; calls that
+ * overlap on the GPU (two streams, two threads) race on it and must be
+ * ordered by the caller. A call that fails after queuing kernels waits for
+ * them before it returns.
+ * Errors: MAPPER_EINVAL (sizes, eps, minPts, a null X_dev or label_dev, or
+ * X_dev, label_dev or a non-null core_dev that is not device memory of the
+ * current device), MAPPER_ENONFINITE (X holds NaN/Inf), MAPPER_ECUDA. */
 #define MAPPER_NOALLOC_MAX_POINTS 8192
 #define MAPPER_NOALLOC_MAX_DIM 256
 int mapper_dbscan_noalloc(const float* X_dev, int64_t n, int32_t d, int64_t ld, double eps,

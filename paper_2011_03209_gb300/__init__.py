@@ -68,6 +68,11 @@ class Context:
         cores, 2 CUDA cores."""
         _capi.check(self._lib.mapper_set_cross_screen(self.h, int(mode)), "mapper_set_cross_screen")
 
+    def set_band_queue_cap(self, entries: int) -> None:
+        """Band-queue capacity in pairs (0: sized from the tile pairs, the
+        default); band pairs past it are decided inside the screen kernel."""
+        _capi.check(self._lib.mapper_set_band_queue_cap(self.h, int(entries)), "mapper_set_band_queue_cap")
+
     def close(self) -> None:
         if getattr(self, "h", None) is not None and self.h.value:
             self._lib.mapper_destroy(self.h)

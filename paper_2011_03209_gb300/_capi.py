@@ -28,7 +28,7 @@ FP32, BF16, BF16X1 = 0, 1, 2
 # every symbol include/mapper.h declares
 EXPORTS = (
     "mapper_create", "mapper_destroy", "mapper_set_stream", "mapper_set_timing", "mapper_set_pass1_tile_n",
-    "mapper_set_cross_screen", "mapper_selftest_wait", "mapper_set_knn_screen",
+    "mapper_set_cross_screen", "mapper_selftest_wait", "mapper_set_knn_screen", "mapper_set_band_queue_cap",
     "mapper_cover_subset", "mapper_nerve_from_nodes", "mapper_cover_balanced", "mapper_knn_distance",
     "mapper_lens", "mapper_lens_ex", "mapper_cover", "mapper_cover_sizes", "mapper_cover_copy",
     "mapper_cluster", "mapper_clusters_copy", "mapper_nerve", "mapper_graph",
@@ -144,6 +144,7 @@ def load(path: str | None = None):
             "mapper_set_cross_screen": (ctypes.c_int, [P, ctypes.c_int]),
             "mapper_selftest_wait": (ctypes.c_int, [P]),
             "mapper_set_knn_screen": (ctypes.c_int, [P, ctypes.c_int]),
+            "mapper_set_band_queue_cap": (ctypes.c_int, [P, i64]),
             "mapper_cover_subset": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.POINTER(P)]),
             "mapper_nerve_from_nodes": (ctypes.c_int, [P, ctypes.c_int64, ctypes.c_int64, P, P, P,
                                                        ctypes.POINTER(P)]),

@@ -74,6 +74,7 @@ struct mapper_ctx {
     int pass1_forced = 0;                      // 128 or 256: fixed by the caller
     int cross_mode = 0;                        // cross-segment pairs: 0 auto, 1 tensor cores, 2 CUDA cores
     int knn_mode = 0;                          // k-distance screen: 0 auto (tensor cores), 1 tensor, 2 CUDA cores
+    int64_t band_cap = 0;                      // band-queue entries (0: sized from the tile pairs)
 };
 
 struct mapper_cover_t {
@@ -518,8 +519,9 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         t.R = R;
         t.ns = precision == MAPPER_BF16X1 ? 1 : 3;
         t.num_sms = ctx->num_sms;
-        t.queue_cap = (unsigned long long)std::min<int64_t>(
-            int64_t(1) << 25, std::max<int64_t>(int64_t(1) << 20, 128 * PL.n[kListTC]));
+        t.queue_cap = ctx->band_cap > 0 ? (unsigned long long)ctx->band_cap
+                                        : (unsigned long long)std::min<int64_t>(
+                                              int64_t(1) << 25, std::max<int64_t>(int64_t(1) << 20, 128 * PL.n[kListTC]));
         CK(queue.alloc(sizeof(uint2) * t.queue_cap, s), "alloc band queue");
         CK(queue_n.alloc(sizeof(unsigned long long), s), "alloc");
         CK(tc_err.alloc(sizeof(int), s), "alloc");
@@ -950,6 +952,14 @@ int mapper_set_cross_screen(mapper_ctx* ctx, int mode)
     if (!ctx) return fail(MAPPER_EINVAL, "null context");
     if (mode < 0 || mode > 2) return fail(MAPPER_EINVAL, "mode must be 0, 1 or 2");
     ctx->cross_mode = mode;
+    return MAPPER_OK;
+}
+
+int mapper_set_band_queue_cap(mapper_ctx* ctx, int64_t entries)
+{
+    if (!ctx) return fail(MAPPER_EINVAL, "null context");
+    if (entries < 0 || entries > (int64_t(1) << 30)) return fail(MAPPER_EINVAL, "band queue entries must be in [0, 2^30]");
+    ctx->band_cap = entries;
     return MAPPER_OK;
 }
 

@@ -10,13 +10,20 @@
 // held in one file-scope device array of fixed size (about 8.6 MB, held by
 // every GPU that loads the library until the process exits).
 //
-// Use: the first call on a device (from the thread that makes it current)
-// looks up the array's device address with cudaGetSymbolAddress and caches
-// it; make that first call before any stream capture on that device. Every
-// call reuses the same array, so two calls that overlap on the GPU (on two
-// streams, or from two threads) race on it; calls must be ordered.
+// Use: the array's device address is looked up with cudaGetSymbolAddress
+// the first time a call runs in a CUDA context (normally the device's primary
+// context) and cached under that context's unique id, so a context that is
+// destroyed and created again (cudaDeviceReset, a released primary context)
+// gets a fresh lookup; a context whose id cannot be read is looked up on
+// every call. The first call in a context should come before any stream
+// capture. Every call reuses the same array, so two calls that overlap on
+// the GPU (on two streams, or from two threads) race on it; calls must be
+// ordered by the caller.
+#include <cuda.h>
+
 #include <climits>
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <string>
 
@@ -51,21 +58,64 @@ static_assert(sizeof(NaMeta) <= 256, "meta block");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_na_mutex;
-void* g_na_addr[kMaxDevices] = {};
+std::map<unsigned long long, void*> g_na_addr;     // context id -> the array's address there
 
-// Device address of the array on the current device (looked up once).
-cudaError_t scratch_address(int device, unsigned char** out)
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long*);
+
+// Unique id of the calling thread's current CUDA context (ids are never
+// reused within a process); false if it cannot be read.
+bool current_context_id(unsigned long long* id)
 {
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_addr[device]) {
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
         void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_na_addr[device] = p;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PfnCtxGetCurrent>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PfnCtxGetId>(p);
+    });
+    CUcontext ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of the array in the current context (looked up once per
+// context, or on every call when the context's id cannot be read).
+cudaError_t scratch_address(unsigned char** out)
+{
+    unsigned long long id = 0;
+    const bool keyed = current_context_id(&id);
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (keyed) {
+        auto it = g_na_addr.find(id);
+        if (it != g_na_addr.end()) {
+            *out = static_cast<unsigned char*>(it->second);
+            return cudaSuccess;
+        }
     }
-    *out = static_cast<unsigned char*>(g_na_addr[device]);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    if (keyed) g_na_addr[id] = p;
+    *out = static_cast<unsigned char*>(p);
+    return cudaSuccess;
+}
+
+// True if p is device (or managed) memory of `device`.
+cudaError_t on_device(const void* p, int device, bool* ok)
+{
+    cudaPointerAttributes attr{};
+    const cudaError_t e = cudaPointerGetAttributes(&attr, p);
+    if (e != cudaSuccess) return e;
+    *ok = (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) && attr.device == device;
     return cudaSuccess;
 }
 
@@ -139,22 +189,23 @@ extern "C" int mapper_dbscan_noalloc(const float* X_dev, int64_t n, int32_t d, i
 
     int device = 0;
     cudaError_t e = cudaGetDevice(&device);
-    if (e == cudaSuccess && (device < 0 || device >= kMaxDevices)) {
-        set_error("mapper_dbscan_noalloc: device index above 63");
-        return MAPPER_EINVAL;
+    const void* ptrs[3] = {X_dev, label_dev, core_dev};
+    const char* names[3] = {"X_dev", "label_dev", "core_dev"};
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+        if (!ptrs[i]) continue;
+        bool ok = false;
+        e = on_device(ptrs[i], device, &ok);
+        if (e == cudaSuccess && !ok) {
+            set_error(std::string("mapper_dbscan_noalloc: ") + names[i] + " is not device memory of the current device");
+            return MAPPER_EINVAL;
+        }
     }
-    cudaPointerAttributes attr{};
-    if (e == cudaSuccess) e = cudaPointerGetAttributes(&attr, X_dev);
     if (e != cudaSuccess) {
         set_error(std::string("mapper_dbscan_noalloc: ") + cudaGetErrorString(e));
         return MAPPER_ECUDA;
     }
-    if ((attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) || attr.device != device) {
-        set_error("mapper_dbscan_noalloc: X_dev is not device memory of the current device");
-        return MAPPER_EINVAL;
-    }
     unsigned char* base = nullptr;
-    if ((e = scratch_address(device, &base)) != cudaSuccess) {
+    if ((e = scratch_address(&base)) != cudaSuccess) {
         set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         return MAPPER_ECUDA;
     }
@@ -212,6 +263,9 @@ extern "C" int mapper_dbscan_noalloc(const float* X_dev, int64_t n, int32_t d, i
     }
     if (e != cudaSuccess) {
         set_error(std::string("mapper_dbscan_noalloc ") + where + ": " + cudaGetErrorString(e));
+        // kernels queued before the failure still use the shared array: let
+        // them finish so that a retry (on any stream) does not race with them
+        cudaStreamSynchronize(s);
         return MAPPER_ECUDA;
     }
     if (nonfinite) { set_error("X holds NaN or Inf"); return MAPPER_ENONFINITE; }

@@ -126,6 +126,19 @@ def test_many_empty_elements(ctx):
     assert_same_graph(X, res, (97,), (0.15,), 0.5, 3)
 
 
+def test_cover_rounding_gap_closed(ctx, golden_dir):
+    """The hand-worked case where rounding leaves b_k one ulp below a_{k+1}
+    (tests/golden/cover_intervals.json, "rounding_gap"): the device cover
+    closes the gap as the oracle does, so the point at a_{k+1} lies in both
+    elements."""
+    import json
+    import os
+    c = json.load(open(os.path.join(golden_dir, "cover_intervals.json")))["rounding_gap"]
+    lens = torch.tensor([[float.fromhex(x)] for x in c["lens"]], dtype=torch.float64, device="cuda:0")
+    offs, pts = mg.mapper_cover(ctx, lens, (c["n"],), (c["p"],)).numpy()
+    assert [pts[offs[e]:offs[e + 1]].tolist() for e in range(c["n"])] == c["elements"]
+
+
 @pytest.mark.parametrize("prec", PRECISIONS)
 @pytest.mark.parametrize("seed", [0, 1])
 def test_2d_cover(ctx, seed, prec):
@@ -374,6 +387,31 @@ def test_pass1_shapes_agree(prec):
     with mg.Context(0) as c:
         with pytest.raises(mg.MapperError):
             c.set_pass1_tile_n(64)
+
+
+@pytest.mark.parametrize("prec", [mg.BF16, mg.BF16X1])
+@pytest.mark.parametrize("cap", [1, 16])
+def test_band_queue_overflow_exact(prec, cap):
+    """A band queue far smaller than the band: the pairs past its capacity are
+    decided in FP64 inside the tensor-core kernels (count and union passes)
+    instead of by the recheck kernel, and the graph still equals the
+    oracle's."""
+    w = synth.mixture_100k(40_000)
+    Xd = torch.from_numpy(w.X).to("cuda:0")
+    prm = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, prec)
+    with mg.Context(0) as c:
+        c.set_band_queue_cap(cap)
+        g = mg.mapper_graph(c, Xd, prm)
+        st = g.stats()
+        assert st["tile_pairs_tc"] > 0 and st["band_pairs"] > 4 * cap
+        out = g.numpy()
+        out["lens"], out["pca"] = g.lens(w.n, 1)
+        out["elem_offsets"], out["elem_points"] = g.cover().numpy()
+        out["labels"], out["core"] = g.clusters().numpy(len(out["elem_points"]))
+        out["stats"] = st
+        with pytest.raises(mg.MapperError):
+            c.set_band_queue_cap(-1)
+    assert_same_graph(w.X, out, w.n_intervals, w.overlap, w.eps, w.min_pts)
 
 
 @pytest.mark.slow

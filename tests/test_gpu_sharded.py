@@ -1,12 +1,15 @@
 """Element sharding on the GPU: the elements of one cover split over 2 or 3
 shares (as ranks would hold them), each share clustered through a cover
 subset, the shares' nodes merged in element order and the nerve of the merged
-nodes computed by the library equal the single-call graph, node for node and
-edge for edge. The exchange between ranks is covered on CPU ranks
+nodes computed by the library equal the single-call graph and the FP64
+oracle's graph, node for node and edge for edge. The exchange between ranks is covered on CPU ranks
 (test_sharded_gloo.py); here the shares run one after the other on one GPU."""
+import functools
+
 import numpy as np
 import pytest
 
+import oracle
 from paper_2011_03209_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -14,6 +17,13 @@ mg = pytest.importorskip("paper_2011_03209_gb300")
 sharded = pytest.importorskip("paper_2011_03209_gb300.sharded")
 
 pytestmark = pytest.mark.gpu
+
+
+@functools.lru_cache(maxsize=2)
+def _oracle_graph(lens_bytes, shape):
+    w = synth.mixture_100k()
+    lens = np.frombuffer(lens_bytes, dtype=np.float64).reshape(shape)
+    return oracle.mapper_graph(w.X, lens, w.n_intervals, w.overlap, w.eps, w.min_pts)
 
 
 def _same(a, b):
@@ -38,8 +48,11 @@ def test_shares_merge_to_the_whole_graph(prec, world):
         pieces = [sharded.local_nodes(ctx, Xd, cover, p, w.eps, w.min_pts, prec) for p in parts]
         no, nm, ne = sharded.merge_nodes(pieces)
         g = mg.mapper_nerve_from_nodes(ctx, w.n, no, nm, ne).numpy()
+        lens_h = lens.cpu().numpy()
     assert len(whole["edges"]) > 0
     _same(g, whole)
+    # and the merged graph against the oracle's, given the same lens
+    _same(g, _oracle_graph(lens_h.tobytes(), lens_h.shape))
 
 
 @pytest.mark.parametrize("cover_kind", [mg.COVER_UNIFORM, mg.COVER_BALANCED])
@@ -52,7 +65,12 @@ def test_sharded_graph_single_process(cover_kind):
         whole = mg.mapper_graph(ctx, Xd, prm).numpy()
         g, mine = sharded.sharded_graph(ctx, Xd, prm)
         assert mine.size == len(np.unique(mine)) > 0
-        _same(g.numpy(), whole)
+        got = g.numpy()
+        _same(got, whole)
+        lens, _ = mg.mapper_lens(ctx, Xd, w.lens_kind, w.lens_arg)
+        lens_h = lens.cpu().numpy()
+    _same(got, oracle.mapper_graph(w.X, lens_h, w.n_intervals, w.overlap, w.eps, w.min_pts,
+                                   balanced=cover_kind == mg.COVER_BALANCED))
 
 
 def test_cover_subset_and_nodes_reject_bad_input():

@@ -188,6 +188,19 @@ def test_interval_bounds_golden(golden_dir):
     assert got == m["elements"]
 
 
+def test_interval_rounding_gap_is_closed(golden_dir):
+    """A case where rounding leaves b_k one ulp below a_{k+1}; the bounds are
+    compared bit for bit and the point at a_{k+1} must lie in both elements."""
+    c = json.load(open(os.path.join(golden_dir, "cover_intervals.json")))["rounding_gap"]
+    h = float.fromhex
+    a, b = oracle.interval_bounds(h(c["lo"]), h(c["hi"]), c["n"], c["p"])
+    assert [x.hex() for x in map(float, a)] == [h(x).hex() for x in c["a"]]
+    assert [x.hex() for x in map(float, b)] == [h(x).hex() for x in c["b"]]
+    lens = np.array([h(x) for x in c["lens"]])
+    offs, pts = oracle.cover(lens, [c["n"]], [c["p"]])
+    assert [pts[offs[e]:offs[e + 1]].tolist() for e in range(c["n"])] == c["elements"]
+
+
 @pytest.mark.parametrize("n_int,p", [(1, 0.0), (7, 0.0), (20, 0.3), (50, 0.25), (13, 0.6), (4, 0.95)])
 def test_cover_invariants(n_int, p):
     rng = np.random.default_rng(n_int)
