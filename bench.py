@@ -31,7 +31,7 @@ from paper_2011_03209_gb300 import synth  # noqa: E402
 
 LENS_NAMES = {"l2": "L2", "ecc": "eccentricity (exponent 2)", "linf": "L-infinity norm",
               "density": "density (points within eps)", "eccinf": "L-infinity centrality (max distance)"}
-METRIC = "mapper graph ms (1M x 256, exact graph)"
+METRIC = "mapper graph ms and eps-pair TFLOP/s at 1M\u00d7256, BF16-certified vs FP32, exact graph"
 GPU_FP32_LANES = 128                 # FP32 lanes per SM (Blackwell)
 
 
@@ -196,6 +196,94 @@ def run_reference(args):
     }))
 
 
+def _device_loop(ctx, stream, Xd, prm, steps, warmup, sampler=None, barrier=lambda: None):
+    """Device-resident graphs: `warmup` untimed calls, then `steps` calls
+    between two CUDA events on the context's stream. Returns (ms per graph,
+    per-call stats)."""
+    import torch
+    import paper_2011_03209_gb300 as mg
+
+    for _ in range(warmup):
+        g = mg.mapper_graph(ctx, Xd, prm)
+        g.numpy()
+        del g
+    torch.cuda.synchronize()
+    stats = []
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    if sampler is not None:
+        sampler.start()
+        time.sleep(0.3)
+    start.record(stream)
+    for _ in range(steps):
+        g = mg.mapper_graph(ctx, Xd, prm)
+        stats.append(g.stats())
+        del g
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return start.elapsed_time(end) / steps, stats
+
+
+def _e2e_loop(ctx, Xh, prm, steps, warmup, barrier=lambda: None):
+    """End to end through the public API: host X in (pinned), graph back on
+    the host, per call. Warm-up calls first (the first host-input call grows
+    the context's memory pool by the device copy of X). Returns (ms per
+    graph, bytes copied back per graph)."""
+    import torch
+    import paper_2011_03209_gb300 as mg
+
+    for _ in range(warmup):
+        g = mg.mapper_graph(ctx, Xh.numpy(), prm)
+        g.numpy()
+        del g
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(steps):
+        g = mg.mapper_graph(ctx, Xh.numpy(), prm)
+        out = g.numpy()
+        d2h = sum(a.nbytes for a in out.values())
+        del g
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) * 1e3 / steps, d2h
+
+
+def _roofline(prec, w, st, stats, n_sm):
+    """Roofline of the dominant kernel: the count pass (tensor cores for the
+    BF16 screens, CUDA cores for FP32), from its CUDA-event time in `stats`."""
+    import paper_2011_03209_gb300 as mg
+
+    kpairs = st["count_kernel_pairs"]
+    kms = float(np.mean([s["ms_count_kernel"] for s in stats]))
+    peaks, src = _peaks()
+    if prec == mg.FP32:
+        clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
+        peak = n_sm * GPU_FP32_LANES * 2 * clk / 1e12      # FP32 FFMA peak, TFLOP/s
+        achieved = 3.0 * w.d * kpairs / (kms * 1e-3) / 1e12
+        return kms, {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "simt_pass_kernel<1>: 3d FP32 flops (sub + FMA) per pair screened",
+                     "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flops x {clk / 1e6:.0f} MHz (max clock)"}
+    peak = peaks["bf16_tflops"]
+    achieved = 2.0 * w.d * kpairs / (kms * 1e-3) / 1e12
+    tp1 = st.get("tile_pairs_screen1", 0)
+    tp3 = st["tile_pairs_tc"] if not tp1 else st.get("tile_pairs_redo", 0)
+    ns = 1 if prec == mg.BF16X1 else 3
+    kp = -(-w.d // 64) * 64 * 128.0 * 128.0 * 2.0
+    executed = ((tp1 * kp + tp3 * 3 * kp) if tp1 else ns * kp * st["tile_pairs_tc"]) / (kms * 1e-3) / 1e12
+    desc = ("tc_kernel count pass (tcgen05 BF16): one product per tile pair, three products for the "
+            "tile pairs whose one-product band is not empty" if tp1 else
+            "tc_kernel<%d,1> (tcgen05 BF16 count pass): %d BF16 products per pair" % (ns, ns))
+    return kms, {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                 "frac": achieved / peak, "traffic": _traffic(kpairs, st["tile_pairs_tc"]),
+                 "kernel": desc + "; achieved counts 2d algorithmic flops per point pair screened",
+                 "executed_tflops": executed,
+                 "peak_source": f"{src} bf16_tflops (burst: the kernel's launches last a few ms)"}
+
+
 def run_ours(args):
     import torch
     import paper_2011_03209_gb300 as mg
@@ -213,6 +301,13 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     prec = {"bf16": mg.BF16, "bf16x1": mg.BF16X1, "fp32": mg.FP32}[args.precision]
     w = synth.clusters_1m_d256(args.n)
     local_cpus = _bind_local_cpus(local)
@@ -223,92 +318,36 @@ def run_ours(args):
     ctx.set_timing(True)
     if args.pass1_tile_n:
         ctx.set_pass1_tile_n(args.pass1_tile_n)
+    if args.screen:
+        ctx.set_pass1_screen(args.screen)
     lens_kind = {"l2": w.lens_kind, "ecc": (mg.LENS_ECC,), "linf": (mg.LENS_LINF,),
                  "density": (mg.LENS_DENSITY,), "eccinf": (mg.LENS_ECC_INF,)}[args.lens]
     cover_kind = mg.COVER_BALANCED if args.cover == "balanced" else mg.COVER_UNIFORM
-    prm = mg.params(lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, prec, cover_kind,
-                    lens_param=(w.eps,))
 
-    for _ in range(args.warmup):
-        g = mg.mapper_graph(ctx, Xd, prm)
-        last = g.numpy()
-        del g
-    torch.cuda.synchronize()
+    def params(p):
+        return mg.params(lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, p, cover_kind,
+                         lens_param=(w.eps,))
+
+    prm = params(prec)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
 
     # ---- device-resident timed region
     sampler = ClockSampler(local)
-    stats = []
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    time.sleep(0.3)
-    start.record(stream)
-    for _ in range(args.steps):
-        g = mg.mapper_graph(ctx, Xd, prm)
-        stats.append(g.stats())
-        del g
-    end.record(stream)
-    torch.cuda.synchronize()
-    barrier()
+    ms, stats = _device_loop(ctx, stream, Xd, prm, args.steps, args.warmup, sampler, barrier)
     clocks = sampler.stop()
-    ms = start.elapsed_time(end) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms)
 
     # ---- end to end through the public API: host X in, graph back on the host
-    # (warm-up calls first: the first host-input call grows the context's
-    # memory pool by the 1 GB device copy of X)
     ctx.set_timing(False)
-    for _ in range(args.warmup):
-        g = mg.mapper_graph(ctx, Xh.numpy(), prm)
-        g.numpy()
-        del g
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    d2h = 0
-    for _ in range(args.steps):
-        g = mg.mapper_graph(ctx, Xh.numpy(), prm)
-        out = g.numpy()
-        d2h = sum(a.nbytes for a in out.values())
-        del g
-    torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms, d2h = _e2e_loop(ctx, Xh, prm, args.steps, args.warmup, barrier)
+    e2e_ms = max_over_ranks(e2e_ms)
+    ctx.set_timing(True)
 
     st = stats[-1]
     pairs = st["pairs_screened"]                       # unordered pairs incl. self, pass 1
-    kpairs = st["count_kernel_pairs"]                  # ... of them screened by the main kernel
-    kms = float(np.mean([s["ms_count_kernel"] for s in stats]))
     eps_pair_flops = 2.0 * w.d * pairs
     pass1_ms = float(np.mean([s["ms_pass"][0] for s in stats]))
-    peaks, src = _peaks()
-    if prec == mg.FP32:
-        clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
-        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-        peak = n_sm * GPU_FP32_LANES * 2 * clk / 1e12      # FP32 FFMA peak, TFLOP/s
-        achieved = 3.0 * w.d * kpairs / (kms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "simt_pass_kernel<1>: 3d FP32 flops (sub + FMA) per pair screened",
-                "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flops x {clk / 1e6:.0f} MHz (max clock)"}
-    else:
-        peak = peaks["bf16_tflops_sustained"]
-        achieved = 2.0 * w.d * kpairs / (kms * 1e-3) / 1e12
-        ns = 1 if prec == mg.BF16X1 else 3
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": _traffic(kpairs, st["tile_pairs_tc"]),
-                "kernel": "tc_kernel<%d,1> (tcgen05 BF16 count pass): 2d algorithmic flops per pair "
-                          "screened; the kernel executes %d BF16 products per pair" % (ns, ns),
-                "executed_tflops": ns * 2.0 * (-(-w.d // 64) * 64) * 128.0 * 128.0 * st["tile_pairs_tc"]
-                                   / (kms * 1e-3) / 1e12,
-                "peak_source": f"{src} bf16_tflops_sustained (kernel timed inside a long step)"}
+    kms, roof = _roofline(prec, w, st, stats, n_sm)
 
     line = {
         "metric": METRIC, "value": ms / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
@@ -333,7 +372,8 @@ def run_ours(args):
                                         "tile_pairs_out", "tile_pairs_in", "tile_pairs_tc",
                                         "tile_pairs_simt", "union_pairs", "union_skipped", "pairs_screened",
                                         "band_pairs", "fp64_pairs", "near_ties", "n_core", "n_nodes", "n_edges",
-                                        "pass1_tile_n", "tile_pairs_cross")},
+                                        "pass1_tile_n", "tile_pairs_cross") + tuple(
+                                            k for k in ("tile_pairs_screen1", "tile_pairs_redo") if k in st)},
         "ms_tiles": float(np.mean([s["ms_tiles"] for s in stats])),
         "roofline": roof,
         "clocks": clocks,
@@ -343,6 +383,25 @@ def run_ours(args):
                 "host": (f"pinned input, process bound to the {len(local_cpus)} CPUs local to the GPU"
                          if local_cpus else "pinned input, CPU placement left to the system")},
     }
+    extras = (world == 1 and rank == 0 and not args.no_extras and args.lens == "l2" and args.cover == "uniform"
+              and prec != mg.FP32 and args.n == 1_000_000)
+    if extras:
+        # the plain FP32 CUDA-core path of the same pipeline (the comparison
+        # the metric names), device-resident and end to end
+        f_steps = max(1, min(args.steps, 5))
+        f_ms, f_stats = _device_loop(ctx, stream, Xd, params(mg.FP32), f_steps, 1)
+        ctx.set_timing(False)
+        f_e2e, _ = _e2e_loop(ctx, Xh, params(mg.FP32), f_steps, 1)
+        ctx.set_timing(True)
+        f_kms, f_roof = _roofline(mg.FP32, w, f_stats[-1], f_stats, n_sm)
+        line["fp32"] = {"value": f_ms, "unit": "ms", "steps": f_steps,
+                        "e2e": {"value": f_e2e, "unit": "ms"}, "count_kernel_ms": f_kms,
+                        "roofline": f_roof, "nodes": int(f_stats[-1]["n_nodes"]),
+                        "edges": int(f_stats[-1]["n_edges"])}
+        line["speedup_vs_fp32"] = f_ms / ms
+        line["e2e_speedup_vs_fp32"] = f_e2e / e2e_ms
+        line["same_graph_size_as_fp32"] = (int(f_stats[-1]["n_nodes"]) == int(st["n_nodes"]) and
+                                           int(f_stats[-1]["n_edges"]) == int(st["n_edges"]))
     if rank == 0 and not args.no_cpu_baseline and args.lens == "l2" and args.cover == "uniform":
         gl = None
         g = mg.mapper_graph(ctx, Xd, prm)
@@ -353,37 +412,43 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": cms, "unit": "ms", "cores": cores, "kind": "oracle",
                                 "sample": desc}
         line["exact_on_sample"] = exact
+    if extras:
+        line["small_configs"] = measure_small_configs(ctx, 10)
+    ctx.close()
+    if extras:
+        del Xd
+        torch.cuda.empty_cache()
+        line["sweep"] = measure_sweep(2, 1, prec, check_oracle=True)
+        line["serving"] = measure_serving(args.requests, 8, args.rate, args.slots, prec, big_X=w.X)
     if rank == 0:
         print(json.dumps(line))
-    ctx.close()
     if dist is not None:
         dist.destroy_process_group()
 
 
-def run_serving(args):
+def measure_serving(n_requests: int, warmup: int, rate: float, slots: int, prec, big_X=None) -> dict:
     """Serving mix: nine device-resident clouds, a seeded Poisson request
     stream (mean `rate` per second), requests admitted by device-memory
-    footprint into `slots` concurrent slots. Reports graphs/s and the
-    p50/p99 latency from submission to a finished graph."""
+    footprint into `slots` concurrent slots. Returns graphs/s and the
+    p50/p99 latency from submission to a finished graph. big_X: the
+    1M x 256 cloud when the caller holds it already."""
     import torch
     import paper_2011_03209_gb300 as mg
 
-    torch.cuda.set_device(0)
-    Xs = synth.serving_datasets(seed=4)
+    Xs = synth.serving_datasets(seed=4, big_X=big_X)
     samples = [synth.pair_sample(X, 4 + i) for i, X in enumerate(Xs)]
-    reqs = synth.serving_requests(samples, args.requests + args.warmup, args.rate, seed=4)
+    reqs = synth.serving_requests(samples, n_requests + warmup, rate, seed=4)
     Xd = [torch.from_numpy(X).to("cuda:0") for X in Xs]
-    prec = {"bf16": mg.BF16, "bf16x1": mg.BF16X1, "fp32": mg.FP32}[args.precision]
 
     def prm(r):
         return mg.params(r["lens_kind"], r["lens_arg"], r["n_intervals"], r["overlap"], r["eps"],
                          r["min_pts"], prec)
 
-    with mg.Server(0, n_slots=args.slots) as srv:
+    with mg.Server(0, n_slots=slots) as srv:
         ids = [srv.add_dataset(X) for X in Xd]
-        for r in reqs[:args.warmup]:                      # untimed: first calls, pool growth
+        for r in reqs[:warmup]:                           # untimed: first calls, pool growth
             srv.wait(srv.submit(ids[r["dataset"]], prm(r)))
-        timed = reqs[args.warmup:]
+        timed = reqs[warmup:]
         t_base = timed[0]["t"]
         sampler = ClockSampler(0)
         sampler.start()
@@ -394,76 +459,169 @@ def run_serving(args):
             if delay > 0:
                 time.sleep(delay)
             tickets.append(srv.submit(ids[r["dataset"]], prm(r)))
-        lat, runs, nodes = [], [], 0
+        lat, runs, queued, nodes = [], [], [], 0
         for t in tickets:
             g, info = srv.wait(t)
             lat.append(info["latency_s"] * 1e3)
             runs.append(info["run_s"] * 1e3)
+            queued.append(info["queue_s"] * 1e3)
             nodes += g.sizes()[0]
+            del g
         wall = time.perf_counter() - t0
         clocks = sampler.stop()
+    del Xd
     lat = np.asarray(lat)
-    print(json.dumps({
-        "metric": "serving graphs/s (9 resident clouds, Poisson stream)", "value": len(timed) / wall,
-        "unit": "graphs/s", "n_gpus": 1, "steps": len(timed), "warmup": args.warmup,
-        "higher_is_better": True, "dtype": "f32+f64" if prec == mg.FP32 else "bf16+f64", "data": "synthetic",
-        "config": {"workload": "serving_mix_9_clouds", "rate_per_s": args.rate, "slots": args.slots,
-                   "datasets": [list(X.shape) for X in Xs], "precision": args.precision},
-        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-        "mean_run_ms": float(np.mean(runs)), "max_ms": float(lat.max()), "nodes": int(nodes),
-        "wall_s": wall, "clocks": clocks,
-    }))
+    return {"graphs_per_s": len(timed) / wall, "requests": len(timed), "rate_per_s": rate, "slots": slots,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_run_ms": float(np.mean(runs)), "mean_queue_ms": float(np.mean(queued)),
+            "max_ms": float(lat.max()), "nodes": int(nodes), "wall_s": wall,
+            "datasets": [list(X.shape) for X in Xs], "clocks": clocks}
 
 
-def run_sweep(args):
-    """The 2D-lens sweep: 16 graphs (eps at 4 percentiles x 4 overlaps) of
-    the 500,000 x 128 Zipf mixture with a (PC1, PC2) lens on a 30 x 30 grid,
-    as one mapper_graph_sweep call; also timed as 16 mapper_graph calls."""
+def run_serving(args):
+    """The serving mix as its own JSON line (graphs/s, p50/p99 latency)."""
     import torch
     import paper_2011_03209_gb300 as mg
 
     torch.cuda.set_device(0)
-    w, eps, ov = synth.zipf_sweep()
     prec = {"bf16": mg.BF16, "bf16x1": mg.BF16X1, "fp32": mg.FP32}[args.precision]
+    r = measure_serving(args.requests, args.warmup, args.rate, args.slots, prec)
+    print(json.dumps({
+        "metric": "serving graphs/s (9 resident clouds, Poisson stream)", "value": r["graphs_per_s"],
+        "unit": "graphs/s", "n_gpus": 1, "steps": r["requests"], "warmup": args.warmup,
+        "higher_is_better": True, "dtype": "f32+f64" if prec == mg.FP32 else "bf16+f64", "data": "synthetic",
+        "config": {"workload": "serving_mix_9_clouds", "rate_per_s": args.rate, "slots": args.slots,
+                   "datasets": r["datasets"], "precision": args.precision},
+        **{k: r[k] for k in ("p50_ms", "p99_ms", "mean_run_ms", "mean_queue_ms", "max_ms", "nodes", "wall_s",
+                             "clocks")},
+    }))
+
+
+def measure_sweep(steps: int, warmup: int, prec, check_oracle: bool = False) -> dict:
+    """The 2D-lens sweep: 16 graphs (eps at 4 percentiles x 4 overlaps) of
+    the 500,000 x 128 Zipf mixture with a (PC1, PC2) lens on a 30 x 30 grid,
+    as one mapper_graph_sweep call; also timed as 16 mapper_graph calls.
+    check_oracle: compare the cover of the first graph and the DBSCAN of one
+    sampled element of every graph with the oracle."""
+    import torch
+    import paper_2011_03209_gb300 as mg
+
+    w, eps, ov = synth.zipf_sweep()
     Xd = torch.from_numpy(w.X).to("cuda:0")
     stream = torch.cuda.Stream()
+    exact = None
     with mg.Context(0, stream=stream) as ctx:
         base = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, eps[0], w.min_pts, prec)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             gs = mg.mapper_graph_sweep(ctx, Xd, base, eps, ov)
             del gs
         torch.cuda.synchronize()
-        sampler = ClockSampler(0)
-        sampler.start()
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         start.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             gs = mg.mapper_graph_sweep(ctx, Xd, base, eps, ov)
             nodes = [g.sizes()[0] for g in gs]
             tile_n = gs[0].stats()["pass1_tile_n"]
-            del gs
+            if _ < steps - 1:
+                del gs
         end.record(stream)
         torch.cuda.synchronize()
-        clocks = sampler.stop()
-        sweep_ms = start.elapsed_time(end) / args.steps
+        sweep_ms = start.elapsed_time(end) / steps
+        if check_oracle:
+            import oracle
+            rng = np.random.default_rng(7)
+            exact = True
+            for k, (g, e, p) in enumerate(zip(gs, eps, ov)):
+                offs, pts = g.cover().numpy()
+                lab, core = g.clusters().numpy(len(pts))
+                if k == 0:                      # the cover once (the others share its lens)
+                    lens, _ = g.lens(w.n, 2)
+                    ro, rp = oracle.cover(lens, w.n_intervals, (p, p))
+                    exact &= bool(np.array_equal(ro, offs) and np.array_equal(rp, pts))
+                sizes = np.diff(offs)
+                cand = np.nonzero((sizes > 0) & (sizes <= 4000))[0]
+                el = int(rng.choice(cand))
+                s0, t0 = offs[el], offs[el + 1]
+                _, rc, rl, _ = oracle.dbscan(w.X, pts[s0:t0], e, w.min_pts)
+                exact &= bool(np.array_equal(rc, core[s0:t0]) and np.array_equal(rl, lab[s0:t0]))
+        del gs
         start.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             for e, p in zip(eps, ov):
                 g = mg.mapper_graph(ctx, Xd, mg.params(w.lens_kind, w.lens_arg, w.n_intervals, (p, p), e,
                                                        w.min_pts, prec))
                 del g
         end.record(stream)
         torch.cuda.synchronize()
-        single_ms = start.elapsed_time(end) / args.steps
+        single_ms = start.elapsed_time(end) / steps
+    return {"workload": w.name + "_sweep16", "n": w.n, "d": w.d, "lens": "(PC1, PC2)", "grid": [30, 30],
+            "eps": eps, "overlap": ov, "min_pts": w.min_pts, "sweep_ms": sweep_ms,
+            "ms_per_graph": sweep_ms / len(eps), "single_calls_ms": single_ms,
+            "sweep_speedup": single_ms / sweep_ms, "pass1_tile_n": tile_n, "nodes": nodes,
+            "exact_on_sample": exact}
+
+
+def run_sweep(args):
+    """The 2D-lens sweep as its own JSON line."""
+    import torch
+    import paper_2011_03209_gb300 as mg
+
+    torch.cuda.set_device(0)
+    prec = {"bf16": mg.BF16, "bf16x1": mg.BF16X1, "fp32": mg.FP32}[args.precision]
+    sampler = ClockSampler(0)
+    sampler.start()
+    r = measure_sweep(args.steps, args.warmup, prec)
+    clocks = sampler.stop()
     print(json.dumps({
-        "metric": "sweep ms (16 graphs, 500k x 128, 2D lens, 30 x 30 grid)", "value": sweep_ms, "unit": "ms",
+        "metric": "sweep ms (16 graphs, 500k x 128, 2D lens, 30 x 30 grid)", "value": r["sweep_ms"], "unit": "ms",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
         "dtype": "f32+f64" if prec == mg.FP32 else "bf16+f64", "data": "synthetic",
-        "config": {"workload": w.name + "_sweep16", "n": w.n, "d": w.d, "lens": "(PC1, PC2)", "grid": [30, 30],
-                   "eps": eps, "overlap": ov, "min_pts": w.min_pts, "precision": args.precision},
-        "ms_per_graph": sweep_ms / len(eps), "single_calls_ms": single_ms,
-        "sweep_speedup": single_ms / sweep_ms, "pass1_tile_n": tile_n, "nodes": nodes, "clocks": clocks,
+        "config": {k: r[k] for k in ("workload", "n", "d", "lens", "grid", "eps", "overlap", "min_pts")}
+        | {"precision": args.precision},
+        **{k: r[k] for k in ("ms_per_graph", "single_calls_ms", "sweep_speedup", "pass1_tile_n", "nodes")},
+        "clocks": clocks,
     }))
+
+
+def measure_small_configs(ctx, steps: int) -> dict:
+    """The two configurations the oracle finishes in full: 5,000 x 8 (blobs
+    and a circle, L2 lens) and 100,000 x 64 (16 anisotropic Gaussians, PC1
+    lens). Per configuration: the device-resident graph time, the oracle's
+    whole graph (lens, cover, DBSCAN of every element, nerve) timed on the
+    host cores, and whether the two graphs are equal."""
+    import torch
+    import oracle
+    import paper_2011_03209_gb300 as mg
+
+    out = {}
+    for w in (synth.blobs_circle_5k(), synth.mixture_100k()):
+        Xd = torch.from_numpy(w.X).to(f"cuda:{ctx.device}")
+        prm = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, mg.BF16)
+        for _ in range(3):
+            g = mg.mapper_graph(ctx, Xd, prm)
+            del g
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            g = mg.mapper_graph(ctx, Xd, prm)
+            got = g.numpy()
+            if _ < steps - 1:
+                del g
+        gpu_ms = (time.perf_counter() - t0) * 1e3 / steps
+        lens, pca = g.lens(w.n, len(w.lens_kind))
+        del g
+        t0 = time.perf_counter()
+        f = oracle.lens(w.X, w.lens_kind, w.lens_arg)
+        ref_own = oracle.mapper_graph(w.X, f, w.n_intervals, w.overlap, w.eps, w.min_pts)
+        cpu_ms = (time.perf_counter() - t0) * 1e3
+        ref = oracle.mapper_graph(w.X, lens, w.n_intervals, w.overlap, w.eps, w.min_pts)
+        exact = all(np.array_equal(got[k], ref[k]) for k in ("node_offsets", "node_members", "node_elem", "edges"))
+        out[w.name] = {"gpu_ms": gpu_ms, "oracle_ms": cpu_ms, "oracle_cores": oracle.num_threads(),
+                       "exact": bool(exact), "near_ties": int(ref["near_ties"]),
+                       "nodes": int(len(got["node_elem"])), "edges": int(len(got["edges"])),
+                       "oracle_nodes_own_lens": int(len(ref_own["node_elem"])),
+                       "timing": "host wall clock around mapper_graph + copy-out, mean of %d" % steps}
+    return out
 
 
 def run_knn(args):
@@ -600,6 +758,13 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=12.0,
                     help="seconds of oracle DBSCAN per reference sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="clusters workload: skip the FP32 arm, the small configurations, the sweep and the "
+                         "serving sub-objects (profiling runs)")
+    ap.add_argument("--screen", type=int, default=0, choices=[0, 1, 2],
+                    help="clusters workload, BF16: pass-1 screen (0: the library default, 1: one product "
+                         "first and three products for the tile pairs whose band is not empty, 2: three "
+                         "products everywhere)")
     ap.add_argument("--workload", default="clusters", choices=["clusters", "serving", "sweep", "sharded", "knn"],
                     help="clusters: the 1M x 256 graph (default; N ranks = N replicas); serving: the "
                          "request mix; sweep: 16 graphs of the 500k x 128 2D-lens cloud; sharded: the "

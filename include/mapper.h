@@ -63,7 +63,7 @@
 extern "C" {
 #endif
 
-#define MAPPER_ABI_VERSION 4
+#define MAPPER_ABI_VERSION 5
 
 typedef enum mapper_status {
     MAPPER_OK = 0,
@@ -73,7 +73,8 @@ typedef enum mapper_status {
     MAPPER_ETIMEOUT = -4,    /* a bounded device-side wait ran out */
     MAPPER_ENONFINITE = -5,  /* X holds NaN or Inf */
     MAPPER_EINTERNAL = -6,   /* a device-side consistency check failed */
-    MAPPER_ENOTIMPL = -7     /* option not built in this library */
+    MAPPER_ENOTIMPL = -7,    /* option not built in this library */
+    MAPPER_ECANCELED = -8    /* a queued server request dropped by mapper_server_destroy */
 } mapper_status;
 
 typedef enum mapper_lens_kind {
@@ -177,6 +178,10 @@ typedef struct mapper_stats {
                                   element), those screened on the tensor cores with rows
                                   centred per element: all of them when they are at least
                                   1/32 of the rows (BF16 precisions), else none */
+    int64_t tile_pairs_screen1;  /* MAPPER_BF16 two-phase count pass: tile pairs screened first
+                                    with one product (hi.hi); 0 when every pair took three */
+    int64_t tile_pairs_redo;     /* ... of them, the tile pairs with a pair inside the
+                                    one-product band, screened again with three products */
 } mapper_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -196,6 +201,13 @@ int mapper_set_timing(mapper_ctx* ctx, int enabled);
  * work item, 256 = two tile pairs sharing their first tile. Other values:
  * MAPPER_EINVAL. */
 int mapper_set_pass1_tile_n(mapper_ctx* ctx, int tile_n);
+/* Count-pass screen of MAPPER_BF16 (a tuning knob; results do not depend on
+ * it): 0 = the default (1), 1 = two phases: every tile pair first with one
+ * product (hi.hi, the band of MAPPER_BF16X1); the tile pairs that have a pair
+ * inside that band are counted by a second pass with three products, the
+ * others are final after the first, 2 = three products for every tile pair.
+ * Other values: MAPPER_EINVAL. */
+int mapper_set_pass1_screen(mapper_ctx* ctx, int mode);
 /* Where the BF16 precisions screen mixed tile pairs across two segments of
  * one element (a tuning knob; results do not depend on it): 0 = on the
  * tensor cores when they are at least 1/32 of the rows, else on CUDA cores
@@ -214,6 +226,17 @@ int mapper_set_band_queue_cap(mapper_ctx* ctx, int64_t entries);
  * completes. Returns MAPPER_ETIMEOUT after the wait's limit (4 s), the status
  * a pass reports when a wait runs out; the context stays usable. */
 int mapper_selftest_wait(mapper_ctx* ctx);
+/* Accumulation self-test of the tensor-core screen (the paper has no
+ * counterpart): random BF16 rows (magnitudes 2^-4 .. 2^5, random signs) of
+ * row pitch dp (a multiple of 32 in [32, 4096]) through the screen's tcgen05
+ * products (1: hi.hi, 3: hi.hi + hi.lo + lo.hi) for four 128 x 128 tile
+ * pairs. *observed = the largest |accumulator - exact sum| over them,
+ * relative to the sum of the magnitudes of the products; *modelled = the
+ * accumulation term the screen's error bound assumes, relative to the same
+ * sum (dp / 16 * products steps of 2^-22 each, times (1 + 2u')^2). The bound
+ * is sound on this hardware only if observed stays below modelled. */
+int mapper_selftest_mma_error(mapper_ctx* ctx, int32_t dp, int32_t products, uint64_t seed, double* observed,
+                              double* modelled);
 /* Screen of mapper_knn_distance (a tuning knob; results do not depend on
  * it): 0 = tensor cores (default), 1 = tensor cores, 2 = the FP32 CUDA-core
  * screen. Other values: MAPPER_EINVAL. */
@@ -354,12 +377,15 @@ int mapper_graph_footprint(int64_t n, int32_t d, const mapper_params* params, si
 /* A request server (§4.1: the interface recomputes the graph whenever a
  * parameter changes; §4.4: parameter ranges computed offline). Datasets stay
  * resident on the device; requests (dataset, parameters) are queued in
- * arrival order and start as soon as one of n_slots worker slots is free and
- * their estimated footprint fits in hbm_budget_bytes beside the running ones
- * (0 = 80 % of the device's free memory at creation; a request that alone
- * exceeds the budget runs when nothing else does). Each slot is a host thread
- * with its own context and CUDA stream, so running requests overlap on the
- * device. Results are the exact graphs of mapper_graph. Thread-safe. */
+ * arrival order. A free one of n_slots worker slots starts the oldest queued
+ * request whose estimated footprint fits in hbm_budget_bytes beside the
+ * running ones (0 = 80 % of the device's free memory at creation); when
+ * nothing runs, the oldest request starts whatever its size. A younger
+ * request that fits may overtake an older one that does not, at most 8 times
+ * per older request; then the slots wait for the older one. Each slot is a
+ * host thread with its own context and CUDA stream, so running requests
+ * overlap on the device. Results are the exact graphs of mapper_graph.
+ * Thread-safe. */
 typedef struct mapper_server mapper_server;
 
 typedef struct mapper_request_info {
@@ -371,7 +397,10 @@ typedef struct mapper_request_info {
 } mapper_request_info;
 
 int mapper_server_create(mapper_server** out, int device, int n_slots, size_t hbm_budget_bytes);
-/* Stops the slots after their running requests; queued ones are dropped. */
+/* Stops the slots after their running requests. Requests still queued are
+ * dropped: their waiters return MAPPER_ECANCELED. Returns after every thread
+ * inside mapper_server_wait has returned; the server must not be used after
+ * this call starts (a wait that begins afterwards is invalid). */
 void mapper_server_destroy(mapper_server* server);
 /* X_dev: device FP32 cloud (n rows, stride ld), borrowed until destroy. */
 int mapper_server_add_dataset(mapper_server* server, const float* X_dev, int64_t n, int32_t d, int64_t ld,

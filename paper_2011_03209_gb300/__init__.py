@@ -68,6 +68,19 @@ class Context:
         cores, 2 CUDA cores."""
         _capi.check(self._lib.mapper_set_cross_screen(self.h, int(mode)), "mapper_set_cross_screen")
 
+    def set_pass1_screen(self, mode: int) -> None:
+        """MAPPER_BF16 count pass: 0 default, 1 two phases (one product, then
+        three for the tile pairs with a band pair), 2 three products."""
+        _capi.check(self._lib.mapper_set_pass1_screen(self.h, int(mode)), "mapper_set_pass1_screen")
+
+    def selftest_mma_error(self, dp: int, products: int, seed: int = 1):
+        """(observed, modelled) accumulation error of the tensor-core screen's
+        products on random BF16 rows, both relative to the magnitude sum."""
+        o, m = ctypes.c_double(), ctypes.c_double()
+        _capi.check(self._lib.mapper_selftest_mma_error(self.h, int(dp), int(products), int(seed), ctypes.byref(o),
+                                                        ctypes.byref(m)), "mapper_selftest_mma_error")
+        return o.value, m.value
+
     def set_band_queue_cap(self, entries: int) -> None:
         """Band-queue capacity in pairs (0: sized from the tile pairs, the
         default); band pairs past it are decided inside the screen kernel."""

@@ -20,6 +20,7 @@ MAPPER_ETIMEOUT = -4
 MAPPER_ENONFINITE = -5
 MAPPER_EINTERNAL = -6
 MAPPER_ENOTIMPL = -7
+MAPPER_ECANCELED = -8
 
 LENS_L2, LENS_COORD, LENS_PCA, LENS_ECC, LENS_LINF, LENS_DENSITY, LENS_ECC_INF = 0, 1, 2, 3, 4, 5, 6
 COVER_UNIFORM, COVER_BALANCED = 0, 1
@@ -29,6 +30,7 @@ FP32, BF16, BF16X1 = 0, 1, 2
 EXPORTS = (
     "mapper_create", "mapper_destroy", "mapper_set_stream", "mapper_set_timing", "mapper_set_pass1_tile_n",
     "mapper_set_cross_screen", "mapper_selftest_wait", "mapper_set_knn_screen", "mapper_set_band_queue_cap",
+    "mapper_set_pass1_screen", "mapper_selftest_mma_error",
     "mapper_cover_subset", "mapper_nerve_from_nodes", "mapper_cover_balanced", "mapper_knn_distance",
     "mapper_lens", "mapper_lens_ex", "mapper_cover", "mapper_cover_sizes", "mapper_cover_copy",
     "mapper_cluster", "mapper_clusters_copy", "mapper_nerve", "mapper_graph",
@@ -92,6 +94,8 @@ class MapperStats(ctypes.Structure):
         ("fp64_pairs", ctypes.c_int64),
         ("pass1_tile_n", ctypes.c_int64),
         ("tile_pairs_cross", ctypes.c_int64),
+        ("tile_pairs_screen1", ctypes.c_int64),
+        ("tile_pairs_redo", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -145,6 +149,9 @@ def load(path: str | None = None):
             "mapper_selftest_wait": (ctypes.c_int, [P]),
             "mapper_set_knn_screen": (ctypes.c_int, [P, ctypes.c_int]),
             "mapper_set_band_queue_cap": (ctypes.c_int, [P, i64]),
+            "mapper_set_pass1_screen": (ctypes.c_int, [P, ctypes.c_int]),
+            "mapper_selftest_mma_error": (ctypes.c_int, [P, i32, i32, ctypes.c_uint64, ctypes.POINTER(f64),
+                                                         ctypes.POINTER(f64)]),
             "mapper_cover_subset": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.POINTER(P)]),
             "mapper_nerve_from_nodes": (ctypes.c_int, [P, ctypes.c_int64, ctypes.c_int64, P, P, P,
                                                        ctypes.POINTER(P)]),

@@ -75,6 +75,7 @@ struct mapper_ctx {
     int cross_mode = 0;                        // cross-segment pairs: 0 auto, 1 tensor cores, 2 CUDA cores
     int knn_mode = 0;                          // k-distance screen: 0 auto (tensor cores), 1 tensor, 2 CUDA cores
     int64_t band_cap = 0;                      // band-queue entries (0: sized from the tile pairs)
+    int screen_mode = 0;                       // MAPPER_BF16 count pass: 0/1 two phases, 2 three products
 };
 
 struct mapper_cover_t {
@@ -516,6 +517,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         t.Al = L.Al.p;
         t.rn2 = L.rn2.as<float>();
         t.rn = L.rn.as<float>();
+        t.rl = L.rl.as<float>();
         t.R = R;
         t.ns = precision == MAPPER_BF16X1 ? 1 : 3;
         t.num_sms = ctx->num_sms;
@@ -532,21 +534,34 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     }
 
     TcArgs tx{};                                                  // the cross-segment operands
-    Buf xAh, xAl, xrn2, xrn;
+    Buf xAh, xAl, xrn2, xrn, xrl;
     if (cross_tc) {
-        if ((rc = cross_operands(L, X, ld, d, dp, E, &xAh, &xAl, &xrn2, &xrn, s))) return rc;
+        if ((rc = cross_operands(L, X, ld, d, dp, E, &xAh, &xAl, &xrn2, &xrn, &xrl, s))) return rc;
         tx = t;
         tx.Ah = xAh.p;
         tx.Al = xAl.p;
         tx.rn2 = xrn2.as<float>();
         tx.rn = xrn.as<float>();
+        tx.rl = xrl.as<float>();
     }
     st.tile_pairs_cross = cross_tc ? PL.n[kListSimt] : 0;
+    // MAPPER_BF16 count pass in two phases: every tile pair with one product
+    // (hi.hi); only the tile pairs with a pair inside that product's wider band
+    // run again with three products (hi.hi + hi.lo + lo.hi), as a whole
+    const bool two_phase = use_tc && t.ns == 3 && ctx->screen_mode != 2;
+    Buf redo, redo_n;
+    if (two_phase) {
+        const int64_t rcap = std::max<int64_t>(std::max(PL.n[kListTC], cross_tc ? PL.n[kListSimt] : 0), 1);
+        CK(redo.alloc(sizeof(int2) * rcap, s), "alloc");
+        CK(redo_n.alloc(sizeof(unsigned long long), s), "alloc");
+    }
     int tile_n = 0;
-    if (use_tc && PL.n[kListTC] > 0 && (rc = tune_pass1(ctx, a_tc, t, PL.n[kListTC], R, cap, s, &tile_n)))
+    TcArgs t_tune = t, tx_tune = tx;
+    if (two_phase) t_tune.ns = tx_tune.ns = 1;
+    if (use_tc && PL.n[kListTC] > 0 && (rc = tune_pass1(ctx, a_tc, t_tune, PL.n[kListTC], R, cap, s, &tile_n)))
         return rc;
     if (use_tc && PL.n[kListTC] == 0 && cross_tc &&
-        (rc = tune_pass1(ctx, a_simt, tx, PL.n[kListSimt], R, cap, s, &tile_n)))
+        (rc = tune_pass1(ctx, a_simt, tx_tune, PL.n[kListSimt], R, cap, s, &tile_n)))
         return rc;
     pt.mark();                                                    // 1
     CK(allin_pass(1, a_in, PL.n[kListAllIn], s), "pass 1 all-in");
@@ -566,7 +581,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
                         bool last) -> int {
         TcArgs t1 = base;
         t1.ev_begin = first ? tev[0] : nullptr;
-        t1.ev_end = last ? tev[1] : nullptr;
+        t1.ev_end = last && !two_phase ? tev[1] : nullptr;
         if (tile_n == 256) {
             int r2;
             if ((r2 = tc_groups(pa.pairs, np, &gr, &gp, s))) return r2;
@@ -574,7 +589,26 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
             t1.n_groups = np;
             t1.groups_dev = reinterpret_cast<const unsigned long long*>(gp.as<int64_t>() + np);
         }
-        return tc_pass(1, pa, t1, np, s);
+        if (!two_phase) return tc_pass(1, pa, t1, np, s);
+        t1.ns = 1;
+        t1.defer = true;
+        t1.redo = redo.as<int2>();
+        t1.redo_n = redo_n.as<unsigned long long>();
+        CK(cudaMemsetAsync(redo_n.p, 0, sizeof(unsigned long long), s), "memset");
+        int r2;
+        if ((r2 = tc_pass(1, pa, t1, np, s))) return r2;
+        // second phase: the deferred tile pairs (their number stays on the device)
+        PassArgs p2 = pa;
+        p2.pairs = redo.as<int2>();
+        p2.pair_hit = nullptr;
+        TcArgs t2 = base;
+        t2.groups = nullptr;
+        t2.n_groups = 0;
+        t2.groups_dev = nullptr;
+        t2.n_dev = redo_n.as<unsigned long long>();
+        t2.ev_begin = nullptr;
+        t2.ev_end = last ? tev[1] : nullptr;
+        return tc_pass(1, p2, t2, np, s);
     };
     if (use_tc) {
         const bool x_last = cross_tc && PL.n[kListSimt] > 0;
@@ -698,6 +732,8 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     st.union_pairs = (int64_t)h_stats[kStatUnion];
     st.pass1_tile_n = tile_n;
     st.n_rows = R;
+    st.tile_pairs_screen1 = two_phase ? PL.n[kListTC] + (cross_tc ? PL.n[kListSimt] : 0) : 0;
+    st.tile_pairs_redo = (int64_t)h_stats[kStatRedo];
     if (tev[0] && (PL.n[use_tc ? kListTC : kListSimt] > 0 || cross_tc)) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, tev[0], tev[1]), "event time");
@@ -868,6 +904,7 @@ const char* mapper_strerror(int status)
     case MAPPER_ENONFINITE: return "input holds NaN or Inf";
     case MAPPER_EINTERNAL: return "internal consistency check failed";
     case MAPPER_ENOTIMPL: return "not implemented";
+    case MAPPER_ECANCELED: return "request dropped by server shutdown";
     default: return "unknown status";
     }
 }
@@ -939,6 +976,15 @@ int mapper_selftest_wait(mapper_ctx* ctx)
     return tc_wait_selftest(ctx->stream->s);
 }
 
+int mapper_selftest_mma_error(mapper_ctx* ctx, int32_t dp, int32_t products, uint64_t seed, double* observed,
+                              double* modelled)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (!observed || !modelled) return fail(MAPPER_EINVAL, "null output");
+    return tc_mma_probe(products, dp, seed, ctx->num_sms, observed, modelled, ctx->stream->s);
+}
+
 int mapper_set_knn_screen(mapper_ctx* ctx, int mode)
 {
     if (!ctx) return fail(MAPPER_EINVAL, "null context");
@@ -952,6 +998,14 @@ int mapper_set_cross_screen(mapper_ctx* ctx, int mode)
     if (!ctx) return fail(MAPPER_EINVAL, "null context");
     if (mode < 0 || mode > 2) return fail(MAPPER_EINVAL, "mode must be 0, 1 or 2");
     ctx->cross_mode = mode;
+    return MAPPER_OK;
+}
+
+int mapper_set_pass1_screen(mapper_ctx* ctx, int mode)
+{
+    if (!ctx) return fail(MAPPER_EINVAL, "null context");
+    if (mode < 0 || mode > 2) return fail(MAPPER_EINVAL, "pass-1 screen must be 0, 1 or 2");
+    ctx->screen_mode = mode;
     return MAPPER_OK;
 }
 

@@ -17,7 +17,7 @@ constexpr int kPairTileMask = kPairOneEach - 1;
 
 enum : int { kStatBand = 0, kStatTies = 1, kStatScreened = 2, kStatCore = 3, kStatTileOut = 4,
              kStatTileIn = 5, kStatSkipped = 6, kStatTcPairs = 7, kStatSimtPairs = 8, kStatFp64 = 9,
-             kStatUnion = 10, kStatCount = 11 };
+             kStatUnion = 10, kStatRedo = 11, kStatCount = 12 };
 
 // Work lists of tile pairs, classified by bounding spheres.
 enum : int { kListAllIn = 0, kListTC = 1, kListSimt = 2, kListCount = 3 };
@@ -162,6 +162,7 @@ struct TileLayout {
     Buf seg_rad;                 // [n_seg] FP64 upper bound of its rows' distance to its centre
     Buf Ah, Al;                  // [R x dp] BF16 centred rows (hi and lo parts)
     Buf rn2, rn;                 // [R] FP32 |a|^2 and |a| (rounded up)
+    Buf rl;                      // [R] FP32 |a - hi| (rounded up): the residual of the hi part
 };
 
 struct PairLists {
@@ -207,8 +208,8 @@ cudaError_t centred_operands(const float* X, int64_t ld, int d, int dp, const in
                              float* rn, cudaStream_t s);
 // Tensor-core operands for the CUDA-core list (tile pairs of one element, two
 // segments): every row centred on its element's centre, BF16 hi + lo, with
-// FP32 |a|^2 and |a| rounded up (R rows each).
+// FP32 |a|^2, and |a| and |a - hi| rounded up (R rows each).
 int cross_operands(const TileLayout& L, const float* X, int64_t ld, int d, int dp, int64_t E, Buf* Ah, Buf* Al,
-                   Buf* rn2, Buf* rn, cudaStream_t s);
+                   Buf* rn2, Buf* rn, Buf* rl, cudaStream_t s);
 
 }  // namespace mgb

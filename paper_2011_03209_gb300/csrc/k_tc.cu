@@ -30,7 +30,9 @@
 #include <cfloat>
 #include <climits>
 #include <cmath>
+#include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "../../include/mapper.h"
 #include "tc.cuh"
@@ -52,6 +54,7 @@ struct TcParams {
     PassArgs A;
     const float* rn2;
     const float* rn;
+    const float* rl;                          // |a - hi| per row (rounded up), or nullptr
     int64_t n_pairs;
     const int2* groups;                       // W = 2: (pair, pair or -1) sharing tile A
     int64_t n_groups;
@@ -59,11 +62,18 @@ struct TcParams {
     int nkb;                                  // K blocks per row
     double A1, A2, A3;                        // bound constants
     float A1f, A2f, A3f;                      // ... rounded up to FP32
+    float K0f, K1f, K2f;                      // bound from the residual norms (rl set), rounded up
     float eps2_lo, eps2_hi;                   // eps^2 rounded down / up to FP32
     uint2* queue;                             // band pairs: (row a, row b | flags << 30)
     unsigned long long* queue_n;
     unsigned long long queue_cap;
     int* err;                                 // 1: a wait timed out
+    // pass 1, one-product screen of the two-phase count pass: a tile pair with
+    // any pair in the band is not counted here but appended to redo[] (and
+    // flagged in pair_hit) for a three-product pass
+    int defer;
+    int2* redo;
+    unsigned long long* redo_n;
     // k-distance screen (MODE 3): CTA t = (query tile t / kq_chunks, chunk t % kq_chunks)
     // against point tiles chunk * kq_ct .. + kq_ct of the kq_tp point tiles; query
     // tile u is operand tile kq_tp + u
@@ -71,6 +81,7 @@ struct TcParams {
     int kq_ct, kq_chunks, kq_far;
     float* kq_v;                              // lists: [((query * chunks + chunk) * 4 + part) * 16]
     int32_t* kq_i;
+    float* dump;                              // MODE 4 (accumulation probe): [item][128][128] accumulators
 };
 
 // ------------------------------------------------------------------ PTX
@@ -306,7 +317,7 @@ struct SmemTail {
     int consumed;                              // stage fills consumed by the MMA warp
     int s_mm[2][2];                            // union pass: min / max root of the core rows
     uint32_t colcore[2][4];                    // union pass: core columns, bit per column
-    float red[2][8];                           // max |b|^2 and |b| of the columns, per warp
+    float red[2][12];                          // max |b|^2, |b| and |b - hi| of the columns, per warp
     __align__(16) float nbn[2][kT];            // -|b|^2 of the pair's columns
     __align__(16) float nbr[2][kT];            // k-distance pass: |b| (rounded up) of the pair's columns
     uint32_t colmask[4][kT];                   // count pass: neighbour bits per column (by row quadrant)
@@ -593,6 +604,24 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             volatile int dummy = 0;
             mbar_wait(&S.fin, 0, &dummy);
         }
+    } else if constexpr (MODE == 4) {
+        // ------------------------------ epilogue: accumulators to memory (probe)
+        const int quad = warp & 3, part = (warp - 2) >> 2, r = quad * 32 + lane;
+        int git = 0;
+        for (int64_t g = blockIdx.x; g < n_items; g += gridDim.x, ++git) {
+            const int tbuf = git & 1;
+            const bool bad = !mbar_wait(&S.acc_full[tbuf], (uint32_t)((git >> 1) & 1), abort) || *abort;
+            if (epi_sync_or(bad)) break;
+            tc_fence_after();
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tbuf * kAccCols + part * 32), v);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.acc_empty[tbuf]);
+            float* out = P.dump + ((int64_t)g * kT + r) * kT + part * 32;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) out[i] = v[i];
+        }
     } else if constexpr (MODE == 3) {
         // ------------------------------------- epilogue: k smallest distances
         // Warp w holds TMEM lane quadrant (w & 3) = query rows 32 (w & 3) ..
@@ -681,8 +710,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             int2 tp;
             bool one_each;                                    // union pass: see kPairOneEach
             int na, nb;
-            float na2, nra;                                   // row r
-            float c2, c1;                                     // column et (et < 128)
+            float na2, nra, rla;                              // row r
+            float c2, c1, c3;                                 // column et (et < 128)
             bool core_et;                                     // union pass: row et of A | B
             int count_et;                                     // count pass: count of row / column et
         };
@@ -695,9 +724,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             const int64_t sa = (int64_t)f.tp.x * kT, sb = (int64_t)f.tp.y * kT;
             f.na2 = P.rn2[sa + r];
             f.nra = P.rn[sa + r];
+            f.rla = P.rl ? P.rl[sa + r] : 0.f;
             if (et < kT) {
                 f.c2 = P.rn2[sb + et];
                 f.c1 = P.rn[sb + et];
+                f.c3 = P.rl ? P.rl[sb + et] : 0.f;
             }
             if (MODE == 2) {
                 const bool diag = f.tp.x == f.tp.y;
@@ -736,18 +767,23 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             const int tbuf = git & 1;
             const uint32_t acc_phase = (uint32_t)((git >> 1) & 1);
             const bool valid_r = r < na;
-            const float na2 = cur.na2, nra = cur.nra;
+            const float na2 = cur.na2, nra = cur.nra, rla = cur.rla;
             const int pre_count = cur.count_et;
 
             // (1) stage this pair's column data (and core rows, roots) in buffer `buf`
             if (et < kT) {
                 S.nbn[buf][et] = -cur.c2;
-                float m2 = cur.c2, m1 = cur.c1;
+                float m2 = cur.c2, m1 = cur.c1, m3 = cur.c3;
                 for (int o = 16; o; o >>= 1) {
                     m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
                     m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+                    m3 = fmaxf(m3, __shfl_xor_sync(0xffffffffu, m3, o));
                 }
-                if (lane == 0) { S.red[buf][et >> 5] = m2; S.red[buf][4 + (et >> 5)] = m1; }
+                if (lane == 0) {
+                    S.red[buf][et >> 5] = m2;
+                    S.red[buf][4 + (et >> 5)] = m1;
+                    S.red[buf][8 + (et >> 5)] = m3;
+                }
             }
             if (MODE == 2 && et < 2 * kT) {
                 const bool cc = cur.core_et;
@@ -780,7 +816,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             //     u = fl(2 acc - |b|^2); all FP32 with outward rounding
             const float nb2max = fmaxf(fmaxf(S.red[buf][0], S.red[buf][1]), fmaxf(S.red[buf][2], S.red[buf][3]));
             const float nrbmax = fmaxf(fmaxf(S.red[buf][4], S.red[buf][5]), fmaxf(S.red[buf][6], S.red[buf][7]));
-            const float E = __fmaf_ru(P.A1f, __fmul_ru(nra, nrbmax), __fmaf_ru(P.A2f, __fadd_ru(na2, nb2max), P.A3f));
+            float E;
+            if (P.rl) {
+                // from the residual norms: K2 r_a r_b + K1 (r_a |b| + |a| r_b) + K0 |a||b| + A2 (..) + A3
+                const float rlbmax = fmaxf(fmaxf(S.red[buf][8], S.red[buf][9]), fmaxf(S.red[buf][10], S.red[buf][11]));
+                const float cross = __fadd_ru(__fmul_ru(rla, nrbmax), __fmul_ru(nra, rlbmax));
+                E = __fmaf_ru(P.K2f, __fmul_ru(rla, rlbmax),
+                              __fmaf_ru(P.K1f, cross,
+                                        __fmaf_ru(P.K0f, __fmul_ru(nra, nrbmax),
+                                                  __fmaf_ru(P.A2f, __fadd_ru(na2, nb2max), P.A3f))));
+            } else {
+                E = __fmaf_ru(P.A1f, __fmul_ru(nra, nrbmax), __fmaf_ru(P.A2f, __fadd_ru(na2, nb2max), P.A3f));
+            }
             const float k_in = __fadd_ru(__fsub_ru(na2, P.eps2_lo), E);
             const float k_out = __fsub_rd(__fsub_rd(na2, P.eps2_hi), E);
             bool work = true;
@@ -846,9 +893,25 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 }
             }
 
+            // (4b) two-phase count pass: a tile pair with any band pair is left,
+            //      whole, to the three-product pass (nothing of it counted here)
+            bool deferred = false;
+            if (MODE == 1 && P.defer) {
+                uint32_t anyb = 0u;
+#pragma unroll
+                for (int c2 = 0; c2 < kChunks; ++c2) anyb |= band[c2];
+                deferred = epi_sync_or(anyb != 0u);
+                if (deferred && et == 0) {
+                    const unsigned long long at = atomicAdd(P.redo_n, 1ull);
+                    P.redo[at] = A.pairs[q];
+                    if (A.pair_hit) A.pair_hit[q] = 1;
+                    atomicAdd(&A.stats[kStatRedo], 1ull);
+                }
+            }
+
             // (5) band pairs: queued for the FP64 recheck (decided here if the queue is full);
             //     a one-each union pair needs none once any pair is certainly in
-            bool any_in = false;
+            bool any_in = deferred;
             uint32_t all_in = 0u;
 #pragma unroll
             for (int c2 = 0; c2 < kChunks; ++c2) all_in |= inb[c2];
@@ -879,7 +942,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             }
 
             // (6) counts and lists, or unions
-            if (MODE == 1) {
+            if (MODE == 1 && deferred) {
+                // counted by the three-product pass
+            } else if (MODE == 1) {
                 // one thread per row (et < 128) and per column (128 <= et < 256) adds the
                 // pair's neighbours to the count; lists are written only while a count may
                 // still be below cap (the count read one pair ahead is a lower bound)
@@ -1448,6 +1513,39 @@ void tc_bound(int ns, int dp, double eps2, double* A1, double* A2, double* A3)
     *A3 = std::ldexp(1.0, -40) * eps2 + 1e-30;
 }
 
+// The same bound from the residual norms r = |a' - hi| of both rows (a' =
+// fl(x - c), hi = bf16(a'), both per row, rounded up), which are typically
+// ~0.4 u |a| rather than the worst case u |a|. With e = a - a' (|e| <=
+// 2^-24 |a|), t = r - lo (|t| <= u |r|) and |r| <= u (1 + 2^-23) |a|:
+//   NS = 1: a.b - hi_a.hi_b = (e_a + r_a).b + hi_a.(e_b + r_b), so
+//           |.| <= (1 + 2^-7)(|r_a||b| + |a||r_b|) + 3 2^-24 |a||b|;
+//   NS = 3: a.b - P = lo_a.lo_b + (hi_a + lo_a).(t_b + e_b) + (t_a + e_a).b, so
+//           |.| <= (1 + 2^-6)|r_a||r_b| + u (1 + 2^-6)(|a||r_b| + |r_a||b|) + 2^-22 |a||b|.
+// E = K2 |r_a||r_b| + K1 (|r_a||b| + |a||r_b|) + K0 |a||b| + A2 (|a|^2 + |b|^2) + A3,
+// with the accumulation, screen and norm terms and the 1.25 margin of tc_bound.
+void tc_bound_resid(int ns, int dp, double eps2, double* K0, double* K1, double* K2, double* A2, double* A3)
+{
+    const double u = std::ldexp(1.0, -8), v = std::ldexp(1.0, -24);
+    const double up = u + 2.0 * v;
+    const int steps = ns * ((dp + kKB - 1) / kKB) * (kKB / 16);
+    const double accu = steps * std::ldexp(1.0, -22) * (1.0 + 2.0 * up) * (1.0 + 2.0 * up);
+    double o2, o1, o0;
+    if (ns == 1) {
+        o2 = 0.0;
+        o1 = 1.0 + std::ldexp(1.0, -7);
+        o0 = 3.0 * v;
+    } else {
+        o2 = 1.0 + std::ldexp(1.0, -6);
+        o1 = u * (1.0 + std::ldexp(1.0, -6));
+        o0 = std::ldexp(1.0, -22);
+    }
+    *K2 = 1.25 * 2.0 * o2;
+    *K1 = 1.25 * 2.0 * o1;
+    *K0 = 1.25 * (2.0 * (o0 + accu) + 4.0 * v);
+    *A2 = 2.0 * (dp / 32 + 16) * v + 4.0 * v;
+    *A3 = std::ldexp(1.0, -40) * eps2 + 1e-30;
+}
+
 int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaStream_t s)
 {
     if (n_pairs == 0) return MAPPER_OK;
@@ -1470,6 +1568,14 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
     p.A1f = std::nextafter((float)p.A1, INFINITY);
     p.A2f = std::nextafter((float)p.A2, INFINITY);
     p.A3f = std::nextafter((float)p.A3, INFINITY);
+    p.rl = t.rl;
+    if (t.rl) {
+        double K0, K1, K2, A2, A3;
+        tc_bound_resid(t.ns, a.dp, a.eps2, &K0, &K1, &K2, &A2, &A3);
+        p.K0f = std::nextafter((float)K0, INFINITY);
+        p.K1f = std::nextafter((float)K1, INFINITY);
+        p.K2f = std::nextafter((float)K2, INFINITY);
+    }
     p.eps2_lo = (float)a.eps2;
     if ((double)p.eps2_lo > a.eps2) p.eps2_lo = std::nextafter(p.eps2_lo, -INFINITY);
     p.eps2_hi = (float)a.eps2;
@@ -1478,6 +1584,14 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
     p.queue_n = t.queue_n;
     p.queue_cap = t.queue_cap;
     p.err = t.err;
+    const bool defer = mode == 1 && t.defer && t.ns == 1;
+    p.defer = defer ? 1 : 0;
+    p.redo = t.redo;
+    p.redo_n = t.redo_n;
+    if (t.defer && !defer) {
+        set_error("tensor-core pass: deferral needs the one-product count pass");
+        return MAPPER_EINTERNAL;
+    }
     cudaError_t e = cudaMemsetAsync(t.queue_n, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ECUDA; }
     const bool grouped = mode == 1 && t.groups != nullptr;
@@ -1499,6 +1613,7 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
         set_error(std::string("tensor-core pass: ") + cudaGetErrorString(e));
         return MAPPER_ECUDA;
     }
+    if (defer) return MAPPER_OK;              // no pair reaches the band queue
     // FP32 limits of the recheck's lane-split sum (relative error (dp/8 + 5) 2^-24)
     const double eta = 1.5 * (a.dp / 8 + 5) * std::ldexp(1.0, -24);
     const double tiny = 3.0 * (a.d + 2) * std::ldexp(1.0, -149);
@@ -1599,6 +1714,133 @@ int tc_knn_screen(const void* Ah, const void* Al, const float* rn2, const float*
         set_error(std::string("k-distance tensor-core screen: ") + cudaGetErrorString(e));
         return MAPPER_ECUDA;
     }
+    return MAPPER_OK;
+}
+
+namespace {
+
+uint64_t splitmix(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+uint16_t bf16_bits_rn(float f)                // round to nearest even (finite f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+float bf16_value(uint16_t b)
+{
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+}  // namespace
+
+int tc_mma_probe(int ns, int dp, uint64_t seed, int num_sms, double* observed, double* modelled, cudaStream_t s)
+{
+    if ((ns != 1 && ns != 3) || dp < 32 || dp % 32 || dp > 4096) {
+        set_error("accumulation probe: products must be 1 or 3 and the pitch a multiple of 32 in [32, 4096]");
+        return MAPPER_EINVAL;
+    }
+    constexpr int kPairs = 4, kTiles = 2 * kPairs, R = kTiles * kT;
+    // random rows: values sign * 2^e * m with e in [-4, 4], split into BF16 hi + lo
+    std::vector<uint16_t> hi((size_t)R * dp), lo((size_t)R * dp);
+    for (size_t i = 0; i < hi.size(); ++i) {
+        const uint64_t h = splitmix(seed * 0x100000001B3ull + i);
+        const float m = 1.0f + (float)((h >> 11) & 0xFFFFFF) / 16777216.0f;
+        const int e = (int)((h >> 40) % 9) - 4;
+        const float v = std::ldexp(m, e) * ((h >> 63) ? -1.0f : 1.0f);
+        hi[i] = bf16_bits_rn(v);
+        lo[i] = bf16_bits_rn(v - bf16_value(hi[i]));
+    }
+    std::vector<int2> pairs(kPairs);
+    for (int k = 0; k < kPairs; ++k) pairs[k] = make_int2(2 * k, 2 * k + 1);
+    std::vector<int32_t> tile_n(kTiles, kT);
+    Buf dAh, dAl, dpairs, dtn, ddump, derr;
+#define PK(expr)                                                                  \
+    do {                                                                          \
+        cudaError_t e_ = (expr);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            set_error(std::string("accumulation probe: ") + cudaGetErrorString(e_)); \
+            return e_ == cudaErrorMemoryAllocation ? MAPPER_ENOMEM : MAPPER_ECUDA; \
+        }                                                                         \
+    } while (0)
+    PK(dAh.alloc(hi.size() * 2, s));
+    PK(dAl.alloc(lo.size() * 2, s));
+    PK(dpairs.alloc(sizeof(int2) * kPairs, s));
+    PK(dtn.alloc(sizeof(int32_t) * kTiles, s));
+    PK(ddump.alloc(sizeof(float) * (size_t)kPairs * kT * kT, s));
+    PK(derr.alloc(sizeof(int), s));
+    PK(cudaMemcpyAsync(dAh.p, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice, s));
+    PK(cudaMemcpyAsync(dAl.p, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice, s));
+    PK(cudaMemcpyAsync(dpairs.p, pairs.data(), sizeof(int2) * kPairs, cudaMemcpyHostToDevice, s));
+    PK(cudaMemcpyAsync(dtn.p, tile_n.data(), sizeof(int32_t) * kTiles, cudaMemcpyHostToDevice, s));
+    PK(cudaMemsetAsync(derr.p, 0, sizeof(int), s));
+    CUtensorMap mh, ml;
+    if (!make_map(&mh, dAh.p, R, dp) || !make_map(&ml, ns == 3 ? dAl.p : dAh.p, R, dp)) {
+        set_error("cuTensorMapEncodeTiled failed (or is unavailable)");
+        return MAPPER_ECUDA;
+    }
+    TcParams p{};
+    p.A.pairs = dpairs.as<int2>();
+    p.A.tile_n = dtn.as<int32_t>();
+    p.A.dp = dp;
+    p.n_pairs = kPairs;
+    p.nkb = (dp + kKB - 1) / kKB;
+    p.err = derr.as<int>();
+    p.dump = ddump.as<float>();
+    const int grid = std::min(kPairs, num_sms);
+    PK((ns == 3 ? launch<3, 4, 1>(mh, ml, p, grid, s) : launch<1, 4, 1>(mh, ml, p, grid, s)));
+    note_launch();
+    std::vector<float> acc((size_t)kPairs * kT * kT);
+    int h_err = 0;
+    PK(cudaMemcpyAsync(acc.data(), ddump.p, acc.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+    PK(cudaMemcpyAsync(&h_err, derr.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PK(cudaStreamSynchronize(s));
+#undef PK
+    if (h_err) {
+        set_error("accumulation probe gave up waiting on a barrier");
+        return MAPPER_ETIMEOUT;
+    }
+    // exact sums in FP64 (products of BF16 values are exact; the FP64 sum of
+    // 3 dp terms errs by < 3 dp 2^-53 of their magnitude sum)
+    double worst = 0.0;
+    for (int k = 0; k < kPairs; ++k)
+        for (int i = 0; i < kT; ++i)
+            for (int j = 0; j < kT; ++j) {
+                const size_t ra = ((size_t)(2 * k) * kT + i) * dp, rb = ((size_t)(2 * k + 1) * kT + j) * dp;
+                double ex = 0.0, mag = 0.0;
+                for (int c = 0; c < dp; ++c) {
+                    const double ah = bf16_value(hi[ra + c]), bh = bf16_value(hi[rb + c]);
+                    double t = ah * bh;
+                    ex += t;
+                    mag += std::fabs(t);
+                    if (ns == 3) {
+                        const double al = bf16_value(lo[ra + c]), bl = bf16_value(lo[rb + c]);
+                        t = ah * bl;
+                        ex += t;
+                        mag += std::fabs(t);
+                        t = al * bh;
+                        ex += t;
+                        mag += std::fabs(t);
+                    }
+                }
+                const double err = std::fabs((double)acc[((size_t)k * kT + i) * kT + j] - ex);
+                if (mag > 0.0) worst = std::max(worst, err / mag);
+            }
+    const double up = std::ldexp(1.0, -8) + 2.0 * std::ldexp(1.0, -24);
+    const int steps = ns * ((dp + kKB - 1) / kKB) * (kKB / 16);
+    *observed = worst;
+    *modelled = steps * std::ldexp(1.0, -22) * (1.0 + 2.0 * up) * (1.0 + 2.0 * up);
     return MAPPER_OK;
 }
 

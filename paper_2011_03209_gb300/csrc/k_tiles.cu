@@ -489,8 +489,9 @@ __global__ void __launch_bounds__(1024) seg_cent_kernel(const float* __restrict_
 // BF16 operands centred on the segment centre c (FP32): a = fl(x - c),
 // hi = bf16(a), lo = bf16(a - hi) (a - hi is exact in FP32); |a|^2 summed in
 // FP32 (lane partials of at most dp/32 squares, then a shuffle tree) and |a|
-// rounded up. A warp per row, a lane per 8 consecutive columns (16-byte
-// stores); rows come from G when it is set, else from X.
+// rounded up; if rl is set, also |a - hi| (the residual the hi part leaves,
+// summed the same way) rounded up. A warp per row, a lane per 8 consecutive
+// columns (16-byte stores); rows come from G when it is set, else from X.
 __global__ void __launch_bounds__(256) operand_kernel(const float* __restrict__ G, const float* __restrict__ X,
                                                       int64_t ld, bool xvec, const int32_t* __restrict__ row_pt,
                                                       int d, int dp, const int32_t* __restrict__ tile_n,
@@ -499,7 +500,7 @@ __global__ void __launch_bounds__(256) operand_kernel(const float* __restrict__ 
                                                       __nv_bfloat16* __restrict__ Ah,
                                                       __nv_bfloat16* __restrict__ Al,
                                                       float* __restrict__ rn2, float* __restrict__ rn,
-                                                      float norm_infl)
+                                                      float* __restrict__ rl, float norm_infl)
 {
     const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nt = tile_n[t];
@@ -509,7 +510,7 @@ __global__ void __launch_bounds__(256) operand_kernel(const float* __restrict__ 
         const int64_t row = (int64_t)t * kT + r;
         const bool valid = r < nt;
         const float* xr = !valid ? nullptr : (G ? G + row * dp : X + (int64_t)row_pt[row] * ld);
-        float s = 0.f;
+        float s = 0.f, sr = 0.f;
         for (int k0 = 0; k0 < dp; k0 += 256) {
             const int k = k0 + lane * 8;
             if (k >= dp) continue;
@@ -537,19 +538,26 @@ __global__ void __launch_bounds__(256) operand_kernel(const float* __restrict__ 
             for (int u = 0; u < 8; u += 2) {
                 const __nv_bfloat162 h = __floats2bfloat162_rn(a[u], a[u + 1]);
                 const float2 hf = __bfloat1622float2(h);
-                const __nv_bfloat162 l = __floats2bfloat162_rn(a[u] - hf.x, a[u + 1] - hf.y);
+                const float r0 = a[u] - hf.x, r1 = a[u + 1] - hf.y;          // exact
+                const __nv_bfloat162 l = __floats2bfloat162_rn(r0, r1);
                 wh[u >> 1] = *reinterpret_cast<const uint32_t*>(&h);
                 wl[u >> 1] = *reinterpret_cast<const uint32_t*>(&l);
                 s = fmaf(a[u], a[u], s);
                 s = fmaf(a[u + 1], a[u + 1], s);
+                sr = fmaf(r0, r0, sr);
+                sr = fmaf(r1, r1, sr);
             }
             *reinterpret_cast<uint4*>(Ah + row * dp + k) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
             if (Al) *reinterpret_cast<uint4*>(Al + row * dp + k) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
         }
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        for (int o = 16; o; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        }
         if (lane == 0) {
             rn2[row] = s;
             rn[row] = __fmul_ru(__fsqrt_ru(s), norm_infl);
+            if (rl) rl[row] = __fmul_ru(__fsqrt_ru(sr), norm_infl);
         }
     }
 }
@@ -943,13 +951,15 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
         TK(L->Al.alloc(sizeof(__nv_bfloat16) * (size_t)R * dp, s));
         TK(L->rn2.alloc(sizeof(float) * R, s));
         TK(L->rn.alloc(sizeof(float) * R, s));
+        TK(L->rl.alloc(sizeof(float) * R, s));
         const float norm_infl = 1.0f + (float)(dp / 32 + 16) * 5.9604645e-8f;
         const bool xvec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
         operand_kernel<<<(unsigned)T, 256, 0, s>>>(L->G.as<float>(), X, ld, xvec, L->row_pt.as<int32_t>(), d, dp,
                                                    L->tile_n.as<int32_t>(),
                                                    L->tile_seg.as<int32_t>(), L->seg_cent.as<float>(),
                                                    L->Ah.as<__nv_bfloat16>(), L->Al.as<__nv_bfloat16>(),
-                                                   L->rn2.as<float>(), L->rn.as<float>(), norm_infl);
+                                                   L->rn2.as<float>(), L->rn.as<float>(), L->rl.as<float>(),
+                                                   norm_infl);
         note_launch();
         TK(cudaGetLastError());
     }
@@ -965,7 +975,7 @@ cudaError_t centred_operands(const float* X, int64_t ld, int d, int dp, const in
     const bool xvec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
     operand_kernel<<<(unsigned)T, 256, 0, s>>>(nullptr, X, ld, xvec, row_pt, d, dp, tile_n, tile_cent, cents,
                                                static_cast<__nv_bfloat16*>(Ah), static_cast<__nv_bfloat16*>(Al), rn2,
-                                               rn, norm_infl);
+                                               rn, nullptr, norm_infl);
     note_launch();
     return cudaGetLastError();
 }
@@ -976,7 +986,7 @@ cudaError_t centred_operands(const float* X, int64_t ld, int d, int dp, const in
 // centre, so the screen's error bound, and its band, are wider; pairs far
 // apart are still decided at once.
 int cross_operands(const TileLayout& L, const float* X, int64_t ld, int d, int dp, int64_t E, Buf* Ah, Buf* Al,
-                   Buf* rn2, Buf* rn, cudaStream_t s)
+                   Buf* rn2, Buf* rn, Buf* rl, cudaStream_t s)
 {
 #define XK(expr)                                                                      \
     do {                                                                              \
@@ -994,6 +1004,7 @@ int cross_operands(const TileLayout& L, const float* X, int64_t ld, int d, int d
     XK(Al->alloc(sizeof(__nv_bfloat16) * (size_t)R * dp, s));
     XK(rn2->alloc(sizeof(float) * R, s));
     XK(rn->alloc(sizeof(float) * R, s));
+    XK(rl->alloc(sizeof(float) * R, s));
     elem_tiles_kernel<<<grid_for(E + 1), 256, 0, s>>>(L.tile_elem.as<int32_t>(), T, E, etile_off.as<int64_t>());
     seg_cent_kernel<<<(unsigned)E, 1024, 0, s>>>(L.tile_cent.as<float>(), L.tile_n.as<int32_t>(),
                                                etile_off.as<int64_t>(), dp, ecent.as<float>());
@@ -1002,7 +1013,7 @@ int cross_operands(const TileLayout& L, const float* X, int64_t ld, int d, int d
     operand_kernel<<<(unsigned)T, 256, 0, s>>>(L.G.as<float>(), X, ld, xvec, L.row_pt.as<int32_t>(), d, dp,
                                                L.tile_n.as<int32_t>(), L.tile_elem.as<int32_t>(), ecent.as<float>(),
                                                Ah->as<__nv_bfloat16>(), Al->as<__nv_bfloat16>(), rn2->as<float>(),
-                                               rn->as<float>(), norm_infl);
+                                               rn->as<float>(), rl->as<float>(), norm_infl);
     note_launch(3);
     XK(cudaGetLastError());
     return MAPPER_OK;

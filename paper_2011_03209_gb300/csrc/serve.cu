@@ -8,6 +8,14 @@
 // fits beside the requests already running. Each slot is a host thread with
 // its own library context and CUDA stream, so the device work of concurrent
 // requests overlaps; results are exact whatever runs beside them.
+//
+// Admission: a free slot takes the oldest queued request that fits beside
+// the running ones; when nothing runs, the oldest request starts whatever
+// its size. A request that fits may so overtake an older one that does not,
+// but only kMaxOvertakes times: after that the older request is first in
+// line and the slots wait for it (aging), so large requests still start.
+// Shutdown completes every request still queued with MAPPER_ECANCELED and
+// returns only after every thread waiting on a request has left.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -24,6 +32,8 @@
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+constexpr int kMaxOvertakes = 8;      // later requests that may start before a blocked one
 
 struct Dataset {
     const float* X;
@@ -42,6 +52,7 @@ struct Request {
     int status = MAPPER_OK;
     std::string error;
     bool done = false;
+    int overtaken = 0;                // later requests admitted while this one waited
 };
 
 double secs(Clock::time_point a, Clock::time_point b)
@@ -67,9 +78,25 @@ struct mapper_server {
     int init_status = MAPPER_OK;
     std::string init_error;
     int ready = 0;
+    int waiters = 0;                                         // threads inside mapper_server_wait
 };
 
 namespace {
+
+// Index in S->queue of the request a free slot starts now, or -1 (caller
+// holds S->mu): the oldest that fits beside the running requests, unless an
+// older one that does not fit has been overtaken kMaxOvertakes times already.
+int pick_request(const mapper_server* S)
+{
+    if (S->queue.empty()) return -1;
+    if (S->running == 0) return 0;
+    for (size_t i = 0; i < S->queue.size(); ++i) {
+        const Request& r = *S->queue[i];
+        if (S->in_use + r.footprint <= S->budget) return (int)i;
+        if (r.overtaken >= kMaxOvertakes) return -1;
+    }
+    return -1;
+}
 
 void worker_main(mapper_server* S, int slot)
 {
@@ -91,14 +118,12 @@ void worker_main(mapper_server* S, int slot)
         std::shared_ptr<Request> r;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            // the oldest request starts once its footprint fits (or nothing else runs)
-            S->cv_work.wait(lk, [&] {
-                return S->stopping || (!S->queue.empty() &&
-                                       (S->running == 0 || S->in_use + S->queue.front()->footprint <= S->budget));
-            });
-            if (S->stopping && S->queue.empty()) break;
-            r = S->queue.front();
-            S->queue.pop_front();
+            int at = -1;
+            S->cv_work.wait(lk, [&] { return S->stopping || (at = pick_request(S)) >= 0; });
+            if (S->stopping) break;
+            r = S->queue[at];
+            for (int i = 0; i < at; ++i) ++S->queue[i]->overtaken;
+            S->queue.erase(S->queue.begin() + at);
             S->in_use += r->footprint;
             ++S->running;
             r->t_start = Clock::now();
@@ -171,10 +196,26 @@ void mapper_server_destroy(mapper_server* S)
     {
         std::lock_guard<std::mutex> lk(S->mu);
         S->stopping = true;
-        S->queue.clear();                     // queued requests are dropped
+        // queued requests never start: complete them with an error status so
+        // that their waiters return
+        const Clock::time_point now = Clock::now();
+        for (auto& r : S->queue) {
+            r->t_start = r->t_end = now;
+            r->status = MAPPER_ECANCELED;
+            r->error = "request dropped: the server was destroyed before it started";
+            r->done = true;
+        }
+        S->queue.clear();
     }
     S->cv_work.notify_all();
-    for (auto& t : S->workers) t.join();
+    S->cv_done.notify_all();
+    for (auto& t : S->workers) t.join();         // running requests finish
+    {
+        // every thread inside mapper_server_wait leaves before S goes away
+        std::unique_lock<std::mutex> lk(S->mu);
+        S->cv_done.notify_all();
+        S->cv_done.wait(lk, [&] { return S->waiters == 0; });
+    }
     for (auto& kv : S->requests)
         if (kv.second->graph) mapper_free(kv.second->graph);
     delete S;
@@ -225,12 +266,14 @@ int mapper_server_wait(mapper_server* S, int64_t request_id, double timeout_s, m
     if (it == S->requests.end()) return fail(MAPPER_EINVAL, "no such request (or already collected)");
     std::shared_ptr<Request> r = it->second;
     const auto pred = [&] { return r->done; };
-    if (timeout_s < 0) {
-        S->cv_done.wait(lk, pred);
-    } else if (!S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred)) {
-        return fail(MAPPER_ETIMEOUT, "request not finished within the timeout");
-    }
-    S->requests.erase(it);
+    ++S->waiters;
+    bool finished = true;
+    if (timeout_s < 0) S->cv_done.wait(lk, pred);
+    else finished = S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred);
+    --S->waiters;
+    if (S->stopping && S->waiters == 0) S->cv_done.notify_all();    // destroy may be waiting for us
+    if (!finished) return fail(MAPPER_ETIMEOUT, "request not finished within the timeout");
+    S->requests.erase(r->id);
     if (info) {
         info->queue_s = secs(r->t_submit, r->t_start);
         info->run_s = secs(r->t_start, r->t_end);

@@ -13,6 +13,7 @@ struct TcArgs {
     const void* Al;
     const float* rn2;
     const float* rn;
+    const float* rl;                 // |a - hi| per row (rounded up): the tighter bound; or nullptr
     int64_t R;
     int ns;                          // BF16 products per pair: 3 (hi.hi + hi.lo + lo.hi) or 1
     int num_sms;                     // persistent grid size
@@ -26,6 +27,14 @@ struct TcArgs {
     const unsigned long long* groups_dev;   // ... and their number on the device
     const unsigned long long* n_dev; // ungrouped, if set: the pair count on the device
                                      //   (n_pairs then bounds it)
+    // pass 1 with ns = 1 only: the first phase of the two-phase count pass.
+    // Tile pairs with no pair in the one-product band are counted; the others
+    // are appended to redo[] (capacity n_pairs; *redo_n, zeroed by the caller,
+    // receives their number), flagged in pair_hit and counted by a
+    // three-product pass over redo[] afterwards.
+    bool defer;
+    int2* redo;
+    unsigned long long* redo_n;
 };
 
 // Groups the pair list (sorted by tile A, then tile B) into work items of
@@ -62,6 +71,14 @@ constexpr int kKnnList = 8;
 int tc_knn_screen(const void* Ah, const void* Al, const float* rn2, const float* rn, const int32_t* tile_n,
                   int64_t Tp, int64_t q, int dp, int chunk_tiles, int chunks, bool far, float A1f, float A2f,
                   float A3f, float* cand_v, int32_t* cand_i, int* err, cudaStream_t s);
+
+// Accumulation probe: random BF16 rows (values 2^-4 .. 2^5 in magnitude,
+// random signs) through the screen's tcgen05 path (ns products, row pitch
+// dp, M = N = 128, four tile pairs); *observed = the largest |acc - exact|
+// over the accumulators, relative to the sum of the magnitudes of the
+// products, and *modelled = the accumulation term of the screen's error bound
+// relative to the same sum. Returns a mapper_status.
+int tc_mma_probe(int ns, int dp, uint64_t seed, int num_sms, double* observed, double* modelled, cudaStream_t s);
 
 // Runs the passes' bounded mbarrier wait on a barrier that is never
 // completed: MAPPER_ETIMEOUT once it gives up (after 4 s), as designed.

@@ -234,12 +234,12 @@ def eps_from_sample(sq: np.ndarray, q: float) -> float:
     return float(math.sqrt(0.5 * (sq[k] + sq[k + 1])))
 
 
-def serving_datasets(seed: int = 4, big_n: int = 1_000_000):
+def serving_datasets(seed: int = 4, big_n: int = 1_000_000, big_X: np.ndarray | None = None):
     """Nine resident clouds: the 1,000,000 x 256 clustered cloud and eight
     Gaussian mixtures (16 clusters) with n log-uniform in [1e4, 5e5] and d in
-    {32, 64, 128, 256}."""
+    {32, 64, 128, 256}. big_X: the clustered cloud, when already drawn."""
     rng = np.random.default_rng(seed)
-    out = [clusters_1m_d256(big_n).X]
+    out = [clusters_1m_d256(big_n).X if big_X is None else big_X]
     for k in range(8):
         n = int(round(10 ** rng.uniform(4.0, math.log10(5e5))))
         d = int(rng.choice([32, 64, 128, 256]))

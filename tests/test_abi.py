@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version_and_strings(lib):
-    assert lib.mapper_abi_version() == 4
+    assert lib.mapper_abi_version() == 5
     assert lib.mapper_strerror(0) == b"ok"
     assert lib.mapper_strerror(-4) == b"device wait timed out"
 
@@ -50,7 +50,7 @@ def test_struct_layouts_match_header():
     assert _capi.MapperParams.overlap.offset == 32
     assert _capi.MapperParams.cover_kind.offset == 64
     assert _capi.MapperParams.lens_param.offset == 72
-    assert ctypes.sizeof(_capi.MapperStats) == 8 * 34
+    assert ctypes.sizeof(_capi.MapperStats) == 8 * 36
 
 
 def test_null_and_bad_arguments_are_rejected_without_a_gpu(lib):
@@ -70,6 +70,8 @@ def test_knobs_and_new_calls_reject_a_null_context_without_a_gpu(lib):
     assert lib.mapper_set_cross_screen(None, 0) == _capi.MAPPER_EINVAL
     assert lib.mapper_set_knn_screen(None, 0) == _capi.MAPPER_EINVAL
     assert lib.mapper_set_band_queue_cap(None, 0) == _capi.MAPPER_EINVAL
+    assert lib.mapper_set_pass1_screen(None, 0) == _capi.MAPPER_EINVAL
+    assert lib.mapper_selftest_mma_error(None, 64, 1, 1, None, None) == _capi.MAPPER_EINVAL
     assert lib.mapper_selftest_wait(None) == _capi.MAPPER_EINVAL
     assert lib.mapper_lens_ex(None, None, 0, 0, 0, 1, None, None, None, 1, None, None) == _capi.MAPPER_EINVAL
     assert lib.mapper_knn_distance(None, None, 0, 0, 0, None, 0, 1, None) == _capi.MAPPER_EINVAL
@@ -115,7 +117,8 @@ int main(void) {
     p.m = 1; p.lens_kind[0] = MAPPER_LENS_L2; p.n_intervals[0] = 10; p.overlap[0] = 0.25;
     p.eps = 1.0; p.min_pts = 5; p.precision = MAPPER_BF16; p.cover_kind = MAPPER_COVER_UNIFORM;
     if (mapper_graph_footprint(1000, 16, &p, &bytes) != MAPPER_OK || bytes == 0) return 4;
-    printf("%s|%s\n", mapper_strerror(MAPPER_OK), mapper_strerror(MAPPER_ETIMEOUT));
+    printf("%s|%s|%zu|%zu\n", mapper_strerror(MAPPER_OK), mapper_strerror(MAPPER_ETIMEOUT),
+           sizeof(mapper_stats), sizeof(mapper_params));
     return 0;
 }
 """)
@@ -126,4 +129,8 @@ int main(void) {
                    check=True, capture_output=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0, (out.returncode, out.stderr)
-    assert out.stdout.strip() == "ok|device wait timed out"
+    ok, timeout, n_stats, n_params = out.stdout.strip().split("|")
+    assert (ok, timeout) == ("ok", "device wait timed out")
+    # the ctypes mirrors of the structs have the C layout's sizes
+    assert int(n_stats) == ctypes.sizeof(_capi.MapperStats)
+    assert int(n_params) == ctypes.sizeof(_capi.MapperParams)

@@ -389,6 +389,43 @@ def test_pass1_shapes_agree(prec):
             c.set_pass1_tile_n(64)
 
 
+@pytest.mark.parametrize("tile_n", [128, 256])
+def test_two_phase_count_pass_equals_three_products(tile_n):
+    """MAPPER_BF16's count pass screens every tile pair with one product and
+    only the tile pairs holding a pair inside that product's band again with
+    three; the graph equals the one of three products everywhere and the
+    oracle's."""
+    w = synth.mixture_100k()
+    Xd = torch.from_numpy(w.X).to("cuda:0")
+    prm = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, mg.BF16)
+    outs = []
+    for mode in (1, 2):
+        with mg.Context(0) as c:
+            c.set_pass1_tile_n(tile_n)
+            c.set_pass1_screen(mode)
+            g = mg.mapper_graph(c, Xd, prm)
+            st = g.stats()
+            out = g.numpy()
+            out["lens"], out["pca"] = g.lens(w.n, 1)
+            out["elem_offsets"], out["elem_points"] = g.cover().numpy()
+            out["labels"], out["core"] = g.clusters().numpy(len(out["elem_points"]))
+            out["stats"] = st
+            outs.append(out)
+            del g
+    one, three = outs
+    assert one["stats"]["tile_pairs_screen1"] == one["stats"]["tile_pairs_tc"] + one["stats"]["tile_pairs_cross"]
+    assert 0 < one["stats"]["tile_pairs_redo"] < one["stats"]["tile_pairs_screen1"]
+    assert three["stats"]["tile_pairs_screen1"] == 0 and three["stats"]["tile_pairs_redo"] == 0
+    # every tile pair is counted once: the same pairs screened either way
+    assert one["stats"]["count_kernel_pairs"] == three["stats"]["count_kernel_pairs"]
+    for k in ("elem_points", "core", "labels", "node_offsets", "node_members", "node_elem", "edges"):
+        assert np.array_equal(one[k], three[k]), k
+    assert_same_graph(w.X, one, w.n_intervals, w.overlap, w.eps, w.min_pts)
+    with mg.Context(0) as c:
+        with pytest.raises(mg.MapperError):
+            c.set_pass1_screen(3)
+
+
 @pytest.mark.parametrize("prec", [mg.BF16, mg.BF16X1])
 @pytest.mark.parametrize("cap", [1, 16])
 def test_band_queue_overflow_exact(prec, cap):

@@ -88,3 +88,51 @@ def test_server_rejects_unknown_dataset_and_request(data):
             srv.submit(5, _params(reqs[0]))
         with pytest.raises(mg.MapperError):
             srv.wait(12345, timeout=0.1)
+
+
+def test_small_request_overtakes_a_blocked_large_one(data):
+    """Budget for one large and one small request: while the first large
+    request runs, a second large one cannot start, and a small request
+    submitted after it starts first (it fits beside the running one)."""
+    _, Xd, reqs = data
+    big = mg.params((mg.LENS_L2,), (0,), (12,), (0.3,), reqs[0]["eps"], 5, mg.FP32)
+    small = mg.params((mg.LENS_L2,), (0,), (4,), (0.2,), 0.5, 5, mg.BF16)
+    fb = mg.graph_footprint(Xd[1].shape[0], Xd[1].shape[1], big)
+    fs = mg.graph_footprint(Xd[2].shape[0], Xd[2].shape[1], small)
+    assert fs < fb
+    with mg.Server(0, n_slots=2, hbm_budget=fb + fs) as srv:
+        ids = [srv.add_dataset(X) for X in Xd]
+        t1 = srv.submit(ids[1], big)
+        t2 = srv.submit(ids[1], big)
+        t3 = srv.submit(ids[2], small)
+        i1, i2, i3 = (srv.wait(t, timeout=120.0)[1] for t in (t1, t2, t3))
+    assert i1["status"] == i2["status"] == i3["status"] == 0
+    # the second large request waited for the first; the small one did not
+    assert i2["queue_s"] >= 0.9 * i1["run_s"]
+    assert i3["queue_s"] < i2["queue_s"]
+
+
+def test_destroy_completes_a_pending_waiter(data):
+    """A thread waiting without a time limit on a request that is still
+    queued when the server is destroyed returns MAPPER_ECANCELED (or the
+    graph, had the request started); destroy does not leave it waiting."""
+    import threading
+    _, Xd, reqs = data
+    srv = mg.Server(0, n_slots=1)
+    ids = [srv.add_dataset(X) for X in Xd]
+    tickets = [srv.submit(ids[r["dataset"]], _params(r)) for r in reqs[:8]]
+    result = {}
+
+    def waiter():
+        try:
+            g, info = srv.wait(tickets[-1])
+            result["status"] = info["status"]
+        except mg.MapperError as e:
+            result["status"] = e.status
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    srv.close()
+    th.join(timeout=120.0)
+    assert not th.is_alive()
+    assert result["status"] in (0, mg._capi.MAPPER_ECANCELED)
