@@ -77,6 +77,8 @@ def _load():
         lib.oracle_dbscan.restype = ctypes.c_int
         lib.oracle_knn_distance.argtypes = [P, i64, i32, i64, P, i64, i32, P]
         lib.oracle_knn_distance.restype = ctypes.c_int
+        lib.oracle_msf.argtypes = [P, i64, i32, i64, P, i64, f64, P, P, P]
+        lib.oracle_msf.restype = i64
         _lib = lib
         return lib
 
@@ -367,3 +369,45 @@ def knn_distance(X, queries, k: int) -> np.ndarray:
     if rc < 0:
         raise ValueError("bad k-distance arguments")
     return out[:qs.size]
+
+
+# ----------------------------------------------------------- single linkage --
+
+def msf(X, pts, eps: float):
+    """Minimum spanning forest of the eps-graph of the rows `pts`
+    (ascending) of X: edges (u, v, d2) with u < v global indices, in the
+    order of the key (d2, u, v) (Kruskal). The single-linkage dendrogram of
+    the element, cut at eps."""
+    X = _f32(X)
+    pts = np.ascontiguousarray(pts, dtype=np.int32)
+    npt = pts.shape[0]
+    u = np.empty(max(npt, 1), dtype=np.int32)
+    v = np.empty(max(npt, 1), dtype=np.int32)
+    d2 = np.empty(max(npt, 1), dtype=np.float64)
+    k = _load().oracle_msf(_ptr(X), X.shape[0], X.shape[1], X.shape[1], _ptr(pts), npt, float(eps), _ptr(u),
+                           _ptr(v), _ptr(d2))
+    if k < 0:
+        raise MemoryError("oracle_msf: out of memory")
+    return u[:k], v[:k], d2[:k]
+
+
+def single_linkage(pts, u, v, d2, h: float):
+    """Single-linkage clusters at height h of one element: the components of
+    the forest edges with d2 <= h * h; label per member = the smallest point
+    index of its component (every point belongs to a cluster)."""
+    pts = np.asarray(pts)
+    pos = {int(p): i for i, p in enumerate(pts)}
+    parent = list(range(len(pts)))
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+
+    for a, b, w in zip(u, v, d2):
+        if w <= h * h:
+            ra, rb = find(pos[int(a)]), find(pos[int(b)])
+            if ra != rb:
+                parent[max(ra, rb)] = min(ra, rb)
+    return np.array([int(pts[find(i)]) for i in range(len(pts))], dtype=np.int64)

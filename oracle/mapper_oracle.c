@@ -541,3 +541,95 @@ int oracle_knn_distance(const float* X, int64_t n, int32_t d, int64_t ld, const 
     }
     return bad ? -1 : 0;
 }
+
+/* ------------------------------------------------------ single linkage -- */
+
+/* Single-linkage clustering (§5: Lum et al. cluster each cover element by
+ * single linkage, where this tool uses DBSCAN) is the minimum spanning tree
+ * of the element's points: cutting it at a height h gives the clusters.
+ * Reading: within one cover element (pts ascending, global indices), the
+ * minimum spanning forest of the eps-graph, whose edges are the pairs with
+ * squared distance d2 <= eps * eps (the DBSCAN distance above), ordered by
+ * the key (d2, smaller point index, larger point index) so that the forest
+ * is unique when distances tie: Kruskal's algorithm, i.e. every pair in key
+ * order, kept iff its points are not joined yet (union-find). Writes the
+ * kept edges in key order: u[k] < v[k] (global indices) and d2[k]; returns
+ * their number (at most np - 1), or -1 if memory runs out. */
+typedef struct {
+    double d2;
+    int32_t lo, hi;
+} ms_edge;
+
+static int cmp_edge(const void* x, const void* y)
+{
+    const ms_edge* a = (const ms_edge*)x;
+    const ms_edge* b = (const ms_edge*)y;
+    if (a->d2 != b->d2) return a->d2 < b->d2 ? -1 : 1;
+    if (a->lo != b->lo) return a->lo < b->lo ? -1 : 1;
+    if (a->hi != b->hi) return a->hi < b->hi ? -1 : 1;
+    return 0;
+}
+
+static int64_t uf_find(int64_t* parent, int64_t x)
+{
+    while (parent[x] != x) {
+        parent[x] = parent[parent[x]];
+        x = parent[x];
+    }
+    return x;
+}
+
+int64_t oracle_msf(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* pts, int64_t np, double eps,
+                   int32_t* u, int32_t* v, double* d2)
+{
+    (void)n;
+    const double eps2 = eps * eps;
+    /* every pair within eps, in member order */
+    int64_t cap = 1024, m = 0;
+    ms_edge* e = (ms_edge*)malloc(sizeof(ms_edge) * (size_t)cap);
+    if (!e) return -1;
+    for (int64_t i = 0; i < np; ++i) {
+        const float* xi = X + (int64_t)pts[i] * ld;
+        for (int64_t j = i + 1; j < np; ++j) {
+            const double s = sqdist(xi, X + (int64_t)pts[j] * ld, d);
+            if (s > eps2) continue;
+            if (m == cap) {
+                cap *= 2;
+                ms_edge* t = (ms_edge*)realloc(e, sizeof(ms_edge) * (size_t)cap);
+                if (!t) { free(e); return -1; }
+                e = t;
+            }
+            e[m].d2 = s;
+            e[m].lo = pts[i];
+            e[m].hi = pts[j];
+            ++m;
+        }
+    }
+    qsort(e, (size_t)m, sizeof(ms_edge), cmp_edge);
+    /* Kruskal: members are found by binary search in pts (ascending) */
+    int64_t* parent = (int64_t*)malloc(sizeof(int64_t) * (size_t)(np > 0 ? np : 1));
+    if (!parent) { free(e); return -1; }
+    for (int64_t i = 0; i < np; ++i) parent[i] = i;
+    int64_t kept = 0;
+    for (int64_t k = 0; k < m && kept + 1 < np; ++k) {
+        int64_t ia = 0, ib = 0;
+        {
+            int64_t lo = 0, hi = np - 1;
+            while (lo < hi) { int64_t mid = (lo + hi) / 2; if (pts[mid] < e[k].lo) lo = mid + 1; else hi = mid; }
+            ia = lo;
+            lo = 0; hi = np - 1;
+            while (lo < hi) { int64_t mid = (lo + hi) / 2; if (pts[mid] < e[k].hi) lo = mid + 1; else hi = mid; }
+            ib = lo;
+        }
+        const int64_t ra = uf_find(parent, ia), rb = uf_find(parent, ib);
+        if (ra == rb) continue;
+        parent[ra < rb ? rb : ra] = ra < rb ? ra : rb;
+        u[kept] = e[k].lo;
+        v[kept] = e[k].hi;
+        d2[kept] = e[k].d2;
+        ++kept;
+    }
+    free(parent);
+    free(e);
+    return kept;
+}
