@@ -273,10 +273,16 @@ def _roofline(prec, w, st, stats, n_sm):
     tp3 = st["tile_pairs_tc"] if not tp1 else st.get("tile_pairs_redo", 0)
     ns = 1 if prec == mg.BF16X1 else 3
     kp = -(-w.d // 64) * 64 * 128.0 * 128.0 * 2.0
-    executed = ((tp1 * kp + tp3 * 3 * kp) if tp1 else ns * kp * st["tile_pairs_tc"]) / (kms * 1e-3) / 1e12
-    desc = ("tc_kernel count pass (tcgen05 BF16): one product per tile pair, three products for the "
-            "tile pairs whose one-product band is not empty" if tp1 else
-            "tc_kernel<%d,1> (tcgen05 BF16 count pass): %d BF16 products per pair" % (ns, ns))
+    first = 3 if prec == mg.FP8 else 1                 # products of the first phase
+    executed = ((tp1 * first * kp + tp3 * 3 * kp) if tp1 else ns * kp * st["tile_pairs_tc"]) / (kms * 1e-3) / 1e12
+    if prec == mg.FP8:
+        desc = ("tc_kernel count pass (tcgen05): three FP8 E4M3 products per tile pair, then three BF16 "
+                "products for the 32 x 32 blocks whose FP8 band is not empty" if tp1 else
+                "tc_kernel (tcgen05 FP8 E4M3 count pass): three products per pair")
+    else:
+        desc = ("tc_kernel count pass (tcgen05 BF16): one product per tile pair, three products for the "
+                "32 x 32 blocks whose one-product band is not empty" if tp1 else
+                "tc_kernel<%d,1> (tcgen05 BF16 count pass): %d BF16 products per pair" % (ns, ns))
     return kms, {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                  "frac": achieved / peak, "traffic": _traffic(kpairs, st["tile_pairs_tc"]),
                  "kernel": desc + "; achieved counts 2d algorithmic flops per point pair screened",
@@ -308,7 +314,7 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    prec = {"bf16": mg.BF16, "bf16x1": mg.BF16X1, "fp32": mg.FP32}[args.precision]
+    prec = {"bf16": mg.BF16, "bf16x1": mg.BF16X1, "fp32": mg.FP32, "fp8": mg.FP8}[args.precision]
     w = synth.clusters_1m_d256(args.n)
     local_cpus = _bind_local_cpus(local)
     Xh = torch.from_numpy(w.X).pin_memory()
@@ -352,7 +358,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": ms / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if prec == mg.FP32 else "bf16+f64",
+        "vs_baseline": None, "dtype": {mg.FP32: "f32+f64", mg.FP8: "fp8+bf16+f64"}.get(prec, "bf16+f64"),
         "data": "synthetic",
         "config": {"workload": w.name + ("" if args.lens == "l2" else "_" + args.lens)
                    + ("" if args.cover == "uniform" else "_balanced"), "n": w.n, "d": w.d,
@@ -484,7 +490,7 @@ def run_serving(args):
     import paper_2011_03209_gb300 as mg
 
     torch.cuda.set_device(0)
-    prec = {"bf16": mg.BF16, "bf16x1": mg.BF16X1, "fp32": mg.FP32}[args.precision]
+    prec = {"bf16": mg.BF16, "bf16x1": mg.BF16X1, "fp32": mg.FP32, "fp8": mg.FP8}[args.precision]
     r = measure_serving(args.requests, args.warmup, args.rate, args.slots, prec)
     print(json.dumps({
         "metric": "serving graphs/s (9 resident clouds, Poisson stream)", "value": r["graphs_per_s"],
@@ -567,7 +573,7 @@ def run_sweep(args):
     import paper_2011_03209_gb300 as mg
 
     torch.cuda.set_device(0)
-    prec = {"bf16": mg.BF16, "bf16x1": mg.BF16X1, "fp32": mg.FP32}[args.precision]
+    prec = {"bf16": mg.BF16, "bf16x1": mg.BF16X1, "fp32": mg.FP32, "fp8": mg.FP8}[args.precision]
     sampler = ClockSampler(0)
     sampler.start()
     r = measure_sweep(args.steps, args.warmup, prec)
@@ -703,7 +709,7 @@ def run_sharded(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    prec = {"bf16": mg.BF16, "bf16x1": mg.BF16X1, "fp32": mg.FP32}[args.precision]
+    prec = {"bf16": mg.BF16, "bf16x1": mg.BF16X1, "fp32": mg.FP32, "fp8": mg.FP8}[args.precision]
     w = synth.clusters_1m_d256(args.n)
     Xd = torch.from_numpy(w.X).to(f"cuda:{local}")
     stream = torch.cuda.Stream()
@@ -754,7 +760,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "bf16x1", "fp32"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "bf16x1", "fp32", "fp8"])
     ap.add_argument("--ref-budget", type=float, default=12.0,
                     help="seconds of oracle DBSCAN per reference sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")

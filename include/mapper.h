@@ -103,8 +103,14 @@ typedef enum mapper_precision {
     MAPPER_BF16 = 1,         /* tcgen05 tensor cores, BF16 in, FP32 accumulate; rows
                                 centred per group and split hi + lo: three products,
                                 a narrow band */
-    MAPPER_BF16X1 = 2        /* as MAPPER_BF16 with the hi part only: one product, a
+    MAPPER_BF16X1 = 2,       /* as MAPPER_BF16 with the hi part only: one product, a
                                 band about 2^8 times wider */
+    MAPPER_FP8 = 3           /* count pass first on FP8 E4M3 tensor cores (kind::f8f6f4):
+                                rows centred per group, scaled by one power of two per
+                                128-row tile, split hi + lo (three products, FP32
+                                accumulate); the 32 x 32 blocks with a pair in that band
+                                are counted again with the three BF16 products of
+                                MAPPER_BF16; the union pass is MAPPER_BF16's */
 } mapper_precision;
 
 typedef struct mapper_ctx mapper_ctx;
@@ -201,12 +207,14 @@ int mapper_set_timing(mapper_ctx* ctx, int enabled);
  * work item, 256 = two tile pairs sharing their first tile. Other values:
  * MAPPER_EINVAL. */
 int mapper_set_pass1_tile_n(mapper_ctx* ctx, int tile_n);
-/* Count-pass screen of MAPPER_BF16 (a tuning knob; results do not depend on
- * it): 0 = the default (1), 1 = two phases: every tile pair first with one
- * product (hi.hi, the band of MAPPER_BF16X1); the tile pairs that have a pair
- * inside that band are counted by a second pass with three products, the
- * others are final after the first, 2 = three products for every tile pair.
- * Other values: MAPPER_EINVAL. */
+/* Count-pass screen of MAPPER_BF16 and MAPPER_FP8 (a tuning knob; results do
+ * not depend on it): 0 = the default (1), 1 = two phases: every tile pair
+ * first with one BF16 product (hi.hi, the band of MAPPER_BF16X1), or three
+ * FP8 products; each 32 x 32 block of a tile pair that has a pair inside
+ * that band is counted by a second pass with three BF16 products, the others
+ * are final after the first, 2 = one phase: three products (BF16, or FP8
+ * with its band re-decided in FP64) for every tile pair. Other values:
+ * MAPPER_EINVAL. */
 int mapper_set_pass1_screen(mapper_ctx* ctx, int mode);
 /* Where the BF16 precisions screen mixed tile pairs across two segments of
  * one element (a tuning knob; results do not depend on it): 0 = on the
@@ -227,16 +235,18 @@ int mapper_set_band_queue_cap(mapper_ctx* ctx, int64_t entries);
  * a pass reports when a wait runs out; the context stays usable. */
 int mapper_selftest_wait(mapper_ctx* ctx);
 /* Accumulation self-test of the tensor-core screen (the paper has no
- * counterpart): random BF16 rows (magnitudes 2^-4 .. 2^5, random signs) of
- * row pitch dp (a multiple of 32 in [32, 4096]) through the screen's tcgen05
- * products (1: hi.hi, 3: hi.hi + hi.lo + lo.hi) for four 128 x 128 tile
- * pairs. *observed = the largest |accumulator - exact sum| over them,
+ * counterpart): random rows of row pitch dp (a multiple of 32 in [32, 4096])
+ * through the screen's tcgen05 products (1: hi.hi, 3: hi.hi + hi.lo + lo.hi)
+ * for four 128 x 128 tile pairs; format 0 = BF16 parts (magnitudes 2^-4 ..
+ * 2^5, kind::f16), 1 = FP8 E4M3 parts (hi 2^-4 .. 2^5, lo 2^-8 .. 2^1,
+ * kind::f8f6f4). *observed = the largest |accumulator - exact sum| over them,
  * relative to the sum of the magnitudes of the products; *modelled = the
  * accumulation term the screen's error bound assumes, relative to the same
- * sum (dp / 16 * products steps of 2^-22 each, times (1 + 2u')^2). The bound
- * is sound on this hardware only if observed stays below modelled. */
-int mapper_selftest_mma_error(mapper_ctx* ctx, int32_t dp, int32_t products, uint64_t seed, double* observed,
-                              double* modelled);
+ * sum (BF16: (dp / 16 * products + 8) units of 2^-22, times (1 + 2u')^2;
+ * FP8: (dp / 32 * products + 8) units, times 1.3). The bound is sound on
+ * this hardware only if observed stays below modelled. */
+int mapper_selftest_mma_error(mapper_ctx* ctx, int32_t dp, int32_t products, int32_t format, uint64_t seed,
+                              double* observed, double* modelled);
 /* Screen of mapper_knn_distance (a tuning knob; results do not depend on
  * it): 0 = tensor cores (default), 1 = tensor cores, 2 = the FP32 CUDA-core
  * screen. Other values: MAPPER_EINVAL. */

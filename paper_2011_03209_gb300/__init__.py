@@ -14,14 +14,14 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _capi
-from ._capi import (BF16, BF16X1, COVER_BALANCED, COVER_UNIFORM, FP32, LENS_COORD, LENS_DENSITY, LENS_ECC,
+from ._capi import (BF16, BF16X1, COVER_BALANCED, COVER_UNIFORM, FP8, FP32, LENS_COORD, LENS_DENSITY, LENS_ECC,
                     LENS_ECC_INF, LENS_L2, LENS_LINF, LENS_PCA,
                     MapperError, MapperParams)
 
 __all__ = [
     "Context", "Cover", "Clusters", "Graph", "MapperError", "mapper_lens", "mapper_cover",
     "mapper_cluster", "mapper_nerve", "mapper_graph", "params", "LENS_L2", "LENS_COORD",
-    "LENS_PCA", "LENS_ECC", "LENS_LINF", "LENS_DENSITY", "LENS_ECC_INF", "COVER_UNIFORM", "COVER_BALANCED", "FP32", "BF16", "BF16X1", "mapper_dbscan_noalloc", "Server", "graph_footprint",
+    "LENS_PCA", "LENS_ECC", "LENS_LINF", "LENS_DENSITY", "LENS_ECC_INF", "COVER_UNIFORM", "COVER_BALANCED", "FP32", "BF16", "BF16X1", "FP8", "mapper_dbscan_noalloc", "Server", "graph_footprint",
     "mapper_graph_sweep", "mapper_cover_subset", "mapper_nerve_from_nodes", "mapper_knn_distance",
 ]
 
@@ -73,12 +73,14 @@ class Context:
         three for the tile pairs with a band pair), 2 three products."""
         _capi.check(self._lib.mapper_set_pass1_screen(self.h, int(mode)), "mapper_set_pass1_screen")
 
-    def selftest_mma_error(self, dp: int, products: int, seed: int = 1):
+    def selftest_mma_error(self, dp: int, products: int, seed: int = 1, fmt: int = 0):
         """(observed, modelled) accumulation error of the tensor-core screen's
-        products on random BF16 rows, both relative to the magnitude sum."""
+        products on random BF16 (fmt 0) or FP8 E4M3 (fmt 1) rows, both
+        relative to the magnitude sum."""
         o, m = ctypes.c_double(), ctypes.c_double()
-        _capi.check(self._lib.mapper_selftest_mma_error(self.h, int(dp), int(products), int(seed), ctypes.byref(o),
-                                                        ctypes.byref(m)), "mapper_selftest_mma_error")
+        _capi.check(self._lib.mapper_selftest_mma_error(self.h, int(dp), int(products), int(fmt), int(seed),
+                                                        ctypes.byref(o), ctypes.byref(m)),
+                    "mapper_selftest_mma_error")
         return o.value, m.value
 
     def set_band_queue_cap(self, entries: int) -> None:

@@ -24,7 +24,7 @@ MAPPER_ECANCELED = -8
 
 LENS_L2, LENS_COORD, LENS_PCA, LENS_ECC, LENS_LINF, LENS_DENSITY, LENS_ECC_INF = 0, 1, 2, 3, 4, 5, 6
 COVER_UNIFORM, COVER_BALANCED = 0, 1
-FP32, BF16, BF16X1 = 0, 1, 2
+FP32, BF16, BF16X1, FP8 = 0, 1, 2, 3
 
 # every symbol include/mapper.h declares
 EXPORTS = (
@@ -150,7 +150,7 @@ def load(path: str | None = None):
             "mapper_set_knn_screen": (ctypes.c_int, [P, ctypes.c_int]),
             "mapper_set_band_queue_cap": (ctypes.c_int, [P, i64]),
             "mapper_set_pass1_screen": (ctypes.c_int, [P, ctypes.c_int]),
-            "mapper_selftest_mma_error": (ctypes.c_int, [P, i32, i32, ctypes.c_uint64, ctypes.POINTER(f64),
+            "mapper_selftest_mma_error": (ctypes.c_int, [P, i32, i32, i32, ctypes.c_uint64, ctypes.POINTER(f64),
                                                          ctypes.POINTER(f64)]),
             "mapper_cover_subset": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.POINTER(P)]),
             "mapper_nerve_from_nodes": (ctypes.c_int, [P, ctypes.c_int64, ctypes.c_int64, P, P, P,

@@ -297,7 +297,7 @@ int tune_pass1(mapper_ctx* ctx, const PassArgs& a, const TcArgs& t, int64_t n_pa
         *tile_n = ctx->pass1_forced;
         return MAPPER_OK;
     }
-    const uint64_t key = ((uint64_t)a.dp << 8) | (uint64_t)t.ns;
+    const uint64_t key = ((uint64_t)a.dp << 8) | ((uint64_t)t.f8 << 4) | (uint64_t)t.ns;
     auto it = ctx->pass1_tile_n.find(key);
     if (it != ctx->pass1_tile_n.end()) {
         *tile_n = it->second;
@@ -381,12 +381,13 @@ struct CountsOut {
 
 int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
                 const std::shared_ptr<CoverData>& cov, double eps, int32_t min_pts, int32_t precision,
-                std::shared_ptr<ClusterData>* out, int* nonfinite_dev, const TileLayout* layout = nullptr,
+                std::shared_ptr<ClusterData>* out, int* nonfinite_dev, TileLayout* layout = nullptr,
                 const CountsOut* counts_out = nullptr, const PivotSet* pivots = nullptr)
 {
     if (!(eps > 0.0) || !std::isfinite(eps)) return fail(MAPPER_EINVAL, "eps must be finite and > 0");
     if (min_pts < 1) return fail(MAPPER_EINVAL, "min_pts must be >= 1");
-    if (precision != MAPPER_FP32 && precision != MAPPER_BF16 && precision != MAPPER_BF16X1)
+    if (precision != MAPPER_FP32 && precision != MAPPER_BF16 && precision != MAPPER_BF16X1 &&
+        precision != MAPPER_FP8)
         return fail(MAPPER_EINVAL, "unknown precision");
     if (cov->n != n) return fail(MAPPER_EINVAL, "cover was built for another point count");
     cudaStream_t s = ctx->stream->s;
@@ -395,7 +396,8 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     const bool use_tc = precision != MAPPER_FP32;
     const int cap = (!counts_out && min_pts >= 2 && min_pts - 1 <= 64) ? min_pts - 1 : 0;
     const double rows_est = (double)M + 128.0 * (double)E;
-    const double est = rows_est * dp * (use_tc ? 8.0 : 4.0) + rows_est * (40.0 + 4.0 * cap);
+    const double est = rows_est * dp * (use_tc ? (precision == MAPPER_FP8 ? 10.0 : 8.0) : 4.0) +
+                       rows_est * (40.0 + 4.0 * cap);
     if (ctx->budget && est > (double)ctx->budget)
         return fail(MAPPER_ENOMEM, "estimated scratch exceeds the context's HBM budget");
 
@@ -433,6 +435,10 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         if (rc) return rc;
         layout = &own;
     }
+    // FP8 screen: E4M3 operands with per-tile scales beside the BF16 ones (the
+    // union pass and the second phase of the count pass stay in BF16)
+    const bool f8 = precision == MAPPER_FP8;
+    if (f8 && (rc = fp8_operands(layout, X, ld, d, dp, s))) return rc;
     const TileLayout& L = *layout;
     PairLists PL;
     if ((rc = classify_pairs(L, X, ld, d, dp, E, eps, use_tc, &PL, s))) return rc;
@@ -518,6 +524,8 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         t.rn2 = L.rn2.as<float>();
         t.rn = L.rn.as<float>();
         t.rl = L.rl.as<float>();
+        t.tmax = L.tmax.as<float4>();
+        t.tn2min = L.tn2min.as<float>();
         t.R = R;
         t.ns = precision == MAPPER_BF16X1 ? 1 : 3;
         t.num_sms = ctx->num_sms;
@@ -534,30 +542,43 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     }
 
     TcArgs tx{};                                                  // the cross-segment operands
-    Buf xAh, xAl, xrn2, xrn, xrl;
+    Buf xAh, xAl, xrn2, xrn, xrl, xtmax, xtn2min;
     if (cross_tc) {
-        if ((rc = cross_operands(L, X, ld, d, dp, E, &xAh, &xAl, &xrn2, &xrn, &xrl, s))) return rc;
+        if ((rc = cross_operands(L, X, ld, d, dp, E, &xAh, &xAl, &xrn2, &xrn, &xrl, &xtmax, &xtn2min, s))) return rc;
         tx = t;
         tx.Ah = xAh.p;
         tx.Al = xAl.p;
         tx.rn2 = xrn2.as<float>();
         tx.rn = xrn.as<float>();
         tx.rl = xrl.as<float>();
+        tx.tmax = xtmax.as<float4>();
+        tx.tn2min = xtn2min.as<float>();
     }
     st.tile_pairs_cross = cross_tc ? PL.n[kListSimt] : 0;
-    // MAPPER_BF16 count pass in two phases: every tile pair with one product
-    // (hi.hi); only the tile pairs with a pair inside that product's wider band
-    // run again with three products (hi.hi + hi.lo + lo.hi), as a whole
+    // Count pass in two phases (MAPPER_BF16: one BF16 product first; MAPPER_FP8:
+    // three FP8 products first): the 32 x 32 sub-blocks with a pair inside the
+    // first screen's band run again with three BF16 products
+    // (hi.hi + hi.lo + lo.hi); the others are final after the first
     const bool two_phase = use_tc && t.ns == 3 && ctx->screen_mode != 2;
-    Buf redo, redo_n;
+    TcArgs t8 = t;                                                // the FP8 operands of the first phase
+    if (f8) {
+        t8.f8 = true;
+        t8.Ah = L.Fh.p;
+        t8.Al = L.Fl.p;
+        t8.rl = L.frl.as<float>();
+        t8.tmax = L.ftmax.as<float4>();
+    }
+    Buf redo, redo_mask, redo_q;
     if (two_phase) {
         const int64_t rcap = std::max<int64_t>(std::max(PL.n[kListTC], cross_tc ? PL.n[kListSimt] : 0), 1);
         CK(redo.alloc(sizeof(int2) * rcap, s), "alloc");
-        CK(redo_n.alloc(sizeof(unsigned long long), s), "alloc");
+        CK(redo_mask.alloc(sizeof(uint32_t) * rcap, s), "alloc");
+        CK(redo_q.alloc(sizeof(int32_t) * rcap, s), "alloc");
     }
     int tile_n = 0;
-    TcArgs t_tune = t, tx_tune = tx;
-    if (two_phase) t_tune.ns = tx_tune.ns = 1;
+    TcArgs t_tune = f8 ? t8 : t, tx_tune = tx;
+    if (two_phase && !f8) t_tune.ns = 1;
+    if (two_phase) tx_tune.ns = 1;
     if (use_tc && PL.n[kListTC] > 0 && (rc = tune_pass1(ctx, a_tc, t_tune, PL.n[kListTC], R, cap, s, &tile_n)))
         return rc;
     if (use_tc && PL.n[kListTC] == 0 && cross_tc &&
@@ -577,9 +598,9 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     Buf groups, group_pos, xgroups, xgroup_pos;
     // pass 1 on the tensor cores of one pair list (its events bracket the
     // count kernels: both lists' launches when the cross list runs there)
-    auto tc_count = [&](const PassArgs& pa, const TcArgs& base, int64_t np, Buf& gr, Buf& gp, bool first,
-                        bool last) -> int {
-        TcArgs t1 = base;
+    auto tc_count = [&](const PassArgs& pa, const TcArgs& base, const TcArgs& first_screen, int64_t np, Buf& gr,
+                        Buf& gp, bool first, bool last) -> int {
+        TcArgs t1 = first_screen;
         t1.ev_begin = first ? tev[0] : nullptr;
         t1.ev_end = last && !two_phase ? tev[1] : nullptr;
         if (tile_n == 256) {
@@ -590,14 +611,20 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
             t1.groups_dev = reinterpret_cast<const unsigned long long*>(gp.as<int64_t>() + np);
         }
         if (!two_phase) return tc_pass(1, pa, t1, np, s);
-        t1.ns = 1;
+        if (!t1.f8) t1.ns = 1;
         t1.defer = true;
-        t1.redo = redo.as<int2>();
-        t1.redo_n = redo_n.as<unsigned long long>();
-        CK(cudaMemsetAsync(redo_n.p, 0, sizeof(unsigned long long), s), "memset");
+        t1.redo_mask = redo_mask.as<uint32_t>();
+        CK(cudaMemsetAsync(redo_mask.p, 0, sizeof(uint32_t) * np, s), "memset");
         int r2;
         if ((r2 = tc_pass(1, pa, t1, np, s))) return r2;
-        // second phase: the deferred tile pairs (their number stays on the device)
+        // second phase: the tile pairs with deferred sub-blocks in list order,
+        // grouped by tile A as in the first, counting only those sub-blocks
+        // (their number stays on the device)
+        Buf rpos, rgr, rgp;
+        if ((r2 = tc_redo_list(pa.pairs, redo_mask.as<uint32_t>(), np, redo.as<int2>(), redo_q.as<int32_t>(), &rpos,
+                               s)))
+            return r2;
+        const unsigned long long* n_redo = reinterpret_cast<const unsigned long long*>(rpos.as<int64_t>() + np);
         PassArgs p2 = pa;
         p2.pairs = redo.as<int2>();
         p2.pair_hit = nullptr;
@@ -605,16 +632,26 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         t2.groups = nullptr;
         t2.n_groups = 0;
         t2.groups_dev = nullptr;
-        t2.n_dev = redo_n.as<unsigned long long>();
+        t2.n_dev = n_redo;
+        if (tile_n == 256) {
+            if ((r2 = tc_groups_dev(redo.as<int2>(), np, n_redo, &rgr, &rgp, s))) return r2;
+            t2.groups = rgr.as<int2>();
+            t2.n_groups = np;
+            t2.groups_dev = reinterpret_cast<const unsigned long long*>(rgp.as<int64_t>() + np);
+        }
+        t2.sub_mask = redo_mask.as<uint32_t>();
+        t2.sub_q = redo_q.as<int32_t>();
         t2.ev_begin = nullptr;
         t2.ev_end = last ? tev[1] : nullptr;
         return tc_pass(1, p2, t2, np, s);
     };
     if (use_tc) {
         const bool x_last = cross_tc && PL.n[kListSimt] > 0;
-        if (PL.n[kListTC] > 0 && (rc = tc_count(a_tc, t, PL.n[kListTC], groups, group_pos, true, !x_last)))
+        if (PL.n[kListTC] > 0 &&
+            (rc = tc_count(a_tc, t, f8 ? t8 : t, PL.n[kListTC], groups, group_pos, true, !x_last)))
             return rc;
-        if (x_last && (rc = tc_count(a_simt, tx, PL.n[kListSimt], xgroups, xgroup_pos, PL.n[kListTC] == 0, true)))
+        if (x_last &&
+            (rc = tc_count(a_simt, tx, tx, PL.n[kListSimt], xgroups, xgroup_pos, PL.n[kListTC] == 0, true)))
             return rc;
     }
     else CK(simt_pass(1, a_tc, PL.n[kListTC], s), "pass 1 tc list");
@@ -976,13 +1013,13 @@ int mapper_selftest_wait(mapper_ctx* ctx)
     return tc_wait_selftest(ctx->stream->s);
 }
 
-int mapper_selftest_mma_error(mapper_ctx* ctx, int32_t dp, int32_t products, uint64_t seed, double* observed,
-                              double* modelled)
+int mapper_selftest_mma_error(mapper_ctx* ctx, int32_t dp, int32_t products, int32_t format, uint64_t seed,
+                              double* observed, double* modelled)
 {
     int rc = check_ctx(ctx);
     if (rc) return rc;
     if (!observed || !modelled) return fail(MAPPER_EINVAL, "null output");
-    return tc_mma_probe(products, dp, seed, ctx->num_sms, observed, modelled, ctx->stream->s);
+    return tc_mma_probe(products, format, dp, seed, ctx->num_sms, observed, modelled, ctx->stream->s);
 }
 
 int mapper_set_knn_screen(mapper_ctx* ctx, int mode)
@@ -1366,6 +1403,7 @@ int mapper_graph_footprint(int64_t n, int32_t d, const mapper_params* p, size_t*
     auto cluster_bytes = [&](double M, double E, int cap) {
         const double rows = 1.1 * M + 128.0 * E;
         double b = rows * dp * (tc ? 12.0 : 4.0);                // FP32 rows (+ BF16 hi, lo, twice)
+        if (p->precision == MAPPER_FP8) b += rows * dp * 2.0;   // FP8 hi, lo
         b += tc ? (double)n * dp * 4.0 : 0.0;                     // pivot assignment operands
         b += rows * (29.0 + 4.0 * cap) + M * 40.0;
         b += 3.0 * 8.0 * rows * rows / (128.0 * 128.0) / std::max(1.0, E);   // tile-pair lists

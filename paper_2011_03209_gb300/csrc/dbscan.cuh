@@ -125,6 +125,24 @@ cudaError_t select_delta(const int2* pairs, int64_t n, const unsigned long long*
 cudaError_t filter_joined(const PassArgs& a, int64_t T, int2* tile_roots, const int2* pairs, int64_t n,
                           const unsigned long long* n_dev, int2* out, unsigned long long* count, cudaStream_t s);
 
+// --- single-linkage forest (k_mst.cu)
+// Edges of the minimum spanning forests of the eps-graphs of all elements:
+// points u < v, element, the two cover slots (su < sv) and the FP64 d2; n
+// edges (capacity M), in no particular order.
+struct ForestOut {
+    Buf u, v, elem, su, sv, d2;
+    int64_t n = 0;
+};
+// a: the rows of a tile layout (G or X via row_pt, dp, d, tile_n, row_pt,
+// eps2, hi_thr of fp32_thresholds) and a.pairs[0 .. n_pairs) the element tile
+// pairs not certified all-out at eps. Returns a mapper_status.
+int msf_forest(const PassArgs& a, const int32_t* row_slot, const int32_t* slot_point, const int32_t* slot_elem,
+               int64_t M, int64_t R, int64_t T, int64_t n_pairs, ForestOut* out, cudaStream_t s);
+// Single-linkage clusters at height h (edges with d2 <= h^2) in cover-slot
+// space, in the layout of rows_to_slots (every slot a member and core).
+int msf_cut(const ForestOut& f, const int32_t* slot_point, int64_t M, double h, int32_t* lab, int32_t* is_root,
+            int32_t* is_member, int64_t* slot_label, uint8_t* core, cudaStream_t s);
+
 // --- nodes and nerve (k_nerve.cu)
 // Nerve keys (point << 32 | node) of the members of nodes given by offsets.
 cudaError_t node_member_keys(const int64_t* node_off, int64_t N, int64_t G, const int32_t* members,
@@ -163,6 +181,11 @@ struct TileLayout {
     Buf Ah, Al;                  // [R x dp] BF16 centred rows (hi and lo parts)
     Buf rn2, rn;                 // [R] FP32 |a|^2 and |a| (rounded up)
     Buf rl;                      // [R] FP32 |a - hi| (rounded up): the residual of the hi part
+    Buf tmax;                    // [T] float4: largest |a|^2, |a|, |a - hi| of each tile's rows
+    Buf tn2min;                  // [T] smallest |a|^2 of each tile's valid rows
+    Buf Fh, Fl;                  // [R x dp] FP8 E4M3 parts of a / s (s: the tile's scale), if built
+    Buf frl;                     // [R] |a - s hi| (FP8 hi part), rounded up
+    Buf ftmax;                   // [T] float4: largest |a|^2, |a|, frl of each tile, and its scale s
 };
 
 struct PairLists {
@@ -200,6 +223,10 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
 // not gathered).
 int classify_pairs(const TileLayout& L, const float* X, int64_t ld, int d, int dp, int64_t E, double eps,
                    bool use_tc, PairLists* P, cudaStream_t s);
+// FP8 E4M3 operands of a tile layout built with BF16 operands (needs its
+// centres and tmax): per tile a power-of-two scale s, hi and lo parts of a / s
+// (Fh, Fl), frl and ftmax. A no-op when already built. Returns a mapper_status.
+int fp8_operands(TileLayout* L, const float* X, int64_t ld, int d, int dp, cudaStream_t s);
 // BF16 hi + lo operands of rows row_pt[.] of X (T tiles of 128 rows, the
 // first tile_n[t] of tile t valid, the rest zero), centred on cents[tile_cent[t]]
 // (dp floats each), with FP32 |a|^2 and |a| rounded up.
@@ -208,8 +235,9 @@ cudaError_t centred_operands(const float* X, int64_t ld, int d, int dp, const in
                              float* rn, cudaStream_t s);
 // Tensor-core operands for the CUDA-core list (tile pairs of one element, two
 // segments): every row centred on its element's centre, BF16 hi + lo, with
-// FP32 |a|^2, and |a| and |a - hi| rounded up (R rows each).
+// FP32 |a|^2, and |a| and |a - hi| rounded up (R rows each), their largest
+// values per tile (T float4) and the smallest |a|^2 per tile.
 int cross_operands(const TileLayout& L, const float* X, int64_t ld, int d, int dp, int64_t E, Buf* Ah, Buf* Al,
-                   Buf* rn2, Buf* rn, Buf* rl, cudaStream_t s);
+                   Buf* rn2, Buf* rn, Buf* rl, Buf* tmax, Buf* tn2min, cudaStream_t s);
 
 }  // namespace mgb

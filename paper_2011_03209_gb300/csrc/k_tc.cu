@@ -63,17 +63,21 @@ struct TcParams {
     double A1, A2, A3;                        // bound constants
     float A1f, A2f, A3f;                      // ... rounded up to FP32
     float K0f, K1f, K2f;                      // bound from the residual norms (rl set), rounded up
+    float K4f, K5f;                           // FP8: subnormal-floor terms of the bound
     float eps2_lo, eps2_hi;                   // eps^2 rounded down / up to FP32
     uint2* queue;                             // band pairs: (row a, row b | flags << 30)
     unsigned long long* queue_n;
     unsigned long long queue_cap;
     int* err;                                 // 1: a wait timed out
-    // pass 1, one-product screen of the two-phase count pass: a tile pair with
-    // any pair in the band is not counted here but appended to redo[] (and
-    // flagged in pair_hit) for a three-product pass
+    // pass 1, one-product screen of the two-phase count pass: a sub-block with
+    // any pair in the band is not counted here but marked in redo_mask (and
+    // its pair flagged in pair_hit) for a three-product pass
     int defer;
-    int2* redo;
-    unsigned long long* redo_n;
+    uint32_t* redo_mask;                      // first phase: deferred sub-blocks per pair (bit quad * 4 + part)
+    const uint32_t* sub_mask;                 // second phase: sub-blocks to count per pair: sub_mask[sub_q[q]]
+    const int32_t* sub_q;
+    const float4* tmax;                       // count pass: per tile largest |b|^2, |b|, |b - hi|
+    const float* tn2min;                      // count pass: per tile smallest |b|^2 (valid rows)
     // k-distance screen (MODE 3): CTA t = (query tile t / kq_chunks, chunk t % kq_chunks)
     // against point tiles chunk * kq_ct .. + kq_ct of the kq_tp point tiles; query
     // tile u is operand tile kq_tp + u
@@ -162,6 +166,20 @@ constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kT 
 constexpr uint32_t kIdesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(2 * kT >> 3) << 17) |
                              ((uint32_t)(kT >> 4) << 24);
 
+// kind::f8f6f4, A = B = E4M3 (format 0), D = F32, both K-major: K = 32 per
+// instruction, the same 32 bytes of a row as K = 16 of BF16
+constexpr uint32_t kIdescF8 = (1u << 4) | ((uint32_t)(kT >> 3) << 17) | ((uint32_t)(kT >> 4) << 24);
+constexpr uint32_t kIdescF8x2 = (1u << 4) | ((uint32_t)(2 * kT >> 3) << 17) | ((uint32_t)(kT >> 4) << 24);
+
+__device__ __forceinline__ void mma_f8_id(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(
+            tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
 __device__ __forceinline__ void mma_bf16_id(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                             uint32_t acc)
 {
@@ -205,6 +223,32 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v)
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// u = fl(m u + n) for two columns at once (packed FMA, each lane correctly
+// rounded as fmaf).
+__device__ __forceinline__ void fma2_inplace(float& u0, float& u1, float m, float n0, float n1)
+{
+    unsigned long long x, c, mm, r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(u0), "f"(u1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(c) : "f"(n0), "f"(n1));
+    asm("mov.b64 %0, {%1, %1};" : "=l"(mm) : "f"(m));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(x), "l"(mm), "l"(c));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(u0), "=f"(u1) : "l"(r));
+}
+
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
@@ -320,7 +364,8 @@ struct SmemTail {
     float red[2][12];                          // max |b|^2, |b| and |b - hi| of the columns, per warp
     __align__(16) float nbn[2][kT];            // -|b|^2 of the pair's columns
     __align__(16) float nbr[2][kT];            // k-distance pass: |b| (rounded up) of the pair's columns
-    uint32_t colmask[4][kT];                   // count pass: neighbour bits per column (by row quadrant)
+    __align__(16) float wn[kEpiWarps][32];     // count pass: -|b|^2 of each warp's 32 columns
+    uint32_t colmask[4][kT];                   // union pass: neighbour bits per column (by row quadrant)
     uint32_t rowmask[kT / 32][kT];             // neighbour bits per row (by 32-column chunk)
     int par[2][2 * kT];                        // union pass: local union-find / component
     int groot[2][2 * kT];                      // union pass: global root of each core row
@@ -440,7 +485,7 @@ struct TcShape {
 // W = 1: one tile pair per work item. W = 2: a group of one or two tile
 // pairs sharing tile A, computed as one N = 256 product (both B tiles
 // stacked), which halves the A loads; the epilogue takes its pairs in turn.
-template <int NS, int MODE, int W>
+template <int NS, int MODE, int W, int F>
 __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__ CUtensorMap mAh,
                                                          const __grid_constant__ CUtensorMap mAl,
                                                          const TcParams P)
@@ -564,7 +609,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             for (int64_t g = g_begin; g < g_end && !*abort; g += g_step, ++it) {
                 const int3 itm = item(g);
                 const bool diag = W == 1 && itm.x == itm.y;
-                const uint32_t idesc = W == 2 && itm.z >= 0 ? kIdesc2 : kIdesc;
+                const uint32_t idesc = F ? (W == 2 && itm.z >= 0 ? kIdescF8x2 : kIdescF8)
+                                         : (W == 2 && itm.z >= 0 ? kIdesc2 : kIdesc);
                 const int buf = it & 1;
                 const uint32_t acc_phase = (uint32_t)((it >> 1) & 1);
                 if (!mbar_wait(&S.acc_empty[buf], acc_phase ^ 1, abort)) break;
@@ -586,10 +632,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
 #pragma unroll
                     for (int j = 0; j < kKB / 16; ++j) {
                         const uint32_t acc0 = (kb | j) ? 1u : 0u;
-                        mma_bf16_id(d_tmem, smem_desc(ah + 32 * j), smem_desc(bh + 32 * j), idesc, acc0);
-                        if (NS == 3) {
-                            mma_bf16_id(d_tmem, smem_desc(ah + 32 * j), smem_desc(bl + 32 * j), idesc, 1u);
-                            mma_bf16_id(d_tmem, smem_desc(al + 32 * j), smem_desc(bh + 32 * j), idesc, 1u);
+                        if constexpr (F) {
+                            mma_f8_id(d_tmem, smem_desc(ah + 32 * j), smem_desc(bh + 32 * j), idesc, acc0);
+                            if (NS == 3) {
+                                mma_f8_id(d_tmem, smem_desc(ah + 32 * j), smem_desc(bl + 32 * j), idesc, 1u);
+                                mma_f8_id(d_tmem, smem_desc(al + 32 * j), smem_desc(bh + 32 * j), idesc, 1u);
+                            }
+                        } else {
+                            mma_bf16_id(d_tmem, smem_desc(ah + 32 * j), smem_desc(bh + 32 * j), idesc, acc0);
+                            if (NS == 3) {
+                                mma_bf16_id(d_tmem, smem_desc(ah + 32 * j), smem_desc(bl + 32 * j), idesc, 1u);
+                                mma_bf16_id(d_tmem, smem_desc(al + 32 * j), smem_desc(bh + 32 * j), idesc, 1u);
+                            }
                         }
                     }
                     mma_commit(&S.empty[stage]);
@@ -697,11 +751,241 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 P.kq_i[base + i] = li[i];
             }
         }
+    } else if constexpr (MODE == 1) {
+        // ------------------------------------------ epilogue: count pass
+        // Each epilogue warp works alone on one 32 x 32 sub-block of every
+        // tile pair: TMEM lane quadrant quad = A rows 32 quad .. +31 (a row per
+        // lane) and B columns 32 part .. +31; no barrier across warps. Per
+        // pair: screen values u = fl(2 acc - |b|^2) against per-row limits
+        // (all out / all in at once from the row's extremes), then the row
+        // counts (and lists) from the lane's bits and the column counts from
+        // a 32 x 32 bit transpose; band pairs go to the FP64 recheck, or, in
+        // the first phase of the two-phase pass, defer the whole sub-block to
+        // the three-product pass. Each item's group and tile pairs are loaded
+        // while the previous item is processed, its row and column data before
+        // the accumulator wait.
+        const int ew = warp - 2;                              // 0 .. 15
+        const int quad = warp & 3;
+        const int part = ew >> 2;
+        const int sub = quad * 4 + part;
+        const int r = quad * 32 + lane;
+        float* wn = S.wn[ew];
+        struct Item {
+            int q[2], tb[2], nb[2], pre_col[2];               // per pair (B side)
+            float ncol2[2], bn2[2], bn[2], bl[2], bmin2[2];
+            float sb[2];                                      // FP8: the B tiles' scales
+            int ta, na, pre_row;                              // A side (shared by the pairs)
+            float na2, nra, rla, sa;
+            int nbt;
+            bool mine[2];
+        };
+        // the item's group and tile pairs (the first loads of its chain), then the rest
+        struct Head {
+            int2 grp, tp[2];
+        };
+        auto load_head = [&](int64_t g, Head& hd) {
+            hd.grp = group_at(g);
+            hd.tp[0] = A.pairs[hd.grp.x];
+            hd.tp[1] = hd.grp.y >= 0 ? A.pairs[hd.grp.y] : hd.tp[0];
+        };
+        auto load_item = [&](const Head& hd, Item& it) {
+            const int2 grp = hd.grp;
+            it.nbt = grp.y >= 0 ? 2 : 1;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (h >= it.nbt) break;
+                it.q[h] = h ? grp.y : grp.x;
+                it.mine[h] = P.sub_mask ? ((P.sub_mask[P.sub_q[it.q[h]]] >> sub) & 1u) != 0u : true;
+                const int2 tp = hd.tp[h];
+                it.tb[h] = tp.y & kPairTileMask;
+                if (h == 0) {
+                    it.ta = tp.x;
+                    it.na = A.tile_n[tp.x];
+                    const int64_t row = (int64_t)tp.x * kT + r;
+                    it.na2 = P.rn2[row];
+                    it.nra = P.rn[row];
+                    it.rla = P.rl ? P.rl[row] : 0.f;
+                    it.pre_row = A.cap > 0 ? A.count[row] : INT_MAX;
+                    it.sa = F ? P.tmax[tp.x].w : 1.f;
+                }
+                it.nb[h] = A.tile_n[it.tb[h]];
+                const int64_t col = (int64_t)it.tb[h] * kT + part * 32 + lane;
+                it.ncol2[h] = -P.rn2[col];
+                const float4 tm = P.tmax[it.tb[h]];
+                it.bn2[h] = tm.x;
+                it.bn[h] = tm.y;
+                it.bl[h] = tm.z;
+                it.sb[h] = tm.w;
+                it.bmin2[h] = P.tn2min[it.tb[h]];
+                it.pre_col[h] = A.cap > 0 && it.mine[h] && tp.x != it.tb[h] ? A.count[col] : INT_MAX;
+            }
+        };
+        int64_t screened = 0;
+        int git = 0;
+        Item cur;
+        Head head;
+        if ((int64_t)blockIdx.x < n_items) load_head(blockIdx.x, head);
+        for (int64_t g = blockIdx.x; g < n_items; g += gridDim.x, ++git) {
+            load_item(head, cur);
+            if (g + gridDim.x < n_items) load_head(g + gridDim.x, head);
+            const int tbuf = git & 1;
+            const bool bad = !mbar_wait(&S.acc_full[tbuf], (uint32_t)((git >> 1) & 1), abort) || *abort;
+            if (__any_sync(0xffffffffu, bad)) break;
+            tc_fence_after();
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (h >= cur.nbt) break;
+                const int q = cur.q[h];
+                const bool diag = cur.ta == cur.tb[h];
+                const int64_t sa = (int64_t)cur.ta * kT, sb = (int64_t)cur.tb[h] * kT;
+                const int64_t row = sa + r, col = sb + part * 32 + lane;
+                float u[32];
+                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tbuf * kAccCols + h * kT + part * 32), u);
+                if (h == cur.nbt - 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&S.acc_empty[tbuf]);
+                }
+                if (!P.sub_mask && ew == 0 && lane == 0)
+                    screened += diag ? (int64_t)cur.na * (cur.na + 1) / 2 : (int64_t)cur.na * cur.nb[h];
+                if (!cur.mine[h]) continue;
+                __syncwarp();                                 // the previous pair's wn is read
+                wn[lane] = cur.ncol2[h];
+                __syncwarp();
+                // per-row limits: in iff u >= k_in, out iff u < k_out (FP32, outward rounding)
+                float E;
+                if (P.rl) {
+                    const float cross = __fadd_ru(__fmul_ru(cur.rla, cur.bn[h]), __fmul_ru(cur.nra, cur.bl[h]));
+                    E = __fmaf_ru(P.K2f, __fmul_ru(cur.rla, cur.bl[h]),
+                                  __fmaf_ru(P.K1f, cross,
+                                            __fmaf_ru(P.K0f, __fmul_ru(cur.nra, cur.bn[h]),
+                                                      __fmaf_ru(P.A2f, __fadd_ru(cur.na2, cur.bn2[h]), P.A3f))));
+                } else {
+                    E = __fmaf_ru(P.A1f, __fmul_ru(cur.nra, cur.bn[h]),
+                                  __fmaf_ru(P.A2f, __fadd_ru(cur.na2, cur.bn2[h]), P.A3f));
+                }
+                float two = 2.f;
+                if constexpr (F) {
+                    // E4M3 subnormal floor of the scaled rows: K4 (s_b |a| + s_a |b|) + K5 s_a s_b
+                    const float ss = cur.sa * cur.sb[h];              // exact (powers of two)
+                    E = __fmaf_ru(P.K4f, __fadd_ru(__fmul_ru(cur.sb[h], cur.nra), __fmul_ru(cur.sa, cur.bn[h])),
+                                  __fmaf_ru(P.K5f, ss, E));
+                    two = 2.f * ss;
+                }
+                const float k_in = __fadd_ru(__fsub_ru(cur.na2, P.eps2_lo), E);
+                const float k_out = __fsub_rd(__fsub_rd(cur.na2, P.eps2_hi), E);
+                // the row's extremes from the raw accumulator: with x_j = two acc_j -
+                // |b_j|^2 (exact), max x <= RU(two max acc - min |b|^2) and min x >=
+                // RD(two min acc - max |b|^2); x < k_out certifies out and x >= k_in in
+                // (E covers the rounding of the computed screen value too)
+                float vmax = fmax3(u[0], u[1], u[2]);
+#pragma unroll
+                for (int i = 3; i + 1 < 32; i += 2) vmax = fmax3(vmax, u[i], u[i + 1]);
+                vmax = fmaxf(vmax, u[31]);
+                uint32_t in_bits = 0u, keep_bits = 0u;
+                const bool all_out = __fmaf_ru(two, vmax, -cur.bmin2[h]) < k_out;
+                bool all_in = false;
+                if (!all_out) {
+                    float vmin = fmin3(u[0], u[1], u[2]);
+#pragma unroll
+                    for (int i = 3; i + 1 < 32; i += 2) vmin = fmin3(vmin, u[i], u[i + 1]);
+                    vmin = fminf(vmin, u[31]);
+                    all_in = __fmaf_rd(two, vmin, -cur.bn2[h]) >= k_in;
+                }
+                if (all_in) {
+                    in_bits = keep_bits = 0xffffffffu;
+                } else if (!all_out) {
+                    // u = fl(two acc - |b|^2) (two = 2, or 2 s_a s_b for FP8), two
+                    // columns per packed FMA (each lane correctly rounded)
+                    const float4* wn4 = reinterpret_cast<const float4*>(wn);
+#pragma unroll
+                    for (int i4 = 0; i4 < 8; ++i4) {
+                        const float4 nn = wn4[i4];
+                        fma2_inplace(u[4 * i4 + 0], u[4 * i4 + 1], two, nn.x, nn.y);
+                        fma2_inplace(u[4 * i4 + 2], u[4 * i4 + 3], two, nn.z, nn.w);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        if (u[i] >= k_in) in_bits |= 1u << i;
+                        if (u[i] >= k_out) keep_bits |= 1u << i;
+                    }
+                }
+                const int left = cur.nb[h] - part * 32;
+                const uint32_t cand = r >= cur.na ? 0u
+                                                  : (left >= 32 ? 0xffffffffu : (left > 0 ? (1u << left) - 1u : 0u));
+                uint32_t inb = in_bits & cand;
+                const uint32_t band = keep_bits & ~in_bits & cand;
+                if (P.defer && __any_sync(0xffffffffu, band != 0u)) {
+                    // first phase: the sub-block goes to the three-product pass, whole
+                    if (lane == 0) {
+                        if (atomicOr(&P.redo_mask[q], 1u << sub) == 0u) atomicAdd(&A.stats[kStatRedo], 1ull);
+                        if (A.pair_hit) A.pair_hit[q] = 1;
+                    }
+                    continue;
+                }
+                if (A.pair_hit && __any_sync(0xffffffffu, (inb | band) != 0u) && lane == 0) A.pair_hit[q] = 1;
+                // band pairs: queued for the FP64 recheck; decided here if the queue is full
+                uint32_t bq = band;
+                while (bq) {
+                    const int i = __ffs(bq) - 1;
+                    bq &= bq - 1;
+                    const int j = part * 32 + i;
+                    const uint32_t fl = (diag ? 0u : kQBoth) | ((!diag || r < j) ? kQTie : 0u);
+                    bool decided;
+                    const bool in = push_band(P, (int)row, (int)(sb + j), fl, &decided);
+                    if (decided && in) inb |= 1u << i;
+                }
+                // row counts (and the first cap neighbours of each row)
+                const int k = __popc(inb);
+                if (k) {
+                    if (cur.pre_row < A.cap) {
+                        int pos = atomicAdd(&A.count[row], k);
+                        uint32_t bm = inb;
+                        while (bm && pos < A.cap) {
+                            const int i = __ffs(bm) - 1;
+                            bm &= bm - 1;
+                            A.nbr[row * A.cap + pos++] = (int32_t)(sb + part * 32 + i);
+                        }
+                    } else {
+                        atomicAdd(&A.count[row], k);
+                    }
+                }
+                // column counts: 32 x 32 bit transpose, lane j gets column part * 32 + j
+                if (!diag && __any_sync(0xffffffffu, inb != 0u)) {
+                    uint32_t x = inb;
+#pragma unroll
+                    for (int sft = 16; sft >= 1; sft >>= 1) {
+                        const uint32_t m = sft == 16 ? 0x0000FFFFu : sft == 8 ? 0x00FF00FFu : sft == 4 ? 0x0F0F0F0Fu
+                                                               : sft == 2 ? 0x33333333u : 0x55555555u;
+                        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, sft);
+                        x = (lane & sft) ? (((y >> sft) & m) | (x & ~m)) : ((x & m) | ((y & m) << sft));
+                    }
+                    const int kc = __popc(x);
+                    if (kc) {
+                        if (cur.pre_col[h] < A.cap) {
+                            int pos = atomicAdd(&A.count[col], kc);
+                            while (x && pos < A.cap) {
+                                const int i = __ffs(x) - 1;
+                                x &= x - 1;
+                                A.nbr[col * A.cap + pos++] = (int32_t)(sa + quad * 32 + i);
+                            }
+                        } else {
+                            atomicAdd(&A.count[col], kc);
+                        }
+                    }
+                }
+            }
+        }
+        if (screened) {
+            atomicAdd(&A.stats[kStatScreened], (unsigned long long)screened);
+            atomicAdd(&A.stats[kStatTcPairs], (unsigned long long)screened);
+        }
     } else {
         // ---------------------------------------------------- epilogue
-        // kEpiWarps warps: warp w reads TMEM lane quadrant (w & 3) = A rows
-        // 32(w & 3) .. +31 and the 32 kChunks columns of part (w - 2) / 4.
-        // Each pair's norms (and core flags) are loaded one pair ahead.
+        // Union pass. kEpiWarps warps: warp w reads TMEM lane quadrant (w & 3)
+        // = A rows 32(w & 3) .. +31 and the 32 kChunks columns of part
+        // (w - 2) / 4. Each pair's norms and core flags are loaded one pair
+        // ahead.
         const int et = tid - 64;                              // 0 .. kEpiThreads-1
         const int quad = warp & 3;
         const int half = (warp - 2) >> 2;                     // column part
@@ -893,25 +1177,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 }
             }
 
-            // (4b) two-phase count pass: a tile pair with any band pair is left,
-            //      whole, to the three-product pass (nothing of it counted here)
-            bool deferred = false;
-            if (MODE == 1 && P.defer) {
-                uint32_t anyb = 0u;
-#pragma unroll
-                for (int c2 = 0; c2 < kChunks; ++c2) anyb |= band[c2];
-                deferred = epi_sync_or(anyb != 0u);
-                if (deferred && et == 0) {
-                    const unsigned long long at = atomicAdd(P.redo_n, 1ull);
-                    P.redo[at] = A.pairs[q];
-                    if (A.pair_hit) A.pair_hit[q] = 1;
-                    atomicAdd(&A.stats[kStatRedo], 1ull);
-                }
-            }
-
             // (5) band pairs: queued for the FP64 recheck (decided here if the queue is full);
             //     a one-each union pair needs none once any pair is certainly in
-            bool any_in = deferred;
+            bool any_in = false;
             uint32_t all_in = 0u;
 #pragma unroll
             for (int c2 = 0; c2 < kChunks; ++c2) all_in |= inb[c2];
@@ -942,9 +1210,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             }
 
             // (6) counts and lists, or unions
-            if (MODE == 1 && deferred) {
-                // counted by the three-product pass
-            } else if (MODE == 1) {
+            if (MODE == 1) {
                 // one thread per row (et < 128) and per column (128 <= et < 256) adds the
                 // pair's neighbours to the count; lists are written only while a count may
                 // still be below cap (the count read one pair ahead is a lower bound)
@@ -1390,14 +1656,14 @@ constexpr int smem_bytes()
 static_assert(smem_bytes<3, 1>() <= 232448 && smem_bytes<1, 1>() <= 232448, "shared memory");
 static_assert(smem_bytes<3, 2>() <= 232448 && smem_bytes<1, 2>() <= 232448, "shared memory");
 
-template <int NS, int MODE, int W>
+template <int NS, int MODE, int W, int F = 0>
 cudaError_t launch(const CUtensorMap& mh, const CUtensorMap& ml, const TcParams& p, int grid, cudaStream_t s)
 {
     const int smem = smem_bytes<NS, W>();
     cudaError_t e =
-        cudaFuncSetAttribute(tc_kernel<NS, MODE, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(tc_kernel<NS, MODE, W, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    tc_kernel<NS, MODE, W><<<grid, kThreads, smem, s>>>(mh, ml, p);
+    tc_kernel<NS, MODE, W, F><<<grid, kThreads, smem, s>>>(mh, ml, p);
     return cudaGetLastError();
 }
 
@@ -1426,7 +1692,106 @@ __global__ void group_emit_kernel(const int2* __restrict__ pairs, int64_t n, con
     groups[pos[i]] = make_int2((int)i, two ? (int)(i + 1) : -1);
 }
 
+// The same grouping over the first *n_dev entries of a list of capacity n.
+__global__ void group_lead_dev_kernel(const int2* __restrict__ pairs, int64_t n,
+                                      const unsigned long long* __restrict__ n_dev, int32_t* __restrict__ lead)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if ((unsigned long long)i >= *n_dev) {
+        lead[i] = 0;
+        return;
+    }
+    const int a = pairs[i].x;
+    int64_t lo = 0, hi = i;
+    while (lo < hi) {
+        const int64_t m = (lo + hi) >> 1;
+        if (pairs[m].x < a) lo = m + 1; else hi = m;
+    }
+    lead[i] = ((i - lo) & 1) == 0;
+}
+
+__global__ void group_emit_dev_kernel(const int2* __restrict__ pairs, int64_t n,
+                                      const unsigned long long* __restrict__ n_dev, const int32_t* __restrict__ lead,
+                                      const int64_t* __restrict__ pos, int2* __restrict__ groups)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !lead[i]) return;
+    const bool two = (unsigned long long)(i + 1) < *n_dev && pairs[i + 1].x == pairs[i].x;
+    groups[pos[i]] = make_int2((int)i, two ? (int)(i + 1) : -1);
+}
+
+// flag[q] = 1 if the first phase deferred a sub-block of pair q
+__global__ void redo_flag_kernel(const uint32_t* __restrict__ mask, int64_t n, int32_t* __restrict__ flag)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = mask[i] != 0u;
+}
+
+// the deferred pairs in list order: redo[pos[q]] = pairs[q], redo_q[pos[q]] = q
+__global__ void redo_scatter_kernel(const int2* __restrict__ pairs, const int32_t* __restrict__ flag,
+                                    const int64_t* __restrict__ pos, int64_t n, int2* __restrict__ redo,
+                                    int32_t* __restrict__ redo_q)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !flag[i]) return;
+    redo[pos[i]] = pairs[i];
+    redo_q[pos[i]] = (int32_t)i;
+}
+
 }  // namespace
+
+int tc_redo_list(const int2* pairs, const uint32_t* mask, int64_t n, int2* redo, int32_t* redo_q, Buf* pos,
+                 cudaStream_t s)
+{
+    if (n == 0) return MAPPER_OK;
+    Buf flag;
+    cudaError_t e = flag.alloc(sizeof(int32_t) * n, s);
+    if (e == cudaSuccess) e = pos->alloc(sizeof(int64_t) * (n + 1), s);
+    if (e == cudaSuccess) {
+        redo_flag_kernel<<<(unsigned)div_up(n, 256), 256, 0, s>>>(mask, n, flag.as<int32_t>());
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = exclusive_scan_i32_to_i64(flag.as<int32_t>(), pos->as<int64_t>(), n, s);
+    if (e == cudaSuccess) {
+        redo_scatter_kernel<<<(unsigned)div_up(n, 256), 256, 0, s>>>(pairs, flag.as<int32_t>(), pos->as<int64_t>(), n,
+                                                                      redo, redo_q);
+        e = cudaGetLastError();
+    }
+    note_launch(2);
+    if (e != cudaSuccess) {
+        set_error(std::string("tc_redo_list: ") + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? MAPPER_ENOMEM : MAPPER_ECUDA;
+    }
+    return MAPPER_OK;
+}
+
+int tc_groups_dev(const int2* pairs, int64_t n, const unsigned long long* n_dev, Buf* groups, Buf* pos,
+                  cudaStream_t s)
+{
+    if (n == 0) return MAPPER_OK;
+    Buf lead;
+    cudaError_t e = lead.alloc(sizeof(int32_t) * n, s);
+    if (e == cudaSuccess) e = pos->alloc(sizeof(int64_t) * (n + 1), s);
+    if (e == cudaSuccess) e = groups->alloc(sizeof(int2) * (size_t)n, s);
+    const unsigned blocks = (unsigned)div_up(n, 256);
+    if (e == cudaSuccess) {
+        group_lead_dev_kernel<<<blocks, 256, 0, s>>>(pairs, n, n_dev, lead.as<int32_t>());
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = exclusive_scan_i32_to_i64(lead.as<int32_t>(), pos->as<int64_t>(), n, s);
+    if (e == cudaSuccess) {
+        group_emit_dev_kernel<<<blocks, 256, 0, s>>>(pairs, n, n_dev, lead.as<int32_t>(), pos->as<int64_t>(),
+                                                     groups->as<int2>());
+        e = cudaGetLastError();
+    }
+    note_launch(2);
+    if (e != cudaSuccess) {
+        set_error(std::string("tc_groups_dev: ") + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? MAPPER_ENOMEM : MAPPER_ECUDA;
+    }
+    return MAPPER_OK;
+}
 
 int assign_pivots_tc(const float* X, int64_t n, int d, int64_t ld, int dp, const float* Pv, int K,
                      int num_sms, int32_t* piv, float* pd2, cudaStream_t s)
@@ -1494,20 +1859,38 @@ int assign_pivots_tc(const float* X, int64_t n, int d, int64_t ld, int dp, const
 //                     NS = 3: dropping lo.lo and the residuals costs
 //                             <= (u'^2 + 2 rho + rho^2) S,  S = sum |a_k||b_k|
 //   accumulation      m MMA steps of 16 exact products each into the FP32
-//                     accumulator: <= m 2^-22 (1 + 2u')^2 S (two units per
-//                     step, allowing truncation); S <= |a||b|
+//                     accumulator: <= (m + 8) 2^-22 (1 + 2u')^2 S (two units
+//                     per step, allowing truncation, and a floor of 8 units;
+//                     accu_model); S <= |a||b|
 //   screen            u = fl(2 acc - |b|^2): <= v (2|acc| + |b|^2)
 //   norms             FP32 sums of d squares (lane partials and a shuffle
 //                     tree): <= (dp/32 + 16) v per norm, relative
 // A1 = 1.25 (2 (operand + accumulation) + 4v); A2 = 2 (dp/32 + 16) v + 4v;
 // A3 covers subnormal terms. |a| and |b| enter through upper bounds.
+// Accumulation term of the bound, relative to the sum of the products'
+// magnitudes: 2^-22 per MMA step (16 products of K each) plus a floor of 8
+// such units (the hardware's error does not shrink with the step count: at
+// one K block it is already ~2^-22, measured by mapper_selftest_mma_error),
+// times (1 + 2u')^2 for the magnitudes of the BF16 parts.
+double accu_model(int ns, int dp)
+{
+    const double up = std::ldexp(1.0, -8) + 2.0 * std::ldexp(1.0, -24);
+    const int steps = ns * ((dp + kKB - 1) / kKB) * (kKB / 16);
+    return (steps + 8) * std::ldexp(1.0, -22) * (1.0 + 2.0 * up) * (1.0 + 2.0 * up);
+}
+
+double accu_model_f8(int ns, int dp)
+{
+    const int steps = ns * ((dp + 127) / 128) * 4;
+    return (steps + 8) * std::ldexp(1.0, -22) * 1.3;
+}
+
 void tc_bound(int ns, int dp, double eps2, double* A1, double* A2, double* A3)
 {
     const double u = std::ldexp(1.0, -8), v = std::ldexp(1.0, -24);
     const double up = u + 2.0 * v, rho = u * u + 2.0 * v;
-    const int steps = ns * ((dp + kKB - 1) / kKB) * (kKB / 16);
     const double oper = ns == 1 ? (2.0 * up + up * up) : (up * up + 2.0 * rho + rho * rho);
-    const double accu = steps * std::ldexp(1.0, -22) * (1.0 + 2.0 * up) * (1.0 + 2.0 * up);
+    const double accu = accu_model(ns, dp);
     *A1 = 1.25 * (2.0 * (oper + accu) + 4.0 * v);
     *A2 = 2.0 * (dp / 32 + 16) * v + 4.0 * v;
     *A3 = std::ldexp(1.0, -40) * eps2 + 1e-30;
@@ -1526,9 +1909,7 @@ void tc_bound(int ns, int dp, double eps2, double* A1, double* A2, double* A3)
 void tc_bound_resid(int ns, int dp, double eps2, double* K0, double* K1, double* K2, double* A2, double* A3)
 {
     const double u = std::ldexp(1.0, -8), v = std::ldexp(1.0, -24);
-    const double up = u + 2.0 * v;
-    const int steps = ns * ((dp + kKB - 1) / kKB) * (kKB / 16);
-    const double accu = steps * std::ldexp(1.0, -22) * (1.0 + 2.0 * up) * (1.0 + 2.0 * up);
+    const double accu = accu_model(ns, dp);
     double o2, o1, o0;
     if (ns == 1) {
         o2 = 0.0;
@@ -1546,6 +1927,32 @@ void tc_bound_resid(int ns, int dp, double eps2, double* K0, double* K1, double*
     *A3 = std::ldexp(1.0, -40) * eps2 + 1e-30;
 }
 
+// FP8 E4M3 screen (three products of per-tile scaled rows: a / s_a = hi + lo
+// + t, hi = e4m3(a / s_a), r = a / s_a - hi, lo = e4m3(r)). E4M3 rounds to
+// 2^-4 relative above 2^-6 and to 2^-10 absolute below, so per row |t| <=
+// 2^-4 |r| + f with f = 2^-10 sqrt(dp). With R = |r| and N = |a / s| (scaled
+// norms) the algebra of tc_bound_resid gives
+//   |a.b / (s_a s_b) - P| <= 1.14 R_a R_b + 2^-4 1.001 (N_a R_b + R_a N_b)
+//                            + 1.2 f (N_a + N_b) + 6 f^2 + 2^-22 N_a N_b,
+// which times s_a s_b is, in the rows' own units (frl = s R, rn = s N),
+//   K2 frl_a frl_b + K1 (rn_a frl_b + frl_a rn_b) + K4 (s_b rn_a + s_a rn_b) + K5 s_a s_b + K0 rn_a rn_b
+// with the 2 x 1.25 factor, the accumulation (dp / 128 * 4 instructions of
+// K = 32 per product) and the screen and norm terms as for BF16.
+
+void tc_bound_f8(int dp, double eps2, double* K0, double* K1, double* K2, double* K4, double* K5, double* A2,
+                 double* A3)
+{
+    const double v = std::ldexp(1.0, -24);
+    const double f = std::ldexp(1.0, -10) * std::sqrt((double)dp);
+    *K2 = 2.5 * 1.14;
+    *K1 = 2.5 * std::ldexp(1.0, -4) * 1.001;
+    *K4 = 2.5 * 1.2 * f;
+    *K5 = 2.5 * 6.0 * f * f;
+    *K0 = 1.25 * (2.0 * (std::ldexp(1.0, -22) + accu_model_f8(3, dp)) + 4.0 * v);
+    *A2 = 2.0 * (dp / 32 + 16) * v + 4.0 * v;
+    *A3 = std::ldexp(1.0, -40) * eps2 + 1e-30;
+}
+
 int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaStream_t s)
 {
     if (n_pairs == 0) return MAPPER_OK;
@@ -1553,8 +1960,15 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
         set_error("tensor-core screen: more than 2^30 rows");
         return MAPPER_ENOMEM;
     }
+    if (t.f8 && (mode != 1 || t.ns != 3 || !t.rl || !t.tmax)) {
+        set_error("tensor-core pass: the FP8 screen is a three-product count pass");
+        return MAPPER_EINTERNAL;
+    }
+    // FP8 rows of dp bytes are moved as rows of dp / 2 BF16 columns (the same
+    // bytes, the same 128-byte swizzled K blocks, each holding 128 FP8 columns)
+    const int dcols = t.f8 ? a.dp / 2 : a.dp;
     CUtensorMap mh, ml;
-    if (!make_map(&mh, t.Ah, t.R, a.dp) || !make_map(&ml, t.ns == 3 ? t.Al : t.Ah, t.R, a.dp)) {
+    if (!make_map(&mh, t.Ah, t.R, dcols) || !make_map(&ml, t.ns == 3 ? t.Al : t.Ah, t.R, dcols)) {
         set_error("cuTensorMapEncodeTiled failed (or is unavailable)");
         return MAPPER_ECUDA;
     }
@@ -1563,13 +1977,21 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
     p.rn2 = t.rn2;
     p.rn = t.rn;
     p.n_pairs = n_pairs;
-    p.nkb = (a.dp + kKB - 1) / kKB;
+    p.nkb = (dcols + kKB - 1) / kKB;
     tc_bound(t.ns, a.dp, a.eps2, &p.A1, &p.A2, &p.A3);
     p.A1f = std::nextafter((float)p.A1, INFINITY);
     p.A2f = std::nextafter((float)p.A2, INFINITY);
     p.A3f = std::nextafter((float)p.A3, INFINITY);
     p.rl = t.rl;
-    if (t.rl) {
+    if (t.f8) {
+        double K0, K1, K2, K4, K5, A2, A3;
+        tc_bound_f8(a.dp, a.eps2, &K0, &K1, &K2, &K4, &K5, &A2, &A3);
+        p.K0f = std::nextafter((float)K0, INFINITY);
+        p.K1f = std::nextafter((float)K1, INFINITY);
+        p.K2f = std::nextafter((float)K2, INFINITY);
+        p.K4f = std::nextafter((float)K4, INFINITY);
+        p.K5f = std::nextafter((float)K5, INFINITY);
+    } else if (t.rl) {
         double K0, K1, K2, A2, A3;
         tc_bound_resid(t.ns, a.dp, a.eps2, &K0, &K1, &K2, &A2, &A3);
         p.K0f = std::nextafter((float)K0, INFINITY);
@@ -1584,12 +2006,15 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
     p.queue_n = t.queue_n;
     p.queue_cap = t.queue_cap;
     p.err = t.err;
-    const bool defer = mode == 1 && t.defer && t.ns == 1;
+    const bool defer = mode == 1 && t.defer && (t.ns == 1 || t.f8);
     p.defer = defer ? 1 : 0;
-    p.redo = t.redo;
-    p.redo_n = t.redo_n;
-    if (t.defer && !defer) {
-        set_error("tensor-core pass: deferral needs the one-product count pass");
+    p.redo_mask = t.redo_mask;
+    p.sub_mask = t.sub_mask;
+    p.sub_q = t.sub_q;
+    p.tmax = t.tmax;
+    p.tn2min = t.tn2min;
+    if ((t.defer && !defer) || (mode == 1 && (!t.tmax || !t.tn2min)) || (t.sub_mask && !t.sub_q) || (defer && !t.redo_mask)) {
+        set_error("tensor-core pass: inconsistent arguments");
         return MAPPER_EINTERNAL;
     }
     cudaError_t e = cudaMemsetAsync(t.queue_n, 0, sizeof(unsigned long long), s);
@@ -1601,7 +2026,9 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
     const int grid = (int)std::min<int64_t>(grouped ? t.n_groups : n_pairs, t.num_sms);
     if (grid < 1) return MAPPER_OK;
     if (t.ev_begin) cudaEventRecord(t.ev_begin, s);
-    if (grouped)
+    if (t.f8)
+        e = grouped ? launch<3, 1, 2, 1>(mh, ml, p, grid, s) : launch<3, 1, 1, 1>(mh, ml, p, grid, s);
+    else if (grouped)
         e = t.ns == 3 ? launch<3, 1, 2>(mh, ml, p, grid, s) : launch<1, 1, 2>(mh, ml, p, grid, s);
     else if (t.ns == 3)
         e = mode == 1 ? launch<3, 1, 1>(mh, ml, p, grid, s) : launch<3, 2, 1>(mh, ml, p, grid, s);
@@ -1745,23 +2172,51 @@ float bf16_value(uint16_t b)
 
 }  // namespace
 
-int tc_mma_probe(int ns, int dp, uint64_t seed, int num_sms, double* observed, double* modelled, cudaStream_t s)
+// value of an E4M3 byte (sign, 4 exponent bits of bias 7, 3 mantissa bits;
+// exponent 0 subnormal; S.1111.111 is NaN and never generated here)
+double e4m3_value(uint8_t b)
 {
-    if ((ns != 1 && ns != 3) || dp < 32 || dp % 32 || dp > 4096) {
-        set_error("accumulation probe: products must be 1 or 3 and the pitch a multiple of 32 in [32, 4096]");
+    const int e = (b >> 3) & 15, m = b & 7;
+    const double v = e ? std::ldexp(1.0 + m / 8.0, e - 7) : std::ldexp(m / 8.0, -6);
+    return (b & 0x80) ? -v : v;
+}
+
+uint8_t e4m3_random(uint64_t h, int e_lo, int e_hi)        // a normal value 2^e (1 + m/8), e in [e_lo, e_hi]
+{
+    const int e = e_lo + (int)((h >> 8) % (uint64_t)(e_hi - e_lo + 1));
+    const int m = (int)(h & 7);
+    return (uint8_t)(((h >> 63) ? 0x80 : 0) | ((e + 7) << 3) | m);
+}
+
+int tc_mma_probe(int ns, int fmt, int dp, uint64_t seed, int num_sms, double* observed, double* modelled,
+                 cudaStream_t s)
+{
+    if ((ns != 1 && ns != 3) || (fmt != 0 && fmt != 1) || dp < 32 || dp % 32 || dp > 4096) {
+        set_error("accumulation probe: products must be 1 or 3, the format 0 (BF16) or 1 (FP8) and the pitch a "
+                  "multiple of 32 in [32, 4096]");
         return MAPPER_EINVAL;
     }
     constexpr int kPairs = 4, kTiles = 2 * kPairs, R = kTiles * kT;
-    // random rows: values sign * 2^e * m with e in [-4, 4], split into BF16 hi + lo
+    // random rows: BF16 values sign * 2^e * m with e in [-4, 4] split into hi + lo;
+    // FP8 E4M3 hi parts with exponents in [-4, 5] and lo parts in [-8, 1]
+    const int esz = fmt ? 1 : 2;
     std::vector<uint16_t> hi((size_t)R * dp), lo((size_t)R * dp);
+    std::vector<uint8_t> hi8(fmt ? (size_t)R * dp : 0), lo8(fmt ? (size_t)R * dp : 0);
     for (size_t i = 0; i < hi.size(); ++i) {
         const uint64_t h = splitmix(seed * 0x100000001B3ull + i);
+        if (fmt) {
+            hi8[i] = e4m3_random(h, -4, 5);
+            lo8[i] = e4m3_random(splitmix(h), -8, 1);
+            continue;
+        }
         const float m = 1.0f + (float)((h >> 11) & 0xFFFFFF) / 16777216.0f;
         const int e = (int)((h >> 40) % 9) - 4;
         const float v = std::ldexp(m, e) * ((h >> 63) ? -1.0f : 1.0f);
         hi[i] = bf16_bits_rn(v);
         lo[i] = bf16_bits_rn(v - bf16_value(hi[i]));
     }
+    auto hv = [&](size_t i) { return fmt ? e4m3_value(hi8[i]) : (double)bf16_value(hi[i]); };
+    auto lv = [&](size_t i) { return fmt ? e4m3_value(lo8[i]) : (double)bf16_value(lo[i]); };
     std::vector<int2> pairs(kPairs);
     for (int k = 0; k < kPairs; ++k) pairs[k] = make_int2(2 * k, 2 * k + 1);
     std::vector<int32_t> tile_n(kTiles, kT);
@@ -1774,19 +2229,22 @@ int tc_mma_probe(int ns, int dp, uint64_t seed, int num_sms, double* observed, d
             return e_ == cudaErrorMemoryAllocation ? MAPPER_ENOMEM : MAPPER_ECUDA; \
         }                                                                         \
     } while (0)
-    PK(dAh.alloc(hi.size() * 2, s));
-    PK(dAl.alloc(lo.size() * 2, s));
+    PK(dAh.alloc(hi.size() * esz, s));
+    PK(dAl.alloc(lo.size() * esz, s));
     PK(dpairs.alloc(sizeof(int2) * kPairs, s));
     PK(dtn.alloc(sizeof(int32_t) * kTiles, s));
     PK(ddump.alloc(sizeof(float) * (size_t)kPairs * kT * kT, s));
     PK(derr.alloc(sizeof(int), s));
-    PK(cudaMemcpyAsync(dAh.p, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice, s));
-    PK(cudaMemcpyAsync(dAl.p, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice, s));
+    PK(cudaMemcpyAsync(dAh.p, fmt ? (const void*)hi8.data() : (const void*)hi.data(), hi.size() * esz,
+                       cudaMemcpyHostToDevice, s));
+    PK(cudaMemcpyAsync(dAl.p, fmt ? (const void*)lo8.data() : (const void*)lo.data(), lo.size() * esz,
+                       cudaMemcpyHostToDevice, s));
     PK(cudaMemcpyAsync(dpairs.p, pairs.data(), sizeof(int2) * kPairs, cudaMemcpyHostToDevice, s));
     PK(cudaMemcpyAsync(dtn.p, tile_n.data(), sizeof(int32_t) * kTiles, cudaMemcpyHostToDevice, s));
     PK(cudaMemsetAsync(derr.p, 0, sizeof(int), s));
+    const int dcols = fmt ? dp / 2 : dp;                 // FP8 rows moved as BF16 columns of two bytes
     CUtensorMap mh, ml;
-    if (!make_map(&mh, dAh.p, R, dp) || !make_map(&ml, ns == 3 ? dAl.p : dAh.p, R, dp)) {
+    if (!make_map(&mh, dAh.p, R, dcols) || !make_map(&ml, ns == 3 ? dAl.p : dAh.p, R, dcols)) {
         set_error("cuTensorMapEncodeTiled failed (or is unavailable)");
         return MAPPER_ECUDA;
     }
@@ -1795,11 +2253,12 @@ int tc_mma_probe(int ns, int dp, uint64_t seed, int num_sms, double* observed, d
     p.A.tile_n = dtn.as<int32_t>();
     p.A.dp = dp;
     p.n_pairs = kPairs;
-    p.nkb = (dp + kKB - 1) / kKB;
+    p.nkb = (dcols + kKB - 1) / kKB;
     p.err = derr.as<int>();
     p.dump = ddump.as<float>();
     const int grid = std::min(kPairs, num_sms);
-    PK((ns == 3 ? launch<3, 4, 1>(mh, ml, p, grid, s) : launch<1, 4, 1>(mh, ml, p, grid, s)));
+    if (fmt) PK((ns == 3 ? launch<3, 4, 1, 1>(mh, ml, p, grid, s) : launch<1, 4, 1, 1>(mh, ml, p, grid, s)));
+    else PK((ns == 3 ? launch<3, 4, 1>(mh, ml, p, grid, s) : launch<1, 4, 1>(mh, ml, p, grid, s)));
     note_launch();
     std::vector<float> acc((size_t)kPairs * kT * kT);
     int h_err = 0;
@@ -1820,12 +2279,12 @@ int tc_mma_probe(int ns, int dp, uint64_t seed, int num_sms, double* observed, d
                 const size_t ra = ((size_t)(2 * k) * kT + i) * dp, rb = ((size_t)(2 * k + 1) * kT + j) * dp;
                 double ex = 0.0, mag = 0.0;
                 for (int c = 0; c < dp; ++c) {
-                    const double ah = bf16_value(hi[ra + c]), bh = bf16_value(hi[rb + c]);
+                    const double ah = hv(ra + c), bh = hv(rb + c);
                     double t = ah * bh;
                     ex += t;
                     mag += std::fabs(t);
                     if (ns == 3) {
-                        const double al = bf16_value(lo[ra + c]), bl = bf16_value(lo[rb + c]);
+                        const double al = lv(ra + c), bl = lv(rb + c);
                         t = ah * bl;
                         ex += t;
                         mag += std::fabs(t);
@@ -1837,10 +2296,8 @@ int tc_mma_probe(int ns, int dp, uint64_t seed, int num_sms, double* observed, d
                 const double err = std::fabs((double)acc[((size_t)k * kT + i) * kT + j] - ex);
                 if (mag > 0.0) worst = std::max(worst, err / mag);
             }
-    const double up = std::ldexp(1.0, -8) + 2.0 * std::ldexp(1.0, -24);
-    const int steps = ns * ((dp + kKB - 1) / kKB) * (kKB / 16);
     *observed = worst;
-    *modelled = steps * std::ldexp(1.0, -22) * (1.0 + 2.0 * up) * (1.0 + 2.0 * up);
+    *modelled = fmt ? accu_model_f8(ns, dp) : accu_model(ns, dp);
     return MAPPER_OK;
 }
 

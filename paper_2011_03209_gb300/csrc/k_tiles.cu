@@ -17,6 +17,7 @@
 //      hi + lo parts with |a|^2 and |a| for the tensor-core screen.
 // Only speed depends on this ordering; every decision stays exact.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <cfloat>
 #include <climits>
@@ -490,8 +491,11 @@ __global__ void __launch_bounds__(1024) seg_cent_kernel(const float* __restrict_
 // hi = bf16(a), lo = bf16(a - hi) (a - hi is exact in FP32); |a|^2 summed in
 // FP32 (lane partials of at most dp/32 squares, then a shuffle tree) and |a|
 // rounded up; if rl is set, also |a - hi| (the residual the hi part leaves,
-// summed the same way) rounded up. A warp per row, a lane per 8 consecutive
-// columns (16-byte stores); rows come from G when it is set, else from X.
+// summed the same way) rounded up; if tmax is set, the largest |a|^2, |a| and
+// |a - hi| of the tile's rows (x, y, z) and the smallest |a|^2 of its valid
+// rows (tn2min). A warp per row, a lane per 8
+// consecutive columns (16-byte stores); rows come from G when it is set, else
+// from X.
 __global__ void __launch_bounds__(256) operand_kernel(const float* __restrict__ G, const float* __restrict__ X,
                                                       int64_t ld, bool xvec, const int32_t* __restrict__ row_pt,
                                                       int d, int dp, const int32_t* __restrict__ tile_n,
@@ -500,9 +504,14 @@ __global__ void __launch_bounds__(256) operand_kernel(const float* __restrict__ 
                                                       __nv_bfloat16* __restrict__ Ah,
                                                       __nv_bfloat16* __restrict__ Al,
                                                       float* __restrict__ rn2, float* __restrict__ rn,
-                                                      float* __restrict__ rl, float norm_infl)
+                                                      float* __restrict__ rl, float4* __restrict__ tmax,
+                                                      float* __restrict__ tn2min, float norm_infl)
 {
     const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ unsigned smax[4];                          // non-negative floats compare as their bits
+    if (threadIdx.x < 3) smax[threadIdx.x] = 0u;
+    if (threadIdx.x == 3) smax[3] = 0x7f800000u;          // +inf: the smallest |a|^2 of the valid rows
+    __syncthreads();
     const int nt = tile_n[t];
     const float* c = seg_cent + (int64_t)tile_seg[t] * dp;
     const bool vec = G ? true : xvec;
@@ -555,10 +564,121 @@ __global__ void __launch_bounds__(256) operand_kernel(const float* __restrict__ 
             sr += __shfl_xor_sync(0xffffffffu, sr, o);
         }
         if (lane == 0) {
+            const float n1 = __fmul_ru(__fsqrt_ru(s), norm_infl), l1 = __fmul_ru(__fsqrt_ru(sr), norm_infl);
             rn2[row] = s;
-            rn[row] = __fmul_ru(__fsqrt_ru(s), norm_infl);
-            if (rl) rl[row] = __fmul_ru(__fsqrt_ru(sr), norm_infl);
+            rn[row] = n1;
+            if (rl) rl[row] = l1;
+            if (tmax) {
+                atomicMax(&smax[0], __float_as_uint(s));
+                atomicMax(&smax[1], __float_as_uint(n1));
+                atomicMax(&smax[2], __float_as_uint(l1));
+                if (valid) atomicMin(&smax[3], __float_as_uint(s));
+            }
         }
+    }
+    if (tmax) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tmax[t] = make_float4(__uint_as_float(smax[0]), __uint_as_float(smax[1]), __uint_as_float(smax[2]), 0.f);
+            tn2min[t] = __uint_as_float(smax[3]);
+        }
+    }
+}
+
+// FP8 E4M3 operands with one power-of-two scale per tile: the rows of tile t
+// centred on its segment centre (a = fl(x - c), FP32 as for the BF16
+// operands), M = the largest |a_k| of the tile, s = 2^e with 2^e > M / 448
+// (frexp), hi = e4m3(a / s), lo = e4m3(a / s - hi) (the difference exact in
+// FP32); per row |a - s hi| rounded up (frl); per tile (max |a|^2, max |a|,
+// max frl, s) in ftmax. |a|^2 and |a| are those of the BF16 operands (same
+// centred rows), read from tmax. A CTA per tile: the first sweep finds M,
+// the second writes the bytes.
+__global__ void __launch_bounds__(256) fp8_operand_kernel(const float* __restrict__ G, const float* __restrict__ X,
+                                                          int64_t ld, bool xvec, const int32_t* __restrict__ row_pt,
+                                                          int d, int dp, const int32_t* __restrict__ tile_n,
+                                                          const int32_t* __restrict__ tile_seg,
+                                                          const float* __restrict__ seg_cent,
+                                                          const float4* __restrict__ tmax,
+                                                          uint8_t* __restrict__ Fh, uint8_t* __restrict__ Fl,
+                                                          float* __restrict__ frl, float4* __restrict__ ftmax,
+                                                          float norm_infl)
+{
+    const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nt = tile_n[t];
+    const float* c = seg_cent + (int64_t)tile_seg[t] * dp;
+    const bool vec = G ? true : xvec;
+    __shared__ unsigned smax, lmax;
+    if (threadIdx.x == 0) { smax = 0u; lmax = 0u; }
+    __syncthreads();
+    // a = fl(x - c) of 8 columns k .. k + 7 of row r (zero past d and for padding rows)
+    auto centred = [&](int r, int k, float (&a)[8]) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = 0.f;
+        if (r >= nt) return;
+        const int64_t row = (int64_t)t * kT + r;
+        const float* xr = G ? G + row * dp : X + (int64_t)row_pt[row] * ld;
+        if (vec && k + 7 < d) {
+            const float4 x0 = *reinterpret_cast<const float4*>(xr + k);
+            const float4 x1 = *reinterpret_cast<const float4*>(xr + k + 4);
+            a[0] = x0.x; a[1] = x0.y; a[2] = x0.z; a[3] = x0.w;
+            a[4] = x1.x; a[5] = x1.y; a[6] = x1.z; a[7] = x1.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) if (k + u < d) a[u] = xr[k + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = k + u < d ? a[u] - c[k + u] : 0.f;
+    };
+    float m = 0.f;
+    for (int r = warp; r < kT; r += 8)
+        for (int k = lane * 8; k < dp; k += 256) {
+            float a[8];
+            centred(r, k, a);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) m = fmaxf(m, fabsf(a[u]));
+        }
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) atomicMax(&smax, __float_as_uint(m));
+    __syncthreads();
+    const float M = __uint_as_float(smax);
+    int e = 0;
+    if (M > 0.f) {
+        frexpf(M / 448.f, &e);                            // M / 448 < 2^e, up to the division's rounding
+        if (M * ldexpf(1.f, -e) >= 448.f) ++e;           // (exact test)
+    }
+    const float sc = ldexpf(1.f, e), inv = ldexpf(1.f, -e);
+    for (int r = warp; r < kT; r += 8) {
+        const int64_t row = (int64_t)t * kT + r;
+        float sr = 0.f;
+        for (int k = lane * 8; k < dp; k += 256) {
+            float a[8];
+            centred(r, k, a);
+            uint32_t wh[2] = {0u, 0u}, wl[2] = {0u, 0u};
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float x = a[u] * inv;                   // exact (power of two)
+                const __nv_fp8_storage_t h = __nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+                const float hf = __half2float(__half(__nv_cvt_fp8_to_halfraw(h, __NV_E4M3)));
+                const float rr = x - hf;                      // exact
+                const __nv_fp8_storage_t l = __nv_cvt_float_to_fp8(rr, __NV_SATFINITE, __NV_E4M3);
+                wh[u >> 2] |= (uint32_t)h << (8 * (u & 3));
+                wl[u >> 2] |= (uint32_t)l << (8 * (u & 3));
+                sr = fmaf(rr, rr, sr);
+            }
+            *reinterpret_cast<uint2*>(Fh + row * dp + k) = make_uint2(wh[0], wh[1]);
+            *reinterpret_cast<uint2*>(Fl + row * dp + k) = make_uint2(wl[0], wl[1]);
+        }
+        for (int o = 16; o; o >>= 1) sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        if (lane == 0) {
+            const float l1 = __fmul_ru(__fmul_ru(__fsqrt_ru(sr), norm_infl), sc);
+            frl[row] = l1;
+            atomicMax(&lmax, __float_as_uint(l1));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const float4 tm = tmax[t];
+        ftmax[t] = make_float4(tm.x, tm.y, __uint_as_float(lmax), sc);
     }
 }
 
@@ -952,6 +1072,8 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
         TK(L->rn2.alloc(sizeof(float) * R, s));
         TK(L->rn.alloc(sizeof(float) * R, s));
         TK(L->rl.alloc(sizeof(float) * R, s));
+        TK(L->tmax.alloc(sizeof(float4) * T, s));
+        TK(L->tn2min.alloc(sizeof(float) * T, s));
         const float norm_infl = 1.0f + (float)(dp / 32 + 16) * 5.9604645e-8f;
         const bool xvec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
         operand_kernel<<<(unsigned)T, 256, 0, s>>>(L->G.as<float>(), X, ld, xvec, L->row_pt.as<int32_t>(), d, dp,
@@ -959,9 +1081,35 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
                                                    L->tile_seg.as<int32_t>(), L->seg_cent.as<float>(),
                                                    L->Ah.as<__nv_bfloat16>(), L->Al.as<__nv_bfloat16>(),
                                                    L->rn2.as<float>(), L->rn.as<float>(), L->rl.as<float>(),
-                                                   norm_infl);
+                                                   L->tmax.as<float4>(), L->tn2min.as<float>(), norm_infl);
         note_launch();
         TK(cudaGetLastError());
+    }
+    return MAPPER_OK;
+}
+
+int fp8_operands(TileLayout* L, const float* X, int64_t ld, int d, int dp, cudaStream_t s)
+{
+    if (L->T == 0 || L->Fh.p) return MAPPER_OK;
+    const int64_t R = L->R, T = L->T;
+    cudaError_t e = L->Fh.alloc((size_t)R * dp, s);
+    if (e == cudaSuccess) e = L->Fl.alloc((size_t)R * dp, s);
+    if (e == cudaSuccess) e = L->frl.alloc(sizeof(float) * R, s);
+    if (e == cudaSuccess) e = L->ftmax.alloc(sizeof(float4) * T, s);
+    if (e == cudaSuccess) {
+        const float norm_infl = 1.0f + (float)(dp / 32 + 16) * 5.9604645e-8f;
+        const bool xvec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
+        fp8_operand_kernel<<<(unsigned)T, 256, 0, s>>>(L->G.as<float>(), X, ld, xvec, L->row_pt.as<int32_t>(), d, dp,
+                                                       L->tile_n.as<int32_t>(), L->tile_seg.as<int32_t>(),
+                                                       L->seg_cent.as<float>(), L->tmax.as<float4>(),
+                                                       L->Fh.as<uint8_t>(), L->Fl.as<uint8_t>(), L->frl.as<float>(),
+                                                       L->ftmax.as<float4>(), norm_infl);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        set_error(std::string("fp8_operands: ") + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? MAPPER_ENOMEM : MAPPER_ECUDA;
     }
     return MAPPER_OK;
 }
@@ -975,7 +1123,7 @@ cudaError_t centred_operands(const float* X, int64_t ld, int d, int dp, const in
     const bool xvec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
     operand_kernel<<<(unsigned)T, 256, 0, s>>>(nullptr, X, ld, xvec, row_pt, d, dp, tile_n, tile_cent, cents,
                                                static_cast<__nv_bfloat16*>(Ah), static_cast<__nv_bfloat16*>(Al), rn2,
-                                               rn, nullptr, norm_infl);
+                                               rn, nullptr, nullptr, nullptr, norm_infl);
     note_launch();
     return cudaGetLastError();
 }
@@ -986,7 +1134,7 @@ cudaError_t centred_operands(const float* X, int64_t ld, int d, int dp, const in
 // centre, so the screen's error bound, and its band, are wider; pairs far
 // apart are still decided at once.
 int cross_operands(const TileLayout& L, const float* X, int64_t ld, int d, int dp, int64_t E, Buf* Ah, Buf* Al,
-                   Buf* rn2, Buf* rn, Buf* rl, cudaStream_t s)
+                   Buf* rn2, Buf* rn, Buf* rl, Buf* tmax, Buf* tn2min, cudaStream_t s)
 {
 #define XK(expr)                                                                      \
     do {                                                                              \
@@ -1005,6 +1153,8 @@ int cross_operands(const TileLayout& L, const float* X, int64_t ld, int d, int d
     XK(rn2->alloc(sizeof(float) * R, s));
     XK(rn->alloc(sizeof(float) * R, s));
     XK(rl->alloc(sizeof(float) * R, s));
+    XK(tmax->alloc(sizeof(float4) * T, s));
+    XK(tn2min->alloc(sizeof(float) * T, s));
     elem_tiles_kernel<<<grid_for(E + 1), 256, 0, s>>>(L.tile_elem.as<int32_t>(), T, E, etile_off.as<int64_t>());
     seg_cent_kernel<<<(unsigned)E, 1024, 0, s>>>(L.tile_cent.as<float>(), L.tile_n.as<int32_t>(),
                                                etile_off.as<int64_t>(), dp, ecent.as<float>());
@@ -1013,7 +1163,8 @@ int cross_operands(const TileLayout& L, const float* X, int64_t ld, int d, int d
     operand_kernel<<<(unsigned)T, 256, 0, s>>>(L.G.as<float>(), X, ld, xvec, L.row_pt.as<int32_t>(), d, dp,
                                                L.tile_n.as<int32_t>(), L.tile_elem.as<int32_t>(), ecent.as<float>(),
                                                Ah->as<__nv_bfloat16>(), Al->as<__nv_bfloat16>(), rn2->as<float>(),
-                                               rn->as<float>(), rl->as<float>(), norm_infl);
+                                               rn->as<float>(), rl->as<float>(), tmax->as<float4>(),
+                                               tn2min->as<float>(), norm_infl);
     note_launch(3);
     XK(cudaGetLastError());
     return MAPPER_OK;

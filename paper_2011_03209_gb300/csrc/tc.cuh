@@ -14,8 +14,12 @@ struct TcArgs {
     const float* rn2;
     const float* rn;
     const float* rl;                 // |a - hi| per row (rounded up): the tighter bound; or nullptr
+    const float4* tmax;              // per tile: largest |a|^2, |a|, |a - hi| (count pass)
+    const float* tn2min;             // per tile: smallest |a|^2 of the valid rows (count pass)
     int64_t R;
-    int ns;                          // BF16 products per pair: 3 (hi.hi + hi.lo + lo.hi) or 1
+    int ns;                          // products per pair: 3 (hi.hi + hi.lo + lo.hi) or 1
+    bool f8;                         // count pass on FP8 E4M3 operands (Ah, Al: R x dp bytes, per-tile
+                                     //   scale in tmax[t].w; rl: |a - s hi|), ns = 3
     int num_sms;                     // persistent grid size
     uint2* queue;                    // band pairs for the FP64 recheck
     unsigned long long* queue_n;     // entries pushed (may exceed queue_cap)
@@ -28,14 +32,29 @@ struct TcArgs {
     const unsigned long long* n_dev; // ungrouped, if set: the pair count on the device
                                      //   (n_pairs then bounds it)
     // pass 1 with ns = 1 only: the first phase of the two-phase count pass.
-    // Tile pairs with no pair in the one-product band are counted; the others
-    // are appended to redo[] (capacity n_pairs; *redo_n, zeroed by the caller,
-    // receives their number), flagged in pair_hit and counted by a
-    // three-product pass over redo[] afterwards.
+    // Each 32 x 32 sub-block (TMEM lane quadrant, column part) of a tile pair
+    // with no pair in the one-product band is counted; the others set their
+    // bit (quadrant * 4 + part) in redo_mask[q] (one word per pair of the
+    // list, zeroed by the caller), and their pair is flagged in pair_hit.
+    // tc_redo_list then lists the pairs with deferred sub-blocks, and the
+    // second phase (ns = 3) runs over that list with sub_mask = redo_mask and
+    // sub_q = its first-phase indices, counting only those sub-blocks.
     bool defer;
-    int2* redo;
-    unsigned long long* redo_n;
+    uint32_t* redo_mask;
+    const uint32_t* sub_mask;
+    const int32_t* sub_q;
 };
+
+// The pairs q of pairs[0 .. n) with mask[q] != 0, in list order: redo[k] =
+// pairs[q_k], redo_q[k] = q_k (capacity n each); *pos receives [n + 1] int64
+// with their number at pos[n]. Returns a mapper_status.
+int tc_redo_list(const int2* pairs, const uint32_t* mask, int64_t n, int2* redo, int32_t* redo_q, Buf* pos,
+                 cudaStream_t s);
+
+// tc_groups over the first *n_dev entries of a list of capacity n (number of
+// groups at (*pos)[n]). Returns a mapper_status.
+int tc_groups_dev(const int2* pairs, int64_t n, const unsigned long long* n_dev, Buf* groups, Buf* pos,
+                  cudaStream_t s);
 
 // Groups the pair list (sorted by tile A, then tile B) into work items of
 // one or two pairs sharing tile A: groups[k] = (pair index, pair index or -1).
@@ -78,7 +97,10 @@ int tc_knn_screen(const void* Ah, const void* Al, const float* rn2, const float*
 // over the accumulators, relative to the sum of the magnitudes of the
 // products, and *modelled = the accumulation term of the screen's error bound
 // relative to the same sum. Returns a mapper_status.
-int tc_mma_probe(int ns, int dp, uint64_t seed, int num_sms, double* observed, double* modelled, cudaStream_t s);
+// fmt: 0 = BF16 rows (kind::f16), 1 = FP8 E4M3 rows (kind::f8f6f4, the
+// FP8 screen's model).
+int tc_mma_probe(int ns, int fmt, int dp, uint64_t seed, int num_sms, double* observed, double* modelled,
+                 cudaStream_t s);
 
 // Runs the passes' bounded mbarrier wait on a barrier that is never
 // completed: MAPPER_ETIMEOUT once it gives up (after 4 s), as designed.

@@ -17,7 +17,7 @@ mg = pytest.importorskip("paper_2011_03209_gb300")
 
 pytestmark = pytest.mark.gpu
 
-PRECISIONS = [mg.FP32, mg.BF16, mg.BF16X1]
+PRECISIONS = [mg.FP32, mg.BF16, mg.BF16X1, mg.FP8]
 
 
 @pytest.fixture(scope="module")

@@ -81,7 +81,7 @@ TINY = [
 ]
 
 
-PRECISIONS = [mg.FP32, mg.BF16, mg.BF16X1]
+PRECISIONS = [mg.FP32, mg.BF16, mg.BF16X1, mg.FP8]
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
@@ -357,7 +357,7 @@ def _check_graph_properties(res, n_points):
     assert sorted(pairs) == [tuple(e) for e in E.tolist()]
 
 
-@pytest.mark.parametrize("prec", [mg.BF16, mg.BF16X1])
+@pytest.mark.parametrize("prec", [mg.BF16, mg.BF16X1, mg.FP8])
 def test_pass1_shapes_agree(prec):
     """Both pass-1 product shapes (one tile pair per item, N = 128; two pairs
     sharing tile A, N = 256) and the autotuner's pick give the same exact
@@ -389,15 +389,17 @@ def test_pass1_shapes_agree(prec):
             c.set_pass1_tile_n(64)
 
 
+@pytest.mark.parametrize("first", [mg.BF16, mg.FP8])
 @pytest.mark.parametrize("tile_n", [128, 256])
-def test_two_phase_count_pass_equals_three_products(tile_n):
-    """MAPPER_BF16's count pass screens every tile pair with one product and
-    only the tile pairs holding a pair inside that product's band again with
-    three; the graph equals the one of three products everywhere and the
-    oracle's."""
+def test_two_phase_count_pass_equals_three_products(tile_n, first):
+    """The two-phase count pass (a first screen of one BF16 product, or of
+    three FP8 products, then three BF16 products for the 32 x 32 blocks
+    holding a pair inside the first screen's band) gives the graph of one
+    phase (three products everywhere; FP8: its band re-decided in FP64) and
+    the oracle's."""
     w = synth.mixture_100k()
     Xd = torch.from_numpy(w.X).to("cuda:0")
-    prm = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, mg.BF16)
+    prm = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, first)
     outs = []
     for mode in (1, 2):
         with mg.Context(0) as c:
@@ -426,7 +428,7 @@ def test_two_phase_count_pass_equals_three_products(tile_n):
             c.set_pass1_screen(3)
 
 
-@pytest.mark.parametrize("prec", [mg.BF16, mg.BF16X1])
+@pytest.mark.parametrize("prec", [mg.BF16, mg.BF16X1, mg.FP8])
 @pytest.mark.parametrize("cap", [1, 16])
 def test_band_queue_overflow_exact(prec, cap):
     """A band queue far smaller than the band: the pairs past its capacity are
@@ -452,7 +454,7 @@ def test_band_queue_overflow_exact(prec, cap):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("prec", [mg.BF16, mg.FP32])
+@pytest.mark.parametrize("prec", [mg.BF16, mg.FP32, mg.FP8])
 def test_clusters_1m_d256_sampled(ctx, prec):
     """Full-size 1M x 256 workload as the benchmark runs it: lens rows, the
     whole cover, and the DBSCAN of sampled elements against the oracle; the
