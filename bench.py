@@ -35,10 +35,11 @@ METRIC = "mapper graph ms and eps-pair TFLOP/s at 1M\u00d7256, BF16-certified vs
 GPU_FP32_LANES = 128                 # FP32 lanes per SM (Blackwell)
 
 
-def _traffic(kpairs, tile_pairs):
-    """DRAM bytes per launch of the tensor-core count kernel, scaled from the
-    ncu capture recorded in profiles/traffic.json by tile pairs, or None when
-    the kernel source changed since that capture."""
+def _traffic(st):
+    """DRAM bytes of one count pass on the tensor cores (both phases of the
+    two-phase pass), scaled from the ncu capture recorded in
+    profiles/traffic.json by the tile pairs of each phase, or None when the
+    kernel source changed since that capture or the pass ran in one phase."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_2011_03209_gb300", "csrc", "k_tc.cu")
@@ -47,7 +48,10 @@ def _traffic(kpairs, tile_pairs):
     rec = json.load(open(p)).get("tc_kernel_count")
     if not rec or rec.get("source_sha1") != hashlib.sha1(open(src, "rb").read()).hexdigest():
         return None
-    return rec["bytes_per_tile_pair"] * tile_pairs
+    if not st.get("tile_pairs_screen1") or "bytes_per_tile_pair_first" not in rec:
+        return None
+    return (rec["bytes_per_tile_pair_first"] * st["tile_pairs_screen1"] +
+            rec["bytes_per_tile_pair_second"] * st["tile_pairs_redo"])
 
 
 def _bind_local_cpus(device: int):
@@ -284,7 +288,7 @@ def _roofline(prec, w, st, stats, n_sm):
                 "32 x 32 blocks whose one-product band is not empty" if tp1 else
                 "tc_kernel<%d,1> (tcgen05 BF16 count pass): %d BF16 products per pair" % (ns, ns))
     return kms, {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                 "frac": achieved / peak, "traffic": _traffic(kpairs, st["tile_pairs_tc"]),
+                 "frac": achieved / peak, "traffic": _traffic(st) if prec == mg.BF16 else None,
                  "kernel": desc + "; achieved counts 2d algorithmic flops per point pair screened",
                  "executed_tflops": executed,
                  "peak_source": f"{src} bf16_tflops (burst: the kernel's launches last a few ms)"}
@@ -420,6 +424,7 @@ def run_ours(args):
         line["exact_on_sample"] = exact
     if extras:
         line["small_configs"] = measure_small_configs(ctx, 10)
+        line["single_linkage"] = measure_single_linkage(ctx, 3)
     ctx.close()
     if extras:
         del Xd
@@ -587,6 +592,44 @@ def run_sweep(args):
         **{k: r[k] for k in ("ms_per_graph", "single_calls_ms", "sweep_speedup", "pass1_tile_n", "nodes")},
         "clocks": clocks,
     }))
+
+
+def measure_single_linkage(ctx, steps: int) -> dict:
+    """Single linkage (the minimum spanning forests of the cover elements'
+    eps-graphs) of the 100,000 x 64 mixture with its PC1 cover: device time
+    of mapper_single_linkage on the given cover, and its forests of the
+    smallest, median and largest elements against the oracle's Kruskal."""
+    import torch
+    import oracle
+    import paper_2011_03209_gb300 as mg
+
+    w = synth.mixture_100k()
+    Xd = torch.from_numpy(w.X).to(f"cuda:{ctx.device}")
+    lens, _ = mg.mapper_lens(ctx, Xd, w.lens_kind, w.lens_arg)
+    cover = mg.mapper_cover(ctx, lens, w.n_intervals, w.overlap)
+    for _ in range(2):
+        f = mg.mapper_single_linkage(ctx, Xd, cover, w.eps)
+        del f
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f = mg.mapper_single_linkage(ctx, Xd, cover, w.eps)
+        k = f.size()
+        if _ < steps - 1:
+            del f
+    ms = (time.perf_counter() - t0) * 1e3 / steps
+    got = f.numpy()
+    offs, pts = cover.numpy()
+    sizes = np.diff(offs)
+    ne = np.nonzero(sizes)[0]
+    exact = True
+    for e in (int(ne[np.argmin(sizes[ne])]), int(ne[np.argsort(sizes[ne])[len(ne) // 2]]), int(np.argmax(sizes))):
+        u, v, d2 = oracle.msf(w.X, pts[offs[e]:offs[e + 1]], w.eps)
+        mine = got["elem"] == e
+        exact &= bool(np.array_equal(got["u"][mine], u) and np.array_equal(got["v"][mine], v) and
+                      np.array_equal(got["d2"][mine], d2))
+    return {"workload": w.name, "eps": w.eps, "ms": ms, "forest_edges": int(k), "exact_on_sample": exact,
+            "timing": "host wall clock around mapper_single_linkage (the call syncs), mean of %d" % steps}
 
 
 def measure_small_configs(ctx, steps: int) -> dict:

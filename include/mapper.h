@@ -117,6 +117,7 @@ typedef struct mapper_ctx mapper_ctx;
 typedef struct mapper_cover_t mapper_cover_t;
 typedef struct mapper_clusters_t mapper_clusters_t;
 typedef struct mapper_graph_t mapper_graph_t;
+typedef struct mapper_forest_t mapper_forest_t;
 
 /* Parameters of one mapper graph (§3, "Algorithmic details in practice":
  * filter f, number of cover elements n, overlap p, metric, clusterer). */
@@ -299,6 +300,33 @@ int mapper_cluster(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, in
 int mapper_clusters_copy(const mapper_clusters_t* clusters, int64_t* label, uint8_t* core,
                          int on_device);
 
+/* Single linkage (§5: Lum et al. cluster each cover element by single
+ * linkage, where the tool uses DBSCAN). For every element of `cover`, the
+ * minimum spanning forest of its eps-graph: the points of the element, an
+ * edge {p, q} where d2(p, q) <= eps*eps (the DBSCAN distance of this
+ * header), edges ordered by the key (d2, smaller point index, larger point
+ * index), so the forest is unique when distances tie. Equivalently, the
+ * single-linkage dendrogram of the element up to height eps. The result is
+ * read with mapper_forest_sizes / mapper_forest_copy: edge k joins points
+ * u[k] < v[k] of element elem[k] at squared distance d2[k] (the FP64 value of
+ * the defining expression); edges come in no particular order (sort by
+ * (elem, d2, u, v) for a canonical one). X must be the cloud the cover was
+ * built on. MAPPER_EINVAL for eps not finite and > 0, MAPPER_ENONFINITE if X
+ * holds NaN/Inf. */
+int mapper_single_linkage(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, int64_t ld,
+                          const mapper_cover_t* cover, double eps, mapper_forest_t** out);
+int mapper_forest_sizes(const mapper_forest_t* forest, int64_t* n_edges);
+/* elem, u, v: n_edges int32 each; d2: n_edges doubles. Any may be NULL. */
+int mapper_forest_copy(const mapper_forest_t* forest, int32_t* elem, int32_t* u, int32_t* v, double* d2,
+                       int on_device);
+/* Single-linkage clusters at height h, 0 < h <= the forest's eps: in every
+ * element, the components of its forest edges with d2 <= h*h; every point is
+ * a member of its component's cluster (no noise), whose canonical id is the
+ * component's smallest point index. The handle is read like mapper_cluster's
+ * (every point flagged core) and mapper_nerve builds its mapper graph, which
+ * equals the graph of DBSCAN(h, minPts = 1). */
+int mapper_forest_cut(mapper_ctx* ctx, const mapper_forest_t* forest, double h, mapper_clusters_t** out);
+
 /* Nerve (§3: 1D nerve; an edge where two clusters intersect). */
 int mapper_nerve(mapper_ctx* ctx, const mapper_clusters_t* clusters, mapper_graph_t** out);
 
@@ -372,10 +400,10 @@ int mapper_graph_lens(const mapper_graph_t* g, double* lens, double* pca, int64_
 const mapper_cover_t* mapper_graph_cover(const mapper_graph_t* g);
 const mapper_clusters_t* mapper_graph_clusters(const mapper_graph_t* g);
 
-/* Counters of a clusters or graph handle. */
+/* Counters of a clusters, graph or forest handle. */
 int mapper_stats_get(const void* handle, mapper_stats* out);
 
-/* Release any handle (cover, clusters, graph). NULL is a no-op. */
+/* Release any handle (cover, clusters, graph, forest). NULL is a no-op. */
 void mapper_free(void* handle);
 
 /* ------------------------------------------------------------- serving */

@@ -23,6 +23,7 @@ __all__ = [
     "mapper_cluster", "mapper_nerve", "mapper_graph", "params", "LENS_L2", "LENS_COORD",
     "LENS_PCA", "LENS_ECC", "LENS_LINF", "LENS_DENSITY", "LENS_ECC_INF", "COVER_UNIFORM", "COVER_BALANCED", "FP32", "BF16", "BF16X1", "FP8", "mapper_dbscan_noalloc", "Server", "graph_footprint",
     "mapper_graph_sweep", "mapper_cover_subset", "mapper_nerve_from_nodes", "mapper_knn_distance",
+    "mapper_single_linkage", "Forest",
 ]
 
 
@@ -154,6 +155,34 @@ class Clusters(_Handle):
         return lab[:n_members], core[:n_members].astype(bool)
 
 
+class Forest(_Handle):
+    """Single-linkage forest: the minimum spanning forests of the elements'
+    eps-graphs (mapper_single_linkage)."""
+
+    def size(self) -> int:
+        k = ctypes.c_int64()
+        _capi.check(self._lib.mapper_forest_sizes(self.h, ctypes.byref(k)), "mapper_forest_sizes")
+        return k.value
+
+    def numpy(self) -> dict:
+        """Edges sorted by (elem, d2, u, v): elem, u < v (points) and d2."""
+        k = self.size()
+        elem = np.empty(max(k, 1), dtype=np.int32)
+        u = np.empty(max(k, 1), dtype=np.int32)
+        v = np.empty(max(k, 1), dtype=np.int32)
+        d2 = np.empty(max(k, 1), dtype=np.float64)
+        _capi.check(self._lib.mapper_forest_copy(self.h, _vp(elem.ctypes.data), _vp(u.ctypes.data),
+                                                 _vp(v.ctypes.data), _vp(d2.ctypes.data), 0), "mapper_forest_copy")
+        elem, u, v, d2 = elem[:k], u[:k], v[:k], d2[:k]
+        order = np.lexsort((v, u, d2, elem))
+        return dict(elem=elem[order], u=u[order], v=v[order], d2=d2[order])
+
+    def cut(self, ctx: "Context", h: float) -> Clusters:
+        out = ctypes.c_void_p()
+        _capi.check(self._lib.mapper_forest_cut(ctx.h, self.h, float(h), ctypes.byref(out)), "mapper_forest_cut")
+        return Clusters(self._lib, out)
+
+
 class Graph(_Handle):
     def sizes(self):
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
@@ -250,6 +279,16 @@ def mapper_cover(ctx: Context, lens, n_intervals, overlap, balanced: bool = Fals
     fn = ctx._lib.mapper_cover_balanced if balanced else ctx._lib.mapper_cover
     _capi.check(fn(ctx.h, _vp(lens.data_ptr()), n, m, ni, ov, ctypes.byref(h)), "mapper_cover")
     return Cover(ctx._lib, h)
+
+
+def mapper_single_linkage(ctx: Context, X, cover: Cover, eps: float) -> Forest:
+    """Minimum spanning forests of the cover elements' eps-graphs (the
+    single-linkage dendrograms up to eps)."""
+    p, n, d, ld, _keep = _x_args(X)
+    h = ctypes.c_void_p()
+    _capi.check(ctx._lib.mapper_single_linkage(ctx.h, p, n, d, ld, cover.h, float(eps), ctypes.byref(h)),
+                "mapper_single_linkage")
+    return Forest(ctx._lib, h)
 
 
 def mapper_cluster(ctx: Context, X, cover: Cover, eps: float, min_pts: int, precision: int = FP32) -> Clusters:

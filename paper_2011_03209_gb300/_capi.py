@@ -30,7 +30,8 @@ FP32, BF16, BF16X1, FP8 = 0, 1, 2, 3
 EXPORTS = (
     "mapper_create", "mapper_destroy", "mapper_set_stream", "mapper_set_timing", "mapper_set_pass1_tile_n",
     "mapper_set_cross_screen", "mapper_selftest_wait", "mapper_set_knn_screen", "mapper_set_band_queue_cap",
-    "mapper_set_pass1_screen", "mapper_selftest_mma_error",
+    "mapper_set_pass1_screen", "mapper_selftest_mma_error", "mapper_single_linkage", "mapper_forest_sizes",
+    "mapper_forest_copy", "mapper_forest_cut",
     "mapper_cover_subset", "mapper_nerve_from_nodes", "mapper_cover_balanced", "mapper_knn_distance",
     "mapper_lens", "mapper_lens_ex", "mapper_cover", "mapper_cover_sizes", "mapper_cover_copy",
     "mapper_cluster", "mapper_clusters_copy", "mapper_nerve", "mapper_graph",
@@ -150,6 +151,10 @@ def load(path: str | None = None):
             "mapper_set_knn_screen": (ctypes.c_int, [P, ctypes.c_int]),
             "mapper_set_band_queue_cap": (ctypes.c_int, [P, i64]),
             "mapper_set_pass1_screen": (ctypes.c_int, [P, ctypes.c_int]),
+            "mapper_single_linkage": (ctypes.c_int, [P, P, i64, i32, i64, P, f64, ctypes.POINTER(P)]),
+            "mapper_forest_sizes": (ctypes.c_int, [P, ctypes.POINTER(i64)]),
+            "mapper_forest_copy": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int]),
+            "mapper_forest_cut": (ctypes.c_int, [P, P, f64, ctypes.POINTER(P)]),
             "mapper_selftest_mma_error": (ctypes.c_int, [P, i32, i32, i32, ctypes.c_uint64, ctypes.POINTER(f64),
                                                          ctypes.POINTER(f64)]),
             "mapper_cover_subset": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.POINTER(P)]),

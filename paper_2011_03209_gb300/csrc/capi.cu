@@ -27,7 +27,7 @@ using namespace mgb;
 namespace {
 
 constexpr uint32_t kMagic = 0x4d415052u;   // "MAPR"
-enum : uint32_t { kKindCover = 1, kKindClusters = 2, kKindGraph = 3 };
+enum : uint32_t { kKindCover = 1, kKindClusters = 2, kKindGraph = 3, kKindForest = 4 };
 
 struct HandleHdr {
     uint32_t magic;
@@ -88,6 +88,15 @@ struct mapper_clusters_t {
     HandleHdr h{kMagic, kKindClusters};
     std::shared_ptr<ClusterData> c;
     bool view = false;
+};
+
+struct mapper_forest_t {
+    HandleHdr h{kMagic, kKindForest};
+    StreamRef stream;
+    std::shared_ptr<CoverData> cover;
+    ForestOut f;
+    double eps = 0.0;
+    mapper_stats stats{};
 };
 
 struct mapper_graph_t {
@@ -1170,6 +1179,130 @@ int mapper_clusters_copy(const mapper_clusters_t* clusters, int64_t* label, uint
     return copy_out(core, h->c->core.p, M, on_device, s);
 }
 
+int mapper_single_linkage(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t d, int64_t ld,
+                          const mapper_cover_t* cover, double eps, mapper_forest_t** out)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if ((rc = check_x(X_dev, n, d, ld))) return rc;
+    auto* cv = handle_as<mapper_cover_t>(cover, kKindCover);
+    if (!cv || !out) return fail(MAPPER_EINVAL, "bad cover handle or out");
+    *out = nullptr;
+    if (!(eps > 0.0) || !std::isfinite(eps)) return fail(MAPPER_EINVAL, "eps must be finite and > 0");
+    const auto& cov = cv->c;
+    if (cov->n != n) return fail(MAPPER_EINVAL, "cover was built for another point count");
+    cudaStream_t s = ctx->stream->s;
+    const int dp = (d + 31) / 32 * 32;
+    Buf flag;
+    CK(flag.alloc(sizeof(int), s), "alloc");
+    CK(cudaMemsetAsync(flag.p, 0, sizeof(int), s), "memset");
+    // tile layout (FP32 rows gathered) and the element tile pairs that may hold a pair within eps
+    TileLayout L;
+    if ((rc = build_tiles(X_dev, n, d, ld, dp, cov->slot_point.as<int32_t>(), cov->slot_elem.as<int32_t>(), cov->M,
+                          cov->E, 4.0 * eps, false, ctx->num_sms, &L, flag.as<int>(), s)))
+        return rc;
+    PairLists PL;
+    if ((rc = classify_pairs(L, X_dev, ld, d, dp, cov->E, eps, false, &PL, s))) return rc;
+    const int64_t np = PL.n[kListAllIn] + PL.n[kListTC] + PL.n[kListSimt];
+    if (np > INT32_MAX) return fail(MAPPER_ENOMEM, "too many tile pairs for one launch");
+    Buf pairs;
+    CK(pairs.alloc(sizeof(int2) * std::max<int64_t>(np, 1), s), "alloc");
+    int64_t at = 0;
+    for (int li : {(int)kListAllIn, (int)kListTC, (int)kListSimt}) {
+        if (PL.n[li] == 0) continue;
+        CK(cudaMemcpyAsync(pairs.as<int2>() + at, PL.list[li].p, sizeof(int2) * PL.n[li], cudaMemcpyDeviceToDevice, s),
+           "copy");
+        at += PL.n[li];
+    }
+    PassArgs a{};
+    a.G = L.G.as<float>();
+    a.X = X_dev;
+    a.ld = ld;
+    a.xvec = ld % 4 == 0 && ((uintptr_t)X_dev & 15) == 0;
+    a.dp = dp;
+    a.d = d;
+    a.tile_n = L.tile_n.as<int32_t>();
+    a.eps2 = eps * eps;
+    fp32_thresholds(a.eps2, d, &a.lo_thr, &a.hi_thr);
+    a.row_pt = L.row_pt.as<int32_t>();
+    a.pairs = pairs.as<int2>();
+    auto h = std::make_unique<mapper_forest_t>();
+    h->stream = ctx->stream;
+    h->cover = cov;
+    h->eps = eps;
+    if ((rc = msf_forest(a, L.row_slot.as<int32_t>(), cov->slot_point.as<int32_t>(), cov->slot_elem.as<int32_t>(),
+                         cov->M, L.R, L.T, np, &h->f, s)))
+        return rc;
+    int h_nf = 0;
+    CK(cudaMemcpyAsync(&h_nf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    if (h_nf) return fail(MAPPER_ENONFINITE, "X holds NaN or Inf");
+    h->stats.n_points = n;
+    h->stats.n_elements = cov->E;
+    h->stats.n_members = cov->M;
+    h->stats.tile_pairs = PL.n_candidates;
+    h->stats.tile_pairs_out = PL.n_out;
+    h->stats.tile_pairs_in = PL.n[kListAllIn];
+    h->stats.n_edges = h->f.n;
+    h->stats.n_rows = L.R;
+    *out = h.release();
+    return MAPPER_OK;
+}
+
+int mapper_forest_sizes(const mapper_forest_t* forest, int64_t* n_edges)
+{
+    auto* h = handle_as<mapper_forest_t>(forest, kKindForest);
+    if (!h || !n_edges) return fail(MAPPER_EINVAL, "bad forest handle or output");
+    *n_edges = h->f.n;
+    return MAPPER_OK;
+}
+
+int mapper_forest_copy(const mapper_forest_t* forest, int32_t* elem, int32_t* u, int32_t* v, double* d2,
+                       int on_device)
+{
+    auto* h = handle_as<mapper_forest_t>(forest, kKindForest);
+    if (!h) return fail(MAPPER_EINVAL, "bad forest handle");
+    cudaStream_t s = h->stream->s;
+    const size_t n = (size_t)h->f.n;
+    int rc;
+    if (elem && (rc = copy_out(elem, h->f.elem.p, sizeof(int32_t) * n, on_device, s))) return rc;
+    if (u && (rc = copy_out(u, h->f.u.p, sizeof(int32_t) * n, on_device, s))) return rc;
+    if (v && (rc = copy_out(v, h->f.v.p, sizeof(int32_t) * n, on_device, s))) return rc;
+    if (d2 && (rc = copy_out(d2, h->f.d2.p, sizeof(double) * n, on_device, s))) return rc;
+    CK(cudaStreamSynchronize(s), "sync");
+    return MAPPER_OK;
+}
+
+int mapper_forest_cut(mapper_ctx* ctx, const mapper_forest_t* forest, double h, mapper_clusters_t** out)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    auto* f = handle_as<mapper_forest_t>(forest, kKindForest);
+    if (!f || !out) return fail(MAPPER_EINVAL, "bad forest handle or out");
+    *out = nullptr;
+    if (!(h > 0.0) || !(h <= f->eps)) return fail(MAPPER_EINVAL, "the height must be in (0, eps]");
+    cudaStream_t s = ctx->stream->s;
+    const int64_t M = f->cover->M;
+    auto c = std::make_shared<ClusterData>();
+    c->stream = ctx->stream;
+    c->cover = f->cover;
+    CK(c->core.alloc(std::max<int64_t>(M, 1), s), "alloc");
+    CK(c->lab.alloc(sizeof(int32_t) * std::max<int64_t>(M, 1), s), "alloc");
+    CK(c->is_root.alloc(sizeof(int32_t) * std::max<int64_t>(M, 1), s), "alloc");
+    CK(c->is_member.alloc(sizeof(int32_t) * std::max<int64_t>(M, 1), s), "alloc");
+    CK(c->slot_label.alloc(sizeof(int64_t) * std::max<int64_t>(M, 1), s), "alloc");
+    if ((rc = msf_cut(f->f, f->cover->slot_point.as<int32_t>(), M, h, c->lab.as<int32_t>(), c->is_root.as<int32_t>(),
+                      c->is_member.as<int32_t>(), c->slot_label.as<int64_t>(), c->core.as<uint8_t>(), s)))
+        return rc;
+    CK(cudaStreamSynchronize(s), "sync");
+    c->stats = f->stats;
+    c->stats.n_core = M;
+    auto hnd = new mapper_clusters_t;
+    hnd->c = c;
+    *out = hnd;
+    return MAPPER_OK;
+}
+
 int mapper_nerve(mapper_ctx* ctx, const mapper_clusters_t* clusters, mapper_graph_t** out)
 {
     int rc = check_ctx(ctx);
@@ -1562,7 +1695,8 @@ int mapper_stats_get(const void* handle, mapper_stats* out)
     if (!out) return fail(MAPPER_EINVAL, "out is null");
     if (auto* g = handle_as<mapper_graph_t>(handle, kKindGraph)) { *out = g->stats; return MAPPER_OK; }
     if (auto* c = handle_as<mapper_clusters_t>(handle, kKindClusters)) { *out = c->c->stats; return MAPPER_OK; }
-    return fail(MAPPER_EINVAL, "not a graph or clusters handle");
+    if (auto* f = handle_as<mapper_forest_t>(handle, kKindForest)) { *out = f->stats; return MAPPER_OK; }
+    return fail(MAPPER_EINVAL, "not a graph, clusters or forest handle");
 }
 
 void mapper_free(void* handle)
@@ -1580,6 +1714,8 @@ void mapper_free(void* handle)
         delete h;
     } else if (hh->kind == kKindGraph) {
         delete static_cast<mapper_graph_t*>(handle);
+    } else if (hh->kind == kKindForest) {
+        delete static_cast<mapper_forest_t*>(handle);
     }
 }
 

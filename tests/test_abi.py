@@ -71,6 +71,9 @@ def test_knobs_and_new_calls_reject_a_null_context_without_a_gpu(lib):
     assert lib.mapper_set_knn_screen(None, 0) == _capi.MAPPER_EINVAL
     assert lib.mapper_set_band_queue_cap(None, 0) == _capi.MAPPER_EINVAL
     assert lib.mapper_set_pass1_screen(None, 0) == _capi.MAPPER_EINVAL
+    assert lib.mapper_single_linkage(None, None, 0, 0, 0, None, 1.0, None) == _capi.MAPPER_EINVAL
+    assert lib.mapper_forest_sizes(None, None) == _capi.MAPPER_EINVAL
+    assert lib.mapper_forest_cut(None, None, 1.0, None) == _capi.MAPPER_EINVAL
     assert lib.mapper_selftest_mma_error(None, 64, 1, 0, 1, None, None) == _capi.MAPPER_EINVAL
     assert lib.mapper_selftest_wait(None) == _capi.MAPPER_EINVAL
     assert lib.mapper_lens_ex(None, None, 0, 0, 0, 1, None, None, None, 1, None, None) == _capi.MAPPER_EINVAL
