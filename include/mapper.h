@@ -195,7 +195,11 @@ typedef struct mapper_stats {
 
 /* Create a context on CUDA device `device`, ordering all work on
  * `cuda_stream` (a cudaStream_t; NULL = a stream the context creates).
- * hbm_budget_bytes caps the context's scratch (0 = no cap). */
+ * hbm_budget_bytes caps the context's scratch (0 = no cap). When the
+ * environment variable MAPPER_TUNE_CACHE names a file, the context starts
+ * from the pass-1 shapes the autotuner chose before on the same kind of
+ * device (device name and SM count) and mapper_destroy merges its own
+ * choices into the file. */
 int mapper_create(mapper_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream);
 void mapper_destroy(mapper_ctx* ctx);
 /* Use another stream for subsequent calls. */

@@ -11,6 +11,8 @@ import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libmapper_gb300.so")
+# the checked build (device-side index checks); MAPPER_CHECKED=1 loads it instead
+CHECKED_LIB_PATH = os.path.join(_HERE, "_build", "libmapper_gb300_checked.so")
 
 MAPPER_OK = 0
 MAPPER_EINVAL = -1
@@ -131,7 +133,7 @@ def load(path: str | None = None):
     with _lock:
         if _lib is not None:
             return _lib
-        p = path or LIB_PATH
+        p = path or (CHECKED_LIB_PATH if os.environ.get("MAPPER_CHECKED") == "1" else LIB_PATH)
         if not os.path.exists(p):
             raise RuntimeError(
                 f"CUDA library {p} is missing: build it first "

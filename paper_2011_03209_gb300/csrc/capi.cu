@@ -2,6 +2,8 @@
 // argument checks, handle ownership, stream-ordered scratch, size read-backs,
 // and the order of the kernel launches of each step.
 #include <cfloat>
+#include <cstdio>
+#include <cstdlib>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -494,6 +496,8 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     a.root = root.as<int32_t>();
     a.border = border.as<unsigned long long>();
     a.stats = stats.as<unsigned long long>();
+    a.n_rows = R;
+    a.n_tiles = L.T;
     // Mixed tile pairs across two segments of one element have no common
     // centre; when they are many (a cover element holding scattered points,
     // whose tiles have wide spheres), they run on the tensor cores too, with
@@ -673,17 +677,20 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         CK(counts_to_lens(L.row_slot.as<int32_t>(), a.row_pt, a.count, R, counts_out->f, counts_out->m,
                           counts_out->j, s), "counts");
         int h_nf = 0, h_err = 0;
+        unsigned long long h_oob = 0;
         CK(cudaMemcpyAsync(&h_nf, nf, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+        CK(cudaMemcpyAsync(&h_oob, a.stats + kStatOob, sizeof(h_oob), cudaMemcpyDeviceToHost, s), "copy");
         if (use_tc) CK(cudaMemcpyAsync(&h_err, tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
         CK(cudaStreamSynchronize(s), "sync");
         if (h_nf) return fail(MAPPER_ENONFINITE, "X holds NaN or Inf");
         if (h_err) return fail(MAPPER_ETIMEOUT, "a tensor-core pass gave up waiting on a barrier");
+        if (h_oob) return fail(MAPPER_EINTERNAL, "a device-side index check failed");
         *out = c;
         return MAPPER_OK;
     }
     CK(core_flags(a.count, R, min_pts, core.as<uint8_t>(), a.parent, a.border, a.stats, s), "core");
     pt.mark();                                                    // 3
-    CK(list_unions(a.count, a.nbr, cap, a.core, a.parent, a.row_pt, R, s), "list unions");
+    CK(list_unions(a.count, a.nbr, cap, a.core, a.parent, a.row_pt, R, s, a.stats + kStatOob), "list unions");
     CK(allin_pass(2, a_in, PL.n[kListAllIn], s), "pass 2 all-in");
     // Unions in rounds of growing tile distance b - a (tiles of one pivot
     // region are adjacent), after the unions along the neighbour lists: a
@@ -744,7 +751,8 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     pt.mark();                                                    // 4
     CK(flatten(a.parent, a.core, R, root.as<int32_t>(), s), "flatten");
     if (cap) {
-        CK(border_from_lists(a.count, a.nbr, cap, a.core, a.root, a.row_pt, R, a.border, s), "border");
+        CK(border_from_lists(a.count, a.nbr, cap, a.core, a.root, a.row_pt, R, a.border, s, a.stats + kStatOob),
+           "border");
     } else if (min_pts > 1) {
         CK(allin_pass(3, a_in, PL.n[kListAllIn], s), "pass 3 all-in");
         CK(simt_pass(3, a_tc, PL.n[kListTC], s), "pass 3 tc list");
@@ -769,6 +777,9 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     CK(cudaStreamSynchronize(s), "sync");
     if (h_nf) return fail(MAPPER_ENONFINITE, "X holds NaN or Inf");
     if (h_err) return fail(MAPPER_ETIMEOUT, "a tensor-core pass gave up waiting on a barrier");
+    if (h_stats[kStatOob])
+        return fail(MAPPER_EINTERNAL, "a device-side index check failed (" + std::to_string(h_stats[kStatOob]) +
+                                          " indices out of range)");
     st.band_pairs = (int64_t)h_stats[kStatBand];
     st.near_ties = (int64_t)h_stats[kStatTies];
     st.pairs_screened = (int64_t)h_stats[kStatScreened];
@@ -955,6 +966,65 @@ const char* mapper_strerror(int status)
     }
 }
 
+namespace {
+
+// Persistent autotuner choices: a text file named by MAPPER_TUNE_CACHE, a
+// header line with the device name and SM count, then one "key tile_n" line
+// per tuned (row pitch, format, products) key. Read when a context is
+// created on the same kind of device; the context's choices are merged in
+// and the file replaced (write to a temporary, then rename) when it is
+// destroyed. Without the variable nothing is read or written.
+std::string tune_cache_header(int device)
+{
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return std::string();
+    return std::string("mapper-tune-v1 ") + prop.name + " sms=" + std::to_string(prop.multiProcessorCount);
+}
+
+void tune_cache_load(mapper_ctx* ctx)
+{
+    const char* path = std::getenv("MAPPER_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    const std::string want = tune_cache_header(ctx->device);
+    bool ok = std::fgets(line, sizeof(line), f) && !want.empty() && want == std::string(line).substr(0, want.size());
+    unsigned long long key = 0;
+    int tile_n = 0;
+    while (ok && std::fscanf(f, "%llu %d", &key, &tile_n) == 2)
+        if (tile_n == 128 || tile_n == 256) ctx->pass1_tile_n[key] = tile_n;
+    std::fclose(f);
+}
+
+void tune_cache_save(const mapper_ctx* ctx)
+{
+    const char* path = std::getenv("MAPPER_TUNE_CACHE");
+    if (!path || !*path || ctx->pass1_tile_n.empty()) return;
+    const std::string head = tune_cache_header(ctx->device);
+    if (head.empty()) return;
+    std::map<uint64_t, int> all;
+    if (std::FILE* f = std::fopen(path, "r")) {                // keep other contexts' keys
+        char line[512];
+        unsigned long long key = 0;
+        int tile_n = 0;
+        if (std::fgets(line, sizeof(line), f) && head == std::string(line).substr(0, head.size()))
+            while (std::fscanf(f, "%llu %d", &key, &tile_n) == 2) all[key] = tile_n;
+        std::fclose(f);
+    }
+    for (const auto& kv : ctx->pass1_tile_n) all[kv.first] = kv.second;
+    const std::string tmp = std::string(path) + ".tmp" + std::to_string((unsigned long long)(uintptr_t)ctx);
+    std::FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return;
+    std::fprintf(f, "%s\n", head.c_str());
+    for (const auto& kv : all) std::fprintf(f, "%llu %d\n", (unsigned long long)kv.first, kv.second);
+    const bool written = std::fclose(f) == 0;
+    if (written) std::rename(tmp.c_str(), path);
+    else std::remove(tmp.c_str());
+}
+
+}  // namespace
+
 int mapper_create(mapper_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream)
 {
     if (!out) return fail(MAPPER_EINVAL, "out is null");
@@ -981,6 +1051,7 @@ int mapper_create(mapper_ctx** out, int device, size_t hbm_budget_bytes, void* c
         uint64_t thr = UINT64_MAX;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
+    tune_cache_load(ctx.get());
     *out = ctx.release();
     return MAPPER_OK;
 }
@@ -990,6 +1061,7 @@ void mapper_destroy(mapper_ctx* ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream && ctx->stream->s) cudaStreamSynchronize(ctx->stream->s);
+    tune_cache_save(ctx);
     delete ctx;
 }
 
@@ -1226,6 +1298,8 @@ int mapper_single_linkage(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_
     fp32_thresholds(a.eps2, d, &a.lo_thr, &a.hi_thr);
     a.row_pt = L.row_pt.as<int32_t>();
     a.pairs = pairs.as<int2>();
+    a.n_rows = L.R;
+    a.n_tiles = L.T;
     auto h = std::make_unique<mapper_forest_t>();
     h->stream = ctx->stream;
     h->cover = cov;

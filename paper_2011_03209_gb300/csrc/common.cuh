@@ -27,6 +27,22 @@ inline void note_launch(int k = 1) { g_launches += k; }
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Index checks of the checked build (compiled with -DMAPPER_BOUNDS_CHECK):
+// an index outside [0, n) adds one to *oob (when oob is set) and the guarded
+// access is skipped; the host turns a nonzero count into MAPPER_EINTERNAL.
+// In the normal build the checks compile to nothing.
+#ifdef MAPPER_BOUNDS_CHECK
+__device__ __forceinline__ bool mgb_in_range(int64_t i, int64_t n, unsigned long long* oob)
+{
+    if (i >= 0 && i < n) return true;
+    if (oob) atomicAdd(oob, 1ull);
+    return false;
+}
+#define MGB_IN_RANGE(i, n, oob) ::mgb::mgb_in_range((int64_t)(i), (int64_t)(n), (oob))
+#else
+#define MGB_IN_RANGE(i, n, oob) true
+#endif
+
 // ------------------------------------------------------- stream-ordered memory
 // Scratch and result arrays come from the device's stream-ordered pool
 // (cudaMallocAsync); `Buf` frees on destruction on the same stream.

@@ -17,7 +17,7 @@ constexpr int kPairTileMask = kPairOneEach - 1;
 
 enum : int { kStatBand = 0, kStatTies = 1, kStatScreened = 2, kStatCore = 3, kStatTileOut = 4,
              kStatTileIn = 5, kStatSkipped = 6, kStatTcPairs = 7, kStatSimtPairs = 8, kStatFp64 = 9,
-             kStatUnion = 10, kStatRedo = 11, kStatCount = 12 };
+             kStatUnion = 10, kStatRedo = 11, kStatOob = 12, kStatCount = 13 };
 
 // Work lists of tile pairs, classified by bounding spheres.
 enum : int { kListAllIn = 0, kListTC = 1, kListSimt = 2, kListCount = 3 };
@@ -56,6 +56,7 @@ struct PassArgs {
     const int32_t* root;         // pass 3 (flattened)
     unsigned long long* border;  // pass 3 output: (canonical point << 32 | root row), min
     unsigned long long* stats;   // kStat* counters
+    int64_t n_rows, n_tiles;     // rows and tiles of the layout (index checks of the checked build)
 };
 
 // Row `row` of a pass (the tile layout's FP32 rows, or the input rows).
@@ -92,12 +93,13 @@ cudaError_t flatten(const int32_t* parent, const uint8_t* core, int64_t R, int32
                     cudaStream_t s);
 cudaError_t border_from_lists(const int32_t* count, const int32_t* nbr, int cap,
                               const uint8_t* core, const int32_t* root, const int32_t* row_pt,
-                              int64_t R, unsigned long long* border, cudaStream_t s);
+                              int64_t R, unsigned long long* border, cudaStream_t s,
+                              unsigned long long* oob = nullptr);
 // Row space -> cover-slot space: per slot the root slot of its node (or -1),
 // canonical point id (or -1), root flag, member flag and core flag.
 // Unions of each core row with the core rows of its pass-1 neighbour list.
 cudaError_t list_unions(const int32_t* count, const int32_t* nbr, int cap, const uint8_t* core, int32_t* parent,
-                        const int32_t* row_pt, int64_t R, cudaStream_t s);
+                        const int32_t* row_pt, int64_t R, cudaStream_t s, unsigned long long* oob = nullptr);
 cudaError_t rows_to_slots(const int32_t* row_slot, const int32_t* row_pt, const uint8_t* core,
                           const int32_t* root, const unsigned long long* border, int64_t R,
                           int32_t* lab, int32_t* is_root, int32_t* is_member,

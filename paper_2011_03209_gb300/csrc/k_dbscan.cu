@@ -152,12 +152,19 @@ __device__ __forceinline__ PairRows pair_rows(const PassArgs& A, int64_t q)
     PairRows P;
     if (A.pairs) {
         const int2 p = A.pairs[q];
-        const int tb = p.y & kPairTileMask;
-        P.sa = (int64_t)p.x * kT;
+        int ta = p.x, tb = p.y & kPairTileMask;
+        bool ok = true;
+        unsigned long long* oob = A.stats ? A.stats + kStatOob : nullptr;
+        (void)oob;
+        if (!MGB_IN_RANGE(ta, A.n_tiles, oob) || !MGB_IN_RANGE(tb, A.n_tiles, oob)) {
+            ta = tb = 0;
+            ok = false;
+        }
+        P.sa = (int64_t)ta * kT;
         P.sb = (int64_t)tb * kT;
-        P.na = A.tile_n[p.x];
-        P.nb = A.tile_n[tb];
-        P.diag = p.x == tb;
+        P.na = ok ? A.tile_n[ta] : 0;
+        P.nb = ok ? A.tile_n[tb] : 0;
+        P.diag = ta == tb;
     } else {
         const int64_t e = upper_bound_i64(A.pair_off, (int64_t)A.E + 1, q) - 1;
         const int64_t qq = q - A.pair_off[e];
@@ -503,15 +510,16 @@ __global__ void flatten_kernel(const int32_t* __restrict__ parent, const uint8_t
 __global__ void border_lists_kernel(const int32_t* __restrict__ count, const int32_t* __restrict__ nbr,
                                     int cap, const uint8_t* __restrict__ core,
                                     const int32_t* __restrict__ root, const int32_t* __restrict__ row_pt,
-                                    int64_t R, unsigned long long* __restrict__ border)
+                                    int64_t R, unsigned long long* __restrict__ border, unsigned long long* oob)
 {
+    (void)oob;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= R || core[s]) return;
     const int k = min(count[s], cap);
     unsigned long long best = ~0ull;
     for (int i = 0; i < k; ++i) {
         const int q = nbr[s * cap + i];
-        if (q < 0 || !core[q]) continue;
+        if (q < 0 || !MGB_IN_RANGE(q, R, oob) || !core[q]) continue;
         const int r = root[q];
         const unsigned long long code =
             ((unsigned long long)(unsigned)(row_pt ? row_pt[r] : r) << 32) | (unsigned)r;
@@ -526,14 +534,15 @@ __global__ void border_lists_kernel(const int32_t* __restrict__ count, const int
 // skips every tile pair whose core rows already share one root.
 __global__ void list_unions_kernel(const int32_t* __restrict__ count, const int32_t* __restrict__ nbr, int cap,
                                    const uint8_t* __restrict__ core, int32_t* __restrict__ parent,
-                                   const int32_t* __restrict__ row_pt, int64_t R)
+                                   const int32_t* __restrict__ row_pt, int64_t R, unsigned long long* oob)
 {
+    (void)oob;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= R || !core[s]) return;
     const int k = min(count[s], cap);
     for (int i = 0; i < k; ++i) {
         const int q = nbr[s * cap + i];
-        if (q >= 0 && core[q]) gunion(parent, row_pt, (int)s, q);
+        if (q >= 0 && MGB_IN_RANGE(q, R, oob) && core[q]) gunion(parent, row_pt, (int)s, q);
     }
 }
 
@@ -768,19 +777,19 @@ cudaError_t flatten(const int32_t* parent, const uint8_t* core, int64_t R, int32
 
 cudaError_t border_from_lists(const int32_t* count, const int32_t* nbr, int cap,
                               const uint8_t* core, const int32_t* root, const int32_t* row_pt,
-                              int64_t R, unsigned long long* border, cudaStream_t s)
+                              int64_t R, unsigned long long* border, cudaStream_t s, unsigned long long* oob)
 {
     if (R == 0 || cap <= 0) return cudaSuccess;
-    border_lists_kernel<<<grid_for(R), 256, 0, s>>>(count, nbr, cap, core, root, row_pt, R, border);
+    border_lists_kernel<<<grid_for(R), 256, 0, s>>>(count, nbr, cap, core, root, row_pt, R, border, oob);
     note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t list_unions(const int32_t* count, const int32_t* nbr, int cap, const uint8_t* core, int32_t* parent,
-                        const int32_t* row_pt, int64_t R, cudaStream_t s)
+                        const int32_t* row_pt, int64_t R, cudaStream_t s, unsigned long long* oob)
 {
     if (R == 0 || cap == 0) return cudaSuccess;
-    list_unions_kernel<<<grid_for(R), 256, 0, s>>>(count, nbr, cap, core, parent, row_pt, R);
+    list_unions_kernel<<<grid_for(R), 256, 0, s>>>(count, nbr, cap, core, parent, row_pt, R, oob);
     note_launch();
     return cudaGetLastError();
 }

@@ -112,6 +112,7 @@ struct MsfArgs {
     unsigned* cmin;                 // per root row: the smallest FP32 s of its candidate pairs (as bits)
     ulonglong2* ckey;               // per root row: the lightest candidate edge's key
     float eta, tiny;                // |s - d2| <= eta d2 + tiny
+    unsigned long long* oob;        // checked build: indices found out of range
 };
 
 // STAGE 1: component minima of s; STAGE 2: exact keys of the pairs near them.
@@ -125,9 +126,14 @@ __global__ void __launch_bounds__(256, 2) msf_screen_kernel(const MsfArgs M)
     const int tid = threadIdx.x;
     if (A.n_dev && (unsigned long long)blockIdx.x >= *A.n_dev) return;
     const int2 p = A.pairs[blockIdx.x];
-    const int ta = p.x, tb = p.y & kPairTileMask;
+    int ta = p.x, tb = p.y & kPairTileMask;
+    bool ok = true;
+    if (!MGB_IN_RANGE(ta, A.n_tiles, M.oob) || !MGB_IN_RANGE(tb, A.n_tiles, M.oob)) {
+        ta = tb = 0;                                       // checked build: counted, then skipped
+        ok = false;
+    }
     const int64_t sa = (int64_t)ta * kT, sb = (int64_t)tb * kT;
-    const int na = A.tile_n[ta], nb = A.tile_n[tb];
+    const int na = ok ? A.tile_n[ta] : 0, nb = ok ? A.tile_n[tb] : 0;
     const bool diag = ta == tb;
     s_root[tid] = tid < kT ? (tid < na ? M.root[sa + tid] : -1) : (tid - kT < nb ? M.root[sb + tid - kT] : -2);
 
@@ -370,11 +376,12 @@ int msf_forest(const PassArgs& a, const int32_t* row_slot, const int32_t* slot_p
     MK(tr.alloc(sizeof(int2) * std::max<int64_t>(T, 1), s));
     MK(lists[0].alloc(sizeof(int2) * std::max<int64_t>(n_pairs, 1), s));
     MK(lists[1].alloc(sizeof(int2) * std::max<int64_t>(n_pairs, 1), s));
-    MK(counts.alloc(sizeof(unsigned long long) * 4, s));       // n_edges, picks, list lengths
+    MK(counts.alloc(sizeof(unsigned long long) * 5, s));       // n_edges, picks, list lengths, index checks
     unsigned long long* n_edges = counts.as<unsigned long long>();
     unsigned long long* picks = n_edges + 1;
     unsigned long long* len = n_edges + 2;
-    MK(cudaMemsetAsync(counts.p, 0, sizeof(unsigned long long) * 4, s));
+    unsigned long long* oob = n_edges + 4;
+    MK(cudaMemsetAsync(counts.p, 0, sizeof(unsigned long long) * 5, s));
     const unsigned gR = (unsigned)div_up(R, 256);
     msf_init_kernel<<<gR, 256, 0, s>>>(row_slot, R, parent.as<int32_t>(), slot_row.as<int32_t>());
     MK(cudaGetLastError());
@@ -387,6 +394,7 @@ int msf_forest(const PassArgs& a, const int32_t* row_slot, const int32_t* slot_p
     m.cmin = cmin.as<unsigned>();
     m.ckey = ckey.as<ulonglong2>();
     m.eta = (float)(1.5 * (a.d + 4) * std::ldexp(1.0, -24));
+    m.oob = oob;
     m.tiny = (float)(3.0 * (a.d + 2) * std::ldexp(1.0, -149));
     if (m.tiny == 0.f) m.tiny = std::ldexp(1.0f, -149);
     int cur = 0;
@@ -417,10 +425,15 @@ int msf_forest(const PassArgs& a, const int32_t* row_slot, const int32_t* slot_p
         MK(cudaStreamSynchronize(s));
         if (h == 0) break;
     }
-    unsigned long long ne = 0;
+    unsigned long long ne = 0, h_oob = 0;
     MK(cudaMemcpyAsync(&ne, n_edges, sizeof(ne), cudaMemcpyDeviceToHost, s));
+    MK(cudaMemcpyAsync(&h_oob, oob, sizeof(h_oob), cudaMemcpyDeviceToHost, s));
     MK(cudaStreamSynchronize(s));
     out->n = (int64_t)ne;
+    if (h_oob) {
+        set_error("single linkage: a device-side index check failed");
+        return MAPPER_EINTERNAL;
+    }
 #undef MK
     return MAPPER_OK;
 }

@@ -796,7 +796,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 if (h >= it.nbt) break;
                 it.q[h] = h ? grp.y : grp.x;
                 it.mine[h] = P.sub_mask ? ((P.sub_mask[P.sub_q[it.q[h]]] >> sub) & 1u) != 0u : true;
-                const int2 tp = hd.tp[h];
+                int2 tp = hd.tp[h];
+                if (!MGB_IN_RANGE(tp.x, A.n_tiles, A.stats + kStatOob) ||
+                    !MGB_IN_RANGE(tp.y & kPairTileMask, A.n_tiles, A.stats + kStatOob)) {
+                    tp = make_int2(0, 0);                     // checked build: counted, then skipped
+                    it.mine[h] = false;
+                }
                 it.tb[h] = tp.y & kPairTileMask;
                 if (h == 0) {
                     it.ta = tp.x;
@@ -849,9 +854,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 if (!P.sub_mask && ew == 0 && lane == 0)
                     screened += diag ? (int64_t)cur.na * (cur.na + 1) / 2 : (int64_t)cur.na * cur.nb[h];
                 if (!cur.mine[h]) continue;
-                __syncwarp();                                 // the previous pair's wn is read
-                wn[lane] = cur.ncol2[h];
-                __syncwarp();
                 // per-row limits: in iff u >= k_in, out iff u < k_out (FP32, outward rounding)
                 float E;
                 if (P.rl) {
@@ -883,7 +885,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 for (int i = 3; i + 1 < 32; i += 2) vmax = fmax3(vmax, u[i], u[i + 1]);
                 vmax = fmaxf(vmax, u[31]);
                 uint32_t in_bits = 0u, keep_bits = 0u;
-                const bool all_out = __fmaf_ru(two, vmax, -cur.bmin2[h]) < k_out;
+                // padding rows hold no pair: out
+                const bool all_out = r >= cur.na || __fmaf_ru(two, vmax, -cur.bmin2[h]) < k_out;
+                if (__all_sync(0xffffffffu, all_out)) continue;   // nothing in, no band: nothing to do
                 bool all_in = false;
                 if (!all_out) {
                     float vmin = fmin3(u[0], u[1], u[2]);
@@ -892,9 +896,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                     vmin = fminf(vmin, u[31]);
                     all_in = __fmaf_rd(two, vmin, -cur.bn2[h]) >= k_in;
                 }
+                const bool mixed = !all_out && !all_in;
+                if (__any_sync(0xffffffffu, mixed)) {
+                    __syncwarp();                             // the previous pair's wn is read
+                    wn[lane] = cur.ncol2[h];
+                    __syncwarp();
+                }
                 if (all_in) {
                     in_bits = keep_bits = 0xffffffffu;
-                } else if (!all_out) {
+                } else if (mixed) {
                     // u = fl(two acc - |b|^2) (two = 2, or 2 s_a s_b for FP8), two
                     // columns per packed FMA (each lane correctly rounded)
                     const float4* wn4 = reinterpret_cast<const float4*>(wn);
@@ -1003,6 +1013,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             f.tp = A.pairs[q];
             f.one_each = (f.tp.y & kPairOneEach) != 0;
             f.tp.y &= kPairTileMask;
+            if (!MGB_IN_RANGE(f.tp.x, A.n_tiles, A.stats + kStatOob) ||
+                !MGB_IN_RANGE(f.tp.y, A.n_tiles, A.stats + kStatOob))
+                f.tp = make_int2(0, 0);                       // checked build: counted (results flagged)
             f.na = A.tile_n[f.tp.x];
             f.nb = A.tile_n[f.tp.y];
             const int64_t sa = (int64_t)f.tp.x * kT, sb = (int64_t)f.tp.y * kT;
@@ -1546,8 +1559,10 @@ __global__ void __launch_bounds__(256) recheck_kernel(const PassArgs A, const ui
         const bool live = i < n;
         uint2 e = make_uint2(0u, 0u);
         if (live) e = queue[i];
-        const int ra = (int)e.x, rb = (int)(e.y & 0x3FFFFFFFu);
+        int ra = (int)e.x, rb = (int)(e.y & 0x3FFFFFFFu);
         const uint32_t fl = e.y >> 30;
+        if (live && (!MGB_IN_RANGE(ra, A.n_rows, A.stats + kStatOob) || !MGB_IN_RANGE(rb, A.n_rows, A.stats + kStatOob)))
+            ra = rb = 0;                                  // checked build: counted (results flagged)
         const float* xa = live ? pass_row(A, ra) : nullptr;
         const float* xb = live ? pass_row(A, rb) : nullptr;
         float s32 = 0.f;

@@ -6,7 +6,8 @@ The clustering of each cover element is independent ("Mapper Interactive"
 the results, as the next step. Here every rank computes the lens and the
 cover (cheap, and identical on every rank), clusters the elements it owns
 (a longest-processing-time split by the cost n_i^2 d of each element), and
-the ranks exchange their nodes: the one exchange of the path. Every rank then
+the ranks exchange their nodes (all-gathers of plain tensors): the one
+exchange of the path. Every rank then
 merges the nodes in element order and computes the nerve of the merged list
 on its GPU.
 
@@ -75,14 +76,35 @@ def merge_nodes(pieces) -> tuple:
     return offs, mem, node_elem[order].astype(np.int32)
 
 
+_FIELDS = (("elements", np.int32), ("node_offsets", np.int64), ("node_members", np.int32), ("node_elem", np.int32))
+
+
 def exchange(piece: dict, group=None) -> list:
-    """Every rank's piece, on every rank (torch.distributed all-gather; a
-    single piece without a process group)."""
+    """Every rank's piece, on every rank (a single piece without a process
+    group). Two collectives of plain tensors: an all-gather of the four array
+    lengths, then one all-gather of each array padded to the longest rank's
+    length; on NCCL the tensors live on the current CUDA device, on gloo on
+    the host."""
+    import torch
     import torch.distributed as dist
     if not dist.is_available() or not dist.is_initialized():
         return [piece]
-    out = [None] * dist.get_world_size(group)
-    dist.all_gather_object(out, piece, group=group)
+    world = dist.get_world_size(group)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend(group) == "nccl" else torch.device("cpu")
+    lens = torch.tensor([len(piece[k]) for k, _ in _FIELDS], dtype=torch.int64, device=dev)
+    all_lens = [torch.empty_like(lens) for _ in range(world)]
+    dist.all_gather(all_lens, lens, group=group)
+    all_lens = torch.stack(all_lens).cpu().numpy()
+    out = [dict() for _ in range(world)]
+    for f, (key, dtype) in enumerate(_FIELDS):
+        width = max(int(all_lens[:, f].max()), 1)
+        mine = torch.zeros(width, dtype=torch.int64, device=dev)
+        if len(piece[key]):
+            mine[:len(piece[key])] = torch.from_numpy(np.asarray(piece[key], dtype=np.int64)).to(dev)
+        parts = [torch.empty_like(mine) for _ in range(world)]
+        dist.all_gather(parts, mine, group=group)
+        for r in range(world):
+            out[r][key] = parts[r][:int(all_lens[r, f])].cpu().numpy().astype(dtype)
     return out
 
 

@@ -137,3 +137,16 @@ int main(void) {
     # the ctypes mirrors of the structs have the C layout's sizes
     assert int(n_stats) == ctypes.sizeof(_capi.MapperStats)
     assert int(n_params) == ctypes.sizeof(_capi.MapperParams)
+
+
+def test_checked_build_exports_every_symbol():
+    """The checked build (device-side index checks turning an out-of-range
+    index into MAPPER_EINTERNAL) builds from the same sources and exports the
+    same C ABI."""
+    from paper_2011_03209_gb300 import _capi, build
+    path = build.build(checked=True)
+    lib = ctypes.CDLL(path)
+    for name in _capi.EXPORTS:
+        assert hasattr(lib, name), name
+    lib.mapper_abi_version.restype = ctypes.c_int
+    assert lib.mapper_abi_version() == 5

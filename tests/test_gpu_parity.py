@@ -470,11 +470,28 @@ def test_clusters_1m_d256_sampled(ctx, prec):
     nonempty = np.nonzero(sizes)[0]
     picks = [nonempty[np.argmin(sizes[nonempty])],
              nonempty[np.argsort(sizes[nonempty])[len(nonempty) // 3]]]
+    picks.append(int(rng.choice(nonempty[sizes[nonempty] <= 16000])))
     for e in picks:
         s, t = offs[e], offs[e + 1]
         _, core, label, ties = oracle.dbscan(w.X, pts[s:t], w.eps, w.min_pts)
         assert np.array_equal(res["core"][s:t], core), e
         assert np.array_equal(res["labels"][s:t], label), e
         assert ties == 0
+    # the largest element by sampled rows: core flags from the oracle's counts,
+    # labels by what every DBSCAN labelling satisfies
+    e = int(np.argmax(sizes))
+    s, t = offs[e], offs[e + 1]
+    members = pts[s:t]
+    sample = np.sort(rng.choice(t - s, 400, replace=False))
+    cnt = oracle.density_at(w.X[members], sample, w.eps)
+    assert np.array_equal(res["core"][s:t][sample], cnt >= w.min_pts)
+    lab = res["labels"][s:t]
+    pos = {int(p): i for i, p in enumerate(members)}
+    for i in sample:
+        l = int(lab[i])
+        if res["core"][s + i]:
+            assert 0 <= l <= int(members[i]) and res["core"][s + pos[l]] and lab[pos[l]] == l
+        elif l >= 0:
+            assert res["core"][s + pos[l]] and lab[pos[l]] == l
     assert res["stats"]["near_ties"] == 0
     _check_graph_properties(res, w.n)

@@ -136,3 +136,44 @@ def test_destroy_completes_a_pending_waiter(data):
     th.join(timeout=120.0)
     assert not th.is_alive()
     assert result["status"] in (0, mg._capi.MAPPER_ECANCELED)
+
+
+@pytest.mark.slow
+def test_full_size_serving_mix_against_single_calls_and_oracle():
+    """The serving mix at full size (the 1M x 256 cloud and eight mixtures up
+    to 5e5 points): twelve requests through four slots equal the same requests
+    alone; on three of them the DBSCAN of the smallest and of a median element
+    equals the oracle's."""
+    Xs = synth.serving_datasets(seed=4)
+    samples = [synth.pair_sample(X, 4 + i, 20000) for i, X in enumerate(Xs)]
+    reqs = synth.serving_requests(samples, 12, rate=1000.0, seed=11)
+    Xd = [torch.from_numpy(X).to("cuda:0") for X in Xs]
+
+    def prm(r):
+        return mg.params(r["lens_kind"], r["lens_arg"], r["n_intervals"], r["overlap"], r["eps"], r["min_pts"],
+                         mg.BF16)
+
+    with mg.Server(0, n_slots=4) as srv:
+        ids = [srv.add_dataset(X) for X in Xd]
+        tickets = [srv.submit(ids[r["dataset"]], prm(r)) for r in reqs]
+        got = []
+        for t in tickets:
+            g, info = srv.wait(t, timeout=300.0)
+            assert info["status"] == 0
+            got.append((g.numpy(), g))
+    with mg.Context(0) as ctx:
+        for k, (r, (out, g)) in enumerate(zip(reqs, got)):
+            alone = mg.mapper_graph(ctx, Xd[r["dataset"]], prm(r))
+            _same(out, alone.numpy())
+            if k < 3:
+                X = Xs[r["dataset"]]
+                offs, pts = g.cover().numpy()
+                lab, core = g.clusters().numpy(len(pts))
+                sizes = np.diff(offs)
+                ne = np.nonzero(sizes)[0]
+                for e in (int(ne[np.argmin(sizes[ne])]), int(ne[np.argsort(sizes[ne])[len(ne) // 2]])):
+                    s, t = offs[e], offs[e + 1]
+                    if t - s > 20000:
+                        continue
+                    _, rc, rl, ties = oracle.dbscan(X, pts[s:t], r["eps"], r["min_pts"])
+                    assert ties == 0 and np.array_equal(core[s:t], rc) and np.array_equal(lab[s:t], rl), (k, e)
