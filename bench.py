@@ -700,6 +700,7 @@ def run_knn(args):
         end.record(stream)
         torch.cuda.synchronize()
         clocks = sampler.stop()
+        path = ctx.knn_info()
     ms = start.elapsed_time(end) / args.steps
     # tensor-core screen: 2 d algorithmic flops per (query, point) pair (one
     # product; the kernel executes three BF16 products), over the whole call
@@ -727,10 +728,11 @@ def run_knn(args):
         "queries_per_s": q.size / (ms * 1e-3),
         "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
                      "traffic": None, "executed_tflops": 3.0 * tflops,
-                     "kernel": "tc_kernel<3,3,2> (tcgen05 BF16 k-distance screen, top-8 lists per query row and "
-                               "32-column part): 2d algorithmic flops per (query, point) pair over the whole call",
+                     "kernel": "tc_kernel<3,3,2> (tcgen05 BF16 k-distance screen: a sample of the point tiles "
+                               "gives each query a threshold, the full screen keeps the keys below it): 2d "
+                               "algorithmic flops per (query, point) pair over the whole call",
                      "peak_source": f"{src} bf16_tflops_sustained"},
-        "cpu_baseline": cpu, "clocks": clocks,
+        "path": path, "cpu_baseline": cpu, "clocks": clocks,
     }))
 
 

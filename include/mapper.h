@@ -254,8 +254,21 @@ int mapper_selftest_mma_error(mapper_ctx* ctx, int32_t dp, int32_t products, int
                               double* observed, double* modelled);
 /* Screen of mapper_knn_distance (a tuning knob; results do not depend on
  * it): 0 = tensor cores (default), 1 = tensor cores, 2 = the FP32 CUDA-core
- * screen. Other values: MAPPER_EINVAL. */
+ * screen, 3 = tensor cores without the sampled threshold (per-part lists
+ * only). Other values: MAPPER_EINVAL. */
 int mapper_set_knn_screen(mapper_ctx* ctx, int mode);
+/* The path the context's last mapper_knn_distance call took, in info[8]:
+ * [0] 0 = CUDA-core screen, 1 = tensor-core list screen, 2 = tensor-core
+ * screen with a threshold per query from a sample of the points (clouds of
+ * at least 512 tiles of 128 points; k <= 8); [1] the queries whose keys
+ * below their threshold exceeded the capacity and went through the list
+ * screen; [2] that capacity (keys per query); [3] the sample's tile stride;
+ * [4] the keys below the thresholds (all queries); [5] the largest such count
+ * of one query; [6] the candidates whose FP32 distance the merge computed;
+ * [7] those given the FP64 defining expression. Tensor-core paths fill
+ * [6] and [7]; the sampled path [1] .. [5]. Zeros before the first call.
+ * MAPPER_EINVAL for null arguments. */
+int mapper_knn_info(const mapper_ctx* ctx, int64_t* info);
 
 /* -------------------------------------------------------------- the steps */
 

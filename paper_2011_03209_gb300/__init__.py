@@ -61,8 +61,21 @@ class Context:
         _capi.check(self._lib.mapper_set_pass1_tile_n(self.h, int(tile_n)), "mapper_set_pass1_tile_n")
 
     def set_knn_screen(self, mode: int) -> None:
-        """k-distance screen: 0 tensor cores (default), 1 tensor cores, 2 CUDA cores."""
+        """k-distance screen: 0 tensor cores (default), 1 tensor cores, 2 CUDA
+        cores, 3 tensor cores without the sampled threshold."""
         _capi.check(self._lib.mapper_set_knn_screen(self.h, int(mode)), "mapper_set_knn_screen")
+
+    def knn_info(self) -> dict:
+        """The path of the last mapper_knn_distance call: path (0 CUDA cores,
+        1 tensor-core lists, 2 sampled threshold), queries over capacity, the
+        capacity per query, the sample's tile stride, the keys below the
+        thresholds (all queries, and the most of one query) and the merge's
+        FP32 and FP64 candidates."""
+        info = (ctypes.c_int64 * 8)()
+        _capi.check(self._lib.mapper_knn_info(self.h, info), "mapper_knn_info")
+        return {"path": int(info[0]), "over_capacity": int(info[1]), "capacity": int(info[2]),
+                "sample_stride": int(info[3]), "keys": int(info[4]), "max_keys": int(info[5]),
+                "fp32_candidates": int(info[6]), "fp64_candidates": int(info[7])}
 
     def set_cross_screen(self, mode: int) -> None:
         """Mixed tile pairs across two segments: 0 auto (default), 1 tensor

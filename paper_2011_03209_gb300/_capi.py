@@ -31,7 +31,7 @@ FP32, BF16, BF16X1, FP8 = 0, 1, 2, 3
 # every symbol include/mapper.h declares
 EXPORTS = (
     "mapper_create", "mapper_destroy", "mapper_set_stream", "mapper_set_timing", "mapper_set_pass1_tile_n",
-    "mapper_set_cross_screen", "mapper_selftest_wait", "mapper_set_knn_screen", "mapper_set_band_queue_cap",
+    "mapper_set_cross_screen", "mapper_selftest_wait", "mapper_set_knn_screen", "mapper_knn_info", "mapper_set_band_queue_cap",
     "mapper_set_pass1_screen", "mapper_selftest_mma_error", "mapper_single_linkage", "mapper_forest_sizes",
     "mapper_forest_copy", "mapper_forest_cut",
     "mapper_cover_subset", "mapper_nerve_from_nodes", "mapper_cover_balanced", "mapper_knn_distance",
@@ -151,6 +151,7 @@ def load(path: str | None = None):
             "mapper_set_cross_screen": (ctypes.c_int, [P, ctypes.c_int]),
             "mapper_selftest_wait": (ctypes.c_int, [P]),
             "mapper_set_knn_screen": (ctypes.c_int, [P, ctypes.c_int]),
+            "mapper_knn_info": (ctypes.c_int, [P, P]),
             "mapper_set_band_queue_cap": (ctypes.c_int, [P, i64]),
             "mapper_set_pass1_screen": (ctypes.c_int, [P, ctypes.c_int]),
             "mapper_single_linkage": (ctypes.c_int, [P, P, i64, i32, i64, P, f64, ctypes.POINTER(P)]),

@@ -75,7 +75,9 @@ struct mapper_ctx {
     std::map<uint64_t, int> pass1_tile_n;      // autotuner: (row pitch, products) -> N
     int pass1_forced = 0;                      // 128 or 256: fixed by the caller
     int cross_mode = 0;                        // cross-segment pairs: 0 auto, 1 tensor cores, 2 CUDA cores
-    int knn_mode = 0;                          // k-distance screen: 0 auto (tensor cores), 1 tensor, 2 CUDA cores
+    int knn_mode = 0;                          // k-distance screen: 0 auto (tensor cores), 1 tensor, 2 CUDA cores,
+                                               // 3 tensor-core lists only
+    int64_t knn_info[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // the last k-distance call's path (mapper_knn_info)
     int64_t band_cap = 0;                      // band-queue entries (0: sized from the tile pairs)
     int screen_mode = 0;                       // MAPPER_BF16 count pass: 0/1 two phases, 2 three products
 };
@@ -1106,8 +1108,15 @@ int mapper_selftest_mma_error(mapper_ctx* ctx, int32_t dp, int32_t products, int
 int mapper_set_knn_screen(mapper_ctx* ctx, int mode)
 {
     if (!ctx) return fail(MAPPER_EINVAL, "null context");
-    if (mode < 0 || mode > 2) return fail(MAPPER_EINVAL, "mode must be 0, 1 or 2");
+    if (mode < 0 || mode > 3) return fail(MAPPER_EINVAL, "mode must be 0, 1, 2 or 3");
     ctx->knn_mode = mode;
+    return MAPPER_OK;
+}
+
+int mapper_knn_info(const mapper_ctx* ctx, int64_t* info)
+{
+    if (!ctx || !info) return fail(MAPPER_EINVAL, "null argument");
+    for (int i = 0; i < 8; ++i) info[i] = ctx->knn_info[i];
     return MAPPER_OK;
 }
 
@@ -1502,21 +1511,34 @@ int mapper_knn_distance(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t 
     CK(cudaMemcpyAsync(hq.data(), queries, sizeof(int32_t) * q,
                        q_host ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost, s), "copy");
     Buf qd, od, flag;
-    CK(flag.alloc(sizeof(int), s), "alloc");
-    CK(cudaMemsetAsync(flag.p, 0, sizeof(int), s), "memset");
-    CK(check_finite(X_dev, n, d, ld, flag.as<int>(), s), "finite");
-    int h_nf = 0;
-    CK(cudaMemcpyAsync(&h_nf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
-    CK(cudaStreamSynchronize(s), "sync");
-    if (h_nf) return fail(MAPPER_ENONFINITE, "X holds NaN or Inf");
+    // X is checked for NaN / Inf: on the tensor-core path while its operands
+    // are built (a flagged row is then decided by the exact check below)
+    auto finite_or_fail = [&]() -> int {
+        CK(flag.alloc(sizeof(int), s), "alloc");
+        CK(cudaMemsetAsync(flag.p, 0, sizeof(int), s), "memset");
+        CK(check_finite(X_dev, n, d, ld, flag.as<int>(), s), "finite");
+        int h_nf = 0;
+        CK(cudaMemcpyAsync(&h_nf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+        CK(cudaStreamSynchronize(s), "sync");
+        if (h_nf) return fail(MAPPER_ENONFINITE, "X holds NaN or Inf");
+        return MAPPER_OK;
+    };
+    const bool tc = knn_on_tensor_cores(k, ctx->knn_mode != 2) && k >= 1 && k <= n;
+    if (!tc && (rc = finite_or_fail())) return rc;
     for (int64_t i = 0; i < q; ++i)
         if (hq[i] < 0 || hq[i] >= n) return fail(MAPPER_EINVAL, "query index out of range");
     CK(qd.alloc(sizeof(int32_t) * q, s), "alloc");
     CK(od.alloc(sizeof(double) * q, s), "alloc");
     CK(cudaMemcpyAsync(qd.p, hq.data(), sizeof(int32_t) * q, cudaMemcpyHostToDevice, s), "copy");
-    if ((rc = knn_distance(X_dev, n, d, ld, qd.as<int32_t>(), q, k, od.as<double>(), ctx->num_sms,
-                           ctx->knn_mode != 2, s)))
-        return rc;
+    rc = knn_distance(X_dev, n, d, ld, qd.as<int32_t>(), q, k, od.as<double>(), ctx->num_sms, ctx->knn_mode != 2, s,
+                      ctx->knn_info, ctx->knn_mode != 3, tc);
+    if (rc == MAPPER_ENONFINITE && tc) {
+        // a NaN or Inf, or finite rows whose norms pass FP32: the CUDA-core screen
+        if ((rc = finite_or_fail())) return rc;
+        rc = knn_distance(X_dev, n, d, ld, qd.as<int32_t>(), q, k, od.as<double>(), ctx->num_sms, false, s,
+                          ctx->knn_info);
+    }
+    if (rc) return rc;
     return copy_out(out, od.p, sizeof(double) * q, !is_host_pointer(out), s);
 }
 

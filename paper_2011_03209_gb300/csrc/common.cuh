@@ -83,9 +83,22 @@ cudaError_t lens_ecc2(const float* X, int64_t n, int32_t d, int64_t ld, double* 
 // k-th nearest-neighbour distances of q query rows (device indices) over all
 // n rows, the row itself first; out: q doubles on the device. Returns a
 // mapper_status (k in [1, min(16, n)]).
-// tensor_cores: screen on the tensor cores (else the FP32 CUDA-core screen).
+// tensor_cores: screen on the tensor cores (else the FP32 CUDA-core screen);
+// sample: large clouds take the sampled-threshold screen (else the list
+// screen alone). info (nullable, 8 entries): the path taken (0 CUDA cores,
+// 1 tensor-core lists, 2 sampled threshold), the queries over capacity, the
+// capacity per query, the sample's tile stride (0 where not sampled), the
+// keys below the thresholds, the largest such count of a query, and the
+// candidates given FP32 sums and FP64 distances by the merges.
+// screen_finite: the tensor-core path checks the rows for NaN / Inf while
+// it builds its operands (no separate pass) and returns MAPPER_ENONFINITE,
+// computing nothing, if a row's |row - c|^2 is not finite; the caller then
+// decides exactly.
 int knn_distance(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* queries_dev, int64_t q,
-                 int32_t k, double* out_dev, int num_sms, bool tensor_cores, cudaStream_t s);
+                 int32_t k, double* out_dev, int num_sms, bool tensor_cores, cudaStream_t s,
+                 int64_t* info = nullptr, bool sample = true, bool screen_finite = false);
+// Whether knn_distance takes the tensor-core path for these arguments.
+bool knn_on_tensor_cores(int32_t k, bool tensor_cores);
 // L-infinity centrality f(x) = max_y |x - y| into f[p * m + j]; a mapper_status.
 int lens_ecc_inf(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j, int num_sms,
                  bool tensor_cores, cudaStream_t s);

@@ -231,10 +231,12 @@ int classify_pairs(const TileLayout& L, const float* X, int64_t ld, int d, int d
 int fp8_operands(TileLayout* L, const float* X, int64_t ld, int d, int dp, cudaStream_t s);
 // BF16 hi + lo operands of rows row_pt[.] of X (T tiles of 128 rows, the
 // first tile_n[t] of tile t valid, the rest zero), centred on cents[tile_cent[t]]
-// (dp floats each), with FP32 |a|^2 and |a| rounded up.
+// (dp floats each), with FP32 |a|^2 and |a| rounded up. nonfinite (nullable):
+// set to 1 when a valid row's |a|^2 is not finite (a NaN or Inf in the row, or
+// a norm beyond FP32).
 cudaError_t centred_operands(const float* X, int64_t ld, int d, int dp, const int32_t* row_pt, const int32_t* tile_n,
                              const int32_t* tile_cent, const float* cents, int64_t T, void* Ah, void* Al, float* rn2,
-                             float* rn, cudaStream_t s);
+                             float* rn, cudaStream_t s, int* nonfinite = nullptr);
 // Tensor-core operands for the CUDA-core list (tile pairs of one element, two
 // segments): every row centred on its element's centre, BF16 hi + lo, with
 // FP32 |a|^2, and |a| and |a - hi| rounded up (R rows each), their largest

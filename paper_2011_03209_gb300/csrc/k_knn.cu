@@ -459,127 +459,404 @@ __device__ __forceinline__ float fp32_sqdist_rows(const float* __restrict__ x, c
     return s;
 }
 
-// Merge for the tensor-core screen. Its lists hold lower bounds l = key - E
-// of the exact key (d^2, or -d^2 for FAR) with E = A1 |a||b| + A2 (|a|^2 +
-// |b|^2) + A3 for that pair of rows, so u = l + 2E bounds it from above. The
-// k-th smallest exact key is at most U = the k-th smallest u over the lists,
-// and every point that can reach it has l <= U. Each list (kTL smallest l of a
-// 32-point part of a chunk) holds every point of its part below its last l;
-// the candidates are the entries below U of the lists whose last l exceeds U,
-// and every point of the parts whose list does not (the warp screens those
-// together). The candidates are then screened
-// again by their FP32 sums (relative error eta): with T32 the k-th smallest
-// of those keys, only candidates within B32 = (T32 + tiny)(1 + eta) / (1 - eta)
-// + tiny (FAR: the mirror bound) can hold the k-th exact key, and those few
-// get the FP64 defining expression. One warp per query, lane i takes lists
-// i, i + 32, ..
+// Merge for the tensor-core screen. Its keys l are lower bounds of the exact
+// key (d^2, or -d^2 for FAR), and u = RU(l + W), W = RU(Kw (|a|^2 + |b|^2) +
+// A3w), bounds it from above (Kw, A3w cover twice the screen's error bound
+// and the rounding of l). The k-th smallest exact key is at most U = the k-th
+// smallest u over the candidates, and every point that can reach it has l <= U.
+//   LISTS: each list (kTL smallest l of a 32-point part of a chunk) holds
+//   every point of its part below its last l; the candidates are the entries
+//   below U of the lists whose last l exceeds U, and every point of the parts
+//   whose list does not (the warp screens those together).
+//   TAU: the lists of a sample of the points; writes U (a bound of the k-th
+//   smallest exact key over the sample, so over all points) and stops.
+//   FLAT: every point with l <= tau[query] (a TAU bound), unordered; a query
+//   whose count exceeds the capacity is listed in ovf for another pass.
+// The candidates are then screened again by their FP32 sums (relative error
+// eta): with T32 the k-th smallest of those keys, only candidates within B32 =
+// (T32 + tiny)(1 + eta) / (1 - eta) + tiny (FAR: the mirror bound) can hold the
+// k-th exact key, and those few get the FP64 defining expression. One warp per
+// query, lane i takes lists (entries) i, i + 32, ..
 constexpr int kTL = kKnnList;
+enum MergeSrc { kLists = 0, kTau = 1, kFlat = 2 };
 
-template <bool FAR>
-__global__ void __launch_bounds__(256) knn_merge_abs_kernel(const float* __restrict__ X, int d, int64_t ld,
-                                                            const int32_t* __restrict__ queries, int64_t q,
-                                                            int n_lists, const float* __restrict__ cand_v,
-                                                            const int32_t* __restrict__ cand_i, int k,
-                                                            const float* __restrict__ rn2, const float* __restrict__ rn,
-                                                            int64_t q_row0, float A1, float A2, float A3,
-                                                            float eta_lo, float eta_hi, float tiny, int64_t n,
-                                                            int64_t Tp, int chunk_tiles, bool vec4,
-                                                            double* __restrict__ out)
+struct MergeArgs {
+    const float* X;
+    int d;
+    int64_t ld;
+    const int32_t* queries;
+    int64_t q;
+    int n_lists;                     // LISTS / TAU: lists per query
+    const float* cand_v;
+    const int32_t* cand_i;
+    int k;
+    const float* rn2;                // |row|^2 of the operand rows
+    int64_t q_row0;                  // operand row of query 0
+    float Kw, A3w;
+    float eta_lo, eta_hi, tiny;
+    int64_t n, Tp;
+    int chunk_tiles;
+    bool vec4;
+    double* out;                     // LISTS / FLAT: the k-th distance per query
+    float* tau;                      // TAU: U per query
+    const int* count;                // FLAT: entries per query (may exceed cap)
+    int cap;
+    const int64_t* off;              // FLAT, if set: query i's entries at off[i] .. off[i + 1]
+    int* ovf_n;                      // FLAT: queries over capacity, listed in ovf
+    int32_t* ovf;
+    unsigned long long* stats;       // nullable: keys kept (FLAT), FP32 candidates, FP64
+                                     // candidates, largest key count (FLAT)
+    // nullable: the FP64 candidates of a query with at most kF of them go to
+    // one list for knn_fp64_kernel (all lanes busy: one warp-wide FP64
+    // instruction costs the same however few lanes are active); m_off / m_cnt
+    // / m_k per query (m_cnt < 0: settled in the merge)
+    int* f64_n;
+    int64_t f64_cap;
+    int32_t* f64_q;
+    int32_t* f64_j;
+    int64_t* m_off;
+    int32_t* m_cnt;
+    int32_t* m_k;
+};
+constexpr int kF = 8;                // FP64 candidates per query sent to the shared list
+
+// FP32 sum of squared differences of two rows, the warp together: lane l
+// takes columns l, l + 32, .. (vec4: 4 l .. 4 l + 3, + 128, ..) in order with
+// FMAs, then the 32 partial sums meet in a butterfly. A term passes at most
+// ceil(d / 128) 4 + 5 roundings (d + 5 for any d), which the merge's eta covers.
+__device__ __forceinline__ float warp_sqdist_f32(const float* __restrict__ x, const float* __restrict__ y, int d,
+                                                 bool vec4, int lane)
 {
-    constexpr int kCache = 8;                    // candidates cached per lane
-    __shared__ float c_f[8][kCache][32];
-    __shared__ int c_j[8][kCache][32];
+    float s = 0.f;
+    if (vec4) {
+        for (int k = lane * 4; k < d; k += 128) {
+            const float4 p = *reinterpret_cast<const float4*>(x + k), r = __ldg(reinterpret_cast<const float4*>(y + k));
+            float t = p.x - r.x;
+            s = fmaf(t, t, s);
+            t = p.y - r.y;
+            s = fmaf(t, t, s);
+            t = p.z - r.z;
+            s = fmaf(t, t, s);
+            t = p.w - r.w;
+            s = fmaf(t, t, s);
+        }
+    } else {
+        for (int k = lane; k < d; k += 32) {
+            const float t = x[k] - __ldg(y + k);
+            s = fmaf(t, t, s);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+template <bool FAR, int SRC>
+__global__ void __launch_bounds__(256) knn_merge_tc_kernel(const MergeArgs a)
+{
+    constexpr int kMC = 256;                     // FP32 keys cached and FP64 candidates listed per warp
+    __shared__ int s_j[8][kMC];
+    __shared__ float s_f[8][kMC];
+    __shared__ int s_p[8][64];                   // candidates gathering into a batch
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t qi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (qi >= q) return;                         // whole warp
-    const float* cv = cand_v + qi * (int64_t)n_lists * kTL;
-    const int32_t* ci = cand_i + qi * (int64_t)n_lists * kTL;
-    const float na2 = rn2[q_row0 + qi], nra = rn[q_row0 + qi];
+    if (qi >= a.q) return;                       // whole warp
+    const int k = a.k;
+    int64_t e_base = qi * (int64_t)(SRC == kFlat ? a.cap : a.n_lists * kTL), e_cap = a.cap;
+    if (SRC == kFlat && a.off) {
+        e_base = a.off[qi];
+        e_cap = a.off[qi + 1] - e_base;
+    }
+    const float* cv = a.cand_v + e_base;
+    const int32_t* ci = a.cand_i + e_base;
+    int n_ent = 0;                               // FLAT: entries of this query
+    if constexpr (SRC == kFlat) {
+        const int c = a.count[qi];
+        if (a.stats && lane == 0) {
+            atomicAdd(a.stats, (unsigned long long)c);
+            atomicMax(a.stats + 3, (unsigned long long)c);
+        }
+        if (c > e_cap) {
+            if (lane == 0) a.ovf[atomicAdd(a.ovf_n, 1)] = (int32_t)qi;
+            return;
+        }
+        n_ent = c;
+    }
+    const float na2 = a.rn2[a.q_row0 + qi];
+    auto ub = [&](float lo, int j) { return __fadd_ru(lo, __fmaf_ru(a.Kw, __fadd_ru(na2, a.rn2[j]), a.A3w)); };
     float top[kTL];
 #pragma unroll
     for (int i = 0; i < kTL; ++i) top[i] = INFINITY;
     float worst = INFINITY, mlast = INFINITY;
-    for (int l = lane; l < n_lists; l += 32) {
-        const int64_t e0 = (int64_t)l * kTL;
-        mlast = fminf(mlast, cv[e0 + kTL - 1]);
-        for (int i = 0; i < kTL; ++i) {
-            const float lo = cv[e0 + i];
-            if (!(lo < worst)) break;            // ascending list; u >= l
-            const int j = ci[e0 + i];
-            const float E = __fmaf_ru(A1, __fmul_ru(nra, rn[j]), __fmaf_ru(A2, __fadd_ru(na2, rn2[j]), A3));
-            topk_insert(top, k, __fadd_ru(lo, __fmul_ru(2.f, E)), worst);
+    if constexpr (SRC == kFlat) {
+        for (int e = lane; e < n_ent; e += 32) topk_insert(top, k, ub(cv[e], ci[e]), worst);
+    } else {
+        for (int l = lane; l < a.n_lists; l += 32) {
+            const int64_t e0 = (int64_t)l * kTL;
+            mlast = fminf(mlast, cv[e0 + kTL - 1]);
+            for (int i = 0; i < kTL; ++i) {
+                const float lo = cv[e0 + i];
+                if (!(lo < worst)) break;            // ascending list; u >= l
+                topk_insert(top, k, ub(lo, ci[e0 + i]), worst);
+            }
         }
     }
     const float U = warp_kth(top, k, lane);
+    if constexpr (SRC == kTau) {
+        if (lane == 0) a.tau[qi] = U;
+        return;
+    }
 #pragma unroll
     for (int o = 16; o; o >>= 1) mlast = fminf(mlast, __shfl_xor_sync(0xffffffffu, mlast, o));
-    const bool all_complete = U < mlast;
-    const float* xq = X + (int64_t)queries[qi] * ld;
-    // Visits every candidate once: entries below U of complete lists (lane
-    // by list), then all points of the incomplete lists' parts (the warp
-    // together, part by part).
-    auto for_candidates = [&](auto&& visit) {
-        for (int l = lane; l < n_lists; l += 32) {
-            if (!(cv[(int64_t)l * kTL + kTL - 1] > U)) continue;
-            for (int i = 0; i < kTL; ++i) {
-                const int64_t e = (int64_t)l * kTL + i;
-                if (!(cv[e] <= U)) break;
-                visit((int64_t)ci[e]);
+    const bool all_complete = SRC == kFlat || U < mlast;
+    const float* xq = a.X + (int64_t)a.queries[qi] * a.ld;
+    // The candidates as one stream, the same order on every call, in batches
+    // of up to 32: batch(j, valid) runs on the whole warp, lane l holding
+    // candidate base + l. FLAT: the entries up to U; LISTS: entries up to U
+    // of the complete lists, then every point of the parts whose list is
+    // incomplete. Sparse candidates gather in a per-warp buffer first.
+    auto stream = [&](auto&& batch) {
+        int np = 0;                              // pending candidates in s_p
+        auto push = [&](bool c, int j) {
+            const unsigned bal = __ballot_sync(0xffffffffu, c);
+            if (c) s_p[wib][np + __popc(bal & ((1u << lane) - 1u))] = j;
+            np += __popc(bal);
+            __syncwarp();
+            if (np >= 32) {
+                batch(s_p[wib][lane], true);
+                const int rest = np - 32;
+                const int moved = lane < rest ? s_p[wib][32 + lane] : 0;
+                __syncwarp();
+                if (lane < rest) s_p[wib][lane] = moved;
+                np = rest;
+                __syncwarp();
+            }
+        };
+        if constexpr (SRC == kFlat) {
+            for (int e0 = 0; e0 < n_ent; e0 += 32) {
+                const int e = e0 + lane;
+                const bool c = e < n_ent && cv[e] <= U;
+                push(c, c ? ci[e] : 0);
+            }
+        } else {
+            for (int l0 = 0; l0 < a.n_lists; l0 += 32) {
+                const int l = l0 + lane;
+                const bool complete = l < a.n_lists && cv[(int64_t)l * kTL + kTL - 1] > U;
+                for (int i = 0; i < kTL; ++i) {
+                    const bool c = complete && cv[(int64_t)l * kTL + i] <= U;
+                    push(c, c ? ci[(int64_t)l * kTL + i] : 0);
+                }
+            }
+            if (!all_complete) {
+                for (int l = 0; l < a.n_lists; ++l) {
+                    if (cv[(int64_t)l * kTL + kTL - 1] > U) continue;
+                    const int64_t c = l / kParts, part = l % kParts;
+                    const int64_t b0 = c * a.chunk_tiles, b1 = min(a.Tp, b0 + a.chunk_tiles);
+                    for (int64_t t0 = 0; t0 < (b1 - b0) * 32; t0 += 32) {
+                        const int64_t j = (b0 + t0 / 32) * 128 + part * 32 + lane;
+                        push(j < a.n, (int)j);
+                    }
+                }
             }
         }
-        if (all_complete) return;
-        for (int l = 0; l < n_lists; ++l) {
-            if (cv[(int64_t)l * kTL + kTL - 1] > U) continue;
-            const int64_t c = l / kParts, part = l % kParts;
-            const int64_t b0 = c * chunk_tiles, b1 = min(Tp, b0 + chunk_tiles);
-            for (int64_t t = lane; t < (b1 - b0) * 32; t += 32) {
-                const int64_t j = (b0 + t / 32) * 128 + part * 32 + (t & 31);
-                if (j < n) visit(j);
-            }
-        }
+        __syncwarp();
+        if (np > 0) batch(lane < np ? s_p[wib][lane] : 0, lane < np);
+        __syncwarp();
     };
-    // FP32 keys of the candidates: their k-th smallest
+    // FP32 keys g (d^2, FAR -d^2) of the candidates, one per lane (the
+    // sequential FMA sum); g and the exact key e lie within
+    //   e in [klo(g), khi(g)],  d^2 in [RD(RD(f - tiny) / eta_hi), RU(RU(f + tiny) / eta_lo)].
+    // Gk = the k-th smallest g; T_lo = klo(Gk) <= D* <= T_hi = khi(Gk) for the
+    // k-th smallest exact key D* (klo, khi increase with g). Candidates with
+    // khi(g) < T_lo are below D* (at most k - 1 of them: nb), those with
+    // klo(g) > T_hi above it; D* is the (k - nb)-th smallest exact key of the
+    // rest, the few that get the FP64 defining expression. The first kMC
+    // keys are kept for the later passes.
+    const int d = a.d;
+    const float tiny = a.tiny, eta_hi = a.eta_hi, eta_lo = a.eta_lo;
+    auto d2_lo = [&](float f) { return __fdiv_rd(__fsub_rd(f, tiny), eta_hi); };
+    auto d2_hi = [&](float f) { return __fdiv_ru(__fadd_ru(f, tiny), eta_lo); };
+    auto klo = [&](float g) { return FAR ? -d2_hi(-g) : d2_lo(g); };
+    auto khi = [&](float g) { return FAR ? -d2_lo(-g) : d2_hi(g); };
+    int base = 0;                                // candidates before the batch
+    auto key32 = [&](int j, bool valid, bool first) {
+        const int c = base + lane;
+        float f;
+        if (!first && c < kMC) {
+            f = s_f[wib][c];
+        } else {
+            const float* y = a.X + (int64_t)(valid ? j : 0) * a.ld;
+            f = a.vec4 ? fp32_sqdist_rows4(xq, y, d) : fp32_sqdist_rows(xq, y, d);
+            if (first && valid && c < kMC) s_f[wib][c] = f;
+        }
+        return FAR ? -f : f;
+    };
     float topf[kTL];
 #pragma unroll
     for (int i = 0; i < kTL; ++i) topf[i] = INFINITY;
     float worstf = INFINITY;
-    int n_cached = 0;                            // this lane's candidates, kept for the last pass
-    bool spilled = false;
-    for_candidates([&](int64_t j) {
-        const float* y = X + j * ld;
-        const float f = vec4 ? fp32_sqdist_rows4(xq, y, d) : fp32_sqdist_rows(xq, y, d);
-        topk_insert(topf, k, FAR ? -f : f, worstf);
-        if (n_cached < kCache) {
-            c_f[wib][n_cached][lane] = f;
-            c_j[wib][n_cached][lane] = (int)j;
-            ++n_cached;
-        } else {
-            spilled = true;
-        }
+    stream([&](int j, bool valid) {
+        const float g = key32(j, valid, true);
+        if (valid) topk_insert(topf, k, g, worstf);
+        base += __popc(__ballot_sync(0xffffffffu, valid));
     });
-    const float t32 = warp_kth(topf, k, lane);
-    const float b_hi = __fadd_ru(__fdiv_ru(__fmul_ru(__fadd_ru(t32, tiny), eta_hi), eta_lo), tiny);
-    const float b_lo = __fsub_rd(__fdiv_rd(__fmul_rd(__fsub_rd(-t32, tiny), eta_lo), eta_hi), tiny);
+    const int nc = base;
+    const float Gk = warp_kth(topf, k, lane);
+    const float T_lo = klo(Gk), T_hi = khi(Gk);
     double topd[kTL];
 #pragma unroll
     for (int i = 0; i < kTL; ++i) topd[i] = INFINITY;
     double worstd = INFINITY;
-    auto decide = [&](int64_t j, float f) {
-        if (FAR ? !(f >= b_lo) : !(f <= b_hi)) return;
-        const float* y = X + j * ld;
-        const double e2 = vec4 ? exact_sqdist_rows4(xq, y, d) : exact_sqdist_rows(xq, y, d);
-        topk_insert(topd, k, FAR ? -e2 : e2, worstd);
-    };
-    if (__any_sync(0xffffffffu, spilled)) {      // some lane's candidates did not fit: all again
-        for_candidates([&](int64_t j) {
-            const float* y = X + j * ld;
-            decide(j, vec4 ? fp32_sqdist_rows4(xq, y, d) : fp32_sqdist_rows(xq, y, d));
+    int nb = 0, n64 = 0;
+    for (int round = 0;; ++round) {
+        // middle candidates round kMC .. + kMC go to s_j
+        int m = 0;
+        base = 0;
+        stream([&](int j, bool valid) {
+            const float g = key32(j, valid, false);
+            const bool below = valid && khi(g) < T_lo;
+            const bool mid = valid && !below && !(klo(g) > T_hi);
+            if (round == 0) nb += __popc(__ballot_sync(0xffffffffu, below));
+            const unsigned bm = __ballot_sync(0xffffffffu, mid);
+            const int pos = m + __popc(bm & ((1u << lane) - 1u)) - round * kMC;
+            if (mid && pos >= 0 && pos < kMC) s_j[wib][pos] = j;
+            m += __popc(bm);
+            base += __popc(__ballot_sync(0xffffffffu, valid));
         });
-    } else {
-        for (int t = 0; t < n_cached; ++t) decide(c_j[wib][t][lane], c_f[wib][t][lane]);
+        __syncwarp();
+        if (round == 0 && a.f64_n && m <= kF) {
+            // the few FP64 candidates join the shared list
+            int pos = 0;
+            if (lane == 0) pos = atomicAdd(a.f64_n, m);
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if (pos + m <= a.f64_cap) {
+                if (lane < m) {
+                    a.f64_q[pos + lane] = (int32_t)qi;
+                    a.f64_j[pos + lane] = s_j[wib][lane];
+                }
+                if (lane == 0) {
+                    a.m_off[qi] = pos;
+                    a.m_cnt[qi] = m;
+                    a.m_k[qi] = k - nb;
+                }
+                if (a.stats) {
+                    if (lane == 0) {
+                        atomicAdd(a.stats + 1, (unsigned long long)nc);
+                        atomicAdd(a.stats + 2, (unsigned long long)m);
+                    }
+                }
+                return;
+            }
+            if (lane < m && pos + lane < a.f64_cap) a.f64_q[pos + lane] = -1;    // unused slots
+        }
+        const int hi = min(m, (round + 1) * kMC) - round * kMC;
+        for (int t = lane; t < hi; t += 32) {
+            const float* y = a.X + (int64_t)s_j[wib][t] * a.ld;
+            const double e2 = a.vec4 ? exact_sqdist_rows4(xq, y, d) : exact_sqdist_rows(xq, y, d);
+            topk_insert(topd, k - nb, FAR ? -e2 : e2, worstd);
+            ++n64;
+        }
+        __syncwarp();
+        if (m <= (round + 1) * kMC) break;
     }
-    const double kth = warp_kth(topd, k, lane);
-    if (lane == 0) out[qi] = __dsqrt_rn(FAR ? -kth : kth);
+    const double kth = warp_kth(topd, k - nb, lane);
+    if (lane == 0) a.out[qi] = __dsqrt_rn(FAR ? -kth : kth);
+    if (a.stats) {
+        const int e64 = __reduce_add_sync(0xffffffffu, n64);
+        if (lane == 0) {
+            atomicAdd(a.stats + 1, (unsigned long long)nc);
+            atomicAdd(a.stats + 2, (unsigned long long)e64);
+        }
+    }
+}
+
+// FP64 defining expression of the listed (query, point) candidates, one per
+// thread: v[i] = d^2(X[queries[f64_q[i]]], X[f64_j[i]]).
+__global__ void knn_fp64_kernel(const float* __restrict__ X, int d, int64_t ld, bool vec4,
+                                const int32_t* __restrict__ queries, const int* __restrict__ f64_n, int64_t cap,
+                                const int32_t* __restrict__ f64_q, const int32_t* __restrict__ f64_j,
+                                double* __restrict__ v)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= min((int64_t)*f64_n, cap) || f64_q[i] < 0) return;
+    const float* x = X + (int64_t)queries[f64_q[i]] * ld;
+    const float* y = X + (int64_t)f64_j[i] * ld;
+    v[i] = vec4 ? exact_sqdist_rows4(x, y, d) : exact_sqdist_rows(x, y, d);
+}
+
+// The queries whose FP64 candidates went to the list: the m_k-th smallest
+// exact key (d^2; FAR -d^2) of its m_cnt <= kF values.
+template <bool FAR>
+__global__ void knn_f64_select_kernel(int64_t q, const int64_t* __restrict__ m_off, const int32_t* __restrict__ m_cnt,
+                                      const int32_t* __restrict__ m_k, const double* __restrict__ v,
+                                      double* __restrict__ out)
+{
+    const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= q || m_cnt[qi] < 0) return;
+    double top[kF];
+#pragma unroll
+    for (int i = 0; i < kF; ++i) top[i] = INFINITY;
+    double worst = INFINITY;
+    const int m = m_cnt[qi], kk = m_k[qi];
+    for (int i = 0; i < m; ++i) {
+        const double e2 = v[m_off[qi] + i];
+        topk_insert(top, kk, FAR ? -e2 : e2, worst);
+    }
+    double kth = top[0];
+#pragma unroll
+    for (int i = 0; i < kF; ++i)
+        if (i == kk - 1) kth = top[i];
+    out[qi] = __dsqrt_rn(FAR ? -kth : kth);
+}
+
+// out[ovf[i]] = sub[i]
+__global__ void knn_scatter_kernel(const int32_t* __restrict__ ovf, const int* __restrict__ n_ovf,
+                                   const double* __restrict__ sub, double* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < *n_ovf) out[ovf[i]] = sub[i];
+}
+
+// For the queries over capacity: cnt[i] = count[ovf[i]], tau2[i] = tau[ovf[i]]
+__global__ void knn_ovf_gather_kernel(const int32_t* __restrict__ ovf, const int* __restrict__ n_ovf,
+                                      const int* __restrict__ count, const float* __restrict__ tau,
+                                      int32_t* __restrict__ cnt, float* __restrict__ tau2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < *n_ovf) {
+        cnt[i] = count[ovf[i]];
+        tau2[i] = tau[ovf[i]];
+    }
+}
+
+// Operand rows dst0 + i (i < rows, a multiple of 128) := rows src0 + ovf[i]
+// (i < n_ovf) or zero rows: BF16 hi and lo (dp columns) and |row|^2. One
+// warp per row, 16-byte copies.
+__global__ void knn_copy_rows_kernel(uint16_t* __restrict__ Ah, uint16_t* __restrict__ Al, float* __restrict__ rn2,
+                                     int dp, int64_t src0, const int32_t* __restrict__ ovf,
+                                     const int* __restrict__ n_ovf, int64_t dst0, int64_t rows)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= rows) return;
+    const bool live = i < *n_ovf;
+    const int64_t src = live ? src0 + ovf[i] : 0, dst = dst0 + i;
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    for (int c = lane * 8; c < dp; c += 256) {
+        const uint4 h = live ? *reinterpret_cast<const uint4*>(Ah + src * dp + c) : z;
+        const uint4 l = live ? *reinterpret_cast<const uint4*>(Al + src * dp + c) : z;
+        *reinterpret_cast<uint4*>(Ah + dst * dp + c) = h;
+        *reinterpret_cast<uint4*>(Al + dst * dp + c) = l;
+    }
+    if (lane == 0) rn2[dst] = live ? rn2[src] : 0.f;
+}
+
+// sub[i] = queries[ovf[i]]
+__global__ void knn_gather_kernel(const int32_t* __restrict__ ovf, const int* __restrict__ n_ovf,
+                                  const int32_t* __restrict__ queries, int32_t* __restrict__ sub)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < *n_ovf) sub[i] = queries[ovf[i]];
 }
 
 // Layout of the tensor-core screen's operand rows: points 0 .. n-1 in
@@ -644,58 +921,78 @@ __global__ void sample_centre_kernel(const double* __restrict__ part, int64_t n,
     } while (0)
 
 // The tensor-core screen: rows centred on the column means, three BF16
-// products per tile pair; per query the 16 smallest (FAR: largest) screened
-// values, a bound from the screen's absolute error, the exact FP64 distances
-// of the candidates; queries whose 16 values do not settle it go through the
-// CUDA-core screen.
+// products per tile pair. Large clouds: a first screen of a strided sample
+// of the point tiles (lists) gives every query a bound tau of its k-th
+// smallest key (the k-th smallest upper bound over the sample); the second
+// screen over all points keeps every key <= tau, unsorted, and the merge
+// settles the query from those (exact FP64 for the few near the k-th). A
+// query with more keys below tau than the capacity goes through the list
+// screen alone. Small clouds: the list screen over all points, whose merge
+// screens whole parts when a list is incomplete.
+constexpr int64_t kSampleMinTiles = 512;   // point tiles for the sampled path
+constexpr int64_t kSampleTiles = 256;      // about this many sample tiles
+
 template <bool FAR>
 int knn_select_tc(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* queries_dev, int64_t q, int32_t k,
-                  double* out_dev, int num_sms, cudaStream_t s)
+                  double* out_dev, int num_sms, cudaStream_t s, bool sampled = true, int64_t* info = nullptr,
+                  bool screen_finite = false)
 {
     const int dp = (d + 31) / 32 * 32;
     const int64_t Tp = div_up(n, 128), Tq = div_up(q, 128), T = Tp + Tq, R = T * 128;
-    // FP32 re-screen of the candidates (the CUDA-core screen's bound)
-    const double eta = 1.5 * (d + 4) * std::ldexp(1.0, -24);
+    // FP32 re-screen of the candidates: relative error at most (D + 2) 2^-24
+    // (1 + 2^-20) for D <= d + 5 roundings of a term (sequential, or the
+    // merge's warp butterfly), plus at most 2^-150 for each rounding in the
+    // subnormal range; the margin of eta also covers the (d + 2) 2^-53 by
+    // which the FP64 defining expression may differ from d^2
+    const double eta = 1.5 * (d + 8) * std::ldexp(1.0, -24);
     float eta_hi = (float)(1.0 + eta), eta_lo = (float)(1.0 - eta);
     if ((double)eta_hi < 1.0 + eta) eta_hi = std::nextafter(eta_hi, INFINITY);
     if ((double)eta_lo > 1.0 - eta) eta_lo = std::nextafter(eta_lo, 0.f);
-    const float tiny = (float)(3.0 * (d + 2) * std::ldexp(1.0, -149)) + FLT_TRUE_MIN;
+    const float tiny = (float)(3.0 * (d + 8) * std::ldexp(1.0, -149)) + FLT_TRUE_MIN;
     const int sms = num_sms > 0 ? num_sms : 152;
-    // point chunks: fewest waves of one-CTA-per-SM tasks times items per
-    // task; nearest: lists over at most 4096 points each (longer chunks cut
-    // the epilogue's insertions but leave more parts whose list may miss a
-    // candidate, which the merge then screens whole), within 2 GB of lists
-    const int64_t ct_max = FAR ? Tp + 1 : 128;
-    const int64_t c_mem = std::max<int64_t>(1, (int64_t(2) << 30) / std::max<int64_t>(1, q * kParts * kTL * 8));
-    int64_t best_c = 0, best_ct = 0;
-    double best = 1e300;
-    for (int64_t c = 1; c <= std::max<int64_t>(1, std::min<int64_t>(Tp, 8192)); ++c) {
-        int64_t ct = div_up(Tp, c);
-        ct += ct & 1;
-        const int64_t cc = div_up(Tp, ct);
-        if (cc > c_mem && best_c) break;
-        const double cost = (double)div_up(Tq * cc, sms) * (double)(ct / 2 + 4) + (ct > ct_max ? 1e200 : 0.0);
-        if (cost < best) { best = cost; best_c = cc; best_ct = ct; }
-    }
-    if (Tq * best_c > INT32_MAX) {
-        set_error("k-distance: too many queries for one launch");
-        return MAPPER_EINVAL;
-    }
-    Buf cpart, cent, row_pt, tile_n, tile_cent, Ah, Al, rn2, rn, cv, ci, err;
+    // point chunks of a screen over `tiles` tiles: fewest waves of
+    // one-CTA-per-SM tasks times items per task, chunks of at most ct_max
+    // tiles and (lists) at most 2 GB of lists. Nearest, lists: at most 128
+    // tiles per chunk (longer chunks cut the epilogue's insertions but leave
+    // more parts whose list may miss a candidate, which the merge then
+    // screens whole).
+    auto pick_chunks = [&](int64_t tiles, int64_t ct_max, bool lists, int64_t* ct_out, int64_t* c_out,
+                           int64_t Tq = -1) {
+        if (Tq < 0) Tq = div_up(q, 128);
+        const int64_t c_mem =
+            lists ? std::max<int64_t>(1, (int64_t(2) << 30) / std::max<int64_t>(1, q * kParts * kTL * 8)) : INT64_MAX;
+        int64_t best_c = 0, best_ct = 0;
+        double best = 1e300;
+        for (int64_t c = 1; c <= std::max<int64_t>(1, std::min<int64_t>(tiles, 8192)); ++c) {
+            int64_t ct = div_up(tiles, c);
+            ct += ct & 1;
+            const int64_t cc = div_up(tiles, ct);
+            if (cc > c_mem && best_c) break;
+            const double cost = (double)div_up(Tq * cc, sms) * (double)(ct / 2 + 4) + (ct > ct_max ? 1e200 : 0.0);
+            if (cost < best) { best = cost; best_c = cc; best_ct = ct; }
+        }
+        *ct_out = best_ct;
+        *c_out = best_c;
+    };
+    const bool use_sample = sampled && Tp >= kSampleMinTiles;
+    // sampled: room behind the query tiles for the rows of the queries over
+    // capacity (the second append screen)
+    const int64_t R2 = use_sample ? R + Tq * 128 : R;
+    Buf cpart, cent, row_pt, tile_n, tile_cent, Ah, Al, rn2, rn, cv, ci, err, tau, cnt, ovf;
     KNN_TRY(cpart.alloc(sizeof(double) * (kCentRows / kCentGroup) * dp, s));
     KNN_TRY(cent.alloc(sizeof(float) * dp, s));
     KNN_TRY(row_pt.alloc(sizeof(int32_t) * R, s));
     KNN_TRY(tile_n.alloc(sizeof(int32_t) * T, s));
     KNN_TRY(tile_cent.alloc(sizeof(int32_t) * T, s));
-    KNN_TRY(Ah.alloc(sizeof(uint16_t) * (size_t)R * dp, s));
-    KNN_TRY(Al.alloc(sizeof(uint16_t) * (size_t)R * dp, s));
-    KNN_TRY(rn2.alloc(sizeof(float) * R, s));
+    KNN_TRY(Ah.alloc(sizeof(uint16_t) * (size_t)R2 * dp, s));
+    KNN_TRY(Al.alloc(sizeof(uint16_t) * (size_t)R2 * dp, s));
+    KNN_TRY(rn2.alloc(sizeof(float) * R2, s));
     KNN_TRY(rn.alloc(sizeof(float) * R, s));
-    const size_t nc = (size_t)q * best_c * kParts * kTL;
-    KNN_TRY(cv.alloc(sizeof(float) * nc, s));
-    KNN_TRY(ci.alloc(sizeof(int32_t) * nc, s));
-    KNN_TRY(err.alloc(sizeof(int), s));
-    KNN_TRY(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    KNN_TRY(err.alloc(sizeof(int) * 2, s));      // [0]: a wait gave up; [1]: queries over capacity
+    KNN_TRY(cudaMemsetAsync(err.p, 0, sizeof(int) * 2, s));
+    Buf st;
+    KNN_TRY(st.alloc(sizeof(unsigned long long) * 4, s));
+    KNN_TRY(cudaMemsetAsync(st.p, 0, sizeof(unsigned long long) * 4, s));
     sample_sum_kernel<<<dim3((unsigned)div_up(dp, 32), kCentRows / kCentGroup / 8), dim3(32, 8), 0, s>>>(
         X, n, d, ld, dp, cpart.as<double>());
     sample_centre_kernel<<<div_up(dp, 128), 128, 0, s>>>(cpart.as<double>(), n, dp, cent.as<float>());
@@ -705,31 +1002,317 @@ int knn_select_tc(const float* X, int64_t n, int32_t d, int64_t ld, const int32_
     note_launch(2);
     KNN_TRY(cudaGetLastError());
     KNN_TRY(centred_operands(X, ld, d, dp, row_pt.as<int32_t>(), tile_n.as<int32_t>(), tile_cent.as<int32_t>(),
-                             cent.as<float>(), T, Ah.p, Al.p, rn2.as<float>(), rn.as<float>(), s));
-    // error bound of s = |a|^2 + |b|^2 - 2 acc: the screen's constants, plus
-    // 4 units of the rounding of s in each term
+                             cent.as<float>(), T, Ah.p, Al.p, rn2.as<float>(), rn.as<float>(), s,
+                             screen_finite ? err.as<int>() : nullptr));
+    if (screen_finite) {
+        int h_bad = 0;
+        KNN_TRY(cudaMemcpyAsync(&h_bad, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        KNN_TRY(cudaStreamSynchronize(s));
+        if (h_bad) {
+            set_error("k-distance: a row holds NaN or Inf, or a norm beyond FP32");
+            return MAPPER_ENONFINITE;
+        }
+    }
+    // |s - d^2| <= E = A1f |a||b| + A2f (|a|^2 + |b|^2) + A3f for s = |a|^2 + |b|^2 -
+    // 2 acc (the screen's constants plus 4 units of the rounding of s per
+    // term); |a||b| <= (|a|^2 + |b|^2) (1 + 2^-12) / 2 for the rounded-up norms,
+    // so E <= K (|a|^2 + |b|^2) + A3f. The screen's keys (m, c2) are lower
+    // bounds of d^2 (FAR: -d^2) within 2^-20 (|a|^2 + |b|^2) of s -+ E; the
+    // merge's upper bounds add W = Kw (|a|^2 + |b|^2) + A3w to a key.
     double A1, A2, A3;
     tc_bound(3, dp, 0.0, &A1, &A2, &A3);
     const double v = std::ldexp(1.0, -24);
     const float A1f = std::nextafter((float)(A1 + 4.0 * v), INFINITY);
     const float A2f = std::nextafter((float)(A2 + 4.0 * v), INFINITY);
     const float A3f = std::nextafter((float)A3, INFINITY);
-    int rc = tc_knn_screen(Ah.p, Al.p, rn2.as<float>(), rn.as<float>(), tile_n.as<int32_t>(), Tp, q, dp,
-                           (int)best_ct, (int)best_c, FAR, A1f, A2f, A3f, cv.as<float>(), ci.as<int32_t>(),
-                           err.as<int>(), s);
-    if (rc) return rc;
-    knn_merge_abs_kernel<FAR><<<(unsigned)div_up(q, 8), 256, 0, s>>>(
-        X, d, ld, queries_dev, q, (int)(best_c * kParts), cv.as<float>(), ci.as<int32_t>(), k, rn2.as<float>(),
-        rn.as<float>(), Tp * 128, A1f, A2f, A3f, eta_lo, eta_hi, tiny, n, Tp, (int)best_ct,
-        d % 4 == 0 && ld % 4 == 0 && ((uintptr_t)X & 15) == 0, out_dev);
-    note_launch();
-    KNN_TRY(cudaGetLastError());
-    int h_err = 0;
-    KNN_TRY(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    auto round_up = [](double x) {
+        float f = (float)x;
+        if ((double)f < x) f = std::nextafter(f, INFINITY);
+        return f;
+    };
+    const float K = round_up(0.5 * (double)A1f * (1.0 + std::ldexp(1.0, -12)) + (double)A2f);
+    float m;
+    if (FAR) {
+        m = -round_up(1.0 + (double)K);
+    } else {
+        m = (float)(1.0 - (double)K);
+        if ((double)m > 1.0 - (double)K) m = std::nextafter(m, -INFINITY);
+    }
+    const float Kw = round_up(2.0 * (double)K + std::ldexp(1.0, -20));
+    const float A3w = round_up(2.0 * (double)A3f * (1.0 + std::ldexp(1.0, -20)) + std::ldexp(1.0, -147));
+    KnnScreen ks{};
+    ks.Ah = Ah.p;
+    ks.Al = Al.p;
+    ks.rn2 = rn2.as<float>();
+    ks.tile_n = tile_n.as<int32_t>();
+    ks.rows = R2;
+    ks.q_tile0 = Tp;
+    ks.q = q;
+    ks.dp = dp;
+    ks.m = m;
+    ks.c2 = FAR ? 2.f : -2.f;
+    ks.A3f = A3f;
+    ks.err = err.as<int>();
+    MergeArgs ma{};
+    ma.X = X;
+    ma.d = d;
+    ma.ld = ld;
+    ma.queries = queries_dev;
+    ma.q = q;
+    ma.k = k;
+    ma.rn2 = rn2.as<float>();
+    ma.q_row0 = Tp * 128;
+    ma.Kw = Kw;
+    ma.A3w = A3w;
+    ma.eta_lo = eta_lo;
+    ma.eta_hi = eta_hi;
+    ma.tiny = tiny;
+    ma.n = n;
+    ma.Tp = Tp;
+    ma.vec4 = d % 4 == 0 && ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
+    ma.out = out_dev;
+    ma.stats = st.as<unsigned long long>();
+    // list screen over `tiles` screened tiles (operand tile b * stride)
+    auto list_screen = [&](int64_t tiles, int64_t stride, int64_t ct_max) -> int {
+        int64_t ct = 0, c = 0;
+        pick_chunks(tiles, ct_max, true, &ct, &c);
+        if (Tq * c > INT32_MAX) {
+            set_error("k-distance: too many queries for one launch");
+            return MAPPER_EINVAL;
+        }
+        const size_t nc = (size_t)q * c * kParts * kTL;
+        KNN_TRY(cv.alloc(sizeof(float) * nc, s));
+        KNN_TRY(ci.alloc(sizeof(int32_t) * nc, s));
+        ks.n_tiles = tiles;
+        ks.tile_stride = stride;
+        ks.chunk_tiles = (int)ct;
+        ks.chunks = (int)c;
+        ks.tau = nullptr;
+        ks.cand_v = cv.as<float>();
+        ks.cand_i = ci.as<int32_t>();
+        ma.n_lists = (int)(c * kParts);
+        ma.chunk_tiles = (int)ct;
+        ma.cand_v = cv.as<float>();
+        ma.cand_i = ci.as<int32_t>();
+        return tc_knn_screen(ks, s);
+    };
+    const unsigned merge_grid = (unsigned)div_up(q, 8);
+    // the shared FP64 list of the first merge: up to 2 entries per query on
+    // average (queries beyond it settle their own)
+    Buf f64n, f64q, f64j, f64v, moff, mcnt, mk;
+    const int64_t f64_cap = 2 * q + 64;
+    KNN_TRY(f64n.alloc(sizeof(int), s));
+    KNN_TRY(f64q.alloc(sizeof(int32_t) * f64_cap, s));
+    KNN_TRY(f64j.alloc(sizeof(int32_t) * f64_cap, s));
+    KNN_TRY(f64v.alloc(sizeof(double) * f64_cap, s));
+    KNN_TRY(moff.alloc(sizeof(int64_t) * q, s));
+    KNN_TRY(mcnt.alloc(sizeof(int32_t) * q, s));
+    KNN_TRY(mk.alloc(sizeof(int32_t) * q, s));
+    KNN_TRY(cudaMemsetAsync(f64n.p, 0, sizeof(int), s));
+    KNN_TRY(cudaMemsetAsync(mcnt.p, 0xFF, sizeof(int32_t) * q, s));
+    ma.f64_n = f64n.as<int>();
+    ma.f64_cap = f64_cap;
+    ma.f64_q = f64q.as<int32_t>();
+    ma.f64_j = f64j.as<int32_t>();
+    ma.m_off = moff.as<int64_t>();
+    ma.m_cnt = mcnt.as<int32_t>();
+    ma.m_k = mk.as<int32_t>();
+    auto settle_f64 = [&]() -> int {
+        knn_fp64_kernel<<<(unsigned)div_up(f64_cap, 256), 256, 0, s>>>(X, d, ld, ma.vec4, queries_dev, f64n.as<int>(),
+                                                                       f64_cap, f64q.as<int32_t>(),
+                                                                       f64j.as<int32_t>(), f64v.as<double>());
+        knn_f64_select_kernel<FAR><<<(unsigned)div_up(q, 256), 256, 0, s>>>(
+            q, moff.as<int64_t>(), mcnt.as<int32_t>(), mk.as<int32_t>(), f64v.as<double>(), out_dev);
+        note_launch(2);
+        KNN_TRY(cudaGetLastError());
+        return MAPPER_OK;
+    };
+    int64_t cap = 0;
+    if (!use_sample) {
+        int rc = list_screen(Tp, 1, FAR ? Tp + 1 : 128);
+        if (rc) return rc;
+        knn_merge_tc_kernel<FAR, kLists><<<merge_grid, 256, 0, s>>>(ma);
+        note_launch();
+        KNN_TRY(cudaGetLastError());
+        if ((rc = settle_f64())) return rc;
+    } else {
+        const int64_t stride = Tp / kSampleTiles;
+        const int64_t ns = div_up(Tp, stride);
+        // (only U of the lists is used: chunks of any length)
+        int rc = list_screen(ns, stride, ns + 1);
+        if (rc) return rc;
+        KNN_TRY(tau.alloc(sizeof(float) * q, s));
+        ma.tau = tau.as<float>();
+        knn_merge_tc_kernel<FAR, kTau><<<merge_grid, 256, 0, s>>>(ma);
+        note_launch();
+        KNN_TRY(cudaGetLastError());
+        cv.release();
+        ci.release();
+        // expected keys below tau: about stride k; room for 16 times that,
+        // within 1 GB of entries
+        cap = 256;
+        while (cap < 16 * stride * k && cap < 8192) cap *= 2;
+        cap = std::max<int64_t>(64, std::min<int64_t>(cap, (int64_t(1) << 30) / std::max<int64_t>(1, q * 8)));
+        KNN_TRY(cv.alloc(sizeof(float) * (size_t)q * cap, s));
+        KNN_TRY(ci.alloc(sizeof(int32_t) * (size_t)q * cap, s));
+        KNN_TRY(cnt.alloc(sizeof(int) * q, s));
+        KNN_TRY(ovf.alloc(sizeof(int32_t) * q, s));
+        KNN_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int) * q, s));
+        int64_t ct = 0, c = 0;
+        pick_chunks(Tp, Tp + 1, false, &ct, &c);
+        if (Tq * c > INT32_MAX) {
+            set_error("k-distance: too many queries for one launch");
+            return MAPPER_EINVAL;
+        }
+        ks.n_tiles = Tp;
+        ks.tile_stride = 1;
+        ks.chunk_tiles = (int)ct;
+        ks.chunks = (int)c;
+        ks.tau = tau.as<float>();
+        ks.cap = (int)cap;
+        ks.count = cnt.as<int>();
+        ks.cand_v = cv.as<float>();
+        ks.cand_i = ci.as<int32_t>();
+        rc = tc_knn_screen(ks, s);
+        if (rc) return rc;
+        ma.cand_v = cv.as<float>();
+        ma.cand_i = ci.as<int32_t>();
+        ma.count = cnt.as<int>();
+        ma.cap = (int)cap;
+        ma.ovf_n = err.as<int>() + 1;
+        ma.ovf = ovf.as<int32_t>();
+        knn_merge_tc_kernel<FAR, kFlat><<<merge_grid, 256, 0, s>>>(ma);
+        note_launch();
+        KNN_TRY(cudaGetLastError());
+        if ((rc = settle_f64())) return rc;
+        ma.f64_n = nullptr;                      // the second merge settles its own
+    }
+    int h_err[2] = {0, 0};
+    unsigned long long h_st[4] = {0, 0, 0, 0};
+    KNN_TRY(cudaMemcpyAsync(h_err, err.p, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+    KNN_TRY(cudaMemcpyAsync(h_st, st.p, sizeof(h_st), cudaMemcpyDeviceToHost, s));
     KNN_TRY(cudaStreamSynchronize(s));
-    if (h_err) {
+    if (h_err[0]) {
         set_error("k-distance: the tensor-core screen gave up waiting on a barrier");
         return MAPPER_ETIMEOUT;
+    }
+    if (info) {
+        info[0] = use_sample ? 2 : 1;
+        info[1] = h_err[1];
+        info[2] = cap;
+        info[3] = use_sample ? Tp / kSampleTiles : 0;
+        info[4] = (int64_t)h_st[0];
+        info[5] = (int64_t)h_st[3];
+        info[6] = (int64_t)h_st[1];
+        info[7] = (int64_t)h_st[2];
+    }
+    if (h_err[1] > 0) {
+        // queries with more keys below tau than the capacity: exact room for
+        // each (its count), its operand row copied behind the query tiles,
+        // and a second append screen of those queries; the list screen when
+        // the room would pass 2^28 entries
+        const int64_t nq = h_err[1];
+        int* n_ovf = err.as<int>() + 1;
+        Buf sub_q, sub_out;
+        KNN_TRY(sub_q.alloc(sizeof(int32_t) * nq, s));
+        KNN_TRY(sub_out.alloc(sizeof(double) * nq, s));
+        knn_gather_kernel<<<(unsigned)div_up(nq, 256), 256, 0, s>>>(ovf.as<int32_t>(), n_ovf, queries_dev,
+                                                                     sub_q.as<int32_t>());
+        note_launch();
+        KNN_TRY(cudaGetLastError());
+        Buf scnt, off2, tau2;
+        KNN_TRY(scnt.alloc(sizeof(int32_t) * nq, s));
+        KNN_TRY(off2.alloc(sizeof(int64_t) * (nq + 1), s));
+        KNN_TRY(tau2.alloc(sizeof(float) * nq, s));
+        knn_ovf_gather_kernel<<<(unsigned)div_up(nq, 256), 256, 0, s>>>(ovf.as<int32_t>(), n_ovf, cnt.as<int>(),
+                                                                         tau.as<float>(), scnt.as<int32_t>(),
+                                                                         tau2.as<float>());
+        note_launch();
+        KNN_TRY(cudaGetLastError());
+        KNN_TRY(exclusive_scan_i32_to_i64(scnt.as<int32_t>(), off2.as<int64_t>(), nq, s));
+        int64_t total = 0;
+        KNN_TRY(cudaMemcpyAsync(&total, off2.as<int64_t>() + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        KNN_TRY(cudaStreamSynchronize(s));
+        if (total <= (int64_t(1) << 28)) {
+            const int64_t Tq2 = div_up(nq, 128);
+            knn_copy_rows_kernel<<<(unsigned)div_up(Tq2 * 128 * 32, 256), 256, 0, s>>>(
+                static_cast<uint16_t*>(Ah.p), static_cast<uint16_t*>(Al.p), rn2.as<float>(), dp, Tp * 128,
+                ovf.as<int32_t>(), n_ovf, R, Tq2 * 128);
+            note_launch();
+            KNN_TRY(cudaGetLastError());
+            Buf cnt2, cv2, ci2, err2, ovf2;
+            KNN_TRY(cnt2.alloc(sizeof(int) * nq, s));
+            KNN_TRY(cv2.alloc(sizeof(float) * std::max<int64_t>(1, total), s));
+            KNN_TRY(ci2.alloc(sizeof(int32_t) * std::max<int64_t>(1, total), s));
+            KNN_TRY(err2.alloc(sizeof(int), s));
+            KNN_TRY(ovf2.alloc(sizeof(int32_t) * nq, s));
+            KNN_TRY(cudaMemsetAsync(cnt2.p, 0, sizeof(int) * nq, s));
+            KNN_TRY(cudaMemsetAsync(err2.p, 0, sizeof(int), s));
+            int64_t ct = 0, c = 0;
+            pick_chunks(Tp, Tp + 1, false, &ct, &c, Tq2);
+            ks.q = nq;
+            ks.q_tile0 = Tp + Tq;
+            ks.n_tiles = Tp;
+            ks.tile_stride = 1;
+            ks.chunk_tiles = (int)ct;
+            ks.chunks = (int)c;
+            ks.tau = tau2.as<float>();
+            ks.cap = 0;
+            ks.off = off2.as<int64_t>();
+            ks.count = cnt2.as<int>();
+            ks.cand_v = cv2.as<float>();
+            ks.cand_i = ci2.as<int32_t>();
+            int rc = tc_knn_screen(ks, s);
+            if (rc) return rc;
+            ma.q = nq;
+            ma.queries = sub_q.as<int32_t>();
+            ma.q_row0 = R;
+            ma.cand_v = cv2.as<float>();
+            ma.cand_i = ci2.as<int32_t>();
+            ma.count = cnt2.as<int>();
+            ma.cap = 0;
+            ma.off = off2.as<int64_t>();
+            ma.ovf_n = err2.as<int>();
+            ma.ovf = ovf2.as<int32_t>();
+            ma.out = sub_out.as<double>();
+            knn_merge_tc_kernel<FAR, kFlat><<<(unsigned)div_up(nq, 8), 256, 0, s>>>(ma);
+            note_launch();
+            KNN_TRY(cudaGetLastError());
+            knn_scatter_kernel<<<(unsigned)div_up(nq, 256), 256, 0, s>>>(ovf.as<int32_t>(), n_ovf,
+                                                                          sub_out.as<double>(), out_dev);
+            note_launch();
+            KNN_TRY(cudaGetLastError());
+            int h2[2] = {0, 0};
+            KNN_TRY(cudaMemcpyAsync(h2, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+            KNN_TRY(cudaMemcpyAsync(h2 + 1, err2.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+            KNN_TRY(cudaMemcpyAsync(h_st, st.p, sizeof(h_st), cudaMemcpyDeviceToHost, s));
+            KNN_TRY(cudaStreamSynchronize(s));
+            if (h2[0]) {
+                set_error("k-distance: the tensor-core screen gave up waiting on a barrier");
+                return MAPPER_ETIMEOUT;
+            }
+            if (h2[1]) {                          // the same keys as in the first screen
+                set_error("k-distance: second screen found more keys than the first");
+                return MAPPER_EINTERNAL;
+            }
+            if (info) {
+                info[6] = (int64_t)h_st[1];
+                info[7] = (int64_t)h_st[2];
+            }
+        } else {
+            int64_t sub_info[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            const int rc = knn_select_tc<FAR>(X, n, d, ld, sub_q.as<int32_t>(), nq, k, sub_out.as<double>(),
+                                              num_sms, s, false, sub_info);
+            if (rc) return rc;
+            if (info) {
+                info[6] += sub_info[6];
+                info[7] += sub_info[7];
+            }
+            knn_scatter_kernel<<<(unsigned)div_up(nq, 256), 256, 0, s>>>(ovf.as<int32_t>(), n_ovf,
+                                                                          sub_out.as<double>(), out_dev);
+            note_launch();
+            KNN_TRY(cudaGetLastError());
+        }
     }
     return MAPPER_OK;
 }
@@ -800,16 +1383,22 @@ int knn_select(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* 
 
 }  // namespace
 
+bool knn_on_tensor_cores(int32_t k, bool tensor_cores) { return tensor_cores && k <= kKnnList; }
+
 int knn_distance(const float* X, int64_t n, int32_t d, int64_t ld, const int32_t* queries_dev, int64_t q,
-                 int32_t k, double* out_dev, int num_sms, bool tensor_cores, cudaStream_t s)
+                 int32_t k, double* out_dev, int num_sms, bool tensor_cores, cudaStream_t s, int64_t* info,
+                 bool sample, bool screen_finite)
 {
+    if (info)
+        for (int i = 0; i < 8; ++i) info[i] = 0;
     if (q == 0) return MAPPER_OK;
     if (k < 1 || k > kKMax || k > n) {
         set_error("k must be in [1, min(16, n)]");
         return MAPPER_EINVAL;
     }
-    return tensor_cores && k <= kKnnList ? knn_select_tc<false>(X, n, d, ld, queries_dev, q, k, out_dev, num_sms, s)
-                                         : knn_select<false>(X, n, d, ld, queries_dev, q, k, out_dev, num_sms, s);
+    return tensor_cores && k <= kKnnList
+               ? knn_select_tc<false>(X, n, d, ld, queries_dev, q, k, out_dev, num_sms, s, sample, info, screen_finite)
+               : knn_select<false>(X, n, d, ld, queries_dev, q, k, out_dev, num_sms, s);
 }
 
 // L-infinity centrality filter f(x) = max_y d(x, y): the L-infinity norm of

@@ -79,12 +79,17 @@ struct TcParams {
     const float4* tmax;                       // count pass: per tile largest |b|^2, |b|, |b - hi|
     const float* tn2min;                      // count pass: per tile smallest |b|^2 (valid rows)
     // k-distance screen (MODE 3): CTA t = (query tile t / kq_chunks, chunk t % kq_chunks)
-    // against point tiles chunk * kq_ct .. + kq_ct of the kq_tp point tiles; query
-    // tile u is operand tile kq_tp + u
-    int64_t kq_tp, kq_q;
-    int kq_ct, kq_chunks, kq_far;
-    float* kq_v;                              // lists: [((query * chunks + chunk) * 4 + part) * 16]
-    int32_t* kq_i;
+    // against screened point tiles chunk * kq_ct .. + kq_ct of kq_tp; screened
+    // tile b is operand tile b * kq_stride, query tile u operand tile kq_qt0 + u
+    int64_t kq_tp, kq_q, kq_stride, kq_qt0;
+    int kq_ct, kq_chunks;
+    float kq_m, kq_c2;                        // key = RD(RD(|a|^2 m - A3f) + RD(c2 acc + RD(|b|^2 m)))
+    const float* kq_tau;                      // append mode: keep every key <= tau[query]; else lists
+    int kq_cap;                               // append mode: entries per query
+    const int64_t* kq_off;                    // append mode, if set: query i's entries at off[i] .. off[i + 1]
+    int* kq_cnt;                              // append mode: keys found per query (may exceed kq_cap)
+    float* kq_v;                              // lists: [((query * chunks + chunk) * 4 + part) * kKnnL]
+    int32_t* kq_i;                            // append: [query * kq_cap + slot]
     float* dump;                              // MODE 4 (accumulation probe): [item][128][128] accumulators
 };
 
@@ -212,6 +217,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v)
@@ -515,7 +533,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
     auto item = [&](int64_t g) -> int3 {
         if (MODE == 3) {
             const int64_t b0 = kq_ch * P.kq_ct + 2 * g;
-            return make_int3((int)(P.kq_tp + kq_qt), (int)b0, b0 + 1 < kq_bhi ? (int)(b0 + 1) : -1);
+            return make_int3((int)(P.kq_qt0 + kq_qt), (int)(b0 * P.kq_stride),
+                             b0 + 1 < kq_bhi ? (int)((b0 + 1) * P.kq_stride) : -1);
         }
         const int2 grp = group_at(g);
         const int2 tp = A.pairs[grp.x];
@@ -679,71 +698,104 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
     } else if constexpr (MODE == 3) {
         // ------------------------------------- epilogue: k smallest distances
         // Warp w holds TMEM lane quadrant (w & 3) = query rows 32 (w & 3) ..
-        // +31 and the 32-column part (w - 2) / 4 of every point tile; each
-        // thread keeps, over its part of the chunk, the kKnnL smallest lower
-        // bounds key - E of its query row with their points, where key = s =
-        // |a|^2 + |b|^2 - 2 acc (FAR: -s) and E = A1 |a||b| + A2 (|a|^2 +
-        // |b|^2) + A3 bounds |s - d^2| for this pair of rows.
-        const int et = tid - 64;
+        // +31 (a row per lane) and the 32-column part (w - 2) >> 2 of every
+        // point tile, and works alone (no barrier across warps). For query
+        // row a and point b, key = RD(R + t) with R = RD(|a|^2 m - A3) and t =
+        // RD(c2 acc + C_b), C_b = RD(|b|^2 m), is a lower bound of d^2 (FAR:
+        // of -d^2; the host picks m, c2). A row keeps the keys below its
+        // limit T: list mode, the kKnnL smallest per part of the chunk (T =
+        // the list's last entry); append mode, every key <= tau[query] (T =
+        // the next float above tau). key < T implies t < RU(T - R) = thr, so
+        // values with t >= thr are dropped on the FMA result alone, 16 at a
+        // time.
+        const int ew = warp - 2;
         const int quad = warp & 3;
-        const int part = (warp - 2) >> 2;
+        const int part = ew >> 2;
         const int r = quad * 32 + lane;
         const int64_t qi = kq_qt * kT + r;
         const bool valid_r = qi < P.kq_q;
-        const float na2 = P.rn2[(P.kq_tp + kq_qt) * kT + r];
-        const float nra = P.rn[(P.kq_tp + kq_qt) * kT + r];
+        const bool append = P.kq_tau != nullptr;
+        const float c2 = P.kq_c2, m = P.kq_m;
+        const float R = __fmaf_rd(P.rn2[(P.kq_qt0 + kq_qt) * kT + r], m, -P.A3f);
+        float lim = INFINITY;                                 // append: largest key kept
+        if (append && valid_r) lim = P.kq_tau[qi];
+        const float t_app = lim < INFINITY ? nextafterf(lim, INFINITY) : INFINITY;
         float lv[kKnnL];
         int li[kKnnL];
 #pragma unroll
         for (int i = 0; i < kKnnL; ++i) { lv[i] = INFINITY; li[i] = -1; }
-        int it = 0, git = 0;
+        float thr = valid_r ? __fsub_ru(append ? t_app : INFINITY, R) : -INFINITY;
+        float* cst = S.wn[ew];                                // C_b of the warp's 32 columns
+        int git = 0;
         bool stop = false;
-        for (int64_t g = g_begin; g < g_end && !stop; g += g_step, ++git) {
+        for (int64_t g = g_begin; g < g_end; g += g_step, ++git) {
             const int3 itm = item(g);
             const int nbt = itm.z >= 0 ? 2 : 1;
-            for (int h = 0; h < nbt; ++h, ++it) {
-                const int tb = h ? itm.z : itm.y;
-                const int64_t sb = (int64_t)tb * kT;
-                const int buf = it & 1, tbuf = git & 1;
-                const uint32_t acc_phase = (uint32_t)((git >> 1) & 1);
-                // (1) |b|^2 of the pair's columns, (2) the accumulator; the
-                // barrier also publishes (1)
-                if (et < kT) {
-                    S.nbn[buf][et] = P.rn2[sb + et];
-                    S.nbr[buf][et] = P.rn[sb + et];
-                }
-                const bool bad = (h == 0 && !mbar_wait(&S.acc_full[tbuf], acc_phase, abort)) || *abort;
-                if (epi_sync_or(bad)) { stop = true; break; }
-                tc_fence_after();
-                const int nb = A.tile_n[tb];
-                // 8 columns at a time (a compact loop body: the insertion is
-                // rare but long)
+            const int tbuf = git & 1;
+            // the columns' C_b, loaded before the accumulator wait
+            float cj[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int tb = h ? (itm.z >= 0 ? itm.z : itm.y) : itm.y;
+                const int jc = part * 32 + lane;
+                cj[h] = jc < A.tile_n[tb] ? __fmul_rd(P.rn2[(int64_t)tb * kT + jc], m) : INFINITY;
+            }
+            const bool bad = !mbar_wait(&S.acc_full[tbuf], (uint32_t)((git >> 1) & 1), abort) || *abort;
+            if (__any_sync(0xffffffffu, bad)) { stop = true; break; }
+            tc_fence_after();
+            for (int h = 0; h < nbt; ++h) {
+                const int64_t sb = (int64_t)(h ? itm.z : itm.y) * kT;
+                __syncwarp();                                 // the previous tile's reads are done
+                cst[lane] = cj[h];
+                __syncwarp();
 #pragma unroll 1
-                for (int c8 = 0; c8 < 4; ++c8) {
-                    float v[8];
-                    tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) +
-                                 (uint32_t)(tbuf * kAccCols + h * kT + part * 32 + c8 * 8), v);
-                    if (c8 == 3 && h == nbt - 1) {
+                for (int c16 = 0; c16 < 2; ++c16) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) +
+                                  (uint32_t)(tbuf * kAccCols + h * kT + part * 32 + c16 * 16), v);
+                    if (c16 == 1 && h == nbt - 1) {
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&S.acc_empty[tbuf]);
                     }
-                    const int j0 = part * 32 + c8 * 8;
-                    const float* nb2 = S.nbn[buf] + j0;
-                    const float* nbr = S.nbr[buf] + j0;
+                    const float4* c4 = reinterpret_cast<const float4*>(cst + c16 * 16);
+                    float t[16];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const float sq = fmaf(-2.f, v[i], na2 + nb2[i]);
-                        const float E = __fmaf_ru(P.A1f, __fmul_ru(nra, nbr[i]),
-                                                  __fmaf_ru(P.A2f, __fadd_ru(na2, nb2[i]), P.A3f));
-                        const float key = __fsub_rd(P.kq_far ? -sq : sq, E);
-                        if (valid_r && j0 + i < nb && key < lv[kKnnL - 1])
-                            knn_insert(lv, li, key, (int)(sb + j0 + i));
+                    for (int i4 = 0; i4 < 4; ++i4) {
+                        const float4 cc = c4[i4];
+                        t[4 * i4 + 0] = __fmaf_rd(c2, v[4 * i4 + 0], cc.x);
+                        t[4 * i4 + 1] = __fmaf_rd(c2, v[4 * i4 + 1], cc.y);
+                        t[4 * i4 + 2] = __fmaf_rd(c2, v[4 * i4 + 2], cc.z);
+                        t[4 * i4 + 3] = __fmaf_rd(c2, v[4 * i4 + 3], cc.w);
+                    }
+                    float tmin = fmin3(t[0], t[1], t[2]);
+#pragma unroll
+                    for (int i = 3; i + 1 < 16; i += 2) tmin = fmin3(tmin, t[i], t[i + 1]);
+                    tmin = fminf(tmin, t[15]);
+                    if (!__any_sync(0xffffffffu, tmin < thr)) continue;
+                    const int j0 = (int)sb + part * 32 + c16 * 16;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        if (!(t[i] < thr)) continue;
+                        const float key = __fadd_rd(R, t[i]);
+                        if (append) {
+                            if (key < t_app) {
+                                const int slot = atomicAdd(&P.kq_cnt[qi], 1);
+                                const int64_t base = P.kq_off ? P.kq_off[qi] : qi * P.kq_cap;
+                                if (slot < (P.kq_off ? P.kq_off[qi + 1] - base : (int64_t)P.kq_cap)) {
+                                    P.kq_v[base + slot] = key;
+                                    P.kq_i[base + slot] = j0 + i;
+                                }
+                            }
+                        } else if (key < lv[kKnnL - 1]) {
+                            knn_insert(lv, li, key, j0 + i);
+                            thr = __fsub_ru(lv[kKnnL - 1], R);
+                        }
                     }
                 }
             }
         }
-        if (!stop && valid_r) {
+        if (!stop && valid_r && !append) {
             const int64_t base = ((qi * P.kq_chunks + kq_ch) * 4 + part) * kKnnL;
 #pragma unroll
             for (int i = 0; i < kKnnL; ++i) {
@@ -2116,41 +2168,43 @@ int tc_wait_selftest(cudaStream_t s)
     return MAPPER_EINTERNAL;
 }
 
-int tc_knn_screen(const void* Ah, const void* Al, const float* rn2, const float* rn, const int32_t* tile_n,
-                  int64_t Tp, int64_t q, int dp, int chunk_tiles, int chunks, bool far, float A1f, float A2f,
-                  float A3f, float* cand_v, int32_t* cand_i, int* err, cudaStream_t s)
+int tc_knn_screen(const KnnScreen& k, cudaStream_t s)
 {
-    if (q == 0 || Tp == 0) return MAPPER_OK;
-    const int64_t Tq = (q + kT - 1) / kT;
-    const int64_t R = (Tp + Tq) * kT;
-    if (R >= (int64_t(1) << 30) || chunk_tiles < 2 || (chunk_tiles & 1) || chunks < 1 ||
-        Tq * chunks > INT32_MAX) {
+    if (k.q == 0 || k.n_tiles == 0) return MAPPER_OK;
+    const int64_t Tq = (k.q + kT - 1) / kT;
+    if (k.rows >= (int64_t(1) << 30) || k.chunk_tiles < 2 || (k.chunk_tiles & 1) || k.chunks < 1 ||
+        Tq * k.chunks > INT32_MAX || k.tile_stride < 1 || (k.n_tiles - 1) * k.tile_stride >= k.q_tile0 ||
+        (k.q_tile0 + Tq) * kT > k.rows || (k.tau && ((k.cap < 1 && !k.off) || !k.count))) {
         set_error("k-distance tensor-core screen: sizes out of range");
         return MAPPER_EINVAL;
     }
     CUtensorMap mh, ml;
-    if (!make_map(&mh, Ah, R, dp) || !make_map(&ml, Al, R, dp)) {
+    if (!make_map(&mh, k.Ah, k.rows, k.dp) || !make_map(&ml, k.Al, k.rows, k.dp)) {
         set_error("cuTensorMapEncodeTiled failed (or is unavailable)");
         return MAPPER_ECUDA;
     }
     TcParams p{};
-    p.A.tile_n = tile_n;
-    p.A.dp = dp;
-    p.rn2 = rn2;
-    p.rn = rn;
-    p.nkb = (dp + kKB - 1) / kKB;
-    p.err = err;
-    p.A1f = A1f;
-    p.A2f = A2f;
-    p.A3f = A3f;
-    p.kq_tp = Tp;
-    p.kq_q = q;
-    p.kq_ct = chunk_tiles;
-    p.kq_chunks = chunks;
-    p.kq_far = far ? 1 : 0;
-    p.kq_v = cand_v;
-    p.kq_i = cand_i;
-    const cudaError_t e = launch<3, 3, 2>(mh, ml, p, (int)(Tq * chunks), s);
+    p.A.tile_n = k.tile_n;
+    p.A.dp = k.dp;
+    p.rn2 = k.rn2;
+    p.nkb = (k.dp + kKB - 1) / kKB;
+    p.err = k.err;
+    p.A3f = k.A3f;
+    p.kq_tp = k.n_tiles;
+    p.kq_stride = k.tile_stride;
+    p.kq_qt0 = k.q_tile0;
+    p.kq_q = k.q;
+    p.kq_ct = k.chunk_tiles;
+    p.kq_chunks = k.chunks;
+    p.kq_m = k.m;
+    p.kq_c2 = k.c2;
+    p.kq_tau = k.tau;
+    p.kq_cap = k.cap;
+    p.kq_off = k.off;
+    p.kq_cnt = k.count;
+    p.kq_v = k.cand_v;
+    p.kq_i = k.cand_i;
+    const cudaError_t e = launch<3, 3, 2>(mh, ml, p, (int)(Tq * k.chunks), s);
     note_launch();
     if (e != cudaSuccess) {
         set_error(std::string("k-distance tensor-core screen: ") + cudaGetErrorString(e));

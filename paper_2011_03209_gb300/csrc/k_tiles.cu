@@ -505,7 +505,8 @@ __global__ void __launch_bounds__(256) operand_kernel(const float* __restrict__ 
                                                       __nv_bfloat16* __restrict__ Al,
                                                       float* __restrict__ rn2, float* __restrict__ rn,
                                                       float* __restrict__ rl, float4* __restrict__ tmax,
-                                                      float* __restrict__ tn2min, float norm_infl)
+                                                      float* __restrict__ tn2min, float norm_infl,
+                                                      int* __restrict__ nonfinite = nullptr)
 {
     const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ unsigned smax[4];                          // non-negative floats compare as their bits
@@ -563,6 +564,8 @@ __global__ void __launch_bounds__(256) operand_kernel(const float* __restrict__ 
             s += __shfl_xor_sync(0xffffffffu, s, o);
             sr += __shfl_xor_sync(0xffffffffu, sr, o);
         }
+        // a NaN or Inf in the row (or |row - c|^2 beyond FLT_MAX) leaves s non-finite
+        if (nonfinite && lane == 0 && valid && !(s <= FLT_MAX)) *nonfinite = 1;
         if (lane == 0) {
             const float n1 = __fmul_ru(__fsqrt_ru(s), norm_infl), l1 = __fmul_ru(__fsqrt_ru(sr), norm_infl);
             rn2[row] = s;
@@ -1116,14 +1119,14 @@ int fp8_operands(TileLayout* L, const float* X, int64_t ld, int d, int dp, cudaS
 
 cudaError_t centred_operands(const float* X, int64_t ld, int d, int dp, const int32_t* row_pt, const int32_t* tile_n,
                              const int32_t* tile_cent, const float* cents, int64_t T, void* Ah, void* Al, float* rn2,
-                             float* rn, cudaStream_t s)
+                             float* rn, cudaStream_t s, int* nonfinite)
 {
     if (T == 0) return cudaSuccess;
     const float norm_infl = 1.0f + (float)(dp / 32 + 16) * 5.9604645e-8f;
     const bool xvec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
     operand_kernel<<<(unsigned)T, 256, 0, s>>>(nullptr, X, ld, xvec, row_pt, d, dp, tile_n, tile_cent, cents,
                                                static_cast<__nv_bfloat16*>(Ah), static_cast<__nv_bfloat16*>(Al), rn2,
-                                               rn, nullptr, nullptr, nullptr, norm_infl);
+                                               rn, nullptr, nullptr, nullptr, norm_infl, nonfinite);
     note_launch();
     return cudaGetLastError();
 }

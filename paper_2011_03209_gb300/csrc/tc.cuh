@@ -76,20 +76,43 @@ int assign_pivots_tc(const float* X, int64_t n, int d, int64_t ld, int dp, const
 // Entries per list of the k-distance tensor-core screen (k <= this).
 constexpr int kKnnList = 8;
 
-// k-distance screen on tensor cores: operand rows 0 .. 128 Tp are the points
-// (row = point index, tile_n marking the valid rows), rows 128 Tp .. the q
-// queries in order; all centred on one centre and split into BF16 hi + lo.
-// CTA (query tile u, chunk c) screens query tile u against point tiles
-// c chunk_tiles .. (c + 1) chunk_tiles - 1 (three products, N = 256 items of
-// two point tiles) and writes, per query row and 32-column part, the
-// kKnnList smallest lower bounds key - E of key = s = |a|^2 + |b|^2 - 2 acc
-// (FAR: -s), E = A1f |a||b| + A2f (|a|^2 + |b|^2) + A3f (rounded up), with
-// their points: cand_v / cand_i[((query * chunks + c) * 4 + part) * kKnnList
-// + i]. *err = 1 if a
-// bounded wait ran out. Returns a mapper_status.
-int tc_knn_screen(const void* Ah, const void* Al, const float* rn2, const float* rn, const int32_t* tile_n,
-                  int64_t Tp, int64_t q, int dp, int chunk_tiles, int chunks, bool far, float A1f, float A2f,
-                  float A3f, float* cand_v, int32_t* cand_i, int* err, cudaStream_t s);
+// k-distance screen on tensor cores. Operand rows (BF16 hi + lo of the rows
+// centred on one centre, |row|^2 in rn2) hold the points in order (row =
+// point index, tile_n marking the valid rows of each 128-row tile), then the
+// q queries from tile q_tile0 on. CTA (query tile u, chunk c) screens query
+// tile u against screened point tiles c chunk_tiles .. (c + 1) chunk_tiles - 1
+// of n_tiles (screened tile b = operand tile b tile_stride), three products
+// per tile pair. For query row a and point b the screen's key
+//   key = RD(RD(|a|^2 m - A3f) + RD(c2 acc + RD(|b|^2 m)))
+// is a lower bound of d^2 (FAR: of -d^2) when the host sets m = RD(1 - K),
+// c2 = -2 (FAR: m = -RU(1 + K), c2 = 2), with K (|a|^2 + |b|^2) + A3f a bound of
+// the error of |a|^2 + |b|^2 - 2 acc.
+//   List mode (tau null): per query row and 32-column part of the chunk, the
+//   kKnnList smallest keys with their points, cand_v / cand_i[((query *
+//   chunks + c) * 4 + part) * kKnnList + i], ascending, padded with +inf / -1.
+//   Append mode: every key <= tau[query] with its point at cand_v / cand_i[query
+//   * cap + slot], slot < count[query] (count, zeroed by the caller, counts
+//   every such key, also those beyond cap); with off set, at off[query] + slot,
+//   slot < off[query + 1] - off[query].
+// *err = 1 if a bounded wait ran out. Returns a mapper_status.
+struct KnnScreen {
+    const void* Ah;
+    const void* Al;
+    const float* rn2;
+    const int32_t* tile_n;
+    int64_t rows;                 // operand rows (a multiple of 128)
+    int64_t n_tiles, tile_stride, q_tile0, q;
+    int dp, chunk_tiles, chunks;
+    float m, c2, A3f;
+    const float* tau;
+    int cap;
+    const int64_t* off;
+    int* count;
+    float* cand_v;
+    int32_t* cand_i;
+    int* err;
+};
+int tc_knn_screen(const KnnScreen& k, cudaStream_t s);
 
 // Accumulation probe: random BF16 rows (values 2^-4 .. 2^5 in magnitude,
 // random signs) through the screen's tcgen05 path (ns products, row pitch

@@ -13,12 +13,14 @@ mg = pytest.importorskip("paper_2011_03209_gb300")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module", params=[1, 2], ids=["tensor-cores", "cuda-cores"])
+@pytest.fixture(scope="module", params=[1, 3, 2], ids=["tensor-cores", "tensor-lists", "cuda-cores"])
 def ctx(request):
-    """Every test runs with both screens: BF16 tensor-core products (three per
-    tile pair) and the FP32 CUDA-core sums."""
+    """Every test runs with each screen: BF16 tensor-core products (three per
+    tile pair; large clouds with a threshold per query from a sample of the
+    points, or with per-part lists only) and the FP32 CUDA-core sums."""
     c = mg.Context(0)
     c.set_knn_screen(request.param)
+    c.knn_mode = request.param
     yield c
     c.close()
 
@@ -82,6 +84,18 @@ def test_knn_distance_rejects_bad_input(ctx):
         mg.mapper_knn_distance(ctx, torch.from_numpy(Y).to("cuda:0"), [0], 3)
 
 
+def test_knn_distance_huge_finite_rows(ctx):
+    """Finite rows whose squared norms pass FP32 (values near 1e20): the
+    tensor-core path flags them while building its operands and the call
+    falls back to the CUDA-core screen; still exact."""
+    X = synth.tiny_random(300, 6, 21, scale=2.0)
+    X[::37] *= np.float32(3e19)
+    q = np.arange(0, 300, 3, dtype=np.int32)
+    for k in (1, 4):
+        got = mg.mapper_knn_distance(ctx, torch.from_numpy(X).to("cuda:0"), q, k)
+        assert np.array_equal(got, oracle.knn_distance(X, q, k))
+
+
 @pytest.mark.parametrize("k", [1, 5, 16])
 def test_knn_distance_many_chunks(ctx, k):
     """150k points: the screen splits the points into many chunks per query
@@ -92,6 +106,51 @@ def test_knn_distance_many_chunks(ctx, k):
     q = rng.integers(0, X.shape[0], size=200).astype(np.int32)
     got = mg.mapper_knn_distance(ctx, torch.from_numpy(X).to("cuda:0"), q, k)
     assert np.array_equal(got, oracle.knn_distance(X, q, k))
+    info = ctx.knn_info()
+    if ctx.knn_mode == 1 and k <= 8:
+        # 1172 point tiles: the sampled threshold, no query over capacity
+        assert info["path"] == 2 and info["sample_stride"] == 4 and info["over_capacity"] == 0, info
+    else:
+        assert info["path"] == (0 if ctx.knn_mode == 2 or k > 8 else 1), info
+
+
+def _near_duplicate_clusters(n_centres, copies, d, jitter, seed):
+    rng = np.random.default_rng(seed)
+    C = rng.uniform(-5.0, 5.0, size=(n_centres, d))
+    X = np.repeat(C, copies, axis=0) + rng.normal(0.0, jitter, size=(n_centres * copies, d))
+    return X[rng.permutation(len(X))].astype(np.float32)
+
+
+@pytest.mark.parametrize("k", [1, 5, 8])
+def test_knn_distance_sampled_threshold_over_capacity(ctx, k):
+    """80,000 points in 40 tight clusters of 2000 (spread 0.01 against centres
+    10 apart): every point of a query's cluster is within the screen's error
+    band of its k-th neighbour, far more keys below the sampled threshold than
+    the capacity, so those queries go through the list screen; exact all
+    the same."""
+    X = _near_duplicate_clusters(40, 2000, 32, 0.01, seed=101 + k)
+    q = np.random.default_rng(k).integers(0, X.shape[0], size=300).astype(np.int32)
+    got = mg.mapper_knn_distance(ctx, torch.from_numpy(X).to("cuda:0"), q, k)
+    assert np.array_equal(got, oracle.knn_distance(X, q, k))
+    if ctx.knn_mode == 1:
+        info = ctx.knn_info()
+        assert info["path"] == 2 and info["over_capacity"] > 0, info
+
+
+def test_ecc_inf_lens_sampled_threshold():
+    """The L-infinity centrality (the largest distance, the k = 1 farthest
+    screen) of 70,000 points: 68,000 from a Gaussian mixture and 2000 tight
+    copies of a far point, so for most rows the farthest keys crowd the
+    threshold beyond the capacity; sampled rows equal the oracle's."""
+    rng = np.random.default_rng(103)
+    G = synth.gaussian_mixture(68_000, 8, 5, seed=104, centre_box=3.0, std_lo=0.3, std_hi=1.0, anisotropic=True)
+    far = np.full(8, 40.0) + rng.normal(0.0, 1e-3, size=(2000, 8))
+    X = np.concatenate([G, far.astype(np.float32)])[rng.permutation(70_000)].astype(np.float32)
+    rows = np.sort(rng.choice(70_000, size=48, replace=False)).astype(np.int32)
+    with mg.Context(0) as c:
+        f, _ = mg.mapper_lens(c, torch.from_numpy(X).to("cuda:0"), (mg.LENS_ECC_INF,), (0,))
+        got = f.cpu().numpy()[:, 0]
+    assert np.array_equal(got[rows], oracle.knn_distance(X, rows, X.shape[0]))
 
 
 def test_knn_distance_strided_rows_and_ties(ctx):
@@ -121,7 +180,7 @@ def test_knn_distance_wide_rows(ctx):
 
 def test_knn_screen_rejects_bad_mode():
     with mg.Context(0) as c:
-        for mode in (-1, 3):
+        for mode in (-1, 4):
             with pytest.raises(mg.MapperError):
                 c.set_knn_screen(mode)
 
