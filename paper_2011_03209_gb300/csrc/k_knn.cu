@@ -13,11 +13,12 @@
 //
 // Tensor cores (k <= 8, knn_select_tc): rows centred on a sampled mean and
 // split into BF16 hi + lo, three products per tile pair in the count pass's
-// kernel (tc_kernel, MODE 3), whose epilogue keeps per query row and 32-point
-// part of each chunk the 8 smallest lower bounds s - E of the squared
-// distance (E bounds the screen's error for that pair of rows);
-// knn_merge_abs_kernel settles each query from those lists (its comment gives
-// the argument).
+// kernel (tc_kernel, MODE 3), whose epilogue forms lower bounds (keys) of the
+// squared distances. On large clouds a screen of a sample of the point tiles
+// bounds each query's k-th key (tau), a screen of all points keeps every key
+// <= tau, and knn_merge_tc_kernel settles the query from those; small clouds
+// keep per query row and 32-point part of each chunk the 8 smallest keys
+// instead. knn_select_tc and knn_merge_tc_kernel give the arguments.
 //
 // CUDA cores (knn_select): FP32 squared distances (FMA sum of squared
 // differences, relative error at most eta = 1.5 (d + 4) 2^-24 plus a
