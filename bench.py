@@ -383,7 +383,7 @@ def run_ours(args):
                                         "tile_pairs_simt", "union_pairs", "union_skipped", "pairs_screened",
                                         "band_pairs", "fp64_pairs", "near_ties", "n_core", "n_nodes", "n_edges",
                                         "pass1_tile_n", "tile_pairs_cross") + tuple(
-                                            k for k in ("tile_pairs_screen1", "tile_pairs_redo") if k in st)},
+                                            k for k in ("tile_pairs_screen1", "tile_pairs_redo", "redo_blocks", "redo_parts") if k in st)},
         "ms_tiles": float(np.mean([s["ms_tiles"] for s in stats])),
         "roofline": roof,
         "clocks": clocks,
@@ -812,10 +812,11 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="clusters workload: skip the FP32 arm, the small configurations, the sweep and the "
                          "serving sub-objects (profiling runs)")
-    ap.add_argument("--screen", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--screen", type=int, default=0, choices=[0, 1, 2, 3],
                     help="clusters workload, BF16: pass-1 screen (0: the library default, 1: one product "
                          "first and three products for the tile pairs whose band is not empty, 2: three "
-                         "products everywhere)")
+                         "products everywhere, 3: as 1, the first phase deferring every block its rows' "
+                         "extremes do not decide)")
     ap.add_argument("--workload", default="clusters", choices=["clusters", "serving", "sweep", "sharded", "knn"],
                     help="clusters: the 1M x 256 graph (default; N ranks = N replicas); serving: the "
                          "request mix; sweep: 16 graphs of the 500k x 128 2D-lens cloud; sharded: the "

@@ -189,6 +189,14 @@ typedef struct mapper_stats {
                                     with one product (hi.hi); 0 when every pair took three */
     int64_t tile_pairs_redo;     /* ... of them, the tile pairs with a pair inside the
                                     one-product band, screened again with three products */
+    int64_t redo_blocks;         /* ... the 32 x 32 blocks of those pairs that hold one */
+    int64_t redo_parts;          /* ... the 32-column parts of those pairs holding such a block */
+    int64_t pass1_phases;        /* phases of the tensor-core count pass: 2 (a first screen, then
+                                    three products for its deferred blocks) or 1 (three products);
+                                    0 off the tensor cores */
+    double pass1_sample_deferred; /* pass-1 screen 0: the fraction of a sample of the tile pairs
+                                     whose first screen deferred a block (one phase above 0.35);
+                                     -1 when no sample ran */
 } mapper_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -213,12 +221,16 @@ int mapper_set_timing(mapper_ctx* ctx, int enabled);
  * MAPPER_EINVAL. */
 int mapper_set_pass1_tile_n(mapper_ctx* ctx, int tile_n);
 /* Count-pass screen of MAPPER_BF16 and MAPPER_FP8 (a tuning knob; results do
- * not depend on it): 0 = the default (1), 1 = two phases: every tile pair
+ * not depend on it): 0 = the default: per call, the first screen of mode 3
+ * on every 64th tile pair decides (two phases of mode 3 unless more than 35 %
+ * of those pairs defer a block, then one phase), 1 = two phases: every tile pair
  * first with one BF16 product (hi.hi, the band of MAPPER_BF16X1), or three
  * FP8 products; each 32 x 32 block of a tile pair that has a pair inside
  * that band is counted by a second pass with three BF16 products, the others
  * are final after the first, 2 = one phase: three products (BF16, or FP8
- * with its band re-decided in FP64) for every tile pair. Other values:
+ * with its band re-decided in FP64) for every tile pair, 3 = two phases where
+ * the first defers every block with a row that its extremes do not decide
+ * (all in or all out) without screening its values. Other values:
  * MAPPER_EINVAL. */
 int mapper_set_pass1_screen(mapper_ctx* ctx, int mode);
 /* Where the BF16 precisions screen mixed tile pairs across two segments of

@@ -99,6 +99,10 @@ class MapperStats(ctypes.Structure):
         ("tile_pairs_cross", ctypes.c_int64),
         ("tile_pairs_screen1", ctypes.c_int64),
         ("tile_pairs_redo", ctypes.c_int64),
+        ("redo_blocks", ctypes.c_int64),
+        ("redo_parts", ctypes.c_int64),
+        ("pass1_phases", ctypes.c_int64),
+        ("pass1_sample_deferred", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:

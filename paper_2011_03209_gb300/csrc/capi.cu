@@ -79,7 +79,9 @@ struct mapper_ctx {
                                                // 3 tensor-core lists only
     int64_t knn_info[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // the last k-distance call's path (mapper_knn_info)
     int64_t band_cap = 0;                      // band-queue entries (0: sized from the tile pairs)
-    int screen_mode = 0;                       // MAPPER_BF16 count pass: 0/1 two phases, 2 three products
+    int screen_mode = 0;                       // MAPPER_BF16 count pass: 0 one or two phases from a sample,
+                                               // 1 two phases, 2 three products, 3 two phases deferring
+                                               // every mixed block
 };
 
 struct mapper_cover_t {
@@ -296,6 +298,75 @@ int run_cover(mapper_ctx* ctx, const double* lens, int64_t n, int32_t m, const i
     return MAPPER_OK;
 }
 
+// Count-pass phases, decided per call (pass-1 screen 0): the first phase
+// (one BF16 product, or three FP8 ones, deferring every 32 x 32 block whose
+// rows' extremes leave a row undecided) runs on every stride-th pair of the
+// tensor-core list into scratch outputs; with f the fraction of those pairs
+// that defer a block, two phases cost about T1 + f T3 and one phase T3 (T1,
+// T3: the one- and three-product passes over the list; T1 ~ 0.6 T3 at d =
+// 256), so a call takes one phase when f exceeds kDeferMax. Lists shorter
+// than kSampleMinPairs keep two phases.
+constexpr double kDeferMax = 0.35;
+constexpr int64_t kSampleMinPairs = 8192;
+
+int sample_deferral(const mapper_ctx* ctx, const PassArgs& a, const TcArgs& first, int64_t n_pairs, int64_t R,
+                    int cap, cudaStream_t s, double* frac)
+{
+    (void)ctx;
+    const int64_t n_s = std::min<int64_t>(std::max<int64_t>(n_pairs / 64, 2048), n_pairs);
+    const int64_t stride = n_pairs / n_s;
+    Buf sp, cnt, nbr, hit, q, qn, st, err, mask;
+    CK(sp.alloc(sizeof(int2) * n_s, s), "alloc");
+    CK(cnt.alloc(sizeof(int32_t) * R, s), "alloc");
+    if (cap) CK(nbr.alloc(sizeof(int32_t) * (size_t)R * cap, s), "alloc");
+    CK(hit.alloc(n_s, s), "alloc");
+    CK(q.alloc(sizeof(uint2) * 1024, s), "alloc");
+    CK(qn.alloc(sizeof(unsigned long long), s), "alloc");
+    CK(st.alloc(sizeof(unsigned long long) * kStatCount, s), "alloc");
+    CK(err.alloc(sizeof(int), s), "alloc");
+    CK(mask.alloc(sizeof(uint32_t) * n_s, s), "alloc");
+    CK(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * R, s), "memset");
+    if (cap) CK(cudaMemsetAsync(nbr.p, 0xff, sizeof(int32_t) * (size_t)R * cap, s), "memset");
+    CK(cudaMemsetAsync(hit.p, 0, n_s, s), "memset");
+    CK(cudaMemsetAsync(qn.p, 0, sizeof(unsigned long long), s), "memset");
+    CK(cudaMemsetAsync(st.p, 0, sizeof(unsigned long long) * kStatCount, s), "memset");
+    CK(cudaMemsetAsync(err.p, 0, sizeof(int), s), "memset");
+    CK(cudaMemsetAsync(mask.p, 0, sizeof(uint32_t) * n_s, s), "memset");
+    int rc = tc_sample_pairs(a.pairs, stride, n_s, sp.as<int2>(), s);
+    if (rc) return rc;
+    PassArgs as = a;
+    as.pairs = sp.as<int2>();
+    as.count = cnt.as<int32_t>();
+    as.nbr = nbr.as<int32_t>();
+    as.pair_hit = hit.as<uint8_t>();
+    as.stats = st.as<unsigned long long>();
+    TcArgs ts = first;
+    if (!ts.f8) ts.ns = 1;
+    ts.defer = true;
+    ts.defer_mixed = true;
+    ts.redo_mask = mask.as<uint32_t>();
+    ts.sub_mask = nullptr;
+    ts.sub_q = nullptr;
+    ts.queue = q.as<uint2>();
+    ts.queue_n = qn.as<unsigned long long>();
+    ts.queue_cap = 1024;
+    ts.err = err.as<int>();
+    ts.groups = nullptr;
+    ts.groups_dev = nullptr;
+    ts.n_dev = nullptr;
+    ts.ev_begin = ts.ev_end = nullptr;
+    if ((rc = tc_pass(1, as, ts, n_s, s))) return rc;
+    unsigned long long h_redo = 0;
+    int h_err = 0;
+    CK(cudaMemcpyAsync(&h_redo, st.as<unsigned long long>() + kStatRedo, sizeof(h_redo), cudaMemcpyDeviceToHost, s),
+       "copy");
+    CK(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    if (h_err) return fail(MAPPER_ETIMEOUT, "a tensor-core pass gave up waiting on a barrier (phase sample)");
+    *frac = (double)h_redo / (double)n_s;
+    return MAPPER_OK;
+}
+
 // Pass-1 autotuner. The tensor-core count kernel runs its tile pairs as work
 // items of one pair (an M = 128, N = 128 product) or of two pairs sharing
 // tile A (N = 256, tile A loaded once); which is faster depends on the row
@@ -320,8 +391,9 @@ int tune_pass1(mapper_ctx* ctx, const PassArgs& a, const TcArgs& t, int64_t n_pa
     const int64_t n_t = std::min<int64_t>(n_pairs, (int64_t)ctx->num_sms * 32);
     if (n_t < (int64_t)ctx->num_sms * 8) return MAPPER_OK;
     const unsigned long long qcap = 1ull << 20;
-    Buf cnt, nbr, hit, q, qn, st, err, grp, gpos;
+    Buf cnt, nbr, hit, q, qn, st, err, grp, gpos, mask;
     CK(cnt.alloc(sizeof(int32_t) * R, s), "alloc");
+    if (t.defer) CK(mask.alloc(sizeof(uint32_t) * n_t, s), "alloc");
     if (cap) CK(nbr.alloc(sizeof(int32_t) * (size_t)R * cap, s), "alloc");
     CK(hit.alloc(n_t, s), "alloc");
     CK(q.alloc(sizeof(uint2) * qcap, s), "alloc");
@@ -342,20 +414,27 @@ int tune_pass1(mapper_ctx* ctx, const PassArgs& a, const TcArgs& t, int64_t n_pa
     ts.groups = nullptr;
     ts.groups_dev = nullptr;
     ts.n_dev = nullptr;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    ts.redo_mask = mask.as<uint32_t>();
+    ts.sub_mask = nullptr;
+    ts.sub_q = nullptr;
+    // each shape twice, alternating; the faster of each counts
+    constexpr int kRuns = 4;
+    cudaEvent_t ev[2 * kRuns] = {};
     struct Guard {
         cudaEvent_t* e;
-        ~Guard() { for (int i = 0; i < 4; ++i) if (e[i]) cudaEventDestroy(e[i]); }
+        ~Guard() { for (int i = 0; i < 2 * kRuns; ++i) if (e[i]) cudaEventDestroy(e[i]); }
     } guard{ev};
-    for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&ev[i]), "event");
-    for (int v = 0; v < 2; ++v) {
+    for (int i = 0; i < 2 * kRuns; ++i) CK(cudaEventCreate(&ev[i]), "event");
+    for (int run = 0; run < kRuns; ++run) {
+        const int v = run & 1;
         CK(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * R, s), "memset");
         if (cap) CK(cudaMemsetAsync(nbr.p, 0xff, sizeof(int32_t) * (size_t)R * cap, s), "memset");
         CK(cudaMemsetAsync(hit.p, 0, n_t, s), "memset");
         CK(cudaMemsetAsync(st.p, 0, sizeof(unsigned long long) * kStatCount, s), "memset");
+        if (t.defer) CK(cudaMemsetAsync(mask.p, 0, sizeof(uint32_t) * n_t, s), "memset");
         TcArgs tv = ts;
-        tv.ev_begin = ev[2 * v];
-        tv.ev_end = ev[2 * v + 1];
+        tv.ev_begin = ev[2 * run];
+        tv.ev_end = ev[2 * run + 1];
         if (v == 1) {
             int rc = tc_groups(a.pairs, n_t, &grp, &gpos, s);
             if (rc) return rc;
@@ -370,9 +449,12 @@ int tune_pass1(mapper_ctx* ctx, const PassArgs& a, const TcArgs& t, int64_t n_pa
     CK(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
     CK(cudaStreamSynchronize(s), "sync");
     if (h_err) return fail(MAPPER_ETIMEOUT, "a tensor-core pass gave up waiting on a barrier (autotuning)");
-    float ms[2] = {0.f, 0.f};
-    CK(cudaEventElapsedTime(&ms[0], ev[0], ev[1]), "event time");
-    CK(cudaEventElapsedTime(&ms[1], ev[2], ev[3]), "event time");
+    float ms[2] = {INFINITY, INFINITY};
+    for (int run = 0; run < kRuns; ++run) {
+        float m = 0.f;
+        CK(cudaEventElapsedTime(&m, ev[2 * run], ev[2 * run + 1]), "event time");
+        ms[run & 1] = std::min(ms[run & 1], m);
+    }
     *tile_n = ms[1] <= ms[0] ? 256 : 128;
     ctx->pass1_tile_n[key] = *tile_n;
     return MAPPER_OK;
@@ -574,7 +656,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     // three FP8 products first): the 32 x 32 sub-blocks with a pair inside the
     // first screen's band run again with three BF16 products
     // (hi.hi + hi.lo + lo.hi); the others are final after the first
-    const bool two_phase = use_tc && t.ns == 3 && ctx->screen_mode != 2;
+    bool two_phase = use_tc && t.ns == 3 && ctx->screen_mode != 2;
     TcArgs t8 = t;                                                // the FP8 operands of the first phase
     if (f8) {
         t8.f8 = true;
@@ -583,6 +665,16 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         t8.rl = L.frl.as<float>();
         t8.tmax = L.ftmax.as<float4>();
     }
+    // default screen: two phases or one, from a sample of the first phase
+    const bool defer_mixed = ctx->screen_mode == 3 || ctx->screen_mode == 0;
+    st.pass1_sample_deferred = -1.0;
+    if (two_phase && ctx->screen_mode == 0 && PL.n[kListTC] >= kSampleMinPairs) {
+        double f = 0.0;
+        if ((rc = sample_deferral(ctx, a_tc, f8 ? t8 : t, PL.n[kListTC], R, cap, s, &f))) return rc;
+        st.pass1_sample_deferred = f;
+        if (f > kDeferMax) two_phase = false;
+    }
+    st.pass1_phases = use_tc ? (two_phase ? 2 : 1) : 0;
     Buf redo, redo_mask, redo_q;
     if (two_phase) {
         const int64_t rcap = std::max<int64_t>(std::max(PL.n[kListTC], cross_tc ? PL.n[kListSimt] : 0), 1);
@@ -591,9 +683,14 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         CK(redo_q.alloc(sizeof(int32_t) * rcap, s), "alloc");
     }
     int tile_n = 0;
-    TcArgs t_tune = f8 ? t8 : t, tx_tune = tx;
+    // the first (or only) screen: FP8 products when chosen, except a
+    // one-phase pass the sample picked (three BF16 products then)
+    const bool first_f8 = f8 && (two_phase || ctx->screen_mode != 0);
+    TcArgs t_tune = first_f8 ? t8 : t, tx_tune = tx;
     if (two_phase && !f8) t_tune.ns = 1;
     if (two_phase) tx_tune.ns = 1;
+    t_tune.defer = tx_tune.defer = two_phase;                    // timed as the first phase runs
+    t_tune.defer_mixed = tx_tune.defer_mixed = defer_mixed;
     if (use_tc && PL.n[kListTC] > 0 && (rc = tune_pass1(ctx, a_tc, t_tune, PL.n[kListTC], R, cap, s, &tile_n)))
         return rc;
     if (use_tc && PL.n[kListTC] == 0 && cross_tc &&
@@ -628,6 +725,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         if (!two_phase) return tc_pass(1, pa, t1, np, s);
         if (!t1.f8) t1.ns = 1;
         t1.defer = true;
+        t1.defer_mixed = defer_mixed;
         t1.redo_mask = redo_mask.as<uint32_t>();
         CK(cudaMemsetAsync(redo_mask.p, 0, sizeof(uint32_t) * np, s), "memset");
         int r2;
@@ -637,7 +735,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         // (their number stays on the device)
         Buf rpos, rgr, rgp;
         if ((r2 = tc_redo_list(pa.pairs, redo_mask.as<uint32_t>(), np, redo.as<int2>(), redo_q.as<int32_t>(), &rpos,
-                               s)))
+                               s, pa.stats + kStatRedoBlocks)))
             return r2;
         const unsigned long long* n_redo = reinterpret_cast<const unsigned long long*>(rpos.as<int64_t>() + np);
         PassArgs p2 = pa;
@@ -663,7 +761,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     if (use_tc) {
         const bool x_last = cross_tc && PL.n[kListSimt] > 0;
         if (PL.n[kListTC] > 0 &&
-            (rc = tc_count(a_tc, t, f8 ? t8 : t, PL.n[kListTC], groups, group_pos, true, !x_last)))
+            (rc = tc_count(a_tc, t, first_f8 ? t8 : t, PL.n[kListTC], groups, group_pos, true, !x_last)))
             return rc;
         if (x_last &&
             (rc = tc_count(a_simt, tx, tx, PL.n[kListSimt], xgroups, xgroup_pos, PL.n[kListTC] == 0, true)))
@@ -793,6 +891,8 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     st.n_rows = R;
     st.tile_pairs_screen1 = two_phase ? PL.n[kListTC] + (cross_tc ? PL.n[kListSimt] : 0) : 0;
     st.tile_pairs_redo = (int64_t)h_stats[kStatRedo];
+    st.redo_blocks = (int64_t)h_stats[kStatRedoBlocks];
+    st.redo_parts = (int64_t)h_stats[kStatRedoParts];
     if (tev[0] && (PL.n[use_tc ? kListTC : kListSimt] > 0 || cross_tc)) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, tev[0], tev[1]), "event time");
@@ -1131,7 +1231,7 @@ int mapper_set_cross_screen(mapper_ctx* ctx, int mode)
 int mapper_set_pass1_screen(mapper_ctx* ctx, int mode)
 {
     if (!ctx) return fail(MAPPER_EINVAL, "null context");
-    if (mode < 0 || mode > 2) return fail(MAPPER_EINVAL, "pass-1 screen must be 0, 1 or 2");
+    if (mode < 0 || mode > 3) return fail(MAPPER_EINVAL, "pass-1 screen must be 0, 1, 2 or 3");
     ctx->screen_mode = mode;
     return MAPPER_OK;
 }

@@ -17,7 +17,8 @@ constexpr int kPairTileMask = kPairOneEach - 1;
 
 enum : int { kStatBand = 0, kStatTies = 1, kStatScreened = 2, kStatCore = 3, kStatTileOut = 4,
              kStatTileIn = 5, kStatSkipped = 6, kStatTcPairs = 7, kStatSimtPairs = 8, kStatFp64 = 9,
-             kStatUnion = 10, kStatRedo = 11, kStatOob = 12, kStatCount = 13 };
+             kStatUnion = 10, kStatRedo = 11, kStatOob = 12, kStatRedoBlocks = 13, kStatRedoParts = 14,
+             kStatCount = 15 };
 
 // Work lists of tile pairs, classified by bounding spheres.
 enum : int { kListAllIn = 0, kListTC = 1, kListSimt = 2, kListCount = 3 };

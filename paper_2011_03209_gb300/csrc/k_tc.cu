@@ -72,7 +72,7 @@ struct TcParams {
     // pass 1, one-product screen of the two-phase count pass: a sub-block with
     // any pair in the band is not counted here but marked in redo_mask (and
     // its pair flagged in pair_hit) for a three-product pass
-    int defer;
+    int defer;                                // 1: defer blocks with a band pair; 2: every mixed block
     uint32_t* redo_mask;                      // first phase: deferred sub-blocks per pair (bit quad * 4 + part)
     const uint32_t* sub_mask;                 // second phase: sub-blocks to count per pair: sub_mask[sub_q[q]]
     const int32_t* sub_q;
@@ -949,6 +949,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                     all_in = __fmaf_rd(two, vmin, -cur.bn2[h]) >= k_in;
                 }
                 const bool mixed = !all_out && !all_in;
+                auto defer_block = [&]() {
+                    // first phase: the sub-block goes to the three-product pass, whole
+                    if (lane == 0) {
+                        if (atomicOr(&P.redo_mask[q], 1u << sub) == 0u) atomicAdd(&A.stats[kStatRedo], 1ull);
+                        if (A.pair_hit) A.pair_hit[q] = 1;
+                    }
+                };
+                // first phase, extremes only: a block with a row neither all in
+                // nor all out is deferred without looking at its values
+                if (P.defer == 2 && __any_sync(0xffffffffu, mixed)) {
+                    defer_block();
+                    continue;
+                }
                 if (__any_sync(0xffffffffu, mixed)) {
                     __syncwarp();                             // the previous pair's wn is read
                     wn[lane] = cur.ncol2[h];
@@ -978,11 +991,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 uint32_t inb = in_bits & cand;
                 const uint32_t band = keep_bits & ~in_bits & cand;
                 if (P.defer && __any_sync(0xffffffffu, band != 0u)) {
-                    // first phase: the sub-block goes to the three-product pass, whole
-                    if (lane == 0) {
-                        if (atomicOr(&P.redo_mask[q], 1u << sub) == 0u) atomicAdd(&A.stats[kStatRedo], 1ull);
-                        if (A.pair_hit) A.pair_hit[q] = 1;
-                    }
+                    defer_block();
                     continue;
                 }
                 if (A.pair_hit && __any_sync(0xffffffffu, (inb | band) != 0u) && lane == 0) A.pair_hit[q] = 1;
@@ -1789,10 +1798,28 @@ __global__ void group_emit_dev_kernel(const int2* __restrict__ pairs, int64_t n,
 }
 
 // flag[q] = 1 if the first phase deferred a sub-block of pair q
-__global__ void redo_flag_kernel(const uint32_t* __restrict__ mask, int64_t n, int32_t* __restrict__ flag)
+__global__ void redo_flag_kernel(const uint32_t* __restrict__ mask, int64_t n, int32_t* __restrict__ flag,
+                                 unsigned long long* __restrict__ stats)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) flag[i] = mask[i] != 0u;
+    const uint32_t m = i < n ? mask[i] : 0u;
+    if (i < n) flag[i] = m != 0u;
+    if (stats) {
+        // bit quad * 4 + part: blocks, and parts holding one
+        const int blocks = __reduce_add_sync(0xffffffffu, __popc(m));
+        const int parts = __reduce_add_sync(0xffffffffu, __popc((m | m >> 4 | m >> 8 | m >> 12) & 0xFu));
+        if ((threadIdx.x & 31) == 0 && blocks) {
+            atomicAdd(stats, (unsigned long long)blocks);
+            atomicAdd(stats + 1, (unsigned long long)parts);
+        }
+    }
+}
+
+// every stride-th pair of a list: out[j] = pairs[j * stride], j < n
+__global__ void sample_pairs_kernel(const int2* __restrict__ pairs, int64_t stride, int64_t n, int2* __restrict__ out)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) out[j] = pairs[j * stride];
 }
 
 // the deferred pairs in list order: redo[pos[q]] = pairs[q], redo_q[pos[q]] = q
@@ -1808,15 +1835,28 @@ __global__ void redo_scatter_kernel(const int2* __restrict__ pairs, const int32_
 
 }  // namespace
 
+int tc_sample_pairs(const int2* pairs, int64_t stride, int64_t n, int2* out, cudaStream_t s)
+{
+    if (n == 0) return MAPPER_OK;
+    sample_pairs_kernel<<<(unsigned)div_up(n, 256), 256, 0, s>>>(pairs, stride, n, out);
+    note_launch();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("tc_sample_pairs: ") + cudaGetErrorString(e));
+        return MAPPER_ECUDA;
+    }
+    return MAPPER_OK;
+}
+
 int tc_redo_list(const int2* pairs, const uint32_t* mask, int64_t n, int2* redo, int32_t* redo_q, Buf* pos,
-                 cudaStream_t s)
+                 cudaStream_t s, unsigned long long* stats)
 {
     if (n == 0) return MAPPER_OK;
     Buf flag;
     cudaError_t e = flag.alloc(sizeof(int32_t) * n, s);
     if (e == cudaSuccess) e = pos->alloc(sizeof(int64_t) * (n + 1), s);
     if (e == cudaSuccess) {
-        redo_flag_kernel<<<(unsigned)div_up(n, 256), 256, 0, s>>>(mask, n, flag.as<int32_t>());
+        redo_flag_kernel<<<(unsigned)div_up(n, 256), 256, 0, s>>>(mask, n, flag.as<int32_t>(), stats);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = exclusive_scan_i32_to_i64(flag.as<int32_t>(), pos->as<int64_t>(), n, s);
@@ -2074,7 +2114,7 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
     p.queue_cap = t.queue_cap;
     p.err = t.err;
     const bool defer = mode == 1 && t.defer && (t.ns == 1 || t.f8);
-    p.defer = defer ? 1 : 0;
+    p.defer = defer ? (t.defer_mixed ? 2 : 1) : 0;
     p.redo_mask = t.redo_mask;
     p.sub_mask = t.sub_mask;
     p.sub_q = t.sub_q;

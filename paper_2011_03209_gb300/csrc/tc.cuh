@@ -40,6 +40,8 @@ struct TcArgs {
     // second phase (ns = 3) runs over that list with sub_mask = redo_mask and
     // sub_q = its first-phase indices, counting only those sub-blocks.
     bool defer;
+    bool defer_mixed;                // first phase: defer every block with a row neither all in nor
+                                     // all out (decided from the rows' extremes alone)
     uint32_t* redo_mask;
     const uint32_t* sub_mask;
     const int32_t* sub_q;
@@ -47,9 +49,12 @@ struct TcArgs {
 
 // The pairs q of pairs[0 .. n) with mask[q] != 0, in list order: redo[k] =
 // pairs[q_k], redo_q[k] = q_k (capacity n each); *pos receives [n + 1] int64
-// with their number at pos[n]. Returns a mapper_status.
+// with their number at pos[n]. stats (nullable, two counters): += the
+// deferred blocks and the 32-column parts holding one. Returns a mapper_status.
 int tc_redo_list(const int2* pairs, const uint32_t* mask, int64_t n, int2* redo, int32_t* redo_q, Buf* pos,
-                 cudaStream_t s);
+                 cudaStream_t s, unsigned long long* stats = nullptr);
+// out[j] = pairs[j * stride] for j < n. Returns a mapper_status.
+int tc_sample_pairs(const int2* pairs, int64_t stride, int64_t n, int2* out, cudaStream_t s);
 
 // tc_groups over the first *n_dev entries of a list of capacity n (number of
 // groups at (*pos)[n]). Returns a mapper_status.

@@ -50,7 +50,7 @@ def test_struct_layouts_match_header():
     assert _capi.MapperParams.overlap.offset == 32
     assert _capi.MapperParams.cover_kind.offset == 64
     assert _capi.MapperParams.lens_param.offset == 72
-    assert ctypes.sizeof(_capi.MapperStats) == 8 * 36
+    assert ctypes.sizeof(_capi.MapperStats) == 8 * 40
 
 
 def test_null_and_bad_arguments_are_rejected_without_a_gpu(lib):

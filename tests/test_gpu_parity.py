@@ -401,7 +401,7 @@ def test_two_phase_count_pass_equals_three_products(tile_n, first):
     Xd = torch.from_numpy(w.X).to("cuda:0")
     prm = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, first)
     outs = []
-    for mode in (1, 2):
+    for mode in (1, 2, 3):
         with mg.Context(0) as c:
             c.set_pass1_tile_n(tile_n)
             c.set_pass1_screen(mode)
@@ -414,18 +414,51 @@ def test_two_phase_count_pass_equals_three_products(tile_n, first):
             out["stats"] = st
             outs.append(out)
             del g
-    one, three = outs
+    one, three, mixed = outs
     assert one["stats"]["tile_pairs_screen1"] == one["stats"]["tile_pairs_tc"] + one["stats"]["tile_pairs_cross"]
     assert 0 < one["stats"]["tile_pairs_redo"] < one["stats"]["tile_pairs_screen1"]
+    assert 0 < one["stats"]["redo_blocks"] and one["stats"]["redo_parts"] <= one["stats"]["redo_blocks"]
     assert three["stats"]["tile_pairs_screen1"] == 0 and three["stats"]["tile_pairs_redo"] == 0
+    # the first phase of mode 3 defers every block its extremes leave open:
+    # a superset of mode 1's blocks
+    assert mixed["stats"]["redo_blocks"] >= one["stats"]["redo_blocks"]
     # every tile pair is counted once: the same pairs screened either way
     assert one["stats"]["count_kernel_pairs"] == three["stats"]["count_kernel_pairs"]
+    assert mixed["stats"]["count_kernel_pairs"] == three["stats"]["count_kernel_pairs"]
     for k in ("elem_points", "core", "labels", "node_offsets", "node_members", "node_elem", "edges"):
         assert np.array_equal(one[k], three[k]), k
+        assert np.array_equal(mixed[k], three[k]), k
     assert_same_graph(w.X, one, w.n_intervals, w.overlap, w.eps, w.min_pts)
     with mg.Context(0) as c:
         with pytest.raises(mg.MapperError):
-            c.set_pass1_screen(3)
+            c.set_pass1_screen(4)
+
+
+@pytest.mark.parametrize("first", [mg.BF16, mg.FP8])
+def test_default_screen_samples_the_first_phase(first):
+    """The default count-pass screen samples the first phase on every 64th
+    tile pair and takes one phase or two from the fraction that defers a
+    block; either way the graph is the one of three products everywhere."""
+    w = synth.mixture_100k()
+    Xd = torch.from_numpy(w.X).to("cuda:0")
+    prm = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, first)
+    outs = []
+    for mode in (0, 2):
+        with mg.Context(0) as c:
+            c.set_pass1_screen(mode)
+            g = mg.mapper_graph(c, Xd, prm)
+            out = g.numpy()
+            out["stats"] = g.stats()
+            outs.append(out)
+            del g
+    auto, three = outs
+    st = auto["stats"]
+    assert 0.0 <= st["pass1_sample_deferred"] <= 1.0
+    assert st["pass1_phases"] == (1 if st["pass1_sample_deferred"] > 0.35 else 2)
+    assert (st["tile_pairs_screen1"] > 0) == (st["pass1_phases"] == 2)
+    assert three["stats"]["pass1_phases"] == 1 and three["stats"]["pass1_sample_deferred"] == -1.0
+    for k in ("node_offsets", "node_members", "node_elem", "edges"):
+        assert np.array_equal(auto[k], three[k]), k
 
 
 @pytest.mark.parametrize("prec", [mg.BF16, mg.BF16X1, mg.FP8])
