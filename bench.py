@@ -281,11 +281,12 @@ def _roofline(prec, w, st, stats, n_sm):
     executed = ((tp1 * first * kp + tp3 * 3 * kp) if tp1 else ns * kp * st["tile_pairs_tc"]) / (kms * 1e-3) / 1e12
     if prec == mg.FP8:
         desc = ("tc_kernel count pass (tcgen05): three FP8 E4M3 products per tile pair, then three BF16 "
-                "products for the 32 x 32 blocks whose FP8 band is not empty" if tp1 else
+                "products for the 32 x 32 blocks the first screen leaves open" if tp1 else
                 "tc_kernel (tcgen05 FP8 E4M3 count pass): three products per pair")
     else:
         desc = ("tc_kernel count pass (tcgen05 BF16): one product per tile pair, three products for the "
-                "32 x 32 blocks whose one-product band is not empty" if tp1 else
+                "32 x 32 blocks the first screen leaves open (one phase or two, chosen per call from a "
+                "sample of the first phase)" if tp1 else
                 "tc_kernel<%d,1> (tcgen05 BF16 count pass): %d BF16 products per pair" % (ns, ns))
     return kms, {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                  "frac": achieved / peak, "traffic": _traffic(st) if prec == mg.BF16 else None,

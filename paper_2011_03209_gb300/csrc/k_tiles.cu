@@ -811,99 +811,132 @@ __global__ void __launch_bounds__(256) outlier_seg_kernel(const float* __restric
 }
 
 constexpr int kMaxSegList = 1024;
-constexpr int kClsPer = 8;                     // tiles b per warp step
 
-__global__ void __launch_bounds__(256) classify_kernel(const int64_t* __restrict__ eseg_off,
-                                                       const int64_t* __restrict__ seg_toff,
-                                                       const int32_t* __restrict__ seg_elem,
-                                                       const float* __restrict__ seg_cent,
-                                                       const double* __restrict__ seg_rad,
-                                                       const float* __restrict__ cent,
-                                                       const double* __restrict__ rad,
-                                                       const int32_t* __restrict__ tile_seg,
-                                                       const int32_t* __restrict__ seg_out, int dp, double rel,
-                                                       double eps_out, double eps_in, int use_tc,
-                                                       const float* __restrict__ tsm, int smax,
-                                                       int2* __restrict__ l_in, int2* __restrict__ l_tc,
-                                                       int2* __restrict__ l_simt,
-                                                       unsigned long long* __restrict__ counts)
+// Tile-pair classification by bounding spheres, with the centres of up to
+// kClsA tiles A of one segment per CTA (in shared memory) against one tile B
+// per lane: each
+// tile B's centre is read once per CTA instead of once per tile A, and a
+// lane keeps the kClsA sums itself (a sequential FMA chain over dp columns:
+// the true squared distance lies in [ssum c_lo, ssum c_hi]). CTA c takes block c of the blocks of kClsA tiles
+// that blk_off (exclusive prefix of ceil(tiles / kClsA) per segment) numbers.
+constexpr int kClsA = 8;
+
+__global__ void __launch_bounds__(256) classify_blk_kernel(const int64_t* __restrict__ blk_off, int64_t n_seg,
+                                                           const int64_t* __restrict__ eseg_off,
+                                                           const int64_t* __restrict__ seg_toff,
+                                                           const int32_t* __restrict__ seg_elem,
+                                                           const float* __restrict__ seg_cent,
+                                                           const double* __restrict__ seg_rad,
+                                                           const float* __restrict__ cent,
+                                                           const double* __restrict__ rad,
+                                                           const int32_t* __restrict__ seg_out, int dp, double rel,
+                                                           double c_lo, double c_hi, double eps_out, double eps_in,
+                                                           int use_tc,
+                                                           const float* __restrict__ tsm, int smax,
+                                                           int2* __restrict__ l_in, int2* __restrict__ l_tc,
+                                                           int2* __restrict__ l_simt,
+                                                           unsigned long long* __restrict__ counts)
 {
-    extern __shared__ float s_ca[];
+    extern __shared__ float4 s_ca4[];                    // [kClsA][dp / 4]
     __shared__ int s_seg[kMaxSegList];
     __shared__ int s_nseg;
     __shared__ unsigned long long s_out;
-    const int ta = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = threadIdx.x; k < dp; k += blockDim.x) s_ca[k] = cent[(int64_t)ta * dp + k];
-    const int ga = tile_seg[ta];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t c = blockIdx.x;
+    if (c >= blk_off[n_seg]) return;
+    // the block's segment: the last g with blk_off[g] <= c
+    int64_t lo = 0, hi = n_seg - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (blk_off[mid] <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t ga = lo;
+    const int64_t ta0 = seg_toff[ga] + (c - blk_off[ga]) * kClsA;
+    const int64_t left_a = seg_toff[ga + 1] - ta0;
+    const int na = (int)(left_a < kClsA ? left_a : kClsA);
+    const int dq = dp / 4;
+    for (int k = threadIdx.x; k < kClsA * dq; k += blockDim.x) {
+        const int a = k / dq, kk = k % dq;
+        s_ca4[k] = reinterpret_cast<const float4*>(cent + (ta0 + (a < na ? a : 0)) * dp)[kk];
+    }
     const int64_t g_end = eseg_off[seg_elem[ga] + 1];
     const int64_t g_first = eseg_off[seg_elem[ga]];
     if (threadIdx.x == 0) { s_nseg = 0; s_out = 0ull; }
     __syncthreads();
-    // surviving segments gb >= ga (the own segment always survives)
     const bool listed = g_end - ga <= kMaxSegList;
     for (int64_t gb = ga + warp; gb < g_end && listed; gb += 8) {
         bool keep = gb == ga;
         if (!keep) {
-            const float ssum = dist_sum32(seg_cent + (int64_t)ga * dp, seg_cent + gb * dp, dp, lane);
+            const float ssum = dist_sum32(seg_cent + ga * dp, seg_cent + gb * dp, dp, lane);
             const double Dlo = sqrt((double)ssum * (1.0 - rel)) * (1.0 - 1e-15);
             keep = !(Dlo - seg_rad[ga] - seg_rad[gb] > eps_out);
         }
         if (lane == 0) {
             if (keep) s_seg[atomicAdd(&s_nseg, 1)] = (int)gb;
-            else atomicAdd(&s_out, (unsigned long long)(seg_toff[gb + 1] - seg_toff[gb]));
+            else atomicAdd(&s_out, (unsigned long long)na * (unsigned long long)(seg_toff[gb + 1] - seg_toff[gb]));
         }
     }
     __syncthreads();
     const int nlist = listed ? s_nseg : (int)(g_end - ga);
-    const double ra = rad[ta];
+    double ra[kClsA];
+#pragma unroll
+    for (int a = 0; a < kClsA; ++a) ra[a] = a < na ? rad[ta0 + a] : 0.0;
     int64_t n_out = 0;
     for (int li = 0; li < nlist; ++li) {
         const int64_t gb = listed ? s_seg[li] : ga + li;
-        const int64_t t0 = gb == ga ? ta : seg_toff[gb], t1 = seg_toff[gb + 1];
-        // each warp takes kClsPer tiles b at a time (independent sums, each
-        // with the lane and shuffle order of dist_sum32); lane u classifies b_u
-        for (int64_t tb0 = t0 + warp * kClsPer; tb0 < t1; tb0 += 8 * kClsPer) {
-            float ss[kClsPer];
+        const int64_t t0 = gb == ga ? ta0 : seg_toff[gb], t1 = seg_toff[gb + 1];
+        const int gbi = (int)gb;
+        for (int64_t tb0 = t0 + warp * 32; tb0 < t1; tb0 += 8 * 32) {
+            const int64_t tb = tb0 + lane;
+            const bool live = tb < t1;
+            const float4* cb = reinterpret_cast<const float4*>(cent + (live ? tb : t0) * dp);
+            float acc[kClsA];
 #pragma unroll
-            for (int u = 0; u < kClsPer; ++u) ss[u] = 0.f;
-            for (int k = lane; k < dp; k += 32) {
-                const float a = s_ca[k];
+            for (int a = 0; a < kClsA; ++a) acc[a] = 0.f;
+#pragma unroll 4
+            for (int kk = 0; kk < dq; ++kk) {
+                const float4 b = __ldg(cb + kk);
 #pragma unroll
-                for (int u = 0; u < kClsPer; ++u) {
-                    if (tb0 + u < t1) {
-                        const float v = a - cent[(tb0 + u) * dp + k];
-                        ss[u] = fmaf(v, v, ss[u]);
-                    }
+                for (int a = 0; a < kClsA; ++a) {
+                    const float4 x = s_ca4[a * dq + kk];
+                    float u = x.x - b.x;
+                    acc[a] = fmaf(u, u, acc[a]);
+                    u = x.y - b.y;
+                    acc[a] = fmaf(u, u, acc[a]);
+                    u = x.z - b.z;
+                    acc[a] = fmaf(u, u, acc[a]);
+                    u = x.w - b.w;
+                    acc[a] = fmaf(u, u, acc[a]);
                 }
             }
-            float ssum = 0.f;
+            if (!live) continue;
+            const double rb = rad[tb];
 #pragma unroll
-            for (int u = 0; u < kClsPer; ++u) {
-                for (int o = 16; o; o >>= 1) ss[u] += __shfl_xor_sync(0xffffffffu, ss[u], o);
-                if (lane == u) ssum = ss[u];
-            }
-            const int64_t tb = tb0 + lane;
-            if (tb == ta) ssum = 0.f;
-            if (lane < kClsPer && tb < t1) {
-                const double Dlo = sqrt((double)ssum * (1.0 - rel)) * (1.0 - 1e-15);
-                const double Dhi = sqrt((double)ssum * (1.0 + rel)) * (1.0 + 1e-15);
-                const double rb = rad[tb];
-                const int gb = tile_seg[tb];
+            for (int a = 0; a < kClsA; ++a) {
+                const int64_t ta = ta0 + a;
+                if (a >= na || (gb == ga && tb < ta)) continue;
+                // squared bounds with outward rounding (no square root):
+                // D^2 >= ssum c_lo, D^2 <= ssum c_hi for the true centre distance D
+                const double ssum = tb == ta ? 0.0 : (double)acc[a];
+                const double t_out = __dadd_ru(__dadd_ru(eps_out, ra[a]), rb);
+                const double w_in = __dsub_rd(__dsub_rd(eps_in, ra[a]), rb);
                 int cls;
-                if (Dlo - ra - rb > eps_out) cls = -1;
-                else if (Dhi + ra + rb < eps_in) cls = kListAllIn;
-                else if (tsm && gb != ga &&
-                         ((seg_out[ga] && (double)tsm[(int64_t)ta * smax + (gb - g_first)] - seg_rad[gb] > eps_out) ||
-                          (seg_out[gb] && (double)tsm[tb * smax + (ga - g_first)] - seg_rad[ga] > eps_out)))
+                if (__dmul_rd(ssum, c_lo) > __dmul_ru(t_out, t_out)) cls = -1;
+                else if (w_in > 0.0 && __dadd_ru(__dmul_ru(ssum, c_hi), 1e-36) < __dmul_rd(w_in, w_in))
+                    cls = kListAllIn;                         // (1e-36: the FP32 subnormal roundings)
+                else if (tsm && gbi != (int)ga &&
+                         ((seg_out[ga] && (double)tsm[ta * smax + (gbi - g_first)] - seg_rad[gbi] > eps_out) ||
+                          (seg_out[gbi] && (double)tsm[tb * smax + (ga - g_first)] - seg_rad[ga] > eps_out)))
                     cls = -1;
-                else if (use_tc && ga == gb) cls = kListTC;
+                else if (use_tc && gbi == (int)ga) cls = kListTC;
                 else cls = kListSimt;
                 if (cls < 0) {
                     ++n_out;
                 } else {
                     const unsigned long long at = atomicAdd(&counts[cls], 1ull);
                     int2* dst = cls == kListAllIn ? l_in : (cls == kListTC ? l_tc : l_simt);
-                    dst[at] = make_int2(ta, (int)tb);
+                    dst[at] = make_int2((int)ta, (int)tb);
                 }
             }
         }
@@ -911,6 +944,13 @@ __global__ void __launch_bounds__(256) classify_kernel(const int64_t* __restrict
     if (n_out) atomicAdd(&s_out, (unsigned long long)n_out);
     __syncthreads();
     if (threadIdx.x == 0 && s_out) atomicAdd(&counts[3], s_out);
+}
+
+// blocks of kClsA tiles per segment: cnt[g] = ceil(tiles(g) / kClsA)
+__global__ void seg_blocks_kernel(const int64_t* __restrict__ seg_toff, int64_t n_seg, int64_t* __restrict__ cnt)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n_seg) cnt[g] = (seg_toff[g + 1] - seg_toff[g] + kClsA - 1) / kClsA;
 }
 
 }  // namespace
@@ -1195,20 +1235,44 @@ int classify_pairs(const TileLayout& L, const float* X, int64_t ld, int d, int d
     TK(cudaStreamSynchronize(s));
     P->n_candidates = C;
     for (int k = 0; k < kListCount; ++k) TK(P->list[k].alloc(sizeof(int2) * std::max<int64_t>(C, 1), s));
-    if (C > 0) {
-        const double eps_out = eps * (1.0 + 1e-9), eps_in = eps * (1.0 - 1e-9);
-        const double rel = (double)(dp / 32 + 12) * std::ldexp(1.0, -23);
-        const size_t smem = sizeof(float) * dp;
-        if (smem > 32 * 1024)
-            TK(cudaFuncSetAttribute(classify_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        classify_kernel<<<(unsigned)L.T, 256, smem, s>>>(
-            eseg_off.as<int64_t>(), L.seg_toff.as<int64_t>(), L.seg_elem.as<int32_t>(), L.seg_cent.as<float>(),
-            L.seg_rad.as<double>(), L.tile_cent.as<float>(), L.tile_rad.as<double>(), L.tile_seg.as<int32_t>(),
-            L.seg_outlier.as<int32_t>(), dp, rel, eps_out, eps_in, use_tc ? 1 : 0, nullptr, 0,
-            P->list[kListAllIn].as<int2>(), P->list[kListTC].as<int2>(), P->list[kListSimt].as<int2>(),
+    // blocks of kClsA tiles A per segment for classify_blk_kernel
+    Buf blk_cnt, blk_off;
+    TK(blk_cnt.alloc(sizeof(int64_t) * std::max<int64_t>(L.n_seg, 1), s));
+    TK(blk_off.alloc(sizeof(int64_t) * (L.n_seg + 1), s));
+    if (L.n_seg > 0) {
+        seg_blocks_kernel<<<grid_for(L.n_seg), 256, 0, s>>>(L.seg_toff.as<int64_t>(), L.n_seg,
+                                                            blk_cnt.as<int64_t>());
+        note_launch();
+        TK(cudaGetLastError());
+    }
+    TK(exclusive_scan_i64(blk_cnt.as<int64_t>(), blk_off.as<int64_t>(), L.n_seg, s));
+    const unsigned cls_grid = (unsigned)(div_up(L.T, kClsA) + L.n_seg);
+    const size_t cls_smem = sizeof(float) * kClsA * dp;
+    if (cls_smem > 48 * 1024)
+        TK(cudaFuncSetAttribute(classify_blk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cls_smem));
+    // segment distances: lane partial sums and a shuffle tree (dist_sum32);
+    // tile distances: one FMA chain over dp columns
+    const double rel = (double)(dp / 32 + 12) * std::ldexp(1.0, -23);
+    // |ssum - D^2| <= rel_tile D^2, so D^2 is in [ssum c_lo, ssum c_hi] with
+    // c_lo <= 1 - rel_tile and c_hi >= 1 / (1 - rel_tile) (outward rounding)
+    const double rel_tile = (double)(dp + 24) * std::ldexp(1.0, -24);
+    const double c_lo = std::nextafter(1.0 - rel_tile, 0.0);
+    const double c_hi = std::nextafter(1.0 / (1.0 - rel_tile), INFINITY);
+    const double eps_out = eps * (1.0 + 1e-9), eps_in = eps * (1.0 - 1e-9);
+    auto classify = [&](const float* tsm, int smax) -> int {
+        classify_blk_kernel<<<cls_grid, 256, cls_smem, s>>>(
+            blk_off.as<int64_t>(), L.n_seg, eseg_off.as<int64_t>(), L.seg_toff.as<int64_t>(),
+            L.seg_elem.as<int32_t>(), L.seg_cent.as<float>(), L.seg_rad.as<double>(), L.tile_cent.as<float>(),
+            L.tile_rad.as<double>(), L.seg_outlier.as<int32_t>(), dp, rel, c_lo, c_hi, eps_out, eps_in, use_tc ? 1 : 0,
+            tsm, smax, P->list[kListAllIn].as<int2>(), P->list[kListTC].as<int2>(), P->list[kListSimt].as<int2>(),
             counts.as<unsigned long long>());
         note_launch();
         TK(cudaGetLastError());
+        return MAPPER_OK;
+    };
+    if (C > 0) {
+        const int rc = classify(nullptr, 0);
+        if (rc) return rc;
     }
     unsigned long long h[4] = {0, 0, 0, 0};
     TK(cudaMemcpyAsync(h, counts.p, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -1220,23 +1284,15 @@ int classify_pairs(const TileLayout& L, const float* X, int64_t ld, int d, int d
         const int smax = L.n_groups + 1;
         Buf tsm;
         TK(tsm.alloc(sizeof(float) * (size_t)L.T * smax, s));
-        const double eps_out = eps * (1.0 + 1e-9), eps_in = eps * (1.0 - 1e-9);
-        const double rel = (double)(dp / 32 + 12) * std::ldexp(1.0, -23);
-        const size_t smem = sizeof(float) * dp;
         outlier_seg_kernel<<<(unsigned)L.T, 256, 0, s>>>(L.G.as<float>(), X, ld, d, dp, L.row_pt.as<int32_t>(),
                                                           L.tile_n.as<int32_t>(), L.tile_seg.as<int32_t>(),
                                                           L.tile_elem.as<int32_t>(), L.seg_outlier.as<int32_t>(),
                                                           eseg_off.as<int64_t>(), L.seg_cent.as<float>(), rel, smax,
                                                           tsm.as<float>());
+        note_launch();
         TK(cudaMemsetAsync(counts.p, 0, sizeof(unsigned long long) * 4, s));
-        classify_kernel<<<(unsigned)L.T, 256, smem, s>>>(
-            eseg_off.as<int64_t>(), L.seg_toff.as<int64_t>(), L.seg_elem.as<int32_t>(), L.seg_cent.as<float>(),
-            L.seg_rad.as<double>(), L.tile_cent.as<float>(), L.tile_rad.as<double>(), L.tile_seg.as<int32_t>(),
-            L.seg_outlier.as<int32_t>(), dp, rel, eps_out, eps_in, use_tc ? 1 : 0, tsm.as<float>(), smax,
-            P->list[kListAllIn].as<int2>(), P->list[kListTC].as<int2>(), P->list[kListSimt].as<int2>(),
-            counts.as<unsigned long long>());
-        note_launch(2);
-        TK(cudaGetLastError());
+        const int rc = classify(tsm.as<float>(), smax);
+        if (rc) return rc;
         TK(cudaMemcpyAsync(h, counts.p, sizeof(h), cudaMemcpyDeviceToHost, s));
         TK(cudaStreamSynchronize(s));
     }
