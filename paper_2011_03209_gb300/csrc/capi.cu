@@ -1642,6 +1642,71 @@ int mapper_knn_distance(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t 
     return copy_out(out, od.p, sizeof(double) * q, !is_host_pointer(out), s);
 }
 
+// Host rows to the device (xdev, n x d). When every lens of p is row-local
+// (L2, coordinate, L-infinity norm), the rows go in kLensChunks chunks on a
+// copy stream and each chunk's lens values are computed on the context's
+// stream as soon as it lands, so the lens hides under the copy; *lens_done
+// tells the caller. Otherwise one copy on the context's stream.
+constexpr int kLensChunks = 8;
+
+int copy_rows_with_lens(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld, const mapper_params* p,
+                        float* xdev, double* lens, bool* lens_done)
+{
+    cudaStream_t s = ctx->stream->s;
+    *lens_done = false;
+    bool row_local = n >= 64 * kLensChunks;
+    for (int j = 0; j < p->m; ++j) {
+        const int k = p->lens_kind[j];
+        row_local &= k == MAPPER_LENS_L2 || k == MAPPER_LENS_LINF ||
+                     (k == MAPPER_LENS_COORD && p->lens_arg[j] >= 0 && p->lens_arg[j] < d);
+    }
+    auto copy = [&](int64_t r0, int64_t rows, cudaStream_t st) -> cudaError_t {
+        if (ld == d)
+            return cudaMemcpyAsync(xdev + r0 * d, X + r0 * ld, sizeof(float) * (size_t)rows * d,
+                                   cudaMemcpyHostToDevice, st);
+        return cudaMemcpy2DAsync(xdev + r0 * d, sizeof(float) * d, X + r0 * ld, sizeof(float) * ld,
+                                 sizeof(float) * d, rows, cudaMemcpyHostToDevice, st);
+    };
+    if (!row_local) {
+        CK(copy(0, n, s), "copy X");
+        return MAPPER_OK;
+    }
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[kLensChunks + 1] = {};
+    struct Guard {
+        cudaStream_t* cs;
+        cudaEvent_t* ev;
+        ~Guard()
+        {
+            for (int i = 0; i <= kLensChunks; ++i) if (ev[i]) cudaEventDestroy(ev[i]);
+            if (*cs) cudaStreamDestroy(*cs);
+        }
+    } guard{&cs, ev};
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "stream");
+    for (int i = 0; i <= kLensChunks; ++i) CK(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming), "event");
+    // the copies start once xdev is allocated (stream order of s)
+    CK(cudaEventRecord(ev[kLensChunks], s), "event");
+    CK(cudaStreamWaitEvent(cs, ev[kLensChunks], 0), "wait");
+    const int64_t chunk = (n + kLensChunks - 1) / kLensChunks;
+    for (int c = 0; c < kLensChunks; ++c) {
+        const int64_t r0 = c * chunk, rows = std::min<int64_t>(chunk, n - r0);
+        if (rows <= 0) break;
+        CK(copy(r0, rows, cs), "copy X");
+        CK(cudaEventRecord(ev[c], cs), "event");
+        CK(cudaStreamWaitEvent(s, ev[c], 0), "wait");
+        for (int j = 0; j < p->m; ++j) {
+            const int k = p->lens_kind[j];
+            const float* xr = xdev + r0 * d;
+            double* f = lens + r0 * p->m;
+            if (k == MAPPER_LENS_L2) CK(lens_l2(xr, rows, d, d, f, p->m, j, s), "lens_l2");
+            else if (k == MAPPER_LENS_LINF) CK(lens_linf(xr, rows, d, d, f, p->m, j, s), "lens_linf");
+            else CK(lens_coord(xr, rows, d, p->lens_arg[j], f, p->m, j, s), "lens_coord");
+        }
+    }
+    *lens_done = true;
+    return MAPPER_OK;
+}
+
 int mapper_graph(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
                  const mapper_params* p, mapper_graph_t** out)
 {
@@ -1667,18 +1732,16 @@ int mapper_graph(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t 
     Buf xdev;
     const float* Xd = X;
     int64_t ldd = ld;
+    bool lens_done = false;
     if (is_host_pointer(X)) {
         CK(xdev.alloc(sizeof(float) * (size_t)n * d, s), "alloc X");
-        if (ld == d) {
-            CK(cudaMemcpyAsync(xdev.p, X, sizeof(float) * (size_t)n * d, cudaMemcpyHostToDevice, s), "copy X");
-        } else {
-            CK(cudaMemcpy2DAsync(xdev.p, sizeof(float) * d, X, sizeof(float) * ld, sizeof(float) * d, n,
-                                 cudaMemcpyHostToDevice, s), "copy X");
-        }
         Xd = xdev.as<float>();
         ldd = d;
+        if ((rc = copy_rows_with_lens(ctx, X, n, d, ld, p, xdev.as<float>(), g->lens.as<double>(), &lens_done)))
+            return rc;
     }
-    if ((rc = run_lens(ctx, Xd, n, d, ldd, p->m, p->lens_kind, p->lens_arg, p->lens_param, p->precision,
+    if (!lens_done &&
+        (rc = run_lens(ctx, Xd, n, d, ldd, p->m, p->lens_kind, p->lens_arg, p->lens_param, p->precision,
                        g->lens.as<double>(), &g->pca, &g->n_pca)))
         return rc;
     tm.mark();

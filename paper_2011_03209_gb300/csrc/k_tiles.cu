@@ -910,19 +910,19 @@ __global__ void __launch_bounds__(256) classify_blk_kernel(const int64_t* __rest
                     acc[a] = fmaf(u, u, acc[a]);
                 }
             }
-            if (!live) continue;
-            const double rb = rad[tb];
+            const double rb = live ? rad[tb] : 0.0;
 #pragma unroll
             for (int a = 0; a < kClsA; ++a) {
                 const int64_t ta = ta0 + a;
-                if (a >= na || (gb == ga && tb < ta)) continue;
+                const bool pair = live && a < na && !(gb == ga && tb < ta);
                 // squared bounds with outward rounding (no square root):
                 // D^2 >= ssum c_lo, D^2 <= ssum c_hi for the true centre distance D
                 const double ssum = tb == ta ? 0.0 : (double)acc[a];
                 const double t_out = __dadd_ru(__dadd_ru(eps_out, ra[a]), rb);
                 const double w_in = __dsub_rd(__dsub_rd(eps_in, ra[a]), rb);
                 int cls;
-                if (__dmul_rd(ssum, c_lo) > __dmul_ru(t_out, t_out)) cls = -1;
+                if (!pair) cls = -2;                      // (no memory reads for lanes without a pair)
+                else if (__dmul_rd(ssum, c_lo) > __dmul_ru(t_out, t_out)) cls = -1;
                 else if (w_in > 0.0 && __dadd_ru(__dmul_ru(ssum, c_hi), 1e-36) < __dmul_rd(w_in, w_in))
                     cls = kListAllIn;                         // (1e-36: the FP32 subnormal roundings)
                 else if (tsm && gbi != (int)ga &&
@@ -931,12 +931,21 @@ __global__ void __launch_bounds__(256) classify_blk_kernel(const int64_t* __rest
                     cls = -1;
                 else if (use_tc && gbi == (int)ga) cls = kListTC;
                 else cls = kListSimt;
-                if (cls < 0) {
-                    ++n_out;
-                } else {
-                    const unsigned long long at = atomicAdd(&counts[cls], 1ull);
-                    int2* dst = cls == kListAllIn ? l_in : (cls == kListTC ? l_tc : l_simt);
-                    dst[at] = make_int2((int)ta, (int)tb);
+                if (cls == -1) ++n_out;
+                // one atomic per warp and list: the lanes of a class take
+                // consecutive slots
+#pragma unroll
+                for (int k3 = 0; k3 < kListCount; ++k3) {
+                    const unsigned m = __ballot_sync(0xffffffffu, cls == k3);
+                    if (!m) continue;
+                    const int leader = __ffs(m) - 1;
+                    unsigned long long at = 0;
+                    if (lane == leader) at = atomicAdd(&counts[k3], (unsigned long long)__popc(m));
+                    at = __shfl_sync(0xffffffffu, at, leader);
+                    if (cls == k3) {
+                        int2* dst = k3 == kListAllIn ? l_in : (k3 == kListTC ? l_tc : l_simt);
+                        dst[at + __popc(m & ((1u << lane) - 1u))] = make_int2((int)ta, (int)tb);
+                    }
                 }
             }
         }
