@@ -508,8 +508,8 @@ int mapper_server_load(mapper_server* server, int* running, int* queued, size_t*
  * GPU work. The first call in a CUDA context (normally the device's primary
  * context) looks up the array's device address there (cudaGetSymbolAddress)
  * and caches it under the context's unique id, so the address is valid for
- * that context's lifetime and a context created again gets a new lookup:
- * make the first call in a context before any stream capture. The call waits
+ * that context's lifetime and a context created again gets a new lookup.
+ * The call waits
  * for its stream (it reads a status word back before returning). Every call
  * shares the array and clears what must start at zero itself; calls that
  * overlap on the GPU (two streams, two threads) race on it and must be

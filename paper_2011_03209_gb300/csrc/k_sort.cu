@@ -85,6 +85,48 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const T* __res
     if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) out[n] = run;
 }
 
+// Exclusive scan of up to kScanOneMax values in one CTA (one launch, no
+// scratch): thread t sums its contiguous run of the input, the CTA scans the
+// run sums, then each thread writes its run's prefixes.
+constexpr int kScanOneThreads = 1024;
+constexpr int64_t kScanOneMax = 1 << 15;
+
+template <class T>
+__global__ void __launch_bounds__(kScanOneThreads) scan_one_kernel(const T* __restrict__ in, int64_t n,
+                                                                   int64_t* __restrict__ out)
+{
+    __shared__ int64_t warp_sums[kScanOneThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t per = (n + kScanOneThreads - 1) / kScanOneThreads;
+    const int64_t b = (int64_t)tid * per, e = min(n, b + per);
+    int64_t v = 0;
+    for (int64_t i = b; i < e; ++i) v += (int64_t)in[i];
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_sums[lane] = w;
+    }
+    __syncthreads();
+    int64_t run = (warp ? warp_sums[warp - 1] : 0) + x - v;
+    for (int64_t i = b; i < e; ++i) {
+        out[i] = run;
+        run += (int64_t)in[i];
+    }
+    if (tid == kScanOneThreads - 1) out[n] = warp_sums[kScanOneThreads / 32 - 1];
+}
+
 template <class T>
 cudaError_t exclusive_scan_impl(const T* in, int64_t* out, int64_t n, cudaStream_t s)
 {
@@ -93,6 +135,10 @@ cudaError_t exclusive_scan_impl(const T* in, int64_t* out, int64_t n, cudaStream
     const int64_t nb = div_up(n, kScanTile);
     if (nb == 1) {
         { scan_apply_kernel<T><<<1, kScanThreads, 0, s>>>(in, n, nullptr, out, true); note_launch(); }
+        return cudaGetLastError();
+    }
+    if (n <= kScanOneMax) {
+        { scan_one_kernel<T><<<1, kScanOneThreads, 0, s>>>(in, n, out); note_launch(); }
         return cudaGetLastError();
     }
     Buf sums, offs;
