@@ -529,6 +529,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
     const int64_t g_begin = MODE == 3 ? 0 : blockIdx.x;
     const int64_t g_step = MODE == 3 ? 1 : gridDim.x;
     const int64_t g_end = MODE == 3 ? (kq_bhi > kq_ch * P.kq_ct ? (kq_bhi - kq_ch * P.kq_ct + 1) / 2 : 0) : n_items;
+    // the k-th work item of this CTA. Count pass: runs of kRun consecutive
+    // items (consecutive groups of the list mostly share tile A, whose blocks
+    // then stay in the stages), the CTAs' runs interleaved so that the CTAs
+    // working at one time stay close in the list (tiles shared through L2)
+    constexpr int kRun = MODE == 1 ? 4 : 1;
+    auto item_at = [&](int64_t k) -> int64_t {
+        if (MODE == 3) return k;
+        return ((k / kRun) * (int64_t)gridDim.x + blockIdx.x) * kRun + (k % kRun);
+    };
+    // item_at(k + 1) from g = item_at(k)
+    auto next_item = [&](int64_t k, int64_t g) -> int64_t {
+        if (kRun == 1) return g + g_step;
+        return ((k + 1) % kRun) ? g + 1 : g + ((int64_t)gridDim.x - 1) * kRun + 1;
+    };
     // tiles of item g: (A, B0, B1 or -1)
     auto item = [&](int64_t g) -> int3 {
         if (MODE == 3) {
@@ -572,7 +586,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             int stage = 0;
             uint32_t phase = 0;
             int issued = 0;
-            for (int64_t g = g_begin; g < g_end && !*abort; g += g_step) {
+            // count pass: the (tile A, K block) whose A blocks each stage holds;
+            // a fill that needs the same ones leaves them in place
+            int64_t tag[MODE == 1 ? kStages : 1];
+#pragma unroll
+            for (int i = 0; i < (MODE == 1 ? kStages : 1); ++i) tag[i] = -1;
+            constexpr int nA = NS == 3 ? 2 : 1;                 // A blocks per stage (hi, lo)
+            for (int64_t k = 0, g = kRun == 1 ? g_begin : item_at(0); g < g_end && !*abort; g = next_item(k, g), ++k) {
                 const int3 itm = item(g);
                 const int2 tp = make_int2(itm.x, itm.y);
                 const bool diag = W == 1 && tp.x == tp.y;
@@ -583,21 +603,27 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 for (int kb = 0; kb < P.nkb; ++kb) {
                     if (!mbar_wait(&S.empty[stage], phase ^ 1, abort)) break;
                     unsigned char* st = smem + stage * kStageBytes;
-                    mbar_expect_tx(&S.full[stage], bytes);
+                    bool keepA = false;
+                    if constexpr (MODE == 1) {
+                        const int64_t want = (int64_t)tp.x * 4096 + kb;
+                        keepA = tag[stage] == want;
+                        tag[stage] = want;
+                    }
+                    mbar_expect_tx(&S.full[stage], keepA ? bytes - (uint32_t)(nA * kBlk) : bytes);
                     if (W == 1) {
-                        tma_load(st, &mAh, kb * kKB, tp.x * kT, &S.full[stage]);
+                        if (!keepA) tma_load(st, &mAh, kb * kKB, tp.x * kT, &S.full[stage]);
                         if (!diag) tma_load(st + kBlk, &mAh, kb * kKB, tp.y * kT, &S.full[stage]);
                         if (NS == 3) {
-                            tma_load(st + 2 * kBlk, &mAl, kb * kKB, tp.x * kT, &S.full[stage]);
+                            if (!keepA) tma_load(st + 2 * kBlk, &mAl, kb * kKB, tp.x * kT, &S.full[stage]);
                             if (!diag) tma_load(st + 3 * kBlk, &mAl, kb * kKB, tp.y * kT, &S.full[stage]);
                         }
                     } else {
                         constexpr int bo = NS == 3 ? 2 : 1;      // first B block
-                        tma_load(st, &mAh, kb * kKB, tp.x * kT, &S.full[stage]);
+                        if (!keepA) tma_load(st, &mAh, kb * kKB, tp.x * kT, &S.full[stage]);
                         tma_load(st + bo * kBlk, &mAh, kb * kKB, tp.y * kT, &S.full[stage]);
                         if (nbt == 2) tma_load(st + (bo + 1) * kBlk, &mAh, kb * kKB, tb1 * kT, &S.full[stage]);
                         if (NS == 3) {
-                            tma_load(st + kBlk, &mAl, kb * kKB, tp.x * kT, &S.full[stage]);
+                            if (!keepA) tma_load(st + kBlk, &mAl, kb * kKB, tp.x * kT, &S.full[stage]);
                             tma_load(st + 4 * kBlk, &mAl, kb * kKB, tp.y * kT, &S.full[stage]);
                             if (nbt == 2) tma_load(st + 5 * kBlk, &mAl, kb * kKB, tb1 * kT, &S.full[stage]);
                         }
@@ -625,7 +651,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             int stage = 0;
             uint32_t phase = 0;
             int it = 0;
-            for (int64_t g = g_begin; g < g_end && !*abort; g += g_step, ++it) {
+            for (int64_t k = 0, g = kRun == 1 ? g_begin : item_at(0); g < g_end && !*abort;
+                 g = next_item(k, g), ++k, ++it) {
                 const int3 itm = item(g);
                 const bool diag = W == 1 && itm.x == itm.y;
                 const uint32_t idesc = F ? (W == 2 && itm.z >= 0 ? kIdescF8x2 : kIdescF8)
@@ -881,10 +908,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
         int git = 0;
         Item cur;
         Head head;
-        if ((int64_t)blockIdx.x < n_items) load_head(blockIdx.x, head);
-        for (int64_t g = blockIdx.x; g < n_items; g += gridDim.x, ++git) {
+        int64_t g = item_at(0), g_next = 0;
+        if (g < n_items) load_head(g, head);
+        for (int64_t k = 0; g < n_items; ++k, ++git, g = g_next) {
+            g_next = next_item(k, g);
             load_item(head, cur);
-            if (g + gridDim.x < n_items) load_head(g + gridDim.x, head);
+            if (g_next < n_items) load_head(g_next, head);
             const int tbuf = git & 1;
             const bool bad = !mbar_wait(&S.acc_full[tbuf], (uint32_t)((git >> 1) & 1), abort) || *abort;
             if (__any_sync(0xffffffffu, bad)) break;
