@@ -187,7 +187,7 @@ int run_density(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
 
 int run_lens(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld, int32_t m,
              const int32_t* kinds, const int32_t* args, const double* lens_param, int32_t precision,
-             double* lens_dev, Buf* pca_dev, int64_t* n_pca)
+             double* lens_dev, Buf* pca_dev, int64_t* n_pca, PivotSet* split = nullptr)
 {
     cudaStream_t s = ctx->stream->s;
     int K = 0;
@@ -213,7 +213,13 @@ int run_lens(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld, 
         *n_pca = (int64_t)d * (K + 1);
     }
     for (int j = 0; j < m; ++j) {
-        if (kinds[j] == MAPPER_LENS_L2) CK(lens_l2(X, n, d, ld, lens_dev, m, j, s), "lens_l2");
+        if (kinds[j] == MAPPER_LENS_L2 && split) {
+            // the first L2 lens also writes the points' split for the pivot assignment
+            const int dp = (d + 31) / 32 * 32;
+            CK(lens_l2_split(X, n, d, ld, lens_dev, m, j, split->c.as<float>(), dp, split->xh.p,
+                             split->xn2.as<float>(), s), "lens_l2");
+            split = nullptr;
+        } else if (kinds[j] == MAPPER_LENS_L2) CK(lens_l2(X, n, d, ld, lens_dev, m, j, s), "lens_l2");
         else if (kinds[j] == MAPPER_LENS_COORD)
             CK(lens_coord(X, n, ld, args[j], lens_dev, m, j, s), "lens_coord");
         else if (kinds[j] == MAPPER_LENS_ECC)
@@ -1650,7 +1656,7 @@ int mapper_knn_distance(mapper_ctx* ctx, const float* X_dev, int64_t n, int32_t 
 constexpr int kLensChunks = 8;
 
 int copy_rows_with_lens(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld, const mapper_params* p,
-                        float* xdev, double* lens, bool* lens_done)
+                        float* xdev, double* lens, bool* lens_done, const PivotSet* split)
 {
     cudaStream_t s = ctx->stream->s;
     *lens_done = false;
@@ -1694,11 +1700,18 @@ int copy_rows_with_lens(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, i
         CK(copy(r0, rows, cs), "copy X");
         CK(cudaEventRecord(ev[c], cs), "event");
         CK(cudaStreamWaitEvent(s, ev[c], 0), "wait");
+        bool split_done = false;
         for (int j = 0; j < p->m; ++j) {
             const int k = p->lens_kind[j];
             const float* xr = xdev + r0 * d;
             double* f = lens + r0 * p->m;
-            if (k == MAPPER_LENS_L2) CK(lens_l2(xr, rows, d, d, f, p->m, j, s), "lens_l2");
+            if (k == MAPPER_LENS_L2 && split && !split_done) {
+                const int dp = (d + 31) / 32 * 32;
+                CK(lens_l2_split(xr, rows, d, d, f, p->m, j, split->c.as<float>(), dp,
+                                 static_cast<uint16_t*>(split->xh.p) + r0 * dp, split->xn2.as<float>() + r0, s),
+                   "lens_l2");
+                split_done = true;
+            } else if (k == MAPPER_LENS_L2) CK(lens_l2(xr, rows, d, d, f, p->m, j, s), "lens_l2");
             else if (k == MAPPER_LENS_LINF) CK(lens_linf(xr, rows, d, d, f, p->m, j, s), "lens_linf");
             else CK(lens_coord(xr, rows, d, p->lens_arg[j], f, p->m, j, s), "lens_coord");
         }
@@ -1733,17 +1746,32 @@ int mapper_graph(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t 
     const float* Xd = X;
     int64_t ldd = ld;
     bool lens_done = false;
+    // tensor-core graphs with an L2 lens: the lens pass also writes the
+    // points' split for the pivot assignment of the tile layout
+    bool has_l2 = false;
+    for (int j = 0; j < p->m; ++j) has_l2 |= p->lens_kind[j] == MAPPER_LENS_L2;
+    const bool fuse_split = has_l2 && p->precision != MAPPER_FP32 && d <= 32768;
+    PivotSet piv;
+    const int dp = (d + 31) / 32 * 32;
+    if (fuse_split) {
+        CK(pivot_alloc(n, dp, &piv, s), "alloc pivots");
+        if ((rc = pivot_prepare(X, n, d, ld, dp, is_host_pointer(X), &piv, s))) return rc;
+    }
     if (is_host_pointer(X)) {
         CK(xdev.alloc(sizeof(float) * (size_t)n * d, s), "alloc X");
         Xd = xdev.as<float>();
         ldd = d;
-        if ((rc = copy_rows_with_lens(ctx, X, n, d, ld, p, xdev.as<float>(), g->lens.as<double>(), &lens_done)))
+        if ((rc = copy_rows_with_lens(ctx, X, n, d, ld, p, xdev.as<float>(), g->lens.as<double>(), &lens_done,
+                                      fuse_split ? &piv : nullptr)))
             return rc;
     }
-    if (!lens_done &&
-        (rc = run_lens(ctx, Xd, n, d, ldd, p->m, p->lens_kind, p->lens_arg, p->lens_param, p->precision,
-                       g->lens.as<double>(), &g->pca, &g->n_pca)))
-        return rc;
+    bool split_written = fuse_split && lens_done;
+    if (!lens_done) {
+        if ((rc = run_lens(ctx, Xd, n, d, ldd, p->m, p->lens_kind, p->lens_arg, p->lens_param, p->precision,
+                           g->lens.as<double>(), &g->pca, &g->n_pca, fuse_split ? &piv : nullptr)))
+            return rc;
+        split_written = fuse_split;
+    }
     tm.mark();
     std::shared_ptr<CoverData> cov;
     if (p->cover_kind != MAPPER_COVER_UNIFORM && p->cover_kind != MAPPER_COVER_BALANCED)
@@ -1752,7 +1780,10 @@ int mapper_graph(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t 
                         flag.as<int>(), p->cover_kind == MAPPER_COVER_BALANCED))) return rc;
     tm.mark();
     std::shared_ptr<ClusterData> cl;
-    if ((rc = run_cluster(ctx, Xd, n, d, ldd, cov, p->eps, p->min_pts, p->precision, &cl, flag.as<int>())))
+    // the pivot assignment on the points split by the lens pass
+    if (split_written && (rc = pivot_assign(Xd, n, d, ldd, dp, true, ctx->num_sms, &piv, s))) return rc;
+    if ((rc = run_cluster(ctx, Xd, n, d, ldd, cov, p->eps, p->min_pts, p->precision, &cl, flag.as<int>(), nullptr,
+                          nullptr, split_written ? &piv : nullptr)))
         return rc;
     tm.mark();
     g->clusters = cl;

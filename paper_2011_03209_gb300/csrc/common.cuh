@@ -102,6 +102,11 @@ bool knn_on_tensor_cores(int32_t k, bool tensor_cores);
 // L-infinity centrality f(x) = max_y |x - y| into f[p * m + j]; a mapper_status.
 int lens_ecc_inf(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j, int num_sms,
                  bool tensor_cores, cudaStream_t s);
+// lens_l2 that also writes, for the pivot assignment, the rows x - c rounded to
+// BF16 (xh: n rows of pitch dp, columns d .. dp zero) and |x - c|^2 in FP32
+// (xn2); d <= 32768 (else cudaErrorInvalidValue).
+cudaError_t lens_l2_split(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j,
+                          const float* c, int dp, void* xh, float* xn2, cudaStream_t s);
 cudaError_t lens_coord(const float* X, int64_t n, int64_t ld, int32_t col, double* f, int m,
                        int j, cudaStream_t s);
 cudaError_t lens_linf(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j,

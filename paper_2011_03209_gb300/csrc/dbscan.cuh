@@ -204,12 +204,21 @@ struct PairLists {
 struct PivotSet {
     int K = 0;
     Buf Pv, piv, pd2;
+    // set by pivot_prepare: the pivots' centre c and the points' split for
+    // the tensor-core assignment (written by the lens pass, lens_l2_split)
+    bool split = false;
+    Buf c, xh, xn2;
 };
 // Allocates the set on stream `alloc_s` (where it is later freed) and
 // computes it on stream `s` (which must wait for alloc_s).
 cudaError_t pivot_alloc(int64_t n, int dp, PivotSet* P, cudaStream_t alloc_s);
 int pivot_assign(const float* X, int64_t n, int32_t d, int64_t ld, int dp, bool bf16, int num_sms, PivotSet* P,
                  cudaStream_t s);
+// Before the lens pass (P from pivot_alloc): the pivot rows (X's rows
+// k n / K; X in host memory when `host`), their FP32 centre c, and room for the
+// points' BF16 split (rows past n zeroed), which lens_l2_split then writes;
+// pivot_assign afterwards skips its own split. A mapper_status.
+int pivot_prepare(const float* X, int64_t n, int32_t d, int64_t ld, int dp, bool host, PivotSet* P, cudaStream_t s);
 
 // Orders every element's points by pivot group, lays them out in tiles
 // (a tile never mixes groups) and gathers rows. tau: distance under which two

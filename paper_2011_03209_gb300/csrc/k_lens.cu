@@ -8,6 +8,8 @@
 // expression; the L2 lens rounds the exact sum of squares once. Rows are staged
 // through shared memory so the loads stay coalesced while every thread walks
 // its own row in order.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace mgb {
@@ -108,13 +110,20 @@ __device__ __forceinline__ unsigned long long mad_wide(uint32_t a, unsigned long
 
 constexpr int kL2Per = 8;                     // values per lane per 256-column chunk
 
-__device__ __forceinline__ void l2_load(const float* __restrict__ x, int k0, int d, int lane, unsigned* v)
+// lane l takes columns k0 + 8 l .. k0 + 8 l + 7 of the chunk (two 16-byte
+// loads when the row allows; the exact sum does not depend on the order)
+__device__ __forceinline__ void l2_load(const float* __restrict__ x, int k0, int d, int lane, unsigned* v, bool vec)
 {
-#pragma unroll
-    for (int i = 0; i < kL2Per; ++i) {
-        const int k = k0 + i * 32 + lane;
-        v[i] = k < d ? __float_as_uint(__ldg(x + k)) : 0u;
+    const int k = k0 + kL2Per * lane;
+    if (vec && k + kL2Per <= d) {
+        const uint4 a = __ldg(reinterpret_cast<const uint4*>(x + k));
+        const uint4 b = __ldg(reinterpret_cast<const uint4*>(x + k + 4));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        return;
     }
+#pragma unroll
+    for (int i = 0; i < kL2Per; ++i) v[i] = k + i < d ? __float_as_uint(__ldg(x + k + i)) : 0u;
 }
 
 // sqrt of (hi 2^64 + lo) 2^(2 emax - 364): the 128-bit value rounded once
@@ -153,13 +162,19 @@ __device__ __forceinline__ int lane_emax(const unsigned* v, int* raw)
 
 // A warp sums 32 rows in turn (all lanes on one row), lane i keeps row i's
 // sum, and the 32 double conversions and square roots then run side by side.
+// SPLIT: the same pass also writes the rows for the pivot assignment, x - c
+// rounded to BF16 (pitch dp, zero padded) and |x - c|^2 in FP32.
+template <bool SPLIT>
 __global__ void __launch_bounds__(256) lens_l2_exact_kernel(const float* __restrict__ X, int64_t n, int32_t d,
-                                                            int64_t ld, double* __restrict__ f, int m, int j)
+                                                            int64_t ld, double* __restrict__ f, int m, int j,
+                                                            const float* __restrict__ c, int dp,
+                                                            __nv_bfloat16* __restrict__ xh, float* __restrict__ xn2)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const bool one_chunk = d <= 32 * kL2Per;
+    const bool vec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
     for (int64_t r0 = warp * 32; r0 < n; r0 += nwarp * 32) {
         unsigned long long my_hi = 0ull, my_lo = 0ull;
         int my_emax = 1;
@@ -170,7 +185,7 @@ __global__ void __launch_bounds__(256) lens_l2_exact_kernel(const float* __restr
             unsigned v[kL2Per];
             int emax = 1, raw_max = 0;
             for (int k0 = 0; k0 < d; k0 += 32 * kL2Per) {
-                l2_load(x, k0, d, lane, v);
+                l2_load(x, k0, d, lane, v, vec);
                 int raw;
                 emax = max(emax, lane_emax(v, &raw));
                 raw_max = max(raw_max, raw);
@@ -179,7 +194,7 @@ __global__ void __launch_bounds__(256) lens_l2_exact_kernel(const float* __restr
             unsigned special = 0u;                                 // 1: an Inf, 2: a NaN
             if (__any_sync(0xffffffffu, raw_max == 255)) {
                 for (int k0 = 0; k0 < d; k0 += 32 * kL2Per) {
-                    l2_load(x, k0, d, lane, v);
+                    l2_load(x, k0, d, lane, v, vec);
 #pragma unroll
                     for (int t = 0; t < kL2Per; ++t)
                         if (((v[t] >> 23) & 0xFFu) == 0xFFu) special |= (v[t] & 0x7FFFFFu) ? 2u : 1u;
@@ -187,8 +202,9 @@ __global__ void __launch_bounds__(256) lens_l2_exact_kernel(const float* __restr
                 special = __reduce_or_sync(0xffffffffu, special);
             }
             unsigned long long hi = 0ull, lo = 0ull;
+            float n2 = 0.f;
             for (int k0 = 0; k0 < d && !special; k0 += 32 * kL2Per) {
-                if (!one_chunk) l2_load(x, k0, d, lane, v);
+                if (!one_chunk) l2_load(x, k0, d, lane, v, vec);
                 int raw;
                 const int el = lane_emax(v, &raw);
                 unsigned long long s1 = 0ull, s2 = 0ull;
@@ -211,6 +227,32 @@ __global__ void __launch_bounds__(256) lens_l2_exact_kernel(const float* __restr
                 }
                 add128_shifted(hi, lo, s1, 52 - 2 * (emax - el));
                 add128_shifted(hi, lo, s2, 38 - 2 * (emax - el));
+                if constexpr (SPLIT) {
+                    const int col0 = k0 + kL2Per * lane;
+                    float a[kL2Per];
+#pragma unroll
+                    for (int t = 0; t < kL2Per; ++t) {
+                        a[t] = col0 + t < d ? __uint_as_float(v[t]) - c[col0 + t] : 0.f;
+                        n2 = fmaf(a[t], a[t], n2);
+                    }
+                    __nv_bfloat16* dst = xh + (r0 + i) * dp + col0;
+                    if (col0 + kL2Per <= dp) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int t = 0; t < kL2Per; t += 2) {
+                            const __nv_bfloat162 h = __floats2bfloat162_rn(a[t], a[t + 1]);
+                            w[t >> 1] = *reinterpret_cast<const uint32_t*>(&h);
+                        }
+                        *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+                    } else {
+                        for (int t = 0; t < kL2Per && col0 + t < dp; ++t) dst[t] = __float2bfloat16_rn(a[t]);
+                    }
+                }
+            }
+            if constexpr (SPLIT) {
+#pragma unroll
+                for (int o = 16; o; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+                if (lane == 0) xn2[r0 + i] = n2;
             }
 #pragma unroll
             for (int o = 16; o; o >>= 1) {
@@ -503,13 +545,25 @@ __global__ void __launch_bounds__(1024) power_iter_kernel(const double* __restri
 
 }  // namespace
 
+cudaError_t lens_l2_split(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j,
+                          const float* c, int dp, void* xh, float* xn2, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    if (d > 32768) return cudaErrorInvalidValue;
+    const int blocks = (int)std::min<int64_t>(div_up(n, 8 * 32), 152 * 8);
+    lens_l2_exact_kernel<true><<<blocks, 256, 0, s>>>(X, n, d, ld, f, m, j, c, dp,
+                                                      static_cast<__nv_bfloat16*>(xh), xn2);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t lens_l2(const float* X, int64_t n, int32_t d, int64_t ld, double* f, int m, int j,
                     cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
     if (d <= 32768) {
         const int blocks = (int)std::min<int64_t>(div_up(n, 8 * 32), 152 * 8);
-        lens_l2_exact_kernel<<<blocks, 256, 0, s>>>(X, n, d, ld, f, m, j);
+        lens_l2_exact_kernel<false><<<blocks, 256, 0, s>>>(X, n, d, ld, f, m, j, nullptr, 0, nullptr, nullptr);
     } else {
         lens_rows_kernel<0><<<div_up(n, kRows), kRows, 0, s>>>(X, n, d, ld, nullptr, nullptr, f, m, j);
     }

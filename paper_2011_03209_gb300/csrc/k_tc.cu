@@ -1930,7 +1930,7 @@ int tc_groups_dev(const int2* pairs, int64_t n, const unsigned long long* n_dev,
 }
 
 int assign_pivots_tc(const float* X, int64_t n, int d, int64_t ld, int dp, const float* Pv, int K,
-                     int num_sms, int32_t* piv, float* pd2, cudaStream_t s)
+                     int num_sms, int32_t* piv, float* pd2, cudaStream_t s, const PivotSplit* pre)
 {
     if (K > kPivN) { set_error("assign_pivots_tc: more than 256 pivots"); return MAPPER_EINVAL; }
     const int64_t n_tiles = (n + kT - 1) / kT, rows = n_tiles * kT;
@@ -1943,23 +1943,32 @@ int assign_pivots_tc(const float* X, int64_t n, int d, int64_t ld, int dp, const
             return e_ == cudaErrorMemoryAllocation ? MAPPER_ENOMEM : MAPPER_ECUDA;       \
         }                                                                                \
     } while (0)
-    AK(c.alloc(sizeof(float) * dp, s));
-    AK(xh.alloc(sizeof(__nv_bfloat16) * (size_t)rows * dp, s));
-    AK(xn2.alloc(sizeof(float) * rows, s));
     AK(ph.alloc(sizeof(__nv_bfloat16) * (size_t)kPivN * dp, s));
     AK(pn2.alloc(sizeof(float) * kPivN, s));
     AK(err.alloc(sizeof(int), s));
     AK(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-    mean_rows_kernel<<<1, 256, 0, s>>>(Pv, K, dp, c.as<float>());
-    const bool vec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
-    split_rows_kernel<<<num_sms * 8, 256, 0, s>>>(X, n, d, ld, dp, c.as<float>(), rows, xh.as<__nv_bfloat16>(),
-                                                  xn2.as<float>(), 0.f, vec);
-    split_rows_kernel<<<8, 256, 0, s>>>(Pv, K, d, dp, dp, c.as<float>(), kPivN, ph.as<__nv_bfloat16>(),
-                                        pn2.as<float>(), INFINITY, true);
-    note_launch(3);
+    const float* cc = pre ? pre->c : nullptr;
+    const void* xhp = pre ? pre->xh : nullptr;
+    const float* xn2p = pre ? pre->xn2 : nullptr;
+    if (!pre) {
+        AK(c.alloc(sizeof(float) * dp, s));
+        AK(xh.alloc(sizeof(__nv_bfloat16) * (size_t)rows * dp, s));
+        AK(xn2.alloc(sizeof(float) * rows, s));
+        mean_rows_kernel<<<1, 256, 0, s>>>(Pv, K, dp, c.as<float>());
+        const bool vec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
+        split_rows_kernel<<<num_sms * 8, 256, 0, s>>>(X, n, d, ld, dp, c.as<float>(), rows,
+                                                      xh.as<__nv_bfloat16>(), xn2.as<float>(), 0.f, vec);
+        note_launch(2);
+        cc = c.as<float>();
+        xhp = xh.p;
+        xn2p = xn2.as<float>();
+    }
+    split_rows_kernel<<<8, 256, 0, s>>>(Pv, K, d, dp, dp, cc, kPivN, ph.as<__nv_bfloat16>(), pn2.as<float>(),
+                                        INFINITY, true);
+    note_launch();
     AK(cudaGetLastError());
     CUtensorMap mxh, mph;
-    if (!make_map(&mxh, xh.p, rows, dp) || !make_map(&mph, ph.p, kPivN, dp, kPivN)) {
+    if (!make_map(&mxh, xhp, rows, dp) || !make_map(&mph, ph.p, kPivN, dp, kPivN)) {
         set_error("cuTensorMapEncodeTiled failed (or is unavailable)");
         return MAPPER_ECUDA;
     }
@@ -1967,7 +1976,7 @@ int assign_pivots_tc(const float* X, int64_t n, int d, int64_t ld, int dp, const
     p.n = n;
     p.n_tiles = n_tiles;
     p.nkb = (dp + kKB - 1) / kKB;
-    p.xn2 = xn2.as<float>();
+    p.xn2 = xn2p;
     p.pn2 = pn2.as<float>();
     p.piv = piv;
     p.pd2 = pd2;

@@ -51,6 +51,16 @@ __global__ void pivot_gather_kernel(const float* __restrict__ X, int64_t n, int 
     for (int j = threadIdx.x; j < dp; j += blockDim.x) Pv[(int64_t)k * dp + j] = j < d ? X[p * ld + j] : 0.f;
 }
 
+// c[k] = the FP32 sum of the K pivots' column k in pivot order, / K
+__global__ void pivot_mean_kernel(const float* __restrict__ Pv, int K, int dp, float* __restrict__ c)
+{
+    for (int k = threadIdx.x; k < dp; k += blockDim.x) {
+        float s = 0.f;
+        for (int i = 0; i < K; ++i) s += Pv[(int64_t)i * dp + k];
+        c[k] = s / (float)K;
+    }
+}
+
 // Nearest pivot of every point (FP32 distances; ties to the lower index).
 // CTA: 128 points x 128 pivots per step, 32 dimensions staged at a time.
 __global__ void __launch_bounds__(256, 2) assign_kernel(const float* __restrict__ X, int64_t n, int d,
@@ -977,11 +987,14 @@ int pivot_assign(const float* X, int64_t n, int32_t d, int64_t ld, int dp, bool 
                  cudaStream_t s)
 {
     const int K = P->K;
-    pivot_gather_kernel<<<K, 128, 0, s>>>(X, n, d, ld, dp, K, P->Pv.as<float>());
-    note_launch();
+    if (!P->split) {
+        pivot_gather_kernel<<<K, 128, 0, s>>>(X, n, d, ld, dp, K, P->Pv.as<float>());
+        note_launch();
+    }
     if (bf16) {
+        const PivotSplit pre{P->c.as<float>(), P->xh.p, P->xn2.as<float>()};
         const int rc = assign_pivots_tc(X, n, d, ld, dp, P->Pv.as<float>(), K, num_sms, P->piv.as<int32_t>(),
-                                        P->pd2.as<float>(), s);
+                                        P->pd2.as<float>(), s, P->split ? &pre : nullptr);
         if (rc) return rc;
     } else {
         assign_kernel<<<grid_for(n, kT), 256, 0, s>>>(X, n, d, ld, P->Pv.as<float>(), dp, K, P->piv.as<int32_t>(),
@@ -994,6 +1007,51 @@ int pivot_assign(const float* X, int64_t n, int32_t d, int64_t ld, int dp, bool 
         return MAPPER_ECUDA;
     }
     return MAPPER_OK;
+}
+
+int pivot_prepare(const float* X, int64_t n, int32_t d, int64_t ld, int dp, bool host, PivotSet* P, cudaStream_t s)
+{
+#define PK(expr)                                                                      \
+    do {                                                                              \
+        cudaError_t e_ = (expr);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            set_error(std::string("pivot_prepare: ") + cudaGetErrorString(e_));       \
+            return e_ == cudaErrorMemoryAllocation ? MAPPER_ENOMEM : MAPPER_ECUDA;    \
+        }                                                                             \
+    } while (0)
+    const int K = P->K;
+    const int64_t rows = div_up(n, kT) * kT;
+    PK(P->c.alloc(sizeof(float) * dp, s));
+    PK(P->xh.alloc(sizeof(uint16_t) * (size_t)rows * dp, s));
+    PK(P->xn2.alloc(sizeof(float) * rows, s));
+    if (rows > n) {
+        PK(cudaMemsetAsync(static_cast<uint16_t*>(P->xh.p) + n * dp, 0, sizeof(uint16_t) * (size_t)(rows - n) * dp, s));
+        PK(cudaMemsetAsync(P->xn2.as<float>() + n, 0, sizeof(float) * (rows - n), s));
+    }
+    if (!host) {
+        pivot_gather_kernel<<<K, 128, 0, s>>>(X, n, d, ld, dp, K, P->Pv.as<float>());
+        pivot_mean_kernel<<<1, 256, 0, s>>>(P->Pv.as<float>(), K, dp, P->c.as<float>());
+        note_launch(2);
+        PK(cudaGetLastError());
+    } else {
+        // the same rows and sums on the host (X there); two pageable copies
+        std::vector<float> pv((size_t)K * dp, 0.f), c(dp, 0.f);
+        for (int k = 0; k < K; ++k) {
+            const float* x = X + ((int64_t)k * n / K) * ld;
+            for (int j = 0; j < d; ++j) pv[(size_t)k * dp + j] = x[j];
+        }
+        for (int j = 0; j < dp; ++j) {
+            float sum = 0.f;
+            for (int k = 0; k < K; ++k) sum += pv[(size_t)k * dp + j];
+            c[j] = sum / (float)K;
+        }
+        PK(cudaMemcpyAsync(P->Pv.p, pv.data(), sizeof(float) * pv.size(), cudaMemcpyHostToDevice, s));
+        PK(cudaMemcpyAsync(P->c.p, c.data(), sizeof(float) * dp, cudaMemcpyHostToDevice, s));
+        PK(cudaStreamSynchronize(s));                  // the host vectors go out of scope
+    }
+    P->split = true;
+    return MAPPER_OK;
+#undef PK
 }
 
 int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const int32_t* slot_point,

@@ -74,9 +74,16 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
 // Nearest of K <= 256 pivots (rows of Pv, pitch dp) for every point of X, on
 // tensor cores (rows centred and rounded to BF16, one MMA of N = 256 per 16
 // columns); near ties may resolve either way, which only orders the layout.
-// Returns a mapper_status.
+// pre (nullable): the points already centred on c and split (xh: BF16 rows
+// of pitch dp, n_tiles * 128 of them, the rows past n zero; xn2: |x - c|^2),
+// c (dp floats) being the pivots' centre of this call. Returns a mapper_status.
+struct PivotSplit {
+    const float* c;
+    const void* xh;
+    const float* xn2;
+};
 int assign_pivots_tc(const float* X, int64_t n, int d, int64_t ld, int dp, const float* Pv, int K,
-                     int num_sms, int32_t* piv, float* pd2, cudaStream_t s);
+                     int num_sms, int32_t* piv, float* pd2, cudaStream_t s, const PivotSplit* pre = nullptr);
 
 // Entries per list of the k-distance tensor-core screen (k <= this).
 constexpr int kKnnList = 8;
