@@ -250,6 +250,26 @@ def test_host_input_equals_device_input(ctx, kinds, args, pinned):
     assert np.array_equal(la, lb)
 
 
+def test_host_strided_input_equals_device_input(ctx):
+    """Host rows with a pitch above d (a column slice of a wider CPU tensor)
+    take the two-dimensional chunked copy; the graph and the lens equal those
+    of the device input."""
+    X = synth.gaussian_mixture(4099, 13, 4, seed=83, centre_box=5.0, std_lo=0.5, std_hi=1.0,
+                               anisotropic=False)
+    wide = np.zeros((X.shape[0], 16), dtype=np.float32)
+    wide[:, :13] = X
+    eps = _eps(X, 5, 83)
+    prm = mg.params((0,), (0,), (8,), (0.3,), eps, 5, mg.BF16)
+    dev = mg.mapper_graph(ctx, torch.from_numpy(X).to("cuda:0"), prm)
+    hst = mg.mapper_graph(ctx, torch.from_numpy(wide)[:, :13], prm)
+    a, b = dev.numpy(), hst.numpy()
+    for k in ("node_offsets", "node_members", "node_elem", "edges"):
+        assert np.array_equal(a[k], b[k]), k
+    la, _ = dev.lens(X.shape[0], 1)
+    lb, _ = hst.lens(X.shape[0], 1)
+    assert np.array_equal(la, lb)
+
+
 def test_pca_lens_basis_and_bits(ctx):
     X = synth.gaussian_mixture(6000, 12, 5, seed=4, centre_box=5.0, std_lo=0.3, std_hi=1.5,
                                anisotropic=True)
