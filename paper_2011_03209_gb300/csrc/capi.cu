@@ -1,6 +1,7 @@
 // capi.cu -- the C ABI (include/mapper.h) and the host side of the pipeline:
 // argument checks, handle ownership, stream-ordered scratch, size read-backs,
 // and the order of the kernel launches of each step.
+#include <algorithm>
 #include <cfloat>
 #include <cstdio>
 #include <cstdlib>
@@ -347,6 +348,10 @@ int sample_deferral(const mapper_ctx* ctx, const PassArgs& a, const TcArgs& firs
     as.pair_hit = hit.as<uint8_t>();
     as.stats = st.as<unsigned long long>();
     TcArgs ts = first;
+    // several radii: every radius writes the same scratch outputs
+    for (int e = 0; e < ts.n_radii; ++e)
+        ts.radii[e] = RadiusOut{cnt.as<int32_t>(), nbr.as<int32_t>(), hit.as<uint8_t>(), q.as<uint2>(),
+                                qn.as<unsigned long long>(), st.as<unsigned long long>(), ts.radii[e].eps2};
     if (!ts.f8) ts.ns = 1;
     ts.defer = true;
     ts.defer_mixed = true;
@@ -361,7 +366,7 @@ int sample_deferral(const mapper_ctx* ctx, const PassArgs& a, const TcArgs& firs
     ts.groups_dev = nullptr;
     ts.n_dev = nullptr;
     ts.ev_begin = ts.ev_end = nullptr;
-    if ((rc = tc_pass(1, as, ts, n_s, s))) return rc;
+    if ((rc = tc_pass(ts.n_radii > 0 ? 5 : 1, as, ts, n_s, s))) return rc;
     unsigned long long h_redo = 0;
     int h_err = 0;
     CK(cudaMemcpyAsync(&h_redo, st.as<unsigned long long>() + kStatRedo, sizeof(h_redo), cudaMemcpyDeviceToHost, s),
@@ -480,17 +485,32 @@ struct CountsOut {
     int m, j;
 };
 
-int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
-                const std::shared_ptr<CoverData>& cov, double eps, int32_t min_pts, int32_t precision,
-                std::shared_ptr<ClusterData>* out, int* nonfinite_dev, TileLayout* layout = nullptr,
-                const CountsOut* counts_out = nullptr, const PivotSet* pivots = nullptr)
+// The same for n_radii radii eps[0] < eps[1] < .. of one cover (at most
+// kMaxRadii; one radius unless the screen runs on BF16 tensor cores): one tile
+// layout and one classification (pairs all out at the largest radius dropped,
+// all in at the smallest counted without distances), one count pass over the
+// mixed pairs for every radius (mode 5 of tc_pass), then the unions, border
+// rows and labels of each radius. outs[e] receives radius e's clusters.
+int run_cluster_radii(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
+                      const std::shared_ptr<CoverData>& cov, int n_radii, const double* eps_list, int32_t min_pts,
+                      int32_t precision, std::shared_ptr<ClusterData>* outs, int* nonfinite_dev,
+                      TileLayout* layout = nullptr, const CountsOut* counts_out = nullptr,
+                      const PivotSet* pivots = nullptr)
 {
-    if (!(eps > 0.0) || !std::isfinite(eps)) return fail(MAPPER_EINVAL, "eps must be finite and > 0");
+    if (n_radii < 1 || n_radii > kMaxRadii) return fail(MAPPER_EINVAL, "bad number of radii");
+    for (int e = 0; e < n_radii; ++e) {
+        if (!(eps_list[e] > 0.0) || !std::isfinite(eps_list[e])) return fail(MAPPER_EINVAL, "eps must be finite and > 0");
+        if (e > 0 && !(eps_list[e] > eps_list[e - 1])) return fail(MAPPER_EINTERNAL, "radii not ascending");
+    }
     if (min_pts < 1) return fail(MAPPER_EINVAL, "min_pts must be >= 1");
     if (precision != MAPPER_FP32 && precision != MAPPER_BF16 && precision != MAPPER_BF16X1 &&
         precision != MAPPER_FP8)
         return fail(MAPPER_EINVAL, "unknown precision");
     if (cov->n != n) return fail(MAPPER_EINVAL, "cover was built for another point count");
+    const int K = n_radii;
+    if (K > 1 && (precision == MAPPER_FP32 || precision == MAPPER_FP8 || counts_out))
+        return fail(MAPPER_EINTERNAL, "several radii need the BF16 tensor-core screen");
+    const double eps_min = eps_list[0], eps_max = eps_list[K - 1];
     cudaStream_t s = ctx->stream->s;
     const int64_t M = cov->M, E = cov->E;
     const int dp = (d + 31) / 32 * 32;
@@ -498,14 +518,11 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     const int cap = (!counts_out && min_pts >= 2 && min_pts - 1 <= 64) ? min_pts - 1 : 0;
     const double rows_est = (double)M + 128.0 * (double)E;
     const double est = rows_est * dp * (use_tc ? (precision == MAPPER_FP8 ? 10.0 : 8.0) : 4.0) +
-                       rows_est * (40.0 + 4.0 * cap);
+                       K * rows_est * (40.0 + 4.0 * cap);
     if (ctx->budget && est > (double)ctx->budget)
         return fail(MAPPER_ENOMEM, "estimated scratch exceeds the context's HBM budget");
 
-    auto c = std::make_shared<ClusterData>();
-    c->stream = ctx->stream;
-    c->cover = cov;
-    mapper_stats& st = c->stats;
+    mapper_stats st{};                                            // shared by the radii
     st.n_points = n;
     st.n_elements = E;
     st.n_members = M;
@@ -516,9 +533,21 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     }
     st.sum_ni2 = s2;
 
-    Buf stats, flag;
-    CK(stats.alloc(sizeof(unsigned long long) * kStatCount, s), "alloc");
-    CK(cudaMemsetAsync(stats.p, 0, sizeof(unsigned long long) * kStatCount, s), "memset");
+    // per radius: outputs, counters and the pass arguments
+    struct Radius {
+        Buf stats, count, nbr, core, parent, root, border, hit_tc, hit_simt, queue, queue_n;
+        PassArgs a, a_in, a_tc, a_simt;
+    };
+    std::vector<Radius> rs(K);
+    Buf shared_stats, flag;                                       // K > 1: the count pass's own counters
+    for (int e = 0; e < K; ++e) {
+        CK(rs[e].stats.alloc(sizeof(unsigned long long) * kStatCount, s), "alloc");
+        CK(cudaMemsetAsync(rs[e].stats.p, 0, sizeof(unsigned long long) * kStatCount, s), "memset");
+    }
+    if (K > 1) {
+        CK(shared_stats.alloc(sizeof(unsigned long long) * kStatCount, s), "alloc");
+        CK(cudaMemsetAsync(shared_stats.p, 0, sizeof(unsigned long long) * kStatCount, s), "memset");
+    }
     int* nf = nonfinite_dev;
     if (!nf) {
         CK(flag.alloc(sizeof(int), s), "alloc");
@@ -532,7 +561,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     int rc = MAPPER_OK;
     if (!layout) {
         rc = build_tiles(X, n, d, ld, dp, cov->slot_point.as<int32_t>(), cov->slot_elem.as<int32_t>(), M, E,
-                         4.0 * eps, use_tc, ctx->num_sms, &own, nf, s, pivots);
+                         4.0 * eps_max, use_tc, ctx->num_sms, &own, nf, s, pivots);
         if (rc) return rc;
         layout = &own;
     }
@@ -542,7 +571,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     if (f8 && (rc = fp8_operands(layout, X, ld, d, dp, s))) return rc;
     const TileLayout& L = *layout;
     PairLists PL;
-    if ((rc = classify_pairs(L, X, ld, d, dp, E, eps, use_tc, &PL, s))) return rc;
+    if ((rc = classify_pairs(L, X, ld, d, dp, E, eps_max, use_tc, &PL, s, eps_min))) return rc;
     const int64_t R = L.R;
     st.tile_pairs = PL.n_candidates;
     st.tile_pairs_out = PL.n_out;
@@ -553,47 +582,53 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     if (PL.n[kListSimt] > INT32_MAX || PL.n[kListTC] > INT32_MAX || PL.n[kListAllIn] > INT32_MAX)
         return fail(MAPPER_ENOMEM, "too many tile pairs for one launch");
 
-    Buf count, nbr, core, parent, root, border;
-    CK(count.alloc(sizeof(int32_t) * R, s), "alloc");
-    CK(core.alloc(R, s), "alloc");
-    CK(parent.alloc(sizeof(int32_t) * R, s), "alloc");
-    CK(root.alloc(sizeof(int32_t) * R, s), "alloc");
-    CK(border.alloc(sizeof(unsigned long long) * R, s), "alloc");
-    if (cap) {
-        // every writer fills the slots below cap it reserves; -1 marks any left
-        CK(nbr.alloc(sizeof(int32_t) * (size_t)R * cap, s), "alloc");
-        CK(cudaMemsetAsync(nbr.p, 0xff, sizeof(int32_t) * (size_t)R * cap, s), "memset");
-    }
-    CK(cudaMemsetAsync(count.p, 0, sizeof(int32_t) * R, s), "memset");
-
-    PassArgs a{};
-    a.G = L.G.as<float>();
-    a.X = X;
-    a.ld = ld;
-    a.xvec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
-    a.dp = dp;
-    a.d = d;
-    a.tile_n = L.tile_n.as<int32_t>();
-    a.eps2 = eps * eps;
-    a.tie_thr = 1e-12 * a.eps2;
-    fp32_thresholds(a.eps2, d, &a.lo_thr, &a.hi_thr);
-    a.row_pt = L.row_pt.as<int32_t>();
-    a.count = count.as<int32_t>();
-    a.nbr = nbr.as<int32_t>();
-    a.cap = cap;
-    a.core = core.as<uint8_t>();
-    a.parent = parent.as<int32_t>();
-    a.root = root.as<int32_t>();
-    a.border = border.as<unsigned long long>();
-    a.stats = stats.as<unsigned long long>();
-    a.n_rows = R;
-    a.n_tiles = L.T;
     // Mixed tile pairs across two segments of one element have no common
     // centre; when they are many (a cover element holding scattered points,
     // whose tiles have wide spheres), they run on the tensor cores too, with
     // a second operand set centred per element, instead of on CUDA cores.
     const bool cross_tc = use_tc && PL.n[kListSimt] > 0 && ctx->cross_mode != 2 &&
                           (ctx->cross_mode == 1 || PL.n[kListSimt] * 32 >= R);
+    const unsigned long long queue_cap =
+        ctx->band_cap > 0 ? (unsigned long long)ctx->band_cap
+                          : (unsigned long long)std::min<int64_t>(
+                                int64_t(1) << 25, std::max<int64_t>(int64_t(1) << 20, 128 * PL.n[kListTC]));
+    for (int e = 0; e < K; ++e) {
+        Radius& rd = rs[e];
+        CK(rd.count.alloc(sizeof(int32_t) * R, s), "alloc");
+        CK(rd.core.alloc(R, s), "alloc");
+        CK(rd.parent.alloc(sizeof(int32_t) * R, s), "alloc");
+        CK(rd.root.alloc(sizeof(int32_t) * R, s), "alloc");
+        CK(rd.border.alloc(sizeof(unsigned long long) * R, s), "alloc");
+        if (cap) {
+            // every writer fills the slots below cap it reserves; -1 marks any left
+            CK(rd.nbr.alloc(sizeof(int32_t) * (size_t)R * cap, s), "alloc");
+            CK(cudaMemsetAsync(rd.nbr.p, 0xff, sizeof(int32_t) * (size_t)R * cap, s), "memset");
+        }
+        CK(cudaMemsetAsync(rd.count.p, 0, sizeof(int32_t) * R, s), "memset");
+        PassArgs& a = rd.a;
+        a = PassArgs{};
+        a.G = L.G.as<float>();
+        a.X = X;
+        a.ld = ld;
+        a.xvec = ld % 4 == 0 && ((uintptr_t)X & 15) == 0;
+        a.dp = dp;
+        a.d = d;
+        a.tile_n = L.tile_n.as<int32_t>();
+        a.eps2 = eps_list[e] * eps_list[e];
+        a.tie_thr = 1e-12 * a.eps2;
+        fp32_thresholds(a.eps2, d, &a.lo_thr, &a.hi_thr);
+        a.row_pt = L.row_pt.as<int32_t>();
+        a.count = rd.count.as<int32_t>();
+        a.nbr = rd.nbr.as<int32_t>();
+        a.cap = cap;
+        a.core = rd.core.as<uint8_t>();
+        a.parent = rd.parent.as<int32_t>();
+        a.root = rd.root.as<int32_t>();
+        a.border = rd.border.as<unsigned long long>();
+        a.stats = rd.stats.as<unsigned long long>();
+        a.n_rows = R;
+        a.n_tiles = L.T;
+    }
     // tensor-core pairs in (a, b) order: pairs sharing tile A form the
     // groups of the pass-1 kernel, and consecutive groups, which run on
     // neighbouring SMs at the same time, share tiles in L2
@@ -608,19 +643,29 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     }
     // pass 1 flags the screened tile pairs holding a neighbour pair; only
     // those can matter to the union pass
-    Buf hit_tc, hit_simt;
-    CK(hit_tc.alloc(std::max<int64_t>(PL.n[kListTC], 1), s), "alloc");
-    CK(hit_simt.alloc(std::max<int64_t>(PL.n[kListSimt], 1), s), "alloc");
-    CK(cudaMemsetAsync(hit_tc.p, 0, std::max<int64_t>(PL.n[kListTC], 1), s), "memset");
-    CK(cudaMemsetAsync(hit_simt.p, 0, std::max<int64_t>(PL.n[kListSimt], 1), s), "memset");
-    PassArgs a_in = a, a_tc = a, a_simt = a;
-    a_in.pairs = PL.list[kListAllIn].as<int2>();
-    a_tc.pairs = PL.list[kListTC].as<int2>();
-    a_tc.pair_hit = hit_tc.as<uint8_t>();
-    a_simt.pairs = PL.list[kListSimt].as<int2>();
-    a_simt.pair_hit = hit_simt.as<uint8_t>();
+    for (int e = 0; e < K; ++e) {
+        Radius& rd = rs[e];
+        CK(rd.hit_tc.alloc(std::max<int64_t>(PL.n[kListTC], 1), s), "alloc");
+        CK(rd.hit_simt.alloc(std::max<int64_t>(PL.n[kListSimt], 1), s), "alloc");
+        CK(cudaMemsetAsync(rd.hit_tc.p, 0, std::max<int64_t>(PL.n[kListTC], 1), s), "memset");
+        CK(cudaMemsetAsync(rd.hit_simt.p, 0, std::max<int64_t>(PL.n[kListSimt], 1), s), "memset");
+        rd.a_in = rd.a_tc = rd.a_simt = rd.a;
+        rd.a_in.pairs = PL.list[kListAllIn].as<int2>();
+        rd.a_tc.pairs = PL.list[kListTC].as<int2>();
+        rd.a_tc.pair_hit = rd.hit_tc.as<uint8_t>();
+        rd.a_simt.pairs = PL.list[kListSimt].as<int2>();
+        rd.a_simt.pair_hit = rd.hit_simt.as<uint8_t>();
+        if (use_tc) {
+            CK(rd.queue.alloc(sizeof(uint2) * queue_cap, s), "alloc band queue");
+            CK(rd.queue_n.alloc(sizeof(unsigned long long), s), "alloc");
+        }
+    }
+    // the count pass's arguments: the largest radius's (its counters: the
+    // shared ones when there are several radii)
+    PassArgs a_tc = rs[K - 1].a_tc, a_simt = rs[K - 1].a_simt;
+    if (K > 1) a_tc.stats = a_simt.stats = shared_stats.as<unsigned long long>();
     TcArgs t{};
-    Buf queue, queue_n, tc_err;
+    Buf tc_err;
     if (use_tc) {
         t.Ah = L.Ah.p;
         t.Al = L.Al.p;
@@ -632,15 +677,11 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         t.R = R;
         t.ns = precision == MAPPER_BF16X1 ? 1 : 3;
         t.num_sms = ctx->num_sms;
-        t.queue_cap = ctx->band_cap > 0 ? (unsigned long long)ctx->band_cap
-                                        : (unsigned long long)std::min<int64_t>(
-                                              int64_t(1) << 25, std::max<int64_t>(int64_t(1) << 20, 128 * PL.n[kListTC]));
-        CK(queue.alloc(sizeof(uint2) * t.queue_cap, s), "alloc band queue");
-        CK(queue_n.alloc(sizeof(unsigned long long), s), "alloc");
+        t.queue_cap = queue_cap;
         CK(tc_err.alloc(sizeof(int), s), "alloc");
         CK(cudaMemsetAsync(tc_err.p, 0, sizeof(int), s), "memset");
-        t.queue = queue.as<uint2>();
-        t.queue_n = queue_n.as<unsigned long long>();
+        t.queue = rs[K - 1].queue.as<uint2>();
+        t.queue_n = rs[K - 1].queue_n.as<unsigned long long>();
         t.err = tc_err.as<int>();
     }
 
@@ -658,6 +699,21 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         tx.tn2min = xtn2min.as<float>();
     }
     st.tile_pairs_cross = cross_tc ? PL.n[kListSimt] : 0;
+    // the radii of a count pass over several (mode 5): per radius its
+    // outputs and the hit flags of one pair list (none in a second phase)
+    auto with_radii = [&](TcArgs v, bool simt_list, bool hits) {
+        if (K == 1) return v;
+        v.n_radii = K;
+        for (int e = 0; e < K; ++e) {
+            Radius& rd = rs[e];
+            v.radii[e] = RadiusOut{rd.a.count, rd.a.nbr,
+                                   hits ? (simt_list ? rd.a_simt.pair_hit : rd.a_tc.pair_hit) : nullptr,
+                                   rd.queue.as<uint2>(), rd.queue_n.as<unsigned long long>(),
+                                   rd.stats.as<unsigned long long>(), rd.a.eps2};
+        }
+        return v;
+    };
+    const int count_mode = K > 1 ? 5 : 1;
     // Count pass in two phases (MAPPER_BF16: one BF16 product first; MAPPER_FP8:
     // three FP8 products first): the 32 x 32 sub-blocks with a pair inside the
     // first screen's band run again with three BF16 products
@@ -676,7 +732,8 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     st.pass1_sample_deferred = -1.0;
     if (two_phase && ctx->screen_mode == 0 && PL.n[kListTC] >= kSampleMinPairs) {
         double f = 0.0;
-        if ((rc = sample_deferral(ctx, a_tc, f8 ? t8 : t, PL.n[kListTC], R, cap, s, &f))) return rc;
+        if ((rc = sample_deferral(ctx, a_tc, with_radii(f8 ? t8 : t, false, true), PL.n[kListTC], R, cap, s, &f)))
+            return rc;
         st.pass1_sample_deferred = f;
         if (f > kDeferMax) two_phase = false;
     }
@@ -703,7 +760,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         (rc = tune_pass1(ctx, a_simt, tx_tune, PL.n[kListSimt], R, cap, s, &tile_n)))
         return rc;
     pt.mark();                                                    // 1
-    CK(allin_pass(1, a_in, PL.n[kListAllIn], s), "pass 1 all-in");
+    for (int e = 0; e < K; ++e) CK(allin_pass(1, rs[e].a_in, PL.n[kListAllIn], s), "pass 1 all-in");
     cudaEvent_t tev[2] = {nullptr, nullptr};
     if (ctx->timing) {
         CK(cudaEventCreate(&tev[0]), "event");
@@ -717,8 +774,8 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
     // pass 1 on the tensor cores of one pair list (its events bracket the
     // count kernels: both lists' launches when the cross list runs there)
     auto tc_count = [&](const PassArgs& pa, const TcArgs& base, const TcArgs& first_screen, int64_t np, Buf& gr,
-                        Buf& gp, bool first, bool last) -> int {
-        TcArgs t1 = first_screen;
+                        Buf& gp, bool first, bool last, bool simt_list) -> int {
+        TcArgs t1 = with_radii(first_screen, simt_list, true);
         t1.ev_begin = first ? tev[0] : nullptr;
         t1.ev_end = last && !two_phase ? tev[1] : nullptr;
         if (tile_n == 256) {
@@ -728,14 +785,14 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
             t1.n_groups = np;
             t1.groups_dev = reinterpret_cast<const unsigned long long*>(gp.as<int64_t>() + np);
         }
-        if (!two_phase) return tc_pass(1, pa, t1, np, s);
+        if (!two_phase) return tc_pass(count_mode, pa, t1, np, s);
         if (!t1.f8) t1.ns = 1;
         t1.defer = true;
         t1.defer_mixed = defer_mixed;
         t1.redo_mask = redo_mask.as<uint32_t>();
         CK(cudaMemsetAsync(redo_mask.p, 0, sizeof(uint32_t) * np, s), "memset");
         int r2;
-        if ((r2 = tc_pass(1, pa, t1, np, s))) return r2;
+        if ((r2 = tc_pass(count_mode, pa, t1, np, s))) return r2;
         // second phase: the tile pairs with deferred sub-blocks in list order,
         // grouped by tile A as in the first, counting only those sub-blocks
         // (their number stays on the device)
@@ -747,7 +804,7 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         PassArgs p2 = pa;
         p2.pairs = redo.as<int2>();
         p2.pair_hit = nullptr;
-        TcArgs t2 = base;
+        TcArgs t2 = with_radii(base, simt_list, false);
         t2.groups = nullptr;
         t2.n_groups = 0;
         t2.groups_dev = nullptr;
@@ -762,27 +819,30 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         t2.sub_q = redo_q.as<int32_t>();
         t2.ev_begin = nullptr;
         t2.ev_end = last ? tev[1] : nullptr;
-        return tc_pass(1, p2, t2, np, s);
+        return tc_pass(count_mode, p2, t2, np, s);
     };
     if (use_tc) {
         const bool x_last = cross_tc && PL.n[kListSimt] > 0;
         if (PL.n[kListTC] > 0 &&
-            (rc = tc_count(a_tc, t, first_f8 ? t8 : t, PL.n[kListTC], groups, group_pos, true, !x_last)))
+            (rc = tc_count(a_tc, t, first_f8 ? t8 : t, PL.n[kListTC], groups, group_pos, true, !x_last, false)))
             return rc;
         if (x_last &&
-            (rc = tc_count(a_simt, tx, tx, PL.n[kListSimt], xgroups, xgroup_pos, PL.n[kListTC] == 0, true)))
+            (rc = tc_count(a_simt, tx, tx, PL.n[kListSimt], xgroups, xgroup_pos, PL.n[kListTC] == 0, true, true)))
             return rc;
     }
-    else CK(simt_pass(1, a_tc, PL.n[kListTC], s), "pass 1 tc list");
+    else CK(simt_pass(1, rs[0].a_tc, PL.n[kListTC], s), "pass 1 tc list");
     if (!use_tc && tev[0]) CK(cudaEventRecord(tev[0], s), "event");
-    if (!cross_tc) CK(simt_pass(1, a_simt, PL.n[kListSimt], s), "pass 1");
+    if (!cross_tc)
+        for (int e = 0; e < K; ++e) CK(simt_pass(1, rs[e].a_simt, PL.n[kListSimt], s), "pass 1");
     if (!use_tc && tev[1]) CK(cudaEventRecord(tev[1], s), "event");
     pt.mark();                                                    // 2
+    int h_err = 0;
     if (counts_out) {
         // the counts are final after pass 1 (band pairs re-decided)
+        const PassArgs& a = rs[0].a;
         CK(counts_to_lens(L.row_slot.as<int32_t>(), a.row_pt, a.count, R, counts_out->f, counts_out->m,
                           counts_out->j, s), "counts");
-        int h_nf = 0, h_err = 0;
+        int h_nf = 0;
         unsigned long long h_oob = 0;
         CK(cudaMemcpyAsync(&h_nf, nf, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
         CK(cudaMemcpyAsync(&h_oob, a.stats + kStatOob, sizeof(h_oob), cudaMemcpyDeviceToHost, s), "copy");
@@ -791,128 +851,159 @@ int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t l
         if (h_nf) return fail(MAPPER_ENONFINITE, "X holds NaN or Inf");
         if (h_err) return fail(MAPPER_ETIMEOUT, "a tensor-core pass gave up waiting on a barrier");
         if (h_oob) return fail(MAPPER_EINTERNAL, "a device-side index check failed");
-        *out = c;
+        auto c = std::make_shared<ClusterData>();
+        c->stream = ctx->stream;
+        c->cover = cov;
+        c->stats = st;
+        outs[0] = c;
         return MAPPER_OK;
     }
-    CK(core_flags(a.count, R, min_pts, core.as<uint8_t>(), a.parent, a.border, a.stats, s), "core");
-    pt.mark();                                                    // 3
-    CK(list_unions(a.count, a.nbr, cap, a.core, a.parent, a.row_pt, R, s, a.stats + kStatOob), "list unions");
-    CK(allin_pass(2, a_in, PL.n[kListAllIn], s), "pass 2 all-in");
-    // Unions in rounds of growing tile distance b - a (tiles of one pivot
-    // region are adjacent), after the unions along the neighbour lists: a
-    // pair is kept only if its core rows are not all joined yet (from the
-    // second round on when there are no lists), and pairs whose two sides are
-    // each already one component only need one neighbour pair.
-    auto union_rounds = [&](const PassArgs& base, const TcArgs& tbase, int64_t n, bool tc) -> int {
-        if (n == 0) return MAPPER_OK;
-        // every count stays on the device: each launch covers the list's
-        // capacity n and reads its length there, so the rounds need no host
-        // round trip
-        static const int kBounds[] = {-1, 1, 4, 16, 64, INT_MAX};
-        Buf hits, sel, kept, cnt, troots;
-        CK(troots.alloc(sizeof(int2) * std::max<int64_t>(L.T, 1), s), "alloc");
-        CK(hits.alloc(sizeof(int2) * n, s), "alloc");
-        CK(sel.alloc(sizeof(int2) * n, s), "alloc");
-        CK(kept.alloc(sizeof(int2) * n, s), "alloc");
-        CK(cnt.alloc(sizeof(unsigned long long) * 3, s), "alloc");
-        unsigned long long* c_hit = cnt.as<unsigned long long>();
-        unsigned long long* c_sel = c_hit + 1;
-        unsigned long long* c_kept = c_hit + 2;
-        CK(cudaMemsetAsync(c_hit, 0, sizeof(unsigned long long), s), "memset");
-        CK(select_hit(base.pairs, base.pair_hit, n, hits.as<int2>(), c_hit, s), "select");
-        CK(add_counter(base.stats + kStatUnion, c_hit, s), "count");
-        for (int k = 0; k + 1 < (int)(sizeof(kBounds) / sizeof(kBounds[0])); ++k) {
-            CK(cudaMemsetAsync(c_sel, 0, sizeof(unsigned long long) * 2, s), "memset");
-            CK(select_delta(hits.as<int2>(), n, c_hit, kBounds[k], kBounds[k + 1], sel.as<int2>(), c_sel, s),
-               "select");
-            const int2* list = sel.as<int2>();
-            const unsigned long long* c_list = c_sel;
-            if (k > 0 || cap) {
-                CK(filter_joined(base, L.T, troots.as<int2>(), sel.as<int2>(), n, c_sel, kept.as<int2>(), c_kept, s),
-                   "filter");
-                list = kept.as<int2>();
-                c_list = c_kept;
+    unsigned long long h_shared[kStatCount] = {};
+    if (K > 1) CK(cudaMemcpyAsync(h_shared, shared_stats.p, sizeof(h_shared), cudaMemcpyDeviceToHost, s), "copy");
+    float ms_count = 0.f;
+    bool have_ms_count = false;
+    for (int e = 0; e < K; ++e) {
+        Radius& rd = rs[e];
+        const PassArgs& a = rd.a;
+        auto c = std::make_shared<ClusterData>();
+        c->stream = ctx->stream;
+        c->cover = cov;
+        c->stats = st;
+        Timer pr(ctx->timing, s);
+        CK(core_flags(a.count, R, min_pts, rd.core.as<uint8_t>(), a.parent, a.border, a.stats, s), "core");
+        pr.mark();                                                // 0
+        CK(list_unions(a.count, a.nbr, cap, a.core, a.parent, a.row_pt, R, s, a.stats + kStatOob), "list unions");
+        CK(allin_pass(2, rd.a_in, PL.n[kListAllIn], s), "pass 2 all-in");
+        // Unions in rounds of growing tile distance b - a (tiles of one pivot
+        // region are adjacent), after the unions along the neighbour lists: a
+        // pair is kept only if its core rows are not all joined yet (from the
+        // second round on when there are no lists), and pairs whose two sides are
+        // each already one component only need one neighbour pair.
+        auto union_rounds = [&](const PassArgs& base, const TcArgs& tbase, int64_t n, bool tc) -> int {
+            if (n == 0) return MAPPER_OK;
+            // every count stays on the device: each launch covers the list's
+            // capacity n and reads its length there, so the rounds need no host
+            // round trip
+            static const int kBounds[] = {-1, 1, 4, 16, 64, INT_MAX};
+            Buf hits, sel, kept, cnt, troots;
+            CK(troots.alloc(sizeof(int2) * std::max<int64_t>(L.T, 1), s), "alloc");
+            CK(hits.alloc(sizeof(int2) * n, s), "alloc");
+            CK(sel.alloc(sizeof(int2) * n, s), "alloc");
+            CK(kept.alloc(sizeof(int2) * n, s), "alloc");
+            CK(cnt.alloc(sizeof(unsigned long long) * 3, s), "alloc");
+            unsigned long long* c_hit = cnt.as<unsigned long long>();
+            unsigned long long* c_sel = c_hit + 1;
+            unsigned long long* c_kept = c_hit + 2;
+            CK(cudaMemsetAsync(c_hit, 0, sizeof(unsigned long long), s), "memset");
+            CK(select_hit(base.pairs, base.pair_hit, n, hits.as<int2>(), c_hit, s), "select");
+            CK(add_counter(base.stats + kStatUnion, c_hit, s), "count");
+            for (int k = 0; k + 1 < (int)(sizeof(kBounds) / sizeof(kBounds[0])); ++k) {
+                CK(cudaMemsetAsync(c_sel, 0, sizeof(unsigned long long) * 2, s), "memset");
+                CK(select_delta(hits.as<int2>(), n, c_hit, kBounds[k], kBounds[k + 1], sel.as<int2>(), c_sel, s),
+                   "select");
+                const int2* list = sel.as<int2>();
+                const unsigned long long* c_list = c_sel;
+                if (k > 0 || cap) {
+                    CK(filter_joined(base, L.T, troots.as<int2>(), sel.as<int2>(), n, c_sel, kept.as<int2>(), c_kept,
+                                     s), "filter");
+                    list = kept.as<int2>();
+                    c_list = c_kept;
+                }
+                PassArgs ar = base;
+                ar.pairs = list;
+                ar.n_dev = c_list;
+                ar.pair_hit = nullptr;
+                int r2;
+                if (tc) {
+                    TcArgs t2 = tbase;
+                    t2.n_dev = c_list;
+                    if ((r2 = tc_pass(2, ar, t2, n, s))) return r2;
+                } else {
+                    CK(simt_pass(2, ar, n, s), "pass 2");
+                }
             }
-            PassArgs ar = base;
-            ar.pairs = list;
-            ar.n_dev = c_list;
-            ar.pair_hit = nullptr;
-            int r2;
-            if (tc) {
-                TcArgs t2 = tbase;
-                t2.n_dev = c_list;
-                if ((r2 = tc_pass(2, ar, t2, n, s))) return r2;
-            } else {
-                CK(simt_pass(2, ar, n, s), "pass 2");
-            }
+            return MAPPER_OK;
+        };
+        if (use_tc) {
+            if ((rc = union_rounds(rd.a_tc, t, PL.n[kListTC], true))) return rc;
+            if ((rc = union_rounds(rd.a_simt, tx, PL.n[kListSimt], cross_tc))) return rc;
+        } else {
+            if ((rc = union_rounds(rd.a_simt, t, PL.n[kListSimt], false))) return rc;
         }
-        return MAPPER_OK;
-    };
-    if (use_tc) {
-        if ((rc = union_rounds(a_tc, t, PL.n[kListTC], true))) return rc;
-        if ((rc = union_rounds(a_simt, tx, PL.n[kListSimt], cross_tc))) return rc;
-    } else {
-        if ((rc = union_rounds(a_simt, t, PL.n[kListSimt], false))) return rc;
-    }
-    pt.mark();                                                    // 4
-    CK(flatten(a.parent, a.core, R, root.as<int32_t>(), s), "flatten");
-    if (cap) {
-        CK(border_from_lists(a.count, a.nbr, cap, a.core, a.root, a.row_pt, R, a.border, s, a.stats + kStatOob),
-           "border");
-    } else if (min_pts > 1) {
-        CK(allin_pass(3, a_in, PL.n[kListAllIn], s), "pass 3 all-in");
-        CK(simt_pass(3, a_tc, PL.n[kListTC], s), "pass 3 tc list");
-        CK(simt_pass(3, a_simt, PL.n[kListSimt], s), "pass 3");
-    }
-    pt.mark();                                                    // 5
+        pr.mark();                                                // 1
+        CK(flatten(a.parent, a.core, R, rd.root.as<int32_t>(), s), "flatten");
+        if (cap) {
+            CK(border_from_lists(a.count, a.nbr, cap, a.core, a.root, a.row_pt, R, a.border, s, a.stats + kStatOob),
+               "border");
+        } else if (min_pts > 1) {
+            CK(allin_pass(3, rd.a_in, PL.n[kListAllIn], s), "pass 3 all-in");
+            CK(simt_pass(3, rd.a_tc, PL.n[kListTC], s), "pass 3 tc list");
+            CK(simt_pass(3, rd.a_simt, PL.n[kListSimt], s), "pass 3");
+        }
+        pr.mark();                                                // 2
 
-    CK(c->core.alloc(M, s), "alloc");
-    CK(c->lab.alloc(sizeof(int32_t) * M, s), "alloc");
-    CK(c->is_root.alloc(sizeof(int32_t) * M, s), "alloc");
-    CK(c->is_member.alloc(sizeof(int32_t) * M, s), "alloc");
-    CK(c->slot_label.alloc(sizeof(int64_t) * M, s), "alloc");
-    CK(rows_to_slots(L.row_slot.as<int32_t>(), a.row_pt, a.core, a.root, a.border, R, c->lab.as<int32_t>(),
-                     c->is_root.as<int32_t>(), c->is_member.as<int32_t>(), c->slot_label.as<int64_t>(),
-                     c->core.as<uint8_t>(), s), "labels");
+        CK(c->core.alloc(M, s), "alloc");
+        CK(c->lab.alloc(sizeof(int32_t) * M, s), "alloc");
+        CK(c->is_root.alloc(sizeof(int32_t) * M, s), "alloc");
+        CK(c->is_member.alloc(sizeof(int32_t) * M, s), "alloc");
+        CK(c->slot_label.alloc(sizeof(int64_t) * M, s), "alloc");
+        CK(rows_to_slots(L.row_slot.as<int32_t>(), a.row_pt, a.core, a.root, a.border, R, c->lab.as<int32_t>(),
+                         c->is_root.as<int32_t>(), c->is_member.as<int32_t>(), c->slot_label.as<int64_t>(),
+                         c->core.as<uint8_t>(), s), "labels");
 
-    unsigned long long h_stats[kStatCount];
-    int h_nf = 0, h_err = 0;
-    CK(cudaMemcpyAsync(h_stats, stats.p, sizeof(h_stats), cudaMemcpyDeviceToHost, s), "copy");
-    CK(cudaMemcpyAsync(&h_nf, nf, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
-    if (use_tc) CK(cudaMemcpyAsync(&h_err, tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
-    CK(cudaStreamSynchronize(s), "sync");
-    if (h_nf) return fail(MAPPER_ENONFINITE, "X holds NaN or Inf");
-    if (h_err) return fail(MAPPER_ETIMEOUT, "a tensor-core pass gave up waiting on a barrier");
-    if (h_stats[kStatOob])
-        return fail(MAPPER_EINTERNAL, "a device-side index check failed (" + std::to_string(h_stats[kStatOob]) +
-                                          " indices out of range)");
-    st.band_pairs = (int64_t)h_stats[kStatBand];
-    st.near_ties = (int64_t)h_stats[kStatTies];
-    st.pairs_screened = (int64_t)h_stats[kStatScreened];
-    st.n_core = (int64_t)h_stats[kStatCore];
-    st.union_skipped = (int64_t)h_stats[kStatSkipped];
-    st.fp64_pairs = (int64_t)h_stats[kStatFp64];
-    st.union_pairs = (int64_t)h_stats[kStatUnion];
-    st.pass1_tile_n = tile_n;
-    st.n_rows = R;
-    st.tile_pairs_screen1 = two_phase ? PL.n[kListTC] + (cross_tc ? PL.n[kListSimt] : 0) : 0;
-    st.tile_pairs_redo = (int64_t)h_stats[kStatRedo];
-    st.redo_blocks = (int64_t)h_stats[kStatRedoBlocks];
-    st.redo_parts = (int64_t)h_stats[kStatRedoParts];
-    if (tev[0] && (PL.n[use_tc ? kListTC : kListSimt] > 0 || cross_tc)) {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, tev[0], tev[1]), "event time");
-        st.ms_count_kernel = ms;
+        unsigned long long h_stats[kStatCount];
+        int h_nf = 0;
+        CK(cudaMemcpyAsync(h_stats, a.stats, sizeof(h_stats), cudaMemcpyDeviceToHost, s), "copy");
+        CK(cudaMemcpyAsync(&h_nf, nf, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+        if (use_tc) CK(cudaMemcpyAsync(&h_err, tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+        CK(cudaStreamSynchronize(s), "sync");
+        if (h_nf) return fail(MAPPER_ENONFINITE, "X holds NaN or Inf");
+        if (h_err) return fail(MAPPER_ETIMEOUT, "a tensor-core pass gave up waiting on a barrier");
+        // the count pass's counters (kept apart when there are several radii)
+        for (int k : {(int)kStatScreened, (int)kStatTcPairs, (int)kStatRedo, (int)kStatRedoBlocks,
+                      (int)kStatRedoParts, (int)kStatOob})
+            h_stats[k] += h_shared[k];
+        if (h_stats[kStatOob])
+            return fail(MAPPER_EINTERNAL, "a device-side index check failed (" + std::to_string(h_stats[kStatOob]) +
+                                              " indices out of range)");
+        mapper_stats& sr = c->stats;
+        sr.band_pairs = (int64_t)h_stats[kStatBand];
+        sr.near_ties = (int64_t)h_stats[kStatTies];
+        sr.pairs_screened = (int64_t)h_stats[kStatScreened];
+        sr.n_core = (int64_t)h_stats[kStatCore];
+        sr.union_skipped = (int64_t)h_stats[kStatSkipped];
+        sr.fp64_pairs = (int64_t)h_stats[kStatFp64];
+        sr.union_pairs = (int64_t)h_stats[kStatUnion];
+        sr.pass1_tile_n = tile_n;
+        sr.n_rows = R;
+        sr.tile_pairs_screen1 = two_phase ? PL.n[kListTC] + (cross_tc ? PL.n[kListSimt] : 0) : 0;
+        sr.tile_pairs_redo = (int64_t)h_stats[kStatRedo];
+        sr.redo_blocks = (int64_t)h_stats[kStatRedoBlocks];
+        sr.redo_parts = (int64_t)h_stats[kStatRedoParts];
+        if (tev[0] && (PL.n[use_tc ? kListTC : kListSimt] > 0 || cross_tc)) {
+            if (!have_ms_count) CK(cudaEventElapsedTime(&ms_count, tev[0], tev[1]), "event time");
+            have_ms_count = true;
+            sr.ms_count_kernel = ms_count;
+        }
+        sr.count_kernel_pairs = (int64_t)h_stats[use_tc ? kStatTcPairs : kStatSimtPairs];
+        if (pt.n >= 3 && pr.n >= 3) {
+            sr.ms_tiles = pt.ms(0, 1);
+            sr.ms_pass[0] = pt.ms(1, 2);
+            sr.ms_pass[1] = pr.ms(0, 1);
+            sr.ms_pass[2] = pr.ms(1, 2);
+        }
+        outs[e] = c;
     }
-    st.count_kernel_pairs = (int64_t)h_stats[use_tc ? kStatTcPairs : kStatSimtPairs];
-    if (pt.n >= 6) {
-        st.ms_tiles = pt.ms(0, 1);
-        st.ms_pass[0] = pt.ms(1, 2);
-        st.ms_pass[1] = pt.ms(3, 4);
-        st.ms_pass[2] = pt.ms(4, 5);
-    }
-    *out = c;
     return MAPPER_OK;
+}
+
+int run_cluster(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
+                const std::shared_ptr<CoverData>& cov, double eps, int32_t min_pts, int32_t precision,
+                std::shared_ptr<ClusterData>* out, int* nonfinite_dev, TileLayout* layout = nullptr,
+                const CountsOut* counts_out = nullptr, const PivotSet* pivots = nullptr)
+{
+    return run_cluster_radii(ctx, X, n, d, ld, cov, 1, &eps, min_pts, precision, out, nonfinite_dev, layout,
+                             counts_out, pivots);
 }
 
 // Density filter (§4.1 names density among the derived filters; no estimator
@@ -1898,11 +1989,27 @@ int mapper_graph_sweep(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, in
         if ((rc = build_tiles(Xd, n, d, ldd, dp, cov->slot_point.as<int32_t>(), cov->slot_elem.as<int32_t>(), cov->M,
                               cov->E, 4.0 * eps_max, use_tc, ctx->num_sms, &L, flag.as<int>(), s, &piv)))
             return rc;
+        // the overlap's distinct radii, ascending; on the BF16 tensor-core
+        // screen up to kMaxRadii of them share one count pass
+        std::vector<double> radii;
+        for (int j = i; j < n_sweep; ++j)
+            if (overlap[j] == overlap[i]) radii.push_back(eps[j]);
+        for (double r : radii)
+            if (!(r > 0.0) || !std::isfinite(r)) return fail(MAPPER_EINVAL, "eps must be finite and > 0");
+        std::sort(radii.begin(), radii.end());
+        radii.erase(std::unique(radii.begin(), radii.end()), radii.end());
+        const int per_pass = (p->precision == MAPPER_BF16 || p->precision == MAPPER_BF16X1) ? kMaxRadii : 1;
+        std::vector<std::shared_ptr<ClusterData>> by_radius(radii.size());
+        for (size_t r0 = 0; r0 < radii.size(); r0 += per_pass) {
+            const int k = (int)std::min<size_t>(per_pass, radii.size() - r0);
+            if ((rc = run_cluster_radii(ctx, Xd, n, d, ldd, cov, k, radii.data() + r0, p->min_pts, p->precision,
+                                        by_radius.data() + r0, flag.as<int>(), &L)))
+                return rc;
+        }
         for (int j = i; j < n_sweep; ++j) {
             if (done[j] || overlap[j] != overlap[i]) continue;
-            std::shared_ptr<ClusterData> cl;
-            if ((rc = run_cluster(ctx, Xd, n, d, ldd, cov, eps[j], p->min_pts, p->precision, &cl, flag.as<int>(), &L)))
-                return rc;
+            const std::shared_ptr<ClusterData>& cl =
+                by_radius[std::lower_bound(radii.begin(), radii.end(), eps[j]) - radii.begin()];
             auto g = std::make_unique<mapper_graph_t>();
             g->stream = ctx->stream;
             g->n = n;

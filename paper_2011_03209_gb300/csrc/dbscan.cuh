@@ -232,9 +232,11 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
 // pair within eps), all-in, or mixed (to the tensor-core list when both tiles
 // are one non-outlier segment and use_tc, else to the CUDA-core list).
 // X, ld, d: the rows (read for the outlier tiles' distance bounds when G is
-// not gathered).
+// not gathered). eps_all_in (if > 0, <= eps): the radius a pair must be all in
+// at to go to the all-in list (the smallest of several radii sharing the
+// lists; out stays decided at eps, the largest).
 int classify_pairs(const TileLayout& L, const float* X, int64_t ld, int d, int dp, int64_t E, double eps,
-                   bool use_tc, PairLists* P, cudaStream_t s);
+                   bool use_tc, PairLists* P, cudaStream_t s, double eps_all_in = 0.0);
 // FP8 E4M3 operands of a tile layout built with BF16 operands (needs its
 // centres and tmax): per tile a power-of-two scale s, hi and lo parts of a / s
 // (Fh, Fl), frl and ftmax. A no-op when already built. Returns a mapper_status.

@@ -91,6 +91,19 @@ struct TcParams {
     float* kq_v;                              // lists: [((query * chunks + chunk) * 4 + part) * kKnnL]
     int32_t* kq_i;                            // append: [query * kq_cap + slot]
     float* dump;                              // MODE 4 (accumulation probe): [item][128][128] accumulators
+    // MODE 5 (count pass over several radii, ascending): per radius its
+    // outputs and eps^2 (double; FP32 rounded down / up)
+    struct Radius {
+        int32_t* count;
+        int32_t* nbr;
+        uint8_t* pair_hit;
+        uint2* queue;
+        unsigned long long* queue_n;
+        unsigned long long* stats;
+        double eps2, tie_thr;
+        float eps2_lo, eps2_hi;
+    } rad[kMaxRadii];
+    int n_rad;
 };
 
 // ------------------------------------------------------------------ PTX
@@ -368,6 +381,25 @@ __device__ __forceinline__ bool push_band(const TcParams& P, int ra, int rb, uin
     return d2 <= A.eps2;
 }
 
+// The same for radius e of a count pass over several radii.
+__device__ __forceinline__ bool push_band_radius(const TcParams& P, uint2* queue, unsigned long long* queue_n,
+                                                 unsigned long long* stats, double eps2, double tie_thr, int ra,
+                                                 int rb, uint32_t flags, bool* decided)
+{
+    const unsigned long long at = atomicAdd(queue_n, 1ull);
+    if (at < P.queue_cap) {
+        queue[at] = make_uint2((uint32_t)ra, (uint32_t)rb | (flags << 30));
+        *decided = false;
+        return false;
+    }
+    const PassArgs& A = P.A;
+    const double d2 = exact_sqdist(pass_row(A, ra), pass_row(A, rb), A.d);
+    atomicAdd(&stats[kStatBand], 1ull);
+    if ((flags & kQTie) && fabs(d2 - eps2) <= tie_thr) atomicAdd(&stats[kStatTies], 1ull);
+    *decided = true;
+    return d2 <= eps2;
+}
+
 // ------------------------------------------------------------------ kernel
 // Per-pair epilogue data is double-buffered (index: pair counter & 1): a
 // pair's buffer is written before the barrier that follows the accumulator
@@ -533,7 +565,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
     // items (consecutive groups of the list mostly share tile A, whose blocks
     // then stay in the stages), the CTAs' runs interleaved so that the CTAs
     // working at one time stay close in the list (tiles shared through L2)
-    constexpr int kRun = MODE == 1 ? 4 : 1;
+    constexpr bool kCountPass = MODE == 1 || MODE == 5;
+    constexpr int kRun = kCountPass ? 4 : 1;
     auto item_at = [&](int64_t k) -> int64_t {
         if (MODE == 3) return k;
         return ((k / kRun) * (int64_t)gridDim.x + blockIdx.x) * kRun + (k % kRun);
@@ -588,9 +621,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             int issued = 0;
             // count pass: the (tile A, K block) whose A blocks each stage holds;
             // a fill that needs the same ones leaves them in place
-            int64_t tag[MODE == 1 ? kStages : 1];
+            int64_t tag[kCountPass ? kStages : 1];
 #pragma unroll
-            for (int i = 0; i < (MODE == 1 ? kStages : 1); ++i) tag[i] = -1;
+            for (int i = 0; i < (kCountPass ? kStages : 1); ++i) tag[i] = -1;
             constexpr int nA = NS == 3 ? 2 : 1;                 // A blocks per stage (hi, lo)
             for (int64_t k = 0, g = kRun == 1 ? g_begin : item_at(0); g < g_end && !*abort; g = next_item(k, g), ++k) {
                 const int3 itm = item(g);
@@ -604,7 +637,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                     if (!mbar_wait(&S.empty[stage], phase ^ 1, abort)) break;
                     unsigned char* st = smem + stage * kStageBytes;
                     bool keepA = false;
-                    if constexpr (MODE == 1) {
+                    if constexpr (kCountPass) {
                         const int64_t want = (int64_t)tp.x * 4096 + kb;
                         keepA = tag[stage] == want;
                         tag[stage] = want;
@@ -830,7 +863,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 P.kq_i[base + i] = li[i];
             }
         }
-    } else if constexpr (MODE == 1) {
+    } else if constexpr (kCountPass) {
         // ------------------------------------------ epilogue: count pass
         // Each epilogue warp works alone on one 32 x 32 sub-block of every
         // tile pair: TMEM lane quadrant quad = A rows 32 quad .. +31 (a row per
@@ -889,7 +922,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                     it.na2 = P.rn2[row];
                     it.nra = P.rn[row];
                     it.rla = P.rl ? P.rl[row] : 0.f;
-                    it.pre_row = A.cap > 0 ? A.count[row] : INT_MAX;
+                    it.pre_row = MODE == 1 && A.cap > 0 ? A.count[row] : INT_MAX;
                     it.sa = F ? P.tmax[tp.x].w : 1.f;
                 }
                 it.nb[h] = A.tile_n[it.tb[h]];
@@ -901,7 +934,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 it.bl[h] = tm.z;
                 it.sb[h] = tm.w;
                 it.bmin2[h] = P.tn2min[it.tb[h]];
-                it.pre_col[h] = A.cap > 0 && it.mine[h] && tp.x != it.tb[h] ? A.count[col] : INT_MAX;
+                it.pre_col[h] = MODE == 1 && A.cap > 0 && it.mine[h] && tp.x != it.tb[h] ? A.count[col] : INT_MAX;
             }
         };
         int64_t screened = 0;
@@ -954,6 +987,152 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                     E = __fmaf_ru(P.K4f, __fadd_ru(__fmul_ru(cur.sb[h], cur.nra), __fmul_ru(cur.sa, cur.bn[h])),
                                   __fmaf_ru(P.K5f, ss, E));
                     two = 2.f * ss;
+                }
+                if constexpr (MODE == 5) {
+                    // Several radii, ascending, each with the limits of the
+                    // one-radius pass below. A row all out at a radius is all
+                    // out at every smaller one; the screen values are formed
+                    // once and compared with each radius's limits.
+                    const int nr = P.n_rad;
+                    const bool pad = r >= cur.na;             // padding rows hold no pair
+                    auto k_in_of = [&](float lo) { return __fadd_ru(__fsub_ru(cur.na2, lo), E); };
+                    auto k_out_of = [&](float hi) { return __fsub_rd(__fsub_rd(cur.na2, hi), E); };
+                    float vmax = fmax3(u[0], u[1], u[2]);
+#pragma unroll
+                    for (int i = 3; i + 1 < 32; i += 2) vmax = fmax3(vmax, u[i], u[i + 1]);
+                    vmax = fmaxf(vmax, u[31]);
+                    const float xmax = __fmaf_ru(two, vmax, -cur.bmin2[h]);
+                    int e_lo = nr;                            // radii e_lo .. nr - 1 hold a row not all out
+#pragma unroll
+                    for (int e = kMaxRadii - 1; e >= 0; --e) {
+                        if (e >= nr) continue;
+                        const bool out = pad || xmax < k_out_of(P.rad[e].eps2_hi);
+                        if (__all_sync(0xffffffffu, out)) break;
+                        e_lo = e;
+                    }
+                    if (e_lo == nr) continue;                 // all out at every radius
+                    float vmin = fmin3(u[0], u[1], u[2]);
+#pragma unroll
+                    for (int i = 3; i + 1 < 32; i += 2) vmin = fmin3(vmin, u[i], u[i + 1]);
+                    vmin = fminf(vmin, u[31]);
+                    const float xmin = __fmaf_rd(two, vmin, -cur.bn2[h]);
+                    bool mixed = false;
+#pragma unroll
+                    for (int e = 0; e < kMaxRadii; ++e) {
+                        if (e < e_lo || e >= nr) continue;
+                        const bool out = pad || xmax < k_out_of(P.rad[e].eps2_hi);
+                        mixed |= !out && !(xmin >= k_in_of(P.rad[e].eps2_lo));
+                    }
+                    mixed = __any_sync(0xffffffffu, mixed);
+                    auto defer_radii = [&]() {
+                        if (lane == 0) {
+                            if (atomicOr(&P.redo_mask[q], 1u << sub) == 0u) atomicAdd(&A.stats[kStatRedo], 1ull);
+#pragma unroll
+                            for (int e = 0; e < kMaxRadii; ++e)
+                                if (e < nr && P.rad[e].pair_hit) P.rad[e].pair_hit[q] = 1;
+                        }
+                    };
+                    if (P.defer == 2 && mixed) {
+                        defer_radii();
+                        continue;
+                    }
+                    if (mixed) {
+                        __syncwarp();                         // the previous pair's wn is read
+                        wn[lane] = cur.ncol2[h];
+                        __syncwarp();
+                        const float4* wn4 = reinterpret_cast<const float4*>(wn);
+#pragma unroll
+                        for (int i4 = 0; i4 < 8; ++i4) {
+                            const float4 nn = wn4[i4];
+                            fma2_inplace(u[4 * i4 + 0], u[4 * i4 + 1], two, nn.x, nn.y);
+                            fma2_inplace(u[4 * i4 + 2], u[4 * i4 + 3], two, nn.z, nn.w);
+                        }
+                    }
+                    const int left = cur.nb[h] - part * 32;
+                    const uint32_t cand = pad ? 0u : (left >= 32 ? 0xffffffffu : (left > 0 ? (1u << left) - 1u : 0u));
+                    // in and band bits of one radius
+                    auto bits_of = [&](float lo, float hi, uint32_t& inb, uint32_t& band) {
+                        const float k_in = k_in_of(lo), k_out = k_out_of(hi);
+                        const bool out = pad || xmax < k_out;
+                        uint32_t ib = 0u, kb = 0u;
+                        if (!out && xmin >= k_in) {
+                            ib = kb = 0xffffffffu;
+                        } else if (!out) {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) {
+                                if (u[i] >= k_in) ib |= 1u << i;
+                                if (u[i] >= k_out) kb |= 1u << i;
+                            }
+                        }
+                        inb = ib & cand;
+                        band = kb & ~ib & cand;
+                    };
+                    if (P.defer == 1) {
+                        bool any_band = false;
+#pragma unroll
+                        for (int e = 0; e < kMaxRadii; ++e) {
+                            if (e < e_lo || e >= nr) continue;
+                            uint32_t ib, bd;
+                            bits_of(P.rad[e].eps2_lo, P.rad[e].eps2_hi, ib, bd);
+                            any_band |= bd != 0u;
+                        }
+                        if (__any_sync(0xffffffffu, any_band)) {
+                            defer_radii();
+                            continue;
+                        }
+                    }
+#pragma unroll
+                    for (int e = 0; e < kMaxRadii; ++e) {
+                        if (e < e_lo || e >= nr) continue;
+                        int32_t* const cnt = P.rad[e].count;
+                        int32_t* const nbl = P.rad[e].nbr;
+                        uint32_t inb, band;
+                        bits_of(P.rad[e].eps2_lo, P.rad[e].eps2_hi, inb, band);
+                        if (!__any_sync(0xffffffffu, (inb | band) != 0u)) continue;
+                        if (lane == 0 && P.rad[e].pair_hit) P.rad[e].pair_hit[q] = 1;
+                        uint32_t bq = band;
+                        while (bq) {
+                            const int i = __ffs(bq) - 1;
+                            bq &= bq - 1;
+                            const int j = part * 32 + i;
+                            const uint32_t fl = (diag ? 0u : kQBoth) | ((!diag || r < j) ? kQTie : 0u);
+                            bool decided;
+                            const bool in = push_band_radius(P, P.rad[e].queue, P.rad[e].queue_n, P.rad[e].stats,
+                                                             P.rad[e].eps2, P.rad[e].tie_thr, (int)row, (int)(sb + j),
+                                                             fl, &decided);
+                            if (decided && in) inb |= 1u << i;
+                        }
+                        const int k = __popc(inb);
+                        if (k) {
+                            int pos = atomicAdd(&cnt[row], k);
+                            uint32_t bm = inb;
+                            while (bm && pos < A.cap) {
+                                const int i = __ffs(bm) - 1;
+                                bm &= bm - 1;
+                                nbl[row * A.cap + pos++] = (int32_t)(sb + part * 32 + i);
+                            }
+                        }
+                        if (!diag && __any_sync(0xffffffffu, inb != 0u)) {
+                            uint32_t x = inb;
+#pragma unroll
+                            for (int sft = 16; sft >= 1; sft >>= 1) {
+                                const uint32_t m = sft == 16 ? 0x0000FFFFu : sft == 8 ? 0x00FF00FFu
+                                                 : sft == 4 ? 0x0F0F0F0Fu : sft == 2 ? 0x33333333u : 0x55555555u;
+                                const uint32_t y = __shfl_xor_sync(0xffffffffu, x, sft);
+                                x = (lane & sft) ? (((y >> sft) & m) | (x & ~m)) : ((x & m) | ((y & m) << sft));
+                            }
+                            const int kc = __popc(x);
+                            if (kc) {
+                                int pos = atomicAdd(&cnt[col], kc);
+                                while (x && pos < A.cap) {
+                                    const int i = __ffs(x) - 1;
+                                    x &= x - 1;
+                                    nbl[col * A.cap + pos++] = (int32_t)(sa + quad * 32 + i);
+                                }
+                            }
+                        }
+                    }
+                    continue;
                 }
                 const float k_in = __fadd_ru(__fsub_ru(cur.na2, P.eps2_lo), E);
                 const float k_out = __fsub_rd(__fsub_rd(cur.na2, P.eps2_hi), E);
@@ -2109,6 +2288,21 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
         set_error("tensor-core pass: the FP8 screen is a three-product count pass");
         return MAPPER_EINTERNAL;
     }
+    if (mode == 5) {
+        bool ok = t.n_radii >= 1 && t.n_radii <= kMaxRadii && !t.f8;
+        for (int e = 0; ok && e < t.n_radii; ++e) {
+            const RadiusOut& o = t.radii[e];
+            ok = o.count && o.queue && o.queue_n && o.stats && (a.cap == 0 || o.nbr) && o.eps2 > 0.0 &&
+                 std::isfinite(o.eps2) && (e == 0 || o.eps2 >= t.radii[e - 1].eps2);
+        }
+        if (!ok) {
+            set_error("tensor-core pass: bad radii for the count pass over several radii");
+            return MAPPER_EINTERNAL;
+        }
+    }
+    // the error bound grows with eps^2 (its A3 term): the largest radius's
+    // bound holds for every radius of a mode-5 pass
+    const double eps2_b = mode == 5 ? t.radii[t.n_radii - 1].eps2 : a.eps2;
     // FP8 rows of dp bytes are moved as rows of dp / 2 BF16 columns (the same
     // bytes, the same 128-byte swizzled K blocks, each holding 128 FP8 columns)
     const int dcols = t.f8 ? a.dp / 2 : a.dp;
@@ -2123,7 +2317,7 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
     p.rn = t.rn;
     p.n_pairs = n_pairs;
     p.nkb = (dcols + kKB - 1) / kKB;
-    tc_bound(t.ns, a.dp, a.eps2, &p.A1, &p.A2, &p.A3);
+    tc_bound(t.ns, a.dp, eps2_b, &p.A1, &p.A2, &p.A3);
     p.A1f = std::nextafter((float)p.A1, INFINITY);
     p.A2f = std::nextafter((float)p.A2, INFINITY);
     p.A3f = std::nextafter((float)p.A3, INFINITY);
@@ -2138,33 +2332,54 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
         p.K5f = std::nextafter((float)K5, INFINITY);
     } else if (t.rl) {
         double K0, K1, K2, A2, A3;
-        tc_bound_resid(t.ns, a.dp, a.eps2, &K0, &K1, &K2, &A2, &A3);
+        tc_bound_resid(t.ns, a.dp, eps2_b, &K0, &K1, &K2, &A2, &A3);
         p.K0f = std::nextafter((float)K0, INFINITY);
         p.K1f = std::nextafter((float)K1, INFINITY);
         p.K2f = std::nextafter((float)K2, INFINITY);
     }
-    p.eps2_lo = (float)a.eps2;
-    if ((double)p.eps2_lo > a.eps2) p.eps2_lo = std::nextafter(p.eps2_lo, -INFINITY);
-    p.eps2_hi = (float)a.eps2;
-    if ((double)p.eps2_hi < a.eps2) p.eps2_hi = std::nextafter(p.eps2_hi, INFINITY);
+    auto f32_lo = [](double x) {
+        float f = (float)x;
+        return (double)f > x ? std::nextafter(f, -INFINITY) : f;
+    };
+    auto f32_hi = [](double x) {
+        float f = (float)x;
+        return (double)f < x ? std::nextafter(f, INFINITY) : f;
+    };
+    p.eps2_lo = f32_lo(a.eps2);
+    p.eps2_hi = f32_hi(a.eps2);
+    if (mode == 5) {
+        p.n_rad = t.n_radii;
+        for (int e = 0; e < t.n_radii; ++e) {
+            const RadiusOut& o = t.radii[e];
+            p.rad[e] = {o.count, o.nbr, o.pair_hit, o.queue, o.queue_n, o.stats, o.eps2, 1e-12 * o.eps2,
+                        f32_lo(o.eps2), f32_hi(o.eps2)};
+        }
+    }
     p.queue = t.queue;
     p.queue_n = t.queue_n;
     p.queue_cap = t.queue_cap;
     p.err = t.err;
-    const bool defer = mode == 1 && t.defer && (t.ns == 1 || t.f8);
+    const bool count_pass = mode == 1 || mode == 5;
+    const bool defer = count_pass && t.defer && (t.ns == 1 || t.f8);
     p.defer = defer ? (t.defer_mixed ? 2 : 1) : 0;
     p.redo_mask = t.redo_mask;
     p.sub_mask = t.sub_mask;
     p.sub_q = t.sub_q;
     p.tmax = t.tmax;
     p.tn2min = t.tn2min;
-    if ((t.defer && !defer) || (mode == 1 && (!t.tmax || !t.tn2min)) || (t.sub_mask && !t.sub_q) || (defer && !t.redo_mask)) {
+    if ((t.defer && !defer) || (count_pass && (!t.tmax || !t.tn2min)) || (t.sub_mask && !t.sub_q) || (defer && !t.redo_mask)) {
         set_error("tensor-core pass: inconsistent arguments");
         return MAPPER_EINTERNAL;
     }
-    cudaError_t e = cudaMemsetAsync(t.queue_n, 0, sizeof(unsigned long long), s);
+    cudaError_t e = cudaSuccess;
+    if (mode == 5) {
+        for (int r = 0; r < t.n_radii && e == cudaSuccess; ++r)
+            e = cudaMemsetAsync(t.radii[r].queue_n, 0, sizeof(unsigned long long), s);
+    } else {
+        e = cudaMemsetAsync(t.queue_n, 0, sizeof(unsigned long long), s);
+    }
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return MAPPER_ECUDA; }
-    const bool grouped = mode == 1 && t.groups != nullptr;
+    const bool grouped = (mode == 1 || mode == 5) && t.groups != nullptr;
     p.groups = grouped ? t.groups : nullptr;
     p.n_groups = grouped ? t.n_groups : 0;
     p.n_dev = grouped ? t.groups_dev : t.n_dev;
@@ -2173,6 +2388,9 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
     if (t.ev_begin) cudaEventRecord(t.ev_begin, s);
     if (t.f8)
         e = grouped ? launch<3, 1, 2, 1>(mh, ml, p, grid, s) : launch<3, 1, 1, 1>(mh, ml, p, grid, s);
+    else if (mode == 5)
+        e = grouped ? (t.ns == 3 ? launch<3, 5, 2>(mh, ml, p, grid, s) : launch<1, 5, 2>(mh, ml, p, grid, s))
+                    : (t.ns == 3 ? launch<3, 5, 1>(mh, ml, p, grid, s) : launch<1, 5, 1>(mh, ml, p, grid, s));
     else if (grouped)
         e = t.ns == 3 ? launch<3, 1, 2>(mh, ml, p, grid, s) : launch<1, 1, 2>(mh, ml, p, grid, s);
     else if (t.ns == 3)
@@ -2189,13 +2407,30 @@ int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaS
     // FP32 limits of the recheck's lane-split sum (relative error (dp/8 + 5) 2^-24)
     const double eta = 1.5 * (a.dp / 8 + 5) * std::ldexp(1.0, -24);
     const double tiny = 3.0 * (a.d + 2) * std::ldexp(1.0, -149);
-    float lo32 = (float)(a.eps2 * (1.0 - eta) - tiny), hi32 = (float)(a.eps2 * (1.0 + eta) + tiny);
-    if ((double)lo32 > a.eps2 * (1.0 - eta) - tiny) lo32 = std::nextafter(lo32, -INFINITY);
-    if ((double)hi32 < a.eps2 * (1.0 + eta) + tiny) hi32 = std::nextafter(hi32, INFINITY);
     const int rgrid = t.num_sms * 16;
-    if (mode == 1) recheck_kernel<1><<<rgrid, 256, 0, s>>>(a, t.queue, t.queue_n, t.queue_cap, lo32, hi32);
-    else recheck_kernel<2><<<rgrid, 256, 0, s>>>(a, t.queue, t.queue_n, t.queue_cap, lo32, hi32);
-    note_launch();
+    auto recheck = [&](const PassArgs& ar, const uint2* queue, const unsigned long long* queue_n) {
+        float lo32 = (float)(ar.eps2 * (1.0 - eta) - tiny), hi32 = (float)(ar.eps2 * (1.0 + eta) + tiny);
+        if ((double)lo32 > ar.eps2 * (1.0 - eta) - tiny) lo32 = std::nextafter(lo32, -INFINITY);
+        if ((double)hi32 < ar.eps2 * (1.0 + eta) + tiny) hi32 = std::nextafter(hi32, INFINITY);
+        if (mode == 2) recheck_kernel<2><<<rgrid, 256, 0, s>>>(ar, queue, queue_n, t.queue_cap, lo32, hi32);
+        else recheck_kernel<1><<<rgrid, 256, 0, s>>>(ar, queue, queue_n, t.queue_cap, lo32, hi32);
+        note_launch();
+    };
+    if (mode == 5) {
+        for (int r = 0; r < t.n_radii; ++r) {
+            const RadiusOut& o = t.radii[r];
+            PassArgs ar = a;
+            ar.count = o.count;
+            ar.nbr = o.nbr;
+            ar.pair_hit = o.pair_hit;
+            ar.stats = o.stats;
+            ar.eps2 = o.eps2;
+            ar.tie_thr = 1e-12 * o.eps2;
+            recheck(ar, o.queue, o.queue_n);
+        }
+    } else {
+        recheck(a, t.queue, t.queue_n);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error(std::string("band recheck: ") + cudaGetErrorString(e));

@@ -1282,8 +1282,9 @@ int cross_operands(const TileLayout& L, const float* X, int64_t ld, int d, int d
 }
 
 int classify_pairs(const TileLayout& L, const float* X, int64_t ld, int d, int dp, int64_t E, double eps, bool use_tc,
-                   PairLists* P, cudaStream_t s)
+                   PairLists* P, cudaStream_t s, double eps_all_in)
 {
+    if (!(eps_all_in > 0.0)) eps_all_in = eps;
     Buf etile_off, cnt, cand_off, counts, eseg_off;
     TK(etile_off.alloc(sizeof(int64_t) * (E + 1), s));
     TK(eseg_off.alloc(sizeof(int64_t) * (E + 1), s));
@@ -1325,7 +1326,7 @@ int classify_pairs(const TileLayout& L, const float* X, int64_t ld, int d, int d
     const double rel_tile = (double)(dp + 24) * std::ldexp(1.0, -24);
     const double c_lo = std::nextafter(1.0 - rel_tile, 0.0);
     const double c_hi = std::nextafter(1.0 / (1.0 - rel_tile), INFINITY);
-    const double eps_out = eps * (1.0 + 1e-9), eps_in = eps * (1.0 - 1e-9);
+    const double eps_out = eps * (1.0 + 1e-9), eps_in = eps_all_in * (1.0 - 1e-9);
     auto classify = [&](const float* tsm, int smax) -> int {
         classify_blk_kernel<<<cls_grid, 256, cls_smem, s>>>(
             blk_off.as<int64_t>(), L.n_seg, eseg_off.as<int64_t>(), L.seg_toff.as<int64_t>(),

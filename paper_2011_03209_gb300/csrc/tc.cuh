@@ -5,6 +5,21 @@
 
 namespace mgb {
 
+// Count pass over several radii of one cover (mode 5 of tc_pass): one
+// contraction whose epilogue decides every pair against each radius in turn,
+// writing each radius's counts, lists, hit flags and band queue (the FP64
+// recheck then runs per radius). Radii ascending, at most kMaxRadii.
+constexpr int kMaxRadii = 4;
+struct RadiusOut {
+    int32_t* count;                  // [R] neighbour counts, zeroed by the caller
+    int32_t* nbr;                    // [R * cap] first cap neighbours (cap of the PassArgs), or nullptr
+    uint8_t* pair_hit;               // per tile pair of the list: holds a neighbour pair (nullable)
+    uint2* queue;                    // band pairs of this radius (capacity TcArgs::queue_cap)
+    unsigned long long* queue_n;     // entries pushed (may exceed the capacity)
+    unsigned long long* stats;       // this radius's kStat* counters (band, ties, FP64, index checks)
+    double eps2;
+};
+
 // Operands of the tensor-core screen: rows centred on their segment's
 // centroid, split into BF16 hi and lo parts (R x dp each, row-major), with
 // |a|^2 (FP32, to nearest) and |a| (FP32, rounded up) per row.
@@ -45,6 +60,10 @@ struct TcArgs {
     uint32_t* redo_mask;
     const uint32_t* sub_mask;
     const int32_t* sub_q;
+    // mode 5: the radii (ascending) and their outputs; the PassArgs' count,
+    // nbr, pair_hit, eps2 and this struct's queue are not used then
+    int n_radii;
+    RadiusOut radii[kMaxRadii];
 };
 
 // The pairs q of pairs[0 .. n) with mask[q] != 0, in list order: redo[k] =
@@ -67,8 +86,9 @@ int tc_groups_dev(const int2* pairs, int64_t n, const unsigned long long* n_dev,
 // of groups) on stream s, without a host round trip. Returns a mapper_status.
 int tc_groups(const int2* pairs, int64_t n, Buf* groups, Buf* pos, cudaStream_t s);
 
-// Pass `mode` (1 = counts and neighbour lists, 2 = unions) over the tile
-// pairs a.pairs[0 .. n_pairs) on tensor cores. Returns a mapper_status.
+// Pass `mode` (1 = counts and neighbour lists, 2 = unions, 5 = counts and
+// lists for each of t.radii, BF16 operands) over the tile pairs a.pairs[0 ..
+// n_pairs) on tensor cores. Returns a mapper_status.
 int tc_pass(int mode, const PassArgs& a, const TcArgs& t, int64_t n_pairs, cudaStream_t s);
 
 // Nearest of K <= 256 pivots (rows of Pv, pitch dp) for every point of X, on

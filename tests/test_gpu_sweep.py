@@ -46,3 +46,99 @@ def test_sweep_rejects_bad_arguments():
         base = mg.params((0,), (0,), (4,), (0.2,), 0.5, 3, mg.BF16)
         with pytest.raises(mg.MapperError):
             mg.mapper_graph_sweep(ctx, X, base, [0.5, -1.0], [0.2, 0.2])
+
+
+def _against_oracle(w, g, grid, p, e, min_pts):
+    got = g.numpy()
+    lens, _ = g.lens(w.n, len(grid))
+    ref = oracle.mapper_graph(w.X, lens, grid, (p,) * len(grid), e, min_pts)
+    _same(got, ref)
+    return got, ref
+
+
+# Radii of one overlap share one count pass (up to four per pass, the rest in
+# a second): five distinct radii, one of them twice, in every pass-1 screen.
+@pytest.mark.parametrize("prec,screen", [(mg.BF16, 0), (mg.BF16, 1), (mg.BF16, 2), (mg.BF16, 3),
+                                         (mg.BF16X1, 0)])
+def test_sweep_radii_share_a_count_pass(prec, screen):
+    w = synth.mixture_100k(30_000)
+    eps = [w.eps * f for f in (1.2, 0.8, 1.0, 0.9, 1.1, 1.0)]
+    ov = [w.overlap[0]] * len(eps)
+    Xd = torch.from_numpy(w.X).to("cuda:0")
+    with mg.Context(0) as ctx:
+        ctx.set_pass1_screen(screen)
+        base = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, eps[0], w.min_pts, prec)
+        graphs = mg.mapper_graph_sweep(ctx, Xd, base, eps, ov)
+        band = 0
+        for g, e in zip(graphs, eps):
+            got, ref = _against_oracle(w, g, w.n_intervals, ov[0], e, w.min_pts)
+            assert len(ref["node_elem"]) > 0
+            band += g.stats()["band_pairs"]
+        assert band > 0
+
+
+# The fused count pass without neighbour lists (minPts 1: no lists; minPts
+# 70: no lists, border rows from pass 3) and with the band queue far smaller
+# than the band (pairs past it decided in FP64 inside the kernel).
+@pytest.mark.parametrize("min_pts,queue_cap", [(1, 0), (70, 0), (10, 64)])
+def test_sweep_radii_lists_and_queue(min_pts, queue_cap):
+    w = synth.mixture_100k(30_000)
+    eps = [w.eps * f for f in (0.85, 1.0, 1.15)]
+    ov = [w.overlap[0]] * len(eps)
+    Xd = torch.from_numpy(w.X).to("cuda:0")
+    with mg.Context(0) as ctx:
+        if queue_cap:
+            ctx.set_band_queue_cap(queue_cap)
+        base = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, eps[0], min_pts, mg.BF16)
+        graphs = mg.mapper_graph_sweep(ctx, Xd, base, eps, ov)
+        for g, e in zip(graphs, eps):
+            _against_oracle(w, g, w.n_intervals, ov[0], e, min_pts)
+            if queue_cap:
+                assert g.stats()["band_pairs"] > 4 * queue_cap
+
+
+# Cross-segment pairs (scattered points and a halo of outliers around
+# clusters) on the tensor cores with their own operands, radii fused, and on
+# CUDA cores; then the FP8 screen on a 2D lens, whose sweep runs one count
+# pass per radius.
+def _halo_cloud(seed=55):
+    X = synth.gaussian_mixture(6000, 32, 6, seed=seed, centre_box=6.0, std_lo=0.4, std_hi=0.9, anisotropic=False)
+    rng = np.random.default_rng(seed + 1)
+    lo, hi = X.min(axis=0) * 2.0, X.max(axis=0) * 2.0
+    r = 5.0 * synth.eps_at_percentile(X, 3, seed, n_pairs=6000)
+    u = rng.standard_normal((2500, 32))
+    u *= r / np.linalg.norm(u, axis=1, keepdims=True)
+    Y = np.concatenate([X, rng.uniform(lo, hi, size=(1000, 32)).astype(np.float32),
+                        (X[rng.integers(0, 6000, size=2500)] + u).astype(np.float32)])
+    return np.ascontiguousarray(Y[rng.permutation(Y.shape[0])])
+
+
+@pytest.mark.parametrize("prec,cross", [(mg.BF16, 1), (mg.BF16, 2), (mg.BF16X1, 1)])
+def test_sweep_radii_cross_segment_pairs(prec, cross):
+    X = _halo_cloud()
+    w = synth.Workload("halo", X, (mg.LENS_L2,), (0,), (2,), (0.2,), 1.0, 4)
+    eps = [synth.eps_at_percentile(X, q, 55, n_pairs=8000) for q in (2.5, 3.0, 3.5)]
+    ov = [0.2] * len(eps)
+    with mg.Context(0) as ctx:
+        ctx.set_cross_screen(cross)
+        base = mg.params(w.lens_kind, w.lens_arg, (2,), (0.2,), eps[0], 4, prec)
+        graphs = mg.mapper_graph_sweep(ctx, torch.from_numpy(X).to("cuda:0"), base, eps, ov)
+        for g, e in zip(graphs, eps):
+            _against_oracle(w, g, (2,), 0.2, e, 4)
+            st = g.stats()
+            assert st["tile_pairs_cross"] == (st["tile_pairs_simt"] if cross == 1 else 0)
+            if cross == 1:
+                assert st["tile_pairs_cross"] > 0
+
+
+def test_sweep_radii_fp8_2d():
+    w = synth.zipf_mixture_500k(20_000)
+    sq = synth.pair_sample(w.X, 3, 20_000)
+    eps = [synth.eps_from_sample(sq, q) for q in (0.7, 1.0, 1.4)]
+    ov = [0.3] * len(eps)
+    Xd = torch.from_numpy(w.X).to("cuda:0")
+    with mg.Context(0) as ctx:
+        base = mg.params(w.lens_kind, w.lens_arg, (8, 8), (0.3, 0.3), eps[0], w.min_pts, mg.FP8)
+        graphs = mg.mapper_graph_sweep(ctx, Xd, base, eps, ov)
+        for g, e in zip(graphs, eps):
+            _against_oracle(w, g, (8, 8), 0.3, e, w.min_pts)
