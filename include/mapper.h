@@ -408,8 +408,11 @@ int mapper_graph(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t 
  * parameters): n_sweep graphs of one cloud, graph i with radius eps[i] and
  * overlap[i] (for every filter dimension), the other parameters from
  * `params`. The lens is computed once, the cover and the tile layout once per
- * distinct overlap and shared by its radii. out: n_sweep handles (each
- * released with mapper_free). Results equal n_sweep mapper_graph calls. */
+ * distinct overlap and shared by its radii; on the BF16 screens (MAPPER_BF16,
+ * MAPPER_BF16X1) up to four distinct radii of one overlap also share one
+ * count pass (one contraction, each radius decided in its epilogue). out:
+ * n_sweep handles (each released with mapper_free; graphs of equal (eps,
+ * overlap) share their clusters). Results equal n_sweep mapper_graph calls. */
 int mapper_graph_sweep(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int64_t ld,
                        const mapper_params* params, int32_t n_sweep, const double* eps, const double* overlap,
                        mapper_graph_t** out);
