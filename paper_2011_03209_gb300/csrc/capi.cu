@@ -382,9 +382,10 @@ int sample_deferral(const mapper_ctx* ctx, const PassArgs& a, const TcArgs& firs
 // items of one pair (an M = 128, N = 128 product) or of two pairs sharing
 // tile A (N = 256, tile A loaded once); which is faster depends on the row
 // pitch (MMA work per pair against the fixed epilogue work) and the number of
-// products. The first call for a (pitch, products) key times both shapes on
-// a prefix of its own pair list, into scratch outputs, and the context keeps
-// the faster; lists too short to time take N = 256 without caching.
+// products. The first call for a (pitch, products, screen format, one radius
+// or several) key times both shapes on a prefix of its own pair list, into
+// scratch outputs, and the context keeps the faster; lists too short to time
+// take N = 256 without caching.
 int tune_pass1(mapper_ctx* ctx, const PassArgs& a, const TcArgs& t, int64_t n_pairs, int64_t R, int cap,
                cudaStream_t s, int* tile_n)
 {
@@ -392,7 +393,8 @@ int tune_pass1(mapper_ctx* ctx, const PassArgs& a, const TcArgs& t, int64_t n_pa
         *tile_n = ctx->pass1_forced;
         return MAPPER_OK;
     }
-    const uint64_t key = ((uint64_t)a.dp << 8) | ((uint64_t)t.f8 << 4) | (uint64_t)t.ns;
+    const uint64_t key = ((uint64_t)a.dp << 8) | ((uint64_t)(t.n_radii > 1) << 5) | ((uint64_t)t.f8 << 4) |
+                         (uint64_t)t.ns;
     auto it = ctx->pass1_tile_n.find(key);
     if (it != ctx->pass1_tile_n.end()) {
         *tile_n = it->second;
@@ -421,6 +423,11 @@ int tune_pass1(mapper_ctx* ctx, const PassArgs& a, const TcArgs& t, int64_t n_pa
     ts.queue = q.as<uint2>();
     ts.queue_n = qn.as<unsigned long long>();
     ts.queue_cap = qcap;
+    // several radii: the kernel over several radii is timed, every radius
+    // writing the same scratch outputs
+    for (int e = 0; e < ts.n_radii; ++e)
+        ts.radii[e] = RadiusOut{cnt.as<int32_t>(), nbr.as<int32_t>(), hit.as<uint8_t>(), q.as<uint2>(),
+                                qn.as<unsigned long long>(), st.as<unsigned long long>(), ts.radii[e].eps2};
     ts.err = err.as<int>();
     ts.groups = nullptr;
     ts.groups_dev = nullptr;
@@ -453,7 +460,7 @@ int tune_pass1(mapper_ctx* ctx, const PassArgs& a, const TcArgs& t, int64_t n_pa
             tv.n_groups = n_t;
             tv.groups_dev = reinterpret_cast<const unsigned long long*>(gpos.as<int64_t>() + n_t);
         }
-        int rc = tc_pass(1, as, tv, n_t, s);
+        int rc = tc_pass(ts.n_radii > 0 ? 5 : 1, as, tv, n_t, s);
         if (rc) return rc;
     }
     int h_err = 0;
@@ -754,10 +761,11 @@ int run_cluster_radii(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int
     if (two_phase) tx_tune.ns = 1;
     t_tune.defer = tx_tune.defer = two_phase;                    // timed as the first phase runs
     t_tune.defer_mixed = tx_tune.defer_mixed = defer_mixed;
-    if (use_tc && PL.n[kListTC] > 0 && (rc = tune_pass1(ctx, a_tc, t_tune, PL.n[kListTC], R, cap, s, &tile_n)))
+    if (use_tc && PL.n[kListTC] > 0 &&
+        (rc = tune_pass1(ctx, a_tc, with_radii(t_tune, false, true), PL.n[kListTC], R, cap, s, &tile_n)))
         return rc;
     if (use_tc && PL.n[kListTC] == 0 && cross_tc &&
-        (rc = tune_pass1(ctx, a_simt, tx_tune, PL.n[kListSimt], R, cap, s, &tile_n)))
+        (rc = tune_pass1(ctx, a_simt, with_radii(tx_tune, true, true), PL.n[kListSimt], R, cap, s, &tile_n)))
         return rc;
     pt.mark();                                                    // 1
     for (int e = 0; e < K; ++e) CK(allin_pass(1, rs[e].a_in, PL.n[kListAllIn], s), "pass 1 all-in");

@@ -922,7 +922,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                     it.na2 = P.rn2[row];
                     it.nra = P.rn[row];
                     it.rla = P.rl ? P.rl[row] : 0.f;
-                    it.pre_row = MODE == 1 && A.cap > 0 ? A.count[row] : INT_MAX;
+                    if constexpr (MODE == 5) {
+                        // bit e: radius e's list of this row is full (its count can only grow)
+                        int full = A.cap > 0 ? 0 : 0xF;
+#pragma unroll
+                        for (int e = 0; e < kMaxRadii; ++e)
+                            if (A.cap > 0 && e < P.n_rad && P.rad[e].count[row] >= A.cap) full |= 1 << e;
+                        it.pre_row = full;
+                    } else {
+                        it.pre_row = MODE == 1 && A.cap > 0 ? A.count[row] : INT_MAX;
+                    }
                     it.sa = F ? P.tmax[tp.x].w : 1.f;
                 }
                 it.nb[h] = A.tile_n[it.tb[h]];
@@ -934,7 +943,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                 it.bl[h] = tm.z;
                 it.sb[h] = tm.w;
                 it.bmin2[h] = P.tn2min[it.tb[h]];
-                it.pre_col[h] = MODE == 1 && A.cap > 0 && it.mine[h] && tp.x != it.tb[h] ? A.count[col] : INT_MAX;
+                if constexpr (MODE == 5) {
+                    // (W = 2: rows only; the columns' reads would not fit the registers)
+                    int full = A.cap > 0 ? 0 : 0xF;
+                    if constexpr (W == 1) {
+#pragma unroll
+                        for (int e = 0; e < kMaxRadii; ++e)
+                            if (A.cap > 0 && it.mine[h] && tp.x != it.tb[h] && e < P.n_rad &&
+                                P.rad[e].count[col] >= A.cap)
+                                full |= 1 << e;
+                    }
+                    it.pre_col[h] = full;
+                } else {
+                    it.pre_col[h] = MODE == 1 && A.cap > 0 && it.mine[h] && tp.x != it.tb[h] ? A.count[col] : INT_MAX;
+                }
             }
         };
         int64_t screened = 0;
@@ -1102,14 +1124,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                                                              fl, &decided);
                             if (decided && in) inb |= 1u << i;
                         }
+                        // counts, and list entries while the list has room (read
+                        // before the item: a full list takes no returning atomic)
                         const int k = __popc(inb);
                         if (k) {
-                            int pos = atomicAdd(&cnt[row], k);
-                            uint32_t bm = inb;
-                            while (bm && pos < A.cap) {
-                                const int i = __ffs(bm) - 1;
-                                bm &= bm - 1;
-                                nbl[row * A.cap + pos++] = (int32_t)(sb + part * 32 + i);
+                            if ((cur.pre_row >> e) & 1) {
+                                atomicAdd(&cnt[row], k);
+                            } else {
+                                int pos = atomicAdd(&cnt[row], k);
+                                uint32_t bm = inb;
+                                while (bm && pos < A.cap) {
+                                    const int i = __ffs(bm) - 1;
+                                    bm &= bm - 1;
+                                    nbl[row * A.cap + pos++] = (int32_t)(sb + part * 32 + i);
+                                }
                             }
                         }
                         if (!diag && __any_sync(0xffffffffu, inb != 0u)) {
@@ -1123,11 +1151,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
                             }
                             const int kc = __popc(x);
                             if (kc) {
-                                int pos = atomicAdd(&cnt[col], kc);
-                                while (x && pos < A.cap) {
-                                    const int i = __ffs(x) - 1;
-                                    x &= x - 1;
-                                    nbl[col * A.cap + pos++] = (int32_t)(sa + quad * 32 + i);
+                                if ((cur.pre_col[h] >> e) & 1) {
+                                    atomicAdd(&cnt[col], kc);
+                                } else {
+                                    int pos = atomicAdd(&cnt[col], kc);
+                                    while (x && pos < A.cap) {
+                                        const int i = __ffs(x) - 1;
+                                        x &= x - 1;
+                                        nbl[col * A.cap + pos++] = (int32_t)(sa + quad * 32 + i);
+                                    }
                                 }
                             }
                         }
