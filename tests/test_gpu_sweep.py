@@ -142,3 +142,36 @@ def test_sweep_radii_fp8_2d():
         graphs = mg.mapper_graph_sweep(ctx, Xd, base, eps, ov)
         for g, e in zip(graphs, eps):
             _against_oracle(w, g, (8, 8), 0.3, e, w.min_pts)
+
+
+# The bench's 16-graph sweep at full size (500k x 128, (PC1, PC2) on a 30 x 30
+# grid, four radii fused per overlap): the cover of each overlap bit for bit
+# and the DBSCAN of two sampled elements of every graph against the oracle,
+# and every graph equal to its own single call on two of the radii.
+@pytest.mark.slow
+def test_sweep_500k_grid_fused_radii_sampled():
+    w, eps, ov = synth.zipf_sweep()
+    Xd = torch.from_numpy(w.X).to("cuda:0")
+    rng = np.random.default_rng(11)
+    with mg.Context(0) as ctx:
+        base = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, eps[0], w.min_pts, mg.BF16)
+        graphs = mg.mapper_graph_sweep(ctx, Xd, base, eps, ov)
+        lens, _ = graphs[0].lens(w.n, 2)
+        covers = {}
+        for k, (g, e, p) in enumerate(zip(graphs, eps, ov)):
+            offs, pts = g.cover().numpy()
+            if p not in covers:
+                ro, rp = oracle.cover(lens, w.n_intervals, (p, p))
+                assert np.array_equal(ro, offs) and np.array_equal(rp, pts), p
+                covers[p] = True
+            lab, core = g.clusters().numpy(len(pts))
+            sizes = np.diff(offs)
+            cand = np.nonzero((sizes > 0) & (sizes <= 3000))[0]
+            for el in rng.choice(cand, 2, replace=False):
+                s0, t0 = offs[el], offs[el + 1]
+                _, rc, rl, _ = oracle.dbscan(w.X, pts[s0:t0], e, w.min_pts)
+                assert np.array_equal(rc, core[s0:t0]) and np.array_equal(rl, lab[s0:t0]), (k, el)
+        for k in (3, 12):
+            one = mg.mapper_graph(ctx, Xd, mg.params(w.lens_kind, w.lens_arg, w.n_intervals, (ov[k], ov[k]), eps[k],
+                                                     w.min_pts, mg.BF16))
+            _same(graphs[k].numpy(), one.numpy())
