@@ -175,3 +175,29 @@ def test_sweep_500k_grid_fused_radii_sampled():
             one = mg.mapper_graph(ctx, Xd, mg.params(w.lens_kind, w.lens_arg, w.n_intervals, (ov[k], ov[k]), eps[k],
                                                      w.min_pts, mg.BF16))
             _same(graphs[k].numpy(), one.numpy())
+
+
+# Radii from below the nearest-neighbour distance (no pair in) to beyond the
+# cloud's diameter in parts (every pair in), on rows of odd width (padded
+# operand columns), two overlaps and two screens: the fused pass's early exit
+# at the smaller radii and the all-in lists of the larger ones.
+@pytest.mark.parametrize("prec", [mg.BF16, mg.BF16X1])
+def test_sweep_radii_extremes_odd_width(prec):
+    X = synth.gaussian_mixture(3000, 37, 5, seed=21, centre_box=8.0, std_lo=0.3, std_hi=1.2, anisotropic=True)
+    w = synth.Workload("odd", X, (mg.LENS_L2,), (0,), (6,), (0.3,), 1.0, 4)
+    sq = synth.pair_sample(X, 5, 20_000)
+    Y = X.astype(np.float64)
+    g2 = (Y * Y).sum(1)
+    d2 = g2[:, None] + g2[None, :] - 2.0 * Y @ Y.T
+    np.fill_diagonal(d2, np.inf)
+    nearest = float(np.sqrt(max(d2.min(), 0.0)))               # every pair is farther than this
+    diameter = 2.0 * float(np.sqrt(((Y - Y.mean(0)) ** 2).sum(1).max()))   # no pair is farther
+    radii = [0.5 * nearest, synth.eps_from_sample(sq, 1.0), synth.eps_from_sample(sq, 20.0), 1.01 * diameter]
+    eps = radii * 2
+    ov = [0.3] * 4 + [0.15] * 4
+    with mg.Context(0) as ctx:
+        base = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, eps[0], w.min_pts, prec)
+        graphs = mg.mapper_graph_sweep(ctx, torch.from_numpy(X).to("cuda:0"), base, eps, ov)
+        for g, e, p in zip(graphs, eps, ov):
+            got, ref = _against_oracle(w, g, w.n_intervals, p, e, w.min_pts)
+        assert graphs[0].stats()["n_core"] == 0 and graphs[3].stats()["tile_pairs_out"] == 0
