@@ -201,3 +201,6 @@ def test_sweep_radii_extremes_odd_width(prec):
         for g, e, p in zip(graphs, eps, ov):
             got, ref = _against_oracle(w, g, w.n_intervals, p, e, w.min_pts)
         assert graphs[0].stats()["n_core"] == 0 and graphs[3].stats()["tile_pairs_out"] == 0
+        # the same sweep from host memory (copied inside the call)
+        for gh, g in zip(mg.mapper_graph_sweep(ctx, X, base, eps, ov), graphs):
+            _same(gh.numpy(), g.numpy())
