@@ -50,8 +50,9 @@ def _traffic(st):
         return None
     if not st.get("tile_pairs_screen1") or "bytes_per_tile_pair_first" not in rec:
         return None
+    # pairs sent straight to three products move the second phase's bytes
     return (rec["bytes_per_tile_pair_first"] * st["tile_pairs_screen1"] +
-            rec["bytes_per_tile_pair_second"] * st["tile_pairs_redo"])
+            rec["bytes_per_tile_pair_second"] * (st["tile_pairs_redo"] + st.get("tile_pairs_direct", 0)))
 
 
 def _bind_local_cpus(device: int):
@@ -384,7 +385,7 @@ def run_ours(args):
                                         "tile_pairs_simt", "union_pairs", "union_skipped", "pairs_screened",
                                         "band_pairs", "fp64_pairs", "near_ties", "n_core", "n_nodes", "n_edges",
                                         "pass1_tile_n", "tile_pairs_cross") + tuple(
-                                            k for k in ("tile_pairs_screen1", "tile_pairs_redo", "redo_blocks", "redo_parts") if k in st)},
+                                            k for k in ("tile_pairs_screen1", "tile_pairs_redo", "redo_blocks", "redo_parts", "tile_pairs_direct") if k in st)},
         "ms_tiles": float(np.mean([s["ms_tiles"] for s in stats])),
         "roofline": roof,
         "clocks": clocks,

@@ -63,7 +63,7 @@
 extern "C" {
 #endif
 
-#define MAPPER_ABI_VERSION 5
+#define MAPPER_ABI_VERSION 6
 
 typedef enum mapper_status {
     MAPPER_OK = 0,
@@ -195,8 +195,15 @@ typedef struct mapper_stats {
                                     three products for its deferred blocks) or 1 (three products);
                                     0 off the tensor cores */
     double pass1_sample_deferred; /* pass-1 screen 0: the fraction of a sample of the tile pairs
-                                     whose first screen deferred a block (one phase above 0.35);
-                                     -1 when no sample ran */
+                                     whose first screen deferred a block; -1 when no sample ran.
+                                     MAPPER_BF16 with one radius: one phase or two, and the pairs
+                                     sent straight to three products, follow the sample's
+                                     fractions per bin of the tile-pair statistic below; otherwise
+                                     one phase above 0.35 */
+    int64_t tile_pairs_direct;    /* pass-1 screen 0, two phases (MAPPER_BF16): tensor-core tile
+                                     pairs sent straight to three products, those whose bin of
+                                     (|c_a - c_b|^2 + r_a^2 + r_b^2) / eps^2 (tile spheres) deferred
+                                     a block in at least half of its sampled pairs */
 } mapper_stats;
 
 /* ---------------------------------------------------------------- context */

@@ -103,6 +103,7 @@ class MapperStats(ctypes.Structure):
         ("redo_parts", ctypes.c_int64),
         ("pass1_phases", ctypes.c_int64),
         ("pass1_sample_deferred", ctypes.c_double),
+        ("tile_pairs_direct", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:

@@ -315,9 +315,24 @@ int run_cover(mapper_ctx* ctx, const double* lens, int64_t n, int32_t m, const i
 // than kSampleMinPairs keep two phases.
 constexpr double kDeferMax = 0.35;
 constexpr int64_t kSampleMinPairs = 8192;
+// Within a two-phase pass (MAPPER_BF16), the sample also decides per bin of
+// the tile-pair statistic (pair_bins): a pair skipping the first phase saves
+// its one-product screen (~0.55 T3/pair) and costs a three-product screen
+// (T3/pair) when it would not have deferred, so bins whose sampled pairs
+// deferred a block at least kDirectRate of the time (with at least
+// kDirectSamples sampled pairs) go straight to three products.
+// The same rates then choose one phase or two: two when the estimate
+// sum over sampled pairs of (1 if its bin goes straight, else kPhase1Cost +
+// its bin's deferred fraction), in T3 units per pair, is below kTwoPhaseGain
+// per pair (one phase costs 1).
+constexpr double kDirectRate = 0.5;
+constexpr unsigned long long kDirectSamples = 16;
+constexpr double kPhase1Cost = 0.55;
+constexpr double kTwoPhaseGain = 0.97;
 
 int sample_deferral(const mapper_ctx* ctx, const PassArgs& a, const TcArgs& first, int64_t n_pairs, int64_t R,
-                    int cap, cudaStream_t s, double* frac)
+                    int cap, cudaStream_t s, double* frac, const uint8_t* bins = nullptr,
+                    unsigned long long* h_bins = nullptr)
 {
     (void)ctx;
     const int64_t n_s = std::min<int64_t>(std::max<int64_t>(n_pairs / 64, 2048), n_pairs);
@@ -369,6 +384,13 @@ int sample_deferral(const mapper_ctx* ctx, const PassArgs& a, const TcArgs& firs
     if ((rc = tc_pass(ts.n_radii > 0 ? 5 : 1, as, ts, n_s, s))) return rc;
     unsigned long long h_redo = 0;
     int h_err = 0;
+    Buf bc;
+    if (bins && h_bins) {
+        CK(bc.alloc(sizeof(unsigned long long) * 2 * kPairBins, s), "alloc");
+        CK(sample_bins(mask.as<uint32_t>(), n_s, bins, stride, bc.as<unsigned long long>(), s), "sample bins");
+        CK(cudaMemcpyAsync(h_bins, bc.p, sizeof(unsigned long long) * 2 * kPairBins, cudaMemcpyDeviceToHost, s),
+           "copy");
+    }
     CK(cudaMemcpyAsync(&h_redo, st.as<unsigned long long>() + kStatRedo, sizeof(h_redo), cudaMemcpyDeviceToHost, s),
        "copy");
     CK(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
@@ -737,13 +759,52 @@ int run_cluster_radii(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int
     // default screen: two phases or one, from a sample of the first phase
     const bool defer_mixed = ctx->screen_mode == 3 || ctx->screen_mode == 0;
     st.pass1_sample_deferred = -1.0;
+    int64_t n_direct = 0;                                         // TC-list pairs straight to three products
     if (two_phase && ctx->screen_mode == 0 && PL.n[kListTC] >= kSampleMinPairs) {
         double f = 0.0;
-        if ((rc = sample_deferral(ctx, a_tc, with_radii(f8 ? t8 : t, false, true), PL.n[kListTC], R, cap, s, &f)))
+        const int64_t n = PL.n[kListTC];
+        const bool per_bin = K == 1 && !f8;
+        Buf bins;
+        unsigned long long h_bins[2 * kPairBins] = {};
+        if (per_bin) {
+            CK(bins.alloc(n, s), "alloc");
+            CK(pair_bins(L, PL.list[kListTC].as<int2>(), n, dp, eps_max, bins.as<uint8_t>(), s), "pair bins");
+        }
+        if ((rc = sample_deferral(ctx, a_tc, with_radii(f8 ? t8 : t, false, true), n, R, cap, s, &f,
+                                  per_bin ? bins.as<uint8_t>() : nullptr, per_bin ? h_bins : nullptr)))
             return rc;
         st.pass1_sample_deferred = f;
-        if (f > kDeferMax) two_phase = false;
+        uint8_t chosen[kPairBins] = {};
+        bool any = false;
+        if (per_bin) {
+            double est_one = 0.0, est_two = 0.0;
+            for (int b = 0; b < kPairBins; ++b) {
+                const double c = (double)h_bins[2 * b];
+                if (c == 0.0) continue;
+                const double p = (double)h_bins[2 * b + 1] / c;
+                chosen[b] = h_bins[2 * b] >= kDirectSamples && p >= kDirectRate;
+                est_one += c;
+                est_two += chosen[b] ? c : c * (kPhase1Cost + p);
+            }
+            two_phase = est_two < kTwoPhaseGain * est_one;
+            for (int b = 0; two_phase && b < kPairBins; ++b) any |= chosen[b] != 0;
+        } else if (f > kDeferMax) {
+            two_phase = false;
+        }
+        if (any) {
+            // the chosen bins' pairs first (list order kept within each part)
+            Buf dchosen, part, pos;
+            CK(dchosen.alloc(kPairBins, s), "alloc");
+            CK(part.alloc(sizeof(int2) * n, s), "alloc");
+            CK(cudaMemcpyAsync(dchosen.p, chosen, kPairBins, cudaMemcpyHostToDevice, s), "copy");
+            CK(partition_pairs(PL.list[kListTC].as<int2>(), bins.as<uint8_t>(), dchosen.as<uint8_t>(), n,
+                               part.as<int2>(), &pos, s), "partition");
+            CK(cudaMemcpyAsync(PL.list[kListTC].p, part.p, sizeof(int2) * n, cudaMemcpyDeviceToDevice, s), "copy");
+            CK(cudaMemcpyAsync(&n_direct, pos.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "copy");
+            CK(cudaStreamSynchronize(s), "sync");
+        }
     }
+    st.tile_pairs_direct = n_direct;
     st.pass1_phases = use_tc ? (two_phase ? 2 : 1) : 0;
     Buf redo, redo_mask, redo_q;
     if (two_phase) {
@@ -782,10 +843,10 @@ int run_cluster_radii(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int
     // pass 1 on the tensor cores of one pair list (its events bracket the
     // count kernels: both lists' launches when the cross list runs there)
     auto tc_count = [&](const PassArgs& pa, const TcArgs& base, const TcArgs& first_screen, int64_t np, Buf& gr,
-                        Buf& gp, bool first, bool last, bool simt_list) -> int {
+                        Buf& gp, bool first, bool last, bool simt_list, bool two) -> int {
         TcArgs t1 = with_radii(first_screen, simt_list, true);
         t1.ev_begin = first ? tev[0] : nullptr;
-        t1.ev_end = last && !two_phase ? tev[1] : nullptr;
+        t1.ev_end = last && !two ? tev[1] : nullptr;
         if (tile_n == 256) {
             int r2;
             if ((r2 = tc_groups(pa.pairs, np, &gr, &gp, s))) return r2;
@@ -793,7 +854,7 @@ int run_cluster_radii(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int
             t1.n_groups = np;
             t1.groups_dev = reinterpret_cast<const unsigned long long*>(gp.as<int64_t>() + np);
         }
-        if (!two_phase) return tc_pass(count_mode, pa, t1, np, s);
+        if (!two) return tc_pass(count_mode, pa, t1, np, s);
         if (!t1.f8) t1.ns = 1;
         t1.defer = true;
         t1.defer_mixed = defer_mixed;
@@ -831,11 +892,20 @@ int run_cluster_radii(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int
     };
     if (use_tc) {
         const bool x_last = cross_tc && PL.n[kListSimt] > 0;
-        if (PL.n[kListTC] > 0 &&
-            (rc = tc_count(a_tc, t, first_f8 ? t8 : t, PL.n[kListTC], groups, group_pos, true, !x_last, false)))
+        const int64_t n_rest = PL.n[kListTC] - n_direct;
+        Buf dgroups, dgroup_pos;
+        // the pairs sent straight to three products, then the rest in the chosen phases
+        if (n_direct > 0 &&
+            (rc = tc_count(a_tc, t, t, n_direct, dgroups, dgroup_pos, true, n_rest == 0 && !x_last, false, false)))
             return rc;
-        if (x_last &&
-            (rc = tc_count(a_simt, tx, tx, PL.n[kListSimt], xgroups, xgroup_pos, PL.n[kListTC] == 0, true, true)))
+        PassArgs a_rest = a_tc;
+        a_rest.pairs += n_direct;
+        a_rest.pair_hit += n_direct;
+        if (n_rest > 0 && (rc = tc_count(a_rest, t, first_f8 ? t8 : t, n_rest, groups, group_pos, n_direct == 0,
+                                         !x_last, false, two_phase)))
+            return rc;
+        if (x_last && (rc = tc_count(a_simt, tx, tx, PL.n[kListSimt], xgroups, xgroup_pos, PL.n[kListTC] == 0, true,
+                                     true, two_phase)))
             return rc;
     }
     else CK(simt_pass(1, rs[0].a_tc, PL.n[kListTC], s), "pass 1 tc list");
@@ -984,7 +1054,7 @@ int run_cluster_radii(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int
         sr.union_pairs = (int64_t)h_stats[kStatUnion];
         sr.pass1_tile_n = tile_n;
         sr.n_rows = R;
-        sr.tile_pairs_screen1 = two_phase ? PL.n[kListTC] + (cross_tc ? PL.n[kListSimt] : 0) : 0;
+        sr.tile_pairs_screen1 = two_phase ? PL.n[kListTC] - n_direct + (cross_tc ? PL.n[kListSimt] : 0) : 0;
         sr.tile_pairs_redo = (int64_t)h_stats[kStatRedo];
         sr.redo_blocks = (int64_t)h_stats[kStatRedoBlocks];
         sr.redo_parts = (int64_t)h_stats[kStatRedoParts];

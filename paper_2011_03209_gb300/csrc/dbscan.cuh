@@ -237,6 +237,22 @@ int build_tiles(const float* X, int64_t n, int32_t d, int64_t ld, int dp, const 
 // lists; out stays decided at eps, the largest).
 int classify_pairs(const TileLayout& L, const float* X, int64_t ld, int d, int dp, int64_t E, double eps,
                    bool use_tc, PairLists* P, cudaStream_t s, double eps_all_in = 0.0);
+// Count-pass phase choice per tile pair: bin[q] (< kPairBins) of the pair's
+// statistic (|c_a - c_b|^2 + r_a^2 + r_b^2) / eps^2 from the layout's tile
+// spheres, on a log2 scale of 8 bins per octave from 2^-4.
+constexpr int kPairBins = 64;
+cudaError_t pair_bins(const TileLayout& L, const int2* pairs, int64_t n, int dp, double eps, uint8_t* bin,
+                      cudaStream_t s);
+// Tally of a sample of the list (sample pair j = list pair j * stride, mask[j]
+// its first phase's deferred blocks): cnt[2 b] sampled pairs of bin b,
+// cnt[2 b + 1] of them that deferred a block (2 kPairBins counters, zeroed here).
+cudaError_t sample_bins(const uint32_t* mask, int64_t n_s, const uint8_t* bin, int64_t stride,
+                        unsigned long long* cnt, cudaStream_t s);
+// Stable partition of pairs[0 .. n): those whose bin is chosen (chosen: kPairBins
+// bytes on the device) first, then the rest, into out; *pos receives [n + 1]
+// int64 with their number at pos[n].
+cudaError_t partition_pairs(const int2* pairs, const uint8_t* bin, const uint8_t* chosen, int64_t n, int2* out,
+                            Buf* pos, cudaStream_t s);
 // FP8 E4M3 operands of a tile layout built with BF16 operands (needs its
 // centres and tmax): per tile a power-of-two scale s, hi and lo parts of a / s
 // (Fh, Fl), frl and ftmax. A no-op when already built. Returns a mapper_status.

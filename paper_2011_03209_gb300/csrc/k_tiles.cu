@@ -965,6 +965,69 @@ __global__ void __launch_bounds__(256) classify_blk_kernel(const int64_t* __rest
     if (threadIdx.x == 0 && s_out) atomicAdd(&counts[3], s_out);
 }
 
+// Bin of a tile pair's statistic s = (|c_a - c_b|^2 + r_a^2 + r_b^2) / eps^2
+// (tile centres and radii): where rows concentrate around their tile centre,
+// as in high dimension, s is about the typical squared distance of the
+// pair's rows over eps^2, so s near 1 means rows whose distances straddle
+// eps. bin = floor(8 (log2 s + 4)) clamped to [0, kPairBins), in FP32 (a
+// binning, decided by no result; FP64 on one lane would cost the FP64 pipe a
+// whole warp's issue). A warp per pair.
+__global__ void __launch_bounds__(256) pair_bin_kernel(const int2* __restrict__ pairs, int64_t n,
+                                                       const float* __restrict__ cent,
+                                                       const double* __restrict__ rad, int dp, float inv_eps2,
+                                                       uint8_t* __restrict__ bin)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= n) return;
+    const int2 tp = pairs[q];
+    const int a = tp.x, b = tp.y & kPairTileMask;
+    const float* ca = cent + (int64_t)a * dp;
+    const float* cb = cent + (int64_t)b * dp;
+    float d2 = 0.f;
+    for (int k = lane; k < dp; k += 32) {
+        const float t = ca[k] - cb[k];
+        d2 = fmaf(t, t, d2);
+    }
+    for (int o = 16; o; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    if (lane == 0) {
+        const float ra = (float)rad[a], rb = (float)rad[b];
+        const float s = (d2 + ra * ra + rb * rb) * inv_eps2;
+        const float l = s > 0.f ? 8.f * (__log2f(s) + 4.f) : 0.f;        // NaN and below 0: bin 0
+        bin[q] = (uint8_t)(!(l >= 0.f) ? 0 : (l >= (float)kPairBins ? kPairBins - 1 : (int)l));
+    }
+}
+
+// Per bin of the sampled pairs (pair j of the sample is pairs[j * stride] of
+// the list): cnt[2 b] sampled pairs, cnt[2 b + 1] of them with a deferred block.
+__global__ void sample_bin_kernel(const uint32_t* __restrict__ mask, int64_t n_s, const uint8_t* __restrict__ bin,
+                                  int64_t stride, unsigned long long* __restrict__ cnt)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_s) return;
+    const int b = bin[j * stride];
+    atomicAdd(&cnt[2 * b], 1ull);
+    if (mask[j]) atomicAdd(&cnt[2 * b + 1], 1ull);
+}
+
+// flag[q] = chosen[bin[q]]
+__global__ void bin_flag_kernel(const uint8_t* __restrict__ bin, int64_t n, const uint8_t* __restrict__ chosen,
+                                int32_t* __restrict__ flag)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) flag[q] = chosen[bin[q]];
+}
+
+// Stable partition: the flagged pairs first (pos = their exclusive prefix,
+// pos[n] their number), then the others, each in list order.
+__global__ void partition_kernel(const int2* __restrict__ in, int64_t n, const int32_t* __restrict__ flag,
+                                 const int64_t* __restrict__ pos, int2* __restrict__ out)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    out[flag[q] ? pos[q] : pos[n] + (q - pos[q])] = in[q];
+}
+
 // blocks of kClsA tiles per segment: cnt[g] = ceil(tiles(g) / kClsA)
 __global__ void seg_blocks_kernel(const int64_t* __restrict__ seg_toff, int64_t n_seg, int64_t* __restrict__ cnt)
 {
@@ -973,6 +1036,42 @@ __global__ void seg_blocks_kernel(const int64_t* __restrict__ seg_toff, int64_t 
 }
 
 }  // namespace
+
+cudaError_t pair_bins(const TileLayout& L, const int2* pairs, int64_t n, int dp, double eps, uint8_t* bin,
+                      cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    pair_bin_kernel<<<grid_for(n * 32), 256, 0, s>>>(pairs, n, L.tile_cent.as<float>(), L.tile_rad.as<double>(),
+                                                     dp, (float)(1.0 / (eps * eps)), bin);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t sample_bins(const uint32_t* mask, int64_t n_s, const uint8_t* bin, int64_t stride,
+                        unsigned long long* cnt, cudaStream_t s)
+{
+    MGB_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 2 * kPairBins, s));
+    if (n_s == 0) return cudaSuccess;
+    sample_bin_kernel<<<grid_for(n_s), 256, 0, s>>>(mask, n_s, bin, stride, cnt);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t partition_pairs(const int2* pairs, const uint8_t* bin, const uint8_t* chosen, int64_t n, int2* out,
+                            Buf* pos, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    Buf flag;
+    MGB_TRY(flag.alloc(sizeof(int32_t) * n, s));
+    MGB_TRY(pos->alloc(sizeof(int64_t) * (n + 1), s));
+    bin_flag_kernel<<<grid_for(n), 256, 0, s>>>(bin, n, chosen, flag.as<int32_t>());
+    note_launch();
+    MGB_TRY(cudaGetLastError());
+    MGB_TRY(exclusive_scan_i32_to_i64(flag.as<int32_t>(), pos->as<int64_t>(), n, s));
+    partition_kernel<<<grid_for(n), 256, 0, s>>>(pairs, n, flag.as<int32_t>(), pos->as<int64_t>(), out);
+    note_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t pivot_alloc(int64_t n, int dp, PivotSet* P, cudaStream_t alloc_s)
 {

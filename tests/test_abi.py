@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version_and_strings(lib):
-    assert lib.mapper_abi_version() == 5
+    assert lib.mapper_abi_version() == 6
     assert lib.mapper_strerror(0) == b"ok"
     assert lib.mapper_strerror(-4) == b"device wait timed out"
 
@@ -50,7 +50,7 @@ def test_struct_layouts_match_header():
     assert _capi.MapperParams.overlap.offset == 32
     assert _capi.MapperParams.cover_kind.offset == 64
     assert _capi.MapperParams.lens_param.offset == 72
-    assert ctypes.sizeof(_capi.MapperStats) == 8 * 40
+    assert ctypes.sizeof(_capi.MapperStats) == 8 * 41
 
 
 def test_null_and_bad_arguments_are_rejected_without_a_gpu(lib):
@@ -149,4 +149,4 @@ def test_checked_build_exports_every_symbol():
     for name in _capi.EXPORTS:
         assert hasattr(lib, name), name
     lib.mapper_abi_version.restype = ctypes.c_int
-    assert lib.mapper_abi_version() == 5
+    assert lib.mapper_abi_version() == 6

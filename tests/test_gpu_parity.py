@@ -457,8 +457,10 @@ def test_two_phase_count_pass_equals_three_products(tile_n, first):
 @pytest.mark.parametrize("first", [mg.BF16, mg.FP8])
 def test_default_screen_samples_the_first_phase(first):
     """The default count-pass screen samples the first phase on every 64th
-    tile pair and takes one phase or two from the fraction that defers a
-    block; either way the graph is the one of three products everywhere."""
+    tile pair and takes one phase or two from the fractions that defer a
+    block (per bin of the tile-pair statistic for the BF16 first phase,
+    overall for the FP8 one); either way the graph is the one of three
+    products everywhere."""
     w = synth.mixture_100k()
     Xd = torch.from_numpy(w.X).to("cuda:0")
     prm = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, first)
@@ -474,8 +476,11 @@ def test_default_screen_samples_the_first_phase(first):
     auto, three = outs
     st = auto["stats"]
     assert 0.0 <= st["pass1_sample_deferred"] <= 1.0
-    assert st["pass1_phases"] == (1 if st["pass1_sample_deferred"] > 0.35 else 2)
+    if first != mg.BF16:
+        assert st["pass1_phases"] == (1 if st["pass1_sample_deferred"] > 0.35 else 2)
+    assert st["pass1_phases"] in (1, 2)
     assert (st["tile_pairs_screen1"] > 0) == (st["pass1_phases"] == 2)
+    assert st["pass1_phases"] == 2 or st["tile_pairs_direct"] == 0
     assert three["stats"]["pass1_phases"] == 1 and three["stats"]["pass1_sample_deferred"] == -1.0
     for k in ("node_offsets", "node_members", "node_elem", "edges"):
         assert np.array_equal(auto[k], three[k]), k
@@ -548,3 +553,38 @@ def test_clusters_1m_d256_sampled(ctx, prec):
             assert res["core"][s + pos[l]] and lab[pos[l]] == l
     assert res["stats"]["near_ties"] == 0
     _check_graph_properties(res, w.n)
+
+
+def test_default_screen_sends_deferring_bins_to_three_products():
+    """On the 256-column clusters cloud the default screen's sample finds bins
+    of the tile-pair statistic whose pairs all defer a block; those pairs skip
+    the first phase. The graph equals the one of three products everywhere,
+    the first phase screens exactly the other tensor-core pairs, and two
+    sampled elements equal the oracle's DBSCAN."""
+    w = synth.clusters_1m_d256(200_000)
+    Xd = torch.from_numpy(w.X).to("cuda:0")
+    prm = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, w.eps, w.min_pts, mg.BF16)
+    outs = []
+    for mode in (0, 2):
+        with mg.Context(0) as c:
+            c.set_pass1_screen(mode)
+            g = mg.mapper_graph(c, Xd, prm)
+            out = g.numpy()
+            out["stats"] = g.stats()
+            out["elem_offsets"], out["elem_points"] = g.cover().numpy()
+            out["labels"], out["core"] = g.clusters().numpy(len(out["elem_points"]))
+            outs.append(out)
+            del g
+    auto, three = outs
+    st = auto["stats"]
+    assert st["pass1_phases"] == 2 and st["tile_pairs_direct"] > 0
+    assert st["tile_pairs_screen1"] == st["tile_pairs_tc"] - st["tile_pairs_direct"] + st["tile_pairs_cross"]
+    assert three["stats"]["tile_pairs_direct"] == 0
+    for k in ("node_offsets", "node_members", "node_elem", "edges", "labels", "core"):
+        assert np.array_equal(auto[k], three[k]), k
+    offs, pts = auto["elem_offsets"], auto["elem_points"]
+    sizes = np.diff(offs)
+    for el in np.nonzero((sizes > 500) & (sizes <= 3000))[0][:2]:
+        s0, t0 = offs[el], offs[el + 1]
+        _, rc, rl, _ = oracle.dbscan(w.X, pts[s0:t0], w.eps, w.min_pts)
+        assert np.array_equal(rc, auto["core"][s0:t0]) and np.array_equal(rl, auto["labels"][s0:t0]), el
