@@ -36,10 +36,11 @@ GPU_FP32_LANES = 128                 # FP32 lanes per SM (Blackwell)
 
 
 def _traffic(st):
-    """DRAM bytes of one count pass on the tensor cores (both phases of the
-    two-phase pass), scaled from the ncu capture recorded in
-    profiles/traffic.json by the tile pairs of each phase, or None when the
-    kernel source changed since that capture or the pass ran in one phase."""
+    """DRAM bytes of one count pass on the tensor cores (the pairs sent
+    straight to three products and both phases of the rest), scaled from the
+    ncu captures recorded in profiles/traffic.json by the tile pairs of each
+    launch, or None when the kernel source changed since those captures or
+    the pass ran in one phase."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_2011_03209_gb300", "csrc", "k_tc.cu")
@@ -50,9 +51,9 @@ def _traffic(st):
         return None
     if not st.get("tile_pairs_screen1") or "bytes_per_tile_pair_first" not in rec:
         return None
-    # pairs sent straight to three products move the second phase's bytes
     return (rec["bytes_per_tile_pair_first"] * st["tile_pairs_screen1"] +
-            rec["bytes_per_tile_pair_second"] * (st["tile_pairs_redo"] + st.get("tile_pairs_direct", 0)))
+            rec["bytes_per_tile_pair_second"] * st["tile_pairs_redo"] +
+            rec.get("bytes_per_tile_pair_direct", 0.0) * st.get("tile_pairs_direct", 0))
 
 
 def _bind_local_cpus(device: int):
@@ -275,7 +276,8 @@ def _roofline(prec, w, st, stats, n_sm):
     peak = peaks["bf16_tflops"]
     achieved = 2.0 * w.d * kpairs / (kms * 1e-3) / 1e12
     tp1 = st.get("tile_pairs_screen1", 0)
-    tp3 = st["tile_pairs_tc"] if not tp1 else st.get("tile_pairs_redo", 0)
+    # three products: the second phase's pairs and those sent straight to it
+    tp3 = st["tile_pairs_tc"] if not tp1 else st.get("tile_pairs_redo", 0) + st.get("tile_pairs_direct", 0)
     ns = 1 if prec == mg.BF16X1 else 3
     kp = -(-w.d // 64) * 64 * 128.0 * 128.0 * 2.0
     first = 3 if prec == mg.FP8 else 1                 # products of the first phase
@@ -286,8 +288,9 @@ def _roofline(prec, w, st, stats, n_sm):
                 "tc_kernel (tcgen05 FP8 E4M3 count pass): three products per pair")
     else:
         desc = ("tc_kernel count pass (tcgen05 BF16): one product per tile pair, three products for the "
-                "32 x 32 blocks the first screen leaves open (one phase or two, chosen per call from a "
-                "sample of the first phase)" if tp1 else
+                "32 x 32 blocks the first screen leaves open and for the tile pairs whose bin of the "
+                "sampled first phase mostly deferred (phases and bins chosen per call from a sample of "
+                "the first phase)" if tp1 else
                 "tc_kernel<%d,1> (tcgen05 BF16 count pass): %d BF16 products per pair" % (ns, ns))
     return kms, {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                  "frac": achieved / peak, "traffic": _traffic(st) if prec == mg.BF16 else None,
