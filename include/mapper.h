@@ -196,10 +196,9 @@ typedef struct mapper_stats {
                                     0 off the tensor cores */
     double pass1_sample_deferred; /* pass-1 screen 0: the fraction of a sample of the tile pairs
                                      whose first screen deferred a block; -1 when no sample ran.
-                                     MAPPER_BF16 with one radius: one phase or two, and the pairs
-                                     sent straight to three products, follow the sample's
-                                     fractions per bin of the tile-pair statistic below; otherwise
-                                     one phase above 0.35 */
+                                     MAPPER_BF16: one phase or two, and the pairs sent straight to
+                                     three products, follow the sample's fractions per bin of the
+                                     tile-pair statistic below; MAPPER_FP8: one phase above 0.35 */
     int64_t tile_pairs_direct;    /* pass-1 screen 0, two phases (MAPPER_BF16): tensor-core tile
                                      pairs sent straight to three products, those whose bin of
                                      (|c_a - c_b|^2 + r_a^2 + r_b^2) / eps^2 (tile spheres) deferred

@@ -729,14 +729,15 @@ int run_cluster_radii(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int
     }
     st.tile_pairs_cross = cross_tc ? PL.n[kListSimt] : 0;
     // the radii of a count pass over several (mode 5): per radius its
-    // outputs and the hit flags of one pair list (none in a second phase)
-    auto with_radii = [&](TcArgs v, bool simt_list, bool hits) {
+    // outputs and the hit flags of one pair list from pair `off` on (none in
+    // a second phase)
+    auto with_radii = [&](TcArgs v, bool simt_list, bool hits, int64_t off = 0) {
         if (K == 1) return v;
         v.n_radii = K;
         for (int e = 0; e < K; ++e) {
             Radius& rd = rs[e];
             v.radii[e] = RadiusOut{rd.a.count, rd.a.nbr,
-                                   hits ? (simt_list ? rd.a_simt.pair_hit : rd.a_tc.pair_hit) : nullptr,
+                                   hits ? (simt_list ? rd.a_simt.pair_hit : rd.a_tc.pair_hit) + off : nullptr,
                                    rd.queue.as<uint2>(), rd.queue_n.as<unsigned long long>(),
                                    rd.stats.as<unsigned long long>(), rd.a.eps2};
         }
@@ -763,7 +764,7 @@ int run_cluster_radii(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int
     if (two_phase && ctx->screen_mode == 0 && PL.n[kListTC] >= kSampleMinPairs) {
         double f = 0.0;
         const int64_t n = PL.n[kListTC];
-        const bool per_bin = K == 1 && !f8;
+        const bool per_bin = !f8;
         Buf bins;
         unsigned long long h_bins[2 * kPairBins] = {};
         if (per_bin) {
@@ -843,8 +844,8 @@ int run_cluster_radii(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int
     // pass 1 on the tensor cores of one pair list (its events bracket the
     // count kernels: both lists' launches when the cross list runs there)
     auto tc_count = [&](const PassArgs& pa, const TcArgs& base, const TcArgs& first_screen, int64_t np, Buf& gr,
-                        Buf& gp, bool first, bool last, bool simt_list, bool two) -> int {
-        TcArgs t1 = with_radii(first_screen, simt_list, true);
+                        Buf& gp, bool first, bool last, bool simt_list, bool two, int64_t off) -> int {
+        TcArgs t1 = with_radii(first_screen, simt_list, true, off);
         t1.ev_begin = first ? tev[0] : nullptr;
         t1.ev_end = last && !two ? tev[1] : nullptr;
         if (tile_n == 256) {
@@ -896,16 +897,16 @@ int run_cluster_radii(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int
         Buf dgroups, dgroup_pos;
         // the pairs sent straight to three products, then the rest in the chosen phases
         if (n_direct > 0 &&
-            (rc = tc_count(a_tc, t, t, n_direct, dgroups, dgroup_pos, true, n_rest == 0 && !x_last, false, false)))
+            (rc = tc_count(a_tc, t, t, n_direct, dgroups, dgroup_pos, true, n_rest == 0 && !x_last, false, false, 0)))
             return rc;
         PassArgs a_rest = a_tc;
         a_rest.pairs += n_direct;
         a_rest.pair_hit += n_direct;
         if (n_rest > 0 && (rc = tc_count(a_rest, t, first_f8 ? t8 : t, n_rest, groups, group_pos, n_direct == 0,
-                                         !x_last, false, two_phase)))
+                                         !x_last, false, two_phase, n_direct)))
             return rc;
         if (x_last && (rc = tc_count(a_simt, tx, tx, PL.n[kListSimt], xgroups, xgroup_pos, PL.n[kListTC] == 0, true,
-                                     true, two_phase)))
+                                     true, two_phase, 0)))
             return rc;
     }
     else CK(simt_pass(1, rs[0].a_tc, PL.n[kListTC], s), "pass 1 tc list");

@@ -204,3 +204,22 @@ def test_sweep_radii_extremes_odd_width(prec):
         # the same sweep from host memory (copied inside the call)
         for gh, g in zip(mg.mapper_graph_sweep(ctx, X, base, eps, ov), graphs):
             _same(gh.numpy(), g.numpy())
+
+
+# Radii fused on a cloud whose sample sends the tile pairs of mostly-deferring
+# bins straight to three products and runs the rest in two phases: every graph
+# equals its own single call.
+def test_sweep_radii_with_pairs_sent_straight():
+    w = synth.clusters_1m_d256(200_000)
+    eps = [w.eps * f for f in (0.9, 1.0, 1.1)]
+    ov = [w.overlap[0]] * 3
+    Xd = torch.from_numpy(w.X).to("cuda:0")
+    with mg.Context(0) as ctx:
+        base = mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, eps[0], w.min_pts, mg.BF16)
+        graphs = mg.mapper_graph_sweep(ctx, Xd, base, eps, ov)
+        st = graphs[0].stats()
+        assert st["pass1_phases"] == 2 and st["tile_pairs_direct"] > 0
+        for g, e in zip(graphs, eps):
+            one = mg.mapper_graph(ctx, Xd, mg.params(w.lens_kind, w.lens_arg, w.n_intervals, w.overlap, e,
+                                                     w.min_pts, mg.BF16))
+            _same(g.numpy(), one.numpy())
