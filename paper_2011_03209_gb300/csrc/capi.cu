@@ -829,6 +829,10 @@ int run_cluster_radii(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int
     if (use_tc && PL.n[kListTC] == 0 && cross_tc &&
         (rc = tune_pass1(ctx, a_simt, with_radii(tx_tune, true, true), PL.n[kListSimt], R, cap, s, &tile_n)))
         return rc;
+    // the pairs sent straight to three products: the shape tuned for three products
+    int tile_n_direct = tile_n;
+    if (n_direct > 0 && (rc = tune_pass1(ctx, a_tc, with_radii(t, false, true), n_direct, R, cap, s, &tile_n_direct)))
+        return rc;
     pt.mark();                                                    // 1
     for (int e = 0; e < K; ++e) CK(allin_pass(1, rs[e].a_in, PL.n[kListAllIn], s), "pass 1 all-in");
     cudaEvent_t tev[2] = {nullptr, nullptr};
@@ -844,11 +848,11 @@ int run_cluster_radii(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int
     // pass 1 on the tensor cores of one pair list (its events bracket the
     // count kernels: both lists' launches when the cross list runs there)
     auto tc_count = [&](const PassArgs& pa, const TcArgs& base, const TcArgs& first_screen, int64_t np, Buf& gr,
-                        Buf& gp, bool first, bool last, bool simt_list, bool two, int64_t off) -> int {
+                        Buf& gp, bool first, bool last, bool simt_list, bool two, int64_t off, int tn) -> int {
         TcArgs t1 = with_radii(first_screen, simt_list, true, off);
         t1.ev_begin = first ? tev[0] : nullptr;
         t1.ev_end = last && !two ? tev[1] : nullptr;
-        if (tile_n == 256) {
+        if (tn == 256) {
             int r2;
             if ((r2 = tc_groups(pa.pairs, np, &gr, &gp, s))) return r2;
             t1.groups = gr.as<int2>();
@@ -879,7 +883,7 @@ int run_cluster_radii(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int
         t2.n_groups = 0;
         t2.groups_dev = nullptr;
         t2.n_dev = n_redo;
-        if (tile_n == 256) {
+        if (tn == 256) {
             if ((r2 = tc_groups_dev(redo.as<int2>(), np, n_redo, &rgr, &rgp, s))) return r2;
             t2.groups = rgr.as<int2>();
             t2.n_groups = np;
@@ -897,16 +901,17 @@ int run_cluster_radii(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int
         Buf dgroups, dgroup_pos;
         // the pairs sent straight to three products, then the rest in the chosen phases
         if (n_direct > 0 &&
-            (rc = tc_count(a_tc, t, t, n_direct, dgroups, dgroup_pos, true, n_rest == 0 && !x_last, false, false, 0)))
+            (rc = tc_count(a_tc, t, t, n_direct, dgroups, dgroup_pos, true, n_rest == 0 && !x_last, false, false, 0,
+                           tile_n_direct)))
             return rc;
         PassArgs a_rest = a_tc;
         a_rest.pairs += n_direct;
         a_rest.pair_hit += n_direct;
         if (n_rest > 0 && (rc = tc_count(a_rest, t, first_f8 ? t8 : t, n_rest, groups, group_pos, n_direct == 0,
-                                         !x_last, false, two_phase, n_direct)))
+                                         !x_last, false, two_phase, n_direct, tile_n)))
             return rc;
         if (x_last && (rc = tc_count(a_simt, tx, tx, PL.n[kListSimt], xgroups, xgroup_pos, PL.n[kListTC] == 0, true,
-                                     true, two_phase, 0)))
+                                     true, two_phase, 0, tile_n)))
             return rc;
     }
     else CK(simt_pass(1, rs[0].a_tc, PL.n[kListTC], s), "pass 1 tc list");
