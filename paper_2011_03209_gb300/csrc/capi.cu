@@ -823,8 +823,12 @@ int run_cluster_radii(mapper_ctx* ctx, const float* X, int64_t n, int32_t d, int
     if (two_phase) tx_tune.ns = 1;
     t_tune.defer = tx_tune.defer = two_phase;                    // timed as the first phase runs
     t_tune.defer_mixed = tx_tune.defer_mixed = defer_mixed;
-    if (use_tc && PL.n[kListTC] > 0 &&
-        (rc = tune_pass1(ctx, a_tc, with_radii(t_tune, false, true), PL.n[kListTC], R, cap, s, &tile_n)))
+    // timed on the pairs the first screen will take (after those sent straight)
+    PassArgs a_first = a_tc;
+    a_first.pairs += n_direct;
+    if (use_tc && PL.n[kListTC] > n_direct &&
+        (rc = tune_pass1(ctx, a_first, with_radii(t_tune, false, true), PL.n[kListTC] - n_direct, R, cap, s,
+                         &tile_n)))
         return rc;
     if (use_tc && PL.n[kListTC] == 0 && cross_tc &&
         (rc = tune_pass1(ctx, a_simt, with_radii(tx_tune, true, true), PL.n[kListSimt], R, cap, s, &tile_n)))
